@@ -1,0 +1,87 @@
+"""The conservative angular-tile binning rule (FP32 emulation in the oracle) checked
+against FP64 truth: no pixel-Gaussian pair that can reach alpha >= 1/255 may fall in
+a tile the rule rejects, and every tile cone must contain its pixels' FP64 rays."""
+import math
+
+import numpy as np
+import pytest
+
+import synthetic as S
+
+
+def _cases():
+    c1cam, c1sc = S.c1()
+    kb = S.c3_camera(96, 96)
+    kb_sc = S.uniform_box_scene(400, seed=3)
+    blob_cam = S.pinhole(160, 90, 150.0)
+    blob_sc = S.blob_scene(3000, seed=1, cam=blob_cam)
+    ragged = S.pinhole(70, 45, 40.0, 33.0, 21.0, cam_to_world=S.look_at((0.1, 0.0, -0.5), (0.2, 0.1, 4.0)))
+    rag_sc = S.uniform_box_scene(500, seed=9, log_scale_mean=-2.5)
+    return {"c1": (c1cam, c1sc), "kb96": (kb, kb_sc), "blob160": (blob_cam, blob_sc), "ragged": (ragged, rag_sc)}
+
+
+CASES = _cases()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_binning_is_conservative(oracle_lib, name):
+    O = oracle_lib
+    cam, sc = CASES[name]
+    if name == "blob160":
+        floor_cam = S.pinhole(320, 180, 300.0)
+        sc = sc.with_rho2(O.floor_rho2([floor_cam], sc.means).astype(np.float32))
+    total, pg, pt, pas = O.bin_counts(cam, sc, dense=True)
+    pix, g = O.pairs_above(cam, sc, (1.0 / 255.0) * (1 - 1e-3))
+    assert pix.size > 0
+    tx, _ = O.tile_grid(cam)
+    tile = (pix // cam.width) // 16 * tx + (pix % cam.width) // 16
+    missed = pas[g, tile] == 0
+    assert missed.sum() == 0, f"{missed.sum()} of {pix.size} contributing pairs not binned"
+    # the rule should not be wildly loose either (pairs per contributing pair)
+    assert total == pas.sum() and total >= np.unique(g * 100000 + tile).size
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_tile_cones_contain_fp64_rays(oracle_lib, name):
+    O = oracle_lib
+    cam, _ = CASES[name]
+    table = O.tile_table(cam)
+    d, _, _, valid = O.rays(cam)
+    tx, _ = O.tile_grid(cam)
+    ii = np.arange(cam.width * cam.height)
+    tile = (ii // cam.width) // 16 * tx + (ii % cam.width) // 16
+    a = table[tile, :3].astype(float)
+    sg = table[tile, 3].astype(float)
+    chord = np.linalg.norm(a - d, axis=1)
+    ok = ~valid | (chord <= 2 * sg)
+    assert ok.all()
+    # every tile with a valid pixel is non-empty; empty tiles have no valid pixel
+    has_valid = np.bincount(tile[valid], minlength=table.shape[0]) > 0
+    assert np.array_equal(has_valid, table[:, 3] >= 0)
+    # footprint bound m >= (|dx|^2 + |dy|^2)/3 for every pixel of the tile
+    _, dx, dy, _ = O.rays(cam)
+    m = ((dx ** 2).sum(1) + (dy ** 2).sum(1)) / 3
+    assert (m[valid] <= table[tile[valid], 5]).all()
+
+
+def test_fp32_rule_directions_track_fp64(oracle_lib):
+    for cam in (S.pinhole(1280, 720, 1200.0), S.c3_camera(512, 512)):
+        rng = np.random.default_rng(0)
+        xs = rng.uniform(0, cam.width, 4000).astype(np.float32)
+        ys = rng.uniform(0, cam.height, 4000).astype(np.float32)
+        f, valid = oracle_lib.fdir(cam, xs, ys)
+        d, _, _, v64 = oracle_lib.rays(cam, xs.astype(float), ys.astype(float))
+        assert np.array_equal(valid, v64)
+        err = np.linalg.norm(f[valid] - d[valid], axis=1).max()
+        assert err < 1e-6
+
+
+def test_rule_culls_transparent_and_keeps_near(oracle_lib):
+    cam = S.pinhole(64, 48, 60.0)
+    sc = S.uniform_box_scene(3, seed=0)
+    sc.opacity_logits[:] = np.array([math.log(1 / 300.0 / (1 - 1 / 300.0)), 0.0, 0.0], np.float32)
+    sc.means[2] = np.array([0.0, 0.0, 0.01], np.float32)     # almost at the optical centre
+    recs = oracle_lib.bin_gauss(cam, sc)
+    assert recs[0, 9] == 0.0            # sigma < 1/255: can never contribute
+    total, pg, pt, _ = oracle_lib.bin_counts(cam, sc)
+    assert pg[0] == 0 and pg[2] == pt.size   # the near Gaussian covers every tile
