@@ -1,0 +1,314 @@
+"""Benchmark: anti-aliased Mrays/s of the ConeGaussian render on one B300.
+
+Workload (the headline configuration): pinhole 1280x720 (f = 1200) and the same
+camera at 1/8 resolution (160x90), 500k Gaussians drawn from the clustered
+blob + background-shell distribution, SH degree 3, per-Gaussian Eq. 11 floor
+from the 1280x720 view.  One step renders both cameras (936,000 rays).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  `value` is forward Mrays/s with inputs resident in HBM
+(L2 flushed between timed steps); `e2e` is the same metric through the
+host-buffer entry point (camera parameters in, image copied back every step).
+The reference arm times the FP64 oracle on the host cores on a bounded pixel
+sample of the same workload.  Under torchrun every rank renders its own
+replica (no collective); the value sums all ranks' rays over the slowest rank.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synthetic as S  # noqa: E402
+
+METRIC = "anti-aliased Mrays/s fwd & fwd+bwd at stated RGB err vs FP32 plain; p50/p99 ms"
+WORKLOAD = "pinhole 1280x720 + 160x90 (1/8), 500k Gaussians (64 blobs + shell), SH3, Eq.11 floor"
+# FP32 operations per pixel-Gaussian pair evaluation of the forward rasteriser,
+# counted from the per-pair code (an FMA counts as 2): ~148 for the response with
+# rho^2 = 0 (K = I/3) plus ~12 for compositing; the floor path (rho^2 > 0) adds ~52.
+FLOPS_PER_PAIR_NOFLOOR = 160
+FLOPS_PER_PAIR_FLOOR = 212
+SMS, FP32_LANES = 148, 128
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
+                if out.returncode == 0 and out.stdout.strip():
+                    self.rows.append([x.strip() for x in out.stdout.strip().split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if "Active" in r[3 + k]
+                          and "Not" not in r[3 + k]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def build_workload(n=500_000, seed=0):
+    cams = S.c2_cameras()
+    sc = S.c2_scene(n, seed=seed)
+    return cams, sc
+
+
+def cpu_baseline(cams, sc, rho2, budget_s=15.0):
+    """The FP64 oracle as it stands, on the host cores, on a bounded pixel sample."""
+    import oracle
+    sc = sc.with_rho2(rho2)
+    rng = np.random.default_rng(1)
+    cam = cams[0]
+    npx = 16
+    t = 0.0
+    while True:
+        pix = rng.choice(cam.n_pixels, size=npx, replace=False).astype(np.int32)
+        t0 = time.perf_counter()
+        oracle.render(cam, sc, pix=pix)
+        t = time.perf_counter() - t0
+        if t > budget_s / 4 or npx >= 65536:
+            break
+        npx = int(min(65536, npx * max(2.0, min(8.0, budget_s / 4 / max(t, 1e-3)))))
+    return {"value": npx / t / 1e6, "unit": "Mrays/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{npx} random pixels of the 1280x720 view (same 500k-Gaussian scene, culled FP64 oracle)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    cams, sc = build_workload()
+    import oracle
+    rho2 = oracle.floor_rho2([cams[0]], sc.means).astype(np.float32)
+    # size each step to ~ (a few seconds) of CPU work
+    cal = cpu_baseline(cams, sc, rho2, budget_s=4.0)
+    per_step_px = max(64, int(cal["value"] * 1e6 * 3.0))
+    scr = sc.with_rho2(rho2)
+    rng = np.random.default_rng(2)
+    times = []
+    for k in range(args.warmup + args.steps):
+        pix = rng.choice(cams[0].n_pixels, size=per_step_px, replace=False).astype(np.int32)
+        t0 = time.perf_counter()
+        oracle.render(cams[0], scr, pix=pix)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    value = per_step_px * len(times) / tot / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Mrays/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD + " (oracle: pixel sample per step)", "pixels_per_step": per_step_px},
+            "cpu_baseline": {"value": value, "unit": "Mrays/s", "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"{per_step_px} random pixels of the 1280x720 view per step"},
+            "e2e": {"value": value, "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_2609_13397_b300 as cg
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    cams, sc = build_workload()
+    ctx = cg.Context(local_rank)
+    ctx.set_scene_from(sc)
+    views = []
+    for c in cams:
+        v = ctx.view()
+        v.set_camera_from(c)
+        views.append(v)
+    rho2 = ctx.compute_floor([views[0]])
+    ctx.set_scene_from(sc, rho2=rho2)
+    rays_per_step = sum(v.stats()["n_valid_pixels"] for v in views)
+    outs = [(torch.empty(3, c.height, c.width, device=dev), torch.empty(c.height, c.width, device=dev))
+            for c in cams]
+    flush = torch.empty(256 * 1024 * 1024 // 4, device=dev, dtype=torch.float32)
+    stream = torch.cuda.current_stream()
+
+    def step(flags=0):
+        for v, (o_rgb, o_T) in zip(views, outs):
+            v.render(flags=flags, out_rgb=o_rgb, out_T=o_T)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+
+    # timed region: per-step CUDA events; L2 flushed between steps (outside the events)
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+        tdist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    raster_ms, evals, stage = [], [], {"ms_preprocess": 0.0, "ms_sort": 0.0, "ms_raster": 0.0}
+    launches = 0
+    with ClockSampler(local_rank) as clk:
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            step(flags=cg.PROFILE)
+            ev[k][1].record(stream)
+            for v in views:
+                st = v.stats()
+                raster_ms.append(st["ms_raster"])
+                evals.append(st["n_evaluated"])
+                launches += st["n_launches"]
+                for key in stage:
+                    stage[key] += st[key]
+        torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = sum(step_ms) / len(step_ms)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = rays_per_step * world / (ms * 1e-3) / 1e6
+
+    # forward + backward (adjoint) rate on the same workload, when the adjoint is built
+    fwd_bwd = None
+    try:
+        gl = [torch.ones_like(o[0]) for o in outs]
+        def fb_step():
+            for v, (o_rgb, o_T), g in zip(views, outs, gl):
+                v.render(flags=cg.KEEP_FOR_BACKWARD, out_rgb=o_rgb, out_T=o_T)
+                v.render_backward(g)
+        for _ in range(2):
+            fb_step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fb_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fb_ms = e0.elapsed_time(e1) / args.steps
+        fwd_bwd = {"value": rays_per_step * world / (fb_ms * 1e-3) / 1e6, "unit": "Mrays/s", "ms_per_step": fb_ms}
+    except cg.ConegsError as e:
+        fwd_bwd = {"value": None, "unavailable": str(e)[:120]}
+
+    # end to end through the host-buffer entry point: camera in, image out every step
+    host = [(torch.empty(3, c.height, c.width, pin_memory=True), torch.empty(c.height, c.width, pin_memory=True))
+            for c in cams]
+    def e2e_step():
+        for v, c, (h_rgb, h_T) in zip(views, cams, host):
+            v.set_camera_from(c)
+            v.render_host(h_rgb, h_T)
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    h2d = len(cams) * (4 + 4 + 12) * 4
+    d2h = sum(4 * 4 * c.width * c.height for c in cams)
+
+    peaks = _peaks()
+    clocks = clk.summary()
+    floor_pairs = True
+    fpp = FLOPS_PER_PAIR_FLOOR if floor_pairs else FLOPS_PER_PAIR_NOFLOOR
+    r_ms = sum(raster_ms) / len(raster_ms)
+    r_flops = fpp * sum(evals) / len(evals)
+    achieved = r_flops / (r_ms * 1e-3) / 1e12
+    peak = SMS * FP32_LANES * 2 * (peaks.get("sm_max_mhz", 2032.0)) * 1e6 / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "rays_per_step": rays_per_step, "gaussians": ctx.n,
+                   "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
+        "fwd_bwd": fwd_bwd,
+        "stage_ms_per_step": {k: v / args.steps for k, v in stage.items()},
+        "roofline": {"bound": "alu", "kernel": "raster_fwd_kernel", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "peak_basis": "148 SMs x 128 FP32 lanes x 2 x max SM clock (FMA = 2 flops)",
+                     "flops_per_pair": fpp, "pairs_per_launch": sum(evals) / len(evals),
+                     "ms_per_launch": r_ms},
+        "e2e": {"value": rays_per_step * world / (e2e_ms * 1e-3) / 1e6, "unit": "Mrays/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches // 1,
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cams, sc, rho2.cpu().numpy(), budget_s=args.cpu_budget)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

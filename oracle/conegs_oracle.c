@@ -942,12 +942,16 @@ static int ftest(const float *g, const float *t) {
     float m = t[5];
     float sm = sqrtf(m);
     float c = kr * sm;
+    /* two valid bounds on |x* - mu| and t*, combined by min (monotone in m) */
+    float rfc = 255.0f * ks;
     float tb, rf;
-    if (c < 0.5f) {
-        tb = (L + ks) / (1.0f - c);
-        rf = kap * sqrtf(s2 + ((tb * tb) * r1sq) * m);
+    if (c < 1.0f) {
+        float tbf = (L + ks) / (1.0f - c);
+        float rff = kap * sqrtf(s2 + ((tbf * tbf) * r1sq) * m);
+        rf = fminf(rff, rfc);
+        tb = fminf(tbf, L + rf);
     } else {
-        rf = 255.0f * ks;
+        rf = rfc;
         tb = L + rf;
     }
     if (L <= rf) return 1;

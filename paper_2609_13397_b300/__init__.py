@@ -1,0 +1,224 @@
+"""B300 (sm_103a) ConeGaussian renderer: Python binding of include/conegs.h.
+
+Every step of the render and its adjoint runs in the CUDA library
+(libconegs.so); this module only marshals torch tensors (device memory and
+streams) into the C calls.
+
+    ctx = Context(device=0)
+    ctx.set_scene(means, log_scales, quats, opacity_logits, sh, sh_degree, rho2)
+    view = ctx.view()
+    view.set_camera(model, width, height, (fx, fy, cx, cy), k, cam_to_world, theta_lim)
+    rgb, T = view.render()
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional, Sequence
+
+import torch
+
+from . import _lib
+from ._lib import ConegsError, check, lib
+
+PINHOLE, KB_FISHEYE = 0, 1
+F32, BF16, F16 = 0, 1, 2
+FILTER_NONE, COMP_ADDITIVE, KEEP_FOR_BACKWARD, PROFILE = 1, 2, 4, 8
+
+_DTYPE_CODE = {torch.float32: F32, torch.bfloat16: BF16, torch.float16: F16}
+
+__all__ = ["Context", "View", "ConegsError", "PINHOLE", "KB_FISHEYE", "FILTER_NONE", "COMP_ADDITIVE",
+           "KEEP_FOR_BACKWARD", "PROFILE", "radix_sort_pairs"]
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(t: torch.Tensor, device, dtype=torch.float32) -> torch.Tensor:
+    return t.to(device=device, dtype=dtype).contiguous()
+
+
+def _host_f32(x, n: int):
+    if x is None:
+        return None
+    arr = (ctypes.c_float * n)(*[float(v) for v in list(torch.as_tensor(x, dtype=torch.float64).reshape(-1))])
+    return arr
+
+
+class Context:
+    """A scene resident on one CUDA device plus its views."""
+
+    def __init__(self, device: int = 0, mem_budget_bytes: int = 0):
+        lib()
+        self.device = torch.device("cuda", device)
+        h = ctypes.c_void_p()
+        check(lib().conegs_create(ctypes.byref(h), device, mem_budget_bytes), "create")
+        self._h = h
+        self._scene_refs = None
+        self.n = 0
+        self.sh_degree = 0
+        self.storage = torch.float32
+        self._views = []
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            torch.cuda.synchronize(self.device)
+            lib().conegs_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_scene(self, means, log_scales, quats, opacity_logits, sh, sh_degree: int, rho2=None,
+                  storage: Optional[torch.dtype] = None, stream=None):
+        """Scene parameters (kept by reference).  SH and opacity may be stored in
+        bf16/fp16 (``storage``); everything else is FP32."""
+        dev = self.device
+        storage = storage if storage is not None else torch.float32
+        m = _dev(torch.as_tensor(means), dev)
+        n = m.shape[0]
+        refs = dict(
+            means=m.reshape(n, 3),
+            log_scales=_dev(torch.as_tensor(log_scales), dev).reshape(n, 3),
+            quats=_dev(torch.as_tensor(quats), dev).reshape(n, 4),
+            opacity_logits=_dev(torch.as_tensor(opacity_logits), dev, storage).reshape(n),
+            sh=_dev(torch.as_tensor(sh), dev, storage).reshape(n, (sh_degree + 1) ** 2, 3),
+            rho2=None if rho2 is None else _dev(torch.as_tensor(rho2), dev).reshape(n),
+        )
+        check(lib().conegs_set_scene(self._h, n, _ptr(refs["means"]), _ptr(refs["log_scales"]), _ptr(refs["quats"]),
+                                     _ptr(refs["opacity_logits"]), _ptr(refs["sh"]), sh_degree,
+                                     _DTYPE_CODE[storage], _ptr(refs["rho2"]), _stream(stream)), "set_scene")
+        self._scene_refs = refs
+        self.n, self.sh_degree, self.storage = n, sh_degree, storage
+        return refs
+
+    def set_scene_from(self, scene, storage: Optional[torch.dtype] = None, rho2=None):
+        """Convenience: a synthetic.Scene (numpy arrays)."""
+        return self.set_scene(torch.from_numpy(scene.means), torch.from_numpy(scene.log_scales),
+                              torch.from_numpy(scene.quats), torch.from_numpy(scene.opacity_logits),
+                              torch.from_numpy(scene.sh), scene.sh_degree,
+                              torch.from_numpy(scene.rho2) if rho2 is None else rho2, storage=storage)
+
+    def view(self) -> "View":
+        v = View(self)
+        self._views.append(v)
+        return v
+
+    def compute_floor(self, views: Sequence["View"], stream=None) -> torch.Tensor:
+        """Eq. 11 training-frequency floor of the current scene's Gaussians over ``views``."""
+        out = torch.empty(self.n, device=self.device, dtype=torch.float32)
+        arr = (ctypes.c_void_p * max(len(views), 1))(*[v._h for v in views])
+        check(lib().conegs_compute_floor(self._h, len(views), arr, _ptr(out), _stream(stream)), "compute_floor")
+        return out
+
+
+class View:
+    """One camera and its render scratch (see conegs_view in include/conegs.h)."""
+
+    def __init__(self, ctx: Context):
+        self.ctx = ctx
+        h = ctypes.c_void_p()
+        check(lib().conegs_view_create(ctx._h, ctypes.byref(h)), "view_create")
+        self._h = h
+        self.width = self.height = 0
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value and self.ctx._h is not None:
+            lib().conegs_view_destroy(self._h)
+        self._h = None
+
+    def set_camera(self, model: int, width: int, height: int, intrinsics, distortion=None, cam_to_world=None,
+                   theta_lim: float = 0.0, stream=None):
+        check(lib().conegs_set_camera(self._h, int(model), int(width), int(height), _host_f32(intrinsics, 4),
+                                      _host_f32(distortion, 4), _host_f32(cam_to_world, 12), float(theta_lim),
+                                      _stream(stream)), "set_camera")
+        self.width, self.height = int(width), int(height)
+
+    def set_camera_from(self, cam, stream=None):
+        """Convenience: a synthetic.Camera."""
+        self.set_camera(cam.model, cam.width, cam.height, cam.intrinsics, cam.k, cam.cam_to_world, cam.theta_lim,
+                        stream)
+
+    def render(self, flags: int = 0, out_rgb: Optional[torch.Tensor] = None, out_T: Optional[torch.Tensor] = None,
+               stream=None):
+        dev = self.ctx.device
+        if out_rgb is None:
+            out_rgb = torch.empty(3, self.height, self.width, device=dev, dtype=torch.float32)
+        if out_T is None:
+            out_T = torch.empty(self.height, self.width, device=dev, dtype=torch.float32)
+        check(lib().conegs_render(self._h, _ptr(out_rgb), _ptr(out_T), flags, _stream(stream)), "render")
+        return out_rgb, out_T
+
+    def render_host(self, out_rgb_host: torch.Tensor, out_T_host: Optional[torch.Tensor] = None, flags: int = 0,
+                    stream=None):
+        """Render into (pinned) host tensors; returns after the copy completed."""
+        check(lib().conegs_render_host(self._h, _ptr(out_rgb_host), _ptr(out_T_host), flags, _stream(stream)),
+              "render_host")
+        return out_rgb_host, out_T_host
+
+    def render_backward(self, dL_drgb: torch.Tensor, dL_dT: Optional[torch.Tensor] = None, grads=None,
+                        stream=None):
+        """Accumulate scene gradients (dict of FP32 tensors; created if None)."""
+        refs = self.ctx._scene_refs
+        dev = self.ctx.device
+        if grads is None:
+            grads = {k: torch.zeros(refs[k].shape, device=dev, dtype=torch.float32)
+                     for k in ("means", "log_scales", "quats", "opacity_logits", "sh")}
+        check(lib().conegs_render_backward(self._h, _ptr(dL_drgb.contiguous()),
+                                           _ptr(None if dL_dT is None else dL_dT.contiguous()),
+                                           _ptr(grads.get("means")), _ptr(grads.get("log_scales")),
+                                           _ptr(grads.get("quats")), _ptr(grads.get("opacity_logits")),
+                                           _ptr(grads.get("sh")), _stream(stream)), "render_backward")
+        return grads
+
+    def stats(self) -> dict:
+        st = _lib.Stats()
+        check(lib().conegs_get_stats(self._h, ctypes.byref(st)), "get_stats")
+        return {k: getattr(st, k) for k, _ in _lib.Stats._fields_}
+
+    def rays(self, stream=None):
+        P = self.width * self.height
+        dev = self.ctx.device
+        d = torch.empty(3, P, device=dev)
+        dx = torch.empty(3, P, device=dev)
+        dy = torch.empty(3, P, device=dev)
+        valid = torch.empty(P, device=dev, dtype=torch.uint8)
+        check(lib().conegs_get_rays(self._h, _ptr(d), _ptr(dx), _ptr(dy), _ptr(valid), _stream(stream)), "get_rays")
+        return d, dx, dy, valid
+
+    def tile_table(self, stream=None) -> torch.Tensor:
+        st = self.stats()
+        out = torch.empty(st["tiles_x"] * st["tiles_y"], 6, device=self.ctx.device)
+        check(lib().conegs_get_tile_table(self._h, _ptr(out), _stream(stream)), "get_tile_table")
+        return out
+
+    def bin_counts(self, stream=None):
+        st = self.stats()
+        pg = torch.empty(self.ctx.n, device=self.ctx.device, dtype=torch.int32)
+        pt = torch.empty(st["tiles_x"] * st["tiles_y"], device=self.ctx.device, dtype=torch.int32)
+        check(lib().conegs_get_bin_counts(self._h, _ptr(pg), _ptr(pt), _stream(stream)), "get_bin_counts")
+        return pg, pt
+
+    def pairs(self, stream=None):
+        st = self.stats()
+        gid = torch.empty(max(st["n_pairs"], 1), device=self.ctx.device, dtype=torch.int32)
+        rng = torch.empty(st["tiles_x"] * st["tiles_y"], 2, device=self.ctx.device, dtype=torch.int32)
+        check(lib().conegs_get_pairs(self._h, _ptr(gid), _ptr(rng), _stream(stream)), "get_pairs")
+        return gid[: st["n_pairs"]], rng
+
+
+def radix_sort_pairs(ctx: Context, keys: torch.Tensor, values: torch.Tensor, begin_bit: int = 0, end_bit: int = 32,
+                     stream=None):
+    """Stable in-place LSD radix sort of uint32-valued (int32 storage) key/value tensors."""
+    assert keys.dtype == torch.int32 and values.dtype == torch.int32 and keys.is_contiguous()
+    check(lib().conegs_radix_sort_pairs(ctx._h, _ptr(keys), _ptr(values), keys.numel(), begin_bit, end_bit,
+                                        _stream(stream)), "radix_sort_pairs")
+    return keys, values

@@ -1,0 +1,774 @@
+// C ABI of the library (include/conegs.h): contexts, views, scratch memory
+// and the render pipeline
+//   K1 ray table + tile cones (set_camera)
+//   K2a scene cache (set_scene)
+//   K2b view records -> K3 count -> scan/compact -> K4 depth sort ->
+//   K3 emit -> K4 tile sort -> ranges -> K5 raster (render)
+//   K6/K7 adjoint (render_backward)
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/conegs.h"
+#include "common.cuh"
+
+namespace conegs {
+// launchers defined in the other translation units
+cudaError_t launch_ray_table(const CamParams &c, float *d, float *dx, float *dy, uint8_t *valid, cudaStream_t s);
+cudaError_t launch_tile_tables(const CamParams &c, float *table, float *super, cudaStream_t s);
+cudaError_t launch_gauss_scene_rule(const SceneParams &sp, float *binrec, cudaStream_t s);
+cudaError_t launch_bin_count(const CamParams &c, const float *binrec, const float4 *gview, const uint8_t *gflag,
+                             const float *table, const float *super, int64_t n, uint32_t *counts, cudaStream_t s);
+cudaError_t launch_bin_emit(const CamParams &c, const float *binrec, const float4 *gview, const uint8_t *gflag,
+                            const float *table, const float *super, int64_t n_sorted, const uint32_t *order,
+                            const uint32_t *offsets, uint32_t *out_tile, uint32_t *out_gid, cudaStream_t s);
+cudaError_t launch_scene_cache(const SceneParams &sp, float *W, float *sig_eff, cudaStream_t s);
+cudaError_t launch_view_records(const CamParams &c, const SceneParams &sp, float4 *rec, float4 *gview,
+                                uint8_t *gflag, cudaStream_t s);
+int64_t scan_scratch_words(int64_t n);
+cudaError_t exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *scratch, int pred,
+                           cudaStream_t s);
+cudaError_t sum_counts(const uint32_t *in, int64_t n, unsigned long long *d_two, cudaStream_t s);
+cudaError_t launch_compact(const uint32_t *counts, const uint32_t *pos, int64_t n, const float4 *gview,
+                           uint32_t *keys, uint32_t *vals, cudaStream_t s);
+cudaError_t launch_gather(const uint32_t *src, const uint32_t *idx, int64_t n, uint32_t *dst, cudaStream_t s);
+cudaError_t launch_ranges(const uint32_t *keys, int64_t n, uint2 *ranges, int ntiles, cudaStream_t s);
+int64_t radix_scratch_words(int64_t n);
+cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *alt_keys, uint32_t *alt_vals, int64_t n,
+                             int begin_bit, int end_bit, uint32_t *scratch, cudaStream_t s);
+cudaError_t launch_floor(const CamParams *cams_dev, int nv, const float *means, int64_t n, float *rho2,
+                         cudaStream_t s);
+struct RasterArgs {
+    int W, H, tiles_x;
+    const uint2 *ranges;
+    const uint32_t *gids;
+    const float4 *rec;
+    const float *d, *dx, *dy;
+    const uint8_t *valid;
+    float *out_rgb, *out_T, *keep_T;
+    uint32_t *last;
+    unsigned long long *evaluated;
+    int additive;
+};
+cudaError_t launch_raster_fwd(const RasterArgs &a, int ntiles, bool filter, cudaStream_t s);
+struct BackwardArgs;
+cudaError_t launch_backward(const RasterArgs &a, int ntiles, bool filter, const float *dL_drgb, const float *dL_dT,
+                            const float *final_T, float *g_rec, cudaStream_t s);
+cudaError_t launch_backward_params(const CamParams &c, const SceneParams &sp, const float *g_rec,
+                                   const uint8_t *gflag, const float4 *gview, float *g_means, float *g_log_scales,
+                                   float *g_quats, float *g_logits, float *g_sh, cudaStream_t s);
+}  // namespace conegs
+
+using namespace conegs;
+
+namespace conegs {
+static std::atomic<long long> g_launches{0};
+void note_launches(int k) { g_launches += k; }
+long long launches_so_far() { return g_launches.load(); }
+}  // namespace conegs
+
+namespace {
+
+thread_local std::string g_last_error;
+
+conegs_status fail(conegs_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+#define CUDA_TRY(expr)                                                                                  \
+    do {                                                                                                \
+        cudaError_t _e = (expr);                                                                        \
+        if (_e != cudaSuccess) return fail(CONEGS_ERR_CUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(_e), \
+                                           __FILE__, __LINE__);                                         \
+    } while (0)
+
+#define TRY(expr)                              \
+    do {                                       \
+        conegs_status _s = (expr);             \
+        if (_s != CONEGS_OK) return _s;        \
+    } while (0)
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    template <typename T>
+    T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+class DeviceGuard {
+  public:
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev_);
+        if (prev_ != dev) cudaSetDevice(dev);
+        dev_ = dev;
+    }
+    ~DeviceGuard() {
+        if (prev_ != dev_) cudaSetDevice(prev_);
+    }
+
+  private:
+    int prev_ = 0, dev_ = 0;
+};
+
+}  // namespace
+
+struct conegs_ctx {
+    int device = 0;
+    size_t budget = 0;
+    std::atomic<size_t> used{0};
+    std::mutex mu;
+    // scene
+    SceneParams sp{};
+    bool has_scene = false;
+    uint64_t scene_gen = 0;
+    DevBuf W, sig_eff, binrec;
+    cudaEvent_t scene_ready = nullptr;
+    std::vector<conegs_view *> views;
+};
+
+struct conegs_view {
+    conegs_ctx *ctx = nullptr;
+    CamParams cam{};
+    bool has_cam = false;
+    DevBuf d, dx, dy, valid, table, super;
+    // per-render scratch
+    DevBuf rec, gview, gflag, counts, vispos, scan_scr, dkeys, dvals, dkeys_alt, dvals_alt, sorted_counts, offsets;
+    DevBuf pair_tile, pair_gid, pair_tile_alt, pair_gid_alt, ranges, last, sums, rs_scr, tmp_rgb, tmp_T;
+    DevBuf g_rec, keep_T;
+    unsigned long long *h_sums = nullptr;   // pinned
+    int64_t n_visible = 0, n_pairs = 0, n_valid = 0, n_launches = 0;
+    bool has_forward = false;
+    unsigned last_flags = 0;
+    uint64_t forward_gen = 0;
+    cudaEvent_t done = nullptr;
+    cudaEvent_t prof[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    bool profiled = false;
+    DevBuf evaluated;
+    cudaStream_t last_stream = nullptr;
+    bool has_stream = false;
+};
+
+namespace {
+
+conegs_status ensure(conegs_ctx *ctx, DevBuf &b, size_t need, cudaStream_t s) {
+    if (need <= b.bytes) return CONEGS_OK;
+    size_t want = std::max<size_t>(need + need / 4, 256);
+    if (ctx->budget) {
+        size_t cur = ctx->used.load();
+        if (cur - b.bytes + want > ctx->budget) {
+            want = need;
+            if (cur - b.bytes + want > ctx->budget)
+                return fail(CONEGS_ERR_BUDGET, "memory budget exceeded: need %zu more bytes (budget %zu, in use %zu)",
+                            want - b.bytes, ctx->budget, cur);
+        }
+    }
+    if (b.p) {
+        cudaError_t e = cudaFreeAsync(b.p, s);
+        if (e != cudaSuccess) return fail(CONEGS_ERR_CUDA, "cudaFreeAsync: %s", cudaGetErrorString(e));
+        ctx->used -= b.bytes;
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    void *p = nullptr;
+    cudaError_t e = cudaMallocAsync(&p, want, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(CONEGS_ERR_OOM, "cudaMallocAsync(%zu bytes): %s", want, cudaGetErrorString(e));
+    }
+    b.p = p;
+    b.bytes = want;
+    ctx->used += want;
+    return CONEGS_OK;
+}
+
+void release(conegs_ctx *ctx, DevBuf &b) {
+    if (b.p) {
+        cudaFree(b.p);
+        ctx->used -= b.bytes;
+    }
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+// Serialise a view's work across the streams it is used on.
+conegs_status view_begin(conegs_view *v, cudaStream_t s) {
+    if (v->has_stream && v->last_stream != s) CUDA_TRY(cudaStreamWaitEvent(s, v->done, 0));
+    return CONEGS_OK;
+}
+
+conegs_status view_end(conegs_view *v, cudaStream_t s) {
+    CUDA_TRY(cudaEventRecord(v->done, s));
+    v->last_stream = s;
+    v->has_stream = true;
+    return CONEGS_OK;
+}
+
+int bits_for(int64_t n) {
+    int b = 0;
+    while ((1LL << b) < n) ++b;
+    return std::max(b, 1);
+}
+
+float kb_P_host(const float k[4], float th) {
+    // FP32 rule (no contraction: the host compiler runs with -ffp-contract=off)
+    float t2 = th * th;
+    float p = ((k[3] * t2 + k[2]) * t2 + k[1]) * t2 + k[0];
+    return th * (1.0f + t2 * p);
+}
+
+float derive_theta_lim(const float k[4]) {
+    const double thmax = 95.0 * M_PI / 180.0;
+    const int steps = 200000;
+    double prev = 0.0;
+    for (int i = 0; i <= steps; ++i) {
+        double th = thmax * i / steps, t2 = th * th;
+        double slope = 1 + 3 * k[0] * t2 + 5 * k[1] * t2 * t2 + 7 * k[2] * t2 * t2 * t2 + 9 * k[3] * t2 * t2 * t2 * t2;
+        if (slope < 0.25) return (float)prev;
+        prev = th;
+    }
+    return (float)thmax;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *conegs_last_error(void) { return g_last_error.c_str(); }
+
+const char *conegs_version(void) { return "conegs 0.1 sm_103a"; }
+
+conegs_status conegs_create(conegs_ctx **out, int device, size_t mem_budget_bytes) {
+    if (!out) return fail(CONEGS_ERR_ARG, "conegs_create: out is NULL");
+    int ndev = 0;
+    CUDA_TRY(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return fail(CONEGS_ERR_ARG, "conegs_create: bad device %d", device);
+    DeviceGuard g(device);
+    auto *ctx = new conegs_ctx();
+    ctx->device = device;
+    ctx->budget = mem_budget_bytes;
+    cudaError_t e = cudaEventCreateWithFlags(&ctx->scene_ready, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        delete ctx;
+        return fail(CONEGS_ERR_CUDA, "cudaEventCreate: %s", cudaGetErrorString(e));
+    }
+    *out = ctx;
+    return CONEGS_OK;
+}
+
+void conegs_view_destroy(conegs_view *v);
+
+void conegs_destroy(conegs_ctx *ctx) {
+    if (!ctx) return;
+    DeviceGuard g(ctx->device);
+    cudaDeviceSynchronize();
+    std::vector<conegs_view *> vs;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        vs = ctx->views;
+    }
+    for (auto *v : vs) conegs_view_destroy(v);
+    release(ctx, ctx->W);
+    release(ctx, ctx->sig_eff);
+    release(ctx, ctx->binrec);
+    if (ctx->scene_ready) cudaEventDestroy(ctx->scene_ready);
+    delete ctx;
+}
+
+conegs_status conegs_set_scene(conegs_ctx *ctx, int64_t n, const float *means, const float *log_scales,
+                               const float *quats, const void *opacity_logits, const void *sh, int sh_degree,
+                               int storage, const float *rho2, void *stream) {
+    if (!ctx) return fail(CONEGS_ERR_ARG, "set_scene: ctx is NULL");
+    if (n < 0 || n > (1LL << 31) - 1) return fail(CONEGS_ERR_ARG, "set_scene: bad n %lld", (long long)n);
+    if (sh_degree < 0 || sh_degree > 3) return fail(CONEGS_ERR_ARG, "set_scene: sh_degree %d not in 0..3", sh_degree);
+    if (storage < 0 || storage > 2) return fail(CONEGS_ERR_ARG, "set_scene: bad storage dtype %d", storage);
+    if (n > 0 && (!means || !log_scales || !quats || !opacity_logits || !sh))
+        return fail(CONEGS_ERR_ARG, "set_scene: NULL parameter array");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    TRY(ensure(ctx, ctx->W, sizeof(float) * 9 * (size_t)std::max<int64_t>(n, 1), s));
+    TRY(ensure(ctx, ctx->sig_eff, sizeof(float) * (size_t)std::max<int64_t>(n, 1), s));
+    TRY(ensure(ctx, ctx->binrec, sizeof(float) * 6 * (size_t)std::max<int64_t>(n, 1), s));
+    SceneParams sp{};
+    sp.n = n;
+    sp.sh_degree = sh_degree;
+    sp.storage = storage;
+    sp.means = means;
+    sp.log_scales = log_scales;
+    sp.quats = quats;
+    sp.rho2 = rho2;
+    sp.logits = opacity_logits;
+    sp.sh = sh;
+    sp.W = ctx->W.as<float>();
+    sp.sig_eff = ctx->sig_eff.as<float>();
+    sp.binrec = ctx->binrec.as<float>();
+    CUDA_TRY(launch_scene_cache(sp, ctx->W.as<float>(), ctx->sig_eff.as<float>(), s));
+    CUDA_TRY(launch_gauss_scene_rule(sp, ctx->binrec.as<float>(), s));
+    CUDA_TRY(cudaEventRecord(ctx->scene_ready, s));
+    ctx->sp = sp;
+    ctx->has_scene = true;
+    ctx->scene_gen++;
+    return CONEGS_OK;
+}
+
+conegs_status conegs_view_create(conegs_ctx *ctx, conegs_view **out) {
+    if (!ctx || !out) return fail(CONEGS_ERR_ARG, "view_create: NULL argument");
+    DeviceGuard g(ctx->device);
+    auto *v = new conegs_view();
+    v->ctx = ctx;
+    cudaError_t e = cudaEventCreateWithFlags(&v->done, cudaEventDisableTiming);
+    for (int k = 0; k < 5 && e == cudaSuccess; ++k) e = cudaEventCreate(&v->prof[k]);
+    if (e == cudaSuccess) e = cudaMallocHost(&v->h_sums, 3 * sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+        if (v->done) cudaEventDestroy(v->done);
+        delete v;
+        return fail(CONEGS_ERR_CUDA, "view_create: %s", cudaGetErrorString(e));
+    }
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->views.push_back(v);
+    }
+    *out = v;
+    return CONEGS_OK;
+}
+
+void conegs_view_destroy(conegs_view *v) {
+    if (!v) return;
+    conegs_ctx *ctx = v->ctx;
+    DeviceGuard g(ctx->device);
+    if (v->done) {
+        cudaEventSynchronize(v->done);
+        cudaEventDestroy(v->done);
+    }
+    DevBuf *bufs[] = {&v->d, &v->dx, &v->dy, &v->valid, &v->table, &v->super, &v->rec, &v->gview, &v->gflag,
+                      &v->counts, &v->vispos, &v->scan_scr, &v->dkeys, &v->dvals, &v->dkeys_alt, &v->dvals_alt,
+                      &v->sorted_counts, &v->offsets, &v->pair_tile, &v->pair_gid, &v->pair_tile_alt,
+                      &v->pair_gid_alt, &v->ranges, &v->last, &v->sums, &v->rs_scr, &v->tmp_rgb, &v->tmp_T,
+                      &v->g_rec, &v->keep_T};
+    for (DevBuf *b : bufs) release(ctx, *b);
+    if (v->h_sums) cudaFreeHost(v->h_sums);
+    for (int k = 0; k < 5; ++k)
+        if (v->prof[k]) cudaEventDestroy(v->prof[k]);
+    release(ctx, v->evaluated);
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->views.erase(std::remove(ctx->views.begin(), ctx->views.end(), v), ctx->views.end());
+    }
+    delete v;
+}
+
+conegs_status conegs_set_camera(conegs_view *v, int model, int width, int height, const float *intr,
+                                const float *dist, const float *c2w, float theta_lim, void *stream) {
+    if (!v) return fail(CONEGS_ERR_ARG, "set_camera: view is NULL");
+    if (model != CONEGS_PINHOLE && model != CONEGS_KB_FISHEYE)
+        return fail(CONEGS_ERR_ARG, "set_camera: unknown camera model %d", model);
+    if (width <= 0 || height <= 0 || (int64_t)width * height > (1LL << 30))
+        return fail(CONEGS_ERR_ARG, "set_camera: bad size %dx%d", width, height);
+    if (!intr) return fail(CONEGS_ERR_ARG, "set_camera: intrinsics is NULL");
+    if (!(intr[0] > 0.0f) || !(intr[1] > 0.0f) || !std::isfinite(intr[2]) || !std::isfinite(intr[3]))
+        return fail(CONEGS_ERR_ARG, "set_camera: focal lengths must be positive and finite");
+    conegs_ctx *ctx = v->ctx;
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    CamParams c{};
+    c.model = model;
+    c.W = width;
+    c.H = height;
+    c.tiles_x = (width + TILE - 1) / TILE;
+    c.tiles_y = (height + TILE - 1) / TILE;
+    c.supers_x = (c.tiles_x + SUPER - 1) / SUPER;
+    c.supers_y = (c.tiles_y + SUPER - 1) / SUPER;
+    c.fx = intr[0]; c.fy = intr[1]; c.cx = intr[2]; c.cy = intr[3];
+    for (int i = 0; i < 4; ++i) c.k[i] = (model == CONEGS_KB_FISHEYE && dist) ? dist[i] : 0.0f;
+    for (int r = 0; r < 3; ++r) {
+        for (int k = 0; k < 3; ++k) c.R[3 * r + k] = c2w ? c2w[4 * r + k] : (r == k ? 1.0f : 0.0f);
+        c.o[r] = c2w ? c2w[4 * r + 3] : 0.0f;
+    }
+    if (model == CONEGS_KB_FISHEYE) {
+        float th = theta_lim > 0.0f ? theta_lim : derive_theta_lim(c.k);
+        if (!(th > 0.0f) || th > 3.2f) return fail(CONEGS_ERR_ARG, "set_camera: bad theta_lim %g", th);
+        // theta_d must increase on [0, theta_lim]
+        for (int i = 1; i <= 1000; ++i) {
+            double t = (double)th * i / 1000, t2 = t * t;
+            double slope = 1 + 3 * c.k[0] * t2 + 5 * c.k[1] * t2 * t2 + 7 * c.k[2] * t2 * t2 * t2 +
+                           9 * c.k[3] * t2 * t2 * t2 * t2;
+            if (!(slope > 0.0)) return fail(CONEGS_ERR_NOCONVERGE, "set_camera: theta_d not monotone below theta_lim");
+        }
+        c.thlim = th;
+        float rl = kb_P_host(c.k, th);
+        c.rlim2 = rl * rl;
+    }
+    TRY(view_begin(v, s));
+    const size_t P = (size_t)width * height;
+    const size_t nt = (size_t)c.tiles_x * c.tiles_y, ns = (size_t)c.supers_x * c.supers_y;
+    TRY(ensure(ctx, v->d, sizeof(float) * 3 * P, s));
+    TRY(ensure(ctx, v->dx, sizeof(float) * 3 * P, s));
+    TRY(ensure(ctx, v->dy, sizeof(float) * 3 * P, s));
+    TRY(ensure(ctx, v->valid, P, s));
+    TRY(ensure(ctx, v->table, sizeof(float) * 6 * nt, s));
+    TRY(ensure(ctx, v->super, sizeof(float) * 6 * ns, s));
+    TRY(ensure(ctx, v->ranges, sizeof(uint2) * nt, s));
+    TRY(ensure(ctx, v->last, sizeof(uint32_t) * P, s));
+    CUDA_TRY(launch_ray_table(c, v->d.as<float>(), v->dx.as<float>(), v->dy.as<float>(), v->valid.as<uint8_t>(), s));
+    CUDA_TRY(launch_tile_tables(c, v->table.as<float>(), v->super.as<float>(), s));
+    v->cam = c;
+    v->has_cam = true;
+    v->has_forward = false;
+    // count valid pixels once (host copy of the mask is small relative to the table)
+    if (model == CONEGS_PINHOLE) {
+        v->n_valid = (int64_t)P;
+    } else {
+        std::vector<uint8_t> mask(P);
+        CUDA_TRY(cudaMemcpyAsync(mask.data(), v->valid.p, P, cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        int64_t cnt = 0;
+        for (uint8_t m : mask) cnt += m;
+        v->n_valid = cnt;
+    }
+    return view_end(v, s);
+}
+
+static conegs_status render_impl(conegs_view *v, float *out_rgb, float *out_T, unsigned flags, cudaStream_t s) {
+    conegs_ctx *ctx = v->ctx;
+    const CamParams &c = v->cam;
+    const int64_t n = ctx->sp.n;
+    const int64_t P = (int64_t)c.W * c.H;
+    const int nt = c.tiles_x * c.tiles_y;
+    CUDA_TRY(cudaStreamWaitEvent(s, ctx->scene_ready, 0));
+    const long long launches0 = launches_so_far();
+    const size_t nn = (size_t)std::max<int64_t>(n, 1);
+    TRY(ensure(ctx, v->rec, sizeof(float4) * REC_F4 * nn, s));
+    TRY(ensure(ctx, v->gview, sizeof(float4) * nn, s));
+    TRY(ensure(ctx, v->gflag, nn, s));
+    TRY(ensure(ctx, v->counts, sizeof(uint32_t) * nn, s));
+    TRY(ensure(ctx, v->vispos, sizeof(uint32_t) * nn, s));
+    TRY(ensure(ctx, v->scan_scr, sizeof(uint32_t) * (size_t)scan_scratch_words((int64_t)nn), s));
+    TRY(ensure(ctx, v->sums, 2 * sizeof(unsigned long long), s));
+    SceneParams sp = ctx->sp;
+    const bool prof = (flags & CONEGS_PROFILE) != 0;
+    if (prof) {
+        TRY(ensure(ctx, v->evaluated, sizeof(unsigned long long), s));
+        CUDA_TRY(cudaMemsetAsync(v->evaluated.p, 0, sizeof(unsigned long long), s));
+        CUDA_TRY(cudaEventRecord(v->prof[0], s));
+    }
+    CUDA_TRY(launch_view_records(c, sp, v->rec.as<float4>(), v->gview.as<float4>(), v->gflag.as<uint8_t>(), s));
+    CUDA_TRY(launch_bin_count(c, sp.binrec, v->gview.as<float4>(), v->gflag.as<uint8_t>(), v->table.as<float>(),
+                              v->super.as<float>(), n, v->counts.as<uint32_t>(), s));
+    CUDA_TRY(sum_counts(v->counts.as<uint32_t>(), n, v->sums.as<unsigned long long>(), s));
+    CUDA_TRY(exclusive_scan(v->counts.as<uint32_t>(), v->vispos.as<uint32_t>(), n, v->scan_scr.as<uint32_t>(), 1, s));
+    if (prof) CUDA_TRY(cudaEventRecord(v->prof[1], s));
+    CUDA_TRY(cudaMemcpyAsync(v->h_sums, v->sums.p, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    const uint64_t total = v->h_sums[0];
+    const int64_t M = (int64_t)v->h_sums[1];
+    if (total >= (1ULL << 31)) return fail(CONEGS_ERR_OVERFLOW, "render: %llu tile/Gaussian pairs exceed 2^31",
+                                           (unsigned long long)total);
+    const int64_t Pn = (int64_t)total;
+    const size_t mm = (size_t)std::max<int64_t>(M, 1), pp = (size_t)std::max<int64_t>(Pn, 1);
+    TRY(ensure(ctx, v->dkeys, sizeof(uint32_t) * mm, s));
+    TRY(ensure(ctx, v->dvals, sizeof(uint32_t) * mm, s));
+    TRY(ensure(ctx, v->dkeys_alt, sizeof(uint32_t) * mm, s));
+    TRY(ensure(ctx, v->dvals_alt, sizeof(uint32_t) * mm, s));
+    TRY(ensure(ctx, v->sorted_counts, sizeof(uint32_t) * mm, s));
+    TRY(ensure(ctx, v->offsets, sizeof(uint32_t) * mm, s));
+    TRY(ensure(ctx, v->pair_tile, sizeof(uint32_t) * pp, s));
+    TRY(ensure(ctx, v->pair_gid, sizeof(uint32_t) * pp, s));
+    TRY(ensure(ctx, v->pair_tile_alt, sizeof(uint32_t) * pp, s));
+    TRY(ensure(ctx, v->pair_gid_alt, sizeof(uint32_t) * pp, s));
+    const int64_t sortmax = std::max<int64_t>(std::max<int64_t>(M, Pn), 1);
+    TRY(ensure(ctx, v->rs_scr, sizeof(uint32_t) * (size_t)radix_scratch_words(sortmax), s));
+    TRY(ensure(ctx, v->scan_scr, sizeof(uint32_t) * (size_t)scan_scratch_words(std::max<int64_t>(M, n)), s));
+    CUDA_TRY(launch_compact(v->counts.as<uint32_t>(), v->vispos.as<uint32_t>(), n, v->gview.as<float4>(),
+                            v->dkeys.as<uint32_t>(), v->dvals.as<uint32_t>(), s));
+    CUDA_TRY(radix_sort_pairs(v->dkeys.as<uint32_t>(), v->dvals.as<uint32_t>(), v->dkeys_alt.as<uint32_t>(),
+                              v->dvals_alt.as<uint32_t>(), M, 0, 32, v->rs_scr.as<uint32_t>(), s));
+    CUDA_TRY(launch_gather(v->counts.as<uint32_t>(), v->dvals.as<uint32_t>(), M, v->sorted_counts.as<uint32_t>(), s));
+    CUDA_TRY(exclusive_scan(v->sorted_counts.as<uint32_t>(), v->offsets.as<uint32_t>(), M, v->scan_scr.as<uint32_t>(),
+                            0, s));
+    CUDA_TRY(launch_bin_emit(c, sp.binrec, v->gview.as<float4>(), v->gflag.as<uint8_t>(), v->table.as<float>(),
+                             v->super.as<float>(), M, v->dvals.as<uint32_t>(), v->offsets.as<uint32_t>(),
+                             v->pair_tile.as<uint32_t>(), v->pair_gid.as<uint32_t>(), s));
+    CUDA_TRY(radix_sort_pairs(v->pair_tile.as<uint32_t>(), v->pair_gid.as<uint32_t>(), v->pair_tile_alt.as<uint32_t>(),
+                              v->pair_gid_alt.as<uint32_t>(), Pn, 0, bits_for(nt), v->rs_scr.as<uint32_t>(), s));
+    CUDA_TRY(launch_ranges(v->pair_tile.as<uint32_t>(), Pn, v->ranges.as<uint2>(), nt, s));
+    if (prof) CUDA_TRY(cudaEventRecord(v->prof[2], s));
+    RasterArgs a{};
+    a.W = c.W;
+    a.H = c.H;
+    a.tiles_x = c.tiles_x;
+    a.ranges = v->ranges.as<uint2>();
+    a.gids = v->pair_gid.as<uint32_t>();
+    a.rec = v->rec.as<float4>();
+    a.d = v->d.as<float>();
+    a.dx = v->dx.as<float>();
+    a.dy = v->dy.as<float>();
+    a.valid = v->valid.as<uint8_t>();
+    a.out_rgb = out_rgb;
+    a.out_T = out_T;
+    a.last = v->last.as<uint32_t>();
+    a.additive = (flags & CONEGS_COMP_ADDITIVE) ? 1 : 0;
+    if (flags & CONEGS_KEEP_FOR_BACKWARD) {
+        TRY(ensure(ctx, v->keep_T, sizeof(float) * (size_t)std::max<int64_t>(P, 1), s));
+        a.keep_T = v->keep_T.as<float>();
+    }
+    a.evaluated = prof ? v->evaluated.as<unsigned long long>() : nullptr;
+    CUDA_TRY(launch_raster_fwd(a, nt, !(flags & CONEGS_FILTER_NONE), s));
+    if (prof) {
+        CUDA_TRY(cudaEventRecord(v->prof[3], s));
+        CUDA_TRY(cudaMemcpyAsync(v->h_sums + 2, v->evaluated.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                 s));
+    }
+    v->profiled = prof;
+    v->n_launches = launches_so_far() - launches0;
+    v->n_visible = M;
+    v->n_pairs = Pn;
+    v->last_flags = flags;
+    v->has_forward = true;
+    v->forward_gen = ctx->scene_gen;
+    (void)P;
+    return CONEGS_OK;
+}
+
+conegs_status conegs_render(conegs_view *v, float *out_rgb, float *out_T, unsigned flags, void *stream) {
+    if (!v || !out_rgb) return fail(CONEGS_ERR_ARG, "render: NULL argument");
+    if (!v->has_cam) return fail(CONEGS_ERR_STATE, "render: set_camera was not called on this view");
+    if (!v->ctx->has_scene) return fail(CONEGS_ERR_STATE, "render: set_scene was not called");
+    DeviceGuard g(v->ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    TRY(view_begin(v, s));
+    conegs_status st = render_impl(v, out_rgb, out_T, flags, s);
+    if (st != CONEGS_OK) {
+        v->has_forward = false;
+        view_end(v, s);
+        return st;
+    }
+    return view_end(v, s);
+}
+
+conegs_status conegs_render_host(conegs_view *v, float *out_rgb_host, float *out_T_host, unsigned flags,
+                                 void *stream) {
+    if (!v || !out_rgb_host) return fail(CONEGS_ERR_ARG, "render_host: NULL argument");
+    if (!v->has_cam) return fail(CONEGS_ERR_STATE, "render_host: set_camera was not called on this view");
+    if (!v->ctx->has_scene) return fail(CONEGS_ERR_STATE, "render_host: set_scene was not called");
+    DeviceGuard g(v->ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    TRY(view_begin(v, s));
+    const size_t P = (size_t)v->cam.W * v->cam.H;
+    TRY(ensure(v->ctx, v->tmp_rgb, sizeof(float) * 3 * P, s));
+    TRY(ensure(v->ctx, v->tmp_T, sizeof(float) * P, s));
+    conegs_status st = render_impl(v, v->tmp_rgb.as<float>(), v->tmp_T.as<float>(), flags, s);
+    if (st != CONEGS_OK) {
+        view_end(v, s);
+        return st;
+    }
+    CUDA_TRY(cudaMemcpyAsync(out_rgb_host, v->tmp_rgb.p, sizeof(float) * 3 * P, cudaMemcpyDeviceToHost, s));
+    if (out_T_host) CUDA_TRY(cudaMemcpyAsync(out_T_host, v->tmp_T.p, sizeof(float) * P, cudaMemcpyDeviceToHost, s));
+    TRY(view_end(v, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return CONEGS_OK;
+}
+
+conegs_status conegs_render_backward(conegs_view *v, const float *dL_drgb, const float *dL_dT, float *g_means,
+                                     float *g_log_scales, float *g_quats, float *g_opacity_logits, float *g_sh,
+                                     void *stream) {
+    if (!v || !dL_drgb) return fail(CONEGS_ERR_ARG, "render_backward: NULL argument");
+    if (!v->has_forward || !(v->last_flags & CONEGS_KEEP_FOR_BACKWARD))
+        return fail(CONEGS_ERR_STATE, "render_backward: no forward render with CONEGS_KEEP_FOR_BACKWARD on this view");
+    conegs_ctx *ctx = v->ctx;
+    if (v->forward_gen != ctx->scene_gen) return fail(CONEGS_ERR_STATE, "render_backward: scene changed since forward");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    TRY(view_begin(v, s));
+    const CamParams &c = v->cam;
+    const int64_t n = ctx->sp.n;
+    const int nt = c.tiles_x * c.tiles_y;
+    TRY(ensure(ctx, v->g_rec, sizeof(float) * 16 * (size_t)std::max<int64_t>(n, 1), s));
+    CUDA_TRY(cudaMemsetAsync(v->g_rec.p, 0, sizeof(float) * 16 * (size_t)std::max<int64_t>(n, 1), s));
+    RasterArgs a{};
+    a.W = c.W;
+    a.H = c.H;
+    a.tiles_x = c.tiles_x;
+    a.ranges = v->ranges.as<uint2>();
+    a.gids = v->pair_gid.as<uint32_t>();
+    a.rec = v->rec.as<float4>();
+    a.d = v->d.as<float>();
+    a.dx = v->dx.as<float>();
+    a.dy = v->dy.as<float>();
+    a.valid = v->valid.as<uint8_t>();
+    a.last = v->last.as<uint32_t>();
+    a.additive = (v->last_flags & CONEGS_COMP_ADDITIVE) ? 1 : 0;
+    CUDA_TRY(launch_backward(a, nt, !(v->last_flags & CONEGS_FILTER_NONE), dL_drgb, dL_dT, v->keep_T.as<float>(),
+                             v->g_rec.as<float>(), s));
+    CUDA_TRY(launch_backward_params(c, ctx->sp, v->g_rec.as<float>(), v->gflag.as<uint8_t>(), v->gview.as<float4>(),
+                                    g_means, g_log_scales, g_quats, g_opacity_logits, g_sh, s));
+    return view_end(v, s);
+}
+
+conegs_status conegs_get_stats(const conegs_view *v, conegs_stats *out) {
+    if (!v || !out) return fail(CONEGS_ERR_ARG, "get_stats: NULL argument");
+    memset(out, 0, sizeof(*out));
+    out->n_gaussians = v->ctx->has_scene ? v->ctx->sp.n : 0;
+    out->n_visible = v->n_visible;
+    out->n_pairs = v->n_pairs;
+    out->width = v->cam.W;
+    out->height = v->cam.H;
+    out->tiles_x = v->cam.tiles_x;
+    out->tiles_y = v->cam.tiles_y;
+    out->n_valid_pixels = v->n_valid;
+    out->n_launches = v->n_launches;
+    const DevBuf *bufs[] = {&v->d, &v->dx, &v->dy, &v->valid, &v->table, &v->super, &v->rec, &v->gview, &v->gflag,
+                            &v->counts, &v->vispos, &v->scan_scr, &v->dkeys, &v->dvals, &v->dkeys_alt, &v->dvals_alt,
+                            &v->sorted_counts, &v->offsets, &v->pair_tile, &v->pair_gid, &v->pair_tile_alt,
+                            &v->pair_gid_alt, &v->ranges, &v->last, &v->sums, &v->rs_scr, &v->tmp_rgb, &v->tmp_T,
+                            &v->g_rec, &v->keep_T};
+    size_t tot = 0;
+    for (const DevBuf *b : bufs) tot += b->bytes;
+    out->device_bytes = tot;
+    if (v->profiled && v->has_forward) {
+        CUDA_TRY(cudaEventSynchronize(v->prof[3]));
+        float t01 = 0, t12 = 0, t23 = 0, t03 = 0;
+        CUDA_TRY(cudaEventElapsedTime(&t01, v->prof[0], v->prof[1]));
+        CUDA_TRY(cudaEventElapsedTime(&t12, v->prof[1], v->prof[2]));
+        CUDA_TRY(cudaEventElapsedTime(&t23, v->prof[2], v->prof[3]));
+        CUDA_TRY(cudaEventElapsedTime(&t03, v->prof[0], v->prof[3]));
+        out->ms_preprocess = t01;
+        out->ms_sort = t12;
+        out->ms_raster = t23;
+        out->ms_total = t03;
+        out->n_evaluated = (int64_t)v->h_sums[2];
+    }
+    return CONEGS_OK;
+}
+
+conegs_status conegs_compute_floor(conegs_ctx *ctx, int n_views, conegs_view *const *views, float *rho2_out,
+                                   void *stream) {
+    if (!ctx || !rho2_out || n_views < 0 || (n_views > 0 && !views))
+        return fail(CONEGS_ERR_ARG, "compute_floor: bad argument");
+    if (!ctx->has_scene) return fail(CONEGS_ERR_STATE, "compute_floor: set_scene was not called");
+    std::vector<CamParams> cams;
+    for (int i = 0; i < n_views; ++i) {
+        if (!views[i] || !views[i]->has_cam) return fail(CONEGS_ERR_STATE, "compute_floor: view %d has no camera", i);
+        cams.push_back(views[i]->cam);
+    }
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    void *dcams = nullptr;
+    if (n_views > 0) {
+        CUDA_TRY(cudaMallocAsync(&dcams, sizeof(CamParams) * cams.size(), s));
+        CUDA_TRY(cudaMemcpyAsync(dcams, cams.data(), sizeof(CamParams) * cams.size(), cudaMemcpyHostToDevice, s));
+    }
+    CUDA_TRY(cudaStreamWaitEvent(s, ctx->scene_ready, 0));
+    CUDA_TRY(launch_floor(reinterpret_cast<const CamParams *>(dcams), n_views, ctx->sp.means, ctx->sp.n, rho2_out, s));
+    if (dcams) CUDA_TRY(cudaFreeAsync(dcams, s));
+    // the host vector must outlive the async copy
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return CONEGS_OK;
+}
+
+conegs_status conegs_get_rays(const conegs_view *v, float *d, float *dx, float *dy, uint8_t *valid, void *stream) {
+    if (!v || !v->has_cam) return fail(CONEGS_ERR_STATE, "get_rays: no camera");
+    DeviceGuard g(v->ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t P = (size_t)v->cam.W * v->cam.H;
+    CUDA_TRY(cudaStreamWaitEvent(s, v->done, 0));
+    if (d) CUDA_TRY(cudaMemcpyAsync(d, v->d.p, sizeof(float) * 3 * P, cudaMemcpyDeviceToDevice, s));
+    if (dx) CUDA_TRY(cudaMemcpyAsync(dx, v->dx.p, sizeof(float) * 3 * P, cudaMemcpyDeviceToDevice, s));
+    if (dy) CUDA_TRY(cudaMemcpyAsync(dy, v->dy.p, sizeof(float) * 3 * P, cudaMemcpyDeviceToDevice, s));
+    if (valid) CUDA_TRY(cudaMemcpyAsync(valid, v->valid.p, P, cudaMemcpyDeviceToDevice, s));
+    return CONEGS_OK;
+}
+
+conegs_status conegs_get_tile_table(const conegs_view *v, float *table, void *stream) {
+    if (!v || !v->has_cam || !table) return fail(CONEGS_ERR_STATE, "get_tile_table: no camera");
+    DeviceGuard g(v->ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(cudaStreamWaitEvent(s, v->done, 0));
+    const size_t nt = (size_t)v->cam.tiles_x * v->cam.tiles_y;
+    CUDA_TRY(cudaMemcpyAsync(table, v->table.p, sizeof(float) * 6 * nt, cudaMemcpyDeviceToDevice, s));
+    return CONEGS_OK;
+}
+
+}  // extern "C"
+
+namespace {
+__global__ void range_counts_kernel(const uint2 *ranges, int nt, int32_t *out) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < nt) out[t] = (int32_t)(ranges[t].y - ranges[t].x);
+}
+__global__ void ranges_i32_kernel(const uint2 *ranges, int nt, int32_t *out) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < nt) {
+        out[2 * t] = (int32_t)ranges[t].x;
+        out[2 * t + 1] = (int32_t)ranges[t].y;
+    }
+}
+}  // namespace
+
+extern "C" {
+
+conegs_status conegs_get_bin_counts(const conegs_view *v, int32_t *per_gaussian, int32_t *per_tile, void *stream) {
+    if (!v || !v->has_forward) return fail(CONEGS_ERR_STATE, "get_bin_counts: no render on this view");
+    DeviceGuard g(v->ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(cudaStreamWaitEvent(s, v->done, 0));
+    const int nt = v->cam.tiles_x * v->cam.tiles_y;
+    if (per_gaussian && v->ctx->sp.n > 0)
+        CUDA_TRY(cudaMemcpyAsync(per_gaussian, v->counts.p, sizeof(uint32_t) * (size_t)v->ctx->sp.n,
+                                 cudaMemcpyDeviceToDevice, s));
+    if (per_tile) {
+        range_counts_kernel<<<(nt + 255) / 256, 256, 0, s>>>(v->ranges.as<uint2>(), nt, per_tile);
+        CUDA_TRY(cudaGetLastError());
+    }
+    return CONEGS_OK;
+}
+
+conegs_status conegs_get_pairs(const conegs_view *v, int32_t *gaussian_ids, int32_t *tile_ranges, void *stream) {
+    if (!v || !v->has_forward) return fail(CONEGS_ERR_STATE, "get_pairs: no render on this view");
+    DeviceGuard g(v->ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(cudaStreamWaitEvent(s, v->done, 0));
+    const int nt = v->cam.tiles_x * v->cam.tiles_y;
+    if (gaussian_ids && v->n_pairs > 0)
+        CUDA_TRY(cudaMemcpyAsync(gaussian_ids, v->pair_gid.p, sizeof(uint32_t) * (size_t)v->n_pairs,
+                                 cudaMemcpyDeviceToDevice, s));
+    if (tile_ranges) {
+        ranges_i32_kernel<<<(nt + 255) / 256, 256, 0, s>>>(v->ranges.as<uint2>(), nt, tile_ranges);
+        CUDA_TRY(cudaGetLastError());
+    }
+    return CONEGS_OK;
+}
+
+conegs_status conegs_radix_sort_pairs(conegs_ctx *ctx, uint32_t *keys, uint32_t *values, int64_t n, int begin_bit,
+                                      int end_bit, void *stream) {
+    if (!ctx || n < 0 || (n > 0 && (!keys || !values))) return fail(CONEGS_ERR_ARG, "radix_sort_pairs: bad argument");
+    if (begin_bit < 0 || end_bit > 32 || begin_bit > end_bit) return fail(CONEGS_ERR_ARG, "radix_sort_pairs: bad bits");
+    if (n > (1LL << 31)) return fail(CONEGS_ERR_ARG, "radix_sort_pairs: n too large");
+    if (n <= 1) return CONEGS_OK;
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    void *ak = nullptr, *av = nullptr, *scr = nullptr;
+    CUDA_TRY(cudaMallocAsync(&ak, sizeof(uint32_t) * (size_t)n, s));
+    CUDA_TRY(cudaMallocAsync(&av, sizeof(uint32_t) * (size_t)n, s));
+    CUDA_TRY(cudaMallocAsync(&scr, sizeof(uint32_t) * (size_t)radix_scratch_words(n), s));
+    cudaError_t e = radix_sort_pairs(keys, values, (uint32_t *)ak, (uint32_t *)av, n, begin_bit, end_bit,
+                                     (uint32_t *)scr, s);
+    cudaFreeAsync(ak, s);
+    cudaFreeAsync(av, s);
+    cudaFreeAsync(scr, s);
+    if (e != cudaSuccess) return fail(CONEGS_ERR_CUDA, "radix_sort_pairs: %s", cudaGetErrorString(e));
+    return CONEGS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,258 @@
+// K3: conservative angular-tile binning.
+//
+// The paper has no binning stage; this one is the library's own rule,
+// written so that its decisions are reproducible bit for bit: every
+// operation below is one correctly rounded FP32 operation (_rn intrinsics,
+// no contraction) in a fixed order, and the transcendental functions the
+// rule needs are replaced by fixed polynomials (Taylor series of exp, sin
+// and cos).  The rule:
+//   * tile cone: axis a_t = ray of the tile centre; half-angle gamma from the
+//     largest chord |a_t - d_p| over the tile's valid pixel rays, inflated;
+//     m_t >= (|delta_x|^2 + |delta_y|^2)/3 over the tile;
+//   * Gaussian bound: alpha >= 1/255 needs q^T A^-1 q <= kappa^2 =
+//     2 ln(255 sigma), so the world distance from mu to a contributing
+//     centre ray is at most kappa sqrt(s_max^2 + t*^2 m) (A >= I and
+//     Sigma_render <= Sigma_fp,eff, Eq. 9 and 12), with
+//     t* <= (L + kappa s_max) / (1 - kappa (1 + s_max/s_min) sqrt(m)) and
+//     |x* - mu| <= 255 kappa s_max (from det A <= (255 sigma)^2);
+//   * a (Gaussian, tile) pair is kept when the angle between mu - o and a_t
+//     is at most beta + gamma, sin(beta) = bound / L (chord form).
+// Two levels: super-tiles of 8x8 tiles prune (conservatively, with extra
+// margins), then the exact per-tile rule decides.
+#include "rule.cuh"
+
+namespace conegs {
+
+// ---------------------------------------------------------------- tile tables
+
+// One CTA of 256 threads per tile; thread = pixel.  Max-reductions are exact
+// and order independent.
+__global__ void __launch_bounds__(256) tile_table_kernel(CamParams c, float *__restrict__ table) {
+    const int t = blockIdx.x;
+    const int tx = t % c.tiles_x, ty = t / c.tiles_x;
+    const int i = tx * TILE + (threadIdx.x % TILE), j = ty * TILE + (threadIdx.x / TILE);
+    __shared__ float s_a[3];
+    if (threadIdx.x == 0) {
+        float a[3];
+        rule_dir(c, (float)(TILE * tx + TILE / 2), (float)(TILE * ty + TILE / 2), a);
+        s_a[0] = a[0]; s_a[1] = a[1]; s_a[2] = a[2];
+    }
+    __syncthreads();
+    float ch2 = -1.0f, mm = 0.0f;
+    if (i < c.W && j < c.H) {
+        float x = (float)i + 0.5f, y = (float)j + 0.5f;
+        if (rule_valid(c, x, y)) {
+            float d[3], ex[3], ey[3];
+            rule_dir(c, x, y, d);
+            float e0 = r_sub(s_a[0], d[0]), e1 = r_sub(s_a[1], d[1]), e2 = r_sub(s_a[2], d[2]);
+            ch2 = r_add(r_add(r_mul(e0, e0), r_mul(e1, e1)), r_mul(e2, e2));
+            rule_edge(c, x, y, d, 0, ex);
+            rule_edge(c, x, y, d, 1, ey);
+            mm = r_div(r_add(r_add(r_add(r_mul(ex[0], ex[0]), r_mul(ex[1], ex[1])), r_mul(ex[2], ex[2])),
+                       r_add(r_add(r_mul(ey[0], ey[0]), r_mul(ey[1], ey[1])), r_mul(ey[2], ey[2]))),
+                    3.0f);
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        ch2 = fmaxf(ch2, __shfl_xor_sync(0xffffffffu, ch2, off));
+        mm = fmaxf(mm, __shfl_xor_sync(0xffffffffu, mm, off));
+    }
+    __shared__ float s_ch[8], s_mm[8];
+    if ((threadIdx.x & 31) == 0) {
+        s_ch[threadIdx.x >> 5] = ch2;
+        s_mm[threadIdx.x >> 5] = mm;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float chm = s_ch[0], mmm = s_mm[0];
+        for (int w = 1; w < 8; ++w) {
+            chm = fmaxf(chm, s_ch[w]);
+            mmm = fmaxf(mmm, s_mm[w]);
+        }
+        float *o = table + 6 * (size_t)t;
+        o[0] = s_a[0]; o[1] = s_a[1]; o[2] = s_a[2];
+        if (chm < 0.0f) {
+            o[3] = -1.0f; o[4] = 0.0f; o[5] = 0.0f;
+        } else {
+            float sg = r_add(r_mul(r_sqrt(chm), 0.5f), 2e-6f);
+            sg = fminf(sg, 1.0f);
+            o[3] = sg;
+            o[4] = r_sqrt(r_sub(1.0f, r_mul(sg, sg)));
+            o[5] = r_mul(mmm, 1.01f);
+        }
+    }
+}
+
+// Super-tile cones containing every child tile cone (pruning only; extra margins).
+__global__ void super_table_kernel(CamParams c, const float *__restrict__ table, float *__restrict__ super) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= c.supers_x * c.supers_y) return;
+    const int sx = s % c.supers_x, sy = s / c.supers_x;
+    float a[3];
+    rule_dir(c, (float)(TILE * SUPER * sx + TILE * SUPER / 2), (float)(TILE * SUPER * sy + TILE * SUPER / 2), a);
+    float best = -1.0f, mmax = 0.0f;
+    for (int cy = 0; cy < SUPER; ++cy)
+        for (int cx = 0; cx < SUPER; ++cx) {
+            int tx = sx * SUPER + cx, ty = sy * SUPER + cy;
+            if (tx >= c.tiles_x || ty >= c.tiles_y) continue;
+            const float *t = table + 6 * (size_t)(ty * c.tiles_x + tx);
+            if (t[3] < 0.0f) continue;
+            float e0 = a[0] - t[0], e1 = a[1] - t[1], e2 = a[2] - t[2];
+            float sa = 0.5f * sqrtf(e0 * e0 + e1 * e1 + e2 * e2);
+            sa = fminf(sa, 1.0f);
+            float ca = sqrtf(fmaxf(1.0f - sa * sa, 0.0f));
+            float shalf = sa * t[4] + ca * t[3];      // sin((alpha + gamma)/2)
+            float chalf = ca * t[4] - sa * t[3];      // cos((alpha + gamma)/2)
+            if (chalf < 1e-3f) shalf = 1.0f;
+            best = fmaxf(best, shalf);
+            mmax = fmaxf(mmax, t[5]);
+        }
+    float *o = super + 6 * (size_t)s;
+    o[0] = a[0]; o[1] = a[1]; o[2] = a[2];
+    if (best < 0.0f) {
+        o[3] = -1.0f; o[4] = 0.0f; o[5] = 0.0f;
+        return;
+    }
+    float sg = fminf(best * 1.0001f + 1e-6f, 1.0f);
+    o[3] = sg;
+    o[4] = sqrtf(fmaxf(1.0f - sg * sg, 0.0f));
+    o[5] = mmax * 1.0001f;
+}
+
+// ---------------------------------------------------------------- Gaussian bounds
+
+__global__ void gauss_scene_rule_kernel(SceneParams sp, float *__restrict__ binrec) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= sp.n) return;
+    float ls[3] = {sp.log_scales[3 * i], sp.log_scales[3 * i + 1], sp.log_scales[3 * i + 2]};
+    float logit = load_scalar(sp.logits, i, sp.storage);
+    float rho2 = sp.rho2 ? sp.rho2[i] : 0.0f;
+    float rec[6];
+    rule_gauss_scene(ls, logit, rho2, rec);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) binrec[6 * i + k] = rec[k];
+}
+
+// Per view: u, L (float4) and the view flag (0 culled, 1 normal, 2 pass-all).
+__global__ void gauss_view_rule_kernel(CamParams c, SceneParams sp, float4 *__restrict__ gview,
+                                       uint8_t *__restrict__ gflag) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= sp.n) return;
+    float mu[3] = {sp.means[3 * i], sp.means[3 * i + 1], sp.means[3 * i + 2]};
+    float flag = sp.binrec[6 * i + 5], u[3], L;
+    rule_gauss_view(c, mu, flag, u, L);
+    gview[i] = make_float4(u[0], u[1], u[2], L);
+    gflag[i] = (uint8_t)flag;
+}
+
+// ---------------------------------------------------------------- count / emit
+
+// One warp per Gaussian.  MODE 0: count tiles into counts[gid].
+// MODE 1: emit tile ids at offsets[pos] for the Gaussian order[pos].
+template <int MODE>
+__global__ void __launch_bounds__(256) bin_kernel(CamParams c, const float *__restrict__ binrec,
+                                                  const float4 *__restrict__ gview,
+                                                  const uint8_t *__restrict__ gflag, const float *__restrict__ table,
+                                                  const float *__restrict__ super, int64_t n,
+                                                  const uint32_t *__restrict__ order,
+                                                  const uint32_t *__restrict__ offsets,
+                                                  uint32_t *__restrict__ counts, uint32_t *__restrict__ out_tile,
+                                                  uint32_t *__restrict__ out_gid) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= n) return;
+    const uint32_t gid = MODE == 0 ? (uint32_t)w : order[w];
+    const uint8_t fl = gflag[gid];
+    if (fl == 0) {
+        if (MODE == 0 && lane == 0) counts[gid] = 0;
+        return;
+    }
+    float g[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) g[k] = binrec[6 * (size_t)gid + k];
+    g[5] = (float)fl;
+    const float4 gv = gview[gid];
+    const int nsup = c.supers_x * c.supers_y;
+    uint32_t base = MODE == 1 ? offsets[w] : 0;
+    uint32_t cnt = 0;
+    for (int s0 = 0; s0 < nsup; s0 += 32) {
+        const int s = s0 + lane;
+        bool sp = false;
+        if (s < nsup) sp = rule_test(g, gv, super + 6 * (size_t)s);
+        uint32_t bal = __ballot_sync(0xffffffffu, sp);
+        while (bal) {
+            const int b = __ffs(bal) - 1;
+            bal &= bal - 1;
+            const int ss = s0 + b;
+            const int sx = ss % c.supers_x, sy = ss / c.supers_x;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int child = lane + 32 * h;
+                const int tx = sx * SUPER + (child % SUPER), ty = sy * SUPER + (child / SUPER);
+                bool tp = false;
+                uint32_t tile = 0;
+                if (tx < c.tiles_x && ty < c.tiles_y) {
+                    tile = (uint32_t)(ty * c.tiles_x + tx);
+                    tp = rule_test(g, gv, table + 6 * (size_t)tile);
+                }
+                const uint32_t tb = __ballot_sync(0xffffffffu, tp);
+                if (MODE == 1 && tp) {
+                    const uint32_t pos = base + cnt + __popc(tb & ((1u << lane) - 1u));
+                    out_tile[pos] = tile;
+                    out_gid[pos] = gid;
+                }
+                cnt += __popc(tb);
+            }
+        }
+    }
+    if (MODE == 0 && lane == 0) counts[gid] = cnt;
+}
+
+// ---------------------------------------------------------------- launchers
+
+cudaError_t launch_tile_tables(const CamParams &c, float *table, float *super, cudaStream_t s) {
+    const int nt = c.tiles_x * c.tiles_y, ns = c.supers_x * c.supers_y;
+    if (nt == 0) return cudaSuccess;
+    tile_table_kernel<<<nt, 256, 0, s>>>(c, table);
+    note_launches(1);
+    super_table_kernel<<<(unsigned)div_up(ns, 128), 128, 0, s>>>(c, table, super);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gauss_scene_rule(const SceneParams &sp, float *binrec, cudaStream_t s) {
+    if (sp.n == 0) return cudaSuccess;
+    gauss_scene_rule_kernel<<<(unsigned)div_up(sp.n, 256), 256, 0, s>>>(sp, binrec);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gauss_view_rule(const CamParams &c, const SceneParams &sp, float4 *gview, uint8_t *gflag,
+                                   cudaStream_t s) {
+    if (sp.n == 0) return cudaSuccess;
+    gauss_view_rule_kernel<<<(unsigned)div_up(sp.n, 256), 256, 0, s>>>(c, sp, gview, gflag);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bin_count(const CamParams &c, const float *binrec, const float4 *gview, const uint8_t *gflag,
+                             const float *table, const float *super, int64_t n, uint32_t *counts, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    bin_kernel<0><<<(unsigned)div_up(n * 32, 256), 256, 0, s>>>(c, binrec, gview, gflag, table, super, n, nullptr,
+                                                               nullptr, counts, nullptr, nullptr);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bin_emit(const CamParams &c, const float *binrec, const float4 *gview, const uint8_t *gflag,
+                            const float *table, const float *super, int64_t n_sorted, const uint32_t *order,
+                            const uint32_t *offsets, uint32_t *out_tile, uint32_t *out_gid, cudaStream_t s) {
+    if (n_sorted == 0) return cudaSuccess;
+    bin_kernel<1><<<(unsigned)div_up(n_sorted * 32, 256), 256, 0, s>>>(c, binrec, gview, gflag, table, super,
+                                                                      n_sorted, order, offsets, nullptr, out_tile,
+                                                                      out_gid);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace conegs

@@ -1,0 +1,57 @@
+// Shared device-side definitions of the ConeGaussian CUDA library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace conegs {
+
+constexpr int TILE = 16;          // tile side in pixels (one CTA of 256 threads per tile)
+constexpr int SUPER = 8;          // tiles per super-tile side (coarse binning level)
+constexpr float ALPHA_MIN = 1.0f / 255.0f;
+constexpr float ALPHA_MAX = 0.99f;
+constexpr float T_STOP = 1e-4f;
+constexpr float T_NEAR = 0.01f;
+constexpr int REC_F4 = 5;         // float4 words per per-view raster record
+
+// Camera passed by value to kernels.
+struct CamParams {
+    int model;        // 0 pinhole, 1 Kannala-Brandt
+    int W, H, tiles_x, tiles_y, supers_x, supers_y;
+    float fx, fy, cx, cy;
+    float k[4];
+    float R[9];       // camera -> world rotation, row-major
+    float o[3];       // optical centre
+    float thlim;      // KB valid half-FOV (rad)
+    float rlim2;      // KB squared normalised radius limit (FP32 rule)
+};
+
+// Scene arrays (caller-owned parameters + library cache), passed by value.
+struct SceneParams {
+    int64_t n;
+    int sh_degree;
+    int storage;                  // 0 f32, 1 bf16, 2 f16
+    const float *means, *log_scales, *quats, *rho2;
+    const void *logits, *sh;
+    // camera-independent cache
+    const float *W;               // [n][9] W_eff = S_eff^-1 R^T
+    const float *sig_eff;         // [n]
+    const float *binrec;          // [n][6] kap, ks, kr, r1sq, s2, flag
+};
+
+__device__ __forceinline__ float load_scalar(const void *p, int64_t i, int storage) {
+    if (storage == 1) return __bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(p)[i]);
+    if (storage == 2) return __half2float(reinterpret_cast<const __half *>(p)[i]);
+    return reinterpret_cast<const float *>(p)[i];
+}
+
+__host__ __device__ __forceinline__ int64_t div_up(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Host-side count of kernel launches issued by the library (reported by
+// conegs_get_stats for the last render).
+void note_launches(int k);
+long long launches_so_far();
+
+}  // namespace conegs

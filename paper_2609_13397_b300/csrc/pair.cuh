@@ -1,0 +1,119 @@
+// Per pixel-Gaussian pair response (Sec. 4.1-4.2) in FP32 registers.
+//
+// With d_u = W d, g_i = W delta_i (W = W_eff), n = |d_u|^2:
+//   t* = -<o_u, d_u>/n,  q = o_u + t* d_u                          (Eq. 2)
+//   e_i = t* (g_i - d_u <d_u, g_i>/n) = t* M_perp W delta_i          (Eq. 6)
+//   Sigma_fp = E E^T / 3, E = [e_x e_y]                               (Eq. 8)
+// Eq. 12 keeps only the world-space footprint variance beyond rho^2.  The
+// world half-edges are f_i = W^-1 e_i = t* (delta_i - d <d_u, g_i>/n); with
+// H' = [f_i . f_j]/3 (eigenpairs lambda_j, v_j) the clamped, re-whitened
+// footprint is E K E^T with K = sum_j max(lambda_j - rho^2, 0)/(3 lambda_j)
+// v_j v_j^T, a 2x2 matrix function of H' (rho = 0 gives K = I/3).
+// A = I + E K E^T, so with G = E^T E and b = E^T q (Sylvester / Woodbury):
+//   det A = det(I + G K),  q^T A^-1 q = |q|^2 - b^T K (I + G K)^-1 b
+//   T = sigma_eff det(A)^-1/2 exp(-q^T A^-1 q / 2)                   (Eq. 9)
+// No 3x3 matrix and no plane basis is formed.
+#pragma once
+#include "common.cuh"
+
+namespace conegs {
+
+struct PixelRays {
+    float d[3], dx[3], dy[3];
+    float d_dx, d_dy, dxdx, dxdy, dydy;   // for the marginal rule (Eq. 12)
+};
+
+__device__ __forceinline__ float dot3(const float a[3], const float b[3]) {
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+// 2x2 matrix function K = f(H') of Eq. 12 (H' symmetric PSD), f(l) = max(l - rho2, 0) / (3 l).
+__device__ __forceinline__ void marginal_K(float h00, float h01, float h11, float rho2, float &k00, float &k01,
+                                           float &k11) {
+    const float mean = 0.5f * (h00 + h11);
+    const float half = 0.5f * (h00 - h11);
+    const float rad = sqrtf(half * half + h01 * h01);
+    const float l1 = mean + rad;
+    if (!(l1 > rho2)) {
+        k00 = k01 = k11 = 0.0f;
+        return;
+    }
+    const float det = h00 * h11 - h01 * h01;
+    const float l2 = fmaxf(det, 0.0f) / l1;   // smaller eigenvalue without cancellation
+    if (l2 > rho2) {
+        // both directions exceed the floor: K = (I - rho2 H'^-1)/3
+        const float s = rho2 / det;
+        k00 = (1.0f - s * h11) * (1.0f / 3.0f);
+        k11 = (1.0f - s * h00) * (1.0f / 3.0f);
+        k01 = (s * h01) * (1.0f / 3.0f);
+    } else {
+        // only the major direction exceeds: K = f(l1) (H' - l2 I)/(l1 - l2)
+        const float f1 = (l1 - rho2) / (3.0f * l1);
+        const float sc = f1 / (l1 - l2);
+        k00 = sc * (h00 - l2);
+        k11 = sc * (h11 - l2);
+        k01 = sc * h01;
+    }
+}
+
+// Response of one pair.  r0..r2 = [W row | o_u], r3 = [rgb | sigma_eff], rho2.
+// Returns false when t* <= T_NEAR (pair skipped).
+template <bool FILTER>
+__device__ __forceinline__ bool pair_response(const float4 r0, const float4 r1, const float4 r2, const float sig,
+                                              const float rho2, const bool additive, const PixelRays &px,
+                                              float &T) {
+    const float du0 = r0.x * px.d[0] + r0.y * px.d[1] + r0.z * px.d[2];
+    const float du1 = r1.x * px.d[0] + r1.y * px.d[1] + r1.z * px.d[2];
+    const float du2 = r2.x * px.d[0] + r2.y * px.d[1] + r2.z * px.d[2];
+    const float n = du0 * du0 + du1 * du1 + du2 * du2;
+    const float inv_n = 1.0f / n;
+    const float p = r0.w * du0 + r1.w * du1 + r2.w * du2;
+    const float ts = -p * inv_n;
+    if (!(ts > T_NEAR)) return false;
+    const float q0 = r0.w + ts * du0, q1 = r1.w + ts * du1, q2 = r2.w + ts * du2;
+    const float qq = q0 * q0 + q1 * q1 + q2 * q2;
+    if (!FILTER) {
+        T = sig * __expf(-0.5f * qq);
+        return true;
+    }
+    const float gx0 = r0.x * px.dx[0] + r0.y * px.dx[1] + r0.z * px.dx[2];
+    const float gx1 = r1.x * px.dx[0] + r1.y * px.dx[1] + r1.z * px.dx[2];
+    const float gx2 = r2.x * px.dx[0] + r2.y * px.dx[1] + r2.z * px.dx[2];
+    const float gy0 = r0.x * px.dy[0] + r0.y * px.dy[1] + r0.z * px.dy[2];
+    const float gy1 = r1.x * px.dy[0] + r1.y * px.dy[1] + r1.z * px.dy[2];
+    const float gy2 = r2.x * px.dy[0] + r2.y * px.dy[1] + r2.z * px.dy[2];
+    const float cx = (du0 * gx0 + du1 * gx1 + du2 * gx2) * inv_n;
+    const float cy = (du0 * gy0 + du1 * gy1 + du2 * gy2) * inv_n;
+    const float ex0 = ts * (gx0 - cx * du0), ex1 = ts * (gx1 - cx * du1), ex2 = ts * (gx2 - cx * du2);
+    const float ey0 = ts * (gy0 - cy * du0), ey1 = ts * (gy1 - cy * du1), ey2 = ts * (gy2 - cy * du2);
+    const float G00 = ex0 * ex0 + ex1 * ex1 + ex2 * ex2;
+    const float G01 = ex0 * ey0 + ex1 * ey1 + ex2 * ey2;
+    const float G11 = ey0 * ey0 + ey1 * ey1 + ey2 * ey2;
+    const float b0 = ex0 * q0 + ex1 * q1 + ex2 * q2;
+    const float b1 = ey0 * q0 + ey1 * q1 + ey2 * q2;
+    float det, bPb;
+    if (rho2 == 0.0f || additive) {
+        // K = I/3
+        const float m00 = 1.0f + G00 * (1.0f / 3.0f), m11 = 1.0f + G11 * (1.0f / 3.0f), m01 = G01 * (1.0f / 3.0f);
+        det = m00 * m11 - m01 * m01;
+        bPb = (b0 * b0 * m11 - 2.0f * b0 * b1 * m01 + b1 * b1 * m00) * (1.0f / 3.0f);
+    } else {
+        const float t2 = ts * ts * (1.0f / 3.0f);
+        const float h00 = t2 * (px.dxdx - 2.0f * cx * px.d_dx + cx * cx);
+        const float h01 = t2 * (px.dxdy - cx * px.d_dy - cy * px.d_dx + cx * cy);
+        const float h11 = t2 * (px.dydy - 2.0f * cy * px.d_dy + cy * cy);
+        float k00, k01, k11;
+        marginal_K(h00, h01, h11, rho2, k00, k01, k11);
+        const float m00 = 1.0f + G00 * k00 + G01 * k01, m01 = G00 * k01 + G01 * k11;
+        const float m10 = G01 * k00 + G11 * k01, m11 = 1.0f + G01 * k01 + G11 * k11;
+        det = m00 * m11 - m01 * m10;
+        const float p00 = k00 * m11 - k01 * m10, p01 = k01 * m00 - k00 * m01;
+        const float p10 = k01 * m11 - k11 * m10, p11 = k11 * m00 - k01 * m01;
+        bPb = b0 * b0 * p00 + b0 * b1 * (p01 + p10) + b1 * b1 * p11;
+    }
+    const float Q = qq - bPb / det;
+    T = sig * rsqrtf(det) * __expf(-0.5f * Q);
+    return true;
+}
+
+}  // namespace conegs

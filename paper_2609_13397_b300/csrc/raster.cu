@@ -1,0 +1,122 @@
+// K5: tile rasteriser, forward (Sec. 3 Eq. 4 compositing over Eq. 9 responses).
+//
+// One CTA of 256 threads per 16x16 tile, one thread per pixel.  The tile's
+// depth-sorted Gaussian list is walked in batches of 256: each thread loads
+// one Gaussian's 80-byte record (5 x float4, coalesced gather) into shared
+// memory, then every thread evaluates the whole batch against its pixel's
+// rays from registers.  Compositing follows the 3DGS conventions: a =
+// min(0.99, T); pairs with a < 1/255 are skipped; a pixel stops before the
+// pair that would take its transmittance below 1e-4; the CTA leaves the
+// list as soon as all its pixels have stopped (__syncthreads_count).
+// Per pixel the kernel writes rgb, the final transmittance and the number of
+// list entries walked up to the last contributing pair (for the adjoint).
+#include "pair.cuh"
+
+namespace conegs {
+
+struct RasterArgs {
+    int W, H, tiles_x;
+    const uint2 *ranges;
+    const uint32_t *gids;
+    const float4 *rec;
+    const float *d, *dx, *dy;
+    const uint8_t *valid;
+    float *out_rgb, *out_T, *keep_T;   // keep_T: copy of the final T kept for the adjoint (may be NULL)
+    uint32_t *last;        // per pixel: list entries up to and including the last contributor
+    unsigned long long *evaluated;   // optional: total pair evaluations (profiling)
+    int additive;
+};
+
+__device__ __forceinline__ void load_pixel(const RasterArgs &a, int64_t pix, int64_t P, PixelRays &px) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        px.d[k] = a.d[k * P + pix];
+        px.dx[k] = a.dx[k * P + pix];
+        px.dy[k] = a.dy[k * P + pix];
+    }
+    px.d_dx = dot3(px.d, px.dx);
+    px.d_dy = dot3(px.d, px.dy);
+    px.dxdx = dot3(px.dx, px.dx);
+    px.dxdy = dot3(px.dx, px.dy);
+    px.dydy = dot3(px.dy, px.dy);
+}
+
+template <bool FILTER>
+__global__ void __launch_bounds__(256) raster_fwd_kernel(const RasterArgs a) {
+    __shared__ float4 s_rec[REC_F4][256];
+    const int tile = blockIdx.x;
+    const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+    const int i = tx * TILE + (threadIdx.x % TILE), j = ty * TILE + (threadIdx.x / TILE);
+    const int64_t P = (int64_t)a.W * a.H;
+    const bool inside = i < a.W && j < a.H;
+    const int64_t pix = (int64_t)j * a.W + i;
+    PixelRays px;
+    bool done = true;
+    if (inside && a.valid[pix]) {
+        load_pixel(a, pix, P, px);
+        done = false;
+    }
+    const uint2 range = a.ranges[tile];
+    float C0 = 0.f, C1 = 0.f, C2 = 0.f, Tacc = 1.0f;
+    uint32_t last = 0, walked = 0;
+    for (uint32_t start = range.x; start < range.y; start += 256) {
+        if (__syncthreads_count(done) == 256) break;
+        const uint32_t idx = start + threadIdx.x;
+        if (idx < range.y) {
+            const float4 *r = a.rec + (size_t)REC_F4 * a.gids[idx];
+#pragma unroll
+            for (int k = 0; k < REC_F4; ++k) s_rec[k][threadIdx.x] = r[k];
+        }
+        __syncthreads();
+        const int nb = (int)min(256u, range.y - start);
+        if (!done) {
+            for (int b = 0; b < nb; ++b) {
+                ++walked;
+                const float4 r3 = s_rec[3][b];
+                float T;
+                if (!pair_response<FILTER>(s_rec[0][b], s_rec[1][b], s_rec[2][b], r3.w, s_rec[4][b].x,
+                                           a.additive != 0, px, T))
+                    continue;
+                const float alpha = fminf(ALPHA_MAX, T);
+                if (alpha < ALPHA_MIN) continue;
+                const float test = Tacc * (1.0f - alpha);
+                if (test < T_STOP) {
+                    done = true;
+                    break;
+                }
+                const float w = alpha * Tacc;
+                C0 += r3.x * w;
+                C1 += r3.y * w;
+                C2 += r3.z * w;
+                Tacc = test;
+                last = walked;
+            }
+        }
+        __syncthreads();
+    }
+    if (a.evaluated) {
+        unsigned long long w = done || inside ? walked : 0;
+        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(a.evaluated, w);
+    }
+    if (inside) {
+        a.out_rgb[pix] = C0;
+        a.out_rgb[P + pix] = C1;
+        a.out_rgb[2 * P + pix] = C2;
+        if (a.out_T) a.out_T[pix] = Tacc;
+        if (a.keep_T) a.keep_T[pix] = Tacc;
+        if (a.last) a.last[pix] = last;
+    }
+}
+
+cudaError_t launch_raster_fwd(const RasterArgs &a, int ntiles, bool filter, cudaStream_t s) {
+    if (ntiles == 0) return cudaSuccess;
+    if (filter)
+        raster_fwd_kernel<true><<<ntiles, 256, 0, s>>>(a);
+    else
+        raster_fwd_kernel<false><<<ntiles, 256, 0, s>>>(a);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace conegs

@@ -1,0 +1,193 @@
+// FP32 binning-rule primitives (see binning.cu for the rule).  Every
+// operation is one correctly rounded FP32 operation through an explicit _rn
+// intrinsic, evaluated in the order written, so the rule's decisions are the
+// same bits on every build and in any reference that follows the same
+// operation sequence.
+#pragma once
+#include "common.cuh"
+
+namespace conegs {
+
+__device__ __forceinline__ float r_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float r_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float r_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float r_div(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float r_sqrt(float a) { return __fsqrt_rn(a); }
+
+// ---------------------------------------------------------------- FP32 rule primitives
+
+__device__ __forceinline__ bool rule_valid(const CamParams &c, float x, float y) {
+    if (c.model == 0) return true;
+    float a = r_div(r_sub(x, c.cx), c.fx);
+    float b = r_div(r_sub(y, c.cy), c.fy);
+    float r2 = r_add(r_mul(a, a), r_mul(b, b));
+    return r2 <= c.rlim2;
+}
+
+__device__ __forceinline__ void rule_sincos(float t, float &sn, float &cs) {
+    const float S1 = (float)(-1.0 / 6.0), S2 = (float)(1.0 / 120.0), S3 = (float)(-1.0 / 5040.0),
+                S4 = (float)(1.0 / 362880.0), S5 = (float)(-1.0 / 39916800.0),
+                S6 = (float)(1.0 / 6227020800.0), S7 = (float)(-1.0 / 1307674368000.0),
+                S8 = (float)(1.0 / 355687428096000.0);
+    const float C1 = (float)(-1.0 / 2.0), C2 = (float)(1.0 / 24.0), C3 = (float)(-1.0 / 720.0),
+                C4 = (float)(1.0 / 40320.0), C5 = (float)(-1.0 / 3628800.0), C6 = (float)(1.0 / 479001600.0),
+                C7 = (float)(-1.0 / 87178291200.0), C8 = (float)(1.0 / 20922789888000.0);
+    float t2 = r_mul(t, t);
+    float s = S8;
+    s = r_add(r_mul(s, t2), S7); s = r_add(r_mul(s, t2), S6); s = r_add(r_mul(s, t2), S5); s = r_add(r_mul(s, t2), S4);
+    s = r_add(r_mul(s, t2), S3); s = r_add(r_mul(s, t2), S2); s = r_add(r_mul(s, t2), S1); s = r_add(r_mul(s, t2), 1.0f);
+    sn = r_mul(s, t);
+    float c = C8;
+    c = r_add(r_mul(c, t2), C7); c = r_add(r_mul(c, t2), C6); c = r_add(r_mul(c, t2), C5); c = r_add(r_mul(c, t2), C4);
+    c = r_add(r_mul(c, t2), C3); c = r_add(r_mul(c, t2), C2); c = r_add(r_mul(c, t2), C1); c = r_add(r_mul(c, t2), 1.0f);
+    cs = c;
+}
+
+static __device__ __noinline__ void rule_dir(const CamParams &c, float x, float y, float out[3]) {
+    float a = r_div(r_sub(x, c.cx), c.fx);
+    float b = r_div(r_sub(y, c.cy), c.fy);
+    float v0, v1, v2;
+    if (c.model == 0) {
+        float n2 = r_add(r_add(r_mul(a, a), r_mul(b, b)), 1.0f);
+        float s = r_sqrt(n2);
+        v0 = r_div(a, s); v1 = r_div(b, s); v2 = r_div(1.0f, s);
+    } else {
+        float r2 = r_add(r_mul(a, a), r_mul(b, b));
+        float r = r_sqrt(r2);
+        float th = fminf(r, c.thlim);
+        for (int it = 0; it < 12; ++it) {
+            float t2 = r_mul(th, th);
+            float p = r_add(r_mul(r_add(r_mul(r_add(r_mul(c.k[3], t2), c.k[2]), t2), c.k[1]), t2), c.k[0]);
+            float f = r_sub(r_mul(th, r_add(1.0f, r_mul(t2, p))), r);
+            float dp = r_add(r_mul(r_add(r_mul(r_add(r_mul(r_mul(9.0f, c.k[3]), t2), r_mul(7.0f, c.k[2])), t2), r_mul(5.0f, c.k[1])), t2),
+                          r_mul(3.0f, c.k[0]));
+            float fp = r_add(1.0f, r_mul(t2, dp));
+            th = r_sub(th, r_div(f, fp));
+            th = fminf(fmaxf(th, 0.0f), c.thlim);
+        }
+        float sn, cs;
+        rule_sincos(th, sn, cs);
+        if (r > 0.0f) {
+            v0 = r_div(r_mul(sn, a), r);
+            v1 = r_div(r_mul(sn, b), r);
+        } else {
+            v0 = 0.0f;
+            v1 = 0.0f;
+        }
+        v2 = cs;
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) out[i] = r_add(r_add(r_mul(c.R[3 * i], v0), r_mul(c.R[3 * i + 1], v1)), r_mul(c.R[3 * i + 2], v2));
+}
+
+static __device__ void rule_edge(const CamParams &c, float x, float y, const float d[3], int axis, float e[3]) {
+    float xp = axis == 0 ? r_add(x, 0.5f) : x, yp = axis == 1 ? r_add(y, 0.5f) : y, t[3];
+    if (rule_valid(c, xp, yp)) {
+        rule_dir(c, xp, yp, t);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) e[i] = r_sub(t[i], d[i]);
+    } else {
+        float xm = axis == 0 ? r_sub(x, 0.5f) : x, ym = axis == 1 ? r_sub(y, 0.5f) : y;
+        rule_dir(c, xm, ym, t);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) e[i] = r_sub(d[i], t[i]);
+    }
+}
+
+// exp(x) = 2^k sum_{j<=9} f^j/j!, x = k ln2 + f (relative error < 1e-5 on [-80, 80]).
+__device__ __forceinline__ float rule_exp(float x) {
+    const float INV_LN2 = (float)(1.0 / 0.69314718055994530942), LN2F = (float)0.69314718055994530942;
+    const float E2 = (float)(1.0 / 2.0), E3 = (float)(1.0 / 6.0), E4 = (float)(1.0 / 24.0),
+                E5 = (float)(1.0 / 120.0), E6 = (float)(1.0 / 720.0), E7 = (float)(1.0 / 5040.0),
+                E8 = (float)(1.0 / 40320.0), E9 = (float)(1.0 / 362880.0);
+    x = fminf(fmaxf(x, -80.0f), 80.0f);
+    float kf = floorf(r_mul(x, INV_LN2));
+    float f = r_sub(x, r_mul(kf, LN2F));
+    float p = E9;
+    p = r_add(r_mul(p, f), E8); p = r_add(r_mul(p, f), E7); p = r_add(r_mul(p, f), E6); p = r_add(r_mul(p, f), E5);
+    p = r_add(r_mul(p, f), E4); p = r_add(r_mul(p, f), E3); p = r_add(r_mul(p, f), E2); p = r_add(r_mul(p, f), 1.0f);
+    p = r_add(r_mul(p, f), 1.0f);
+    int k = (int)kf;
+    float two = __uint_as_float((uint32_t)(k + 127) << 23);
+    return r_mul(p, two);
+}
+
+// Scene-level part of the Gaussian bound: kap, ks, kr, r1sq, s2, flag
+// (flag 0: sigma < 1/255, never contributes; 1: normal).
+static __device__ void rule_gauss_scene(const float ls[3], float logit, float rho2, float rec[6]) {
+    const float K255 = 11.082528f;   // >= 2 ln 255
+    const float LN2LO = 0.6931471f;  // <= ln 2
+    float lmax = fmaxf(fmaxf(ls[0], ls[1]), ls[2]);
+    float lmin = fminf(fminf(ls[0], ls[1]), ls[2]);
+    float s2 = r_add(r_mul(rule_exp(r_mul(2.0f, lmax)), 1.0001f), rho2);
+    float s2mn = r_add(r_mul(rule_exp(r_mul(2.0f, lmin)), 0.9999f), rho2);
+    float kap2 = r_sub(K255, r_mul(2.0f, fmaxf(fmaxf(0.0f, -logit), r_sub(LN2LO, r_mul(0.5f, logit)))));
+    if (!(kap2 > 0.0f)) {
+        rec[0] = rec[1] = rec[2] = rec[3] = rec[4] = 0.0f;
+        rec[5] = 0.0f;
+        return;
+    }
+    float kap = r_sqrt(kap2);
+    float s = r_sqrt(s2);
+    float r1 = r_add(1.0f, r_div(s, r_sqrt(s2mn)));
+    rec[0] = kap;
+    rec[1] = r_mul(kap, s);
+    rec[2] = r_mul(kap, r1);
+    rec[3] = r_mul(r1, r1);
+    rec[4] = s2;
+    rec[5] = 1.0f;
+}
+
+// View-level part: unit direction u = (mu - o)/L and L; flag 2 = pass-all.
+__device__ __forceinline__ void rule_gauss_view(const CamParams &c, const float mu[3], float &flag, float u[3],
+                                                float &L) {
+    float v0 = r_sub(mu[0], c.o[0]), v1 = r_sub(mu[1], c.o[1]), v2 = r_sub(mu[2], c.o[2]);
+    float L2 = r_add(r_add(r_mul(v0, v0), r_mul(v1, v1)), r_mul(v2, v2));
+    L = r_sqrt(L2);
+    u[0] = u[1] = u[2] = 0.0f;
+    if (flag == 0.0f) return;
+    if (!(L > 0.0f)) {
+        flag = 2.0f;
+        return;
+    }
+    u[0] = r_div(v0, L); u[1] = r_div(v1, L); u[2] = r_div(v2, L);
+}
+
+// The per (Gaussian, tile) test.  g: scene rec (kap ks kr r1sq s2 flag); gv: u0 u1 u2 L.
+__device__ __forceinline__ bool rule_test(const float *g, const float4 gv, const float *t) {
+    if (t[3] < 0.0f) return false;
+    if (g[5] == 0.0f) return false;
+    if (g[5] == 2.0f) return true;
+    const float L = gv.w, kap = g[0], ks = g[1], kr = g[2], r1sq = g[3], s2 = g[4];
+    const float m = t[5];
+    float sm = r_sqrt(m);
+    float cc = r_mul(kr, sm);
+    // two valid bounds on |x* - mu| and t*, combined by min (monotone in m)
+    float rfc = r_mul(255.0f, ks);
+    float tb, rf;
+    if (cc < 1.0f) {
+        float tbf = r_div(r_add(L, ks), r_sub(1.0f, cc));
+        float rff = r_mul(kap, r_sqrt(r_add(s2, r_mul(r_mul(r_mul(tbf, tbf), r1sq), m))));
+        rf = fminf(rff, rfc);
+        tb = fminf(tbf, r_add(L, rf));
+    } else {
+        rf = rfc;
+        tb = r_add(L, rf);
+    }
+    if (L <= rf) return true;
+    float rp = r_mul(kap, r_sqrt(r_add(s2, r_mul(r_mul(tb, tb), m))));
+    if (rp >= L) return true;
+    float sb = r_div(rp, L);
+    float cb = r_sqrt(r_sub(1.0f, r_mul(sb, sb)));
+    float sh2 = r_div(r_mul(sb, sb), r_mul(2.0f, r_add(1.0f, cb)));
+    float sbh = r_sqrt(sh2);
+    float cbh = r_sqrt(r_sub(1.0f, sh2));
+    float sphi = r_add(r_mul(sbh, t[4]), r_mul(cbh, t[3]));
+    float e0 = r_sub(gv.x, t[0]), e1 = r_sub(gv.y, t[1]), e2 = r_sub(gv.z, t[2]);
+    float ch2 = r_add(r_add(r_mul(e0, e0), r_mul(e1, e1)), r_mul(e2, e2));
+    float lim = r_add(r_mul(r_mul(2.0f, sphi), 1.0001f), 4e-6f);
+    return ch2 <= r_mul(lim, lim);
+}
+
+
+}  // namespace conegs

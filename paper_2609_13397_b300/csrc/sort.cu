@@ -1,0 +1,321 @@
+// K4: device scan, compaction and stable LSD radix sort of (key, value) pairs.
+//
+// Radix sort: 8-bit digits, reduce-then-scan.  A fixed grid of G blocks
+// each owns one contiguous chunk (a multiple of 4096 items); per pass
+//   upsweep   per-block digit histogram             -> counts[digit][block]
+//   scan      exclusive scan of the 256*G counters (digit-major)
+//   downsweep per 4096-item tile: each warp ranks its 512 items in lane order
+//             with __match_any_sync (stable), warps are offset by a per-digit
+//             scan across warps, items scatter to their global position.
+// Stability of every pass makes the whole sort stable, so equal keys keep
+// their input order (the binning stage relies on it: Gaussians are emitted
+// in depth order and the per-tile lists must keep that order).
+#include "common.cuh"
+
+namespace conegs {
+
+// ---------------------------------------------------------------- scan
+
+constexpr int SCAN_THREADS = 512;
+constexpr int SCAN_ITEMS = 4;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t &total) {
+    __shared__ uint32_t warp_sums[SCAN_THREADS / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t s = lane < SCAN_THREADS / 32 ? warp_sums[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < SCAN_THREADS / 32) warp_sums[lane] = s;
+    }
+    __syncthreads();
+    total = warp_sums[SCAN_THREADS / 32 - 1];
+    const uint32_t before = wid > 0 ? warp_sums[wid - 1] : 0u;
+    __syncthreads();
+    return before + x - v;
+}
+
+// out[i] = sum_{j<i} in[i] (per tile), block_sums[b] = tile total.
+// If pred != 0 the input is (in[i] > 0) instead of in[i].
+__global__ void __launch_bounds__(SCAN_THREADS) scan_tiles_kernel(const uint32_t *__restrict__ in, int64_t n,
+                                                                  uint32_t *__restrict__ out,
+                                                                  uint32_t *__restrict__ block_sums, int pred) {
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    uint32_t v[SCAN_ITEMS], s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        const int64_t i = base + k;
+        uint32_t x = i < n ? in[i] : 0u;
+        if (pred) x = x > 0u ? 1u : 0u;
+        v[k] = s;
+        s += x;
+    }
+    uint32_t total;
+    const uint32_t off = block_exclusive_scan(s, total);
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        const int64_t i = base + k;
+        if (i < n) out[i] = off + v[k];
+    }
+    if (threadIdx.x == 0 && block_sums) block_sums[blockIdx.x] = total;
+}
+
+__global__ void add_offsets_kernel(uint32_t *__restrict__ out, int64_t n, const uint32_t *__restrict__ offs) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] += offs[i / SCAN_TILE];
+}
+
+// Scratch words needed by exclusive_scan for n items.
+int64_t scan_scratch_words(int64_t n) {
+    int64_t w = 0;
+    while (n > SCAN_TILE) {
+        n = div_up(n, SCAN_TILE);
+        w += n;
+    }
+    return w + 1;
+}
+
+// Exclusive scan of n uint32 (or of in[i] > 0 when pred) into out; scratch of
+// scan_scratch_words(n) words.
+cudaError_t exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *scratch, int pred,
+                           cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int64_t nb = div_up(n, SCAN_TILE);
+    uint32_t *bs = nb > 1 ? scratch : nullptr;
+    scan_tiles_kernel<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, out, bs, pred);
+    note_launches(1);
+    if (nb > 1) {
+        cudaError_t e = exclusive_scan(bs, bs, nb, scratch + nb, 0, s);
+        if (e != cudaSuccess) return e;
+        add_offsets_kernel<<<(unsigned)div_up(n, 256), 256, 0, s>>>(out, n, bs);
+        note_launches(1);
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- reductions, compaction, gathers
+
+__global__ void sum_u64_kernel(const uint32_t *__restrict__ in, int64_t n, unsigned long long *__restrict__ total,
+                               unsigned long long *__restrict__ nonzero) {
+    unsigned long long s = 0, z = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t v = in[i];
+        s += v;
+        z += v > 0u;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        z += __shfl_xor_sync(0xffffffffu, z, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(total, s);
+        atomicAdd(nonzero, z);
+    }
+}
+
+cudaError_t sum_counts(const uint32_t *in, int64_t n, unsigned long long *d_two, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(d_two, 0, 2 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess || n == 0) return e;
+    int grid = (int)std::min<int64_t>(div_up(n, 256), 148 * 8);
+    sum_u64_kernel<<<grid, 256, 0, s>>>(in, n, d_two, d_two + 1);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+// Visible Gaussians (count > 0) -> (depth key, id) at their compacted position.
+__global__ void compact_kernel(const uint32_t *__restrict__ counts, const uint32_t *__restrict__ pos, int64_t n,
+                               const float4 *__restrict__ gview, uint32_t *__restrict__ keys,
+                               uint32_t *__restrict__ vals) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || counts[i] == 0u) return;
+    const uint32_t p = pos[i];
+    keys[p] = __float_as_uint(gview[i].w);   // L >= 0: its bits sort like the value
+    vals[p] = (uint32_t)i;
+}
+
+cudaError_t launch_compact(const uint32_t *counts, const uint32_t *pos, int64_t n, const float4 *gview,
+                           uint32_t *keys, uint32_t *vals, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    compact_kernel<<<(unsigned)div_up(n, 256), 256, 0, s>>>(counts, pos, n, gview, keys, vals);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+__global__ void gather_u32_kernel(const uint32_t *__restrict__ src, const uint32_t *__restrict__ idx, int64_t n,
+                                  uint32_t *__restrict__ dst) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = src[idx[i]];
+}
+
+cudaError_t launch_gather(const uint32_t *src, const uint32_t *idx, int64_t n, uint32_t *dst, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    gather_u32_kernel<<<(unsigned)div_up(n, 256), 256, 0, s>>>(src, idx, n, dst);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+// Per-tile [begin, end) ranges from the tile-sorted key array.
+__global__ void ranges_kernel(const uint32_t *__restrict__ keys, int64_t n, uint2 *__restrict__ ranges) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const uint32_t t = keys[p];
+    if (p == 0 || keys[p - 1] != t) ranges[t].x = (uint32_t)p;
+    if (p == n - 1 || keys[p + 1] != t) ranges[t].y = (uint32_t)(p + 1);
+}
+
+cudaError_t launch_ranges(const uint32_t *keys, int64_t n, uint2 *ranges, int ntiles, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)ntiles, s);
+    if (e != cudaSuccess || n == 0) return e;
+    ranges_kernel<<<(unsigned)div_up(n, 256), 256, 0, s>>>(keys, n, ranges);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- radix sort
+
+constexpr int RS_THREADS = 256;
+constexpr int RS_WARPS = RS_THREADS / 32;
+constexpr int RS_ROUNDS = 16;                       // 32-item rounds per warp per tile
+constexpr int RS_TILE = RS_THREADS * RS_ROUNDS;     // 4096 items per tile
+constexpr int RS_MAX_BLOCKS = 148 * 4;
+
+struct RsPlan {
+    int64_t n;
+    int blocks;
+    int64_t chunk;
+};
+
+RsPlan rs_plan(int64_t n) {
+    RsPlan p;
+    p.n = n;
+    int64_t tiles = div_up(n, RS_TILE);
+    int64_t blocks = std::min<int64_t>(tiles, RS_MAX_BLOCKS);
+    if (blocks < 1) blocks = 1;
+    int64_t tiles_per = div_up(tiles, blocks);
+    p.chunk = tiles_per * RS_TILE;
+    p.blocks = (int)std::max<int64_t>(1, div_up(n, p.chunk));
+    return p;
+}
+
+int64_t radix_scratch_words(int64_t n) {
+    RsPlan p = rs_plan(n);
+    int64_t cnt = 256LL * p.blocks;
+    return cnt * 2 + scan_scratch_words(cnt);
+}
+
+__global__ void __launch_bounds__(RS_THREADS) rs_upsweep(const uint32_t *__restrict__ keys, int64_t n, int64_t chunk,
+                                                         int shift, uint32_t mask, uint32_t *__restrict__ counts) {
+    __shared__ uint32_t hist[256];
+    hist[threadIdx.x] = 0u;
+    __syncthreads();
+    const int64_t beg = (int64_t)blockIdx.x * chunk;
+    const int64_t end = std::min<int64_t>(n, beg + chunk);
+    for (int64_t i = beg + threadIdx.x; i < end; i += RS_THREADS) atomicAdd(&hist[(keys[i] >> shift) & mask], 1u);
+    __syncthreads();
+    counts[(int64_t)threadIdx.x * gridDim.x + blockIdx.x] = hist[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(RS_THREADS) rs_downsweep(const uint32_t *__restrict__ kin,
+                                                           const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
+                                                           uint32_t *__restrict__ vout, int64_t n, int64_t chunk,
+                                                           int shift, uint32_t mask,
+                                                           const uint32_t *__restrict__ offsets) {
+    __shared__ uint32_t running[256];
+    __shared__ uint32_t wcount[RS_WARPS][256];
+    __shared__ uint32_t wbase[RS_WARPS][256];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    running[threadIdx.x] = offsets[(int64_t)threadIdx.x * gridDim.x + blockIdx.x];
+#pragma unroll
+    for (int w = 0; w < RS_WARPS; ++w) wcount[w][threadIdx.x] = 0u;
+    __syncthreads();
+    const int64_t beg = (int64_t)blockIdx.x * chunk;
+    const int64_t end = std::min<int64_t>(n, beg + chunk);
+    const uint32_t lt = (1u << lane) - 1u;
+    for (int64_t t0 = beg; t0 < end; t0 += RS_TILE) {
+        uint32_t k[RS_ROUNDS], v[RS_ROUNDS], rank[RS_ROUNDS];
+#pragma unroll
+        for (int r = 0; r < RS_ROUNDS; ++r) {
+            const int64_t i = t0 + (int64_t)wid * (RS_ROUNDS * 32) + r * 32 + lane;
+            const bool ok = i < end;
+            k[r] = ok ? kin[i] : 0u;
+            v[r] = ok ? vin[i] : 0u;
+            const uint32_t dig = ok ? ((k[r] >> shift) & mask) : (256u + (uint32_t)lane);
+            const uint32_t peers = __match_any_sync(0xffffffffu, dig);
+            const int leader = __ffs(peers) - 1;
+            uint32_t old = 0u;
+            if (ok && lane == leader) {
+                old = wcount[wid][dig];
+                wcount[wid][dig] = old + (uint32_t)__popc(peers);
+            }
+            old = __shfl_sync(0xffffffffu, old, leader);
+            rank[r] = ok ? old + (uint32_t)__popc(peers & lt) : 0xffffffffu;
+            __syncwarp();
+        }
+        __syncthreads();
+        {
+            const int d = threadIdx.x;
+            uint32_t b = running[d];
+#pragma unroll
+            for (int w = 0; w < RS_WARPS; ++w) {
+                wbase[w][d] = b;
+                b += wcount[w][d];
+                wcount[w][d] = 0u;
+            }
+            running[d] = b;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < RS_ROUNDS; ++r) {
+            if (rank[r] != 0xffffffffu) {
+                const uint32_t dst = wbase[wid][(k[r] >> shift) & mask] + rank[r];
+                kout[dst] = k[r];
+                vout[dst] = v[r];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Stable sort of (keys, vals) on bits [begin_bit, end_bit); result ends in
+// (keys, vals) (alt_* are same-size scratch).  scratch: radix_scratch_words(n).
+cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *alt_keys, uint32_t *alt_vals, int64_t n,
+                             int begin_bit, int end_bit, uint32_t *scratch, cudaStream_t s) {
+    if (n <= 1 || end_bit <= begin_bit) return cudaSuccess;
+    const RsPlan p = rs_plan(n);
+    const int64_t cnt = 256LL * p.blocks;
+    uint32_t *counts = scratch, *offs = scratch + cnt, *scan_scr = scratch + 2 * cnt;
+    uint32_t *ki = keys, *vi = vals, *ko = alt_keys, *vo = alt_vals;
+    int passes = 0;
+    for (int shift = begin_bit; shift < end_bit; shift += 8) {
+        const int bits = std::min(8, end_bit - shift);
+        const uint32_t mask = (1u << bits) - 1u;
+        rs_upsweep<<<p.blocks, RS_THREADS, 0, s>>>(ki, n, p.chunk, shift, mask, counts);
+        note_launches(1);
+        cudaError_t e = exclusive_scan(counts, offs, cnt, scan_scr, 0, s);
+        if (e != cudaSuccess) return e;
+        rs_downsweep<<<p.blocks, RS_THREADS, 0, s>>>(ki, vi, ko, vo, n, p.chunk, shift, mask, offs);
+        note_launches(1);
+        std::swap(ki, ko);
+        std::swap(vi, vo);
+        ++passes;
+    }
+    if (passes & 1) {
+        cudaMemcpyAsync(keys, ki, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(vals, vi, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace conegs

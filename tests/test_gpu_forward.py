@@ -1,0 +1,231 @@
+"""GPU forward path vs the FP64 oracle, through the C ABI.
+
+Bit-exact: valid masks, tile cone tables, per-Gaussian / per-tile pair counts,
+the per-tile list order, the radix sort.  Within tolerance: ray tables, the
+Eq. 11 floor and the rendered image (1e-4 absolute per RGB channel and on T,
+excluding the pixels the oracle flags as near a compositing threshold).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synthetic as S
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def cg():
+    import paper_2609_13397_b300 as cg
+    return cg
+
+
+def _cases():
+    out = {"c1": S.c1()}
+    out["kb160"] = (S.c3_camera(160, 160), S.uniform_box_scene(1500, seed=3))
+    bcam = S.pinhole(320, 180, 300.0)
+    out["blob320"] = (bcam, S.blob_scene(20000, seed=1, cam=bcam))
+    out["ragged"] = (S.pinhole(70, 45, 40.0, 33.0, 21.0, cam_to_world=S.look_at((0.1, 0.0, -0.5), (0.2, 0.1, 4.0))),
+                     S.uniform_box_scene(500, seed=9, log_scale_mean=-2.5))
+    kb_pose = S.look_at((0.05, -0.1, 0.2), (0.3, 0.2, 4.0))
+    kcam = S.c3_camera(96, 80)
+    kcam.cam_to_world = kb_pose
+    out["kb_ragged"] = (kcam, S.uniform_box_scene(800, seed=5))
+    return out
+
+
+CASES = _cases()
+
+
+def _with_floor(oracle, name, cam, sc):
+    if name == "blob320":
+        return sc.with_rho2(oracle.floor_rho2([S.pinhole(640, 360, 600.0)], sc.means).astype(np.float32))
+    return sc
+
+
+def _setup(cg, cam, sc, storage=None):
+    ctx = cg.Context(0)
+    ctx.set_scene_from(sc, storage=storage)
+    v = ctx.view()
+    v.set_camera_from(cam)
+    return ctx, v
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_ray_table(cg, oracle_lib, name):
+    cam, sc = CASES[name]
+    ctx, v = _setup(cg, cam, sc)
+    d, dx, dy, valid = (t.cpu().numpy() for t in v.rays())
+    torch.cuda.synchronize()
+    od, odx, ody, ovalid = oracle_lib.rays(cam)
+    assert np.array_equal(valid.astype(bool), ovalid)
+    m = ovalid
+    assert np.abs(d.T[m] - od[m]).max() < 2e-7
+    for g, o in ((dx, odx), (dy, ody)):
+        err = np.linalg.norm(g.T[m] - o[m], axis=1) / np.linalg.norm(o[m], axis=1)
+        assert err.max() < 2e-5, err.max()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_tile_table_bit_exact(cg, oracle_lib, name):
+    cam, sc = CASES[name]
+    ctx, v = _setup(cg, cam, sc)
+    g = v.tile_table().cpu().numpy()
+    o = oracle_lib.tile_table(cam)
+    assert np.array_equal(g.view(np.uint32), o.view(np.uint32))
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_pair_counts_bit_exact(cg, oracle_lib, name):
+    cam, sc = CASES[name]
+    sc = _with_floor(oracle_lib, name, cam, sc)
+    ctx, v = _setup(cg, cam, sc)
+    v.render()
+    pg, pt = (t.cpu().numpy() for t in v.bin_counts())
+    total, opg, opt, _ = oracle_lib.bin_counts(cam, sc)
+    assert np.array_equal(pg, opg)
+    assert np.array_equal(pt, opt)
+    assert v.stats()["n_pairs"] == total
+
+
+@pytest.mark.parametrize("name", ["c1", "blob320", "kb_ragged"])
+def test_tile_lists_in_depth_order(cg, oracle_lib, name):
+    """Each tile's list is the binned Gaussians sorted by (FP32 depth key, index)."""
+    cam, sc = CASES[name]
+    ctx, v = _setup(cg, cam, sc)
+    v.render()
+    gid, rng = (t.cpu().numpy() for t in v.pairs())
+    _, _, _, pas = oracle_lib.bin_counts(cam, sc, dense=True)
+    L = oracle_lib.bin_gauss(cam, sc)[:, 3]
+    for t in range(rng.shape[0]):
+        got = gid[rng[t, 0]:rng[t, 1]]
+        want = np.nonzero(pas[:, t])[0]
+        want = want[np.lexsort((want, L[want]))]
+        assert np.array_equal(got, want), t
+
+
+def _render_compare(cg, oracle_lib, cam, sc, flags=0, filt=1, comp=0, storage=None, tol=TOL, pix=None):
+    ctx, v = _setup(cg, cam, sc, storage=storage)
+    rgb, T = v.render(flags=flags)
+    rgb = rgb.cpu().numpy().reshape(3, -1).T
+    T = T.cpu().numpy().reshape(-1)
+    r = oracle_lib.render(cam, sc, pix=pix, filter=filt, comp=comp, eps=2e-3, eps_key=1e-6)
+    if pix is not None:
+        rgb, T = rgb[pix], T[pix]
+    ok = r.flags == 0
+    err = np.abs(rgb - r.rgb)[ok].max(initial=0.0)
+    errT = np.abs(T - r.T)[ok].max(initial=0.0)
+    return err, errT, (~ok).sum(), ok.size
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_render_matches_oracle(cg, oracle_lib, name):
+    cam, sc = CASES[name]
+    sc = _with_floor(oracle_lib, name, cam, sc)
+    err, errT, nflag, npx = _render_compare(cg, oracle_lib, cam, sc)
+    assert nflag <= 0.01 * npx
+    assert err <= TOL and errT <= TOL, (err, errT)
+
+
+@pytest.mark.parametrize("mode", ["filter_none", "additive"])
+def test_render_variants(cg, oracle_lib, mode):
+    cam, sc = CASES["blob320"]
+    sc = _with_floor(oracle_lib, "blob320", cam, sc)
+    if mode == "filter_none":
+        err, errT, nflag, npx = _render_compare(cg, oracle_lib, cam, sc, flags=cg.FILTER_NONE, filt=0)
+    else:
+        err, errT, nflag, npx = _render_compare(cg, oracle_lib, cam, sc, flags=cg.COMP_ADDITIVE, comp=1)
+    assert err <= TOL and errT <= TOL, (err, errT)
+
+
+def test_render_deterministic(cg):
+    cam, sc = CASES["blob320"]
+    ctx, v = _setup(cg, cam, sc)
+    a, ta = v.render()
+    b, tb = v.render()
+    assert torch.equal(a, b) and torch.equal(ta, tb)
+
+
+def test_empty_scene_and_invalid_pixels(cg):
+    cam = S.c3_camera(64, 64)
+    sc = S.uniform_box_scene(0, seed=0)
+    ctx, v = _setup(cg, cam, sc)
+    rgb, T = v.render()
+    assert float(rgb.abs().max()) == 0.0 and float(T.min()) == 1.0
+    sc = S.uniform_box_scene(50, seed=0)
+    ctx.set_scene_from(sc)
+    rgb, T = v.render()
+    _, _, _, valid = v.rays()
+    inv = (valid == 0).reshape(64, 64)
+    assert inv.any()
+    assert float(rgb[:, inv].abs().max()) == 0.0 and float(T[inv].min()) == 1.0
+
+
+def test_floor_matches_oracle(cg, oracle_lib):
+    sc = S.blob_scene(20000, seed=2, cam=S.pinhole(320, 180, 300.0))
+    views = [S.pinhole(640, 360, 600.0), S.pinhole(320, 180, 300.0, cam_to_world=S.look_at((0.3, 0, 0), (0, 0, 6))),
+             S.c3_camera(200, 200)]
+    ctx = cg.Context(0)
+    ctx.set_scene_from(sc)
+    vs = []
+    for c in views:
+        v = ctx.view()
+        v.set_camera_from(c)
+        vs.append(v)
+    g = ctx.compute_floor(vs).cpu().numpy()
+    o = oracle_lib.floor_rho2(views, sc.means)
+    both = (g > 0) & (o > 0)
+    assert ((g > 0) == (o > 0)).mean() > 0.999
+    rel = np.abs(g[both] - o[both]) / o[both]
+    assert np.quantile(rel, 0.999) < 1e-3
+
+
+@pytest.mark.parametrize("n,bits", [(1, 32), (1000, 32), (4097, 12), (100003, 32), (1 << 20, 16), (3 << 20, 7)])
+def test_radix_sort(cg, n, bits):
+    rng = np.random.default_rng(n)
+    keys = rng.integers(0, 1 << bits, n, dtype=np.uint64).astype(np.uint32)
+    keys[: n // 3] = keys[n // 2]            # many ties
+    vals = np.arange(n, dtype=np.uint32)
+    ctx = cg.Context(0)
+    k = torch.from_numpy(keys.view(np.int32)).cuda()
+    v = torch.from_numpy(vals.view(np.int32)).cuda()
+    cg.radix_sort_pairs(ctx, k, v, 0, bits)
+    order = np.argsort(keys, kind="stable")
+    assert np.array_equal(k.cpu().numpy().view(np.uint32), keys[order])
+    assert np.array_equal(v.cpu().numpy().view(np.uint32), vals[order])
+
+
+def test_full_size_c2_sampled(cg, oracle_lib):
+    """The 1280x720 + 160x90 workload with 500k Gaussians and the Eq. 11 floor, as
+    the benchmark runs it: sampled pixels against the oracle, all pair counts of
+    a sample of Gaussians bit-exact."""
+    cams = S.c2_cameras()
+    sc = S.c2_scene()
+    ctx = cg.Context(0)
+    ctx.set_scene_from(sc)
+    v0 = ctx.view()
+    v0.set_camera_from(cams[0])
+    rho2 = ctx.compute_floor([v0])
+    ctx.set_scene_from(sc, rho2=rho2)
+    sc = sc.with_rho2(rho2.cpu().numpy())
+    rng = np.random.default_rng(0)
+    for cam in cams:
+        v = ctx.view()
+        v.set_camera_from(cam)
+        rgb, T = v.render()
+        rgb = rgb.cpu().numpy().reshape(3, -1).T
+        T = T.cpu().numpy().reshape(-1)
+        pix = rng.choice(cam.n_pixels, size=min(600, cam.n_pixels), replace=False).astype(np.int32)
+        r = oracle_lib.render(cam, sc, pix=pix, eps=2e-3)
+        ok = r.flags == 0
+        assert ok.mean() > 0.95
+        assert np.abs(rgb[pix] - r.rgb)[ok].max() <= TOL
+        assert np.abs(T[pix] - r.T)[ok].max() <= TOL
+        pg, _ = v.bin_counts()
+        sub = rng.choice(sc.n, size=3000, replace=False)
+        _, opg, _, _ = oracle_lib.bin_counts(cam, sc.subset(sub))
+        assert np.array_equal(pg.cpu().numpy()[sub], opg)
