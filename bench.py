@@ -35,9 +35,11 @@ import synthetic as S  # noqa: E402
 
 METRIC = "anti-aliased Mrays/s fwd & fwd+bwd at stated RGB err vs FP32 plain; p50/p99 ms"
 WORKLOAD = "pinhole 1280x720 + 160x90 (1/8), 500k Gaussians (64 blobs + shell), SH3, Eq.11 floor"
-# FP32 operations per pixel-Gaussian pair evaluation of the forward rasteriser,
-# counted from the per-pair code (an FMA counts as 2): ~148 for the response with
-# rho^2 = 0 (K = I/3) plus ~12 for compositing; the floor path (rho^2 > 0) adds ~52.
+# FP32 operations of the forward rasteriser, counted from its code (an FMA counts
+# as 2): 27 per tile-list entry walked (the visual-cone pre-test: e = d - u,
+# a linear and a quadratic form in e), and per full pair evaluation ~148 for the response with rho^2 = 0
+# (K = I/3) plus ~12 for compositing; the floor path (rho^2 > 0) adds ~52.
+FLOPS_PER_WALK = 27
 FLOPS_PER_PAIR_NOFLOOR = 160
 FLOPS_PER_PAIR_FLOOR = 212
 SMS, FP32_LANES = 148, 128
@@ -172,11 +174,18 @@ def run_ours(args, rank, world, local_rank):
     outs = [(torch.empty(3, c.height, c.width, device=dev), torch.empty(c.height, c.width, device=dev))
             for c in cams]
     flush = torch.empty(256 * 1024 * 1024 // 4, device=dev, dtype=torch.float32)
-    stream = torch.cuda.current_stream()
+    main = torch.cuda.current_stream()
+    streams = [torch.cuda.Stream(device=dev) for _ in views]
 
     def step(flags=0):
-        for v, (o_rgb, o_T) in zip(views, outs):
-            v.render(flags=flags, out_rgb=o_rgb, out_T=o_T)
+        """Both cameras of the workload; each view on its own stream (they overlap)."""
+        ev0 = torch.cuda.Event()
+        ev0.record(main)
+        for v, st, (o_rgb, o_T) in zip(views, streams, outs):
+            st.wait_event(ev0)
+            v.render(flags=flags, out_rgb=o_rgb, out_T=o_T, stream=st)
+        for st in streams:
+            main.wait_stream(st)
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -189,21 +198,21 @@ def run_ours(args, rank, world, local_rank):
         tdist.barrier()
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    raster_ms, evals, stage = [], [], {"ms_preprocess": 0.0, "ms_sort": 0.0, "ms_raster": 0.0}
+    per_view = [{"ms_raster": [], "n_walked": [], "n_evaluated": [], "ms_preprocess": [], "ms_sort": [],
+                 "ms_total": [],
+                 "n_pairs": [], "n_visible": []} for _ in views]
     launches = 0
     with ClockSampler(local_rank) as clk:
         for k in range(args.steps):
             flush.fill_(float(k))
-            ev[k][0].record(stream)
+            ev[k][0].record(main)
             step(flags=cg.PROFILE)
-            ev[k][1].record(stream)
-            for v in views:
+            ev[k][1].record(main)
+            for v, pv in zip(views, per_view):
                 st = v.stats()
-                raster_ms.append(st["ms_raster"])
-                evals.append(st["n_evaluated"])
+                for key in pv:
+                    pv[key].append(st[key])
                 launches += st["n_launches"]
-                for key in stage:
-                    stage[key] += st[key]
         torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     ms = sum(step_ms) / len(step_ms)
@@ -218,17 +227,22 @@ def run_ours(args, rank, world, local_rank):
     try:
         gl = [torch.ones_like(o[0]) for o in outs]
         def fb_step():
-            for v, (o_rgb, o_T), g in zip(views, outs, gl):
-                v.render(flags=cg.KEEP_FOR_BACKWARD, out_rgb=o_rgb, out_T=o_T)
-                v.render_backward(g)
+            ev0 = torch.cuda.Event()
+            ev0.record(main)
+            for v, st, (o_rgb, o_T), g in zip(views, streams, outs, gl):
+                st.wait_event(ev0)
+                v.render(flags=cg.KEEP_FOR_BACKWARD, out_rgb=o_rgb, out_T=o_T, stream=st)
+                v.render_backward(g, stream=st)
+            for st in streams:
+                main.wait_stream(st)
         for _ in range(2):
             fb_step()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
+        e0.record(main)
         for _ in range(args.steps):
             fb_step()
-        e1.record(stream)
+        e1.record(main)
         torch.cuda.synchronize()
         fb_ms = e0.elapsed_time(e1) / args.steps
         fwd_bwd = {"value": rays_per_step * world / (fb_ms * 1e-3) / 1e6, "unit": "Mrays/s", "ms_per_step": fb_ms}
@@ -239,9 +253,9 @@ def run_ours(args, rank, world, local_rank):
     host = [(torch.empty(3, c.height, c.width, pin_memory=True), torch.empty(c.height, c.width, pin_memory=True))
             for c in cams]
     def e2e_step():
-        for v, c, (h_rgb, h_T) in zip(views, cams, host):
-            v.set_camera_from(c)
-            v.render_host(h_rgb, h_T)
+        for v, c, st, (h_rgb, h_T) in zip(views, cams, streams, host):
+            v.set_camera_from(c, stream=st)
+            v.render_host(h_rgb, h_T, stream=st)
     for _ in range(2):
         e2e_step()
     torch.cuda.synchronize()
@@ -255,10 +269,10 @@ def run_ours(args, rank, world, local_rank):
 
     peaks = _peaks()
     clocks = clk.summary()
-    floor_pairs = True
-    fpp = FLOPS_PER_PAIR_FLOOR if floor_pairs else FLOPS_PER_PAIR_NOFLOOR
-    r_ms = sum(raster_ms) / len(raster_ms)
-    r_flops = fpp * sum(evals) / len(evals)
+    fpp = FLOPS_PER_PAIR_FLOOR      # every visible Gaussian carries an Eq. 11 floor here
+    pv0 = per_view[0]              # the 1280x720 raster launch dominates the step
+    r_ms = statistics.median(pv0["ms_raster"])
+    r_flops = fpp * statistics.median(pv0["n_evaluated"]) + FLOPS_PER_WALK * statistics.median(pv0["n_walked"])
     achieved = r_flops / (r_ms * 1e-3) / 1e12
     peak = SMS * FP32_LANES * 2 * (peaks.get("sm_max_mhz", 2032.0)) * 1e6 / 1e12
     line = {
@@ -268,12 +282,14 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": WORKLOAD, "rays_per_step": rays_per_step, "gaussians": ctx.n,
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
         "fwd_bwd": fwd_bwd,
-        "stage_ms_per_step": {k: v / args.steps for k, v in stage.items()},
+        "views": [{"camera": f"{c.width}x{c.height}", **{k: statistics.median(v) for k, v in pv.items()}}
+                  for c, pv in zip(cams, per_view)],
         "roofline": {"bound": "alu", "kernel": "raster_fwd_kernel", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                      "peak_basis": "148 SMs x 128 FP32 lanes x 2 x max SM clock (FMA = 2 flops)",
-                     "flops_per_pair": fpp, "pairs_per_launch": sum(evals) / len(evals),
-                     "ms_per_launch": r_ms},
+                     "flops_per_pair": fpp, "flops_per_walked_entry": FLOPS_PER_WALK,
+                     "pairs_per_launch": statistics.median(pv0["n_evaluated"]),
+                     "entries_walked_per_launch": statistics.median(pv0["n_walked"]), "ms_per_launch": r_ms},
         "e2e": {"value": rays_per_step * world / (e2e_ms * 1e-3) / 1e6, "unit": "Mrays/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches // 1,

@@ -94,7 +94,8 @@ typedef struct {
     size_t device_bytes;     /* library-owned device memory of this view */
     int64_t n_launches;      /* CUDA kernels launched by the last render */
     /* filled when the last render used CONEGS_PROFILE (get_stats then waits for it): */
-    int64_t n_evaluated;     /* pixel-Gaussian pair evaluations done by the rasteriser */
+    int64_t n_walked;        /* tile-list entries walked by the rasteriser's pixels */
+    int64_t n_evaluated;     /* of those, full pair responses evaluated (past the cone pre-test) */
     float ms_preprocess;     /* view records + bin count + scans */
     float ms_sort;           /* compaction + depth sort + emit + tile sort + ranges */
     float ms_raster;         /* tile rasteriser */

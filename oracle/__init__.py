@@ -175,7 +175,7 @@ class Render:
 
 
 def render(cam, scene, pix: Optional[Sequence[int]] = None, filter: int = FILTER_ANISO,
-           comp: int = COMP_MARGINAL, cull: bool = True, eps: float = 1e-5, eps_key: float = 1e-6,
+           comp: int = COMP_MARGINAL, cull: bool = True, eps: float = 1e-5, eps_key: float = 0.0,
            max_used: int = 0) -> Render:
     """Render pixels (indices into the row-major W x H grid; None = all)."""
     n = scene.n
@@ -224,8 +224,11 @@ def floor_rho2(cams, means) -> np.ndarray:
 
 # ------------------------------------------------------------------ FP32 binning emulation
 
+TILE = 8   # tile side (pixels) of the binning rule
+
+
 def tile_grid(cam):
-    return (cam.width + 15) // 16, (cam.height + 15) // 16
+    return (cam.width + TILE - 1) // TILE, (cam.height + TILE - 1) // TILE
 
 
 def tile_table(cam) -> np.ndarray:

@@ -31,7 +31,9 @@
  *     T_acc (1 - a_k) < 1e-4; background is 0.
  *   - pairs with t* <= 0.01 (behind / at the optical centre) are skipped.
  *   - the per-ray depth order uses the Gaussian key |mu - o| (the t* of the
- *     ray through mu), ties broken by Gaussian index.
+ *     ray through mu), ties broken by Gaussian index; like the valid mask,
+ *     this integer decision is taken in FP32 by a fixed operation sequence
+ *     so that every implementation orders pairs identically.
  *   - KB fisheye: theta_d = theta (1 + k1 th^2 + k2 th^4 + k3 th^6 + k4 th^8),
  *     pixel valid iff its normalised radius is inside theta_d(theta_lim);
  *     an edge ray that leaves the valid disc is replaced by the backward
@@ -211,7 +213,16 @@ static int project(const ocam *c, const double X[3], double *px, double *py) {
 
 typedef struct {
     double mu[3], W[9], Winv[9], s[3], seff[3], sig, sig_eff, rho2, rgb[3], L;
+    double key;  /* depth key: |mu - o| by the FP32 rule (see f32_depth_key) */
 } ogauss;
+
+/* The depth order is decided in FP32 (the same decision on every side):
+ * key = sqrt((v0*v0 + v1*v1) + v2*v2), v = mu - o, each op one rounded FP32 op. */
+static double f32_depth_key(const double *mu, const double *o) {
+    float v0 = (float)mu[0] - (float)o[0], v1 = (float)mu[1] - (float)o[1], v2 = (float)mu[2] - (float)o[2];
+    float L2 = (v0 * v0 + v1 * v1) + v2 * v2;
+    return (double)sqrtf(L2);
+}
 
 /* Real spherical harmonics up to degree 3 (positive-constant real basis). */
 static void sh_basis(const double v[3], double Y[16]) {
@@ -262,6 +273,7 @@ static void prep_gauss(const double o[3], const double *mu, const double *ls, co
     double v[3];
     for (int i = 0; i < 3; ++i) v[i] = mu[i] - o[i];
     g->L = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    g->key = f32_depth_key(mu, o);
     for (int i = 0; i < 3; ++i) v[i] /= g->L;
     double Y[16];
     sh_basis(v, Y);
@@ -508,7 +520,7 @@ static void composite(cand *cs, int nc, const ogauss *g, double eps, double eps_
     for (int k = 0; k < nc; ++k) {
         double T = cs[k].T;
         if (fabs(cs[k].ts - T_NEAR) <= eps * T_NEAR) fl |= FL_TNEAR;
-        if (k > 0 && fabs(cs[k].L - cs[k - 1].L) <= eps_key * cs[k].L) fl |= FL_KEY_TIE;
+        if (eps_key > 0 && k > 0 && fabs(cs[k].L - cs[k - 1].L) <= eps_key * cs[k].L) fl |= FL_KEY_TIE;
         if (fabs(T - ALPHA_MIN) <= eps * ALPHA_MIN) fl |= FL_ALPHA_MIN;
         if (fabs(T - ALPHA_MAX) <= eps * ALPHA_MAX) fl |= FL_ALPHA_MAX;
         if (T < ALPHA_MIN) continue;
@@ -650,12 +662,12 @@ void or_render(const double *campk, int n, const double *means, const double *lo
                 double T, ts;
                 if (!pair_response(&g[k], c.o, d, dx, dy, filter, comp, &T, &ts, NULL)) {
                     if (fabs(ts - T_NEAR) <= eps * T_NEAR && T >= ALPHA_MIN * (1 - eps)) {
-                        cs[nc].L = g[k].L; cs[nc].T = 0.0; cs[nc].ts = ts; cs[nc].idx = k; ++nc;
+                        cs[nc].L = g[k].key; cs[nc].T = 0.0; cs[nc].ts = ts; cs[nc].idx = k; ++nc;
                     }
                     continue;
                 }
                 if (T < ALPHA_MIN * (1.0 - eps)) continue;
-                cs[nc].L = g[k].L; cs[nc].T = T; cs[nc].ts = ts; cs[nc].idx = k;
+                cs[nc].L = g[k].key; cs[nc].T = T; cs[nc].ts = ts; cs[nc].idx = k;
                 ++nc;
             }
             composite(cs, nc, g, eps, eps_key, o_rgb, &Tout[t], &flags[t], &ncontrib[t], u, max_used);
@@ -677,21 +689,32 @@ long or_pairs_above(const double *campk, int n, const double *means, const doubl
     for (int i = 0; i < n; ++i)
         prep_gauss(c.o, means + 3 * (size_t)i, log_scales + 3 * (size_t)i, quats + 4 * (size_t)i, logits[i], sh0,
                    0, rho2 ? rho2[i] : 0.0, &g[i]);
-    long cnt = 0;
-    for (int p = 0; p < c.W * c.H; ++p) {
-        double x = (p % c.W) + 0.5, y = (p / c.W) + 0.5, d[3], dx[3], dy[3];
-        if (!pixel_rays(&c, x, y, d, dx, dy)) continue;
-        for (int k = 0; k < n; ++k) {
-            double T, ts;
-            pair_response(&g[k], c.o, d, dx, dy, FILTER_ANISO, COMP_MARGINAL, &T, &ts, NULL);
-            if (ts > T_NEAR * (1 - 1e-6) && T >= thr) {
-                if (cnt < cap) { out_pix[cnt] = p; out_g[cnt] = k; }
-                ++cnt;
+    int P = c.W * c.H;
+    long *cnt = (long *)calloc((size_t)P + 1, sizeof(long));
+    /* pass 1: count per pixel; pass 2: fill in pixel order */
+    for (int pass = 0; pass < 2; ++pass) {
+#pragma omp parallel for schedule(dynamic, 8)
+        for (int p = 0; p < P; ++p) {
+            double x = (p % c.W) + 0.5, y = (p / c.W) + 0.5, d[3], dx[3], dy[3];
+            if (!pixel_rays(&c, x, y, d, dx, dy)) continue;
+            long k0 = pass ? cnt[p] : 0, k = k0;
+            for (int j = 0; j < n; ++j) {
+                double T, ts;
+                pair_response(&g[j], c.o, d, dx, dy, FILTER_ANISO, COMP_MARGINAL, &T, &ts, NULL);
+                if (ts > T_NEAR * (1 - 1e-6) && T >= thr) {
+                    if (pass && k < cap) { out_pix[k] = p; out_g[k] = j; }
+                    ++k;
+                }
             }
+            if (!pass) cnt[p + 1] = k - k0;
         }
+        if (!pass)
+            for (int p = 0; p < P; ++p) cnt[p + 1] += cnt[p];
     }
+    long total = cnt[P];
+    free(cnt);
     free(g);
-    return cnt;
+    return total;
 }
 
 /* Eq. 11: rho^2 = min over visible training views of tr(Sigma_fp)/2 at the
@@ -842,9 +865,9 @@ static void fedge(const fcam *c, float x, float y, const float d[3], int axis, f
     }
 }
 
-#define TILE 16
+#define TILE 8
 
-/* Tile cone table: per tile (row-major over ceil(W/16) x ceil(H/16)) 6 floats
+/* Tile cone table: per tile (row-major over ceil(W/8) x ceil(H/8)) 6 floats
  * a0 a1 a2 (axis = ray of the tile centre), sg = sin(gamma/2) (inflated),
  * cg = cos(gamma/2), m = max over pixels of (|dx|^2+|dy|^2)/3 (x1.01);
  * sg = -1 marks a tile without valid pixels. */

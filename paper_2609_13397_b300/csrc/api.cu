@@ -21,16 +21,18 @@
 namespace conegs {
 // launchers defined in the other translation units
 cudaError_t launch_ray_table(const CamParams &c, float *d, float *dx, float *dy, uint8_t *valid, cudaStream_t s);
-cudaError_t launch_tile_tables(const CamParams &c, float *table, float *super, cudaStream_t s);
+cudaError_t launch_tile_tables(const CamParams &c, float *table, float *super, float *mcam, cudaStream_t s);
 cudaError_t launch_gauss_scene_rule(const SceneParams &sp, float *binrec, cudaStream_t s);
-cudaError_t launch_bin_count(const CamParams &c, const float *binrec, const float4 *gview, const uint8_t *gflag,
-                             const float *table, const float *super, int64_t n, uint32_t *counts, cudaStream_t s);
-cudaError_t launch_bin_emit(const CamParams &c, const float *binrec, const float4 *gview, const uint8_t *gflag,
-                            const float *table, const float *super, int64_t n_sorted, const uint32_t *order,
-                            const uint32_t *offsets, uint32_t *out_tile, uint32_t *out_gid, cudaStream_t s);
+cudaError_t launch_bin_count(const CamParams &c, const float *binrec, const float4 *gview, const float2 *gcone,
+                             const uint8_t *gflag, const float *table, const float *super, int64_t n,
+                             uint32_t *counts, cudaStream_t s);
+cudaError_t launch_bin_emit(const CamParams &c, const float *binrec, const float4 *gview, const float2 *gcone,
+                            const uint8_t *gflag, const float *table, const float *super, int64_t n_sorted,
+                            const uint32_t *order, const uint32_t *offsets, uint32_t *out_tile, uint32_t *out_gid,
+                            cudaStream_t s);
 cudaError_t launch_scene_cache(const SceneParams &sp, float *W, float *sig_eff, cudaStream_t s);
-cudaError_t launch_view_records(const CamParams &c, const SceneParams &sp, float4 *rec, float4 *gview,
-                                uint8_t *gflag, cudaStream_t s);
+cudaError_t launch_view_records(const CamParams &c, const SceneParams &sp, const float *mcam, float4 *rec,
+                                float4 *gview, float2 *gcone, uint8_t *gflag, cudaStream_t s);
 int64_t scan_scratch_words(int64_t n);
 cudaError_t exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *scratch, int pred,
                            cudaStream_t s);
@@ -142,9 +144,9 @@ struct conegs_view {
     conegs_ctx *ctx = nullptr;
     CamParams cam{};
     bool has_cam = false;
-    DevBuf d, dx, dy, valid, table, super;
+    DevBuf d, dx, dy, valid, table, super, mcam;
     // per-render scratch
-    DevBuf rec, gview, gflag, counts, vispos, scan_scr, dkeys, dvals, dkeys_alt, dvals_alt, sorted_counts, offsets;
+    DevBuf rec, gview, gcone, gflag, counts, vispos, scan_scr, dkeys, dvals, dkeys_alt, dvals_alt, sorted_counts, offsets;
     DevBuf pair_tile, pair_gid, pair_tile_alt, pair_gid_alt, ranges, last, sums, rs_scr, tmp_rgb, tmp_T;
     DevBuf g_rec, keep_T;
     unsigned long long *h_sums = nullptr;   // pinned
@@ -330,7 +332,7 @@ conegs_status conegs_view_create(conegs_ctx *ctx, conegs_view **out) {
     v->ctx = ctx;
     cudaError_t e = cudaEventCreateWithFlags(&v->done, cudaEventDisableTiming);
     for (int k = 0; k < 5 && e == cudaSuccess; ++k) e = cudaEventCreate(&v->prof[k]);
-    if (e == cudaSuccess) e = cudaMallocHost(&v->h_sums, 3 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMallocHost(&v->h_sums, 4 * sizeof(unsigned long long));
     if (e != cudaSuccess) {
         if (v->done) cudaEventDestroy(v->done);
         delete v;
@@ -352,7 +354,7 @@ void conegs_view_destroy(conegs_view *v) {
         cudaEventSynchronize(v->done);
         cudaEventDestroy(v->done);
     }
-    DevBuf *bufs[] = {&v->d, &v->dx, &v->dy, &v->valid, &v->table, &v->super, &v->rec, &v->gview, &v->gflag,
+    DevBuf *bufs[] = {&v->d, &v->dx, &v->dy, &v->valid, &v->table, &v->super, &v->mcam, &v->rec, &v->gview, &v->gcone, &v->gflag,
                       &v->counts, &v->vispos, &v->scan_scr, &v->dkeys, &v->dvals, &v->dkeys_alt, &v->dvals_alt,
                       &v->sorted_counts, &v->offsets, &v->pair_tile, &v->pair_gid, &v->pair_tile_alt,
                       &v->pair_gid_alt, &v->ranges, &v->last, &v->sums, &v->rs_scr, &v->tmp_rgb, &v->tmp_T,
@@ -419,10 +421,11 @@ conegs_status conegs_set_camera(conegs_view *v, int model, int width, int height
     TRY(ensure(ctx, v->valid, P, s));
     TRY(ensure(ctx, v->table, sizeof(float) * 6 * nt, s));
     TRY(ensure(ctx, v->super, sizeof(float) * 6 * ns, s));
+    TRY(ensure(ctx, v->mcam, sizeof(float), s));
     TRY(ensure(ctx, v->ranges, sizeof(uint2) * nt, s));
     TRY(ensure(ctx, v->last, sizeof(uint32_t) * P, s));
     CUDA_TRY(launch_ray_table(c, v->d.as<float>(), v->dx.as<float>(), v->dy.as<float>(), v->valid.as<uint8_t>(), s));
-    CUDA_TRY(launch_tile_tables(c, v->table.as<float>(), v->super.as<float>(), s));
+    CUDA_TRY(launch_tile_tables(c, v->table.as<float>(), v->super.as<float>(), v->mcam.as<float>(), s));
     v->cam = c;
     v->has_cam = true;
     v->has_forward = false;
@@ -451,6 +454,7 @@ static conegs_status render_impl(conegs_view *v, float *out_rgb, float *out_T, u
     const size_t nn = (size_t)std::max<int64_t>(n, 1);
     TRY(ensure(ctx, v->rec, sizeof(float4) * REC_F4 * nn, s));
     TRY(ensure(ctx, v->gview, sizeof(float4) * nn, s));
+    TRY(ensure(ctx, v->gcone, sizeof(float2) * nn, s));
     TRY(ensure(ctx, v->gflag, nn, s));
     TRY(ensure(ctx, v->counts, sizeof(uint32_t) * nn, s));
     TRY(ensure(ctx, v->vispos, sizeof(uint32_t) * nn, s));
@@ -459,13 +463,14 @@ static conegs_status render_impl(conegs_view *v, float *out_rgb, float *out_T, u
     SceneParams sp = ctx->sp;
     const bool prof = (flags & CONEGS_PROFILE) != 0;
     if (prof) {
-        TRY(ensure(ctx, v->evaluated, sizeof(unsigned long long), s));
-        CUDA_TRY(cudaMemsetAsync(v->evaluated.p, 0, sizeof(unsigned long long), s));
+        TRY(ensure(ctx, v->evaluated, 2 * sizeof(unsigned long long), s));
+        CUDA_TRY(cudaMemsetAsync(v->evaluated.p, 0, 2 * sizeof(unsigned long long), s));
         CUDA_TRY(cudaEventRecord(v->prof[0], s));
     }
-    CUDA_TRY(launch_view_records(c, sp, v->rec.as<float4>(), v->gview.as<float4>(), v->gflag.as<uint8_t>(), s));
-    CUDA_TRY(launch_bin_count(c, sp.binrec, v->gview.as<float4>(), v->gflag.as<uint8_t>(), v->table.as<float>(),
-                              v->super.as<float>(), n, v->counts.as<uint32_t>(), s));
+    CUDA_TRY(launch_view_records(c, sp, v->mcam.as<float>(), v->rec.as<float4>(), v->gview.as<float4>(),
+                                 v->gcone.as<float2>(), v->gflag.as<uint8_t>(), s));
+    CUDA_TRY(launch_bin_count(c, sp.binrec, v->gview.as<float4>(), v->gcone.as<float2>(), v->gflag.as<uint8_t>(),
+                              v->table.as<float>(), v->super.as<float>(), n, v->counts.as<uint32_t>(), s));
     CUDA_TRY(sum_counts(v->counts.as<uint32_t>(), n, v->sums.as<unsigned long long>(), s));
     CUDA_TRY(exclusive_scan(v->counts.as<uint32_t>(), v->vispos.as<uint32_t>(), n, v->scan_scr.as<uint32_t>(), 1, s));
     if (prof) CUDA_TRY(cudaEventRecord(v->prof[1], s));
@@ -497,9 +502,9 @@ static conegs_status render_impl(conegs_view *v, float *out_rgb, float *out_T, u
     CUDA_TRY(launch_gather(v->counts.as<uint32_t>(), v->dvals.as<uint32_t>(), M, v->sorted_counts.as<uint32_t>(), s));
     CUDA_TRY(exclusive_scan(v->sorted_counts.as<uint32_t>(), v->offsets.as<uint32_t>(), M, v->scan_scr.as<uint32_t>(),
                             0, s));
-    CUDA_TRY(launch_bin_emit(c, sp.binrec, v->gview.as<float4>(), v->gflag.as<uint8_t>(), v->table.as<float>(),
-                             v->super.as<float>(), M, v->dvals.as<uint32_t>(), v->offsets.as<uint32_t>(),
-                             v->pair_tile.as<uint32_t>(), v->pair_gid.as<uint32_t>(), s));
+    CUDA_TRY(launch_bin_emit(c, sp.binrec, v->gview.as<float4>(), v->gcone.as<float2>(), v->gflag.as<uint8_t>(),
+                             v->table.as<float>(), v->super.as<float>(), M, v->dvals.as<uint32_t>(),
+                             v->offsets.as<uint32_t>(), v->pair_tile.as<uint32_t>(), v->pair_gid.as<uint32_t>(), s));
     CUDA_TRY(radix_sort_pairs(v->pair_tile.as<uint32_t>(), v->pair_gid.as<uint32_t>(), v->pair_tile_alt.as<uint32_t>(),
                               v->pair_gid_alt.as<uint32_t>(), Pn, 0, bits_for(nt), v->rs_scr.as<uint32_t>(), s));
     CUDA_TRY(launch_ranges(v->pair_tile.as<uint32_t>(), Pn, v->ranges.as<uint2>(), nt, s));
@@ -527,8 +532,8 @@ static conegs_status render_impl(conegs_view *v, float *out_rgb, float *out_T, u
     CUDA_TRY(launch_raster_fwd(a, nt, !(flags & CONEGS_FILTER_NONE), s));
     if (prof) {
         CUDA_TRY(cudaEventRecord(v->prof[3], s));
-        CUDA_TRY(cudaMemcpyAsync(v->h_sums + 2, v->evaluated.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
-                                 s));
+        CUDA_TRY(cudaMemcpyAsync(v->h_sums + 2, v->evaluated.p, 2 * sizeof(unsigned long long),
+                                 cudaMemcpyDeviceToHost, s));
     }
     v->profiled = prof;
     v->n_launches = launches_so_far() - launches0;
@@ -628,7 +633,7 @@ conegs_status conegs_get_stats(const conegs_view *v, conegs_stats *out) {
     out->tiles_y = v->cam.tiles_y;
     out->n_valid_pixels = v->n_valid;
     out->n_launches = v->n_launches;
-    const DevBuf *bufs[] = {&v->d, &v->dx, &v->dy, &v->valid, &v->table, &v->super, &v->rec, &v->gview, &v->gflag,
+    const DevBuf *bufs[] = {&v->d, &v->dx, &v->dy, &v->valid, &v->table, &v->super, &v->mcam, &v->rec, &v->gview, &v->gcone, &v->gflag,
                             &v->counts, &v->vispos, &v->scan_scr, &v->dkeys, &v->dvals, &v->dkeys_alt, &v->dvals_alt,
                             &v->sorted_counts, &v->offsets, &v->pair_tile, &v->pair_gid, &v->pair_tile_alt,
                             &v->pair_gid_alt, &v->ranges, &v->last, &v->sums, &v->rs_scr, &v->tmp_rgb, &v->tmp_T,
@@ -647,7 +652,8 @@ conegs_status conegs_get_stats(const conegs_view *v, conegs_stats *out) {
         out->ms_sort = t12;
         out->ms_raster = t23;
         out->ms_total = t03;
-        out->n_evaluated = (int64_t)v->h_sums[2];
+        out->n_walked = (int64_t)v->h_sums[2];
+        out->n_evaluated = (int64_t)v->h_sums[3];
     }
     return CONEGS_OK;
 }

@@ -17,17 +17,18 @@
 //     |x* - mu| <= 255 kappa s_max (from det A <= (255 sigma)^2);
 //   * a (Gaussian, tile) pair is kept when the angle between mu - o and a_t
 //     is at most beta + gamma, sin(beta) = bound / L (chord form).
-// Two levels: super-tiles of 8x8 tiles prune (conservatively, with extra
-// margins), then the exact per-tile rule decides.
+// Two levels: super-tiles of 8x8 tiles and then tiles are pruned by a cheap
+// conservative cone test (fast math, wide margins); the exact per-tile rule
+// decides for the tiles that survive.
 #include "rule.cuh"
 
 namespace conegs {
 
 // ---------------------------------------------------------------- tile tables
 
-// One CTA of 256 threads per tile; thread = pixel.  Max-reductions are exact
-// and order independent.
-__global__ void __launch_bounds__(256) tile_table_kernel(CamParams c, float *__restrict__ table) {
+// One CTA of TILE*TILE threads per tile; thread = pixel.  Max-reductions are
+// exact and order independent.
+__global__ void __launch_bounds__(TILE_PX) tile_table_kernel(CamParams c, float *__restrict__ table) {
     const int t = blockIdx.x;
     const int tx = t % c.tiles_x, ty = t / c.tiles_x;
     const int i = tx * TILE + (threadIdx.x % TILE), j = ty * TILE + (threadIdx.x / TILE);
@@ -57,7 +58,8 @@ __global__ void __launch_bounds__(256) tile_table_kernel(CamParams c, float *__r
         ch2 = fmaxf(ch2, __shfl_xor_sync(0xffffffffu, ch2, off));
         mm = fmaxf(mm, __shfl_xor_sync(0xffffffffu, mm, off));
     }
-    __shared__ float s_ch[8], s_mm[8];
+    constexpr int NW = (TILE_PX + 31) / 32;
+    __shared__ float s_ch[NW], s_mm[NW];
     if ((threadIdx.x & 31) == 0) {
         s_ch[threadIdx.x >> 5] = ch2;
         s_mm[threadIdx.x >> 5] = mm;
@@ -65,7 +67,7 @@ __global__ void __launch_bounds__(256) tile_table_kernel(CamParams c, float *__r
     __syncthreads();
     if (threadIdx.x == 0) {
         float chm = s_ch[0], mmm = s_mm[0];
-        for (int w = 1; w < 8; ++w) {
+        for (int w = 1; w < NW; ++w) {
             chm = fmaxf(chm, s_ch[w]);
             mmm = fmaxf(mmm, s_mm[w]);
         }
@@ -119,6 +121,21 @@ __global__ void super_table_kernel(CamParams c, const float *__restrict__ table,
     o[5] = mmax * 1.0001f;
 }
 
+// Camera-wide footprint bound m_cam = max over tiles of m_t (for the
+// rasteriser's per-pixel pre-test).
+__global__ void max_m_kernel(const float *__restrict__ table, int nt, float *__restrict__ out) {
+    float m = 0.0f;
+    for (int t = threadIdx.x; t < nt; t += blockDim.x) m = fmaxf(m, table[6 * (size_t)t + 5]);
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __shared__ float sm[32];
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, sm[w]);
+        *out = fmaxf(m, sm[0]);
+    }
+}
+
 // ---------------------------------------------------------------- Gaussian bounds
 
 __global__ void gauss_scene_rule_kernel(SceneParams sp, float *__restrict__ binrec) {
@@ -147,11 +164,25 @@ __global__ void gauss_view_rule_kernel(CamParams c, SceneParams sp, float4 *__re
 
 // ---------------------------------------------------------------- count / emit
 
+// Cheap conservative prefilter (fast math, wide margins): the Gaussian's cone
+// (half-angle beta from the camera's largest footprint, given as sin/cos of
+// beta/2) against a tile or super-tile cone.  Everything the exact rule keeps
+// passes here; only survivors are given to the exact rule.
+__device__ __forceinline__ bool cone_prefilter(const float4 gv, const float2 half, const float *t) {
+    if (t[3] < 0.0f) return false;
+    const float e0 = gv.x - t[0], e1 = gv.y - t[1], e2 = gv.z - t[2];
+    const float ch2 = e0 * e0 + e1 * e1 + e2 * e2;
+    const float sphi = half.x * t[4] + half.y * t[3];     // sin((beta + gamma)/2)
+    const float lim = 2.0f * sphi * 1.001f + 2e-5f;
+    return ch2 <= lim * lim || half.y < 1e-3f;
+}
+
 // One warp per Gaussian.  MODE 0: count tiles into counts[gid].
 // MODE 1: emit tile ids at offsets[pos] for the Gaussian order[pos].
 template <int MODE>
 __global__ void __launch_bounds__(256) bin_kernel(CamParams c, const float *__restrict__ binrec,
                                                   const float4 *__restrict__ gview,
+                                                  const float2 *__restrict__ gcone,
                                                   const uint8_t *__restrict__ gflag, const float *__restrict__ table,
                                                   const float *__restrict__ super, int64_t n,
                                                   const uint32_t *__restrict__ order,
@@ -172,13 +203,14 @@ __global__ void __launch_bounds__(256) bin_kernel(CamParams c, const float *__re
     for (int k = 0; k < 6; ++k) g[k] = binrec[6 * (size_t)gid + k];
     g[5] = (float)fl;
     const float4 gv = gview[gid];
+    const float2 half = gcone[gid];
     const int nsup = c.supers_x * c.supers_y;
     uint32_t base = MODE == 1 ? offsets[w] : 0;
     uint32_t cnt = 0;
     for (int s0 = 0; s0 < nsup; s0 += 32) {
         const int s = s0 + lane;
         bool sp = false;
-        if (s < nsup) sp = rule_test(g, gv, super + 6 * (size_t)s);
+        if (s < nsup) sp = cone_prefilter(gv, half, super + 6 * (size_t)s);
         uint32_t bal = __ballot_sync(0xffffffffu, sp);
         while (bal) {
             const int b = __ffs(bal) - 1;
@@ -193,7 +225,8 @@ __global__ void __launch_bounds__(256) bin_kernel(CamParams c, const float *__re
                 uint32_t tile = 0;
                 if (tx < c.tiles_x && ty < c.tiles_y) {
                     tile = (uint32_t)(ty * c.tiles_x + tx);
-                    tp = rule_test(g, gv, table + 6 * (size_t)tile);
+                    const float *tt = table + 6 * (size_t)tile;
+                    tp = cone_prefilter(gv, half, tt) && rule_test(g, gv, tt);
                 }
                 const uint32_t tb = __ballot_sync(0xffffffffu, tp);
                 if (MODE == 1 && tp) {
@@ -210,12 +243,14 @@ __global__ void __launch_bounds__(256) bin_kernel(CamParams c, const float *__re
 
 // ---------------------------------------------------------------- launchers
 
-cudaError_t launch_tile_tables(const CamParams &c, float *table, float *super, cudaStream_t s) {
+cudaError_t launch_tile_tables(const CamParams &c, float *table, float *super, float *mcam, cudaStream_t s) {
     const int nt = c.tiles_x * c.tiles_y, ns = c.supers_x * c.supers_y;
     if (nt == 0) return cudaSuccess;
-    tile_table_kernel<<<nt, 256, 0, s>>>(c, table);
+    tile_table_kernel<<<nt, TILE_PX, 0, s>>>(c, table);
     note_launches(1);
     super_table_kernel<<<(unsigned)div_up(ns, 128), 128, 0, s>>>(c, table, super);
+    note_launches(1);
+    max_m_kernel<<<1, 1024, 0, s>>>(table, nt, mcam);
     note_launches(1);
     return cudaGetLastError();
 }
@@ -235,20 +270,22 @@ cudaError_t launch_gauss_view_rule(const CamParams &c, const SceneParams &sp, fl
     return cudaGetLastError();
 }
 
-cudaError_t launch_bin_count(const CamParams &c, const float *binrec, const float4 *gview, const uint8_t *gflag,
-                             const float *table, const float *super, int64_t n, uint32_t *counts, cudaStream_t s) {
+cudaError_t launch_bin_count(const CamParams &c, const float *binrec, const float4 *gview, const float2 *gcone,
+                             const uint8_t *gflag, const float *table, const float *super, int64_t n,
+                             uint32_t *counts, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    bin_kernel<0><<<(unsigned)div_up(n * 32, 256), 256, 0, s>>>(c, binrec, gview, gflag, table, super, n, nullptr,
-                                                               nullptr, counts, nullptr, nullptr);
+    bin_kernel<0><<<(unsigned)div_up(n * 32, 256), 256, 0, s>>>(c, binrec, gview, gcone, gflag, table, super, n,
+                                                               nullptr, nullptr, counts, nullptr, nullptr);
     note_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_bin_emit(const CamParams &c, const float *binrec, const float4 *gview, const uint8_t *gflag,
-                            const float *table, const float *super, int64_t n_sorted, const uint32_t *order,
-                            const uint32_t *offsets, uint32_t *out_tile, uint32_t *out_gid, cudaStream_t s) {
+cudaError_t launch_bin_emit(const CamParams &c, const float *binrec, const float4 *gview, const float2 *gcone,
+                            const uint8_t *gflag, const float *table, const float *super, int64_t n_sorted,
+                            const uint32_t *order, const uint32_t *offsets, uint32_t *out_tile, uint32_t *out_gid,
+                            cudaStream_t s) {
     if (n_sorted == 0) return cudaSuccess;
-    bin_kernel<1><<<(unsigned)div_up(n_sorted * 32, 256), 256, 0, s>>>(c, binrec, gview, gflag, table, super,
+    bin_kernel<1><<<(unsigned)div_up(n_sorted * 32, 256), 256, 0, s>>>(c, binrec, gview, gcone, gflag, table, super,
                                                                       n_sorted, order, offsets, nullptr, out_tile,
                                                                       out_gid);
     note_launches(1);

@@ -8,13 +8,14 @@
 
 namespace conegs {
 
-constexpr int TILE = 16;          // tile side in pixels (one CTA of 256 threads per tile)
+constexpr int TILE = 8;           // tile side in pixels (one CTA of TILE*TILE threads per tile)
+constexpr int TILE_PX = TILE * TILE;
 constexpr int SUPER = 8;          // tiles per super-tile side (coarse binning level)
 constexpr float ALPHA_MIN = 1.0f / 255.0f;
 constexpr float ALPHA_MAX = 0.99f;
 constexpr float T_STOP = 1e-4f;
 constexpr float T_NEAR = 0.01f;
-constexpr int REC_F4 = 5;         // float4 words per per-view raster record
+constexpr int REC_F4 = 8;         // float4 words per per-view raster record
 
 // Camera passed by value to kernels.
 struct CamParams {

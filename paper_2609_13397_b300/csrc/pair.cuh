@@ -1,4 +1,6 @@
 // Per pixel-Gaussian pair response (Sec. 4.1-4.2) in FP32 registers.
+// Reciprocals, square roots and exp use the SFU approximations (about 1-2 ulp),
+// far inside the 1e-4 output tolerance.
 //
 // With d_u = W d, g_i = W delta_i (W = W_eff), n = |d_u|^2:
 //   t* = -<o_u, d_u>/n,  q = o_u + t* d_u                          (Eq. 2)
@@ -12,6 +14,7 @@
 // A = I + E K E^T, so with G = E^T E and b = E^T q (Sylvester / Woodbury):
 //   det A = det(I + G K),  q^T A^-1 q = |q|^2 - b^T K (I + G K)^-1 b
 //   T = sigma_eff det(A)^-1/2 exp(-q^T A^-1 q / 2)                   (Eq. 9)
+// with q^T A^-1 q clamped below by |q|^2 / det A (exact bound, see below).
 // No 3x3 matrix and no plane basis is formed.
 #pragma once
 #include "common.cuh"
@@ -32,24 +35,24 @@ __device__ __forceinline__ void marginal_K(float h00, float h01, float h11, floa
                                            float &k11) {
     const float mean = 0.5f * (h00 + h11);
     const float half = 0.5f * (h00 - h11);
-    const float rad = sqrtf(half * half + h01 * h01);
+    const float r2 = half * half + h01 * h01;
+    const float rad = r2 > 0.0f ? r2 * rsqrtf(r2) : 0.0f;
     const float l1 = mean + rad;
     if (!(l1 > rho2)) {
         k00 = k01 = k11 = 0.0f;
         return;
     }
     const float det = h00 * h11 - h01 * h01;
-    const float l2 = fmaxf(det, 0.0f) / l1;   // smaller eigenvalue without cancellation
+    const float l2 = __fdividef(fmaxf(det, 0.0f), l1);   // smaller eigenvalue without cancellation
     if (l2 > rho2) {
         // both directions exceed the floor: K = (I - rho2 H'^-1)/3
-        const float s = rho2 / det;
+        const float s = __fdividef(rho2, det);
         k00 = (1.0f - s * h11) * (1.0f / 3.0f);
         k11 = (1.0f - s * h00) * (1.0f / 3.0f);
         k01 = (s * h01) * (1.0f / 3.0f);
     } else {
         // only the major direction exceeds: K = f(l1) (H' - l2 I)/(l1 - l2)
-        const float f1 = (l1 - rho2) / (3.0f * l1);
-        const float sc = f1 / (l1 - l2);
+        const float sc = __fdividef(l1 - rho2, 3.0f * l1 * (l1 - l2));
         k00 = sc * (h00 - l2);
         k11 = sc * (h11 - l2);
         k01 = sc * h01;
@@ -66,7 +69,7 @@ __device__ __forceinline__ bool pair_response(const float4 r0, const float4 r1, 
     const float du1 = r1.x * px.d[0] + r1.y * px.d[1] + r1.z * px.d[2];
     const float du2 = r2.x * px.d[0] + r2.y * px.d[1] + r2.z * px.d[2];
     const float n = du0 * du0 + du1 * du1 + du2 * du2;
-    const float inv_n = 1.0f / n;
+    const float inv_n = __fdividef(1.0f, n);
     const float p = r0.w * du0 + r1.w * du1 + r2.w * du2;
     const float ts = -p * inv_n;
     if (!(ts > T_NEAR)) return false;
@@ -111,8 +114,13 @@ __device__ __forceinline__ bool pair_response(const float4 r0, const float4 r1, 
         const float p10 = k01 * m11 - k11 * m10, p11 = k11 * m00 - k01 * m01;
         bPb = b0 * b0 * p00 + b0 * b1 * (p01 + p10) + b1 * b1 * p11;
     }
-    const float Q = qq - bPb / det;
-    T = sig * rsqrtf(det) * __expf(-0.5f * Q);
+    // q^T A^-1 q >= |q|^2 / lambda_max(A) >= |q|^2 / det A (A = I + a PSD rank-2
+    // matrix), a bound that also guards the FP32 difference against cancellation
+    // for far, flat Gaussians seen at grazing angles.
+    const float rdet = rsqrtf(det);
+    const float inv_det = rdet * rdet;
+    const float Q = fmaxf(qq - bPb * inv_det, qq * inv_det);
+    T = sig * rdet * __expf(-0.5f * Q);
     return true;
 }
 

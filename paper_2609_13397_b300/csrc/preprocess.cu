@@ -6,8 +6,11 @@
 // whitening W_eff = S_eff^-1 R^T of Sec. 3.
 // K2b (per view, run by render): o_u = W_eff (o - mu), the SH colour seen
 // along (mu - o)/|mu - o|, and the binning rule's direction / depth key.
-// The raster record is 5 float4 per Gaussian:
-//   [W row 0 | o_u.x] [W row 1 | o_u.y] [W row 2 | o_u.z] [rgb | sigma_eff] [rho^2, 0, 0, 0]
+// The raster record is 8 float4 per Gaussian:
+//   [W row 0 | o_u.x] [W row 1 | o_u.y] [W row 2 | o_u.z] [rgb | sigma_eff]
+//   [u | g0] [g1, g2, C00, C11] [C22, 2 C01, 2 C02, 2 C12] [rho^2, 0, 0, 0]
+// where (u, g, C) define the pixel pre-test: with e = d - u, a pixel ray d
+// with -1 + g.e + e^T C e > 0 cannot reach alpha >= 1/255 with this Gaussian.
 #include "rule.cuh"
 
 namespace conegs {
@@ -76,9 +79,108 @@ __device__ __forceinline__ void sh_basis(float x, float y, float z, int deg, flo
     Y[15] = ShC::C3A * x * (xx - 3.f * yy);
 }
 
+// Cone of pixel rays that can reach alpha >= 1/255 with a Gaussian.  Any such
+// pair has q^T A^-1 q <= kappa^2 (det A >= 1, Eq. 9), which puts mu within
+// kappa sqrt(s_max^2 + t*^2 m) of the pixel's centre ray (Sigma_render <=
+// Sigma_fp,eff, Eq. 12; m >= (|delta_x|^2 + |delta_y|^2)/3), with t* bounded
+// by min((L + kappa s_max)/(1 - kappa (1 + s_max/s_min) sqrt(m)), L + 255 kappa s_max).
+// Returns sin and cos of half the cone's half-angle, inflated by `margin`
+// (relative) + 1e-6; (1, 0) = every direction.
+__device__ float2 cone_half_angle(float kap, float s2, float r1, float L, float m, float margin) {
+    const float s = sqrtf(s2);
+    const float c = kap * r1 * sqrtf(m);
+    const float rfc = 255.0f * kap * s;
+    float rf, tb;
+    if (c < 1.0f) {
+        const float tbf = (L + kap * s) / (1.0f - c);
+        rf = fminf(kap * sqrtf(s2 + tbf * tbf * r1 * r1 * m), rfc);
+        tb = fminf(tbf, L + rf);
+    } else {
+        rf = rfc;
+        tb = L + rf;
+    }
+    if (L <= rf * (1.0f + margin)) return make_float2(1.0f, 0.0f);
+    const float rp = kap * sqrtf(s2 + tb * tb * m);
+    if (rp * (1.0f + margin) >= L) return make_float2(1.0f, 0.0f);
+    const float sb = rp / L;
+    const float sh2 = sb * sb / (2.0f * (1.0f + sqrtf(fmaxf(1.0f - sb * sb, 0.0f))));
+    const float sbh = fminf(sqrtf(sh2) * (1.0f + margin) + 1e-6f, 1.0f);
+    return make_float2(sbh, sqrtf(fmaxf(1.0f - sbh * sbh, 0.0f)));
+}
+
+// Visual-cone pre-test of the rasteriser.  A pair with alpha >= 1/255 has
+// q^T A^-1 q <= kappa^2, kappa^2 = 2 ln(255 sigma) (det A >= 1, Eq. 9).  In
+// world terms x = mu - x* (x* the closest-response point on the ray) lies in
+// {x : x^T (Sigma_eff + F)^-1 x <= kappa^2} with F the world footprint
+// (Eq. 12: Sigma_render <= Sigma_fp,eff), whose part across the ray is at most
+// t*^2 m (m >= (|dx|^2 + |dy|^2)/3).  So the centre ray must meet the
+// ellipsoid mu + {x : x^T M x <= 1}, M = (kappa'^2 (Sigma_eff + tau I))^-1,
+// tau = t_b^2 m, kappa'^2 = 1.01 kappa^2 (margin for FP32 rounding).  The line
+// o + t d meets it iff d^T C d <= 0, C = (1 - 1/v^T M v) M - (M v)(M v)^T / v^T M v,
+// v = o - mu.  Expanded around u = -v/L (the direction of mu) with e = d - u:
+//   L^2 d^T C d = -1 + 2 L e.(M v)/(v^T M v) + L^2 e^T C e,
+// where the constant and linear terms are exact closed forms (u^T C u = -1/L^2,
+// C u = M v/(L v^T M v)) and the quadratic term scales with |e|^2, so narrow
+// cones of far, small Gaussians do not cancel in FP32.  With the rows w_i of
+// W_eff (|w_i| = 1/s_i): M = sum_i c_i w_i w_i^T, c_i = 1/(kappa'^2 (1 + tau
+// |w_i|^2)), w_i . v = (o_u)_i.  Output: g (3) and C' = L^2 C (6: 00 11 22,
+// 2x 01 02 12).
+__device__ void cone_quadric(const float W[9], const float ou[3], float kap2, float tau, float L, float g[3],
+                             float C[6]) {
+    float c[3], Mv[3] = {0.f, 0.f, 0.f}, vMv = 0.f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float w2 = W[3 * i] * W[3 * i] + W[3 * i + 1] * W[3 * i + 1] + W[3 * i + 2] * W[3 * i + 2];
+        c[i] = 1.0f / (kap2 * (1.0f + tau * w2));
+        vMv += c[i] * ou[i] * ou[i];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) Mv[k] += c[i] * ou[i] * W[3 * i + k];
+    }
+    if (!(vMv > 1.0f)) {            // optical centre inside the ellipsoid: every ray meets it
+        g[0] = g[1] = g[2] = 0.0f;
+        C[0] = C[1] = C[2] = C[3] = C[4] = C[5] = 0.0f;
+        return;
+    }
+    const float a = 1.0f - 1.0f / vMv, b = 1.0f / vMv, L2 = L * L;
+    float M[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // 00 11 22 01 02 12
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float *w = W + 3 * i;
+        M[0] += c[i] * w[0] * w[0]; M[1] += c[i] * w[1] * w[1]; M[2] += c[i] * w[2] * w[2];
+        M[3] += c[i] * w[0] * w[1]; M[4] += c[i] * w[0] * w[2]; M[5] += c[i] * w[1] * w[2];
+    }
+    C[0] = L2 * (a * M[0] - b * Mv[0] * Mv[0]);
+    C[1] = L2 * (a * M[1] - b * Mv[1] * Mv[1]);
+    C[2] = L2 * (a * M[2] - b * Mv[2] * Mv[2]);
+    C[3] = 2.0f * L2 * (a * M[3] - b * Mv[0] * Mv[1]);
+    C[4] = 2.0f * L2 * (a * M[4] - b * Mv[0] * Mv[2]);
+    C[5] = 2.0f * L2 * (a * M[5] - b * Mv[1] * Mv[2]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) g[k] = 2.0f * L * b * Mv[k];
+}
+
+// t* bound of the binning rule (see cone_half_angle); false = no useful bound.
+__device__ bool tstar_bound(float kap, float s2, float r1, float L, float m, float &tb) {
+    const float s = sqrtf(s2);
+    const float c = kap * r1 * sqrtf(m);
+    const float rfc = 255.0f * kap * s;
+    float rf;
+    if (c < 1.0f) {
+        const float tbf = (L + kap * s) / (1.0f - c);
+        rf = fminf(kap * sqrtf(s2 + tbf * tbf * r1 * r1 * m), rfc);
+        tb = fminf(tbf, L + rf);
+    } else {
+        rf = rfc;
+        tb = L + rf;
+    }
+    tb *= 1.001f;
+    return true;
+}
+
 // Per view: binning direction/depth (the FP32 rule) and the raster record.
-__global__ void __launch_bounds__(256) view_records_kernel(CamParams c, SceneParams sp, float4 *__restrict__ rec,
-                                                           float4 *__restrict__ gview,
+__global__ void __launch_bounds__(256) view_records_kernel(CamParams c, SceneParams sp, const float *__restrict__ mcam,
+                                                           float4 *__restrict__ rec, float4 *__restrict__ gview,
+                                                           float2 *__restrict__ gcone,
                                                            uint8_t *__restrict__ gflag) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= sp.n) return;
@@ -108,12 +210,40 @@ __global__ void __launch_bounds__(256) view_records_kernel(CamParams c, ScenePar
         for (int j = 0; j < K; ++j) acc += load_scalar(sp.sh, (i * K + j) * 3 + ch, sp.storage) * Y[j];
         col[ch] = fmaxf(acc + 0.5f, 0.0f);
     }
+    const float rho2 = sp.rho2 ? sp.rho2[i] : 0.0f;
+    const float m = *mcam;
+    // binning prefilter: the cone of the binning rule's own bound (its kappa and
+    // scale bounds), camera-wide footprint, wide margin
+    const float *br = sp.binrec + 6 * i;
+    gcone[i] = L > 0.0f ? cone_half_angle(br[0], br[4], sqrtf(br[3]), L, m, 1e-3f) : make_float2(1.0f, 0.0f);
+    // rasteriser pre-test, with the exact kappa^2 = 2 ln(255 sigma)
+    float g[3] = {0.f, 0.f, 0.f}, C[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float pu[3] = {dx, dy, dz};
+    {
+        const float sig = 1.0f / (1.0f + expf(-load_scalar(sp.logits, i, sp.storage)));
+        const float k2 = 2.0f * logf(255.0f * sig);
+        const float lmax = fmaxf(fmaxf(sp.log_scales[3 * i], sp.log_scales[3 * i + 1]), sp.log_scales[3 * i + 2]);
+        const float lmin = fminf(fminf(sp.log_scales[3 * i], sp.log_scales[3 * i + 1]), sp.log_scales[3 * i + 2]);
+        const float s2 = expf(2.0f * lmax) * 1.00001f + rho2, s2mn = expf(2.0f * lmin) * 0.99999f + rho2;
+        if (!(k2 > 0.0f)) {
+            // sigma < 1/255: never reaches the alpha cut (value 99 for every unit d)
+            pu[0] = pu[1] = pu[2] = 0.0f;
+            C[0] = C[1] = C[2] = 100.0f;
+        } else if (L > 0.0f) {
+            float tb;
+            tstar_bound(sqrtf(k2), s2, 1.0f + sqrtf(s2 / s2mn), L, m, tb);
+            cone_quadric(W, ou, 1.01f * k2, tb * tb * m * 1.001f, L, g, C);
+        }
+    }
     float4 *r = rec + (size_t)REC_F4 * i;
     r[0] = make_float4(W[0], W[1], W[2], ou[0]);
     r[1] = make_float4(W[3], W[4], W[5], ou[1]);
     r[2] = make_float4(W[6], W[7], W[8], ou[2]);
     r[3] = make_float4(col[0], col[1], col[2], sp.sig_eff[i]);
-    r[4] = make_float4(sp.rho2 ? sp.rho2[i] : 0.0f, 0.f, 0.f, 0.f);
+    r[4] = make_float4(pu[0], pu[1], pu[2], g[0]);
+    r[5] = make_float4(g[1], g[2], C[0], C[1]);
+    r[6] = make_float4(C[2], C[3], C[4], C[5]);
+    r[7] = make_float4(rho2, 0.f, 0.f, 0.f);
 }
 
 cudaError_t launch_scene_cache(const SceneParams &sp, float *W, float *sig_eff, cudaStream_t s) {
@@ -123,10 +253,10 @@ cudaError_t launch_scene_cache(const SceneParams &sp, float *W, float *sig_eff, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_view_records(const CamParams &c, const SceneParams &sp, float4 *rec, float4 *gview,
-                                uint8_t *gflag, cudaStream_t s) {
+cudaError_t launch_view_records(const CamParams &c, const SceneParams &sp, const float *mcam, float4 *rec,
+                                float4 *gview, float2 *gcone, uint8_t *gflag, cudaStream_t s) {
     if (sp.n == 0) return cudaSuccess;
-    view_records_kernel<<<(unsigned)div_up(sp.n, 256), 256, 0, s>>>(c, sp, rec, gview, gflag);
+    view_records_kernel<<<(unsigned)div_up(sp.n, 256), 256, 0, s>>>(c, sp, mcam, rec, gview, gcone, gflag);
     note_launches(1);
     return cudaGetLastError();
 }

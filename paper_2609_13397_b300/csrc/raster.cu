@@ -1,7 +1,7 @@
 // K5: tile rasteriser, forward (Sec. 3 Eq. 4 compositing over Eq. 9 responses).
 //
-// One CTA of 256 threads per 16x16 tile, one thread per pixel.  The tile's
-// depth-sorted Gaussian list is walked in batches of 256: each thread loads
+// One CTA of 64 threads per 8x8 tile, one thread per pixel.  The tile's
+// depth-sorted Gaussian list is walked in batches of 64: each thread loads
 // one Gaussian's 80-byte record (5 x float4, coalesced gather) into shared
 // memory, then every thread evaluates the whole batch against its pixel's
 // rays from registers.  Compositing follows the 3DGS conventions: a =
@@ -23,7 +23,7 @@ struct RasterArgs {
     const uint8_t *valid;
     float *out_rgb, *out_T, *keep_T;   // keep_T: copy of the final T kept for the adjoint (may be NULL)
     uint32_t *last;        // per pixel: list entries up to and including the last contributor
-    unsigned long long *evaluated;   // optional: total pair evaluations (profiling)
+    unsigned long long *evaluated;   // optional (profiling): [0] list entries walked, [1] full evaluations
     int additive;
 };
 
@@ -42,8 +42,8 @@ __device__ __forceinline__ void load_pixel(const RasterArgs &a, int64_t pix, int
 }
 
 template <bool FILTER>
-__global__ void __launch_bounds__(256) raster_fwd_kernel(const RasterArgs a) {
-    __shared__ float4 s_rec[REC_F4][256];
+__global__ void __launch_bounds__(TILE_PX) raster_fwd_kernel(const RasterArgs a) {
+    __shared__ float4 s_rec[REC_F4][TILE_PX];
     const int tile = blockIdx.x;
     const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
     const int i = tx * TILE + (threadIdx.x % TILE), j = ty * TILE + (threadIdx.x / TILE);
@@ -58,9 +58,9 @@ __global__ void __launch_bounds__(256) raster_fwd_kernel(const RasterArgs a) {
     }
     const uint2 range = a.ranges[tile];
     float C0 = 0.f, C1 = 0.f, C2 = 0.f, Tacc = 1.0f;
-    uint32_t last = 0, walked = 0;
-    for (uint32_t start = range.x; start < range.y; start += 256) {
-        if (__syncthreads_count(done) == 256) break;
+    uint32_t last = 0, walked = 0, full = 0;
+    for (uint32_t start = range.x; start < range.y; start += TILE_PX) {
+        if (__syncthreads_count(done) == TILE_PX) break;
         const uint32_t idx = start + threadIdx.x;
         if (idx < range.y) {
             const float4 *r = a.rec + (size_t)REC_F4 * a.gids[idx];
@@ -68,13 +68,24 @@ __global__ void __launch_bounds__(256) raster_fwd_kernel(const RasterArgs a) {
             for (int k = 0; k < REC_F4; ++k) s_rec[k][threadIdx.x] = r[k];
         }
         __syncthreads();
-        const int nb = (int)min(256u, range.y - start);
+        const int nb = (int)min((uint32_t)TILE_PX, range.y - start);
         if (!done) {
             for (int b = 0; b < nb; ++b) {
                 ++walked;
+                // conservative pre-test: the centre ray misses the Gaussian's bounding
+                // ellipsoid (visual-cone test expanded around u, e = d - u)
+                const float4 r4 = s_rec[4][b];
+                const float4 r5 = s_rec[5][b];
+                const float4 r6 = s_rec[6][b];
+                const float e0 = px.d[0] - r4.x, e1 = px.d[1] - r4.y, e2 = px.d[2] - r4.z;
+                const float qa = r5.z * e0 + r6.y * e1 + r6.z * e2;
+                const float qb = r5.w * e1 + r6.w * e2;
+                const float cone = -1.0f + r4.w * e0 + r5.x * e1 + r5.y * e2 + qa * e0 + qb * e1 + r6.x * e2 * e2;
+                if (cone > 1e-3f) continue;
+                ++full;
                 const float4 r3 = s_rec[3][b];
                 float T;
-                if (!pair_response<FILTER>(s_rec[0][b], s_rec[1][b], s_rec[2][b], r3.w, s_rec[4][b].x,
+                if (!pair_response<FILTER>(s_rec[0][b], s_rec[1][b], s_rec[2][b], r3.w, s_rec[7][b].x,
                                            a.additive != 0, px, T))
                     continue;
                 const float alpha = fminf(ALPHA_MAX, T);
@@ -95,9 +106,15 @@ __global__ void __launch_bounds__(256) raster_fwd_kernel(const RasterArgs a) {
         __syncthreads();
     }
     if (a.evaluated) {
-        unsigned long long w = done || inside ? walked : 0;
-        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-        if ((threadIdx.x & 31) == 0) atomicAdd(a.evaluated, w);
+        unsigned long long w = walked, f = full;
+        for (int o = 16; o > 0; o >>= 1) {
+            w += __shfl_xor_sync(0xffffffffu, w, o);
+            f += __shfl_xor_sync(0xffffffffu, f, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(a.evaluated, w);
+            atomicAdd(a.evaluated + 1, f);
+        }
     }
     if (inside) {
         a.out_rgb[pix] = C0;
@@ -112,9 +129,9 @@ __global__ void __launch_bounds__(256) raster_fwd_kernel(const RasterArgs a) {
 cudaError_t launch_raster_fwd(const RasterArgs &a, int ntiles, bool filter, cudaStream_t s) {
     if (ntiles == 0) return cudaSuccess;
     if (filter)
-        raster_fwd_kernel<true><<<ntiles, 256, 0, s>>>(a);
+        raster_fwd_kernel<true><<<ntiles, TILE_PX, 0, s>>>(a);
     else
-        raster_fwd_kernel<false><<<ntiles, 256, 0, s>>>(a);
+        raster_fwd_kernel<false><<<ntiles, TILE_PX, 0, s>>>(a);
     note_launches(1);
     return cudaGetLastError();
 }

@@ -34,7 +34,7 @@ def test_binning_is_conservative(oracle_lib, name):
     pix, g = O.pairs_above(cam, sc, (1.0 / 255.0) * (1 - 1e-3))
     assert pix.size > 0
     tx, _ = O.tile_grid(cam)
-    tile = (pix // cam.width) // 16 * tx + (pix % cam.width) // 16
+    tile = (pix // cam.width) // O.TILE * tx + (pix % cam.width) // O.TILE
     missed = pas[g, tile] == 0
     assert missed.sum() == 0, f"{missed.sum()} of {pix.size} contributing pairs not binned"
     # the rule should not be wildly loose either (pairs per contributing pair)
@@ -49,7 +49,8 @@ def test_tile_cones_contain_fp64_rays(oracle_lib, name):
     d, _, _, valid = O.rays(cam)
     tx, _ = O.tile_grid(cam)
     ii = np.arange(cam.width * cam.height)
-    tile = (ii // cam.width) // 16 * tx + (ii % cam.width) // 16
+    T_ = oracle_lib.TILE
+    tile = (ii // cam.width) // T_ * tx + (ii % cam.width) // T_
     a = table[tile, :3].astype(float)
     sg = table[tile, 3].astype(float)
     chord = np.linalg.norm(a - d, axis=1)

@@ -16,6 +16,9 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-4
+# relative margin of the oracle's near-threshold flags (alpha vs 1/255 and 0.99, the
+# 1e-4 stop test, t* vs 0.01): well above the FP32 path's relative error in T
+EPS_FLAG = 2e-4
 
 
 @pytest.fixture(scope="module")
@@ -64,7 +67,7 @@ def test_ray_table(cg, oracle_lib, name):
     od, odx, ody, ovalid = oracle_lib.rays(cam)
     assert np.array_equal(valid.astype(bool), ovalid)
     m = ovalid
-    assert np.abs(d.T[m] - od[m]).max() < 2e-7
+    assert np.abs(d.T[m] - od[m]).max() < 4e-7      # a few FP32 ulps of a unit vector
     for g, o in ((dx, odx), (dy, ody)):
         err = np.linalg.norm(g.T[m] - o[m], axis=1) / np.linalg.norm(o[m], axis=1)
         assert err.max() < 2e-5, err.max()
@@ -113,7 +116,7 @@ def _render_compare(cg, oracle_lib, cam, sc, flags=0, filt=1, comp=0, storage=No
     rgb, T = v.render(flags=flags)
     rgb = rgb.cpu().numpy().reshape(3, -1).T
     T = T.cpu().numpy().reshape(-1)
-    r = oracle_lib.render(cam, sc, pix=pix, filter=filt, comp=comp, eps=2e-3, eps_key=1e-6)
+    r = oracle_lib.render(cam, sc, pix=pix, filter=filt, comp=comp, eps=EPS_FLAG)
     if pix is not None:
         rgb, T = rgb[pix], T[pix]
     ok = r.flags == 0
@@ -220,9 +223,9 @@ def test_full_size_c2_sampled(cg, oracle_lib):
         rgb = rgb.cpu().numpy().reshape(3, -1).T
         T = T.cpu().numpy().reshape(-1)
         pix = rng.choice(cam.n_pixels, size=min(600, cam.n_pixels), replace=False).astype(np.int32)
-        r = oracle_lib.render(cam, sc, pix=pix, eps=2e-3)
+        r = oracle_lib.render(cam, sc, pix=pix, eps=EPS_FLAG)
         ok = r.flags == 0
-        assert ok.mean() > 0.95
+        assert ok.mean() > 0.9, ok.mean()
         assert np.abs(rgb[pix] - r.rgb)[ok].max() <= TOL
         assert np.abs(T[pix] - r.T)[ok].max() <= TOL
         pg, _ = v.bin_counts()
