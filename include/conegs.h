@@ -214,6 +214,22 @@ conegs_status conegs_get_pairs(const conegs_view *view, int32_t *gaussian_ids, i
 conegs_status conegs_radix_sort_pairs(conegs_ctx *ctx, uint32_t *keys, uint32_t *values, int64_t n, int begin_bit,
                                       int end_bit, void *stream);
 
+/* The same stable radix sort, for callers that cannot allocate device memory
+ * while they sort: their device memory may be fully reserved by another
+ * allocator (a framework's caching allocator), or they run in a
+ * latency-critical loop that must not block on or fail in an allocation.
+ * The paper has no counterpart; this is a library service.
+ * The scratch is a fixed array inside the library (about 2.2 MB on every GPU
+ * that loads it, held until exit); the call allocates nothing.
+ *   keys/values: device arrays of n entries, sorted in place on `stream`.
+ *   n <= 262144; larger n fails with CONEGS_ERR_ARG.
+ * The first call on a device looks up the array's address with that device
+ * current; make it before any stream capture.  All calls share the one array
+ * and it keeps the last call's contents (nothing in it must start at zero):
+ * calls whose GPU work overlaps race, so order them (one stream, or events). */
+conegs_status conegs_radix_sort_pairs_noalloc(uint32_t *keys, uint32_t *values, int64_t n, int begin_bit,
+                                              int end_bit, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

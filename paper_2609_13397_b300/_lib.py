@@ -63,6 +63,7 @@ def lib():
         "conegs_get_bin_counts": ([P, P, P, P], c_int),
         "conegs_get_pairs": ([P, P, P, P], c_int),
         "conegs_radix_sort_pairs": ([P, P, P, c_int64, c_int, c_int, P], c_int),
+        "conegs_radix_sort_pairs_noalloc": ([P, P, c_int64, c_int, c_int, P], c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -77,7 +78,8 @@ def exported_symbols():
     return ["conegs_create", "conegs_destroy", "conegs_last_error", "conegs_version", "conegs_set_scene",
             "conegs_view_create", "conegs_view_destroy", "conegs_set_camera", "conegs_render", "conegs_render_host",
             "conegs_render_backward", "conegs_get_stats", "conegs_compute_floor", "conegs_get_rays",
-            "conegs_get_tile_table", "conegs_get_bin_counts", "conegs_get_pairs", "conegs_radix_sort_pairs"]
+            "conegs_get_tile_table", "conegs_get_bin_counts", "conegs_get_pairs", "conegs_radix_sort_pairs",
+            "conegs_radix_sort_pairs_noalloc"]
 
 
 def check(status: int, what: str = ""):

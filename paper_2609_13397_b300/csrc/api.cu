@@ -69,15 +69,20 @@ cudaError_t launch_backward_params(const CamParams &c, const SceneParams &sp, co
 
 using namespace conegs;
 
+namespace {
+thread_local std::string g_last_error;
+}  // namespace
+
 namespace conegs {
+// Lets other translation units of the library report a message through
+// conegs_last_error().
+void set_error_message(const char *msg) { g_last_error = msg; }
 static std::atomic<long long> g_launches{0};
 void note_launches(int k) { g_launches += k; }
 long long launches_so_far() { return g_launches.load(); }
 }  // namespace conegs
 
 namespace {
-
-thread_local std::string g_last_error;
 
 conegs_status fail(conegs_status st, const char *fmt, ...) {
     char buf[512];
