@@ -301,6 +301,29 @@ def run_ours(args, rank, world, local_rank):
         print(json.dumps(line), flush=True)
 
 
+def run_probe(args):
+    """Small fixed workloads for ncu captures: set up C2 and render one view a few
+    times (no timing, no JSON)."""
+    import torch
+    import paper_2609_13397_b300 as cg
+    cams, sc = build_workload()
+    ctx = cg.Context(0)
+    ctx.set_scene_from(sc)
+    v = ctx.view()
+    v.set_camera_from(cams[0])
+    rho2 = ctx.compute_floor([v])
+    ctx.set_scene_from(sc, rho2=rho2)
+    if args.probe == "raster-1/8":
+        v.set_camera_from(cams[1])
+    flags = cg.KEEP_FOR_BACKWARD if args.probe == "backward" else 0
+    for _ in range(3):
+        rgb, _ = v.render(flags=flags)
+        if args.probe == "backward":
+            v.render_backward(torch.ones_like(rgb))
+    torch.cuda.synchronize()
+    print("probe ok", args.probe, v.stats()["n_pairs"])
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -309,7 +332,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--probe", choices=["raster", "raster-1/8", "backward"], default=None,
+                    help="set up C2 and render 3 times for a profiler capture (prints no JSON)")
     args = ap.parse_args()
+    if args.probe:
+        run_probe(args)
+        return
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
