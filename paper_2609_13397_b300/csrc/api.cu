@@ -16,7 +16,7 @@
 #include <vector>
 
 #include "../../include/conegs.h"
-#include "common.cuh"
+#include "raster.cuh"
 
 namespace conegs {
 // launchers defined in the other translation units
@@ -46,20 +46,7 @@ cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *alt_keys,
                              int begin_bit, int end_bit, uint32_t *scratch, cudaStream_t s);
 cudaError_t launch_floor(const CamParams *cams_dev, int nv, const float *means, int64_t n, float *rho2,
                          cudaStream_t s);
-struct RasterArgs {
-    int W, H, tiles_x;
-    const uint2 *ranges;
-    const uint32_t *gids;
-    const float4 *rec;
-    const float *d, *dx, *dy;
-    const uint8_t *valid;
-    float *out_rgb, *out_T, *keep_T;
-    uint32_t *last;
-    unsigned long long *evaluated;
-    int additive;
-};
 cudaError_t launch_raster_fwd(const RasterArgs &a, int ntiles, bool filter, cudaStream_t s);
-struct BackwardArgs;
 cudaError_t launch_backward(const RasterArgs &a, int ntiles, bool filter, const float *dL_drgb, const float *dL_dT,
                             const float *final_T, float *g_rec, cudaStream_t s);
 cudaError_t launch_backward_params(const CamParams &c, const SceneParams &sp, const float *g_rec,

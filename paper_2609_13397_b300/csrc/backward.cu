@@ -1,13 +1,476 @@
-// K6/K7 placeholder (filled in by the adjoint implementation).
-#include "common.cuh"
+// K6/K7: adjoint of the render (reverse-mode, hand written).
+//
+// K6 walks each tile's list back to front for every pixel, recovering the
+// transmittance before each contributing pair by division from the final T
+// kept by the forward pass (T_k = T_{k+1} / (1 - a_k)); no per-pair state is
+// stored by the forward.  Each pair's response is recomputed with the same
+// code as the forward (so the same pairs pass the alpha and stop tests) and
+// differentiated.  For C = sum_k c_k a_k T_k and T_fin = prod_k (1 - a_k):
+//   dL/dc_k = a_k T_k dL/dC
+//   dL/da_k = T_k c_k.dL/dC - (S_k.dL/dC + T_fin dL/dT_fin)/(1 - a_k),
+//   S_k = sum_{j>k} c_j a_j T_j (colour behind k)                    (Eq. 4)
+// and da/dT = 1 below the 0.99 clamp.  Per pair the gradient w.r.t. the view
+// record (W_eff 9, o_u 3, sigma_eff, rgb 3) is reduced over the warp and
+// added atomically to a per-Gaussian buffer.
+// K7 applies the chain rule from the record to the scene parameters:
+// o_u = W (o - mu), W_ab = R_ba / s_eff,a, s_eff = sqrt(s^2 + rho^2),
+// sigma_eff = sigma prod s/s_eff (Eq. 10), s = exp(log s),
+// sigma = sigmoid(logit), R = R(q/|q|), rgb = max(0, SH(u) + 1/2),
+// u = (mu - o)/|mu - o|.  rho^2 is not differentiated.
+#include "raster.cuh"
+
 namespace conegs {
-struct RasterArgs;
-cudaError_t launch_backward(const RasterArgs &, int, bool, const float *, const float *, const float *, float *,
-                            cudaStream_t) {
-    return cudaErrorNotSupported;
+
+// Reverse-mode of pair_response<FILTER> given dL/dT.  Accumulates dL/dW (9,
+// row-major), dL/do_u (3) and returns dL/dsigma_eff.
+template <bool FILTER>
+__device__ __forceinline__ float pair_adjoint(const PairFwd &f, const float4 r0, const float4 r1, const float4 r2,
+                                              const float sig, const float rho2, const PixelRays &px, float gT,
+                                              float gW[9], float gou[3]) {
+    const float T = f.T;
+    const float gsig = sig > 0.0f ? gT * T / sig : 0.0f;
+    const float gQ = -0.5f * T * gT;
+    float gqq = 0.0f, gdu[3] = {0.f, 0.f, 0.f}, gq[3] = {0.f, 0.f, 0.f}, gts = 0.0f, ginv_n = 0.0f;
+    float ggx[3] = {0.f, 0.f, 0.f}, ggy[3] = {0.f, 0.f, 0.f};
+    if (!FILTER) {
+        gqq = gQ;
+    } else {
+        float gdet = -0.5f * T * gT * f.inv_det;             // T ~ det^-1/2
+        float gbPb = 0.0f;
+        if (!f.clamped) {                                    // Q = qq - bPb/det
+            gqq = gQ;
+            gbPb = -gQ * f.inv_det;
+            gdet += gQ * f.bPb * f.inv_det * f.inv_det;
+        } else {                                             // Q = qq/det
+            gqq = gQ * f.inv_det;
+            gdet += -gQ * f.qq * f.inv_det * f.inv_det;
+        }
+        // bPb = b0^2 p00 + b0 b1 (p01 + p10) + b1^2 p11
+        const float b0 = f.b0, b1 = f.b1;
+        const float gb0 = gbPb * (2.0f * b0 * f.p00 + b1 * (f.p01 + f.p10));
+        const float gb1 = gbPb * (b0 * (f.p01 + f.p10) + 2.0f * b1 * f.p11);
+        const float gp00 = gbPb * b0 * b0, gp01 = gbPb * b0 * b1, gp10 = gp01, gp11 = gbPb * b1 * b1;
+        // P = K adj(M)
+        const float k00 = f.k00, k01 = f.k01, k11 = f.k11;
+        const float m00 = f.m00, m01 = f.m01, m10 = f.m10, m11 = f.m11;
+        float gk00 = gp00 * m11 - gp01 * m01;
+        float gk01 = -gp00 * m10 + gp01 * m00 + gp10 * m11 - gp11 * m01;
+        float gk11 = -gp10 * m10 + gp11 * m00;
+        float gm00 = gp01 * k01 + gp11 * k11 + gdet * m11;
+        float gm11 = gp00 * k00 + gp10 * k01 + gdet * m00;
+        float gm01 = -gp01 * k00 - gp11 * k01 - gdet * m10;
+        float gm10 = -gp00 * k01 - gp10 * k11 - gdet * m01;
+        // M = I + G K
+        const float G00 = f.G00, G01 = f.G01, G11 = f.G11;
+        const float gG00 = gm00 * k00 + gm01 * k01;
+        const float gG01 = gm00 * k01 + gm01 * k11 + gm10 * k00 + gm11 * k01;
+        const float gG11 = gm10 * k01 + gm11 * k11;
+        gk00 += gm00 * G00 + gm10 * G01;
+        gk01 += gm00 * G01 + gm01 * G00 + gm10 * G11 + gm11 * G01;
+        gk11 += gm01 * G01 + gm11 * G11;
+        // K = f(H') (Eq. 12); H' = t2 A, t2 = ts^2/3
+        float gcx = 0.0f, gcy = 0.0f;
+        if (f.kcase == 1 || f.kcase == 2) {
+            const float h00 = f.h00, h01 = f.h01, h11 = f.h11;
+            float gh00 = 0.f, gh01 = 0.f, gh11 = 0.f;
+            const float dh = h00 * h11 - h01 * h01;
+            if (f.kcase == 1) {                              // K = (I - rho2 H'^-1)/3
+                const float s = rho2 / dh;
+                const float gs = (-gk00 * h11 - gk11 * h00 + gk01 * h01) * (1.0f / 3.0f);
+                gh11 += -gk00 * s * (1.0f / 3.0f);
+                gh00 += -gk11 * s * (1.0f / 3.0f);
+                gh01 += gk01 * s * (1.0f / 3.0f);
+                const float gdh = -gs * s / dh;
+                gh00 += gdh * h11;
+                gh11 += gdh * h00;
+                gh01 += -2.0f * gdh * h01;
+            } else {                                         // K = sc (H' - l2 I)
+                const float mean = 0.5f * (h00 + h11), half = 0.5f * (h00 - h11);
+                const float r2 = half * half + h01 * h01;
+                const float rad = r2 > 0.0f ? sqrtf(r2) : 0.0f;
+                const float l1 = mean + rad;
+                const float l2 = fmaxf(dh, 0.0f) / l1;
+                const float D = 3.0f * l1 * (l1 - l2);
+                const float sc = (l1 - rho2) / D;
+                const float gsc = gk00 * (h00 - l2) + gk11 * (h11 - l2) + gk01 * h01;
+                gh00 += gk00 * sc;
+                gh11 += gk11 * sc;
+                gh01 += gk01 * sc;
+                float gl2 = -(gk00 + gk11) * sc;
+                const float gN = gsc / D, gD = -gsc * sc / D;
+                float gl1 = gN + gD * 3.0f * (2.0f * l1 - l2);
+                gl2 += gD * (-3.0f * l1);
+                const float gdh2 = dh > 0.0f ? gl2 / l1 : 0.0f;
+                gl1 += -gl2 * l2 / l1;
+                gh00 += gdh2 * h11;
+                gh11 += gdh2 * h00;
+                gh01 += -2.0f * gdh2 * h01;
+                const float ghalf = rad > 0.0f ? gl1 * half / rad : 0.0f;
+                gh01 += rad > 0.0f ? gl1 * h01 / rad : 0.0f;
+                gh00 += 0.5f * gl1 + 0.5f * ghalf;
+                gh11 += 0.5f * gl1 - 0.5f * ghalf;
+            }
+            const float gt2 = gh00 * f.A00 + gh01 * f.A01 + gh11 * f.A11;
+            const float gA00 = gh00 * f.t2, gA01 = gh01 * f.t2, gA11 = gh11 * f.t2;
+            gts += gt2 * (2.0f / 3.0f) * f.ts;
+            gcx += gA00 * (2.0f * f.cx - 2.0f * px.d_dx) + gA01 * (f.cy - px.d_dy);
+            gcy += gA11 * (2.0f * f.cy - 2.0f * px.d_dy) + gA01 * (f.cx - px.d_dx);
+        }
+        // G, b from e_x, e_y, q
+        float gex[3], gey[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            gex[k] = 2.0f * gG00 * f.ex[k] + gG01 * f.ey[k] + gb0 * f.q[k];
+            gey[k] = 2.0f * gG11 * f.ey[k] + gG01 * f.ex[k] + gb1 * f.q[k];
+            gq[k] += gb0 * f.ex[k] + gb1 * f.ey[k];
+        }
+        // e_i = ts (g_i - c_i du)
+        const float ts = f.ts;
+        float gxe = 0.f, gye = 0.f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            gts += gex[k] * (f.gx[k] - f.cx * f.du[k]) + gey[k] * (f.gy[k] - f.cy * f.du[k]);
+            ggx[k] += ts * gex[k];
+            ggy[k] += ts * gey[k];
+            gxe += gex[k] * f.du[k];
+            gye += gey[k] * f.du[k];
+            gdu[k] += -ts * (f.cx * gex[k] + f.cy * gey[k]);
+        }
+        gcx += -ts * gxe;
+        gcy += -ts * gye;
+        // c_i = (du . g_i) inv_n
+        float dgx = 0.f, dgy = 0.f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            gdu[k] += (gcx * f.gx[k] + gcy * f.gy[k]) * f.inv_n;
+            ggx[k] += gcx * f.inv_n * f.du[k];
+            ggy[k] += gcy * f.inv_n * f.du[k];
+            dgx += f.du[k] * f.gx[k];
+            dgy += f.du[k] * f.gy[k];
+        }
+        ginv_n += gcx * dgx + gcy * dgy;
+    }
+    // qq = q.q ; q = o_u + ts du
+    const float ou[3] = {r0.w, r1.w, r2.w};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) gq[k] += 2.0f * gqq * f.q[k];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        gou[k] += gq[k];
+        gts += gq[k] * f.du[k];
+        gdu[k] += f.ts * gq[k];
+    }
+    // ts = -p inv_n ; p = o_u . du ; inv_n = 1/n ; n = du . du
+    const float gp = -gts * f.inv_n;
+    ginv_n += -gts * f.p;
+    const float gn = -ginv_n * f.inv_n * f.inv_n;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        gou[k] += gp * f.du[k];
+        gdu[k] += gp * ou[k] + 2.0f * gn * f.du[k];
+    }
+    // du = W d, g_x = W dx, g_y = W dy
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+            gW[3 * a + b] += gdu[a] * px.d[b] + (FILTER ? ggx[a] * px.dx[b] + ggy[a] * px.dy[b] : 0.0f);
+    return gsig;
 }
-cudaError_t launch_backward_params(const CamParams &, const SceneParams &, const float *, const uint8_t *,
-                                   const float4 *, float *, float *, float *, float *, float *, cudaStream_t) {
-    return cudaErrorNotSupported;
+
+template <bool FILTER>
+__global__ void __launch_bounds__(TILE_PX) raster_bwd_kernel(const RasterArgs a, const float *__restrict__ dL_drgb,
+                                                             const float *__restrict__ dL_dT,
+                                                             const float *__restrict__ final_T,
+                                                             float *__restrict__ g_rec) {
+    __shared__ float4 s_rec[REC_F4][TILE_PX];
+    __shared__ uint32_t s_gid[TILE_PX];
+    const int tile = blockIdx.x;
+    const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+    const int i = tx * TILE + (threadIdx.x % TILE), j = ty * TILE + (threadIdx.x / TILE);
+    const int64_t P = (int64_t)a.W * a.H;
+    const bool inside = i < a.W && j < a.H;
+    const int64_t pix = (int64_t)j * a.W + i;
+    const int lane = threadIdx.x & 31;
+    PixelRays px;
+    uint32_t last = 0;
+    float T = 1.0f, Tfin = 1.0f, GC[3] = {0.f, 0.f, 0.f}, GT = 0.f, S[3] = {0.f, 0.f, 0.f};
+    if (inside && a.valid[pix]) {
+        load_pixel(a, pix, P, px);
+        last = a.last[pix];
+        T = Tfin = final_T[pix];
+        GC[0] = dL_drgb[pix]; GC[1] = dL_drgb[P + pix]; GC[2] = dL_drgb[2 * P + pix];
+        GT = dL_dT ? dL_dT[pix] : 0.0f;
+    }
+    const uint2 range = a.ranges[tile];
+    // the CTA only needs the entries up to its pixels' furthest last contributor
+    __shared__ uint32_t s_maxlast;
+    if (threadIdx.x == 0) s_maxlast = 0;
+    __syncthreads();
+    atomicMax(&s_maxlast, last);
+    __syncthreads();
+    const uint32_t stop = range.x + s_maxlast;
+    for (uint32_t end = stop; end > range.x;) {
+        const uint32_t start = end - min((uint32_t)TILE_PX, end - range.x);
+        const uint32_t nb = end - start;
+        __syncthreads();
+        if (threadIdx.x < nb) {
+            const uint32_t gid = a.gids[start + threadIdx.x];
+            s_gid[threadIdx.x] = gid;
+            const float4 *r = a.rec + (size_t)REC_F4 * gid;
+#pragma unroll
+            for (int k = 0; k < REC_F4; ++k) s_rec[k][threadIdx.x] = r[k];
+        }
+        __syncthreads();
+        for (int b = (int)nb - 1; b >= 0; --b) {
+            const uint32_t walk = start + b - range.x + 1;     // 1-based walk index of this entry
+            bool active = walk <= last;
+            float gW[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, gou[3] = {0.f, 0.f, 0.f};
+            float gsig = 0.f, grgb[3] = {0.f, 0.f, 0.f};
+            if (active) {
+                const float4 r4 = s_rec[4][b], r5 = s_rec[5][b], r6 = s_rec[6][b];
+                const float e0 = px.d[0] - r4.x, e1 = px.d[1] - r4.y, e2 = px.d[2] - r4.z;
+                const float qa = r5.z * e0 + r6.y * e1 + r6.z * e2;
+                const float qb = r5.w * e1 + r6.w * e2;
+                const float cone = -1.0f + r4.w * e0 + r5.x * e1 + r5.y * e2 + qa * e0 + qb * e1 + r6.x * e2 * e2;
+                active = !(cone > 1e-3f);
+            }
+            PairFwd f;
+            float Tresp = 0.f;
+            if (active) {
+                active = pair_response<FILTER, true>(s_rec[0][b], s_rec[1][b], s_rec[2][b], s_rec[3][b].w,
+                                                     s_rec[7][b].x, a.additive != 0, px, Tresp, &f);
+            }
+            float alpha = 0.f;
+            if (active) {
+                alpha = fminf(ALPHA_MAX, Tresp);
+                active = !(alpha < ALPHA_MIN);
+            }
+            if (active) {
+                const float4 r3 = s_rec[3][b];
+                const float one_m = 1.0f - alpha;
+                const float Tb = T / one_m;                     // transmittance before this pair
+                const float cG = r3.x * GC[0] + r3.y * GC[1] + r3.z * GC[2];
+                const float SG = S[0] * GC[0] + S[1] * GC[1] + S[2] * GC[2];
+                const float galpha = Tb * cG - (SG + GT * Tfin) / one_m;
+                const float w = alpha * Tb;
+                grgb[0] = w * GC[0]; grgb[1] = w * GC[1]; grgb[2] = w * GC[2];
+                S[0] += r3.x * w; S[1] += r3.y * w; S[2] += r3.z * w;
+                T = Tb;
+                const float gT = Tresp < ALPHA_MAX ? galpha : 0.0f;
+                gsig = pair_adjoint<FILTER>(f, s_rec[0][b], s_rec[1][b], s_rec[2][b], r3.w, s_rec[7][b].x, px, gT,
+                                            gW, gou);
+            }
+            // warp reduction, then one thread per warp adds to the Gaussian's buffer
+            const unsigned any = __ballot_sync(0xffffffffu, active);
+            if (any) {
+                float v[16];
+#pragma unroll
+                for (int k = 0; k < 9; ++k) v[k] = gW[k];
+                v[9] = gou[0]; v[10] = gou[1]; v[11] = gou[2]; v[12] = gsig;
+                v[13] = grgb[0]; v[14] = grgb[1]; v[15] = grgb[2];
+#pragma unroll
+                for (int k = 0; k < 16; ++k)
+                    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+                if (lane == 0) {
+                    float *dst = g_rec + 16 * (size_t)s_gid[b];
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) atomicAdd(dst + k, v[k]);
+                }
+            }
+        }
+        end = start;
+    }
 }
+
+cudaError_t launch_backward(const RasterArgs &a, int ntiles, bool filter, const float *dL_drgb, const float *dL_dT,
+                            const float *final_T, float *g_rec, cudaStream_t s) {
+    if (ntiles == 0) return cudaSuccess;
+    if (filter)
+        raster_bwd_kernel<true><<<ntiles, TILE_PX, 0, s>>>(a, dL_drgb, dL_dT, final_T, g_rec);
+    else
+        raster_bwd_kernel<false><<<ntiles, TILE_PX, 0, s>>>(a, dL_drgb, dL_dT, final_T, g_rec);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- K7: chain to the scene parameters
+
+// d Y_j / d(x, y, z) of the real SH basis (positive constants, l-major).
+__device__ __forceinline__ void sh_basis_grad(float x, float y, float z, int j, float g[3]) {
+    const float C1 = 0.48860251190291992f, C2A = 1.0925484305920792f, C2B = 0.31539156525252005f,
+                C2C = 0.54627421529603959f, C3A = 0.59004358992664352f, C3B = 2.8906114426405538f,
+                C3C = 0.45704579946446572f, C3D = 0.37317633259011540f, C3E = 1.4453057213202769f;
+    g[0] = g[1] = g[2] = 0.0f;
+    switch (j) {
+        case 1: g[1] = C1; break;
+        case 2: g[2] = C1; break;
+        case 3: g[0] = C1; break;
+        case 4: g[0] = C2A * y; g[1] = C2A * x; break;
+        case 5: g[1] = C2A * z; g[2] = C2A * y; break;
+        case 6: g[2] = 6.f * C2B * z; break;
+        case 7: g[0] = C2A * z; g[2] = C2A * x; break;
+        case 8: g[0] = 2.f * C2C * x; g[1] = -2.f * C2C * y; break;
+        case 9: g[0] = 6.f * C3A * x * y; g[1] = C3A * (3.f * x * x - 3.f * y * y); break;
+        case 10: g[0] = C3B * y * z; g[1] = C3B * x * z; g[2] = C3B * x * y; break;
+        case 11: g[1] = C3C * (5.f * z * z - 1.f); g[2] = 10.f * C3C * y * z; break;
+        case 12: g[2] = C3D * (15.f * z * z - 3.f); break;
+        case 13: g[0] = C3C * (5.f * z * z - 1.f); g[2] = 10.f * C3C * x * z; break;
+        case 14: g[0] = 2.f * C3E * x * z; g[1] = -2.f * C3E * y * z; g[2] = C3E * (x * x - y * y); break;
+        case 15: g[0] = C3A * (3.f * x * x - 3.f * y * y); g[1] = -6.f * C3A * x * y; break;
+        default: break;
+    }
+}
+
+__device__ __forceinline__ float sh_basis_value(float x, float y, float z, int j) {
+    const float Y0 = 0.28209479177387814f, C1 = 0.48860251190291992f, C2A = 1.0925484305920792f,
+                C2B = 0.31539156525252005f, C2C = 0.54627421529603959f, C3A = 0.59004358992664352f,
+                C3B = 2.8906114426405538f, C3C = 0.45704579946446572f, C3D = 0.37317633259011540f,
+                C3E = 1.4453057213202769f;
+    switch (j) {
+        case 0: return Y0;
+        case 1: return C1 * y;
+        case 2: return C1 * z;
+        case 3: return C1 * x;
+        case 4: return C2A * x * y;
+        case 5: return C2A * y * z;
+        case 6: return C2B * (3.f * z * z - 1.f);
+        case 7: return C2A * x * z;
+        case 8: return C2C * (x * x - y * y);
+        case 9: return C3A * y * (3.f * x * x - y * y);
+        case 10: return C3B * x * y * z;
+        case 11: return C3C * y * (5.f * z * z - 1.f);
+        case 12: return C3D * z * (5.f * z * z - 3.f);
+        case 13: return C3C * x * (5.f * z * z - 1.f);
+        case 14: return C3E * z * (x * x - y * y);
+        default: return C3A * x * (x * x - 3.f * y * y);
+    }
+}
+
+__global__ void __launch_bounds__(256) backward_params_kernel(CamParams c, SceneParams sp,
+                                                              const float *__restrict__ g_rec,
+                                                              const uint8_t *__restrict__ gflag,
+                                                              float *__restrict__ g_means, float *__restrict__ g_ls,
+                                                              float *__restrict__ g_quats,
+                                                              float *__restrict__ g_logits, float *__restrict__ g_sh) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= sp.n || gflag[i] == 0) return;
+    const float *gr = g_rec + 16 * i;
+    bool any = false;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) any |= gr[k] != 0.0f;
+    if (!any) return;
+    const float mu[3] = {sp.means[3 * i], sp.means[3 * i + 1], sp.means[3 * i + 2]};
+    const float v[3] = {mu[0] - c.o[0], mu[1] - c.o[1], mu[2] - c.o[2]};   // mu - o
+    const float L = sqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    // quaternion, rotation, scales
+    const float qr[4] = {sp.quats[4 * i], sp.quats[4 * i + 1], sp.quats[4 * i + 2], sp.quats[4 * i + 3]};
+    const float qn = sqrtf(qr[0] * qr[0] + qr[1] * qr[1] + qr[2] * qr[2] + qr[3] * qr[3]);
+    const float w = qr[0] / qn, x = qr[1] / qn, y = qr[2] / qn, z = qr[3] / qn;
+    const float R[9] = {1.f - 2.f * (y * y + z * z), 2.f * (x * y - w * z), 2.f * (x * z + w * y),
+                        2.f * (x * y + w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z - w * x),
+                        2.f * (x * z - w * y), 2.f * (y * z + w * x), 1.f - 2.f * (x * x + y * y)};
+    const float rho2 = sp.rho2 ? sp.rho2[i] : 0.0f;
+    float s[3], seff[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        s[a] = expf(sp.log_scales[3 * i + a]);
+        seff[a] = sqrtf(s[a] * s[a] + rho2);
+    }
+    const float logit = load_scalar(sp.logits, i, sp.storage);
+    const float sig = 1.0f / (1.0f + expf(-logit));
+    const float sig_eff = sp.sig_eff[i];
+    // dL/dW including o_u = W (o - mu); dL/dmu from o_u
+    float gW[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) gW[3 * a + b] = gr[3 * a + b] + gr[9 + a] * (-v[b]);
+    float gmu[3] = {0.f, 0.f, 0.f};
+    const float *Wm = sp.W + 9 * i;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) gmu[b] = -(Wm[b] * gr[9] + Wm[3 + b] * gr[10] + Wm[6 + b] * gr[11]);
+    // W_ab = R_ba / seff_a
+    float gR[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, gseff[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            gR[3 * b + a] += gW[3 * a + b] / seff[a];
+            gseff[a] += -gW[3 * a + b] * R[3 * b + a] / (seff[a] * seff[a]);
+        }
+    // sigma_eff = sigma prod s/seff
+    const float gsig_eff = gr[12];
+    float gls[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float gs = gseff[a] * s[a] / seff[a] + gsig_eff * sig_eff * (1.0f / s[a] - s[a] / (seff[a] * seff[a]));
+        gls[a] = gs * s[a];
+    }
+    const float gsig = sig > 0.0f ? gsig_eff * sig_eff / sig : 0.0f;
+    const float glogit = gsig * sig * (1.0f - sig);
+    // R(q/|q|)
+    const float gw = 2.f * (-z * gR[1] + y * gR[2] + z * gR[3] - x * gR[5] - y * gR[6] + x * gR[7]);
+    const float gx = 2.f * (y * gR[1] + z * gR[2] + y * gR[3] - 2.f * x * gR[4] - w * gR[5] + z * gR[6] +
+                            w * gR[7] - 2.f * x * gR[8]);
+    const float gy = 2.f * (-2.f * y * gR[0] + x * gR[1] + w * gR[2] + x * gR[3] + z * gR[5] - w * gR[6] +
+                            z * gR[7] - 2.f * y * gR[8]);
+    const float gz = 2.f * (-2.f * z * gR[0] - w * gR[1] + x * gR[2] + w * gR[3] - 2.f * z * gR[4] + y * gR[5] +
+                            x * gR[6] + y * gR[7]);
+    const float dotq = w * gw + x * gx + y * gy + z * gz;
+    const float gqn[4] = {(gw - w * dotq) / qn, (gx - x * dotq) / qn, (gy - y * dotq) / qn, (gz - z * dotq) / qn};
+    // colour: rgb = max(0, SH(u) + 1/2), u = (mu - o)/L
+    const int K = (sp.sh_degree + 1) * (sp.sh_degree + 1);
+    float u[3] = {0.f, 0.f, 1.f};
+    if (L > 0.0f) { u[0] = v[0] / L; u[1] = v[1] / L; u[2] = v[2] / L; }
+    float gu[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        const float grgb = gr[13 + ch];
+        if (grgb == 0.0f) continue;
+        float raw = 0.5f;
+        for (int j = 0; j < K; ++j) raw += load_scalar(sp.sh, (i * K + j) * 3 + ch, sp.storage) * sh_basis_value(u[0], u[1], u[2], j);
+        if (!(raw > 0.0f)) continue;
+        for (int j = 0; j < K; ++j) {
+            const float Y = sh_basis_value(u[0], u[1], u[2], j);
+            if (g_sh) g_sh[(i * K + j) * 3 + ch] += grgb * Y;
+            if (j > 0) {
+                float gY[3];
+                sh_basis_grad(u[0], u[1], u[2], j, gY);
+                const float c_j = load_scalar(sp.sh, (i * K + j) * 3 + ch, sp.storage) * grgb;
+                gu[0] += c_j * gY[0]; gu[1] += c_j * gY[1]; gu[2] += c_j * gY[2];
+            }
+        }
+    }
+    if (L > 0.0f) {
+        const float ud = u[0] * gu[0] + u[1] * gu[1] + u[2] * gu[2];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) gmu[k] += (gu[k] - u[k] * ud) / L;
+    }
+    if (g_means) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) g_means[3 * i + k] += gmu[k];
+    }
+    if (g_ls) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) g_ls[3 * i + k] += gls[k];
+    }
+    if (g_quats) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) g_quats[4 * i + k] += gqn[k];
+    }
+    if (g_logits) g_logits[i] += glogit;
+}
+
+cudaError_t launch_backward_params(const CamParams &c, const SceneParams &sp, const float *g_rec,
+                                   const uint8_t *gflag, const float4 *gview, float *g_means, float *g_log_scales,
+                                   float *g_quats, float *g_logits, float *g_sh, cudaStream_t s) {
+    (void)gview;
+    if (sp.n == 0) return cudaSuccess;
+    backward_params_kernel<<<(unsigned)div_up(sp.n, 256), 256, 0, s>>>(c, sp, g_rec, gflag, g_means, g_log_scales,
+                                                                      g_quats, g_logits, g_sh);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
 }  // namespace conegs

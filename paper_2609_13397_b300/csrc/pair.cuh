@@ -26,13 +26,26 @@ struct PixelRays {
     float d_dx, d_dy, dxdx, dxdy, dydy;   // for the marginal rule (Eq. 12)
 };
 
+// Intermediates of one pair evaluation, kept for the adjoint.
+struct PairFwd {
+    float du[3], gx[3], gy[3], inv_n, p, ts, q[3], qq, cx, cy, ex[3], ey[3];
+    float G00, G01, G11, b0, b1;
+    int kcase;                 // 0: K = I/3; 1: K = (I - rho2 H'^-1)/3; 2: rank-1 K; 3: K = 0
+    float k00, k01, k11;
+    float t2, A00, A01, A11, h00, h01, h11;
+    float m00, m01, m10, m11, det, p00, p01, p10, p11, bPb, inv_det;
+    bool clamped;              // Q = |q|^2/det (lower bound) was active
+    float T;
+};
+
 __device__ __forceinline__ float dot3(const float a[3], const float b[3]) {
     return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
 }
 
 // 2x2 matrix function K = f(H') of Eq. 12 (H' symmetric PSD), f(l) = max(l - rho2, 0) / (3 l).
-__device__ __forceinline__ void marginal_K(float h00, float h01, float h11, float rho2, float &k00, float &k01,
-                                           float &k11) {
+// Returns the case (1: both eigenvalues above rho2, 2: only the larger, 3: neither).
+__device__ __forceinline__ int marginal_K(float h00, float h01, float h11, float rho2, float &k00, float &k01,
+                                          float &k11) {
     const float mean = 0.5f * (h00 + h11);
     const float half = 0.5f * (h00 - h11);
     const float r2 = half * half + h01 * h01;
@@ -40,7 +53,7 @@ __device__ __forceinline__ void marginal_K(float h00, float h01, float h11, floa
     const float l1 = mean + rad;
     if (!(l1 > rho2)) {
         k00 = k01 = k11 = 0.0f;
-        return;
+        return 3;
     }
     const float det = h00 * h11 - h01 * h01;
     const float l2 = __fdividef(fmaxf(det, 0.0f), l1);   // smaller eigenvalue without cancellation
@@ -50,21 +63,24 @@ __device__ __forceinline__ void marginal_K(float h00, float h01, float h11, floa
         k00 = (1.0f - s * h11) * (1.0f / 3.0f);
         k11 = (1.0f - s * h00) * (1.0f / 3.0f);
         k01 = (s * h01) * (1.0f / 3.0f);
+        return 1;
     } else {
         // only the major direction exceeds: K = f(l1) (H' - l2 I)/(l1 - l2)
         const float sc = __fdividef(l1 - rho2, 3.0f * l1 * (l1 - l2));
         k00 = sc * (h00 - l2);
         k11 = sc * (h11 - l2);
         k01 = sc * h01;
+        return 2;
     }
 }
 
-// Response of one pair.  r0..r2 = [W row | o_u], r3 = [rgb | sigma_eff], rho2.
-// Returns false when t* <= T_NEAR (pair skipped).
-template <bool FILTER>
+// Response of one pair.  r0..r2 = [W row | o_u], sig = sigma_eff, rho2.
+// Returns false when t* <= T_NEAR (pair skipped).  With STORE the
+// intermediates are copied to *st (the arithmetic is the same either way).
+template <bool FILTER, bool STORE = false>
 __device__ __forceinline__ bool pair_response(const float4 r0, const float4 r1, const float4 r2, const float sig,
                                               const float rho2, const bool additive, const PixelRays &px,
-                                              float &T) {
+                                              float &T, PairFwd *st = nullptr) {
     const float du0 = r0.x * px.d[0] + r0.y * px.d[1] + r0.z * px.d[2];
     const float du1 = r1.x * px.d[0] + r1.y * px.d[1] + r1.z * px.d[2];
     const float du2 = r2.x * px.d[0] + r2.y * px.d[1] + r2.z * px.d[2];
@@ -75,8 +91,14 @@ __device__ __forceinline__ bool pair_response(const float4 r0, const float4 r1, 
     if (!(ts > T_NEAR)) return false;
     const float q0 = r0.w + ts * du0, q1 = r1.w + ts * du1, q2 = r2.w + ts * du2;
     const float qq = q0 * q0 + q1 * q1 + q2 * q2;
+    if (STORE) {
+        st->du[0] = du0; st->du[1] = du1; st->du[2] = du2;
+        st->inv_n = inv_n; st->p = p; st->ts = ts;
+        st->q[0] = q0; st->q[1] = q1; st->q[2] = q2; st->qq = qq;
+    }
     if (!FILTER) {
         T = sig * __expf(-0.5f * qq);
+        if (STORE) st->T = T;
         return true;
     }
     const float gx0 = r0.x * px.dx[0] + r0.y * px.dx[1] + r0.z * px.dx[2];
@@ -100,27 +122,55 @@ __device__ __forceinline__ bool pair_response(const float4 r0, const float4 r1, 
         const float m00 = 1.0f + G00 * (1.0f / 3.0f), m11 = 1.0f + G11 * (1.0f / 3.0f), m01 = G01 * (1.0f / 3.0f);
         det = m00 * m11 - m01 * m01;
         bPb = (b0 * b0 * m11 - 2.0f * b0 * b1 * m01 + b1 * b1 * m00) * (1.0f / 3.0f);
+        if (STORE) {
+            st->kcase = 0;
+            st->k00 = st->k11 = 1.0f / 3.0f; st->k01 = 0.0f;
+            st->m00 = m00; st->m01 = m01; st->m10 = m01; st->m11 = m11;
+            st->p00 = m11 * (1.0f / 3.0f); st->p01 = -m01 * (1.0f / 3.0f);
+            st->p10 = -m01 * (1.0f / 3.0f); st->p11 = m00 * (1.0f / 3.0f);
+        }
     } else {
         const float t2 = ts * ts * (1.0f / 3.0f);
-        const float h00 = t2 * (px.dxdx - 2.0f * cx * px.d_dx + cx * cx);
-        const float h01 = t2 * (px.dxdy - cx * px.d_dy - cy * px.d_dx + cx * cy);
-        const float h11 = t2 * (px.dydy - 2.0f * cy * px.d_dy + cy * cy);
+        const float A00 = px.dxdx - 2.0f * cx * px.d_dx + cx * cx;
+        const float A01 = px.dxdy - cx * px.d_dy - cy * px.d_dx + cx * cy;
+        const float A11 = px.dydy - 2.0f * cy * px.d_dy + cy * cy;
+        const float h00 = t2 * A00, h01 = t2 * A01, h11 = t2 * A11;
         float k00, k01, k11;
-        marginal_K(h00, h01, h11, rho2, k00, k01, k11);
+        const int kc = marginal_K(h00, h01, h11, rho2, k00, k01, k11);
         const float m00 = 1.0f + G00 * k00 + G01 * k01, m01 = G00 * k01 + G01 * k11;
         const float m10 = G01 * k00 + G11 * k01, m11 = 1.0f + G01 * k01 + G11 * k11;
         det = m00 * m11 - m01 * m10;
         const float p00 = k00 * m11 - k01 * m10, p01 = k01 * m00 - k00 * m01;
         const float p10 = k01 * m11 - k11 * m10, p11 = k11 * m00 - k01 * m01;
         bPb = b0 * b0 * p00 + b0 * b1 * (p01 + p10) + b1 * b1 * p11;
+        if (STORE) {
+            st->kcase = kc;
+            st->k00 = k00; st->k01 = k01; st->k11 = k11;
+            st->t2 = t2; st->A00 = A00; st->A01 = A01; st->A11 = A11;
+            st->h00 = h00; st->h01 = h01; st->h11 = h11;
+            st->m00 = m00; st->m01 = m01; st->m10 = m10; st->m11 = m11;
+            st->p00 = p00; st->p01 = p01; st->p10 = p10; st->p11 = p11;
+        }
     }
     // q^T A^-1 q >= |q|^2 / lambda_max(A) >= |q|^2 / det A (A = I + a PSD rank-2
     // matrix), a bound that also guards the FP32 difference against cancellation
     // for far, flat Gaussians seen at grazing angles.
     const float rdet = rsqrtf(det);
     const float inv_det = rdet * rdet;
-    const float Q = fmaxf(qq - bPb * inv_det, qq * inv_det);
+    const float Qa = qq - bPb * inv_det, Qb = qq * inv_det;
+    const float Q = fmaxf(Qa, Qb);
     T = sig * rdet * __expf(-0.5f * Q);
+    if (STORE) {
+        st->gx[0] = gx0; st->gx[1] = gx1; st->gx[2] = gx2;
+        st->gy[0] = gy0; st->gy[1] = gy1; st->gy[2] = gy2;
+        st->cx = cx; st->cy = cy;
+        st->ex[0] = ex0; st->ex[1] = ex1; st->ex[2] = ex2;
+        st->ey[0] = ey0; st->ey[1] = ey1; st->ey[2] = ey2;
+        st->G00 = G00; st->G01 = G01; st->G11 = G11; st->b0 = b0; st->b1 = b1;
+        st->det = det; st->bPb = bPb; st->inv_det = inv_det;
+        st->clamped = !(Qa >= Qb);
+        st->T = T;
+    }
     return true;
 }
 

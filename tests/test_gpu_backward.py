@@ -1,0 +1,102 @@
+"""GPU adjoint (conegs_render_backward) vs the FP64 gradient oracle (oracle/grad.py,
+itself pinned to finite differences of the C oracle).  Loss L = sum w_rgb . rgb +
+w_T . T with seeded weights; pixels the oracle flags as near a compositing
+threshold get zero weight (the render is not differentiable there)."""
+import numpy as np
+import pytest
+
+import synthetic as S
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+REL = 2e-3     # relative error of each gradient group (FP32 adjoint vs FP64 oracle)
+
+
+@pytest.fixture(scope="module")
+def cg():
+    import paper_2609_13397_b300 as cg
+    return cg
+
+
+def _case(name):
+    if name == "pinhole":
+        cam = S.pinhole(40, 30, 36.0, cam_to_world=S.look_at((0.05, 0.0, 0.0), (0.1, 0.05, 4.0)))
+        sc = S.uniform_box_scene(150, seed=2, log_scale_mean=-2.6, log_scale_std=0.4, sh_degree=1)
+    elif name == "floor":
+        cam = S.pinhole(40, 30, 36.0, cam_to_world=S.look_at((0.05, 0.0, 0.0), (0.1, 0.05, 4.0)))
+        sc = S.uniform_box_scene(150, seed=4, log_scale_mean=-3.2, log_scale_std=0.5, sh_degree=2)
+        import oracle
+        sc = sc.with_rho2(oracle.floor_rho2([S.pinhole(160, 120, 144.0)], sc.means).astype(np.float32))
+    elif name == "coarse_floor":       # footprints well above the floor: the marginal rule is active
+        cam = S.pinhole(20, 15, 18.0, cam_to_world=S.look_at((0.0, 0.05, 0.0), (0.0, 0.0, 4.0)))
+        sc = S.uniform_box_scene(150, seed=6, log_scale_mean=-3.0, log_scale_std=0.6, sh_degree=3)
+        import oracle
+        sc = sc.with_rho2(oracle.floor_rho2([S.pinhole(80, 60, 72.0)], sc.means).astype(np.float32))
+    else:                              # fisheye
+        cam = S.c3_camera(48, 48)
+        sc = S.uniform_box_scene(150, seed=5, log_scale_mean=-2.4, log_scale_std=0.4, sh_degree=1)
+    return cam, sc
+
+
+@pytest.mark.parametrize("name,mode", [("pinhole", "aniso"), ("floor", "aniso"), ("coarse_floor", "aniso"),
+                                       ("fisheye", "aniso"), ("pinhole", "filter_none"),
+                                       ("coarse_floor", "additive")])
+def test_backward_matches_gradient_oracle(cg, oracle_lib, name, mode):
+    from oracle import grad as G
+    cam, sc = _case(name)
+    filt = mode != "filter_none"
+    add = mode == "additive"
+    rng = np.random.default_rng(7)
+    P = cam.n_pixels
+    w_rgb = rng.normal(size=(P, 3))
+    w_T = rng.normal(size=P)
+    ref = oracle_lib.render(cam, sc, filter=int(filt), comp=int(add), eps=2e-4)
+    flagged = ref.flags != 0
+    w_rgb[flagged] = 0.0
+    w_T[flagged] = 0.0
+    _, g_ref = G.loss_and_grad(cam, sc, np.arange(P), w_rgb, w_T, filter_on=filt, additive=add)
+
+    ctx = cg.Context(0)
+    ctx.set_scene_from(sc)
+    v = ctx.view()
+    v.set_camera_from(cam)
+    flags = cg.KEEP_FOR_BACKWARD | (0 if filt else cg.FILTER_NONE) | (cg.COMP_ADDITIVE if add else 0)
+    rgb, T = v.render(flags=flags)
+    dL_drgb = torch.from_numpy(w_rgb.T.reshape(3, cam.height, cam.width).astype(np.float32)).cuda()
+    dL_dT = torch.from_numpy(w_T.reshape(cam.height, cam.width).astype(np.float32)).cuda()
+    g = v.render_backward(dL_drgb, dL_dT)
+    torch.cuda.synchronize()
+    pairs = [("means", "means"), ("log_scales", "log_scales"), ("quats", "quats"), ("opacity_logits", "logits"),
+             ("sh", "sh")]
+    for gk, ok in pairs:
+        got = g[gk].cpu().numpy().astype(np.float64).reshape(g_ref[ok].shape)
+        want = g_ref[ok]
+        err = np.linalg.norm(got - want) / max(np.linalg.norm(want), 1e-12)
+        assert err < REL, (gk, err)
+
+
+def test_backward_requires_forward_state(cg):
+    cam, sc = _case("pinhole")
+    ctx = cg.Context(0)
+    ctx.set_scene_from(sc)
+    v = ctx.view()
+    v.set_camera_from(cam)
+    rgb, _ = v.render()                                  # no KEEP_FOR_BACKWARD
+    with pytest.raises(cg.ConegsError) as e:
+        v.render_backward(torch.ones_like(rgb))
+    assert e.value.status == 6
+
+
+def test_backward_accumulates_over_views(cg):
+    cam, sc = _case("pinhole")
+    ctx = cg.Context(0)
+    ctx.set_scene_from(sc)
+    v = ctx.view()
+    v.set_camera_from(cam)
+    rgb, _ = v.render(flags=cg.KEEP_FOR_BACKWARD)
+    g1 = v.render_backward(torch.ones_like(rgb))
+    g2 = v.render_backward(torch.ones_like(rgb), grads={k: t.clone() for k, t in g1.items()})
+    torch.cuda.synchronize()
+    for k in g1:
+        assert torch.allclose(g2[k], 2 * g1[k], rtol=1e-5, atol=1e-7)
