@@ -1,0 +1,193 @@
+"""Serving loop with continuous batching over the C ABI.
+
+The scene stays resident in one conegs context.  Requests (a camera each) are
+queued as they arrive and admitted as soon as a slot is free and the memory
+they need fits the server's budget; each slot owns a view (ray table and
+render scratch) and a CUDA stream, and runs on its own host thread (the C
+calls release the GIL), so requests that arrive while others are on the GPU
+start right away and their kernels overlap on the device.  Every request's
+image is copied to pinned host memory; latency is measured from arrival to
+the end of that copy.
+
+Memory admission: a request's footprint is estimated from its pixel count,
+its tile count and the scene size (ray table 37 B/px, image 16 B/px, tile
+tables, per-Gaussian view records, and a pair-list allowance); a request is
+admitted only while the sum over in-flight requests stays within the budget.
+A render that still exceeds the library's own budget (CONEGS_ERR_BUDGET) is
+re-queued once memory frees up.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import statistics
+import threading
+import time
+from typing import List, Optional
+
+import torch
+
+from . import ConegsError, Context
+
+PER_PIXEL_BYTES = 37 + 16 + 16 + 8          # ray table + image + host staging + per-pixel state
+PER_TILE_BYTES = 24 + 8 + 8                 # tile cone, ranges, counters
+PER_GAUSSIAN_BYTES = 128 + 16 + 8 + 24      # view record, direction/depth, cone, counts/keys
+PAIRS_PER_PIXEL = 12                        # pair-list allowance (8 B + 8 B sort scratch per pair)
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    arrival_s: float
+    camera: object        # anything with model, width, height, intrinsics, k, cam_to_world, theta_lim
+    flags: int = 0
+
+
+@dataclasses.dataclass
+class Result:
+    rid: int
+    width: int
+    height: int
+    rays: int
+    t_arrival: float
+    t_admit: float
+    t_done: float
+    rgb: Optional[torch.Tensor] = None
+    T: Optional[torch.Tensor] = None
+    error: Optional[str] = None
+
+    @property
+    def latency_ms(self) -> float:
+        return 1e3 * (self.t_done - self.t_arrival)
+
+
+def estimate_bytes(cam, n_gaussians: int) -> int:
+    P = cam.width * cam.height
+    tiles = ((cam.width + 7) // 8) * ((cam.height + 7) // 8)
+    return P * PER_PIXEL_BYTES + tiles * PER_TILE_BYTES + n_gaussians * PER_GAUSSIAN_BYTES + \
+        P * PAIRS_PER_PIXEL * 16
+
+
+class Server:
+    def __init__(self, ctx: Context, slots: int = 4, mem_budget_bytes: int = 32 << 30, keep_images: bool = False):
+        self.ctx = ctx
+        self.budget = int(mem_budget_bytes)
+        self.keep_images = keep_images
+        self._slots = [(ctx.view(), torch.cuda.Stream(device=ctx.device)) for _ in range(slots)]
+        self._queue: collections.deque = collections.deque()
+        self._cv = threading.Condition()
+        self._in_use = 0
+        self._closed = False
+        self._t0 = time.perf_counter()
+        self.results: List[Result] = []
+        self._threads = [threading.Thread(target=self._worker, args=(k,), daemon=True) for k in range(slots)]
+        for t in self._threads:
+            t.start()
+
+    def now(self) -> float:
+        return time.perf_counter() - self._t0
+
+    def submit(self, req: Request, t_arrival: Optional[float] = None):
+        with self._cv:
+            self._queue.append((req, self.now() if t_arrival is None else t_arrival))
+            self._cv.notify_all()
+
+    def _admit(self):
+        """Head-of-queue request that fits the memory budget (FIFO)."""
+        if not self._queue:
+            return None
+        req, ta = self._queue[0]
+        need = estimate_bytes(req.camera, self.ctx.n)
+        if self._in_use + need > self.budget and self._in_use > 0:
+            return None
+        self._queue.popleft()
+        self._in_use += need
+        return req, ta, need
+
+    def _worker(self, k: int):
+        view, stream = self._slots[k]
+        torch.cuda.set_device(self.ctx.device)
+        host = {}
+        while True:
+            with self._cv:
+                item = None
+                while not self._closed:
+                    item = self._admit()
+                    if item is not None:
+                        break
+                    self._cv.wait(0.05)
+                if item is None:
+                    return
+            req, ta, need = item
+            t_admit = self.now()
+            cam = req.camera
+            res = Result(req.rid, cam.width, cam.height, 0, ta, t_admit, 0.0)
+            try:
+                key = (cam.height, cam.width)
+                if key not in host:
+                    host.clear()
+                    host[key] = (torch.empty(3, cam.height, cam.width, pin_memory=True),
+                                 torch.empty(cam.height, cam.width, pin_memory=True))
+                h_rgb, h_T = host[key]
+                with torch.cuda.stream(stream):
+                    view.set_camera_from(cam, stream=stream)
+                    view.render_host(h_rgb, h_T, flags=req.flags, stream=stream)
+                res.rays = int(view.stats()["n_valid_pixels"])
+                if self.keep_images:
+                    res.rgb, res.T = h_rgb.clone(), h_T.clone()
+            except ConegsError as e:
+                if e.status == 7:                       # library budget: retry when memory frees up
+                    with self._cv:
+                        self._in_use -= need
+                        self._queue.appendleft((req, ta))
+                        self._cv.notify_all()
+                    time.sleep(0.01)
+                    continue
+                res.error = str(e)
+            res.t_done = self.now()
+            with self._cv:
+                self._in_use -= need
+                self.results.append(res)
+                self._cv.notify_all()
+
+    def drain(self, n_expected: int, timeout_s: float = 600.0):
+        t_end = time.perf_counter() + timeout_s
+        with self._cv:
+            while len(self.results) < n_expected and time.perf_counter() < t_end:
+                self._cv.wait(0.05)
+        return sorted(self.results, key=lambda r: r.rid)
+
+    def close(self):
+        with self._cv:
+            self._closed = True
+            self._cv.notify_all()
+        for t in self._threads:
+            t.join(timeout=30)
+        for view, _ in self._slots:
+            view.close()
+
+    def play(self, requests: List[Request], realtime: bool = True) -> List[Result]:
+        """Submit requests at their arrival times (seconds from now) and wait for all."""
+        start = self.now()
+        for r in requests:
+            if realtime:
+                delay = start + r.arrival_s - self.now()
+                if delay > 0:
+                    time.sleep(delay)
+            self.submit(r, start + r.arrival_s if realtime else None)
+        return self.drain(len(requests))
+
+
+def summarize(results: List[Result]) -> dict:
+    ok = [r for r in results if r.error is None]
+    lat = sorted(r.latency_ms for r in ok)
+    if not lat:
+        return {"requests": len(results), "errors": len(results)}
+    span = max(r.t_done for r in ok) - min(r.t_arrival for r in ok)
+
+    def pct(p):
+        return lat[min(len(lat) - 1, int(round(p / 100.0 * (len(lat) - 1))))]
+
+    return {"requests": len(results), "errors": len(results) - len(ok), "p50_ms": pct(50), "p99_ms": pct(99),
+            "mean_ms": statistics.mean(lat), "rays": sum(r.rays for r in ok),
+            "mrays_per_s": sum(r.rays for r in ok) / span / 1e6 if span > 0 else None, "span_s": span}

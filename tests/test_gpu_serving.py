@@ -1,0 +1,93 @@
+"""Serving with continuous batching: every request's image is the same alone and
+in the mix (bitwise: the computation of a request does not depend on what else
+is in flight), admission respects the memory budget, and a malformed request
+fails alone without stopping the others."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import synthetic as S
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _requests(n, seed=0):
+    base = list(S.c5_requests(n, rate_hz=400.0, seed=seed))
+    out = []
+    for r in base:                                     # keep the test small: cap the resolution
+        c = r.camera
+        scale = min(1.0, 320.0 / max(c.width, c.height))
+        cam = c.scaled(scale) if scale < 1.0 else c
+        out.append(dataclasses.replace(r, camera=cam))
+    return out
+
+
+@pytest.fixture(scope="module")
+def scene_ctx():
+    import paper_2609_13397_b300 as cg
+    sc = S.blob_scene(60000, seed=3, cam=S.c4_rig()[0])
+    ctx = cg.Context(0)
+    ctx.set_scene_from(sc, storage=torch.float16)
+    return ctx
+
+
+def test_alone_equals_mixed(scene_ctx):
+    from paper_2609_13397_b300 import serving
+    from paper_2609_13397_b300.serving import Request
+    reqs = [Request(r.rid, r.arrival_s, r.camera) for r in _requests(24)]
+    alone = serving.Server(scene_ctx, slots=1, keep_images=True)
+    ra = []
+    for r in reqs:                       # one at a time
+        alone.submit(r)
+        ra = alone.drain(len(ra) + 1)
+    alone.close()
+    mixed = serving.Server(scene_ctx, slots=6, keep_images=True)
+    for r in reqs:                       # all at once: they overlap on the device
+        mixed.submit(r)
+    rm = mixed.drain(len(reqs))
+    mixed.close()
+    assert len(ra) == len(rm) == len(reqs)
+    overlap = sum(1 for a in rm for b in rm if a.rid < b.rid and a.t_admit < b.t_done and b.t_admit < a.t_done)
+    assert overlap > 0                   # requests really were in flight together
+    for a, b in zip(ra, rm):
+        assert a.error is None and b.error is None
+        assert torch.equal(a.rgb, b.rgb) and torch.equal(a.T, b.T)
+    stats = serving.summarize(rm)
+    assert stats["p99_ms"] >= stats["p50_ms"] > 0 and stats["rays"] > 0
+
+
+def test_memory_admission_limits_concurrency(scene_ctx):
+    from paper_2609_13397_b300 import serving
+    from paper_2609_13397_b300.serving import Request, estimate_bytes
+    reqs = [Request(r.rid, 0.0, r.camera) for r in _requests(12, seed=1)]
+    biggest = max(estimate_bytes(r.camera, scene_ctx.n) for r in reqs)
+    srv = serving.Server(scene_ctx, slots=6, mem_budget_bytes=int(biggest * 1.5))
+    for r in reqs:
+        srv.submit(r)
+    res = srv.drain(len(reqs))
+    srv.close()
+    assert all(r.error is None for r in res)
+    # no two requests whose estimates exceed the budget together were in flight at once
+    for a in res:
+        for b in res:
+            if a.rid < b.rid and a.t_admit < b.t_done and b.t_admit < a.t_done:
+                ea = estimate_bytes(reqs[a.rid].camera, scene_ctx.n)
+                eb = estimate_bytes(reqs[b.rid].camera, scene_ctx.n)
+                assert ea + eb <= int(biggest * 1.5)
+
+
+def test_malformed_request_fails_alone(scene_ctx):
+    from paper_2609_13397_b300 import serving
+    from paper_2609_13397_b300.serving import Request
+    reqs = [Request(r.rid, 0.0, r.camera) for r in _requests(6, seed=2)]
+    bad = dataclasses.replace(reqs[2].camera, fx=-1.0)
+    reqs[2] = Request(2, 0.0, bad)
+    srv = serving.Server(scene_ctx, slots=3)
+    for r in reqs:
+        srv.submit(r)
+    res = srv.drain(len(reqs))
+    srv.close()
+    assert res[2].error is not None and "ERR_ARG" in res[2].error
+    assert all(r.error is None for k, r in enumerate(res) if k != 2)
