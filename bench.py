@@ -324,6 +324,165 @@ def run_probe(args):
     print("probe ok", args.probe, v.stats()["n_pairs"])
 
 
+def _timed(fn, steps, stream):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def _line(metric_value, ms, args, workload, extra):
+    line = {"metric": METRIC, "value": metric_value, "unit": "Mrays/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": {"workload": workload}}
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+
+
+def run_config(args):
+    """The other benchmark workloads (C1, C3, C4, C5), one JSON line each."""
+    import torch
+    import paper_2609_13397_b300 as cg
+    dev = torch.device("cuda", 0)
+    main_s = torch.cuda.current_stream()
+    if args.config == "c1":
+        cam, sc = S.c1()
+        ctx = cg.Context(0)
+        ctx.set_scene_from(sc)
+        v = ctx.view()
+        v.set_camera_from(cam)
+        out = (torch.empty(3, cam.height, cam.width, device=dev), torch.empty(cam.height, cam.width, device=dev))
+        for _ in range(args.warmup):
+            v.render(out_rgb=out[0], out_T=out[1])
+        ms = _timed(lambda: v.render(out_rgb=out[0], out_T=out[1]), args.steps, main_s)
+        rays = v.stats()["n_valid_pixels"]
+        _line(rays / ms / 1e3, ms, args, "C1: pinhole 64x48 f=60, 1000 Gaussians, FP32", {"rays_per_step": rays})
+        return
+    if args.config == "c3":
+        cam = S.c3_camera()
+        sc = S.c3_scene()
+        tgt = S.perturbed(sc, seed=1)
+        ctx = cg.Context(0)
+        ctx.set_scene_from(tgt)
+        v = ctx.view()
+        v.set_camera_from(cam)
+        target, _ = v.render()
+        target = target.clone()
+        ctx.set_scene_from(sc)
+        valid = v.rays()[3].reshape(cam.height, cam.width).bool()
+        nval = int(valid.sum())
+        out = (torch.empty(3, cam.height, cam.width, device=dev), torch.empty(cam.height, cam.width, device=dev))
+        grads = {k: torch.zeros(t.shape, device=dev) for k, t in ctx._scene_refs.items() if k != "rho2"}
+        grads = {"means": grads["means"], "log_scales": grads["log_scales"], "quats": grads["quats"],
+                 "opacity_logits": grads["opacity_logits"], "sh": grads["sh"]}
+
+        def fwd():
+            v.render(out_rgb=out[0], out_T=out[1])
+
+        def fwd_bwd():
+            v.render(flags=cg.KEEP_FOR_BACKWARD, out_rgb=out[0], out_T=out[1])
+            g = torch.sign(out[0] - target) * valid / (3.0 * nval)      # d/d rgb of the mean L1 loss
+            v.render_backward(g, grads=grads)
+
+        for _ in range(args.warmup):
+            fwd_bwd()
+        ms_f = _timed(fwd, args.steps, main_s)
+        ms_fb = _timed(fwd_bwd, args.steps, main_s)
+        v.render(flags=cg.PROFILE, out_rgb=out[0], out_T=out[1])
+        st = v.stats()
+        _line(nval / ms_f / 1e3, ms_f, args,
+              "C3: KB fisheye 190 deg 1024x1024, k~U(-0.05,0.05), 1M Gaussians; L1 vs perturbed-scene render",
+              {"fwd_bwd": {"value": nval / ms_fb / 1e3, "unit": "Mrays/s", "ms_per_step": ms_fb},
+               "rays_per_step": nval, "pairs": st["n_pairs"],
+               "profile": {k: st[k] for k in ("n_visible", "n_walked", "n_evaluated", "ms_preprocess", "ms_sort",
+                                              "ms_raster", "ms_total")}})
+        return
+    if args.config == "c4":
+        rig = S.c4_rig()
+        sc = S.blob_scene(3_000_000, seed=0, cam=rig[0])
+        ctx = cg.Context(0)
+        ctx.set_scene_from(sc, storage=torch.bfloat16)
+        views = []
+        for c in rig:
+            vv = ctx.view()
+            vv.set_camera_from(c)
+            views.append(vv)
+        rho2 = ctx.compute_floor(views)
+        ctx.set_scene_from(sc, storage=torch.bfloat16, rho2=rho2)
+        streams = [torch.cuda.Stream(device=dev) for _ in views]
+        outs = [(torch.empty(3, c.height, c.width, device=dev), torch.empty(c.height, c.width, device=dev))
+                for c in rig]
+        ones = [torch.full_like(o[0], 1e-3) for o in outs]
+        grads = [{k: torch.zeros(t.shape, device=dev) for k, t in ctx._scene_refs.items() if k != "rho2"}
+                 for _ in views]
+        for gd in grads:
+            gd["opacity_logits"] = gd.pop("opacity_logits")
+        rays = sum(vv.stats()["n_valid_pixels"] for vv in views)
+
+        def step(backward):
+            ev0 = torch.cuda.Event()
+            ev0.record(main_s)
+            for vv, st, (o_rgb, o_T), g1, gd in zip(views, streams, outs, ones, grads):
+                st.wait_event(ev0)
+                vv.render(flags=cg.KEEP_FOR_BACKWARD if backward else 0, out_rgb=o_rgb, out_T=o_T, stream=st)
+                if backward:
+                    vv.render_backward(g1, grads=gd, stream=st)
+            for st in streams:
+                main_s.wait_stream(st)
+
+        for _ in range(args.warmup):
+            step(True)
+        ms_f = _timed(lambda: step(False), args.steps, main_s)
+        ms_fb = _timed(lambda: step(True), args.steps, main_s)
+        prof = []
+        for vv, c, (o_rgb, o_T) in zip(views, rig, outs):
+            vv.render(flags=cg.PROFILE, out_rgb=o_rgb, out_T=o_T)
+            st = vv.stats()
+            prof.append({"camera": f"{'pinhole' if c.model == 0 else 'kb'} {c.width}x{c.height}",
+                         **{k: st[k] for k in ("n_pairs", "n_walked", "n_evaluated", "ms_preprocess", "ms_sort",
+                                               "ms_raster", "ms_total")}})
+        _line(rays / ms_f / 1e3, ms_f, args,
+              "C4: 8 cameras (4 pinhole, 4 KB) at 1,1/2,1/4,1/8 of 1920x1080, 3M Gaussians, Eq.11 floor over the rig, "
+              "SH/opacity BF16", {"fwd_bwd": {"value": rays / ms_fb / 1e3, "unit": "Mrays/s", "ms_per_step": ms_fb},
+                                  "rays_per_step": rays, "dtype_storage": "bf16", "views": prof})
+        return
+    if args.config == "c5":
+        from paper_2609_13397_b300 import serving
+        rig = S.c4_rig()
+        sc = S.blob_scene(args.c5_gaussians, seed=0, cam=rig[0])
+        ctx = cg.Context(0)
+        ctx.set_scene_from(sc, storage=torch.float16)
+        views = []
+        for c in rig:
+            vv = ctx.view()
+            vv.set_camera_from(c)
+            views.append(vv)
+        rho2 = ctx.compute_floor(views)
+        ctx.set_scene_from(sc, storage=torch.float16, rho2=rho2)
+        for vv in views:
+            vv.close()
+        reqs = [serving.Request(r.rid, r.arrival_s, r.camera)
+                for r in S.c5_requests(args.c5_requests, rate_hz=args.c5_rate, seed=0)]
+        srv = serving.Server(ctx, slots=args.c5_slots, mem_budget_bytes=64 << 30)
+        warm = [serving.Request(10_000 + r.rid, 0.0, r.camera) for r in reqs[:2 * args.c5_slots]]
+        for r in warm:
+            srv.submit(r)
+        srv.drain(len(warm))
+        srv.results.clear()
+        res = srv.play(reqs, realtime=True)
+        srv.close()
+        st = serving.summarize(res)
+        _line(st["mrays_per_s"], st["mean_ms"], args,
+              f"C5: serving, {args.c5_gaussians} Gaussians resident, SH3 FP16, Poisson {args.c5_rate} req/s, "
+              f"W=round(160*24^u) H=round(120*18^u), zoom 8^U(-1,1), pinhole/KB 50/50, {args.c5_slots} slots",
+              {"serving": st, "dtype_storage": "f16"})
+        return
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -332,11 +491,20 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--config", choices=["c2", "c1", "c3", "c4", "c5"], default="c2",
+                    help="c2 (default) is the headline workload; the others print their own line")
+    ap.add_argument("--c5-requests", type=int, default=400)
+    ap.add_argument("--c5-rate", type=float, default=200.0)
+    ap.add_argument("--c5-slots", type=int, default=6)
+    ap.add_argument("--c5-gaussians", type=int, default=5_000_000)
     ap.add_argument("--probe", choices=["raster", "raster-1/8", "backward"], default=None,
                     help="set up C2 and render 3 times for a profiler capture (prints no JSON)")
     args = ap.parse_args()
     if args.probe:
         run_probe(args)
+        return
+    if args.config != "c2" and args.impl == "ours":
+        run_config(args)
         return
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", 0))

@@ -635,6 +635,7 @@ conegs_status conegs_get_stats(const conegs_view *v, conegs_stats *out) {
     out->device_bytes = tot;
     if (v->profiled && v->has_forward) {
         CUDA_TRY(cudaEventSynchronize(v->prof[3]));
+        CUDA_TRY(cudaEventSynchronize(v->done));   // the counters are copied after prof[3]
         float t01 = 0, t12 = 0, t23 = 0, t03 = 0;
         CUDA_TRY(cudaEventElapsedTime(&t01, v->prof[0], v->prof[1]));
         CUDA_TRY(cudaEventElapsedTime(&t12, v->prof[1], v->prof[2]));

@@ -226,7 +226,10 @@ __global__ void __launch_bounds__(256) bin_kernel(CamParams c, const float *__re
                 if (tx < c.tiles_x && ty < c.tiles_y) {
                     tile = (uint32_t)(ty * c.tiles_x + tx);
                     const float *tt = table + 6 * (size_t)tile;
-                    tp = cone_prefilter(gv, half, tt) && rule_test(g, gv, tt);
+                    if (cone_prefilter(gv, half, tt)) {
+                        const int f = rule_test_fast(g, gv, tt);
+                        tp = f == 2 ? rule_test(g, gv, tt) : f == 1;
+                    }
                 }
                 const uint32_t tb = __ballot_sync(0xffffffffu, tp);
                 if (MODE == 1 && tp) {

@@ -42,38 +42,47 @@ __global__ void __launch_bounds__(TILE_PX) raster_fwd_kernel(const RasterArgs a)
         }
         __syncthreads();
         const int nb = (int)min((uint32_t)TILE_PX, range.y - start);
+        // phase 1: cone pre-test of every staged entry against this pixel (the
+        // shared-memory reads are broadcasts: all lanes read the same entry)
+        unsigned long long mask = 0ull;
         if (!done) {
+            walked += (uint32_t)nb;
             for (int b = 0; b < nb; ++b) {
-                ++walked;
-                // conservative pre-test: the centre ray misses the Gaussian's bounding
-                // ellipsoid (visual-cone test expanded around u, e = d - u)
-                const float4 r4 = s_rec[4][b];
-                const float4 r5 = s_rec[5][b];
-                const float4 r6 = s_rec[6][b];
+                const float4 r4 = s_rec[4][b], r5 = s_rec[5][b], r6 = s_rec[6][b];
                 const float e0 = px.d[0] - r4.x, e1 = px.d[1] - r4.y, e2 = px.d[2] - r4.z;
                 const float qa = r5.z * e0 + r6.y * e1 + r6.z * e2;
                 const float qb = r5.w * e1 + r6.w * e2;
                 const float cone = -1.0f + r4.w * e0 + r5.x * e1 + r5.y * e2 + qa * e0 + qb * e1 + r6.x * e2 * e2;
-                if (cone > 1e-3f) continue;
+                if (!(cone > 1e-3f)) mask |= 1ull << b;
+            }
+        }
+        // phase 2: each lane walks its own passing entries in depth order, so
+        // the warp's lanes evaluate different entries in lockstep
+        while (__any_sync(0xffffffffu, mask != 0ull)) {
+            if (mask != 0ull) {
+                const int b = __ffsll((long long)mask) - 1;
+                mask &= mask - 1ull;
                 ++full;
                 const float4 r3 = s_rec[3][b];
                 float T;
-                if (!pair_response<FILTER>(s_rec[0][b], s_rec[1][b], s_rec[2][b], r3.w, s_rec[7][b].x,
-                                           a.additive != 0, px, T))
-                    continue;
-                const float alpha = fminf(ALPHA_MAX, T);
-                if (alpha < ALPHA_MIN) continue;
-                const float test = Tacc * (1.0f - alpha);
-                if (test < T_STOP) {
-                    done = true;
-                    break;
+                if (pair_response<FILTER>(s_rec[0][b], s_rec[1][b], s_rec[2][b], r3.w, s_rec[7][b].x,
+                                          a.additive != 0, px, T)) {
+                    const float alpha = fminf(ALPHA_MAX, T);
+                    if (!(alpha < ALPHA_MIN)) {
+                        const float test = Tacc * (1.0f - alpha);
+                        if (test < T_STOP) {
+                            done = true;
+                            mask = 0ull;
+                        } else {
+                            const float w = alpha * Tacc;
+                            C0 += r3.x * w;
+                            C1 += r3.y * w;
+                            C2 += r3.z * w;
+                            Tacc = test;
+                            last = start - range.x + (uint32_t)b + 1u;
+                        }
+                    }
                 }
-                const float w = alpha * Tacc;
-                C0 += r3.x * w;
-                C1 += r3.y * w;
-                C2 += r3.z * w;
-                Tacc = test;
-                last = walked;
             }
         }
         __syncthreads();

@@ -190,4 +190,55 @@ __device__ __forceinline__ bool rule_test(const float *g, const float4 gv, const
 }
 
 
+// The same test evaluated with fast arithmetic (FMA contraction, SFU
+// reciprocal square roots and divisions).  Returns 1 (the exact rule passes),
+// 0 (the exact rule fails) or 2 (too close to a branch or to the final
+// comparison to tell: evaluate rule_test).  The bands are far wider than the
+// fast chain's rounding error (~1e-5 relative once the cancellations at
+// c -> 1 and sin(beta) -> 1 are excluded), so a 0/1 answer is always the
+// exact rule's.
+__device__ __forceinline__ int rule_test_fast(const float *g, const float4 gv, const float *t) {
+    if (t[3] < 0.0f) return 0;
+    if (g[5] == 0.0f) return 0;
+    if (g[5] == 2.0f) return 1;
+    const float L = gv.w, kap = g[0], ks = g[1], kr = g[2], r1sq = g[3], s2 = g[4];
+    const float m = t[5];
+    const float sm = m > 0.0f ? m * rsqrtf(m) : 0.0f;
+    const float cc = kr * sm;
+    if (fabsf(cc - 1.0f) < 1e-2f) return 2;
+    const float rfc = 255.0f * ks;
+    float tb, rf;
+    if (cc < 1.0f) {
+        const float tbf = __fdividef(L + ks, 1.0f - cc);
+        const float x = s2 + tbf * tbf * r1sq * m;
+        const float rff = kap * x * rsqrtf(x);
+        rf = fminf(rff, rfc);
+        tb = fminf(tbf, L + rf);
+    } else {
+        rf = rfc;
+        tb = L + rf;
+    }
+    if (L < rf * (1.0f - 1e-3f)) return 1;
+    if (L <= rf * (1.0f + 1e-3f)) return 2;
+    const float y = s2 + tb * tb * m;
+    const float rp = kap * y * rsqrtf(y);
+    if (rp > L * (1.0f + 1e-3f)) return 1;
+    if (rp >= L * (1.0f - 1e-2f)) return 2;
+    const float sb = __fdividef(rp, L);
+    const float om = 1.0f - sb * sb;
+    const float cb = om * rsqrtf(om);
+    const float sh2 = __fdividef(sb * sb, 2.0f * (1.0f + cb));
+    const float sbh = sh2 * rsqrtf(sh2);
+    const float oh = 1.0f - sh2;
+    const float cbh = oh * rsqrtf(oh);
+    const float sphi = sbh * t[4] + cbh * t[3];
+    const float e0 = gv.x - t[0], e1 = gv.y - t[1], e2 = gv.z - t[2];
+    const float ch2 = e0 * e0 + e1 * e1 + e2 * e2;
+    const float lim = 2.0f * sphi * 1.0001f + 4e-6f;
+    const float l2 = lim * lim;
+    if (ch2 < l2 * (1.0f - 1e-4f) - 1e-12f) return 1;
+    if (ch2 > l2 * (1.0f + 1e-4f) + 1e-12f) return 0;
+    return 2;
+}
+
 }  // namespace conegs
