@@ -47,6 +47,9 @@ cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *alt_keys,
 cudaError_t launch_floor(const CamParams *cams_dev, int nv, const float *means, int64_t n, float *rho2,
                          cudaStream_t s);
 cudaError_t launch_raster_fwd(const RasterArgs &a, int ntiles, bool filter, cudaStream_t s);
+int64_t split_scratch_words(int ntiles, int64_t n_pairs);
+cudaError_t launch_raster_split(const RasterArgs &a, int ntiles, int64_t n_pairs, bool filter, uint32_t *scratch,
+                                uint32_t *scan_scratch, cudaStream_t s);
 cudaError_t launch_backward(const RasterArgs &a, int ntiles, bool filter, const float *dL_drgb, const float *dL_dT,
                             const float *final_T, float *g_rec, cudaStream_t s);
 cudaError_t launch_backward_params(const CamParams &c, const SceneParams &sp, const float *g_rec,
@@ -140,7 +143,7 @@ struct conegs_view {
     // per-render scratch
     DevBuf rec, gview, gcone, gflag, counts, vispos, scan_scr, dkeys, dvals, dkeys_alt, dvals_alt, sorted_counts, offsets;
     DevBuf pair_tile, pair_gid, pair_tile_alt, pair_gid_alt, ranges, last, sums, rs_scr, tmp_rgb, tmp_T;
-    DevBuf g_rec, keep_T;
+    DevBuf g_rec, keep_T, split;
     unsigned long long *h_sums = nullptr;   // pinned
     int64_t n_visible = 0, n_pairs = 0, n_valid = 0, n_launches = 0;
     bool has_forward = false;
@@ -350,7 +353,7 @@ void conegs_view_destroy(conegs_view *v) {
                       &v->counts, &v->vispos, &v->scan_scr, &v->dkeys, &v->dvals, &v->dkeys_alt, &v->dvals_alt,
                       &v->sorted_counts, &v->offsets, &v->pair_tile, &v->pair_gid, &v->pair_tile_alt,
                       &v->pair_gid_alt, &v->ranges, &v->last, &v->sums, &v->rs_scr, &v->tmp_rgb, &v->tmp_T,
-                      &v->g_rec, &v->keep_T};
+                      &v->g_rec, &v->keep_T, &v->split};
     for (DevBuf *b : bufs) release(ctx, *b);
     if (v->h_sums) cudaFreeHost(v->h_sums);
     for (int k = 0; k < 5; ++k)
@@ -521,7 +524,10 @@ static conegs_status render_impl(conegs_view *v, float *out_rgb, float *out_T, u
         a.keep_T = v->keep_T.as<float>();
     }
     a.evaluated = prof ? v->evaluated.as<unsigned long long>() : nullptr;
-    CUDA_TRY(launch_raster_fwd(a, nt, !(flags & CONEGS_FILTER_NONE), s));
+    TRY(ensure(ctx, v->split, sizeof(uint32_t) * (size_t)split_scratch_words(nt, Pn), s));
+    TRY(ensure(ctx, v->scan_scr, sizeof(uint32_t) * (size_t)scan_scratch_words(std::max<int64_t>(std::max<int64_t>(M, n), nt)), s));
+    CUDA_TRY(launch_raster_split(a, nt, Pn, !(flags & CONEGS_FILTER_NONE), v->split.as<uint32_t>(),
+                                 v->scan_scr.as<uint32_t>(), s));
     if (prof) {
         CUDA_TRY(cudaEventRecord(v->prof[3], s));
         CUDA_TRY(cudaMemcpyAsync(v->h_sums + 2, v->evaluated.p, 2 * sizeof(unsigned long long),
@@ -629,7 +635,7 @@ conegs_status conegs_get_stats(const conegs_view *v, conegs_stats *out) {
                             &v->counts, &v->vispos, &v->scan_scr, &v->dkeys, &v->dvals, &v->dkeys_alt, &v->dvals_alt,
                             &v->sorted_counts, &v->offsets, &v->pair_tile, &v->pair_gid, &v->pair_tile_alt,
                             &v->pair_gid_alt, &v->ranges, &v->last, &v->sums, &v->rs_scr, &v->tmp_rgb, &v->tmp_T,
-                            &v->g_rec, &v->keep_T};
+                            &v->g_rec, &v->keep_T, &v->split};
     size_t tot = 0;
     for (const DevBuf *b : bufs) tot += b->bytes;
     out->device_bytes = tot;

@@ -9,9 +9,11 @@
 //   dL/dc_k = a_k T_k dL/dC
 //   dL/da_k = T_k c_k.dL/dC - (S_k.dL/dC + T_fin dL/dT_fin)/(1 - a_k),
 //   S_k = sum_{j>k} c_j a_j T_j (colour behind k)                    (Eq. 4)
-// and da/dT = 1 below the 0.99 clamp.  Per pair the gradient w.r.t. the view
-// record (W_eff 9, o_u 3, sigma_eff, rgb 3) is reduced over the warp and
-// added atomically to a per-Gaussian buffer.
+// and da/dT = 1 below the 0.99 clamp.  As in the forward pass, a broadcast
+// cone pre-test builds each lane's mask of the staged entries it reached,
+// then lanes walk their own passing entries back to front in lockstep; each
+// pair's gradient w.r.t. the view record (W_eff 9, o_u 3, sigma_eff, rgb 3)
+// is added atomically to a per-Gaussian buffer.
 // K7 applies the chain rule from the record to the scene parameters:
 // o_u = W (o - mu), W_ab = R_ba / s_eff,a, s_eff = sqrt(s^2 + rho^2),
 // sigma_eff = sigma prod s/s_eff (Eq. 10), s = exp(log s),
@@ -191,7 +193,6 @@ __global__ void __launch_bounds__(TILE_PX) raster_bwd_kernel(const RasterArgs a,
     const int64_t P = (int64_t)a.W * a.H;
     const bool inside = i < a.W && j < a.H;
     const int64_t pix = (int64_t)j * a.W + i;
-    const int lane = threadIdx.x & 31;
     PixelRays px;
     uint32_t last = 0;
     float T = 1.0f, Tfin = 1.0f, GC[3] = {0.f, 0.f, 0.f}, GT = 0.f, S[3] = {0.f, 0.f, 0.f};
@@ -222,62 +223,55 @@ __global__ void __launch_bounds__(TILE_PX) raster_bwd_kernel(const RasterArgs a,
             for (int k = 0; k < REC_F4; ++k) s_rec[k][threadIdx.x] = r[k];
         }
         __syncthreads();
-        for (int b = (int)nb - 1; b >= 0; --b) {
-            const uint32_t walk = start + b - range.x + 1;     // 1-based walk index of this entry
-            bool active = walk <= last;
-            float gW[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, gou[3] = {0.f, 0.f, 0.f};
-            float gsig = 0.f, grgb[3] = {0.f, 0.f, 0.f};
-            if (active) {
+        // phase 1: broadcast pre-test of the staged entries this pixel reached
+        unsigned long long mask = 0ull;
+        if (last > 0) {
+            for (int b = 0; b < (int)nb; ++b) {
+                const uint32_t walk = start + b - range.x + 1;     // 1-based walk index of this entry
+                if (walk > last) break;
                 const float4 r4 = s_rec[4][b], r5 = s_rec[5][b], r6 = s_rec[6][b];
                 const float e0 = px.d[0] - r4.x, e1 = px.d[1] - r4.y, e2 = px.d[2] - r4.z;
                 const float qa = r5.z * e0 + r6.y * e1 + r6.z * e2;
                 const float qb = r5.w * e1 + r6.w * e2;
                 const float cone = -1.0f + r4.w * e0 + r5.x * e1 + r5.y * e2 + qa * e0 + qb * e1 + r6.x * e2 * e2;
-                active = !(cone > 1e-3f);
+                if (!(cone > 1e-3f)) mask |= 1ull << b;
             }
+        }
+        // phase 2: lanes walk their own passing entries back to front in lockstep
+        while (__any_sync(0xffffffffu, mask != 0ull)) {
+            if (mask == 0ull) continue;
+            const int b = 63 - __clzll((long long)mask);
+            mask &= ~(1ull << b);
             PairFwd f;
             float Tresp = 0.f;
-            if (active) {
-                active = pair_response<FILTER, true>(s_rec[0][b], s_rec[1][b], s_rec[2][b], s_rec[3][b].w,
-                                                     s_rec[7][b].x, a.additive != 0, px, Tresp, &f);
-            }
-            float alpha = 0.f;
-            if (active) {
-                alpha = fminf(ALPHA_MAX, Tresp);
-                active = !(alpha < ALPHA_MIN);
-            }
-            if (active) {
-                const float4 r3 = s_rec[3][b];
-                const float one_m = 1.0f - alpha;
-                const float Tb = T / one_m;                     // transmittance before this pair
-                const float cG = r3.x * GC[0] + r3.y * GC[1] + r3.z * GC[2];
-                const float SG = S[0] * GC[0] + S[1] * GC[1] + S[2] * GC[2];
-                const float galpha = Tb * cG - (SG + GT * Tfin) / one_m;
-                const float w = alpha * Tb;
-                grgb[0] = w * GC[0]; grgb[1] = w * GC[1]; grgb[2] = w * GC[2];
-                S[0] += r3.x * w; S[1] += r3.y * w; S[2] += r3.z * w;
-                T = Tb;
-                const float gT = Tresp < ALPHA_MAX ? galpha : 0.0f;
-                gsig = pair_adjoint<FILTER>(f, s_rec[0][b], s_rec[1][b], s_rec[2][b], r3.w, s_rec[7][b].x, px, gT,
-                                            gW, gou);
-            }
-            // warp reduction, then one thread per warp adds to the Gaussian's buffer
-            const unsigned any = __ballot_sync(0xffffffffu, active);
-            if (any) {
-                float v[16];
+            if (!pair_response<FILTER, true>(s_rec[0][b], s_rec[1][b], s_rec[2][b], s_rec[3][b].w, s_rec[7][b].x,
+                                             a.additive != 0, px, Tresp, &f))
+                continue;
+            const float alpha = fminf(ALPHA_MAX, Tresp);
+            if (alpha < ALPHA_MIN) continue;
+            const float4 r3 = s_rec[3][b];
+            const float one_m = 1.0f - alpha;
+            const float Tb = T / one_m;                     // transmittance before this pair
+            const float cG = r3.x * GC[0] + r3.y * GC[1] + r3.z * GC[2];
+            const float SG = S[0] * GC[0] + S[1] * GC[1] + S[2] * GC[2];
+            const float galpha = Tb * cG - (SG + GT * Tfin) / one_m;
+            const float w = alpha * Tb;
+            float gW[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, gou[3] = {0.f, 0.f, 0.f};
+            S[0] += r3.x * w; S[1] += r3.y * w; S[2] += r3.z * w;
+            T = Tb;
+            const float gT = Tresp < ALPHA_MAX ? galpha : 0.0f;
+            const float gsig = pair_adjoint<FILTER>(f, s_rec[0][b], s_rec[1][b], s_rec[2][b], r3.w, s_rec[7][b].x,
+                                                    px, gT, gW, gou);
+            float *dst = g_rec + 16 * (size_t)s_gid[b];
 #pragma unroll
-                for (int k = 0; k < 9; ++k) v[k] = gW[k];
-                v[9] = gou[0]; v[10] = gou[1]; v[11] = gou[2]; v[12] = gsig;
-                v[13] = grgb[0]; v[14] = grgb[1]; v[15] = grgb[2];
-#pragma unroll
-                for (int k = 0; k < 16; ++k)
-                    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-                if (lane == 0) {
-                    float *dst = g_rec + 16 * (size_t)s_gid[b];
-#pragma unroll
-                    for (int k = 0; k < 16; ++k) atomicAdd(dst + k, v[k]);
-                }
-            }
+            for (int k = 0; k < 9; ++k) atomicAdd(dst + k, gW[k]);
+            atomicAdd(dst + 9, gou[0]);
+            atomicAdd(dst + 10, gou[1]);
+            atomicAdd(dst + 11, gou[2]);
+            atomicAdd(dst + 12, gsig);
+            atomicAdd(dst + 13, w * GC[0]);
+            atomicAdd(dst + 14, w * GC[1]);
+            atomicAdd(dst + 15, w * GC[2]);
         }
         end = start;
     }

@@ -98,5 +98,6 @@ def test_backward_accumulates_over_views(cg):
     g1 = v.render_backward(torch.ones_like(rgb))
     g2 = v.render_backward(torch.ones_like(rgb), grads={k: t.clone() for k, t in g1.items()})
     torch.cuda.synchronize()
-    for k in g1:
-        assert torch.allclose(g2[k], 2 * g1[k], rtol=1e-5, atol=1e-7)
+    for k in g1:   # atomics add in any order: compare at the gradient's own scale
+        scale = float(g1[k].abs().max()) + 1e-12
+        assert float((g2[k] - 2 * g1[k]).abs().max()) <= 1e-5 * scale

@@ -232,3 +232,23 @@ def test_full_size_c2_sampled(cg, oracle_lib):
         sub = rng.choice(sc.n, size=3000, replace=False)
         _, opg, _, _ = oracle_lib.bin_counts(cam, sc.subset(sub))
         assert np.array_equal(pg.cpu().numpy()[sub], opg)
+
+
+def test_split_long_lists_match_oracle(cg, oracle_lib):
+    """A small low-resolution view of a dense scene: every tile list spans many
+    1024-entry segments processed by separate CTAs and merged front to back."""
+    cam = S.pinhole(24, 16, 12.0)
+    sc = S.blob_scene(40000, seed=11, cam=S.pinhole(240, 160, 120.0), n_blobs=4)
+    sc = sc.with_rho2(oracle_lib.floor_rho2([S.pinhole(240, 160, 120.0)], sc.means).astype(np.float32))
+    ctx, v = _setup(cg, cam, sc)
+    rgb, T = v.render(flags=cg.PROFILE)
+    st = v.stats()
+    _, pt = v.bin_counts()
+    assert int(pt.max()) > 4 * 1024                       # lists really span several segments
+    rgb = rgb.cpu().numpy().reshape(3, -1).T
+    T = T.cpu().numpy().reshape(-1)
+    r = oracle_lib.render(cam, sc, eps=EPS_FLAG)
+    ok = r.flags == 0
+    assert ok.mean() > 0.8
+    assert np.abs(rgb - r.rgb)[ok].max() <= TOL and np.abs(T - r.T)[ok].max() <= TOL
+    assert st["n_walked"] > 0
