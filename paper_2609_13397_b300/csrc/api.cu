@@ -46,12 +46,11 @@ cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *alt_keys,
                              int begin_bit, int end_bit, uint32_t *scratch, cudaStream_t s);
 cudaError_t launch_floor(const CamParams *cams_dev, int nv, const float *means, int64_t n, float *rho2,
                          cudaStream_t s);
-cudaError_t launch_raster_fwd(const RasterArgs &a, int ntiles, bool filter, cudaStream_t s);
-int64_t split_scratch_words(int ntiles, int64_t n_pairs);
-cudaError_t launch_raster_split(const RasterArgs &a, int ntiles, int64_t n_pairs, bool filter, uint32_t *scratch,
+cudaError_t launch_raster_split(const RasterArgs &a, int ntiles, bool filter, uint32_t *scratch,
                                 uint32_t *scan_scratch, cudaStream_t s);
-cudaError_t launch_backward(const RasterArgs &a, int ntiles, bool filter, const float *dL_drgb, const float *dL_dT,
-                            const float *final_T, float *g_rec, cudaStream_t s);
+cudaError_t launch_backward(const RasterArgs &a, int ntiles, bool filter, uint32_t *split_scratch,
+                            const float *dL_drgb, const float *dL_dT, const float *final_T, float *g_rec,
+                            cudaStream_t s);
 cudaError_t launch_backward_params(const CamParams &c, const SceneParams &sp, const float *g_rec,
                                    const uint8_t *gflag, const float4 *gview, float *g_means, float *g_log_scales,
                                    float *g_quats, float *g_logits, float *g_sh, cudaStream_t s);
@@ -524,9 +523,9 @@ static conegs_status render_impl(conegs_view *v, float *out_rgb, float *out_T, u
         a.keep_T = v->keep_T.as<float>();
     }
     a.evaluated = prof ? v->evaluated.as<unsigned long long>() : nullptr;
-    TRY(ensure(ctx, v->split, sizeof(uint32_t) * (size_t)split_scratch_words(nt, Pn), s));
+    TRY(ensure(ctx, v->split, sizeof(uint32_t) * (size_t)split_scratch_words(nt), s));
     TRY(ensure(ctx, v->scan_scr, sizeof(uint32_t) * (size_t)scan_scratch_words(std::max<int64_t>(std::max<int64_t>(M, n), nt)), s));
-    CUDA_TRY(launch_raster_split(a, nt, Pn, !(flags & CONEGS_FILTER_NONE), v->split.as<uint32_t>(),
+    CUDA_TRY(launch_raster_split(a, nt, !(flags & CONEGS_FILTER_NONE), v->split.as<uint32_t>(),
                                  v->scan_scr.as<uint32_t>(), s));
     if (prof) {
         CUDA_TRY(cudaEventRecord(v->prof[3], s));
@@ -612,8 +611,8 @@ conegs_status conegs_render_backward(conegs_view *v, const float *dL_drgb, const
     a.valid = v->valid.as<uint8_t>();
     a.last = v->last.as<uint32_t>();
     a.additive = (v->last_flags & CONEGS_COMP_ADDITIVE) ? 1 : 0;
-    CUDA_TRY(launch_backward(a, nt, !(v->last_flags & CONEGS_FILTER_NONE), dL_drgb, dL_dT, v->keep_T.as<float>(),
-                             v->g_rec.as<float>(), s));
+    CUDA_TRY(launch_backward(a, nt, !(v->last_flags & CONEGS_FILTER_NONE), v->split.as<uint32_t>(), dL_drgb, dL_dT,
+                             v->keep_T.as<float>(), v->g_rec.as<float>(), s));
     CUDA_TRY(launch_backward_params(c, ctx->sp, v->g_rec.as<float>(), v->gflag.as<uint8_t>(), v->gview.as<float4>(),
                                     g_means, g_log_scales, g_quats, g_opacity_logits, g_sh, s));
     return view_end(v, s);

@@ -13,7 +13,8 @@
 // cone pre-test builds each lane's mask of the staged entries it reached,
 // then lanes walk their own passing entries back to front in lockstep; each
 // pair's gradient w.r.t. the view record (W_eff 9, o_u 3, sigma_eff, rgb 3)
-// is added atomically to a per-Gaussian buffer.
+// is added to a per-Gaussian buffer with four float4 atomics (lanes of a warp
+// often hold the same entry at once, which rules out shared-memory sums).
 // K7 applies the chain rule from the record to the scene parameters:
 // o_u = W (o - mu), W_ab = R_ba / s_eff,a, s_eff = sqrt(s^2 + rho^2),
 // sigma_eff = sigma prod s/s_eff (Eq. 10), s = exp(log s),
@@ -180,39 +181,73 @@ __device__ __forceinline__ float pair_adjoint(const PairFwd &f, const float4 r0,
     return gsig;
 }
 
-template <bool FILTER>
-__global__ void __launch_bounds__(TILE_PX) raster_bwd_kernel(const RasterArgs a, const float *__restrict__ dL_drgb,
+// One CTA per tile (FIRST: a tile's whole list, or the first segment of a split
+// list) or per later segment of a split list.  A segment is walked back to
+// front from the state the forward's suffix pass left: T after the segment and
+// the colour composited behind it; pixels whose walk ended before the segment
+// sit out.
+template <bool FILTER, bool FIRST>
+__global__ void __launch_bounds__(TILE_PX) raster_bwd_kernel(const RasterArgs a, const SegArgs g,
+                                                             const float *__restrict__ dL_drgb,
                                                              const float *__restrict__ dL_dT,
                                                              const float *__restrict__ final_T,
                                                              float *__restrict__ g_rec) {
     __shared__ float4 s_rec[REC_F4][TILE_PX];
     __shared__ uint32_t s_gid[TILE_PX];
-    const int tile = blockIdx.x;
+    __shared__ uint32_t s_maxlast;
+    uint2 tw;
+    if (FIRST) {
+        tw = make_uint2(blockIdx.x, 0u);
+    } else {
+        if (blockIdx.x >= *g.total) return;
+        tw = g.work[blockIdx.x];
+    }
+    const int tile = (int)tw.x;
+    const uint32_t nseg = g.nseg[tile];
     const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
     const int i = tx * TILE + (threadIdx.x % TILE), j = ty * TILE + (threadIdx.x / TILE);
     const int64_t P = (int64_t)a.W * a.H;
     const bool inside = i < a.W && j < a.H;
     const int64_t pix = (int64_t)j * a.W + i;
+    const uint2 range = a.ranges[tile];
+    uint32_t b0 = range.x, b1 = range.y;
+    if (nseg > 1) {
+        const uint32_t seg = seg_length_dev(g.stat);
+        b0 = range.x + tw.y * seg;
+        b1 = min(range.y, b0 + seg);
+    }
     PixelRays px;
     uint32_t last = 0;
     float T = 1.0f, Tfin = 1.0f, GC[3] = {0.f, 0.f, 0.f}, GT = 0.f, S[3] = {0.f, 0.f, 0.f};
     if (inside && a.valid[pix]) {
-        load_pixel(a, pix, P, px);
-        last = a.last[pix];
-        T = Tfin = final_T[pix];
-        GC[0] = dL_drgb[pix]; GC[1] = dL_drgb[P + pix]; GC[2] = dL_drgb[2 * P + pix];
-        GT = dL_dT ? dL_dT[pix] : 0.0f;
+        bool active = true;
+        Tfin = final_T[pix];
+        T = Tfin;
+        if (nseg > 1) {
+            const size_t q = (size_t)tile * TILE_PX + threadIdx.x;
+            const uint32_t reach = g.rp_end[q];
+            active = reach != NO_STOP && tw.y <= reach;
+            if (active) {
+                const float4 st = g.seg_c[(size_t)(g.seg_off[tile] + tw.y) * TILE_PX + threadIdx.x];
+                S[0] = st.x; S[1] = st.y; S[2] = st.z;
+                T = st.w;
+            }
+        }
+        if (active) {
+            load_pixel(a, pix, P, px);
+            last = a.last[pix];
+            GC[0] = dL_drgb[pix]; GC[1] = dL_drgb[P + pix]; GC[2] = dL_drgb[2 * P + pix];
+            GT = dL_dT ? dL_dT[pix] : 0.0f;
+        }
     }
-    const uint2 range = a.ranges[tile];
     // the CTA only needs the entries up to its pixels' furthest last contributor
-    __shared__ uint32_t s_maxlast;
     if (threadIdx.x == 0) s_maxlast = 0;
     __syncthreads();
     atomicMax(&s_maxlast, last);
     __syncthreads();
-    const uint32_t stop = range.x + s_maxlast;
-    for (uint32_t end = stop; end > range.x;) {
-        const uint32_t start = end - min((uint32_t)TILE_PX, end - range.x);
+    const uint32_t stop = min(b1, range.x + s_maxlast);
+    for (uint32_t end = stop; end > b0;) {
+        const uint32_t start = end - min((uint32_t)TILE_PX, end - b0);
         const uint32_t nb = end - start;
         __syncthreads();
         if (threadIdx.x < nb) {
@@ -262,29 +297,31 @@ __global__ void __launch_bounds__(TILE_PX) raster_bwd_kernel(const RasterArgs a,
             const float gT = Tresp < ALPHA_MAX ? galpha : 0.0f;
             const float gsig = pair_adjoint<FILTER>(f, s_rec[0][b], s_rec[1][b], s_rec[2][b], r3.w, s_rec[7][b].x,
                                                     px, gT, gW, gou);
-            float *dst = g_rec + 16 * (size_t)s_gid[b];
-#pragma unroll
-            for (int k = 0; k < 9; ++k) atomicAdd(dst + k, gW[k]);
-            atomicAdd(dst + 9, gou[0]);
-            atomicAdd(dst + 10, gou[1]);
-            atomicAdd(dst + 11, gou[2]);
-            atomicAdd(dst + 12, gsig);
-            atomicAdd(dst + 13, w * GC[0]);
-            atomicAdd(dst + 14, w * GC[1]);
-            atomicAdd(dst + 15, w * GC[2]);
+            float4 *dst = reinterpret_cast<float4 *>(g_rec + 16 * (size_t)s_gid[b]);   // 64-byte aligned
+            atomicAdd(dst, make_float4(gW[0], gW[1], gW[2], gW[3]));
+            atomicAdd(dst + 1, make_float4(gW[4], gW[5], gW[6], gW[7]));
+            atomicAdd(dst + 2, make_float4(gW[8], gou[0], gou[1], gou[2]));
+            atomicAdd(dst + 3, make_float4(gsig, w * GC[0], w * GC[1], w * GC[2]));
         }
         end = start;
     }
 }
 
-cudaError_t launch_backward(const RasterArgs &a, int ntiles, bool filter, const float *dL_drgb, const float *dL_dT,
-                            const float *final_T, float *g_rec, cudaStream_t s) {
+cudaError_t launch_backward(const RasterArgs &a, int ntiles, bool filter, uint32_t *split_scratch,
+                            const float *dL_drgb, const float *dL_dT, const float *final_T, float *g_rec,
+                            cudaStream_t s) {
     if (ntiles == 0) return cudaSuccess;
-    if (filter)
-        raster_bwd_kernel<true><<<ntiles, TILE_PX, 0, s>>>(a, dL_drgb, dL_dT, final_T, g_rec);
-    else
-        raster_bwd_kernel<false><<<ntiles, TILE_PX, 0, s>>>(a, dL_drgb, dL_dT, final_T, g_rec);
-    note_launches(1);
+    int64_t items = 0;
+    const SegArgs g = split_args(split_scratch, ntiles, &items);
+    const unsigned later = (unsigned)(items - ntiles);
+    if (filter) {
+        raster_bwd_kernel<true, true><<<ntiles, TILE_PX, 0, s>>>(a, g, dL_drgb, dL_dT, final_T, g_rec);
+        raster_bwd_kernel<true, false><<<later, TILE_PX, 0, s>>>(a, g, dL_drgb, dL_dT, final_T, g_rec);
+    } else {
+        raster_bwd_kernel<false, true><<<ntiles, TILE_PX, 0, s>>>(a, g, dL_drgb, dL_dT, final_T, g_rec);
+        raster_bwd_kernel<false, false><<<later, TILE_PX, 0, s>>>(a, g, dL_drgb, dL_dT, final_T, g_rec);
+    }
+    note_launches(2);
     return cudaGetLastError();
 }
 

@@ -2,6 +2,8 @@
 itself pinned to finite differences of the C oracle).  Loss L = sum w_rgb . rgb +
 w_T . T with seeded weights; pixels the oracle flags as near a compositing
 threshold get zero weight (the render is not differentiable there)."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -101,3 +103,48 @@ def test_backward_accumulates_over_views(cg):
     for k in g1:   # atomics add in any order: compare at the gradient's own scale
         scale = float(g1[k].abs().max()) + 1e-12
         assert float((g2[k] - 2 * g1[k]).abs().max()) <= 1e-5 * scale
+
+
+def test_backward_split_lists_match_gradient_oracle(cg, oracle_lib):
+    """Tile lists of a few thousand faint, wide Gaussians: the lists are cut into
+    256-entry segments walked by separate CTAs, and pixels composite hundreds of
+    pairs across segment boundaries before (or without) reaching the stop rule,
+    so the adjoint walks each segment back to front from the per-segment state
+    the forward leaves."""
+    from oracle import grad as G
+    cam = S.pinhole(16, 16, 10.0)
+    sc = S.uniform_box_scene(2500, seed=21, log_scale_mean=-0.3, log_scale_std=0.3, sh_degree=1)
+    rng = np.random.default_rng(22)
+    sc = dataclasses.replace(sc, opacity_logits=rng.normal(-4.0, 0.5, sc.n).astype(np.float32))
+    sc = sc.with_rho2(oracle_lib.floor_rho2([S.pinhole(64, 64, 40.0)], sc.means).astype(np.float32))
+    P = cam.n_pixels
+    ref = oracle_lib.render(cam, sc, eps=3e-5)
+    assert ref.ncontrib.max() > 600                      # walks cross several 256-entry segments
+    assert (ref.T < 2e-4).any() and (ref.T > 2e-4).any()   # some pixels stop, some do not
+    w_rgb = rng.normal(size=(P, 3))
+    w_T = rng.normal(size=P)
+    flagged = ref.flags != 0
+    w_rgb[flagged] = 0.0
+    w_T[flagged] = 0.0
+    assert flagged.mean() < 0.2
+    _, g_ref = G.loss_and_grad(cam, sc, np.arange(P), w_rgb, w_T, chunk=64)
+
+    ctx = cg.Context(0)
+    ctx.set_scene_from(sc)
+    v = ctx.view()
+    v.set_camera_from(cam)
+    rgb, T = v.render(flags=cg.KEEP_FOR_BACKWARD)
+    _, pt = v.bin_counts()
+    assert int(pt.max()) > 4 * 256
+    ok = ~flagged
+    assert np.abs(rgb.cpu().numpy().reshape(3, -1).T - ref.rgb)[ok].max() <= 1e-4
+    assert np.abs(T.cpu().numpy().reshape(-1) - ref.T)[ok].max() <= 1e-4
+    dL_drgb = torch.from_numpy(w_rgb.T.reshape(3, cam.height, cam.width).astype(np.float32)).cuda()
+    dL_dT = torch.from_numpy(w_T.reshape(cam.height, cam.width).astype(np.float32)).cuda()
+    g = v.render_backward(dL_drgb, dL_dT)
+    torch.cuda.synchronize()
+    for gk, ok_ in (("means", "means"), ("log_scales", "log_scales"), ("quats", "quats"),
+                    ("opacity_logits", "logits"), ("sh", "sh")):
+        got = g[gk].cpu().numpy().astype(np.float64).reshape(g_ref[ok_].shape)
+        err = np.linalg.norm(got - g_ref[ok_]) / max(np.linalg.norm(g_ref[ok_]), 1e-12)
+        assert err < REL, (gk, err)
