@@ -24,12 +24,12 @@ cudaError_t launch_ray_table(const CamParams &c, float *d, float *dx, float *dy,
 cudaError_t launch_tile_tables(const CamParams &c, float *table, float *super, float *mcam, cudaStream_t s);
 cudaError_t launch_gauss_scene_rule(const SceneParams &sp, float *binrec, cudaStream_t s);
 cudaError_t launch_bin_count(const CamParams &c, const float *binrec, const float4 *gview, const float2 *gcone,
-                             const uint8_t *gflag, const float *table, const float *super, int64_t n,
-                             uint32_t *counts, cudaStream_t s);
+                             const uint8_t *gflag, const float *table, const float *super, const float *mcam,
+                             int64_t n, uint32_t *counts, uint4 *cache, cudaStream_t s);
 cudaError_t launch_bin_emit(const CamParams &c, const float *binrec, const float4 *gview, const float2 *gcone,
-                            const uint8_t *gflag, const float *table, const float *super, int64_t n_sorted,
-                            const uint32_t *order, const uint32_t *offsets, uint32_t *out_tile, uint32_t *out_gid,
-                            cudaStream_t s);
+                            const uint8_t *gflag, const float *table, const float *super, const float *mcam,
+                            int64_t n_sorted, const uint32_t *order, const uint32_t *offsets, const uint4 *cache,
+                            uint32_t *out_tile, uint32_t *out_gid, cudaStream_t s);
 cudaError_t launch_scene_cache(const SceneParams &sp, float *W, float *sig_eff, cudaStream_t s);
 cudaError_t launch_view_records(const CamParams &c, const SceneParams &sp, const float *mcam, float4 *rec,
                                 float4 *gview, float2 *gcone, uint8_t *gflag, cudaStream_t s);
@@ -138,7 +138,7 @@ struct conegs_view {
     conegs_ctx *ctx = nullptr;
     CamParams cam{};
     bool has_cam = false;
-    DevBuf d, dx, dy, valid, table, super, mcam;
+    DevBuf d, dx, dy, valid, table, super, mcam, bincache;
     // per-render scratch
     DevBuf rec, gview, gcone, gflag, counts, vispos, scan_scr, dkeys, dvals, dkeys_alt, dvals_alt, sorted_counts, offsets;
     DevBuf pair_tile, pair_gid, pair_tile_alt, pair_gid_alt, ranges, last, sums, rs_scr, tmp_rgb, tmp_T;
@@ -222,6 +222,25 @@ float kb_P_host(const float k[4], float th) {
     float t2 = th * th;
     float p = ((k[3] * t2 + k[2]) * t2 + k[1]) * t2 + k[0];
     return th * (1.0f + t2 * p);
+}
+
+// Stretch envelope of the KB projection on the sphere: the image moves by at most
+// max(r'(theta), r(theta)/sin(theta)) per unit of arc (radial and tangential),
+// so lip[j] bounds it on [0, theta_lim j/16] (dense sampling, 1% headroom).
+void kb_lipschitz(const float k[4], float thlim, float lip[17]) {
+    double env = 1.0;
+    lip[0] = 1.01f;
+    for (int j = 1; j <= 16; ++j) {
+        const double a = (double)thlim * (j - 1) / 16, b = (double)thlim * j / 16;
+        for (int i = 0; i <= 2000; ++i) {
+            const double th = a + (b - a) * i / 2000, t2 = th * th;
+            const double r = th * (1 + t2 * (k[0] + t2 * (k[1] + t2 * (k[2] + t2 * k[3]))));
+            const double dr = 1 + t2 * (3 * k[0] + t2 * (5 * k[1] + t2 * (7 * k[2] + t2 * 9 * k[3])));
+            const double tang = th > 1e-9 ? r / std::sin(th) : 1.0;
+            env = std::max(env, std::max(std::fabs(dr), std::fabs(tang)));
+        }
+        lip[j] = (float)(env * 1.01);
+    }
 }
 
 float derive_theta_lim(const float k[4]) {
@@ -348,7 +367,7 @@ void conegs_view_destroy(conegs_view *v) {
         cudaEventSynchronize(v->done);
         cudaEventDestroy(v->done);
     }
-    DevBuf *bufs[] = {&v->d, &v->dx, &v->dy, &v->valid, &v->table, &v->super, &v->mcam, &v->rec, &v->gview, &v->gcone, &v->gflag,
+    DevBuf *bufs[] = {&v->d, &v->dx, &v->dy, &v->valid, &v->table, &v->super, &v->mcam, &v->rec, &v->gview, &v->gcone, &v->gflag, &v->bincache,
                       &v->counts, &v->vispos, &v->scan_scr, &v->dkeys, &v->dvals, &v->dkeys_alt, &v->dvals_alt,
                       &v->sorted_counts, &v->offsets, &v->pair_tile, &v->pair_gid, &v->pair_tile_alt,
                       &v->pair_gid_alt, &v->ranges, &v->last, &v->sums, &v->rs_scr, &v->tmp_rgb, &v->tmp_T,
@@ -405,6 +424,7 @@ conegs_status conegs_set_camera(conegs_view *v, int model, int width, int height
         c.thlim = th;
         float rl = kb_P_host(c.k, th);
         c.rlim2 = rl * rl;
+        kb_lipschitz(c.k, th, c.lip);
     }
     TRY(view_begin(v, s));
     const size_t P = (size_t)width * height;
@@ -415,7 +435,7 @@ conegs_status conegs_set_camera(conegs_view *v, int model, int width, int height
     TRY(ensure(ctx, v->valid, P, s));
     TRY(ensure(ctx, v->table, sizeof(float) * 6 * nt, s));
     TRY(ensure(ctx, v->super, sizeof(float) * 6 * ns, s));
-    TRY(ensure(ctx, v->mcam, sizeof(float), s));
+    TRY(ensure(ctx, v->mcam, 2 * sizeof(float), s));
     TRY(ensure(ctx, v->ranges, sizeof(uint2) * nt, s));
     TRY(ensure(ctx, v->last, sizeof(uint32_t) * P, s));
     CUDA_TRY(launch_ray_table(c, v->d.as<float>(), v->dx.as<float>(), v->dy.as<float>(), v->valid.as<uint8_t>(), s));
@@ -450,6 +470,7 @@ static conegs_status render_impl(conegs_view *v, float *out_rgb, float *out_T, u
     TRY(ensure(ctx, v->gview, sizeof(float4) * nn, s));
     TRY(ensure(ctx, v->gcone, sizeof(float2) * nn, s));
     TRY(ensure(ctx, v->gflag, nn, s));
+    TRY(ensure(ctx, v->bincache, sizeof(uint4) * nn, s));
     TRY(ensure(ctx, v->counts, sizeof(uint32_t) * nn, s));
     TRY(ensure(ctx, v->vispos, sizeof(uint32_t) * nn, s));
     TRY(ensure(ctx, v->scan_scr, sizeof(uint32_t) * (size_t)scan_scratch_words((int64_t)nn), s));
@@ -464,7 +485,8 @@ static conegs_status render_impl(conegs_view *v, float *out_rgb, float *out_T, u
     CUDA_TRY(launch_view_records(c, sp, v->mcam.as<float>(), v->rec.as<float4>(), v->gview.as<float4>(),
                                  v->gcone.as<float2>(), v->gflag.as<uint8_t>(), s));
     CUDA_TRY(launch_bin_count(c, sp.binrec, v->gview.as<float4>(), v->gcone.as<float2>(), v->gflag.as<uint8_t>(),
-                              v->table.as<float>(), v->super.as<float>(), n, v->counts.as<uint32_t>(), s));
+                              v->table.as<float>(), v->super.as<float>(), v->mcam.as<float>(), n,
+                              v->counts.as<uint32_t>(), v->bincache.as<uint4>(), s));
     CUDA_TRY(sum_counts(v->counts.as<uint32_t>(), n, v->sums.as<unsigned long long>(), s));
     CUDA_TRY(exclusive_scan(v->counts.as<uint32_t>(), v->vispos.as<uint32_t>(), n, v->scan_scr.as<uint32_t>(), 1, s));
     if (prof) CUDA_TRY(cudaEventRecord(v->prof[1], s));
@@ -497,8 +519,9 @@ static conegs_status render_impl(conegs_view *v, float *out_rgb, float *out_T, u
     CUDA_TRY(exclusive_scan(v->sorted_counts.as<uint32_t>(), v->offsets.as<uint32_t>(), M, v->scan_scr.as<uint32_t>(),
                             0, s));
     CUDA_TRY(launch_bin_emit(c, sp.binrec, v->gview.as<float4>(), v->gcone.as<float2>(), v->gflag.as<uint8_t>(),
-                             v->table.as<float>(), v->super.as<float>(), M, v->dvals.as<uint32_t>(),
-                             v->offsets.as<uint32_t>(), v->pair_tile.as<uint32_t>(), v->pair_gid.as<uint32_t>(), s));
+                             v->table.as<float>(), v->super.as<float>(), v->mcam.as<float>(), M,
+                             v->dvals.as<uint32_t>(), v->offsets.as<uint32_t>(), v->bincache.as<uint4>(),
+                             v->pair_tile.as<uint32_t>(), v->pair_gid.as<uint32_t>(), s));
     CUDA_TRY(radix_sort_pairs(v->pair_tile.as<uint32_t>(), v->pair_gid.as<uint32_t>(), v->pair_tile_alt.as<uint32_t>(),
                               v->pair_gid_alt.as<uint32_t>(), Pn, 0, bits_for(nt), v->rs_scr.as<uint32_t>(), s));
     CUDA_TRY(launch_ranges(v->pair_tile.as<uint32_t>(), Pn, v->ranges.as<uint2>(), nt, s));
@@ -630,7 +653,7 @@ conegs_status conegs_get_stats(const conegs_view *v, conegs_stats *out) {
     out->tiles_y = v->cam.tiles_y;
     out->n_valid_pixels = v->n_valid;
     out->n_launches = v->n_launches;
-    const DevBuf *bufs[] = {&v->d, &v->dx, &v->dy, &v->valid, &v->table, &v->super, &v->mcam, &v->rec, &v->gview, &v->gcone, &v->gflag,
+    const DevBuf *bufs[] = {&v->d, &v->dx, &v->dy, &v->valid, &v->table, &v->super, &v->mcam, &v->rec, &v->gview, &v->gcone, &v->gflag, &v->bincache,
                             &v->counts, &v->vispos, &v->scan_scr, &v->dkeys, &v->dvals, &v->dkeys_alt, &v->dvals_alt,
                             &v->sorted_counts, &v->offsets, &v->pair_tile, &v->pair_gid, &v->pair_tile_alt,
                             &v->pair_gid_alt, &v->ranges, &v->last, &v->sums, &v->rs_scr, &v->tmp_rgb, &v->tmp_T,

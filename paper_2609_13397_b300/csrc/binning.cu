@@ -121,18 +121,32 @@ __global__ void super_table_kernel(CamParams c, const float *__restrict__ table,
     o[5] = mmax * 1.0001f;
 }
 
-// Camera-wide footprint bound m_cam = max over tiles of m_t (for the
-// rasteriser's per-pixel pre-test).
+// Camera-wide bounds over the tiles: out[0] = max m_t (footprint, for the
+// rasteriser's per-pixel pre-test), out[1] = max sin(gamma_t / 2) (tile cone
+// half-angle, for the binning candidate box).
 __global__ void max_m_kernel(const float *__restrict__ table, int nt, float *__restrict__ out) {
-    float m = 0.0f;
-    for (int t = threadIdx.x; t < nt; t += blockDim.x) m = fmaxf(m, table[6 * (size_t)t + 5]);
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    __shared__ float sm[32];
-    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+    float m = 0.0f, g = 0.0f;
+    for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+        m = fmaxf(m, table[6 * (size_t)t + 5]);
+        g = fmaxf(g, table[6 * (size_t)t + 3]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        g = fmaxf(g, __shfl_xor_sync(0xffffffffu, g, o));
+    }
+    __shared__ float sm[32], sg[32];
+    if ((threadIdx.x & 31) == 0) {
+        sm[threadIdx.x >> 5] = m;
+        sg[threadIdx.x >> 5] = g;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, sm[w]);
-        *out = fmaxf(m, sm[0]);
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            m = fmaxf(m, sm[w]);
+            g = fmaxf(g, sg[w]);
+        }
+        out[0] = fmaxf(m, sm[0]);
+        out[1] = fmaxf(g, sg[0]);
     }
 }
 
@@ -177,22 +191,122 @@ __device__ __forceinline__ bool cone_prefilter(const float4 gv, const float2 hal
     return ch2 <= lim * lim || half.y < 1e-3f;
 }
 
-// One warp per Gaussian.  MODE 0: count tiles into counts[gid].
-// MODE 1: emit tile ids at offsets[pos] for the Gaussian order[pos].
+// Pinhole cameras: the tiles whose centre ray lies within angle beta + gamma_max
+// of the Gaussian's direction u (a superset of what cone_prefilter keeps, with
+// margin) have their centre pixel inside the image of that cone on the plane
+// z = 1 of the camera.  For a cone of half-angle theta around the unit camera-
+// frame axis v (v_z > sin theta) that image is an ellipse; its dual conic is
+// v v^T - sin^2(theta) I, whose tangent lines x = const give
+//   x = (v_x v_z -+ s sqrt(v_x^2 + v_z^2 - s^2)) / (v_z^2 - s^2),  s = sin theta
+// and the same in y.  Returns false (use the super-tile walk) when the cone
+// reaches within about 1 degree of the image plane's horizon.
+__device__ __forceinline__ bool pinhole_tile_box(const CamParams &c, const float4 gv, const float2 half,
+                                                 const float sg_max, int &tx0, int &tx1, int &ty0, int &ty1) {
+    // camera-frame axis: R^T u (R maps camera to world)
+    const float v0 = c.R[0] * gv.x + c.R[3] * gv.y + c.R[6] * gv.z;
+    const float v1 = c.R[1] * gv.x + c.R[4] * gv.y + c.R[7] * gv.z;
+    const float v2 = c.R[2] * gv.x + c.R[5] * gv.y + c.R[8] * gv.z;
+    // sin((beta + gamma_max)/2), widened beyond the prefilter's own margin
+    const float cg = sqrtf(fmaxf(1.0f - sg_max * sg_max, 0.0f));
+    const float sh = fminf((half.x * cg + half.y * sg_max) * 1.002f + 3e-5f, 1.0f);
+    if (!(sh < 0.7f)) return false;                                // theta = 2 asin(sh) must stay below 90 degrees
+    const float s = 2.0f * sh * sqrtf(fmaxf(1.0f - sh * sh, 0.0f));   // sin theta
+    if (!(v2 > s + 0.02f)) return false;
+    const float den = v2 * v2 - s * s;
+    const float rx = s * sqrtf(fmaxf(v0 * v0 + v2 * v2 - s * s, 0.0f));
+    const float ry = s * sqrtf(fmaxf(v1 * v1 + v2 * v2 - s * s, 0.0f));
+    const float inv = 1.0f / den;
+    const float xl = c.fx * ((v0 * v2 - rx) * inv) + c.cx, xh = c.fx * ((v0 * v2 + rx) * inv) + c.cx;
+    const float yl = c.fy * ((v1 * v2 - ry) * inv) + c.cy, yh = c.fy * ((v1 * v2 + ry) * inv) + c.cy;
+    // tile centres sit at TILE t + TILE/2; one tile of slack on each side
+    const float lim = 1e8f;
+    tx0 = max((int)floorf(fmaxf((xl - 0.5f * TILE) / TILE, -lim)), 0);
+    tx1 = min((int)ceilf(fminf((xh - 0.5f * TILE) / TILE, lim)), c.tiles_x - 1);
+    ty0 = max((int)floorf(fmaxf((yl - 0.5f * TILE) / TILE, -lim)), 0);
+    ty1 = min((int)ceilf(fminf((yh - 0.5f * TILE) / TILE, lim)), c.tiles_y - 1);
+    return true;
+}
+
+// Kannala-Brandt cameras: a direction at polar angle theta (from the optical
+// axis) and azimuth a images at normalised radius r(theta) = theta (1 + k1
+// theta^2 + ... + k4 theta^8) (increasing on [0, theta_lim]) and azimuth a, so
+// along any path on the unit sphere the image moves by at most max(r', r /
+// sin theta) per unit of arc.  Every direction within Theta of the axis v is
+// joined to v by an arc of length <= Theta that stays at polar angles <= phi +
+// Theta (phi: the axis's), so its image lies within lip(phi + Theta) Theta of
+// v's image.  A tile centre outside the valid circle has its axis clamped to
+// theta_lim, so cones reaching theta_lim use the super-tile walk instead.
+__device__ __forceinline__ float kb_radius(const CamParams &c, float th) {
+    const float t2 = th * th;
+    return th * (1.0f + t2 * (c.k[0] + t2 * (c.k[1] + t2 * (c.k[2] + t2 * c.k[3]))));
+}
+
+__device__ __forceinline__ bool kb_tile_box(const CamParams &c, const float4 gv, const float2 half,
+                                            const float sg_max, int &tx0, int &tx1, int &ty0, int &ty1) {
+    const float v0 = c.R[0] * gv.x + c.R[3] * gv.y + c.R[6] * gv.z;
+    const float v1 = c.R[1] * gv.x + c.R[4] * gv.y + c.R[7] * gv.z;
+    const float v2 = c.R[2] * gv.x + c.R[5] * gv.y + c.R[8] * gv.z;
+    const float cg = sqrtf(fmaxf(1.0f - sg_max * sg_max, 0.0f));
+    const float sh = fminf((half.x * cg + half.y * sg_max) * 1.002f + 3e-5f, 1.0f);
+    if (!(sh < 0.7f)) return false;
+    const float Th = 2.0f * asinf(sh) + 2e-3f;
+    const float sphi = sqrtf(v0 * v0 + v1 * v1);
+    const float phi = atan2f(sphi, v2);
+    const float thi = phi + Th;
+    if (!(thi < c.thlim - 1e-3f)) return false;
+    const int j = min(16, (int)ceilf(thi / c.thlim * 16.0f + 1e-3f));
+    const float rad = c.lip[j] * Th * 1.001f + 1e-5f;
+    const float sc = sphi > 1e-6f ? kb_radius(c, phi) / sphi : 1.0f;   // r(phi) / sin(phi)
+    const float xn = v0 * sc, yn = v1 * sc;
+    const float lim = 1e8f;
+    const float pxl = c.fx * (xn - rad) + c.cx, pxh = c.fx * (xn + rad) + c.cx;
+    const float pyl = c.fy * (yn - rad) + c.cy, pyh = c.fy * (yn + rad) + c.cy;
+    tx0 = max((int)floorf(fmaxf((pxl - 0.5f * TILE) / TILE, -lim)), 0);
+    tx1 = min((int)ceilf(fminf((pxh - 0.5f * TILE) / TILE, lim)), c.tiles_x - 1);
+    ty0 = max((int)floorf(fmaxf((pyl - 0.5f * TILE) / TILE, -lim)), 0);
+    ty1 = min((int)ceilf(fminf((pyh - 0.5f * TILE) / TILE, lim)), c.tiles_y - 1);
+    return true;
+}
+
+// One warp per Gaussian.  MODE 0: count tiles into counts[gid]; for a Gaussian
+// with a candidate box of at most 64 tiles also cache the box and the 64-bit
+// mask of the candidates that passed (cache[gid]; w = NO_CACHE otherwise).
+// MODE 1: emit tile ids at offsets[pos] for the Gaussian order[pos], from the
+// cached mask when there is one (no rule evaluation), else by the same tests.
+constexpr uint32_t NO_CACHE = 0xffffffffu;
 template <int MODE>
 __global__ void __launch_bounds__(256) bin_kernel(CamParams c, const float *__restrict__ binrec,
                                                   const float4 *__restrict__ gview,
                                                   const float2 *__restrict__ gcone,
                                                   const uint8_t *__restrict__ gflag, const float *__restrict__ table,
-                                                  const float *__restrict__ super, int64_t n,
+                                                  const float *__restrict__ super,
+                                                  const float *__restrict__ mcam, int64_t n,
                                                   const uint32_t *__restrict__ order,
                                                   const uint32_t *__restrict__ offsets,
-                                                  uint32_t *__restrict__ counts, uint32_t *__restrict__ out_tile,
-                                                  uint32_t *__restrict__ out_gid) {
+                                                  uint32_t *__restrict__ counts, uint4 *__restrict__ cache,
+                                                  uint32_t *__restrict__ out_tile, uint32_t *__restrict__ out_gid) {
     const int lane = threadIdx.x & 31;
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (w >= n) return;
     const uint32_t gid = MODE == 0 ? (uint32_t)w : order[w];
+    if (MODE == 1) {
+        const uint4 cc = cache[gid];
+        if (cc.w != NO_CACHE) {
+            const uint32_t base = offsets[w];
+            const unsigned long long m = ((unsigned long long)cc.y << 32) | cc.x;
+            const int tx0 = (int)(cc.z & 0xffffu), ty0 = (int)(cc.z >> 16), bw = (int)(cc.w & 0xffffu);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int k = lane + 32 * h;
+                if ((m >> k) & 1ull) {
+                    const uint32_t pos = base + (uint32_t)__popcll(m & ((1ull << k) - 1ull));
+                    out_tile[pos] = (uint32_t)((ty0 + k / bw) * c.tiles_x + tx0 + k % bw);
+                    out_gid[pos] = gid;
+                }
+            }
+            return;
+        }
+    }
     const uint8_t fl = gflag[gid];
     if (fl == 0) {
         if (MODE == 0 && lane == 0) counts[gid] = 0;
@@ -207,6 +321,42 @@ __global__ void __launch_bounds__(256) bin_kernel(CamParams c, const float *__re
     const int nsup = c.supers_x * c.supers_y;
     uint32_t base = MODE == 1 ? offsets[w] : 0;
     uint32_t cnt = 0;
+    int tx0, tx1, ty0, ty1;
+    if (half.y >= 1e-3f && (c.model == 0 ? pinhole_tile_box(c, gv, half, mcam[1], tx0, tx1, ty0, ty1)
+                                         : kb_tile_box(c, gv, half, mcam[1], tx0, tx1, ty0, ty1))) {
+        // candidate box: every tile in it is tested with the prefilter and the rule
+        const int bw = tx1 - tx0 + 1, bh = ty1 - ty0 + 1;
+        const int nb = (bw > 0 && bh > 0) ? bw * bh : 0;
+        unsigned long long pm = 0ull;
+        for (int k0 = 0; k0 < nb; k0 += 32) {
+            const int k = k0 + lane;
+            bool tp = false;
+            uint32_t tile = 0;
+            if (k < nb) {
+                tile = (uint32_t)((ty0 + k / bw) * c.tiles_x + tx0 + k % bw);
+                const float *tt = table + 6 * (size_t)tile;
+                if (cone_prefilter(gv, half, tt)) {
+                    const int f = rule_test_fast(g, gv, tt);
+                    tp = f == 2 ? rule_test(g, gv, tt) : f == 1;
+                }
+            }
+            const uint32_t tb = __ballot_sync(0xffffffffu, tp);
+            if (MODE == 1 && tp) {
+                const uint32_t pos = base + cnt + __popc(tb & ((1u << lane) - 1u));
+                out_tile[pos] = tile;
+                out_gid[pos] = gid;
+            }
+            if (k0 < 64) pm |= (unsigned long long)tb << k0;
+            cnt += __popc(tb);
+        }
+        if (MODE == 0 && lane == 0) {
+            counts[gid] = cnt;
+            cache[gid] = nb <= 64 ? make_uint4((uint32_t)pm, (uint32_t)(pm >> 32),
+                                               (uint32_t)tx0 | ((uint32_t)ty0 << 16), (uint32_t)bw)
+                                  : make_uint4(0u, 0u, 0u, NO_CACHE);
+        }
+        return;
+    }
     for (int s0 = 0; s0 < nsup; s0 += 32) {
         const int s = s0 + lane;
         bool sp = false;
@@ -241,7 +391,10 @@ __global__ void __launch_bounds__(256) bin_kernel(CamParams c, const float *__re
             }
         }
     }
-    if (MODE == 0 && lane == 0) counts[gid] = cnt;
+    if (MODE == 0 && lane == 0) {
+        counts[gid] = cnt;
+        cache[gid] = make_uint4(0u, 0u, 0u, NO_CACHE);
+    }
 }
 
 // ---------------------------------------------------------------- launchers
@@ -274,23 +427,23 @@ cudaError_t launch_gauss_view_rule(const CamParams &c, const SceneParams &sp, fl
 }
 
 cudaError_t launch_bin_count(const CamParams &c, const float *binrec, const float4 *gview, const float2 *gcone,
-                             const uint8_t *gflag, const float *table, const float *super, int64_t n,
-                             uint32_t *counts, cudaStream_t s) {
+                             const uint8_t *gflag, const float *table, const float *super, const float *mcam,
+                             int64_t n, uint32_t *counts, uint4 *cache, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    bin_kernel<0><<<(unsigned)div_up(n * 32, 256), 256, 0, s>>>(c, binrec, gview, gcone, gflag, table, super, n,
-                                                               nullptr, nullptr, counts, nullptr, nullptr);
+    bin_kernel<0><<<(unsigned)div_up(n * 32, 256), 256, 0, s>>>(c, binrec, gview, gcone, gflag, table, super, mcam, n,
+                                                               nullptr, nullptr, counts, cache, nullptr, nullptr);
     note_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_bin_emit(const CamParams &c, const float *binrec, const float4 *gview, const float2 *gcone,
-                            const uint8_t *gflag, const float *table, const float *super, int64_t n_sorted,
-                            const uint32_t *order, const uint32_t *offsets, uint32_t *out_tile, uint32_t *out_gid,
-                            cudaStream_t s) {
+                            const uint8_t *gflag, const float *table, const float *super, const float *mcam,
+                            int64_t n_sorted, const uint32_t *order, const uint32_t *offsets, const uint4 *cache,
+                            uint32_t *out_tile, uint32_t *out_gid, cudaStream_t s) {
     if (n_sorted == 0) return cudaSuccess;
     bin_kernel<1><<<(unsigned)div_up(n_sorted * 32, 256), 256, 0, s>>>(c, binrec, gview, gcone, gflag, table, super,
-                                                                      n_sorted, order, offsets, nullptr, out_tile,
-                                                                      out_gid);
+                                                                      mcam, n_sorted, order, offsets, nullptr,
+                                                                      const_cast<uint4 *>(cache), out_tile, out_gid);
     note_launches(1);
     return cudaGetLastError();
 }

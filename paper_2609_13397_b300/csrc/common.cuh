@@ -27,6 +27,7 @@ struct CamParams {
     float o[3];       // optical centre
     float thlim;      // KB valid half-FOV (rad)
     float rlim2;      // KB squared normalised radius limit (FP32 rule)
+    float lip[17];    // KB: lip[j] >= max over theta in [0, theta_lim j/16] of max(r'(theta), r(theta)/sin(theta))
 };
 
 // Scene arrays (caller-owned parameters + library cache), passed by value.

@@ -6,7 +6,9 @@
 //   scan      exclusive scan of the 256*G counters (digit-major)
 //   downsweep per 4096-item tile: each warp ranks its 512 items in lane order
 //             with __match_any_sync (stable), warps are offset by a per-digit
-//             scan across warps, items scatter to their global position.
+//             scan across warps; the tile is rearranged in shared memory in
+//             digit order and written out so that runs of one digit land on
+//             consecutive addresses (coalesced stores).
 // Stability of every pass makes the whole sort stable, so equal keys keep
 // their input order (the binning stage relies on it: Gaussians are emitted
 // in depth order and the per-tile lists must keep that order).
@@ -232,9 +234,11 @@ __global__ void __launch_bounds__(RS_THREADS) rs_downsweep(const uint32_t *__res
                                                            uint32_t *__restrict__ vout, int64_t n, int64_t chunk,
                                                            int shift, uint32_t mask,
                                                            const uint32_t *__restrict__ offsets) {
-    __shared__ uint32_t running[256];
-    __shared__ uint32_t wcount[RS_WARPS][256];
-    __shared__ uint32_t wbase[RS_WARPS][256];
+    __shared__ uint32_t running[256];               // global position of the next item of each digit
+    __shared__ uint32_t wcount[RS_WARPS][256];      // per-warp digit counts, then per-warp local bases
+    __shared__ uint32_t gofs[256];                  // global position minus local position, per digit
+    __shared__ uint32_t wsum[RS_WARPS];
+    __shared__ uint32_t s_k[RS_TILE], s_v[RS_TILE];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     running[threadIdx.x] = offsets[(int64_t)threadIdx.x * gridDim.x + blockIdx.x];
 #pragma unroll
@@ -244,13 +248,15 @@ __global__ void __launch_bounds__(RS_THREADS) rs_downsweep(const uint32_t *__res
     const int64_t end = std::min<int64_t>(n, beg + chunk);
     const uint32_t lt = (1u << lane) - 1u;
     for (int64_t t0 = beg; t0 < end; t0 += RS_TILE) {
+        const int tn = (int)std::min<int64_t>(RS_TILE, end - t0);
         uint32_t k[RS_ROUNDS], v[RS_ROUNDS], rank[RS_ROUNDS];
+        // 1. stable rank of each item among the earlier items of its warp with the same digit
 #pragma unroll
         for (int r = 0; r < RS_ROUNDS; ++r) {
-            const int64_t i = t0 + (int64_t)wid * (RS_ROUNDS * 32) + r * 32 + lane;
-            const bool ok = i < end;
-            k[r] = ok ? kin[i] : 0u;
-            v[r] = ok ? vin[i] : 0u;
+            const int li = wid * (RS_ROUNDS * 32) + r * 32 + lane;
+            const bool ok = li < tn;
+            k[r] = ok ? kin[t0 + li] : 0u;
+            v[r] = ok ? vin[t0 + li] : 0u;
             const uint32_t dig = ok ? ((k[r] >> shift) & mask) : (256u + (uint32_t)lane);
             const uint32_t peers = __match_any_sync(0xffffffffu, dig);
             const int leader = __ffs(peers) - 1;
@@ -264,25 +270,53 @@ __global__ void __launch_bounds__(RS_THREADS) rs_downsweep(const uint32_t *__res
             __syncwarp();
         }
         __syncthreads();
+        // 2. digit d (thread d): tile total, exclusive scan over digits -> local bases
+        const int d = threadIdx.x;
+        uint32_t tot = 0;
+#pragma unroll
+        for (int w = 0; w < RS_WARPS; ++w) tot += wcount[w][d];
+        uint32_t x = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[wid] = x;
+        __syncthreads();
+        uint32_t before = 0;
+#pragma unroll
+        for (int w = 0; w < RS_WARPS; ++w) before += w < wid ? wsum[w] : 0u;
+        const uint32_t dbase = before + x - tot;          // first local slot of digit d in this tile
         {
-            const int d = threadIdx.x;
-            uint32_t b = running[d];
+            uint32_t b = dbase;
 #pragma unroll
             for (int w = 0; w < RS_WARPS; ++w) {
-                wbase[w][d] = b;
-                b += wcount[w][d];
-                wcount[w][d] = 0u;
+                const uint32_t c = wcount[w][d];
+                wcount[w][d] = b;                          // now the warp's local base of digit d
+                b += c;
             }
-            running[d] = b;
         }
+        gofs[d] = running[d] - dbase;
+        running[d] += tot;
         __syncthreads();
+        // 3. items to their digit-sorted slot of the tile in shared memory
 #pragma unroll
         for (int r = 0; r < RS_ROUNDS; ++r) {
             if (rank[r] != 0xffffffffu) {
-                const uint32_t dst = wbase[wid][(k[r] >> shift) & mask] + rank[r];
-                kout[dst] = k[r];
-                vout[dst] = v[r];
+                const uint32_t slot = wcount[wid][(k[r] >> shift) & mask] + rank[r];
+                s_k[slot] = k[r];
+                s_v[slot] = v[r];
             }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int w = 0; w < RS_WARPS; ++w) wcount[w][threadIdx.x] = 0u;   // counts of the next tile
+        // 4. write out in slot order: runs of one digit go to consecutive addresses
+        for (int j = threadIdx.x; j < tn; j += RS_THREADS) {
+            const uint32_t kk = s_k[j];
+            const uint32_t dst = gofs[(kk >> shift) & mask] + (uint32_t)j;
+            kout[dst] = kk;
+            vout[dst] = s_v[j];
         }
         __syncthreads();
     }
