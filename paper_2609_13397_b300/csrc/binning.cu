@@ -268,95 +268,31 @@ __device__ __forceinline__ bool kb_tile_box(const CamParams &c, const float4 gv,
     return true;
 }
 
-// One warp per Gaussian.  MODE 0: count tiles into counts[gid]; for a Gaussian
-// with a candidate box of at most 64 tiles also cache the box and the 64-bit
-// mask of the candidates that passed (cache[gid]; w = NO_CACHE otherwise).
-// MODE 1: emit tile ids at offsets[pos] for the Gaussian order[pos], from the
-// cached mask when there is one (no rule evaluation), else by the same tests.
+// Count (MODE 0) and emit (MODE 1) of the (tile, Gaussian) pairs.
+//
+// Each lane prepares one Gaussian (slot): flag, rule record, direction, cone,
+// candidate box.  The warp then walks the concatenation of its 32 slots'
+// candidate tiles 32 at a time, each lane testing one (slot, tile) candidate
+// with the prefilter and the rule, so lanes stay busy whether a Gaussian
+// covers one tile or hundreds.  A slot's passes in an iteration are a
+// contiguous run of the ballot, which its owner lane folds into its count and,
+// for boxes of at most 64 tiles, into a pass mask kept in cache[gid] between
+// the two passes.  MODE 1 (slots = Gaussians in depth order) tests cached
+// candidates by their mask bit instead of the rule and writes pairs at
+// offsets[pos] + rank.  Gaussians without a box (a cone too wide, or reaching
+// a fisheye's rim) take the super-tile walk, one Gaussian per warp.
 constexpr uint32_t NO_CACHE = 0xffffffffu;
+constexpr int BIN_WARPS = 8;
+
+// Super-tile walk for one Gaussian by the whole warp; returns its pair count.
 template <int MODE>
-__global__ void __launch_bounds__(256) bin_kernel(CamParams c, const float *__restrict__ binrec,
-                                                  const float4 *__restrict__ gview,
-                                                  const float2 *__restrict__ gcone,
-                                                  const uint8_t *__restrict__ gflag, const float *__restrict__ table,
-                                                  const float *__restrict__ super,
-                                                  const float *__restrict__ mcam, int64_t n,
-                                                  const uint32_t *__restrict__ order,
-                                                  const uint32_t *__restrict__ offsets,
-                                                  uint32_t *__restrict__ counts, uint4 *__restrict__ cache,
-                                                  uint32_t *__restrict__ out_tile, uint32_t *__restrict__ out_gid) {
+__device__ __forceinline__ uint32_t bin_walk_supers(const CamParams &c, const float *g, const float4 gv,
+                                                    const float2 half, const float *__restrict__ table,
+                                                    const float *__restrict__ super, uint32_t gid, uint32_t base,
+                                                    uint32_t *__restrict__ out_tile, uint32_t *__restrict__ out_gid) {
     const int lane = threadIdx.x & 31;
-    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (w >= n) return;
-    const uint32_t gid = MODE == 0 ? (uint32_t)w : order[w];
-    if (MODE == 1) {
-        const uint4 cc = cache[gid];
-        if (cc.w != NO_CACHE) {
-            const uint32_t base = offsets[w];
-            const unsigned long long m = ((unsigned long long)cc.y << 32) | cc.x;
-            const int tx0 = (int)(cc.z & 0xffffu), ty0 = (int)(cc.z >> 16), bw = (int)(cc.w & 0xffffu);
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int k = lane + 32 * h;
-                if ((m >> k) & 1ull) {
-                    const uint32_t pos = base + (uint32_t)__popcll(m & ((1ull << k) - 1ull));
-                    out_tile[pos] = (uint32_t)((ty0 + k / bw) * c.tiles_x + tx0 + k % bw);
-                    out_gid[pos] = gid;
-                }
-            }
-            return;
-        }
-    }
-    const uint8_t fl = gflag[gid];
-    if (fl == 0) {
-        if (MODE == 0 && lane == 0) counts[gid] = 0;
-        return;
-    }
-    float g[6];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) g[k] = binrec[6 * (size_t)gid + k];
-    g[5] = (float)fl;
-    const float4 gv = gview[gid];
-    const float2 half = gcone[gid];
     const int nsup = c.supers_x * c.supers_y;
-    uint32_t base = MODE == 1 ? offsets[w] : 0;
     uint32_t cnt = 0;
-    int tx0, tx1, ty0, ty1;
-    if (half.y >= 1e-3f && (c.model == 0 ? pinhole_tile_box(c, gv, half, mcam[1], tx0, tx1, ty0, ty1)
-                                         : kb_tile_box(c, gv, half, mcam[1], tx0, tx1, ty0, ty1))) {
-        // candidate box: every tile in it is tested with the prefilter and the rule
-        const int bw = tx1 - tx0 + 1, bh = ty1 - ty0 + 1;
-        const int nb = (bw > 0 && bh > 0) ? bw * bh : 0;
-        unsigned long long pm = 0ull;
-        for (int k0 = 0; k0 < nb; k0 += 32) {
-            const int k = k0 + lane;
-            bool tp = false;
-            uint32_t tile = 0;
-            if (k < nb) {
-                tile = (uint32_t)((ty0 + k / bw) * c.tiles_x + tx0 + k % bw);
-                const float *tt = table + 6 * (size_t)tile;
-                if (cone_prefilter(gv, half, tt)) {
-                    const int f = rule_test_fast(g, gv, tt);
-                    tp = f == 2 ? rule_test(g, gv, tt) : f == 1;
-                }
-            }
-            const uint32_t tb = __ballot_sync(0xffffffffu, tp);
-            if (MODE == 1 && tp) {
-                const uint32_t pos = base + cnt + __popc(tb & ((1u << lane) - 1u));
-                out_tile[pos] = tile;
-                out_gid[pos] = gid;
-            }
-            if (k0 < 64) pm |= (unsigned long long)tb << k0;
-            cnt += __popc(tb);
-        }
-        if (MODE == 0 && lane == 0) {
-            counts[gid] = cnt;
-            cache[gid] = nb <= 64 ? make_uint4((uint32_t)pm, (uint32_t)(pm >> 32),
-                                               (uint32_t)tx0 | ((uint32_t)ty0 << 16), (uint32_t)bw)
-                                  : make_uint4(0u, 0u, 0u, NO_CACHE);
-        }
-        return;
-    }
     for (int s0 = 0; s0 < nsup; s0 += 32) {
         const int s = s0 + lane;
         bool sp = false;
@@ -391,9 +327,252 @@ __global__ void __launch_bounds__(256) bin_kernel(CamParams c, const float *__re
             }
         }
     }
-    if (MODE == 0 && lane == 0) {
+    return cnt;
+}
+
+// Candidate box of one Gaussian walked by the whole warp (boxes too large to
+// gain from packing); returns its pair count.
+template <int MODE>
+__device__ __forceinline__ uint32_t bin_walk_box(const CamParams &c, const float *g, const float4 gv,
+                                                 const float2 half, const float *__restrict__ table, int tx0,
+                                                 int ty0, int bw, uint32_t nb, uint32_t gid, uint32_t base,
+                                                 uint32_t *__restrict__ out_tile, uint32_t *__restrict__ out_gid) {
+    const int lane = threadIdx.x & 31;
+    uint32_t cnt = 0;
+    int qy = 0, qx = lane;                     // candidate k0 + lane = qy * bw + qx
+    while (qx >= bw) {
+        qx -= bw;
+        ++qy;
+    }
+    const int sy = 32 / bw, sx = 32 % bw;      // advance by 32 candidates
+    for (uint32_t k0 = 0; k0 < nb; k0 += 32) {
+        bool tp = false;
+        uint32_t tile = 0;
+        if (k0 + (uint32_t)lane < nb) {
+            tile = (uint32_t)((ty0 + qy) * c.tiles_x + tx0 + qx);
+            const float *tt = table + 6 * (size_t)tile;
+            if (cone_prefilter(gv, half, tt)) {
+                const int f = rule_test_fast(g, gv, tt);
+                tp = f == 2 ? rule_test(g, gv, tt) : f == 1;
+            }
+        }
+        const uint32_t tb = __ballot_sync(0xffffffffu, tp);
+        if (MODE == 1 && tp) {
+            const uint32_t pos = base + cnt + __popc(tb & ((1u << lane) - 1u));
+            out_tile[pos] = tile;
+            out_gid[pos] = gid;
+        }
+        cnt += __popc(tb);
+        qy += sy;
+        qx += sx;
+        if (qx >= bw) {
+            qx -= bw;
+            ++qy;
+        }
+    }
+    return cnt;
+}
+
+// Slots with more candidates than this walk their box with the whole warp.
+constexpr uint32_t PACK_MAX = 96;
+
+template <int MODE>
+__global__ void __launch_bounds__(32 * BIN_WARPS, 3) bin_kernel(CamParams c, const float *__restrict__ binrec,
+                                                             const float4 *__restrict__ gview,
+                                                             const float2 *__restrict__ gcone,
+                                                             const uint8_t *__restrict__ gflag,
+                                                             const float *__restrict__ table,
+                                                             const float *__restrict__ super,
+                                                             const float *__restrict__ mcam, int64_t n,
+                                                             const uint32_t *__restrict__ order,
+                                                             const uint32_t *__restrict__ offsets,
+                                                             uint32_t *__restrict__ counts, uint4 *__restrict__ cache,
+                                                             uint32_t *__restrict__ out_tile,
+                                                             uint32_t *__restrict__ out_gid) {
+    __shared__ float s_g[BIN_WARPS][5][32];        // kap, ks, kr, r1sq, s2 (flag is 1 for boxed slots)
+    __shared__ float4 s_gv[BIN_WARPS][32];
+    __shared__ float2 s_half[BIN_WARPS][32];
+    __shared__ int4 s_box[BIN_WARPS][32];          // tx0, ty0, box width, cached (1) or not
+    __shared__ uint2 s_mask[BIN_WARPS][32];        // MODE 1: cached pass mask
+    __shared__ float s_inv[BIN_WARPS][32];         // 1 / box width
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t pos = ((int64_t)blockIdx.x * BIN_WARPS + wid) * 32 + lane;
+    const bool have = pos < n;
+    const uint32_t gid = have ? (MODE == 0 ? (uint32_t)pos : order[pos]) : 0u;
+    const uint32_t base = (MODE == 1 && have) ? offsets[pos] : 0u;
+    // ---- slot set-up
+    uint32_t nb = 0, fl = 0;
+    bool walk = false, cached = false, big = false;
+    float g[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float4 gv = make_float4(0.f, 0.f, 0.f, 0.f);
+    float2 half = make_float2(0.f, 1.f);
+    int tx0 = 0, tx1 = -1, ty0 = 0, ty1 = -1;
+    if (have) {
+        fl = gflag[gid];
+        if (MODE == 1) {
+            const uint4 cc = cache[gid];
+            if (cc.w != NO_CACHE) {
+                cached = true;
+                tx0 = (int)(cc.z & 0xffffu);
+                ty0 = (int)(cc.z >> 16);
+                const int bw = (int)(cc.w & 0xffffu);
+                nb = (uint32_t)(cc.w >> 16);
+                tx1 = tx0 + bw - 1;
+                s_mask[wid][lane] = make_uint2(cc.x, cc.y);
+            }
+        }
+        if (fl != 0 && !cached) {
+#pragma unroll
+            for (int k = 0; k < 5; ++k) g[k] = binrec[6 * (size_t)gid + k];
+            g[5] = (float)fl;
+            gv = gview[gid];
+            half = gcone[gid];
+            const bool boxed =
+                fl == 1 && half.y >= 1e-3f &&
+                (c.model == 0 ? pinhole_tile_box(c, gv, half, mcam[1], tx0, tx1, ty0, ty1)
+                              : kb_tile_box(c, gv, half, mcam[1], tx0, tx1, ty0, ty1));
+            if (boxed) {
+                const int bw = tx1 - tx0 + 1, bh = ty1 - ty0 + 1;
+                nb = (bw > 0 && bh > 0) ? (uint32_t)(bw * bh) : 0u;
+                big = nb > PACK_MAX;
+            } else {
+                walk = true;                     // pass-all (flag 2) or unbounded cone
+            }
+        }
+    }
+    s_g[wid][0][lane] = g[0]; s_g[wid][1][lane] = g[1]; s_g[wid][2][lane] = g[2];
+    s_g[wid][3][lane] = g[3]; s_g[wid][4][lane] = g[4];
+    s_gv[wid][lane] = gv;
+    s_half[wid][lane] = half;
+    s_box[wid][lane] = make_int4(tx0, ty0, tx1 - tx0 + 1, cached ? 1 : 0);
+    s_inv[wid][lane] = tx1 >= tx0 ? 1.0f / (float)(tx1 - tx0 + 1) : 0.0f;
+    // exclusive prefix of the packed slots' candidate counts (big boxes are walked below)
+    const uint32_t npk = big ? 0u : nb;
+    uint32_t start = npk;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, start, o);
+        if (lane >= o) start += y;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, start, 31);
+    start -= npk;
+    __syncwarp();
+    // ---- packed walk over the candidates of the 32 slots
+    uint32_t cnt = 0;
+    unsigned long long pm = 0ull;
+    for (uint32_t it0 = 0; it0 < total; it0 += 32) {
+        const uint32_t p = it0 + (uint32_t)lane;
+        // owner slot of candidate p: the last lane whose start is <= p (all lanes search)
+        int sl = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const int cand = sl + step;
+            const uint32_t sv = __shfl_sync(0xffffffffu, start, cand & 31);
+            if (cand < 32 && sv <= p) sl = cand;
+        }
+        const uint32_t sstart = __shfl_sync(0xffffffffu, start, sl);
+        bool tp = false;
+        uint32_t tile = 0u;
+        if (p < total) {
+            const uint32_t k = p - sstart;
+            const int4 bx = s_box[wid][sl];
+            // k = ky * width + kx, from a float reciprocal corrected to the exact quotient
+            int ky = (int)((float)k * s_inv[wid][sl]);
+            int kx = (int)k - ky * bx.z;
+            if (kx < 0) {
+                --ky;
+                kx += bx.z;
+            } else if (kx >= bx.z) {
+                ++ky;
+                kx -= bx.z;
+            }
+            tile = (uint32_t)((bx.y + ky) * c.tiles_x + bx.x + kx);
+            if (MODE == 1 && bx.w) {
+                const uint2 m = s_mask[wid][sl];
+                tp = ((k < 32 ? (m.x >> k) : (m.y >> (k - 32))) & 1u) != 0u;
+            } else {
+                const float gg[6] = {s_g[wid][0][sl], s_g[wid][1][sl], s_g[wid][2][sl], s_g[wid][3][sl],
+                                     s_g[wid][4][sl], 1.0f};
+                const float4 sgv = s_gv[wid][sl];
+                const float *tt = table + 6 * (size_t)tile;
+                if (cone_prefilter(sgv, s_half[wid][sl], tt)) {
+                    const int f = rule_test_fast(gg, sgv, tt);
+                    tp = f == 2 ? rule_test(gg, sgv, tt) : f == 1;
+                }
+            }
+        }
+        const uint32_t bal = __ballot_sync(0xffffffffu, tp);
+        // this slot's candidates in the iteration: lanes [lo, hi)
+        const uint32_t lo32 = start > it0 ? start - it0 : 0u;
+        const uint32_t hi32 = start + npk > it0 ? min(start + npk - it0, 32u) : 0u;
+        uint32_t mine = 0u;
+        if (lo32 < hi32) {
+            const uint32_t width = hi32 - lo32;
+            mine = (width == 32u ? bal : (bal >> lo32) & ((1u << width) - 1u));
+        }
+        if (MODE == 1) {
+            // rank among the owner's passing candidates so far (every lane takes part)
+            const uint32_t ocnt = __shfl_sync(0xffffffffu, cnt, sl);
+            const uint32_t obase = __shfl_sync(0xffffffffu, base, sl);
+            const uint32_t olo = __shfl_sync(0xffffffffu, lo32, sl);
+            const uint32_t ogid = __shfl_sync(0xffffffffu, gid, sl);
+            if (tp) {
+                const uint32_t below = bal & ((1u << lane) - 1u) & ~((1u << olo) - 1u);
+                const uint32_t dst = obase + ocnt + (uint32_t)__popc(below);
+                out_tile[dst] = tile;
+                out_gid[dst] = ogid;
+            }
+        }
+        __syncwarp();
+        if (MODE == 0 && nb <= 64u && lo32 < hi32) pm |= (unsigned long long)mine << (it0 + lo32 - start);
+        cnt += (uint32_t)__popc(mine);
+    }
+    // ---- big boxes: one slot at a time by the whole warp
+    uint32_t bb = __ballot_sync(0xffffffffu, big);
+    while (bb) {
+        const int sl = __ffs(bb) - 1;
+        bb &= bb - 1;
+        float gg[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) gg[k] = __shfl_sync(0xffffffffu, g[k], sl);
+        float4 sgv;
+        sgv.x = __shfl_sync(0xffffffffu, gv.x, sl); sgv.y = __shfl_sync(0xffffffffu, gv.y, sl);
+        sgv.z = __shfl_sync(0xffffffffu, gv.z, sl); sgv.w = __shfl_sync(0xffffffffu, gv.w, sl);
+        float2 sh;
+        sh.x = __shfl_sync(0xffffffffu, half.x, sl); sh.y = __shfl_sync(0xffffffffu, half.y, sl);
+        const int btx0 = __shfl_sync(0xffffffffu, tx0, sl), bty0 = __shfl_sync(0xffffffffu, ty0, sl);
+        const int bw = __shfl_sync(0xffffffffu, tx1, sl) - btx0 + 1;
+        const uint32_t bnb = __shfl_sync(0xffffffffu, nb, sl);
+        const uint32_t sgid = __shfl_sync(0xffffffffu, gid, sl);
+        const uint32_t sbase = __shfl_sync(0xffffffffu, base, sl);
+        const uint32_t wc = bin_walk_box<MODE>(c, gg, sgv, sh, table, btx0, bty0, bw, bnb, sgid, sbase, out_tile,
+                                               out_gid);
+        if (lane == sl) cnt = wc;
+    }
+    // ---- slots without a box: the super-tile walk, one slot at a time by the whole warp
+    uint32_t wb = __ballot_sync(0xffffffffu, walk);
+    while (wb) {
+        const int sl = __ffs(wb) - 1;
+        wb &= wb - 1;
+        float gg[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) gg[k] = __shfl_sync(0xffffffffu, g[k], sl);
+        float4 sgv;
+        sgv.x = __shfl_sync(0xffffffffu, gv.x, sl); sgv.y = __shfl_sync(0xffffffffu, gv.y, sl);
+        sgv.z = __shfl_sync(0xffffffffu, gv.z, sl); sgv.w = __shfl_sync(0xffffffffu, gv.w, sl);
+        float2 sh;
+        sh.x = __shfl_sync(0xffffffffu, half.x, sl); sh.y = __shfl_sync(0xffffffffu, half.y, sl);
+        const uint32_t sgid = __shfl_sync(0xffffffffu, gid, sl);
+        const uint32_t sbase = __shfl_sync(0xffffffffu, base, sl);
+        const uint32_t wc = bin_walk_supers<MODE>(c, gg, sgv, sh, table, super, sgid, sbase, out_tile, out_gid);
+        if (lane == sl) cnt = wc;
+    }
+    if (MODE == 0 && have) {
         counts[gid] = cnt;
-        cache[gid] = make_uint4(0u, 0u, 0u, NO_CACHE);
+        cache[gid] = (fl != 0 && !walk && nb <= 64u)
+                         ? make_uint4((uint32_t)pm, (uint32_t)(pm >> 32), (uint32_t)tx0 | ((uint32_t)ty0 << 16),
+                                      (uint32_t)(tx1 - tx0 + 1) | (nb << 16))
+                         : make_uint4(0u, 0u, 0u, NO_CACHE);
     }
 }
 
@@ -430,8 +609,8 @@ cudaError_t launch_bin_count(const CamParams &c, const float *binrec, const floa
                              const uint8_t *gflag, const float *table, const float *super, const float *mcam,
                              int64_t n, uint32_t *counts, uint4 *cache, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    bin_kernel<0><<<(unsigned)div_up(n * 32, 256), 256, 0, s>>>(c, binrec, gview, gcone, gflag, table, super, mcam, n,
-                                                               nullptr, nullptr, counts, cache, nullptr, nullptr);
+    bin_kernel<0><<<(unsigned)div_up(n, 32 * BIN_WARPS), 32 * BIN_WARPS, 0, s>>>(
+        c, binrec, gview, gcone, gflag, table, super, mcam, n, nullptr, nullptr, counts, cache, nullptr, nullptr);
     note_launches(1);
     return cudaGetLastError();
 }
@@ -441,9 +620,9 @@ cudaError_t launch_bin_emit(const CamParams &c, const float *binrec, const float
                             int64_t n_sorted, const uint32_t *order, const uint32_t *offsets, const uint4 *cache,
                             uint32_t *out_tile, uint32_t *out_gid, cudaStream_t s) {
     if (n_sorted == 0) return cudaSuccess;
-    bin_kernel<1><<<(unsigned)div_up(n_sorted * 32, 256), 256, 0, s>>>(c, binrec, gview, gcone, gflag, table, super,
-                                                                      mcam, n_sorted, order, offsets, nullptr,
-                                                                      const_cast<uint4 *>(cache), out_tile, out_gid);
+    bin_kernel<1><<<(unsigned)div_up(n_sorted, 32 * BIN_WARPS), 32 * BIN_WARPS, 0, s>>>(
+        c, binrec, gview, gcone, gflag, table, super, mcam, n_sorted, order, offsets, nullptr,
+        const_cast<uint4 *>(cache), out_tile, out_gid);
     note_launches(1);
     return cudaGetLastError();
 }
