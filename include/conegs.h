@@ -100,6 +100,7 @@ typedef struct {
     float ms_sort;           /* compaction + depth sort + emit + tile sort + ranges */
     float ms_raster;         /* tile rasteriser */
     float ms_total;          /* whole render on the device */
+    float ms_raster_main;    /* of ms_raster: the launch that walks every tile's first list segment */
 } conegs_stats;
 
 /* Create a context on CUDA device `device` (its scene and views live there).

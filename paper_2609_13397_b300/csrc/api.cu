@@ -25,11 +25,12 @@ cudaError_t launch_tile_tables(const CamParams &c, float *table, float *super, f
 cudaError_t launch_gauss_scene_rule(const SceneParams &sp, float *binrec, cudaStream_t s);
 cudaError_t launch_bin_count(const CamParams &c, const float *binrec, const float4 *gview, const float2 *gcone,
                              const uint8_t *gflag, const float *table, const float *super, const float *mcam,
-                             int64_t n, uint32_t *counts, uint4 *cache, cudaStream_t s);
+                             int64_t n, uint32_t *counts, uint4 *cache, uint32_t *blist,
+                             unsigned long long *bcursor, unsigned long long bcap, cudaStream_t s);
 cudaError_t launch_bin_emit(const CamParams &c, const float *binrec, const float4 *gview, const float2 *gcone,
                             const uint8_t *gflag, const float *table, const float *super, const float *mcam,
                             int64_t n_sorted, const uint32_t *order, const uint32_t *offsets, const uint4 *cache,
-                            uint32_t *out_tile, uint32_t *out_gid, cudaStream_t s);
+                            const uint32_t *blist, uint32_t *out_tile, uint32_t *out_gid, cudaStream_t s);
 cudaError_t launch_scene_cache(const SceneParams &sp, float *W, float *sig_eff, cudaStream_t s);
 cudaError_t launch_view_records(const CamParams &c, const SceneParams &sp, const float *mcam, float4 *rec,
                                 float4 *gview, float2 *gcone, uint8_t *gflag, cudaStream_t s);
@@ -47,7 +48,7 @@ cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *alt_keys,
 cudaError_t launch_floor(const CamParams *cams_dev, int nv, const float *means, int64_t n, float *rho2,
                          cudaStream_t s);
 cudaError_t launch_raster_split(const RasterArgs &a, int ntiles, bool filter, uint32_t *scratch,
-                                uint32_t *scan_scratch, cudaStream_t s);
+                                uint32_t *scan_scratch, cudaStream_t s, cudaEvent_t main0, cudaEvent_t main1);
 cudaError_t launch_backward(const RasterArgs &a, int ntiles, bool filter, uint32_t *split_scratch,
                             const float *dL_drgb, const float *dL_dT, const float *final_T, float *g_rec,
                             cudaStream_t s);
@@ -138,7 +139,8 @@ struct conegs_view {
     conegs_ctx *ctx = nullptr;
     CamParams cam{};
     bool has_cam = false;
-    DevBuf d, dx, dy, valid, table, super, mcam, bincache;
+    DevBuf d, dx, dy, valid, table, super, mcam, bincache, binlist;
+    uint64_t list_want = 0;   // tile ids the last count pass wanted to keep in binlist
     // per-render scratch
     DevBuf rec, gview, gcone, gflag, counts, vispos, scan_scr, dkeys, dvals, dkeys_alt, dvals_alt, sorted_counts, offsets;
     DevBuf pair_tile, pair_gid, pair_tile_alt, pair_gid_alt, ranges, last, sums, rs_scr, tmp_rgb, tmp_T;
@@ -149,7 +151,7 @@ struct conegs_view {
     unsigned last_flags = 0;
     uint64_t forward_gen = 0;
     cudaEvent_t done = nullptr;
-    cudaEvent_t prof[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t prof[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     bool profiled = false;
     DevBuf evaluated;
     cudaStream_t last_stream = nullptr;
@@ -344,7 +346,7 @@ conegs_status conegs_view_create(conegs_ctx *ctx, conegs_view **out) {
     auto *v = new conegs_view();
     v->ctx = ctx;
     cudaError_t e = cudaEventCreateWithFlags(&v->done, cudaEventDisableTiming);
-    for (int k = 0; k < 5 && e == cudaSuccess; ++k) e = cudaEventCreate(&v->prof[k]);
+    for (int k = 0; k < 6 && e == cudaSuccess; ++k) e = cudaEventCreate(&v->prof[k]);
     if (e == cudaSuccess) e = cudaMallocHost(&v->h_sums, 4 * sizeof(unsigned long long));
     if (e != cudaSuccess) {
         if (v->done) cudaEventDestroy(v->done);
@@ -367,14 +369,14 @@ void conegs_view_destroy(conegs_view *v) {
         cudaEventSynchronize(v->done);
         cudaEventDestroy(v->done);
     }
-    DevBuf *bufs[] = {&v->d, &v->dx, &v->dy, &v->valid, &v->table, &v->super, &v->mcam, &v->rec, &v->gview, &v->gcone, &v->gflag, &v->bincache,
+    DevBuf *bufs[] = {&v->d, &v->dx, &v->dy, &v->valid, &v->table, &v->super, &v->mcam, &v->rec, &v->gview, &v->gcone, &v->gflag, &v->bincache, &v->binlist,
                       &v->counts, &v->vispos, &v->scan_scr, &v->dkeys, &v->dvals, &v->dkeys_alt, &v->dvals_alt,
                       &v->sorted_counts, &v->offsets, &v->pair_tile, &v->pair_gid, &v->pair_tile_alt,
                       &v->pair_gid_alt, &v->ranges, &v->last, &v->sums, &v->rs_scr, &v->tmp_rgb, &v->tmp_T,
                       &v->g_rec, &v->keep_T, &v->split};
     for (DevBuf *b : bufs) release(ctx, *b);
     if (v->h_sums) cudaFreeHost(v->h_sums);
-    for (int k = 0; k < 5; ++k)
+    for (int k = 0; k < 6; ++k)
         if (v->prof[k]) cudaEventDestroy(v->prof[k]);
     release(ctx, v->evaluated);
     {
@@ -470,11 +472,14 @@ static conegs_status render_impl(conegs_view *v, float *out_rgb, float *out_T, u
     TRY(ensure(ctx, v->gview, sizeof(float4) * nn, s));
     TRY(ensure(ctx, v->gcone, sizeof(float2) * nn, s));
     TRY(ensure(ctx, v->gflag, nn, s));
-    TRY(ensure(ctx, v->bincache, sizeof(uint4) * nn, s));
+    TRY(ensure(ctx, v->bincache, 3 * sizeof(uint4) * nn, s));
     TRY(ensure(ctx, v->counts, sizeof(uint32_t) * nn, s));
     TRY(ensure(ctx, v->vispos, sizeof(uint32_t) * nn, s));
     TRY(ensure(ctx, v->scan_scr, sizeof(uint32_t) * (size_t)scan_scratch_words((int64_t)nn), s));
-    TRY(ensure(ctx, v->sums, 2 * sizeof(unsigned long long), s));
+    TRY(ensure(ctx, v->sums, 3 * sizeof(unsigned long long), s));
+    // optional: without room (or over the memory budget) the emit pass evaluates the rule again
+    if (v->list_want > 0 && ensure(ctx, v->binlist, sizeof(uint32_t) * (size_t)v->list_want, s) != CONEGS_OK)
+        v->list_want = 0;
     SceneParams sp = ctx->sp;
     const bool prof = (flags & CONEGS_PROFILE) != 0;
     if (prof) {
@@ -484,16 +489,24 @@ static conegs_status render_impl(conegs_view *v, float *out_rgb, float *out_T, u
     }
     CUDA_TRY(launch_view_records(c, sp, v->mcam.as<float>(), v->rec.as<float4>(), v->gview.as<float4>(),
                                  v->gcone.as<float2>(), v->gflag.as<uint8_t>(), s));
-    CUDA_TRY(launch_bin_count(c, sp.binrec, v->gview.as<float4>(), v->gcone.as<float2>(), v->gflag.as<uint8_t>(),
-                              v->table.as<float>(), v->super.as<float>(), v->mcam.as<float>(), n,
-                              v->counts.as<uint32_t>(), v->bincache.as<uint4>(), s));
+    CUDA_TRY(cudaMemsetAsync(v->sums.as<unsigned long long>() + 2, 0, sizeof(unsigned long long), s));
+    {
+        const unsigned long long cap = std::min<unsigned long long>(v->binlist.bytes / sizeof(uint32_t), 0xffffffffull);
+        CUDA_TRY(launch_bin_count(c, sp.binrec, v->gview.as<float4>(), v->gcone.as<float2>(), v->gflag.as<uint8_t>(),
+                                  v->table.as<float>(), v->super.as<float>(), v->mcam.as<float>(), n,
+                                  v->counts.as<uint32_t>(), v->bincache.as<uint4>(), v->binlist.as<uint32_t>(),
+                                  v->sums.as<unsigned long long>() + 2, cap, s));
+    }
     CUDA_TRY(sum_counts(v->counts.as<uint32_t>(), n, v->sums.as<unsigned long long>(), s));
     CUDA_TRY(exclusive_scan(v->counts.as<uint32_t>(), v->vispos.as<uint32_t>(), n, v->scan_scr.as<uint32_t>(), 1, s));
     if (prof) CUDA_TRY(cudaEventRecord(v->prof[1], s));
-    CUDA_TRY(cudaMemcpyAsync(v->h_sums, v->sums.p, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(v->h_sums, v->sums.p, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     const uint64_t total = v->h_sums[0];
     const int64_t M = (int64_t)v->h_sums[1];
+    // room the count pass wanted for kept tile lists: grown (with headroom) before the next render
+    if (v->h_sums[2] > v->binlist.bytes / sizeof(uint32_t))
+        v->list_want = std::min<uint64_t>(v->h_sums[2] + v->h_sums[2] / 4, 1ull << 28);
     if (total >= (1ULL << 31)) return fail(CONEGS_ERR_OVERFLOW, "render: %llu tile/Gaussian pairs exceed 2^31",
                                            (unsigned long long)total);
     const int64_t Pn = (int64_t)total;
@@ -521,7 +534,7 @@ static conegs_status render_impl(conegs_view *v, float *out_rgb, float *out_T, u
     CUDA_TRY(launch_bin_emit(c, sp.binrec, v->gview.as<float4>(), v->gcone.as<float2>(), v->gflag.as<uint8_t>(),
                              v->table.as<float>(), v->super.as<float>(), v->mcam.as<float>(), M,
                              v->dvals.as<uint32_t>(), v->offsets.as<uint32_t>(), v->bincache.as<uint4>(),
-                             v->pair_tile.as<uint32_t>(), v->pair_gid.as<uint32_t>(), s));
+                             v->binlist.as<uint32_t>(), v->pair_tile.as<uint32_t>(), v->pair_gid.as<uint32_t>(), s));
     CUDA_TRY(radix_sort_pairs(v->pair_tile.as<uint32_t>(), v->pair_gid.as<uint32_t>(), v->pair_tile_alt.as<uint32_t>(),
                               v->pair_gid_alt.as<uint32_t>(), Pn, 0, bits_for(nt), v->rs_scr.as<uint32_t>(), s));
     CUDA_TRY(launch_ranges(v->pair_tile.as<uint32_t>(), Pn, v->ranges.as<uint2>(), nt, s));
@@ -549,7 +562,8 @@ static conegs_status render_impl(conegs_view *v, float *out_rgb, float *out_T, u
     TRY(ensure(ctx, v->split, sizeof(uint32_t) * (size_t)split_scratch_words(nt), s));
     TRY(ensure(ctx, v->scan_scr, sizeof(uint32_t) * (size_t)scan_scratch_words(std::max<int64_t>(std::max<int64_t>(M, n), nt)), s));
     CUDA_TRY(launch_raster_split(a, nt, !(flags & CONEGS_FILTER_NONE), v->split.as<uint32_t>(),
-                                 v->scan_scr.as<uint32_t>(), s));
+                                 v->scan_scr.as<uint32_t>(), s,
+                                 prof ? v->prof[4] : nullptr, prof ? v->prof[5] : nullptr));
     if (prof) {
         CUDA_TRY(cudaEventRecord(v->prof[3], s));
         CUDA_TRY(cudaMemcpyAsync(v->h_sums + 2, v->evaluated.p, 2 * sizeof(unsigned long long),
@@ -653,7 +667,7 @@ conegs_status conegs_get_stats(const conegs_view *v, conegs_stats *out) {
     out->tiles_y = v->cam.tiles_y;
     out->n_valid_pixels = v->n_valid;
     out->n_launches = v->n_launches;
-    const DevBuf *bufs[] = {&v->d, &v->dx, &v->dy, &v->valid, &v->table, &v->super, &v->mcam, &v->rec, &v->gview, &v->gcone, &v->gflag, &v->bincache,
+    const DevBuf *bufs[] = {&v->d, &v->dx, &v->dy, &v->valid, &v->table, &v->super, &v->mcam, &v->rec, &v->gview, &v->gcone, &v->gflag, &v->bincache, &v->binlist,
                             &v->counts, &v->vispos, &v->scan_scr, &v->dkeys, &v->dvals, &v->dkeys_alt, &v->dvals_alt,
                             &v->sorted_counts, &v->offsets, &v->pair_tile, &v->pair_gid, &v->pair_tile_alt,
                             &v->pair_gid_alt, &v->ranges, &v->last, &v->sums, &v->rs_scr, &v->tmp_rgb, &v->tmp_T,
@@ -673,6 +687,9 @@ conegs_status conegs_get_stats(const conegs_view *v, conegs_stats *out) {
         out->ms_sort = t12;
         out->ms_raster = t23;
         out->ms_total = t03;
+        float t45 = 0;
+        CUDA_TRY(cudaEventElapsedTime(&t45, v->prof[4], v->prof[5]));
+        out->ms_raster_main = t45;
         out->n_walked = (int64_t)v->h_sums[2];
         out->n_evaluated = (int64_t)v->h_sums[3];
     }

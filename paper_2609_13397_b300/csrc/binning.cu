@@ -276,13 +276,30 @@ __device__ __forceinline__ bool kb_tile_box(const CamParams &c, const float4 gv,
 // with the prefilter and the rule, so lanes stay busy whether a Gaussian
 // covers one tile or hundreds.  A slot's passes in an iteration are a
 // contiguous run of the ballot, which its owner lane folds into its count and,
-// for boxes of at most 64 tiles, into a pass mask kept in cache[gid] between
-// the two passes.  MODE 1 (slots = Gaussians in depth order) tests cached
-// candidates by their mask bit instead of the rule and writes pairs at
-// offsets[pos] + rank.  Gaussians without a box (a cone too wide, or reaching
-// a fisheye's rim) take the super-tile walk, one Gaussian per warp.
+// for boxes of at most 256 tiles, into a 256-bit pass mask kept in the cache
+// (3 uint4 per Gaussian: box, mask) between the two passes.  MODE 1 (slots =
+// Gaussians in depth order) expands a cached slot's set bits only (no rule
+// evaluation) and writes pairs at offsets[pos] + rank.  Boxes over PACK_MAX
+// tiles walk their box with the whole warp; those over MASK_MAX tiles reserve
+// box-size room in a list buffer (atomic cursor; when it is full the emit pass
+// evaluates the rule again) and the count pass writes their passing tile ids
+// there, which the emit pass copies.  Gaussians without a box (a cone too
+// wide, or reaching a fisheye's rim) take the super-tile walk.
 constexpr uint32_t NO_CACHE = 0xffffffffu;
 constexpr int BIN_WARPS = 8;
+constexpr uint32_t PACK_MAX = 96;      // slots with more candidates walk their box with the whole warp
+constexpr uint32_t MASK_MAX = 256;     // boxes up to this many tiles keep their pass mask
+constexpr uint32_t CACHE_MASK = 0u, CACHE_LIST = 1u;   // cache header .w (NO_CACHE: nothing kept)
+
+// OR a 32-bit chunk of pass bits into the 256-bit mask m at bit offset at.
+__device__ __forceinline__ void mask_or(uint32_t m[8], uint32_t bits, uint32_t at) {
+    const uint32_t wi = at >> 5, sh = at & 31u;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        if ((uint32_t)q == wi) m[q] |= bits << sh;
+        if (sh != 0u && (uint32_t)q == wi + 1u) m[q] |= bits >> (32u - sh);
+    }
+}
 
 // Super-tile walk for one Gaussian by the whole warp; returns its pair count.
 template <int MODE>
@@ -330,12 +347,13 @@ __device__ __forceinline__ uint32_t bin_walk_supers(const CamParams &c, const fl
     return cnt;
 }
 
-// Candidate box of one Gaussian walked by the whole warp (boxes too large to
-// gain from packing); returns its pair count.
+// Candidate box of one Gaussian walked by the whole warp; returns its pair count
+// and (boxes of at most MASK_MAX tiles) its pass mask in m (same on every lane).
 template <int MODE>
 __device__ __forceinline__ uint32_t bin_walk_box(const CamParams &c, const float *g, const float4 gv,
                                                  const float2 half, const float *__restrict__ table, int tx0,
                                                  int ty0, int bw, uint32_t nb, uint32_t gid, uint32_t base,
+                                                 uint32_t m[8], uint32_t *__restrict__ list,
                                                  uint32_t *__restrict__ out_tile, uint32_t *__restrict__ out_gid) {
     const int lane = threadIdx.x & 31;
     uint32_t cnt = 0;
@@ -362,6 +380,12 @@ __device__ __forceinline__ uint32_t bin_walk_box(const CamParams &c, const float
             out_tile[pos] = tile;
             out_gid[pos] = gid;
         }
+        if (MODE == 0 && list && tp) list[cnt + __popc(tb & ((1u << lane) - 1u))] = tile;
+        if (MODE == 0 && nb <= MASK_MAX) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if ((uint32_t)q == (k0 >> 5)) m[q] = tb;
+        }
         cnt += __popc(tb);
         qy += sy;
         qx += sx;
@@ -373,36 +397,37 @@ __device__ __forceinline__ uint32_t bin_walk_box(const CamParams &c, const float
     return cnt;
 }
 
-// Slots with more candidates than this walk their box with the whole warp.
-constexpr uint32_t PACK_MAX = 96;
-
 template <int MODE>
 __global__ void __launch_bounds__(32 * BIN_WARPS, 3) bin_kernel(CamParams c, const float *__restrict__ binrec,
-                                                             const float4 *__restrict__ gview,
-                                                             const float2 *__restrict__ gcone,
-                                                             const uint8_t *__restrict__ gflag,
-                                                             const float *__restrict__ table,
-                                                             const float *__restrict__ super,
-                                                             const float *__restrict__ mcam, int64_t n,
-                                                             const uint32_t *__restrict__ order,
-                                                             const uint32_t *__restrict__ offsets,
-                                                             uint32_t *__restrict__ counts, uint4 *__restrict__ cache,
-                                                             uint32_t *__restrict__ out_tile,
-                                                             uint32_t *__restrict__ out_gid) {
+                                                                const float4 *__restrict__ gview,
+                                                                const float2 *__restrict__ gcone,
+                                                                const uint8_t *__restrict__ gflag,
+                                                                const float *__restrict__ table,
+                                                                const float *__restrict__ super,
+                                                                const float *__restrict__ mcam, int64_t n,
+                                                                const uint32_t *__restrict__ order,
+                                                                const uint32_t *__restrict__ offsets,
+                                                                uint32_t *__restrict__ counts,
+                                                                uint4 *__restrict__ cache,
+                                                                uint32_t *__restrict__ blist,
+                                                                unsigned long long *__restrict__ bcursor,
+                                                                unsigned long long bcap,
+                                                                uint32_t *__restrict__ out_tile,
+                                                                uint32_t *__restrict__ out_gid) {
     __shared__ float s_g[BIN_WARPS][5][32];        // kap, ks, kr, r1sq, s2 (flag is 1 for boxed slots)
     __shared__ float4 s_gv[BIN_WARPS][32];
     __shared__ float2 s_half[BIN_WARPS][32];
     __shared__ int4 s_box[BIN_WARPS][32];          // tx0, ty0, box width, cached (1) or not
-    __shared__ uint2 s_mask[BIN_WARPS][32];        // MODE 1: cached pass mask
     __shared__ float s_inv[BIN_WARPS][32];         // 1 / box width
+    __shared__ uint4 s_mask[BIN_WARPS][2][32];     // MODE 1: cached pass mask (8 words)
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t pos = ((int64_t)blockIdx.x * BIN_WARPS + wid) * 32 + lane;
     const bool have = pos < n;
     const uint32_t gid = have ? (MODE == 0 ? (uint32_t)pos : order[pos]) : 0u;
     const uint32_t base = (MODE == 1 && have) ? offsets[pos] : 0u;
     // ---- slot set-up
-    uint32_t nb = 0, fl = 0;
-    bool walk = false, cached = false, big = false;
+    uint32_t nb = 0, fl = 0, npk = 0, lofs = 0, lcnt = 0;
+    bool walk = false, cached = false, big = false, listed = false;
     float g[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float4 gv = make_float4(0.f, 0.f, 0.f, 0.f);
     float2 half = make_float2(0.f, 1.f);
@@ -410,18 +435,25 @@ __global__ void __launch_bounds__(32 * BIN_WARPS, 3) bin_kernel(CamParams c, con
     if (have) {
         fl = gflag[gid];
         if (MODE == 1) {
-            const uint4 cc = cache[gid];
-            if (cc.w != NO_CACHE) {
+            const uint4 cc = cache[3 * (size_t)gid];
+            if (cc.w == CACHE_LIST) {
+                listed = true;
+                lofs = cc.x;
+                lcnt = cc.y;
+            } else if (cc.w == CACHE_MASK) {
                 cached = true;
-                tx0 = (int)(cc.z & 0xffffu);
-                ty0 = (int)(cc.z >> 16);
-                const int bw = (int)(cc.w & 0xffffu);
-                nb = (uint32_t)(cc.w >> 16);
-                tx1 = tx0 + bw - 1;
-                s_mask[wid][lane] = make_uint2(cc.x, cc.y);
+                tx0 = (int)(cc.x & 0xffffu);
+                ty0 = (int)(cc.x >> 16);
+                tx1 = tx0 + (int)(cc.y & 0xffffu) - 1;
+                nb = cc.y >> 16;
+                const uint4 m0 = cache[3 * (size_t)gid + 1], m1 = cache[3 * (size_t)gid + 2];
+                s_mask[wid][0][lane] = m0;
+                s_mask[wid][1][lane] = m1;
+                npk = (uint32_t)(__popc(m0.x) + __popc(m0.y) + __popc(m0.z) + __popc(m0.w) + __popc(m1.x) +
+                                 __popc(m1.y) + __popc(m1.z) + __popc(m1.w));
             }
         }
-        if (fl != 0 && !cached) {
+        if (fl != 0 && !cached && !listed) {
 #pragma unroll
             for (int k = 0; k < 5; ++k) g[k] = binrec[6 * (size_t)gid + k];
             g[5] = (float)fl;
@@ -435,6 +467,7 @@ __global__ void __launch_bounds__(32 * BIN_WARPS, 3) bin_kernel(CamParams c, con
                 const int bw = tx1 - tx0 + 1, bh = ty1 - ty0 + 1;
                 nb = (bw > 0 && bh > 0) ? (uint32_t)(bw * bh) : 0u;
                 big = nb > PACK_MAX;
+                npk = big ? 0u : nb;
             } else {
                 walk = true;                     // pass-all (flag 2) or unbounded cone
             }
@@ -446,8 +479,8 @@ __global__ void __launch_bounds__(32 * BIN_WARPS, 3) bin_kernel(CamParams c, con
     s_half[wid][lane] = half;
     s_box[wid][lane] = make_int4(tx0, ty0, tx1 - tx0 + 1, cached ? 1 : 0);
     s_inv[wid][lane] = tx1 >= tx0 ? 1.0f / (float)(tx1 - tx0 + 1) : 0.0f;
-    // exclusive prefix of the packed slots' candidate counts (big boxes are walked below)
-    const uint32_t npk = big ? 0u : nb;
+    // exclusive prefix of the packed slots' candidate counts (a cached slot of the emit
+    // pass contributes its passing candidates only; big boxes are walked below)
     uint32_t start = npk;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -459,7 +492,7 @@ __global__ void __launch_bounds__(32 * BIN_WARPS, 3) bin_kernel(CamParams c, con
     __syncwarp();
     // ---- packed walk over the candidates of the 32 slots
     uint32_t cnt = 0;
-    unsigned long long pm = 0ull;
+    uint32_t pm[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
     for (uint32_t it0 = 0; it0 < total; it0 += 32) {
         const uint32_t p = it0 + (uint32_t)lane;
         // owner slot of candidate p: the last lane whose start is <= p (all lanes search)
@@ -474,8 +507,26 @@ __global__ void __launch_bounds__(32 * BIN_WARPS, 3) bin_kernel(CamParams c, con
         bool tp = false;
         uint32_t tile = 0u;
         if (p < total) {
-            const uint32_t k = p - sstart;
+            uint32_t k = p - sstart;
             const int4 bx = s_box[wid][sl];
+            if (MODE == 1 && bx.w) {
+                // the k-th passing candidate of a cached slot: the (k+1)-th set bit of its mask
+                const uint4 m0 = s_mask[wid][0][sl], m1 = s_mask[wid][1][sl];
+                const uint32_t mw[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+                uint32_t rem = k, bit = 0;
+                bool found = false;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const uint32_t pc = (uint32_t)__popc(mw[q]);
+                    if (!found && rem < pc) {
+                        bit = 32u * q + __fns(mw[q], 0u, (int)rem + 1);
+                        found = true;
+                    }
+                    if (!found) rem -= pc;
+                }
+                k = bit;
+                tp = true;
+            }
             // k = ky * width + kx, from a float reciprocal corrected to the exact quotient
             int ky = (int)((float)k * s_inv[wid][sl]);
             int kx = (int)k - ky * bx.z;
@@ -487,10 +538,7 @@ __global__ void __launch_bounds__(32 * BIN_WARPS, 3) bin_kernel(CamParams c, con
                 kx -= bx.z;
             }
             tile = (uint32_t)((bx.y + ky) * c.tiles_x + bx.x + kx);
-            if (MODE == 1 && bx.w) {
-                const uint2 m = s_mask[wid][sl];
-                tp = ((k < 32 ? (m.x >> k) : (m.y >> (k - 32))) & 1u) != 0u;
-            } else {
+            if (!(MODE == 1 && bx.w)) {
                 const float gg[6] = {s_g[wid][0][sl], s_g[wid][1][sl], s_g[wid][2][sl], s_g[wid][3][sl],
                                      s_g[wid][4][sl], 1.0f};
                 const float4 sgv = s_gv[wid][sl];
@@ -524,7 +572,7 @@ __global__ void __launch_bounds__(32 * BIN_WARPS, 3) bin_kernel(CamParams c, con
             }
         }
         __syncwarp();
-        if (MODE == 0 && nb <= 64u && lo32 < hi32) pm |= (unsigned long long)mine << (it0 + lo32 - start);
+        if (MODE == 0 && lo32 < hi32) mask_or(pm, mine, it0 + lo32 - start);
         cnt += (uint32_t)__popc(mine);
     }
     // ---- big boxes: one slot at a time by the whole warp
@@ -545,9 +593,37 @@ __global__ void __launch_bounds__(32 * BIN_WARPS, 3) bin_kernel(CamParams c, con
         const uint32_t bnb = __shfl_sync(0xffffffffu, nb, sl);
         const uint32_t sgid = __shfl_sync(0xffffffffu, gid, sl);
         const uint32_t sbase = __shfl_sync(0xffffffffu, base, sl);
-        const uint32_t wc = bin_walk_box<MODE>(c, gg, sgv, sh, table, btx0, bty0, bw, bnb, sgid, sbase, out_tile,
-                                               out_gid);
-        if (lane == sl) cnt = wc;
+        uint32_t wm[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+        uint32_t *lst = nullptr;
+        unsigned long long lo = 0ull;
+        if (MODE == 0 && bnb > MASK_MAX) {
+            if (lane == 0) lo = atomicAdd(bcursor, (unsigned long long)bnb);
+            lo = __shfl_sync(0xffffffffu, lo, 0);
+            if (lo + bnb <= bcap) lst = blist + lo;
+        }
+        const uint32_t wc = bin_walk_box<MODE>(c, gg, sgv, sh, table, btx0, bty0, bw, bnb, sgid, sbase, wm, lst,
+                                               out_tile, out_gid);
+        if (lane == sl) {
+            cnt = wc;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) pm[q] = wm[q];
+            listed = lst != nullptr;
+            lofs = (uint32_t)lo;
+        }
+    }
+    // ---- emit of list-cached slots: copy the kept tile ids, one slot at a time by the whole warp
+    if (MODE == 1) {
+        uint32_t lb = __ballot_sync(0xffffffffu, listed);
+        while (lb) {
+            const int sl = __ffs(lb) - 1;
+            lb &= lb - 1;
+            const uint32_t o = __shfl_sync(0xffffffffu, lofs, sl), nc = __shfl_sync(0xffffffffu, lcnt, sl);
+            const uint32_t sgid = __shfl_sync(0xffffffffu, gid, sl), sbase = __shfl_sync(0xffffffffu, base, sl);
+            for (uint32_t k = (uint32_t)lane; k < nc; k += 32) {
+                out_tile[sbase + k] = blist[o + k];
+                out_gid[sbase + k] = sgid;
+            }
+        }
     }
     // ---- slots without a box: the super-tile walk, one slot at a time by the whole warp
     uint32_t wb = __ballot_sync(0xffffffffu, walk);
@@ -569,10 +645,16 @@ __global__ void __launch_bounds__(32 * BIN_WARPS, 3) bin_kernel(CamParams c, con
     }
     if (MODE == 0 && have) {
         counts[gid] = cnt;
-        cache[gid] = (fl != 0 && !walk && nb <= 64u)
-                         ? make_uint4((uint32_t)pm, (uint32_t)(pm >> 32), (uint32_t)tx0 | ((uint32_t)ty0 << 16),
-                                      (uint32_t)(tx1 - tx0 + 1) | (nb << 16))
-                         : make_uint4(0u, 0u, 0u, NO_CACHE);
+        if (fl != 0 && !walk && nb <= MASK_MAX) {
+            cache[3 * (size_t)gid] = make_uint4((uint32_t)tx0 | ((uint32_t)ty0 << 16),
+                                                (uint32_t)(tx1 - tx0 + 1) | (nb << 16), 0u, CACHE_MASK);
+            cache[3 * (size_t)gid + 1] = make_uint4(pm[0], pm[1], pm[2], pm[3]);
+            cache[3 * (size_t)gid + 2] = make_uint4(pm[4], pm[5], pm[6], pm[7]);
+        } else if (listed) {
+            cache[3 * (size_t)gid] = make_uint4(lofs, cnt, 0u, CACHE_LIST);
+        } else {
+            cache[3 * (size_t)gid] = make_uint4(0u, 0u, 0u, NO_CACHE);
+        }
     }
 }
 
@@ -607,10 +689,12 @@ cudaError_t launch_gauss_view_rule(const CamParams &c, const SceneParams &sp, fl
 
 cudaError_t launch_bin_count(const CamParams &c, const float *binrec, const float4 *gview, const float2 *gcone,
                              const uint8_t *gflag, const float *table, const float *super, const float *mcam,
-                             int64_t n, uint32_t *counts, uint4 *cache, cudaStream_t s) {
+                             int64_t n, uint32_t *counts, uint4 *cache, uint32_t *blist,
+                             unsigned long long *bcursor, unsigned long long bcap, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     bin_kernel<0><<<(unsigned)div_up(n, 32 * BIN_WARPS), 32 * BIN_WARPS, 0, s>>>(
-        c, binrec, gview, gcone, gflag, table, super, mcam, n, nullptr, nullptr, counts, cache, nullptr, nullptr);
+        c, binrec, gview, gcone, gflag, table, super, mcam, n, nullptr, nullptr, counts, cache, blist, bcursor, bcap,
+        nullptr, nullptr);
     note_launches(1);
     return cudaGetLastError();
 }
@@ -618,11 +702,11 @@ cudaError_t launch_bin_count(const CamParams &c, const float *binrec, const floa
 cudaError_t launch_bin_emit(const CamParams &c, const float *binrec, const float4 *gview, const float2 *gcone,
                             const uint8_t *gflag, const float *table, const float *super, const float *mcam,
                             int64_t n_sorted, const uint32_t *order, const uint32_t *offsets, const uint4 *cache,
-                            uint32_t *out_tile, uint32_t *out_gid, cudaStream_t s) {
+                            const uint32_t *blist, uint32_t *out_tile, uint32_t *out_gid, cudaStream_t s) {
     if (n_sorted == 0) return cudaSuccess;
     bin_kernel<1><<<(unsigned)div_up(n_sorted, 32 * BIN_WARPS), 32 * BIN_WARPS, 0, s>>>(
         c, binrec, gview, gcone, gflag, table, super, mcam, n_sorted, order, offsets, nullptr,
-        const_cast<uint4 *>(cache), out_tile, out_gid);
+        const_cast<uint4 *>(cache), const_cast<uint32_t *>(blist), nullptr, 0ull, out_tile, out_gid);
     note_launches(1);
     return cudaGetLastError();
 }

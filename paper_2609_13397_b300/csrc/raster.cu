@@ -392,9 +392,14 @@ SegArgs split_args(uint32_t *scratch, int ntiles, int64_t *items) {
     return g;
 }
 
+// main0/main1 (may be NULL): events recorded around the first-segment launch.
 cudaError_t launch_raster_split(const RasterArgs &a, int ntiles, bool filter, uint32_t *scratch,
-                                uint32_t *scan_scratch, cudaStream_t s) {
-    if (ntiles == 0) return cudaSuccess;
+                                uint32_t *scan_scratch, cudaStream_t s, cudaEvent_t main0, cudaEvent_t main1) {
+    if (ntiles == 0) {
+        if (main0) cudaEventRecord(main0, s);
+        if (main1) cudaEventRecord(main1, s);
+        return cudaGetLastError();
+    }
     int64_t wmax = 0;
     const SegArgs g = split_args(scratch, ntiles, &wmax);
     uint32_t *nseg = const_cast<uint32_t *>(g.nseg), *off = const_cast<uint32_t *>(g.seg_off);
@@ -416,13 +421,17 @@ cudaError_t launch_raster_split(const RasterArgs &a, int ntiles, bool filter, ui
     ez = cudaMemsetAsync(g.need_item, 0, sizeof(uint32_t) * (size_t)wmax, s);
     if (ez != cudaSuccess) return ez;
     const unsigned later = (unsigned)(wmax - ntiles);
-    if (filter) {
+    if (main0) cudaEventRecord(main0, s);
+    if (filter)
         raster_seg_kernel<true, true><<<ntiles, TILE_PX, 0, s>>>(a, g);
+    else
+        raster_seg_kernel<false, true><<<ntiles, TILE_PX, 0, s>>>(a, g);
+    if (main1) cudaEventRecord(main1, s);
+    if (filter) {
         raster_seg_kernel<true, false><<<later, TILE_PX, 0, s>>>(a, g);
         raster_merge_kernel<<<ntiles, TILE_PX, 0, s>>>(a, g);
         raster_replay_kernel<true><<<(unsigned)wmax, TILE_PX, 0, s>>>(a, g, ntiles);
     } else {
-        raster_seg_kernel<false, true><<<ntiles, TILE_PX, 0, s>>>(a, g);
         raster_seg_kernel<false, false><<<later, TILE_PX, 0, s>>>(a, g);
         raster_merge_kernel<<<ntiles, TILE_PX, 0, s>>>(a, g);
         raster_replay_kernel<false><<<(unsigned)wmax, TILE_PX, 0, s>>>(a, g, ntiles);
