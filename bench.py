@@ -181,12 +181,13 @@ def run_ours(args, rank, world, local_rank):
     streams = [torch.cuda.Stream(device=dev) for _ in views]
 
     def step(flags=0):
-        """Both cameras of the workload; each view on its own stream (they overlap)."""
+        """Both cameras of the workload in one batch call, each view on its own
+        stream (their work overlaps on the device)."""
         ev0 = torch.cuda.Event()
         ev0.record(main)
-        for v, st, (o_rgb, o_T) in zip(views, streams, outs):
+        for st in streams:
             st.wait_event(ev0)
-            v.render(flags=flags, out_rgb=o_rgb, out_T=o_T, stream=st)
+        ctx.render_batch(views, flags=flags, outs=outs, streams=streams)
         for st in streams:
             main.wait_stream(st)
 
@@ -233,9 +234,10 @@ def run_ours(args, rank, world, local_rank):
         def fb_step():
             ev0 = torch.cuda.Event()
             ev0.record(main)
-            for v, st, (o_rgb, o_T), g in zip(views, streams, outs, gl):
+            for st in streams:
                 st.wait_event(ev0)
-                v.render(flags=cg.KEEP_FOR_BACKWARD, out_rgb=o_rgb, out_T=o_T, stream=st)
+            ctx.render_batch(views, flags=cg.KEEP_FOR_BACKWARD, outs=outs, streams=streams)
+            for v, st, g in zip(views, streams, gl):
                 v.render_backward(g, stream=st)
             for st in streams:
                 main.wait_stream(st)
@@ -434,10 +436,11 @@ def run_config(args):
         def step(backward):
             ev0 = torch.cuda.Event()
             ev0.record(main_s)
-            for vv, st, (o_rgb, o_T), g1, gd in zip(views, streams, outs, ones, grads):
+            for st in streams:
                 st.wait_event(ev0)
-                vv.render(flags=cg.KEEP_FOR_BACKWARD if backward else 0, out_rgb=o_rgb, out_T=o_T, stream=st)
-                if backward:
+            ctx.render_batch(views, flags=cg.KEEP_FOR_BACKWARD if backward else 0, outs=outs, streams=streams)
+            if backward:
+                for vv, st, g1, gd in zip(views, streams, ones, grads):
                     vv.render_backward(g1, grads=gd, stream=st)
             for st in streams:
                 main_s.wait_stream(st)

@@ -158,6 +158,20 @@ conegs_status conegs_set_camera(conegs_view *view, int model, int width, int hei
  * what render_backward needs (until the next render or set_camera on it). */
 conegs_status conegs_render(conegs_view *view, float *out_rgb, float *out_T, unsigned flags, void *stream);
 
+/* The same render for n views at once (a camera rig, or the views of one
+ * step), each into its own output on its own stream.  A render needs one host
+ * wait (for its pair count, to size the pair buffers); here the view records
+ * and bin counts of all views are enqueued before the first wait, so the
+ * views' work overlaps on the device.
+ *   views[n]: distinct views of one context, each with a camera;
+ *   out_rgb[n], out_T[n] (out_T may be NULL, or any entry of it), streams[n]
+ *   (may be NULL: every view on the default stream).
+ * flags apply to every view.  Returns the first error; views before the
+ * failing one are rendered, the failing one and the rest are not (their
+ * render_backward then fails with CONEGS_ERR_STATE). */
+conegs_status conegs_render_batch(int n, conegs_view *const *views, float *const *out_rgb, float *const *out_T,
+                                  unsigned flags, void *const *streams);
+
 /* Same as conegs_render, with HOST output buffers (pinned memory recommended):
  * renders into view-owned device memory and copies the result back on
  * `stream`; returns after the copy has completed. */

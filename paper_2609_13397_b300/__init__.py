@@ -112,6 +112,22 @@ class Context:
         self._views.append(v)
         return v
 
+    def render_batch(self, views: Sequence["View"], flags: int = 0, outs=None, streams=None):
+        """Render several views in one call (their work overlaps on the device);
+        returns [(rgb, T)] per view.  outs: optional [(out_rgb, out_T)] per view."""
+        n = len(views)
+        dev = self.device
+        if outs is None:
+            outs = [(torch.empty(3, v.height, v.width, device=dev, dtype=torch.float32),
+                     torch.empty(v.height, v.width, device=dev, dtype=torch.float32)) for v in views]
+        P = ctypes.c_void_p
+        hv = (P * n)(*[v._h for v in views])
+        rgb = (P * n)(*[_ptr(o[0]) for o in outs])
+        Ts = (P * n)(*[_ptr(o[1]) for o in outs])
+        st = (P * n)(*[_stream(None if streams is None else streams[i]) for i in range(n)])
+        check(lib().conegs_render_batch(n, hv, rgb, Ts, flags, st), "render_batch")
+        return list(outs)
+
     def compute_floor(self, views: Sequence["View"], stream=None) -> torch.Tensor:
         """Eq. 11 training-frequency floor of the current scene's Gaussians over ``views``."""
         out = torch.empty(self.n, device=self.device, dtype=torch.float32)

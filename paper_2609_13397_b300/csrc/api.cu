@@ -141,6 +141,7 @@ struct conegs_view {
     bool has_cam = false;
     DevBuf d, dx, dy, valid, table, super, mcam, bincache, binlist;
     uint64_t list_want = 0;   // tile ids the last count pass wanted to keep in binlist
+    long long launches0 = 0;  // launch counter at the start of the current render
     // per-render scratch
     DevBuf rec, gview, gcone, gflag, counts, vispos, scan_scr, dkeys, dvals, dkeys_alt, dvals_alt, sorted_counts, offsets;
     DevBuf pair_tile, pair_gid, pair_tile_alt, pair_gid_alt, ranges, last, sums, rs_scr, tmp_rgb, tmp_T;
@@ -459,14 +460,19 @@ conegs_status conegs_set_camera(conegs_view *v, int model, int width, int height
     return view_end(v, s);
 }
 
-static conegs_status render_impl(conegs_view *v, float *out_rgb, float *out_T, unsigned flags, cudaStream_t s) {
+// A render runs in two halves around the one host synchronisation it needs:
+// render_front enqueues the view records, the bin count and the pair/visible
+// totals (copied to pinned host memory); render_back, after the stream has
+// reached that copy, sizes the pair buffers from the totals and enqueues the
+// sorts, the emit and the rasteriser.
+static conegs_status render_front(conegs_view *v, unsigned flags, cudaStream_t s) {
     conegs_ctx *ctx = v->ctx;
     const CamParams &c = v->cam;
     const int64_t n = ctx->sp.n;
     const int64_t P = (int64_t)c.W * c.H;
     const int nt = c.tiles_x * c.tiles_y;
     CUDA_TRY(cudaStreamWaitEvent(s, ctx->scene_ready, 0));
-    const long long launches0 = launches_so_far();
+    v->launches0 = launches_so_far();
     const size_t nn = (size_t)std::max<int64_t>(n, 1);
     TRY(ensure(ctx, v->rec, sizeof(float4) * REC_F4 * nn, s));
     TRY(ensure(ctx, v->gview, sizeof(float4) * nn, s));
@@ -501,7 +507,17 @@ static conegs_status render_impl(conegs_view *v, float *out_rgb, float *out_T, u
     CUDA_TRY(exclusive_scan(v->counts.as<uint32_t>(), v->vispos.as<uint32_t>(), n, v->scan_scr.as<uint32_t>(), 1, s));
     if (prof) CUDA_TRY(cudaEventRecord(v->prof[1], s));
     CUDA_TRY(cudaMemcpyAsync(v->h_sums, v->sums.p, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaStreamSynchronize(s));
+    return CONEGS_OK;
+}
+
+static conegs_status render_back(conegs_view *v, float *out_rgb, float *out_T, unsigned flags, cudaStream_t s) {
+    conegs_ctx *ctx = v->ctx;
+    const CamParams &c = v->cam;
+    const int64_t n = ctx->sp.n;
+    const int64_t P = (int64_t)c.W * c.H;
+    const int nt = c.tiles_x * c.tiles_y;
+    const SceneParams sp = ctx->sp;
+    const bool prof = (flags & CONEGS_PROFILE) != 0;
     const uint64_t total = v->h_sums[0];
     const int64_t M = (int64_t)v->h_sums[1];
     // room the count pass wanted for kept tile lists: grown (with headroom) before the next render
@@ -570,7 +586,7 @@ static conegs_status render_impl(conegs_view *v, float *out_rgb, float *out_T, u
                                  cudaMemcpyDeviceToHost, s));
     }
     v->profiled = prof;
-    v->n_launches = launches_so_far() - launches0;
+    v->n_launches = launches_so_far() - v->launches0;
     v->n_visible = M;
     v->n_pairs = Pn;
     v->last_flags = flags;
@@ -578,6 +594,12 @@ static conegs_status render_impl(conegs_view *v, float *out_rgb, float *out_T, u
     v->forward_gen = ctx->scene_gen;
     (void)P;
     return CONEGS_OK;
+}
+
+static conegs_status render_impl(conegs_view *v, float *out_rgb, float *out_T, unsigned flags, cudaStream_t s) {
+    TRY(render_front(v, flags, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return render_back(v, out_rgb, out_T, flags, s);
 }
 
 conegs_status conegs_render(conegs_view *v, float *out_rgb, float *out_T, unsigned flags, void *stream) {
@@ -594,6 +616,50 @@ conegs_status conegs_render(conegs_view *v, float *out_rgb, float *out_T, unsign
         return st;
     }
     return view_end(v, s);
+}
+
+conegs_status conegs_render_batch(int n, conegs_view *const *views, float *const *out_rgb, float *const *out_T,
+                                  unsigned flags, void *const *streams) {
+    if (n < 0 || (n > 0 && (!views || !out_rgb))) return fail(CONEGS_ERR_ARG, "render_batch: bad argument");
+    for (int i = 0; i < n; ++i) {
+        if (!views[i] || !out_rgb[i]) return fail(CONEGS_ERR_ARG, "render_batch: NULL view or output %d", i);
+        if (!views[i]->has_cam) return fail(CONEGS_ERR_STATE, "render_batch: view %d has no camera", i);
+        if (views[i]->ctx != views[0]->ctx) return fail(CONEGS_ERR_ARG, "render_batch: views of different contexts");
+        for (int j = 0; j < i; ++j)
+            if (views[j] == views[i]) return fail(CONEGS_ERR_ARG, "render_batch: view %d repeated", i);
+    }
+    if (n == 0) return CONEGS_OK;
+    if (!views[0]->ctx->has_scene) return fail(CONEGS_ERR_STATE, "render_batch: set_scene was not called");
+    DeviceGuard g(views[0]->ctx->device);
+    auto stream_of = [&](int i) { return streams ? (cudaStream_t)streams[i] : (cudaStream_t)0; };
+    int started = 0;
+    conegs_status st = CONEGS_OK;
+    for (; started < n; ++started) {
+        conegs_view *v = views[started];
+        const cudaStream_t s = stream_of(started);
+        v->has_forward = false;
+        st = view_begin(v, s);
+        if (st == CONEGS_OK) st = render_front(v, flags, s);
+        if (st != CONEGS_OK) {
+            view_end(v, s);
+            break;
+        }
+    }
+    // every started view must reach its back half or be closed, even after an error
+    for (int i = 0; i < started; ++i) {
+        conegs_view *v = views[i];
+        const cudaStream_t s = stream_of(i);
+        if (st == CONEGS_OK) {
+            cudaError_t e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) st = fail(CONEGS_ERR_CUDA, "render_batch: %s", cudaGetErrorString(e));
+        }
+        if (st == CONEGS_OK) {
+            st = render_back(v, out_rgb[i], out_T ? out_T[i] : nullptr, flags, s);
+            if (st != CONEGS_OK) v->has_forward = false;
+        }
+        view_end(v, s);
+    }
+    return st;
 }
 
 conegs_status conegs_render_host(conegs_view *v, float *out_rgb_host, float *out_T_host, unsigned flags,

@@ -269,3 +269,26 @@ def test_split_long_lists_match_oracle(cg, oracle_lib):
     assert ok.mean() > 0.8
     assert np.abs(rgb - r.rgb)[ok].max() <= TOL and np.abs(T - r.T)[ok].max() <= TOL
     assert st["n_walked"] > 0
+
+
+def test_render_batch_equals_single_renders(cg):
+    """conegs_render_batch overlaps the views' work but computes each view's image
+    exactly as a single render does."""
+    sc = S.blob_scene(20000, seed=4, cam=S.pinhole(320, 180, 300.0))
+    ctx = cg.Context(0)
+    ctx.set_scene_from(sc)
+    cams = [S.pinhole(320, 180, 300.0), S.c3_camera(96, 96), S.pinhole(40, 24, 37.5)]
+    views = []
+    for c in cams:
+        v = ctx.view()
+        v.set_camera_from(c)
+        views.append(v)
+    single = [v.render() for v in views]
+    streams = [torch.cuda.Stream() for _ in views]
+    batch = ctx.render_batch(views, streams=streams)
+    torch.cuda.synchronize()
+    for (r1, t1), (r2, t2) in zip(single, batch):
+        assert torch.equal(r1, r2) and torch.equal(t1, t2)
+    with pytest.raises(cg.ConegsError) as e:
+        ctx.render_batch([views[0], views[0]])
+    assert e.value.status == 1
