@@ -77,8 +77,15 @@ enum {
     CONEGS_FILTER_NONE = 1u << 0,   /* centre-ray response sigma e^{-D^2/2} (no footprint, Eq. 3 with C=1) */
     CONEGS_COMP_ADDITIVE = 1u << 1, /* use Sigma_fp,eff directly instead of Eq. 12's marginal clamp */
     CONEGS_KEEP_FOR_BACKWARD = 1u << 2, /* keep pair lists and per-pixel state for render_backward */
-    CONEGS_PROFILE = 1u << 3   /* record per-stage CUDA events on the stream and count pair evaluations
+    CONEGS_PROFILE = 1u << 3,  /* record per-stage CUDA events on the stream and count pair evaluations
                                   (read back by conegs_get_stats) */
+    /* Isotropic footprint variants (the comparison axis of Sec. 5), at most one of
+     * FILTER_NONE / FILTER_ISO / FILTER_ZF (else CONEGS_ERR_ARG).  Eq. 6-12 are kept;
+     * the pixel's two half-edge differentials are replaced by a b1, a b2, (b1, b2) an
+     * orthonormal basis across the pixel ray d, so the footprint is isotropic across
+     * the ray with t^2 a^2 / 3 per axis (Eq. 8): */
+    CONEGS_FILTER_ISO = 1u << 4, /* a^2 = (|dx_perp|^2 + |dy_perp|^2) / 2: half-trace of the true footprint */
+    CONEGS_FILTER_ZF = 1u << 5   /* a = |<d, z_cam>| / (2 f_x): paraxial z/f pixel size (VKRayGS-style sizing) */
 };
 
 typedef struct conegs_ctx conegs_ctx;

@@ -23,7 +23,7 @@ _SRC = os.path.join(_HERE, "conegs_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
-FILTER_NONE, FILTER_ANISO = 0, 1
+FILTER_NONE, FILTER_ANISO, FILTER_ISO, FILTER_ZF = 0, 1, 2, 3
 COMP_MARGINAL, COMP_ADDITIVE = 0, 1
 FL_ALPHA_MIN, FL_ALPHA_MAX, FL_STOP, FL_KEY_TIE, FL_TNEAR = 1, 2, 4, 8, 16
 
@@ -247,10 +247,21 @@ def bin_gauss(cam, scene) -> np.ndarray:
     return out
 
 
-def bin_counts(cam, scene, dense: bool = False):
+def zf_footprint_bound(cam) -> np.float32:
+    """FP32 bound 1/(6 f_x^2) of the z/f pseudo-differentials' (|dx|^2 + |dy|^2)/3,
+    by the op sequence the GPU rule uses (fx * fx, times 6, 1 over)."""
+    fx = np.float32(cam.fx)
+    return np.float32(1.0) / (np.float32(6.0) * (fx * fx))
+
+
+def bin_counts(cam, scene, dense: bool = False, zf: bool = False):
     """Per-Gaussian and per-tile pair counts of the binning rule (FP32 emulation);
-    with dense=True also the [n, ntiles] pass matrix."""
+    with dense=True also the [n, ntiles] pass matrix.  zf=True: the rule's
+    footprint bound m of every tile raised to the z/f variant's 1/(6 f_x^2)."""
     table = tile_table(cam)
+    if zf:
+        live = table[:, 3] >= 0
+        table[live, 5] = np.maximum(table[live, 5], zf_footprint_bound(cam))
     recs = bin_gauss(cam, scene)
     n, nt = scene.n, table.shape[0]
     pg = np.zeros(n, np.int32)

@@ -379,7 +379,45 @@ static double lu_solve3(const double *Ain, const double *b, double *x) {
 
 /* ------------------------------------------------------------------ one pair */
 
-enum { FILTER_NONE = 0, FILTER_ANISO = 1 };
+enum { FILTER_NONE = 0, FILTER_ANISO = 1, FILTER_ISO = 2, FILTER_ZF = 3 };
+
+/* Isotropic footprint variants (the comparison axis of Sec. 5: the isotropic
+ * reduction the paper defers to its absent appendix, and the paraxial z/f
+ * sizing of VKRayGS reimplemented in the same framework).  Both keep Eq. 6-9
+ * and only replace the pixel's two half-edge differentials by a b1, a b2, with
+ * (b1, b2) an orthonormal basis of the plane across d: the world footprint at
+ * the max-response point is then isotropic across the ray, t^2 a^2 / 3 per
+ * axis (Eq. 8), and independent of the basis chosen.
+ *   FILTER_ISO: a^2 = (|dx_perp|^2 + |dy_perp|^2) / 2, the half-trace of the
+ *     true footprint (the isotropic reduction the paper uses in Eq. 11);
+ *   FILTER_ZF:  a = |<d, z_cam>| / (2 f_x): per-axis variance z^2 / (12 f_x^2)
+ *     at depth z along the optical axis z_cam (paraxial pixel size z / f). */
+static void footprint_variant(const ocam *c, int filter, const double d[3], double dx[3], double dy[3]) {
+    if (filter != FILTER_ISO && filter != FILTER_ZF) return;
+    double a2;
+    if (filter == FILTER_ISO) {
+        double px[3], py[3], sx = dot3(d, dx), sy = dot3(d, dy);
+        for (int i = 0; i < 3; ++i) { px[i] = dx[i] - sx * d[i]; py[i] = dy[i] - sy * d[i]; }
+        a2 = 0.5 * (dot3(px, px) + dot3(py, py));
+    } else {
+        const double z = d[0] * c->R[2] + d[1] * c->R[5] + d[2] * c->R[8];
+        a2 = z * z / (4.0 * c->fx * c->fx);
+    }
+    /* b1: the coordinate axis least aligned with d, made orthogonal to d */
+    int k = 0;
+    for (int i = 1; i < 3; ++i) if (fabs(d[i]) < fabs(d[k])) k = i;
+    double b1[3] = {0, 0, 0}, b2[3];
+    b1[k] = 1.0;
+    const double s = dot3(b1, d);
+    for (int i = 0; i < 3; ++i) b1[i] -= s * d[i];
+    const double nb = sqrt(dot3(b1, b1));
+    for (int i = 0; i < 3; ++i) b1[i] /= nb;
+    b2[0] = d[1] * b1[2] - d[2] * b1[1];
+    b2[1] = d[2] * b1[0] - d[0] * b1[2];
+    b2[2] = d[0] * b1[1] - d[1] * b1[0];
+    const double a = sqrt(a2);
+    for (int i = 0; i < 3; ++i) { dx[i] = a * b1[i]; dy[i] = a * b2[i]; }
+}
 enum { COMP_MARGINAL = 0, COMP_ADDITIVE = 1 };
 
 /* detail[] layout (when non-NULL, 64 doubles):
@@ -402,7 +440,7 @@ static int pair_response(const ogauss *g, const double o[3], const double d[3], 
     mv3(Mp, ou, q);                   /* q = M_perp o_u */
     double D2 = dot3(q, q);
     double Sfp[9] = {0}, Sr[9] = {0}, ex[3] = {0}, ey[3] = {0}, detA = 1.0, Qf = D2;
-    if (filter == FILTER_ANISO) {
+    if (filter != FILTER_NONE) {
         double MW[9], t1[3];
         mm3(Mp, g->W, MW);
         mv3(MW, dx, t1);
@@ -582,6 +620,7 @@ int or_pair_detail(const double *campk, double x, double y, const double *mu, co
     unpack_cam(campk, &c);
     double d[3], dx[3], dy[3], sh[3] = {0, 0, 0}, ts, T;
     if (!pixel_rays(&c, x, y, d, dx, dy)) return -1;
+    footprint_variant(&c, filter, d, dx, dy);
     ogauss g;
     prep_gauss(c.o, mu, ls, q, logit, sh, 0, rho2, &g);
     memset(detail, 0, 64 * sizeof(double));
@@ -655,6 +694,7 @@ void or_render(const double *campk, int n, const double *means, const double *lo
                 ncontrib[t] = 0;
                 continue;
             }
+            footprint_variant(&c, filter, d, dx, dy);
             double m = (dot3(dx, dx) + dot3(dy, dy)) / 3.0;
             int nc = 0;
             for (int k = 0; k < n; ++k) {

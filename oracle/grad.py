@@ -61,8 +61,30 @@ def _fp32_key(means: np.ndarray, o: np.ndarray) -> np.ndarray:
     return np.sqrt((v[:, 0] * v[:, 0] + v[:, 1] * v[:, 1]) + v[:, 2] * v[:, 2]).astype(np.float64)
 
 
+def _isotropic_differentials(cam, d: np.ndarray, dx: np.ndarray, dy: np.ndarray, footprint: str):
+    """Isotropic footprint variants: the half-edge differentials become a b1, a b2,
+    (b1, b2) orthonormal across d (built here from d x (a coordinate axis), a
+    different basis from the C oracle's: the footprint does not depend on it);
+    a^2 = (|dx_perp|^2 + |dy_perp|^2)/2 ('iso') or a = |<d, z_cam>|/(2 f_x) ('zf')."""
+    if footprint == "own":
+        return dx, dy
+    if footprint == "iso":
+        px = dx - (d * dx).sum(1, keepdims=True) * d
+        py = dy - (d * dy).sum(1, keepdims=True) * d
+        a = np.sqrt(0.5 * ((px * px).sum(1) + (py * py).sum(1)))
+    else:
+        zc = cam.cam_to_world[:, 2].astype(np.float64)
+        a = np.abs(d @ zc) / (2.0 * float(cam.fx))
+    axis = np.eye(3)[np.argmax(np.abs(d), 1)]          # the axis most aligned with d
+    b1 = np.cross(d, np.roll(axis, 1, axis=1))
+    b1 /= np.linalg.norm(b1, axis=1, keepdims=True)
+    b2 = np.cross(d, b1)
+    b2 /= np.linalg.norm(b2, axis=1, keepdims=True)
+    return a[:, None] * b1, a[:, None] * b2
+
+
 def render_torch(cam, params: dict, deg: int, rho2: torch.Tensor, pix: np.ndarray, filter_on: bool = True,
-                 additive: bool = False):
+                 additive: bool = False, footprint: str = "own"):
     """Differentiable FP64 render of pixels ``pix``.  params: means [n,3], log_scales
     [n,3], quats [n,4], logits [n], sh [n,K,3] (FP64 tensors).  Returns rgb [P,3], T [P]."""
     o = torch.as_tensor(cam.cam_to_world[:, 3].astype(np.float64))
@@ -90,6 +112,7 @@ def render_torch(cam, params: dict, deg: int, rho2: torch.Tensor, pix: np.ndarra
     d[~valid] = (0.0, 0.0, 1.0)
     dx[~valid] = (1e-3, 0.0, 0.0)
     dy[~valid] = (0.0, 1e-3, 0.0)
+    dx, dy = _isotropic_differentials(cam, d, dx, dy, footprint)
     d, dx, dy = (torch.as_tensor(a) for a in (d, dx, dy))
     W_o, Winv_o, sig_o, col_o, rho2_o = W[order], Winv[order], sig_eff[order], col[order], rho2[order]
     ou = torch.einsum("nab,nb->na", W_o, (o - means[order]))   # o_u = W (o - mu)
@@ -135,7 +158,7 @@ def render_torch(cam, params: dict, deg: int, rho2: torch.Tensor, pix: np.ndarra
 
 
 def loss_and_grad(cam, scene, pix, w_rgb: np.ndarray, w_T: np.ndarray, filter_on: bool = True,
-                  additive: bool = False, chunk: int = 256):
+                  additive: bool = False, chunk: int = 256, footprint: str = "own"):
     """L = sum w_rgb . rgb + w_T . T over ``pix``; returns (L, grads dict of numpy FP64)."""
     params = {
         "means": torch.tensor(scene.means.astype(np.float64), requires_grad=True),
@@ -149,7 +172,7 @@ def loss_and_grad(cam, scene, pix, w_rgb: np.ndarray, w_T: np.ndarray, filter_on
     total = 0.0
     for s0 in range(0, pix.size, chunk):
         sl = slice(s0, s0 + chunk)
-        rgb, T = render_torch(cam, params, scene.sh_degree, rho2, pix[sl], filter_on, additive)
+        rgb, T = render_torch(cam, params, scene.sh_degree, rho2, pix[sl], filter_on, additive, footprint)
         l = (rgb * torch.as_tensor(w_rgb[sl])).sum() + (T * torch.as_tensor(w_T[sl])).sum()
         l.backward()
         total += float(l.detach())

@@ -25,15 +25,16 @@ cudaError_t launch_tile_tables(const CamParams &c, float *table, float *super, f
 cudaError_t launch_gauss_scene_rule(const SceneParams &sp, float *binrec, cudaStream_t s);
 cudaError_t launch_bin_count(const CamParams &c, const float *binrec, const float4 *gview, const float2 *gcone,
                              const uint8_t *gflag, const float *table, const float *super, const float *mcam,
-                             int64_t n, uint32_t *counts, uint4 *cache, uint32_t *blist,
+                             float mzf, int64_t n, uint32_t *counts, uint4 *cache, uint32_t *blist,
                              unsigned long long *bcursor, unsigned long long bcap, cudaStream_t s);
 cudaError_t launch_bin_emit(const CamParams &c, const float *binrec, const float4 *gview, const float2 *gcone,
                             const uint8_t *gflag, const float *table, const float *super, const float *mcam,
-                            int64_t n_sorted, const uint32_t *order, const uint32_t *offsets, const uint4 *cache,
-                            const uint32_t *blist, uint32_t *out_tile, uint32_t *out_gid, cudaStream_t s);
+                            float mzf, int64_t n_sorted, const uint32_t *order, const uint32_t *offsets,
+                            const uint4 *cache, const uint32_t *blist, uint32_t *out_tile, uint32_t *out_gid,
+                            cudaStream_t s);
 cudaError_t launch_scene_cache(const SceneParams &sp, float *W, float *sig_eff, cudaStream_t s);
-cudaError_t launch_view_records(const CamParams &c, const SceneParams &sp, const float *mcam, float4 *rec,
-                                float4 *gview, float2 *gcone, uint8_t *gflag, cudaStream_t s);
+cudaError_t launch_view_records(const CamParams &c, const SceneParams &sp, const float *mcam, float mzf,
+                                float4 *rec, float4 *gview, float2 *gcone, uint8_t *gflag, cudaStream_t s);
 int64_t scan_scratch_words(int64_t n);
 cudaError_t exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *scratch, int pred,
                            cudaStream_t s);
@@ -460,12 +461,37 @@ conegs_status conegs_set_camera(conegs_view *v, int model, int width, int height
     return view_end(v, s);
 }
 
+// Footprint variant of a render (flags), and the z/f variant's FP32 bound 1/(6 f_x^2)
+// on (|dx|^2 + |dy|^2)/3 (0 for the others); the same op sequence as the oracle.
+static int footprint_mode(unsigned flags) {
+    return (flags & CONEGS_FILTER_ISO) ? FOOTPRINT_ISO : (flags & CONEGS_FILTER_ZF) ? FOOTPRINT_ZF : FOOTPRINT_OWN;
+}
+
+static float zf_bound(const CamParams &c, unsigned flags) {
+    if (!(flags & CONEGS_FILTER_ZF)) return 0.0f;
+    const float f2 = c.fx * c.fx;
+    const float d6 = 6.0f * f2;
+    return 1.0f / d6;
+}
+
+static void set_footprint(RasterArgs &a, const CamParams &c, unsigned flags) {
+    a.footprint = footprint_mode(flags);
+    a.zax[0] = c.R[2];
+    a.zax[1] = c.R[5];
+    a.zax[2] = c.R[8];
+    a.zf_scale = 0.5f / c.fx;
+}
+
 // A render runs in two halves around the one host synchronisation it needs:
 // render_front enqueues the view records, the bin count and the pair/visible
 // totals (copied to pinned host memory); render_back, after the stream has
 // reached that copy, sizes the pair buffers from the totals and enqueues the
 // sorts, the emit and the rasteriser.
 static conegs_status render_front(conegs_view *v, unsigned flags, cudaStream_t s) {
+    {
+        const unsigned fp = flags & (CONEGS_FILTER_NONE | CONEGS_FILTER_ISO | CONEGS_FILTER_ZF);
+        if (fp & (fp - 1u)) return fail(CONEGS_ERR_ARG, "render: FILTER_NONE, FILTER_ISO and FILTER_ZF exclude each other");
+    }
     conegs_ctx *ctx = v->ctx;
     const CamParams &c = v->cam;
     const int64_t n = ctx->sp.n;
@@ -493,14 +519,15 @@ static conegs_status render_front(conegs_view *v, unsigned flags, cudaStream_t s
         CUDA_TRY(cudaMemsetAsync(v->evaluated.p, 0, 2 * sizeof(unsigned long long), s));
         CUDA_TRY(cudaEventRecord(v->prof[0], s));
     }
-    CUDA_TRY(launch_view_records(c, sp, v->mcam.as<float>(), v->rec.as<float4>(), v->gview.as<float4>(),
+    CUDA_TRY(launch_view_records(c, sp, v->mcam.as<float>(), zf_bound(c, flags), v->rec.as<float4>(), v->gview.as<float4>(),
                                  v->gcone.as<float2>(), v->gflag.as<uint8_t>(), s));
     CUDA_TRY(cudaMemsetAsync(v->sums.as<unsigned long long>() + 2, 0, sizeof(unsigned long long), s));
     {
         const unsigned long long cap = std::min<unsigned long long>(v->binlist.bytes / sizeof(uint32_t), 0xffffffffull);
         CUDA_TRY(launch_bin_count(c, sp.binrec, v->gview.as<float4>(), v->gcone.as<float2>(), v->gflag.as<uint8_t>(),
-                                  v->table.as<float>(), v->super.as<float>(), v->mcam.as<float>(), n,
-                                  v->counts.as<uint32_t>(), v->bincache.as<uint4>(), v->binlist.as<uint32_t>(),
+                                  v->table.as<float>(), v->super.as<float>(), v->mcam.as<float>(),
+                                  zf_bound(c, flags), n, v->counts.as<uint32_t>(), v->bincache.as<uint4>(),
+                                  v->binlist.as<uint32_t>(),
                                   v->sums.as<unsigned long long>() + 2, cap, s));
     }
     CUDA_TRY(sum_counts(v->counts.as<uint32_t>(), n, v->sums.as<unsigned long long>(), s));
@@ -548,7 +575,7 @@ static conegs_status render_back(conegs_view *v, float *out_rgb, float *out_T, u
     CUDA_TRY(exclusive_scan(v->sorted_counts.as<uint32_t>(), v->offsets.as<uint32_t>(), M, v->scan_scr.as<uint32_t>(),
                             0, s));
     CUDA_TRY(launch_bin_emit(c, sp.binrec, v->gview.as<float4>(), v->gcone.as<float2>(), v->gflag.as<uint8_t>(),
-                             v->table.as<float>(), v->super.as<float>(), v->mcam.as<float>(), M,
+                             v->table.as<float>(), v->super.as<float>(), v->mcam.as<float>(), zf_bound(c, flags), M,
                              v->dvals.as<uint32_t>(), v->offsets.as<uint32_t>(), v->bincache.as<uint4>(),
                              v->binlist.as<uint32_t>(), v->pair_tile.as<uint32_t>(), v->pair_gid.as<uint32_t>(), s));
     CUDA_TRY(radix_sort_pairs(v->pair_tile.as<uint32_t>(), v->pair_gid.as<uint32_t>(), v->pair_tile_alt.as<uint32_t>(),
@@ -570,6 +597,7 @@ static conegs_status render_back(conegs_view *v, float *out_rgb, float *out_T, u
     a.out_T = out_T;
     a.last = v->last.as<uint32_t>();
     a.additive = (flags & CONEGS_COMP_ADDITIVE) ? 1 : 0;
+    set_footprint(a, c, flags);
     if (flags & CONEGS_KEEP_FOR_BACKWARD) {
         TRY(ensure(ctx, v->keep_T, sizeof(float) * (size_t)std::max<int64_t>(P, 1), s));
         a.keep_T = v->keep_T.as<float>();
@@ -714,6 +742,7 @@ conegs_status conegs_render_backward(conegs_view *v, const float *dL_drgb, const
     a.valid = v->valid.as<uint8_t>();
     a.last = v->last.as<uint32_t>();
     a.additive = (v->last_flags & CONEGS_COMP_ADDITIVE) ? 1 : 0;
+    set_footprint(a, c, v->last_flags);
     CUDA_TRY(launch_backward(a, nt, !(v->last_flags & CONEGS_FILTER_NONE), v->split.as<uint32_t>(), dL_drgb, dL_dT,
                              v->keep_T.as<float>(), v->g_rec.as<float>(), s));
     CUDA_TRY(launch_backward_params(c, ctx->sp, v->g_rec.as<float>(), v->gflag.as<uint8_t>(), v->gview.as<float4>(),

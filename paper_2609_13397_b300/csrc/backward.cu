@@ -187,7 +187,7 @@ __device__ __forceinline__ float pair_adjoint(const PairFwd &f, const float4 r0,
 // the colour composited behind it; pixels whose walk ended before the segment
 // sit out.
 template <bool FILTER, bool FIRST>
-__global__ void __launch_bounds__(TILE_PX) raster_bwd_kernel(const RasterArgs a, const SegArgs g,
+__global__ void __launch_bounds__(TILE_PX, 12) raster_bwd_kernel(const RasterArgs a, const SegArgs g,
                                                              const float *__restrict__ dL_drgb,
                                                              const float *__restrict__ dL_dT,
                                                              const float *__restrict__ final_T,

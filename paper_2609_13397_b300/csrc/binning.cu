@@ -191,6 +191,14 @@ __device__ __forceinline__ bool cone_prefilter(const float4 gv, const float2 hal
     return ch2 <= lim * lim || half.y < 1e-3f;
 }
 
+// A tile's cone record with its footprint bound m raised to mzf (the z/f
+// variant's bound; 0 otherwise, which leaves the record unchanged).
+__device__ __forceinline__ void tile_record(const float *__restrict__ table, uint32_t tile, float mzf, float t[6]) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) t[k] = table[6 * (size_t)tile + k];
+    t[5] = fmaxf(t[5], mzf);
+}
+
 // Pinhole cameras: the tiles whose centre ray lies within angle beta + gamma_max
 // of the Gaussian's direction u (a superset of what cone_prefilter keeps, with
 // margin) have their centre pixel inside the image of that cone on the plane
@@ -305,8 +313,9 @@ __device__ __forceinline__ void mask_or(uint32_t m[8], uint32_t bits, uint32_t a
 template <int MODE>
 __device__ __forceinline__ uint32_t bin_walk_supers(const CamParams &c, const float *g, const float4 gv,
                                                     const float2 half, const float *__restrict__ table,
-                                                    const float *__restrict__ super, uint32_t gid, uint32_t base,
-                                                    uint32_t *__restrict__ out_tile, uint32_t *__restrict__ out_gid) {
+                                                    const float *__restrict__ super, float mzf, uint32_t gid,
+                                                    uint32_t base, uint32_t *__restrict__ out_tile,
+                                                    uint32_t *__restrict__ out_gid) {
     const int lane = threadIdx.x & 31;
     const int nsup = c.supers_x * c.supers_y;
     uint32_t cnt = 0;
@@ -328,7 +337,8 @@ __device__ __forceinline__ uint32_t bin_walk_supers(const CamParams &c, const fl
                 uint32_t tile = 0;
                 if (tx < c.tiles_x && ty < c.tiles_y) {
                     tile = (uint32_t)(ty * c.tiles_x + tx);
-                    const float *tt = table + 6 * (size_t)tile;
+                    float tt[6];
+                    tile_record(table, tile, mzf, tt);
                     if (cone_prefilter(gv, half, tt)) {
                         const int f = rule_test_fast(g, gv, tt);
                         tp = f == 2 ? rule_test(g, gv, tt) : f == 1;
@@ -351,8 +361,8 @@ __device__ __forceinline__ uint32_t bin_walk_supers(const CamParams &c, const fl
 // and (boxes of at most MASK_MAX tiles) its pass mask in m (same on every lane).
 template <int MODE>
 __device__ __forceinline__ uint32_t bin_walk_box(const CamParams &c, const float *g, const float4 gv,
-                                                 const float2 half, const float *__restrict__ table, int tx0,
-                                                 int ty0, int bw, uint32_t nb, uint32_t gid, uint32_t base,
+                                                 const float2 half, const float *__restrict__ table, float mzf,
+                                                 int tx0, int ty0, int bw, uint32_t nb, uint32_t gid, uint32_t base,
                                                  uint32_t m[8], uint32_t *__restrict__ list,
                                                  uint32_t *__restrict__ out_tile, uint32_t *__restrict__ out_gid) {
     const int lane = threadIdx.x & 31;
@@ -368,7 +378,8 @@ __device__ __forceinline__ uint32_t bin_walk_box(const CamParams &c, const float
         uint32_t tile = 0;
         if (k0 + (uint32_t)lane < nb) {
             tile = (uint32_t)((ty0 + qy) * c.tiles_x + tx0 + qx);
-            const float *tt = table + 6 * (size_t)tile;
+            float tt[6];
+            tile_record(table, tile, mzf, tt);
             if (cone_prefilter(gv, half, tt)) {
                 const int f = rule_test_fast(g, gv, tt);
                 tp = f == 2 ? rule_test(g, gv, tt) : f == 1;
@@ -404,7 +415,8 @@ __global__ void __launch_bounds__(32 * BIN_WARPS, 3) bin_kernel(CamParams c, con
                                                                 const uint8_t *__restrict__ gflag,
                                                                 const float *__restrict__ table,
                                                                 const float *__restrict__ super,
-                                                                const float *__restrict__ mcam, int64_t n,
+                                                                const float *__restrict__ mcam, float mzf,
+                                                                int64_t n,
                                                                 const uint32_t *__restrict__ order,
                                                                 const uint32_t *__restrict__ offsets,
                                                                 uint32_t *__restrict__ counts,
@@ -542,7 +554,8 @@ __global__ void __launch_bounds__(32 * BIN_WARPS, 3) bin_kernel(CamParams c, con
                 const float gg[6] = {s_g[wid][0][sl], s_g[wid][1][sl], s_g[wid][2][sl], s_g[wid][3][sl],
                                      s_g[wid][4][sl], 1.0f};
                 const float4 sgv = s_gv[wid][sl];
-                const float *tt = table + 6 * (size_t)tile;
+                float tt[6];
+                tile_record(table, tile, mzf, tt);
                 if (cone_prefilter(sgv, s_half[wid][sl], tt)) {
                     const int f = rule_test_fast(gg, sgv, tt);
                     tp = f == 2 ? rule_test(gg, sgv, tt) : f == 1;
@@ -601,8 +614,8 @@ __global__ void __launch_bounds__(32 * BIN_WARPS, 3) bin_kernel(CamParams c, con
             lo = __shfl_sync(0xffffffffu, lo, 0);
             if (lo + bnb <= bcap) lst = blist + lo;
         }
-        const uint32_t wc = bin_walk_box<MODE>(c, gg, sgv, sh, table, btx0, bty0, bw, bnb, sgid, sbase, wm, lst,
-                                               out_tile, out_gid);
+        const uint32_t wc = bin_walk_box<MODE>(c, gg, sgv, sh, table, mzf, btx0, bty0, bw, bnb, sgid, sbase, wm,
+                                               lst, out_tile, out_gid);
         if (lane == sl) {
             cnt = wc;
 #pragma unroll
@@ -640,7 +653,8 @@ __global__ void __launch_bounds__(32 * BIN_WARPS, 3) bin_kernel(CamParams c, con
         sh.x = __shfl_sync(0xffffffffu, half.x, sl); sh.y = __shfl_sync(0xffffffffu, half.y, sl);
         const uint32_t sgid = __shfl_sync(0xffffffffu, gid, sl);
         const uint32_t sbase = __shfl_sync(0xffffffffu, base, sl);
-        const uint32_t wc = bin_walk_supers<MODE>(c, gg, sgv, sh, table, super, sgid, sbase, out_tile, out_gid);
+        const uint32_t wc =
+            bin_walk_supers<MODE>(c, gg, sgv, sh, table, super, mzf, sgid, sbase, out_tile, out_gid);
         if (lane == sl) cnt = wc;
     }
     if (MODE == 0 && have) {
@@ -689,23 +703,24 @@ cudaError_t launch_gauss_view_rule(const CamParams &c, const SceneParams &sp, fl
 
 cudaError_t launch_bin_count(const CamParams &c, const float *binrec, const float4 *gview, const float2 *gcone,
                              const uint8_t *gflag, const float *table, const float *super, const float *mcam,
-                             int64_t n, uint32_t *counts, uint4 *cache, uint32_t *blist,
+                             float mzf, int64_t n, uint32_t *counts, uint4 *cache, uint32_t *blist,
                              unsigned long long *bcursor, unsigned long long bcap, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     bin_kernel<0><<<(unsigned)div_up(n, 32 * BIN_WARPS), 32 * BIN_WARPS, 0, s>>>(
-        c, binrec, gview, gcone, gflag, table, super, mcam, n, nullptr, nullptr, counts, cache, blist, bcursor, bcap,
-        nullptr, nullptr);
+        c, binrec, gview, gcone, gflag, table, super, mcam, mzf, n, nullptr, nullptr, counts, cache, blist, bcursor,
+        bcap, nullptr, nullptr);
     note_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_bin_emit(const CamParams &c, const float *binrec, const float4 *gview, const float2 *gcone,
                             const uint8_t *gflag, const float *table, const float *super, const float *mcam,
-                            int64_t n_sorted, const uint32_t *order, const uint32_t *offsets, const uint4 *cache,
-                            const uint32_t *blist, uint32_t *out_tile, uint32_t *out_gid, cudaStream_t s) {
+                            float mzf, int64_t n_sorted, const uint32_t *order, const uint32_t *offsets,
+                            const uint4 *cache, const uint32_t *blist, uint32_t *out_tile, uint32_t *out_gid,
+                            cudaStream_t s) {
     if (n_sorted == 0) return cudaSuccess;
     bin_kernel<1><<<(unsigned)div_up(n_sorted, 32 * BIN_WARPS), 32 * BIN_WARPS, 0, s>>>(
-        c, binrec, gview, gcone, gflag, table, super, mcam, n_sorted, order, offsets, nullptr,
+        c, binrec, gview, gcone, gflag, table, super, mcam, mzf, n_sorted, order, offsets, nullptr,
         const_cast<uint4 *>(cache), const_cast<uint32_t *>(blist), nullptr, 0ull, out_tile, out_gid);
     note_launches(1);
     return cudaGetLastError();

@@ -179,6 +179,7 @@ __device__ bool tstar_bound(float kap, float s2, float r1, float L, float m, flo
 
 // Per view: binning direction/depth (the FP32 rule) and the raster record.
 __global__ void __launch_bounds__(256) view_records_kernel(CamParams c, SceneParams sp, const float *__restrict__ mcam,
+                                                           float mzf,
                                                            float4 *__restrict__ rec, float4 *__restrict__ gview,
                                                            float2 *__restrict__ gcone,
                                                            uint8_t *__restrict__ gflag) {
@@ -211,7 +212,7 @@ __global__ void __launch_bounds__(256) view_records_kernel(CamParams c, ScenePar
         col[ch] = fmaxf(acc + 0.5f, 0.0f);
     }
     const float rho2 = sp.rho2 ? sp.rho2[i] : 0.0f;
-    const float m = *mcam;
+    const float m = fmaxf(*mcam, mzf);   // footprint bound (raised for the z/f variant)
     // binning prefilter: the cone of the binning rule's own bound (its kappa and
     // scale bounds), camera-wide footprint, wide margin
     const float *br = sp.binrec + 6 * i;
@@ -253,10 +254,10 @@ cudaError_t launch_scene_cache(const SceneParams &sp, float *W, float *sig_eff, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_view_records(const CamParams &c, const SceneParams &sp, const float *mcam, float4 *rec,
-                                float4 *gview, float2 *gcone, uint8_t *gflag, cudaStream_t s) {
+cudaError_t launch_view_records(const CamParams &c, const SceneParams &sp, const float *mcam, float mzf,
+                                float4 *rec, float4 *gview, float2 *gcone, uint8_t *gflag, cudaStream_t s) {
     if (sp.n == 0) return cudaSuccess;
-    view_records_kernel<<<(unsigned)div_up(sp.n, 256), 256, 0, s>>>(c, sp, mcam, rec, gview, gcone, gflag);
+    view_records_kernel<<<(unsigned)div_up(sp.n, 256), 256, 0, s>>>(c, sp, mcam, mzf, rec, gview, gcone, gflag);
     note_launches(1);
     return cudaGetLastError();
 }

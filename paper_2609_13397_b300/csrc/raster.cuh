@@ -15,7 +15,47 @@ struct RasterArgs {
     uint32_t *last;        // per pixel: list entries up to and including the last contributor
     unsigned long long *evaluated;   // optional (profiling): [0] list entries walked, [1] full evaluations
     int additive;
+    int footprint;         // 0: the pixel's own differentials; 1: isotropic reduction; 2: z/f sizing
+    float zax[3];          // z/f: optical axis (world); zf_scale = 1 / (2 f_x)
+    float zf_scale;
 };
+
+constexpr int FOOTPRINT_OWN = 0, FOOTPRINT_ISO = 1, FOOTPRINT_ZF = 2;
+
+// Isotropic footprint variants: the half-edge differentials become a b1, a b2
+// with (b1, b2) orthonormal across d (b1 from the coordinate axis least aligned
+// with d), a^2 = (|dx_perp|^2 + |dy_perp|^2) / 2 (ISO) or a = |<d, z_cam>| / (2 f_x) (ZF).
+__device__ __forceinline__ void isotropic_differentials(const RasterArgs &a, PixelRays &px) {
+    const float *d = px.d;
+    float s2;
+    if (a.footprint == FOOTPRINT_ISO) {
+        const float sx = dot3(d, px.dx), sy = dot3(d, px.dy);
+        float n2 = 0.f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float ux = px.dx[k] - sx * d[k], uy = px.dy[k] - sy * d[k];
+            n2 += ux * ux + uy * uy;
+        }
+        s2 = 0.5f * n2;
+    } else {
+        const float z = d[0] * a.zax[0] + d[1] * a.zax[1] + d[2] * a.zax[2];
+        s2 = (z * a.zf_scale) * (z * a.zf_scale);
+    }
+    const float ax = fabsf(d[0]), ay = fabsf(d[1]), az = fabsf(d[2]);
+    float b1[3] = {0.f, 0.f, 0.f};
+    if (ax <= ay && ax <= az) b1[0] = 1.f; else if (ay <= az) b1[1] = 1.f; else b1[2] = 1.f;
+    const float s = dot3(b1, d);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) b1[k] -= s * d[k];
+    const float rn = rsqrtf(dot3(b1, b1));
+    const float am = sqrtf(s2);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) b1[k] *= rn;
+    px.dx[0] = am * b1[0]; px.dx[1] = am * b1[1]; px.dx[2] = am * b1[2];
+    px.dy[0] = am * (d[1] * b1[2] - d[2] * b1[1]);
+    px.dy[1] = am * (d[2] * b1[0] - d[0] * b1[2]);
+    px.dy[2] = am * (d[0] * b1[1] - d[1] * b1[0]);
+}
 
 __device__ __forceinline__ void load_pixel(const RasterArgs &a, int64_t pix, int64_t P, PixelRays &px) {
 #pragma unroll
@@ -24,6 +64,7 @@ __device__ __forceinline__ void load_pixel(const RasterArgs &a, int64_t pix, int
         px.dx[k] = a.dx[k * P + pix];
         px.dy[k] = a.dy[k * P + pix];
     }
+    if (a.footprint != FOOTPRINT_OWN) isotropic_differentials(a, px);
     px.d_dx = dot3(px.d, px.dx);
     px.d_dy = dot3(px.d, px.dy);
     px.dxdx = dot3(px.dx, px.dx);

@@ -43,27 +43,30 @@ def _case(name):
 
 @pytest.mark.parametrize("name,mode", [("pinhole", "aniso"), ("floor", "aniso"), ("coarse_floor", "aniso"),
                                        ("fisheye", "aniso"), ("pinhole", "filter_none"),
-                                       ("coarse_floor", "additive")])
+                                       ("coarse_floor", "additive"), ("coarse_floor", "iso"), ("fisheye", "zf")])
 def test_backward_matches_gradient_oracle(cg, oracle_lib, name, mode):
     from oracle import grad as G
     cam, sc = _case(name)
     filt = mode != "filter_none"
     add = mode == "additive"
+    fp = mode if mode in ("iso", "zf") else "own"
+    cfilt = {"own": int(filt), "iso": oracle_lib.FILTER_ISO, "zf": oracle_lib.FILTER_ZF}[fp]
     rng = np.random.default_rng(7)
     P = cam.n_pixels
     w_rgb = rng.normal(size=(P, 3))
     w_T = rng.normal(size=P)
-    ref = oracle_lib.render(cam, sc, filter=int(filt), comp=int(add), eps=2e-4)
+    ref = oracle_lib.render(cam, sc, filter=cfilt, comp=int(add), eps=2e-4)
     flagged = ref.flags != 0
     w_rgb[flagged] = 0.0
     w_T[flagged] = 0.0
-    _, g_ref = G.loss_and_grad(cam, sc, np.arange(P), w_rgb, w_T, filter_on=filt, additive=add)
+    _, g_ref = G.loss_and_grad(cam, sc, np.arange(P), w_rgb, w_T, filter_on=filt, additive=add, footprint=fp)
 
     ctx = cg.Context(0)
     ctx.set_scene_from(sc)
     v = ctx.view()
     v.set_camera_from(cam)
     flags = cg.KEEP_FOR_BACKWARD | (0 if filt else cg.FILTER_NONE) | (cg.COMP_ADDITIVE if add else 0)
+    flags |= {"own": 0, "iso": cg.FILTER_ISO, "zf": cg.FILTER_ZF}[fp]
     rgb, T = v.render(flags=flags)
     dL_drgb = torch.from_numpy(w_rgb.T.reshape(3, cam.height, cam.width).astype(np.float32)).cuda()
     dL_dT = torch.from_numpy(w_T.reshape(cam.height, cam.width).astype(np.float32)).cuda()

@@ -162,6 +162,30 @@ def test_render_variants(cg, oracle_lib, mode):
     assert err <= TOL and errT <= TOL, (err, errT)
 
 
+@pytest.mark.parametrize("name", ["blob320", "wide_surround", "kb_surround", "kb160"])
+@pytest.mark.parametrize("variant", ["iso", "zf"])
+def test_isotropic_footprint_variants(cg, oracle_lib, name, variant):
+    """FILTER_ISO / FILTER_ZF against the oracle's variants: images within the
+    FP32 tolerance; pair lists bit-exact with the binning rule (for z/f with the
+    tiles' footprint bound raised to 1/(6 f_x^2), which keeps the rule conservative
+    for the z/f footprint)."""
+    cam, sc = CASES[name]
+    sc = _with_floor(oracle_lib, name, cam, sc)
+    flags, filt = ((cg.FILTER_ISO, oracle_lib.FILTER_ISO) if variant == "iso"
+                   else (cg.FILTER_ZF, oracle_lib.FILTER_ZF))
+    err, errT, nflag, npx = _render_compare(cg, oracle_lib, cam, sc, flags=flags, filt=filt)
+    assert nflag <= 0.02 * npx
+    assert err <= TOL and errT <= TOL, (err, errT)
+    ctx, v = _setup(cg, cam, sc)
+    v.render(flags=flags)
+    pg, pt = (t.cpu().numpy() for t in v.bin_counts())
+    total, opg, opt, _ = oracle_lib.bin_counts(cam, sc, zf=variant == "zf")
+    assert np.array_equal(pg, opg) and np.array_equal(pt, opt)
+    with pytest.raises(cg.ConegsError) as e:
+        v.render(flags=cg.FILTER_ISO | cg.FILTER_ZF)
+    assert e.value.status == 1
+
+
 def test_render_deterministic(cg):
     cam, sc = CASES["blob320"]
     ctx, v = _setup(cg, cam, sc)

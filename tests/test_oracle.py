@@ -399,3 +399,112 @@ def test_fig2_anisotropic_beats_centre_ray_offaxis_fisheye(oracle_lib):
         trials += 1
         wins += abs(an - ref) < abs(ce - ref)
     assert trials >= 20 and wins >= 0.8 * trials
+
+
+# ---------------------------------------------------------------- isotropic footprint variants
+
+@pytest.mark.parametrize("which", ["pinhole", "kb"])
+@pytest.mark.parametrize("variant", ["iso", "zf"])
+def test_isotropic_variants_closed_form(oracle_lib, which, variant):
+    """An isotropic Gaussian (W = I/s) under a footprint isotropic across the ray
+    (half-edge a b_i, b_i orthonormal across d): Sigma_fp^u = c M_perp with
+    c = t*^2 a^2 / (3 s^2) (Eq. 6, 8), so A = I + c M_perp gives
+    T = sigma / (1 + c) exp(-D^2 / (2 (1 + c))) (Eq. 9), with t* = <mu - o, d> and
+    D the centre ray's distance over s.  a: the pixel's own differentials
+    (iso: a^2 = (|dx_perp|^2 + |dy_perp|^2)/2) or the paraxial z/f size
+    (zf: a = |<d, z_cam>| / (2 f_x))."""
+    O = oracle_lib
+    if which == "pinhole":
+        cam = S.pinhole(160, 120, 90.0, 71.3, 66.2, cam_to_world=S.look_at((0.1, 0.0, -0.2), (0.6, 0.3, 4.0)))
+    else:
+        cam = S.c3_camera(128, 128)
+        cam.cam_to_world = S.look_at((0.0, 0.1, 0.0), (0.4, -0.2, 3.0))
+    R = cam.cam_to_world[:, :3].astype(float)
+    o = cam.cam_to_world[:, 3].astype(float)
+    rng = np.random.default_rng(11)
+    checked = 0
+    for _ in range(30):
+        x, y = rng.uniform(5, cam.width - 5), rng.uniform(5, cam.height - 5)
+        d, dx, dy, valid = O.rays(cam, np.array([x]), np.array([y]))
+        if not valid[0]:
+            continue
+        d, dx, dy = d[0], dx[0], dy[0]
+        t_true = rng.uniform(2.0, 5.0)
+        s = rng.uniform(0.01, 0.05)
+        mu = o + t_true * d + rng.normal(0, 1.5 * s, 3)
+        logit = 0.7
+        p = O.pair(cam, x, y, mu, np.log([s, s, s]), [1.0, 0.0, 0.0, 0.0], logit,
+                   filter=O.FILTER_ISO if variant == "iso" else O.FILTER_ZF, comp=O.COMP_ADDITIVE)
+        v = mu - o
+        ts = float(v @ d)
+        D2 = float((v - ts * d) @ (v - ts * d)) / s ** 2
+        if variant == "iso":
+            px, py = dx - (d @ dx) * d, dy - (d @ dy) * d
+            a2 = 0.5 * (px @ px + py @ py)
+        else:
+            a2 = float(d @ R[:, 2]) ** 2 / (4.0 * cam.fx ** 2)
+        c = ts ** 2 * a2 / (3.0 * s ** 2)
+        sig = 1.0 / (1.0 + math.exp(-logit))
+        want = sig / (1.0 + c) * math.exp(-0.5 * D2 / (1.0 + c))
+        # the camera's rotation is stored in FP32, so its rays are unit to ~1e-7
+        assert abs(p["T"] - want) <= 1e-6 * want + 1e-300, (p["T"], want)
+        checked += 1
+    assert checked >= 15
+
+
+def test_zf_sizing_over_dilates_offaxis_pinhole(oracle_lib):
+    """Pinhole: a pixel at angle theta from the axis spans cos^2(theta)/f radially
+    and cos(theta)/f tangentially, so the paraxial z/f size (cos(theta)/f on both
+    axes) exceeds the true footprint's isotropic reduction off axis and matches
+    it on axis (to O(1/f^2))."""
+    O = oracle_lib
+    cam = S.pinhole(801, 601, 300.0, 400.5, 300.5)
+    xs = np.array([400.5, 500.5, 650.5, 790.5])
+    ys = np.array([300.5, 300.5, 420.5, 590.5])
+    d, dx, dy, _ = O.rays(cam, xs, ys)
+    a_iso, a_zf = [], []
+    for k in range(len(xs)):
+        px, py = dx[k] - (d[k] @ dx[k]) * d[k], dy[k] - (d[k] @ dy[k]) * d[k]
+        a_iso.append(math.sqrt(0.5 * (px @ px + py @ py)))
+        a_zf.append(abs(d[k][2]) / (2.0 * cam.fx))
+    assert abs(a_zf[0] - a_iso[0]) <= 1e-4 * a_iso[0]
+    ratio = np.array(a_zf) / np.array(a_iso)
+    assert np.all(np.diff(ratio) > 0) and ratio[-1] > 1.1
+
+
+def test_fig2_variant_errors_against_supersampled_pixel(oracle_lib):
+    """Fig. 2(c,d) error study over the filter variants: single anisotropic
+    Gaussians seen by a fisheye, responses against the 32x32 supersampled pixel
+    at three eccentricity bands.  The anisotropic footprint has the lowest mean
+    error in every band; the centre ray and the paraxial z/f sizing are far
+    worse, z/f increasingly so off axis; the isotropic reduction trails the
+    anisotropic footprint where footprints shear (the outer band)."""
+    O = oracle_lib
+    cam = S.Camera(S.KB_FISHEYE, 96, 96, 30.0, 30.0, 48.0, 48.0, np.array([0.01, -0.004, 0.0, 0.0]),
+                   theta_lim=1.55)
+    rng = np.random.default_rng(7)
+    means = {}
+    for band in ((0, 30), (30, 62), (62, 80)):
+        err = {k: [] for k in ("centre", "zf", "iso", "aniso")}
+        for _ in range(40):
+            th = rng.uniform(math.radians(band[0]), math.radians(band[1]))
+            ph = rng.uniform(0, 2 * math.pi)
+            dist = rng.uniform(2, 4)
+            mu = dist * np.array([math.sin(th) * math.cos(ph), math.sin(th) * math.sin(ph), math.cos(th)])
+            px, py = _project(cam, mu[None])
+            x, y = float(np.floor(px[0])) + 0.5, float(np.floor(py[0])) + 0.5
+            s = dist * 0.6 / 30.0
+            ls = np.log([s, 0.5 * s, 0.8 * s])
+            q = rng.standard_normal(4)
+            ref = O.bundle(cam, x, y, mu, ls, q, 1.0, nsub=32)
+            if ref < 1e-3:
+                continue
+            for k, f in (("centre", O.FILTER_NONE), ("zf", O.FILTER_ZF), ("iso", O.FILTER_ISO),
+                         ("aniso", O.FILTER_ANISO)):
+                err[k].append(abs(O.pair(cam, x, y, mu, ls, q, 1.0, filter=f)["T"] - ref) / ref)
+        assert len(err["aniso"]) >= 25
+        means[band] = {k: float(np.mean(v)) for k, v in err.items()}
+    for band, m in means.items():
+        assert m["aniso"] < m["zf"] and m["aniso"] < m["centre"] and m["aniso"] <= m["iso"] * 1.02, (band, m)
+    assert means[(62, 80)]["aniso"] < 0.9 * means[(62, 80)]["iso"]
+    assert means[(62, 80)]["zf"] > 2.0 * means[(0, 30)]["zf"]
