@@ -157,6 +157,19 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def reduce_step_time(ms: float, device) -> float:
+    """The slowest rank's step time: every rank waits for it, so the whole job's
+    rate is all ranks' rays over this (MAX over the process group; the local time
+    when not distributed)."""
+    import torch
+    import torch.distributed as tdist
+    if not (tdist.is_available() and tdist.is_initialized()) or tdist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_2609_13397_b300 as cg
@@ -206,25 +219,23 @@ def run_ours(args, rank, world, local_rank):
                  "ms_sort": [],
                  "ms_total": [],
                  "n_pairs": [], "n_visible": []} for _ in views]
-    launches = 0
     with ClockSampler(local_rank) as clk:
         for k in range(args.steps):
             flush.fill_(float(k))
             ev[k][0].record(main)
             step(flags=cg.PROFILE)
             ev[k][1].record(main)
-            for v, pv in zip(views, per_view):
-                st = v.stats()
-                for key in pv:
-                    pv[key].append(st[key])
-                launches += st["n_launches"]
         torch.cuda.synchronize()
+    # per-view stage times and counters of the last timed step (read after the loop,
+    # so that no host wait separates the timed steps)
+    launches = 0
+    for v, pv in zip(views, per_view):
+        st = v.stats()
+        for key in pv:
+            pv[key].append(st[key])
+        launches += st["n_launches"] * args.steps
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    ms = sum(step_ms) / len(step_ms)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_step_time(sum(step_ms) / len(step_ms), dev)
     value = rays_per_step * world / (ms * 1e-3) / 1e6
 
     # forward + backward (adjoint) rate on the same workload, when the adjoint is built
@@ -250,7 +261,7 @@ def run_ours(args, rank, world, local_rank):
             fb_step()
         e1.record(main)
         torch.cuda.synchronize()
-        fb_ms = e0.elapsed_time(e1) / args.steps
+        fb_ms = reduce_step_time(e0.elapsed_time(e1) / args.steps, dev)
         fwd_bwd = {"value": rays_per_step * world / (fb_ms * 1e-3) / 1e6, "unit": "Mrays/s", "ms_per_step": fb_ms}
     except cg.ConegsError as e:
         fwd_bwd = {"value": None, "unavailable": str(e)[:120]}
@@ -259,9 +270,11 @@ def run_ours(args, rank, world, local_rank):
     host = [(torch.empty(3, c.height, c.width, pin_memory=True), torch.empty(c.height, c.width, pin_memory=True))
             for c in cams]
     def e2e_step():
-        for v, c, st, (h_rgb, h_T) in zip(views, cams, streams, host):
+        """Cameras in from host parameters, both views rendered in one batch call whose
+        images land in pinned host memory (conegs_render_host_batch)."""
+        for v, c, st in zip(views, cams, streams):
             v.set_camera_from(c, stream=st)
-            v.render_host(h_rgb, h_T, stream=st)
+        ctx.render_host_batch(views, host, streams=streams)
     for _ in range(2):
         e2e_step()
     torch.cuda.synchronize()
@@ -269,7 +282,7 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(args.steps):
         e2e_step()
     torch.cuda.synchronize()
-    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    e2e_ms = reduce_step_time((time.perf_counter() - t0) * 1e3 / args.steps, dev)
     h2d = len(cams) * (4 + 4 + 12) * 4
     d2h = sum(4 * 4 * c.width * c.height for c in cams)
 

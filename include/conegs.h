@@ -179,6 +179,14 @@ conegs_status conegs_render(conegs_view *view, float *out_rgb, float *out_T, uns
 conegs_status conegs_render_batch(int n, conegs_view *const *views, float *const *out_rgb, float *const *out_T,
                                   unsigned flags, void *const *streams);
 
+/* conegs_render_batch into host memory: each view renders into its own device
+ * scratch and its image is copied to out_rgb_host[i] (and out_T_host[i], when
+ * out_T_host and that entry are non-NULL) on streams[i]; returns after every
+ * copy has completed.  Host buffers should be pinned for asynchronous copies.
+ * Errors as conegs_render_batch. */
+conegs_status conegs_render_host_batch(int n, conegs_view *const *views, float *const *out_rgb_host,
+                                       float *const *out_T_host, unsigned flags, void *const *streams);
+
 /* Same as conegs_render, with HOST output buffers (pinned memory recommended):
  * renders into view-owned device memory and copies the result back on
  * `stream`; returns after the copy has completed. */

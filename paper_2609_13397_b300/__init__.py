@@ -128,6 +128,18 @@ class Context:
         check(lib().conegs_render_batch(n, hv, rgb, Ts, flags, st), "render_batch")
         return list(outs)
 
+    def render_host_batch(self, views: Sequence["View"], host_outs, flags: int = 0, streams=None):
+        """render_batch into (pinned) host tensors [(rgb, T or None)] per view; returns
+        after every copy completed."""
+        n = len(views)
+        P = ctypes.c_void_p
+        hv = (P * n)(*[v._h for v in views])
+        rgb = (P * n)(*[_ptr(o[0]) for o in host_outs])
+        Ts = (P * n)(*[_ptr(o[1]) for o in host_outs])
+        st = (P * n)(*[_stream(None if streams is None else streams[i]) for i in range(n)])
+        check(lib().conegs_render_host_batch(n, hv, rgb, Ts, flags, st), "render_host_batch")
+        return list(host_outs)
+
     def compute_floor(self, views: Sequence["View"], stream=None) -> torch.Tensor:
         """Eq. 11 training-frequency floor of the current scene's Gaussians over ``views``."""
         out = torch.empty(self.n, device=self.device, dtype=torch.float32)

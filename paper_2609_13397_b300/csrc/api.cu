@@ -690,6 +690,40 @@ conegs_status conegs_render_batch(int n, conegs_view *const *views, float *const
     return st;
 }
 
+conegs_status conegs_render_host_batch(int n, conegs_view *const *views, float *const *out_rgb_host,
+                                       float *const *out_T_host, unsigned flags, void *const *streams) {
+    if (n < 0 || (n > 0 && (!views || !out_rgb_host))) return fail(CONEGS_ERR_ARG, "render_host_batch: bad argument");
+    if (n == 0) return CONEGS_OK;
+    std::vector<float *> drgb((size_t)n), dT((size_t)n);
+    for (int i = 0; i < n; ++i) {
+        if (!views[i] || !out_rgb_host[i]) return fail(CONEGS_ERR_ARG, "render_host_batch: NULL view or output %d", i);
+        if (!views[i]->has_cam) return fail(CONEGS_ERR_STATE, "render_host_batch: view %d has no camera", i);
+        conegs_view *v = views[i];
+        DeviceGuard g(v->ctx->device);
+        const cudaStream_t s = streams ? (cudaStream_t)streams[i] : (cudaStream_t)0;
+        const size_t P = (size_t)v->cam.W * v->cam.H;
+        TRY(view_begin(v, s));
+        TRY(ensure(v->ctx, v->tmp_rgb, sizeof(float) * 3 * P, s));
+        TRY(ensure(v->ctx, v->tmp_T, sizeof(float) * P, s));
+        TRY(view_end(v, s));
+        drgb[(size_t)i] = v->tmp_rgb.as<float>();
+        dT[(size_t)i] = v->tmp_T.as<float>();
+    }
+    TRY(conegs_render_batch(n, views, drgb.data(), dT.data(), flags, streams));
+    DeviceGuard g(views[0]->ctx->device);
+    for (int i = 0; i < n; ++i) {
+        conegs_view *v = views[i];
+        const cudaStream_t s = streams ? (cudaStream_t)streams[i] : (cudaStream_t)0;
+        const size_t P = (size_t)v->cam.W * v->cam.H;
+        CUDA_TRY(cudaMemcpyAsync(out_rgb_host[i], v->tmp_rgb.p, sizeof(float) * 3 * P, cudaMemcpyDeviceToHost, s));
+        if (out_T_host && out_T_host[i])
+            CUDA_TRY(cudaMemcpyAsync(out_T_host[i], v->tmp_T.p, sizeof(float) * P, cudaMemcpyDeviceToHost, s));
+        TRY(view_end(v, s));
+    }
+    for (int i = 0; i < n; ++i) CUDA_TRY(cudaStreamSynchronize(streams ? (cudaStream_t)streams[i] : (cudaStream_t)0));
+    return CONEGS_OK;
+}
+
 conegs_status conegs_render_host(conegs_view *v, float *out_rgb_host, float *out_T_host, unsigned flags,
                                  void *stream) {
     if (!v || !out_rgb_host) return fail(CONEGS_ERR_ARG, "render_host: NULL argument");

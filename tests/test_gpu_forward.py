@@ -316,3 +316,21 @@ def test_render_batch_equals_single_renders(cg):
     with pytest.raises(cg.ConegsError) as e:
         ctx.render_batch([views[0], views[0]])
     assert e.value.status == 1
+
+
+def test_render_host_batch_equals_device_render(cg):
+    sc = S.blob_scene(5000, seed=6, cam=S.pinhole(160, 90, 150.0))
+    ctx = cg.Context(0)
+    ctx.set_scene_from(sc)
+    cams = [S.pinhole(160, 90, 150.0), S.c3_camera(48, 40)]
+    views = []
+    for c in cams:
+        v = ctx.view()
+        v.set_camera_from(c)
+        views.append(v)
+    dev = [v.render() for v in views]
+    host = [(torch.empty(3, c.height, c.width, pin_memory=True), torch.empty(c.height, c.width, pin_memory=True))
+            for c in cams]
+    ctx.render_host_batch(views, host, streams=[torch.cuda.Stream() for _ in views])
+    for (r, t), (hr, ht) in zip(dev, host):
+        assert torch.equal(r.cpu(), hr) and torch.equal(t.cpu(), ht)
