@@ -176,8 +176,9 @@ class Render:
 
 def render(cam, scene, pix: Optional[Sequence[int]] = None, filter: int = FILTER_ANISO,
            comp: int = COMP_MARGINAL, cull: bool = True, eps: float = 1e-5, eps_key: float = 0.0,
-           max_used: int = 0) -> Render:
-    """Render pixels (indices into the row-major W x H grid; None = all)."""
+           max_used: int = 0, order: int = 0) -> Render:
+    """Render pixels (indices into the row-major W x H grid; None = all).  order: 0
+    the canonical per-Gaussian key |mu - o|, 1 the exact per-ray t* order."""
     n = scene.n
     if pix is None:
         npix, pix_arr, pptr = cam.width * cam.height, None, None
@@ -194,8 +195,26 @@ def render(cam, scene, pix: Optional[Sequence[int]] = None, filter: int = FILTER
                     ctypes.c_int(scene.sh_degree), _p(_d(scene.rho2)), ctypes.c_int(filter), ctypes.c_int(comp),
                     ctypes.c_int(npix), pptr, ctypes.c_int(int(cull)), ctypes.c_double(eps),
                     ctypes.c_double(eps_key), _p(rgb), _p(T), _p(flags, ctypes.c_int), _p(ncon, ctypes.c_int),
-                    _p(used, ctypes.c_int) if max_used > 0 else None, ctypes.c_int(max_used))
+                    _p(used, ctypes.c_int) if max_used > 0 else None, ctypes.c_int(max_used), ctypes.c_int(order))
     return Render(rgb, T, flags, ncon, pix_arr, used if max_used > 0 else None)
+
+
+def render_subrays(cam, scene, pix: Optional[Sequence[int]] = None, nsub: int = 8, order: int = 0):
+    """Dense sub-ray reference: nsub x nsub centre rays per pixel, each composited on
+    its own (centre-ray responses), averaged.  Returns (rgb [n,3], T [n])."""
+    n = scene.n
+    if pix is None:
+        npix, pptr = cam.width * cam.height, None
+    else:
+        pix_arr = np.ascontiguousarray(np.asarray(pix, np.int32))
+        npix, pptr = pix_arr.size, _p(pix_arr, ctypes.c_int)
+    rgb = np.zeros((npix, 3))
+    T = np.zeros(npix)
+    lib().or_render_subrays(_p(pack_camera(cam)), ctypes.c_int(n), _p(_d(scene.means)), _p(_d(scene.log_scales)),
+                            _p(_d(scene.quats)), _p(_d(scene.opacity_logits)), _p(_d(scene.sh)),
+                            ctypes.c_int(scene.sh_degree), _p(_d(scene.rho2)), ctypes.c_int(npix), pptr,
+                            ctypes.c_int(nsub), ctypes.c_int(order), _p(rgb), _p(T))
+    return rgb, T
 
 
 def pairs_above(cam, scene, thr: float, cap: int = 10_000_000):
