@@ -498,12 +498,26 @@ def run_config(args):
         srv.drain(len(warm))
         srv.results.clear()
         res = srv.play(reqs, realtime=True)
-        srv.close()
         st = serving.summarize(res)
+        # rate sweep: Poisson streams of about 4 s at each rate; a rate is sustained while
+        # requests do not queue up: p99 latency below 0.5 s
+        sweep = []
+        for k, rate in enumerate(float(x) for x in args.c5_sweep.split(",") if x):
+            rq = [serving.Request(20_000 * (k + 1) + r.rid, r.arrival_s, r.camera)
+                  for r in S.c5_requests(max(40, int(4 * rate)), rate_hz=rate, seed=100 + k)]
+            srv.results.clear()
+            sr = serving.summarize(srv.play(rq, realtime=True))
+            offered = sum(r.camera.n_pixels for r in rq) / max(r.arrival_s for r in rq) / 1e6
+            sweep.append({"rate_hz": rate, "offered_mpx_per_s": offered, "mrays_per_s": sr.get("mrays_per_s"),
+                          "p50_ms": sr.get("p50_ms"), "p99_ms": sr.get("p99_ms"), "requests": sr["requests"],
+                          "errors": sr["errors"]})
+        srv.close()
+        ok = [w["rate_hz"] for w in sweep if w["p99_ms"] is not None and w["p99_ms"] < 500.0]
         _line(st["mrays_per_s"], st["mean_ms"], args,
               f"C5: serving, {args.c5_gaussians} Gaussians resident, SH3 FP16, Poisson {args.c5_rate} req/s, "
               f"W=round(160*24^u) H=round(120*18^u), zoom 8^U(-1,1), pinhole/KB 50/50, {args.c5_slots} slots",
-              {"serving": st, "dtype_storage": "f16"})
+              {"serving": st, "dtype_storage": "f16", "sweep": sweep,
+               "sustainable_rate_hz": max(ok) if ok else None})
         return
 
 
@@ -521,6 +535,7 @@ def main():
     ap.add_argument("--c5-rate", type=float, default=200.0)
     ap.add_argument("--c5-slots", type=int, default=6)
     ap.add_argument("--c5-gaussians", type=int, default=5_000_000)
+    ap.add_argument("--c5-sweep", default="50,100,125,150", help="request rates (Hz) of the C5 rate sweep")
     ap.add_argument("--probe", choices=["raster", "raster-1/8", "backward"], default=None,
                     help="set up C2 and render 3 times for a profiler capture (prints no JSON)")
     args = ap.parse_args()
