@@ -495,8 +495,6 @@ static conegs_status render_front(conegs_view *v, unsigned flags, cudaStream_t s
     conegs_ctx *ctx = v->ctx;
     const CamParams &c = v->cam;
     const int64_t n = ctx->sp.n;
-    const int64_t P = (int64_t)c.W * c.H;
-    const int nt = c.tiles_x * c.tiles_y;
     CUDA_TRY(cudaStreamWaitEvent(s, ctx->scene_ready, 0));
     v->launches0 = launches_so_far();
     const size_t nn = (size_t)std::max<int64_t>(n, 1);
@@ -620,7 +618,6 @@ static conegs_status render_back(conegs_view *v, float *out_rgb, float *out_T, u
     v->last_flags = flags;
     v->has_forward = true;
     v->forward_gen = ctx->scene_gen;
-    (void)P;
     return CONEGS_OK;
 }
 

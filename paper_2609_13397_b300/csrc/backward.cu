@@ -21,6 +21,7 @@
 // sigma = sigmoid(logit), R = R(q/|q|), rgb = max(0, SH(u) + 1/2),
 // u = (mu - o)/|mu - o|.  rho^2 is not differentiated.
 #include "raster.cuh"
+#include "sh.cuh"
 
 namespace conegs {
 
@@ -327,56 +328,6 @@ cudaError_t launch_backward(const RasterArgs &a, int ntiles, bool filter, uint32
 
 // ---------------------------------------------------------------- K7: chain to the scene parameters
 
-// d Y_j / d(x, y, z) of the real SH basis (positive constants, l-major).
-__device__ __forceinline__ void sh_basis_grad(float x, float y, float z, int j, float g[3]) {
-    const float C1 = 0.48860251190291992f, C2A = 1.0925484305920792f, C2B = 0.31539156525252005f,
-                C2C = 0.54627421529603959f, C3A = 0.59004358992664352f, C3B = 2.8906114426405538f,
-                C3C = 0.45704579946446572f, C3D = 0.37317633259011540f, C3E = 1.4453057213202769f;
-    g[0] = g[1] = g[2] = 0.0f;
-    switch (j) {
-        case 1: g[1] = C1; break;
-        case 2: g[2] = C1; break;
-        case 3: g[0] = C1; break;
-        case 4: g[0] = C2A * y; g[1] = C2A * x; break;
-        case 5: g[1] = C2A * z; g[2] = C2A * y; break;
-        case 6: g[2] = 6.f * C2B * z; break;
-        case 7: g[0] = C2A * z; g[2] = C2A * x; break;
-        case 8: g[0] = 2.f * C2C * x; g[1] = -2.f * C2C * y; break;
-        case 9: g[0] = 6.f * C3A * x * y; g[1] = C3A * (3.f * x * x - 3.f * y * y); break;
-        case 10: g[0] = C3B * y * z; g[1] = C3B * x * z; g[2] = C3B * x * y; break;
-        case 11: g[1] = C3C * (5.f * z * z - 1.f); g[2] = 10.f * C3C * y * z; break;
-        case 12: g[2] = C3D * (15.f * z * z - 3.f); break;
-        case 13: g[0] = C3C * (5.f * z * z - 1.f); g[2] = 10.f * C3C * x * z; break;
-        case 14: g[0] = 2.f * C3E * x * z; g[1] = -2.f * C3E * y * z; g[2] = C3E * (x * x - y * y); break;
-        case 15: g[0] = C3A * (3.f * x * x - 3.f * y * y); g[1] = -6.f * C3A * x * y; break;
-        default: break;
-    }
-}
-
-__device__ __forceinline__ float sh_basis_value(float x, float y, float z, int j) {
-    const float Y0 = 0.28209479177387814f, C1 = 0.48860251190291992f, C2A = 1.0925484305920792f,
-                C2B = 0.31539156525252005f, C2C = 0.54627421529603959f, C3A = 0.59004358992664352f,
-                C3B = 2.8906114426405538f, C3C = 0.45704579946446572f, C3D = 0.37317633259011540f,
-                C3E = 1.4453057213202769f;
-    switch (j) {
-        case 0: return Y0;
-        case 1: return C1 * y;
-        case 2: return C1 * z;
-        case 3: return C1 * x;
-        case 4: return C2A * x * y;
-        case 5: return C2A * y * z;
-        case 6: return C2B * (3.f * z * z - 1.f);
-        case 7: return C2A * x * z;
-        case 8: return C2C * (x * x - y * y);
-        case 9: return C3A * y * (3.f * x * x - y * y);
-        case 10: return C3B * x * y * z;
-        case 11: return C3C * y * (5.f * z * z - 1.f);
-        case 12: return C3D * z * (5.f * z * z - 3.f);
-        case 13: return C3C * x * (5.f * z * z - 1.f);
-        case 14: return C3E * z * (x * x - y * y);
-        default: return C3A * x * (x * x - 3.f * y * y);
-    }
-}
 
 __global__ void __launch_bounds__(256) backward_params_kernel(CamParams c, SceneParams sp,
                                                               const float *__restrict__ g_rec,
@@ -455,21 +406,52 @@ __global__ void __launch_bounds__(256) backward_params_kernel(CamParams c, Scene
     float u[3] = {0.f, 0.f, 1.f};
     if (L > 0.0f) { u[0] = v[0] / L; u[1] = v[1] / L; u[2] = v[2] / L; }
     float gu[3] = {0.f, 0.f, 0.f};
+    float act[3];                  // dL/drgb of the channels above the max(0, .) clamp
+    bool any_col = false;
 #pragma unroll
-    for (int ch = 0; ch < 3; ++ch) {
-        const float grgb = gr[13 + ch];
-        if (grgb == 0.0f) continue;
-        float raw = 0.5f;
-        for (int j = 0; j < K; ++j) raw += load_scalar(sp.sh, (i * K + j) * 3 + ch, sp.storage) * sh_basis_value(u[0], u[1], u[2], j);
-        if (!(raw > 0.0f)) continue;
-        for (int j = 0; j < K; ++j) {
-            const float Y = sh_basis_value(u[0], u[1], u[2], j);
-            if (g_sh) g_sh[(i * K + j) * 3 + ch] += grgb * Y;
-            if (j > 0) {
-                float gY[3];
-                sh_basis_grad(u[0], u[1], u[2], j, gY);
-                const float c_j = load_scalar(sp.sh, (i * K + j) * 3 + ch, sp.storage) * grgb;
-                gu[0] += c_j * gY[0]; gu[1] += c_j * gY[1]; gu[2] += c_j * gY[2];
+    for (int ch = 0; ch < 3; ++ch) any_col |= gr[13 + ch] != 0.0f;
+    if (any_col) {
+        float Y[16], shc[48];
+        sh_basis(u[0], u[1], u[2], sp.sh_degree, Y);
+        load_sh(sp.sh, i, K, sp.storage, shc);
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            float raw = 0.5f;
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                if (j < K) raw += shc[3 * j + ch] * Y[j];
+            act[ch] = raw > 0.0f ? gr[13 + ch] : 0.0f;
+        }
+        // dL/du = sum_j (sum_ch act_ch c_j,ch) dY_j/du
+        float wj[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            wj[j] = j < K ? act[0] * shc[3 * j] + act[1] * shc[3 * j + 1] + act[2] * shc[3 * j + 2] : 0.0f;
+        sh_basis_grad_acc(u[0], u[1], u[2], sp.sh_degree, wj, gu);
+        if (g_sh && (act[0] != 0.0f || act[1] != 0.0f || act[2] != 0.0f)) {
+            float *gs = g_sh + (size_t)3 * K * i;
+            if (((3 * K) & 3) == 0) {            // float4 read-modify-write (degrees 1 and 3)
+                float4 *g4 = reinterpret_cast<float4 *>(gs);
+#pragma unroll
+                for (int q = 0; q < 12; ++q) {
+                    if (4 * q < 3 * K) {
+                        float4 v = g4[q];
+                        const int e = 4 * q;
+                        v.x += act[(e) % 3] * Y[(e) / 3];
+                        v.y += act[(e + 1) % 3] * Y[(e + 1) / 3];
+                        v.z += act[(e + 2) % 3] * Y[(e + 2) / 3];
+                        v.w += act[(e + 3) % 3] * Y[(e + 3) / 3];
+                        g4[q] = v;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    if (j < K) {
+                        gs[3 * j] += act[0] * Y[j];
+                        gs[3 * j + 1] += act[1] * Y[j];
+                        gs[3 * j + 2] += act[2] * Y[j];
+                    }
             }
         }
     }

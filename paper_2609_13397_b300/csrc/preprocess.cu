@@ -12,6 +12,7 @@
 // where (u, g, C) define the pixel pre-test: with e = d - u, a pixel ray d
 // with -1 + g.e + e^T C e > 0 cannot reach alpha >= 1/255 with this Gaussian.
 #include "rule.cuh"
+#include "sh.cuh"
 
 namespace conegs {
 
@@ -44,40 +45,6 @@ __global__ void __launch_bounds__(256) scene_cache_kernel(SceneParams sp, float 
     sig_eff[i] = sig;
 }
 
-// Real SH basis to degree 3 (positive constants, l-major, m = -l..l).
-struct ShC {
-    static constexpr float Y0 = 0.28209479177387814f;   // 1/(2 sqrt(pi))
-    static constexpr float C1 = 0.48860251190291992f;   // sqrt(3/(4 pi))
-    static constexpr float C2A = 1.0925484305920792f;   // sqrt(15/pi)/2
-    static constexpr float C2B = 0.31539156525252005f;  // sqrt(5/pi)/4
-    static constexpr float C2C = 0.54627421529603959f;  // sqrt(15/pi)/4
-    static constexpr float C3A = 0.59004358992664352f;  // sqrt(35/(2 pi))/4
-    static constexpr float C3B = 2.8906114426405538f;   // sqrt(105/pi)/2
-    static constexpr float C3C = 0.45704579946446572f;  // sqrt(21/(2 pi))/4
-    static constexpr float C3D = 0.37317633259011540f;  // sqrt(7/pi)/4
-    static constexpr float C3E = 1.4453057213202769f;   // sqrt(105/pi)/4
-};
-
-__device__ __forceinline__ void sh_basis(float x, float y, float z, int deg, float Y[16]) {
-    Y[0] = ShC::Y0;
-    if (deg < 1) return;
-    Y[1] = ShC::C1 * y; Y[2] = ShC::C1 * z; Y[3] = ShC::C1 * x;
-    if (deg < 2) return;
-    const float xx = x * x, yy = y * y, zz = z * z;
-    Y[4] = ShC::C2A * x * y;
-    Y[5] = ShC::C2A * y * z;
-    Y[6] = ShC::C2B * (3.f * zz - 1.f);
-    Y[7] = ShC::C2A * x * z;
-    Y[8] = ShC::C2C * (xx - yy);
-    if (deg < 3) return;
-    Y[9] = ShC::C3A * y * (3.f * xx - yy);
-    Y[10] = ShC::C3B * x * y * z;
-    Y[11] = ShC::C3C * y * (5.f * zz - 1.f);
-    Y[12] = ShC::C3D * z * (5.f * zz - 3.f);
-    Y[13] = ShC::C3C * x * (5.f * zz - 1.f);
-    Y[14] = ShC::C3E * z * (xx - yy);
-    Y[15] = ShC::C3A * x * (xx - 3.f * yy);
-}
 
 // Cone of pixel rays that can reach alpha >= 1/255 with a Gaussian.  Any such
 // pair has q^T A^-1 q <= kappa^2 (det A >= 1, Eq. 9), which puts mu within
@@ -204,11 +171,15 @@ __global__ void __launch_bounds__(256) view_records_kernel(CamParams c, ScenePar
     float Y[16];
     sh_basis(dx, dy, dz, sp.sh_degree, Y);
     const int K = (sp.sh_degree + 1) * (sp.sh_degree + 1);
+    float shc[48];
+    load_sh(sp.sh, i, K, sp.storage, shc);
     float col[3];
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) {
         float acc = 0.0f;
-        for (int j = 0; j < K; ++j) acc += load_scalar(sp.sh, (i * K + j) * 3 + ch, sp.storage) * Y[j];
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            if (j < K) acc += shc[3 * j + ch] * Y[j];
         col[ch] = fmaxf(acc + 0.5f, 0.0f);
     }
     const float rho2 = sp.rho2 ? sp.rho2[i] : 0.0f;
