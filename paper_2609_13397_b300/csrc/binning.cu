@@ -199,6 +199,18 @@ __device__ __forceinline__ void tile_record(const float *__restrict__ table, uin
     t[5] = fmaxf(t[5], mzf);
 }
 
+// Tiles whose centre (TILE t + TILE/2 in pixel coordinates) lies within half a
+// pixel of [xl, xh] x [yl, yh] (the margin is far above the FP32 error of the
+// box bounds), clamped to the image.
+__device__ __forceinline__ void tile_range(const CamParams &c, float xl, float xh, float yl, float yh, int &tx0,
+                                           int &tx1, int &ty0, int &ty1) {
+    const float lim = 1e8f;
+    tx0 = max((int)ceilf(fmaxf((xl - 0.5f * TILE - 0.5f) / TILE, -lim)), 0);
+    tx1 = min((int)floorf(fminf((xh - 0.5f * TILE + 0.5f) / TILE, lim)), c.tiles_x - 1);
+    ty0 = max((int)ceilf(fmaxf((yl - 0.5f * TILE - 0.5f) / TILE, -lim)), 0);
+    ty1 = min((int)floorf(fminf((yh - 0.5f * TILE + 0.5f) / TILE, lim)), c.tiles_y - 1);
+}
+
 // Pinhole cameras: the tiles whose centre ray lies within angle beta + gamma_max
 // of the Gaussian's direction u (a superset of what cone_prefilter keeps, with
 // margin) have their centre pixel inside the image of that cone on the plane
@@ -221,17 +233,15 @@ __device__ __forceinline__ bool pinhole_tile_box(const CamParams &c, const float
     const float s = 2.0f * sh * sqrtf(fmaxf(1.0f - sh * sh, 0.0f));   // sin theta
     if (!(v2 > s + 0.02f)) return false;
     const float den = v2 * v2 - s * s;
+    // FP32 error of the extremes grows like 1e-6 / den (normalised units); below
+    // den = 0.05 (a cone near the horizon) the super-tile walk is used instead
+    if (!(den >= 0.05f)) return false;
     const float rx = s * sqrtf(fmaxf(v0 * v0 + v2 * v2 - s * s, 0.0f));
     const float ry = s * sqrtf(fmaxf(v1 * v1 + v2 * v2 - s * s, 0.0f));
     const float inv = 1.0f / den;
     const float xl = c.fx * ((v0 * v2 - rx) * inv) + c.cx, xh = c.fx * ((v0 * v2 + rx) * inv) + c.cx;
     const float yl = c.fy * ((v1 * v2 - ry) * inv) + c.cy, yh = c.fy * ((v1 * v2 + ry) * inv) + c.cy;
-    // tile centres sit at TILE t + TILE/2; one tile of slack on each side
-    const float lim = 1e8f;
-    tx0 = max((int)floorf(fmaxf((xl - 0.5f * TILE) / TILE, -lim)), 0);
-    tx1 = min((int)ceilf(fminf((xh - 0.5f * TILE) / TILE, lim)), c.tiles_x - 1);
-    ty0 = max((int)floorf(fmaxf((yl - 0.5f * TILE) / TILE, -lim)), 0);
-    ty1 = min((int)ceilf(fminf((yh - 0.5f * TILE) / TILE, lim)), c.tiles_y - 1);
+    tile_range(c, xl, xh, yl, yh, tx0, tx1, ty0, ty1);
     return true;
 }
 
@@ -266,13 +276,8 @@ __device__ __forceinline__ bool kb_tile_box(const CamParams &c, const float4 gv,
     const float rad = c.lip[j] * Th * 1.001f + 1e-5f;
     const float sc = sphi > 1e-6f ? kb_radius(c, phi) / sphi : 1.0f;   // r(phi) / sin(phi)
     const float xn = v0 * sc, yn = v1 * sc;
-    const float lim = 1e8f;
-    const float pxl = c.fx * (xn - rad) + c.cx, pxh = c.fx * (xn + rad) + c.cx;
-    const float pyl = c.fy * (yn - rad) + c.cy, pyh = c.fy * (yn + rad) + c.cy;
-    tx0 = max((int)floorf(fmaxf((pxl - 0.5f * TILE) / TILE, -lim)), 0);
-    tx1 = min((int)ceilf(fminf((pxh - 0.5f * TILE) / TILE, lim)), c.tiles_x - 1);
-    ty0 = max((int)floorf(fmaxf((pyl - 0.5f * TILE) / TILE, -lim)), 0);
-    ty1 = min((int)ceilf(fminf((pyh - 0.5f * TILE) / TILE, lim)), c.tiles_y - 1);
+    tile_range(c, c.fx * (xn - rad) + c.cx, c.fx * (xn + rad) + c.cx, c.fy * (yn - rad) + c.cy,
+               c.fy * (yn + rad) + c.cy, tx0, tx1, ty0, ty1);
     return true;
 }
 
