@@ -249,7 +249,7 @@ conegs_status conegs_radix_sort_pairs(conegs_ctx *ctx, uint32_t *keys, uint32_t 
  * allocator (a framework's caching allocator), or they run in a
  * latency-critical loop that must not block on or fail in an allocation.
  * The paper has no counterpart; this is a library service.
- * The scratch is a fixed array inside the library (about 2.2 MB on every GPU
+ * The scratch is a fixed array inside the library (about 2.6 MB on every GPU
  * that loads it, held until exit); the call allocates nothing.
  *   keys/values: device arrays of n entries, sorted in place on `stream`.
  *   n <= 262144; larger n fails with CONEGS_ERR_ARG.

@@ -170,18 +170,8 @@ __global__ void __launch_bounds__(256) view_records_kernel(CamParams c, ScenePar
     if (!(L > 0.0f)) { dx = 0.f; dy = 0.f; dz = 1.f; }
     float Y[16];
     sh_basis(dx, dy, dz, sp.sh_degree, Y);
-    const int K = (sp.sh_degree + 1) * (sp.sh_degree + 1);
-    float shc[48];
-    load_sh(sp.sh, i, K, sp.storage, shc);
     float col[3];
-#pragma unroll
-    for (int ch = 0; ch < 3; ++ch) {
-        float acc = 0.0f;
-#pragma unroll
-        for (int j = 0; j < 16; ++j)
-            if (j < K) acc += shc[3 * j + ch] * Y[j];
-        col[ch] = fmaxf(acc + 0.5f, 0.0f);
-    }
+    sh_colour(sp.sh, i, sp.sh_degree, sp.storage, Y, col);
     const float rho2 = sp.rho2 ? sp.rho2[i] : 0.0f;
     const float m = fmaxf(*mcam, mzf);   // footprint bound (raised for the z/f variant)
     // binning prefilter: the cone of the binning rule's own bound (its kappa and

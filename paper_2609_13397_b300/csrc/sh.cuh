@@ -60,6 +60,33 @@ __device__ __forceinline__ void sh_basis_grad_acc(float x, float y, float z, int
             10.f * ShC::C3C * x * z * w[13] + ShC::C3E * (xx - yy) * w[14];
 }
 
+// rgb = max(0, sum_j c_j Y_j + 1/2) of Gaussian i, consuming the coefficients as
+// they load (float4 loads for FP32 storage when 3K is a multiple of 4).
+__device__ __forceinline__ void sh_colour(const void *sh, int64_t i, int deg, int storage, const float Y[16],
+                                          float col[3]) {
+    const int K = (deg + 1) * (deg + 1), n = 3 * K;
+    float acc[3] = {0.5f, 0.5f, 0.5f};
+    if (storage == 0 && (n & 3) == 0) {
+        const float4 *p = reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(sh) + (size_t)n * i);
+#pragma unroll
+        for (int q = 0; q < 12; ++q) {
+            if (4 * q < n) {
+                const float4 v = p[q];
+                acc[(4 * q) % 3] += v.x * Y[(4 * q) / 3];
+                acc[(4 * q + 1) % 3] += v.y * Y[(4 * q + 1) / 3];
+                acc[(4 * q + 2) % 3] += v.z * Y[(4 * q + 2) / 3];
+                acc[(4 * q + 3) % 3] += v.w * Y[(4 * q + 3) / 3];
+            }
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 48; ++q)
+            if (q < n) acc[q % 3] += load_scalar(sh, (int64_t)n * i + q, storage) * Y[q / 3];
+    }
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) col[ch] = fmaxf(acc[ch], 0.0f);
+}
+
 // The 3K colour coefficients of Gaussian i (c[3 j + channel]), K = (deg + 1)^2:
 // float4 loads for FP32 storage when 3K is a multiple of 4 (degrees 1 and 3).
 __device__ __forceinline__ void load_sh(const void *sh, int64_t i, int K, int storage, float c[48]) {

@@ -4,7 +4,8 @@
 // each owns one contiguous chunk (a multiple of 4096 items); per pass
 //   upsweep   per-block digit histogram             -> counts[digit][block]
 //   scan      exclusive scan of the 256*G counters (digit-major)
-//   downsweep per 4096-item tile: each warp ranks its 512 items in lane order
+//   downsweep per tile (4096 items; 1024 for sorts of up to 2^20 items, so that
+//             small sorts still spread over the SMs): each warp ranks its items in lane order
 //             with __match_any_sync (stable), warps are offset by a per-digit
 //             scan across warps; the tile is rearranged in shared memory in
 //             digit order and written out so that runs of one digit land on
@@ -189,24 +190,28 @@ cudaError_t launch_ranges(const uint32_t *keys, int64_t n, uint2 *ranges, int nt
 
 constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
-constexpr int RS_ROUNDS = 16;                       // 32-item rounds per warp per tile
-constexpr int RS_TILE = RS_THREADS * RS_ROUNDS;     // 4096 items per tile
+constexpr int RS_ROUNDS_LARGE = 16;                 // 32-item rounds per warp per tile: 4096-item tiles
+constexpr int RS_ROUNDS_SMALL = 4;                  // 1024-item tiles for sorts of up to RS_SMALL_N items
+constexpr int64_t RS_SMALL_N = 1 << 20;             // (their 4096-item tiles would not fill 148 SMs)
 constexpr int RS_MAX_BLOCKS = 148 * 4;
 
 struct RsPlan {
     int64_t n;
     int blocks;
     int64_t chunk;
+    int rounds;
 };
 
 RsPlan rs_plan(int64_t n) {
     RsPlan p;
     p.n = n;
-    int64_t tiles = div_up(n, RS_TILE);
+    p.rounds = n <= RS_SMALL_N ? RS_ROUNDS_SMALL : RS_ROUNDS_LARGE;
+    const int64_t tile = (int64_t)RS_THREADS * p.rounds;
+    int64_t tiles = div_up(n, tile);
     int64_t blocks = std::min<int64_t>(tiles, RS_MAX_BLOCKS);
     if (blocks < 1) blocks = 1;
     int64_t tiles_per = div_up(tiles, blocks);
-    p.chunk = tiles_per * RS_TILE;
+    p.chunk = tiles_per * tile;
     p.blocks = (int)std::max<int64_t>(1, div_up(n, p.chunk));
     return p;
 }
@@ -229,6 +234,7 @@ __global__ void __launch_bounds__(RS_THREADS) rs_upsweep(const uint32_t *__restr
     counts[(int64_t)threadIdx.x * gridDim.x + blockIdx.x] = hist[threadIdx.x];
 }
 
+template <int RS_ROUNDS>
 __global__ void __launch_bounds__(RS_THREADS) rs_downsweep(const uint32_t *__restrict__ kin,
                                                            const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
                                                            uint32_t *__restrict__ vout, int64_t n, int64_t chunk,
@@ -238,6 +244,7 @@ __global__ void __launch_bounds__(RS_THREADS) rs_downsweep(const uint32_t *__res
     __shared__ uint32_t wcount[RS_WARPS][256];      // per-warp digit counts, then per-warp local bases
     __shared__ uint32_t gofs[256];                  // global position minus local position, per digit
     __shared__ uint32_t wsum[RS_WARPS];
+    constexpr int RS_TILE = RS_THREADS * RS_ROUNDS;
     __shared__ uint32_t s_k[RS_TILE], s_v[RS_TILE];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     running[threadIdx.x] = offsets[(int64_t)threadIdx.x * gridDim.x + blockIdx.x];
@@ -339,7 +346,10 @@ cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *alt_keys,
         note_launches(1);
         cudaError_t e = exclusive_scan(counts, offs, cnt, scan_scr, 0, s);
         if (e != cudaSuccess) return e;
-        rs_downsweep<<<p.blocks, RS_THREADS, 0, s>>>(ki, vi, ko, vo, n, p.chunk, shift, mask, offs);
+        if (p.rounds == RS_ROUNDS_SMALL)
+            rs_downsweep<RS_ROUNDS_SMALL><<<p.blocks, RS_THREADS, 0, s>>>(ki, vi, ko, vo, n, p.chunk, shift, mask, offs);
+        else
+            rs_downsweep<RS_ROUNDS_LARGE><<<p.blocks, RS_THREADS, 0, s>>>(ki, vi, ko, vo, n, p.chunk, shift, mask, offs);
         note_launches(1);
         std::swap(ki, ko);
         std::swap(vi, vo);

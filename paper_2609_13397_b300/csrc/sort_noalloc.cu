@@ -37,9 +37,9 @@ void set_error_message(const char *msg);
 namespace {
 
 constexpr int64_t NOALLOC_MAX_ITEMS = 1 << 18;
-// digit counters + offsets of at most 64 sort blocks (2^18 items / 4096 per tile),
-// plus the scan scratch for them
-constexpr int64_t NOALLOC_COUNTER_WORDS = 2 * 256 * 64 + 256;
+// digit counters + offsets of at most 256 sort blocks (2^18 items in 1024-item
+// tiles), plus the scan scratch for them
+constexpr int64_t NOALLOC_COUNTER_WORDS = 2 * 256 * 256 + 256;
 constexpr int64_t NOALLOC_WORDS = 2 * NOALLOC_MAX_ITEMS + NOALLOC_COUNTER_WORDS;
 
 static __device__ __align__(256) uint32_t g_sort_scratch[NOALLOC_WORDS];
