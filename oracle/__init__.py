@@ -25,7 +25,8 @@ _lib = None
 
 FILTER_NONE, FILTER_ANISO, FILTER_ISO, FILTER_ZF = 0, 1, 2, 3
 COMP_MARGINAL, COMP_ADDITIVE = 0, 1
-FL_ALPHA_MIN, FL_ALPHA_MAX, FL_STOP, FL_KEY_TIE, FL_TNEAR = 1, 2, 4, 8, 16
+FL_ALPHA_MIN, FL_ALPHA_MAX, FL_STOP, FL_KEY_TIE, FL_TNEAR, FL_UT_NEAR = 1, 2, 4, 8, 16, 32
+UT_DROP, UT_KEEP, UT_NEAR = 0, 1, 2
 
 
 def build(force: bool = False) -> str:
@@ -49,6 +50,8 @@ def lib():
         _lib.or_pairs_above.restype = ctypes.c_long
         _lib.or_bin_counts.restype = ctypes.c_long
         _lib.or_num_threads.restype = ctypes.c_int
+        _lib.or_ut_rect_min.restype = ctypes.c_double
+        _lib.or_ut_rect_min.argtypes = [ctypes.c_double] * 9
         for name in ("or_pair_detail", "or_bundle"):
             getattr(_lib, name).argtypes = None
     return _lib
@@ -176,9 +179,15 @@ class Render:
 
 def render(cam, scene, pix: Optional[Sequence[int]] = None, filter: int = FILTER_ANISO,
            comp: int = COMP_MARGINAL, cull: bool = True, eps: float = 1e-5, eps_key: float = 0.0,
-           max_used: int = 0, order: int = 0) -> Render:
+           max_used: int = 0, order: int = 0, gate: Optional[np.ndarray] = None) -> Render:
     """Render pixels (indices into the row-major W x H grid; None = all).  order: 0
-    the canonical per-Gaussian key |mu - o|, 1 the exact per-ray t* order."""
+    the canonical per-Gaussian key |mu - o|, 1 the exact per-ray t* order.  gate: a
+    [n, ntiles] UT gate (``ut_gate``): only kept tiles are evaluated; pixels where an
+    ambiguous entry contributes get FL_UT_NEAR."""
+    if gate is not None:
+        gate = np.ascontiguousarray(gate, np.uint8)
+        tx, ty = tile_grid(cam)
+        assert gate.shape == (scene.n, tx * ty)
     n = scene.n
     if pix is None:
         npix, pix_arr, pptr = cam.width * cam.height, None, None
@@ -195,7 +204,8 @@ def render(cam, scene, pix: Optional[Sequence[int]] = None, filter: int = FILTER
                     ctypes.c_int(scene.sh_degree), _p(_d(scene.rho2)), ctypes.c_int(filter), ctypes.c_int(comp),
                     ctypes.c_int(npix), pptr, ctypes.c_int(int(cull)), ctypes.c_double(eps),
                     ctypes.c_double(eps_key), _p(rgb), _p(T), _p(flags, ctypes.c_int), _p(ncon, ctypes.c_int),
-                    _p(used, ctypes.c_int) if max_used > 0 else None, ctypes.c_int(max_used), ctypes.c_int(order))
+                    _p(used, ctypes.c_int) if max_used > 0 else None, ctypes.c_int(max_used), ctypes.c_int(order),
+                    _p(gate, ctypes.c_ubyte) if gate is not None else None)
     return Render(rgb, T, flags, ncon, pix_arr, used if max_used > 0 else None)
 
 
@@ -290,3 +300,44 @@ def bin_counts(cam, scene, dense: bool = False, zf: bool = False):
                                 _p(recs, ctypes.c_float), _p(pg, ctypes.c_int), _p(pt, ctypes.c_int),
                                 _p(pas, ctypes.c_ubyte) if dense else None)
     return int(total), pg, pt, pas
+
+
+# ------------------------------------------------------------------ UT binning (3DGUT-style backbone)
+
+def ut_rect_min(c, conic, rect) -> float:
+    """min over the rectangle (x0, x1, y0, y1) of (y - c)^T [[A,B],[B,C]] (y - c)."""
+    A, B, C = conic
+    x0, x1, y0, y1 = rect
+    return float(lib().or_ut_rect_min(float(c[0]), float(c[1]), float(A), float(B), float(C),
+                                      float(x0), float(x1), float(y0), float(y1)))
+
+
+def ut_gate(cam, scene, eps: float = 2e-3):
+    """Unscented-transform binning gate (definition in conegs_oracle.c).
+
+    Returns (gate [n, ntiles] uint8: 0 drop / 1 keep / 2 ambiguous, status [n]:
+    0 the angular-tile rule decides / 1 UT / 2 ambiguous domain decision,
+    geo [n, 6]: ybar, conic A B C, k^2 of status-1 Gaussians).  The angular-tile
+    rule's flags come from its FP32 emulation (``bin_gauss``)."""
+    n = scene.n
+    tx, ty = tile_grid(cam)
+    flags = np.ascontiguousarray(bin_gauss(cam, scene)[:, 9].astype(np.int32))
+    gate = np.zeros((n, tx * ty), np.uint8)
+    status = np.zeros(n, np.int32)
+    geo = np.zeros((n, 6))
+    lib().or_ut_gate(_p(pack_camera(cam)), ctypes.c_int(n), _p(_d(scene.means)), _p(_d(scene.log_scales)),
+                     _p(_d(scene.quats)), _p(_d(scene.opacity_logits)), _p(_d(scene.rho2)),
+                     _p(flags, ctypes.c_int), ctypes.c_double(eps), _p(gate, ctypes.c_ubyte),
+                     _p(status, ctypes.c_int), _p(geo))
+    return gate, status, geo
+
+
+def ut_bin_counts(cam, scene, eps: float = 2e-3):
+    """Per-Gaussian pair counts of UT binning: (sure [n], near [n], status [n]).
+    UT Gaussians keep between sure and sure + near tiles; the others keep
+    exactly their angular-tile rule count (FP32 emulation), which is ``sure``."""
+    gate, status, _ = ut_gate(cam, scene, eps)
+    _, _, _, pas = bin_counts(cam, scene, dense=True)
+    cone = status == 0
+    gate[cone] = pas[cone]
+    return (gate == UT_KEEP).sum(1).astype(np.int64), (gate == UT_NEAR).sum(1).astype(np.int64), status

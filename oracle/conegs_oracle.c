@@ -60,6 +60,7 @@
 #define ALPHA_MAX 0.99
 #define T_STOP 1e-4
 #define T_NEAR 0.01
+#define UT_TILE 8   /* tile side of the UT gate (pixels) */
 
 /* ------------------------------------------------------------------ camera */
 
@@ -560,7 +561,7 @@ static int cand_cmp_ts(const void *a, const void *b) {
 enum { ORDER_KEY = 0, ORDER_TSTAR = 1 };
 
 /* Flag bits of the near-threshold protocol. */
-enum { FL_ALPHA_MIN = 1, FL_ALPHA_MAX = 2, FL_STOP = 4, FL_KEY_TIE = 8, FL_TNEAR = 16 };
+enum { FL_ALPHA_MIN = 1, FL_ALPHA_MAX = 2, FL_STOP = 4, FL_KEY_TIE = 8, FL_TNEAR = 16, FL_UT_NEAR = 32 };
 
 /* Composite one pixel's candidates (Eq. 4 with the 3DGS conventions). */
 static void composite(cand *cs, int nc, const ogauss *g, double eps, double eps_key, double rgb[3],
@@ -680,17 +681,20 @@ double or_bundle(const double *campk, double x, double y, const double *mu, cons
 
 /* Render a list of pixels (npix indices into the W x H grid; NULL = all).
  * Outputs rgb[npix*3], T[npix], flags[npix], ncontrib[npix]; optionally the
- * ids of the contributing Gaussians (used[npix*max_used]). */
+ * ids of the contributing Gaussians (used[npix*max_used]).  gate (optional,
+ * from or_ut_gate): the pixel's tile must be kept for a Gaussian to be
+ * evaluated; a contributing pair whose gate entry is ambiguous sets FL_UT_NEAR. */
 void or_render(const double *campk, int n, const double *means, const double *log_scales, const double *quats,
                const double *logits, const double *sh, int deg, const double *rho2, int filter, int comp,
                int npix, const int *pix, int cull, double eps, double eps_key, double *rgb, double *Tout,
-               int *flags, int *ncontrib, int *used, int max_used, int order) {
+               int *flags, int *ncontrib, int *used, int max_used, int order, const unsigned char *gate) {
     ocam c;
     unpack_cam(campk, &c);
     oscene s = {n, deg, means, log_scales, quats, logits, sh, rho2};
     ogauss *g = (ogauss *)malloc(sizeof(ogauss) * (size_t)(n > 0 ? n : 1));
     prep_all(&c, &s, g);
     int total = pix ? npix : c.W * c.H;
+    const int ntx = (c.W + UT_TILE - 1) / UT_TILE, nt = ntx * ((c.H + UT_TILE - 1) / UT_TILE);
 #pragma omp parallel
     {
         cand *cs = (cand *)malloc(sizeof(cand) * (size_t)(n > 0 ? n : 1));
@@ -709,8 +713,12 @@ void or_render(const double *campk, int n, const double *means, const double *lo
             }
             footprint_variant(&c, filter, d, dx, dy);
             double m = (dot3(dx, dx) + dot3(dy, dy)) / 3.0;
-            int nc = 0;
+            int nc = 0, utnear = 0;
+            const size_t tile = (size_t)((p / c.W) / UT_TILE) * ntx + (p % c.W) / UT_TILE;
             for (int k = 0; k < n; ++k) {
+                /* UT binning: only the gate's tiles are evaluated (Sec. 3, 3DGUT backbone) */
+                const int gv = gate ? gate[(size_t)k * nt + tile] : 1;
+                if (gv == 0) continue;
                 if (cull && !oracle_keep(&g[k], c.o, d, m)) continue;
                 double T, ts;
                 if (!pair_response(&g[k], c.o, d, dx, dy, filter, comp, &T, &ts, NULL)) {
@@ -720,10 +728,12 @@ void or_render(const double *campk, int n, const double *means, const double *lo
                     continue;
                 }
                 if (T < ALPHA_MIN * (1.0 - eps)) continue;
+                if (gv == 2) utnear = 1;
                 cs[nc].L = g[k].key; cs[nc].T = T; cs[nc].ts = ts; cs[nc].idx = k;
                 ++nc;
             }
             composite(cs, nc, g, eps, eps_key, o_rgb, &Tout[t], &flags[t], &ncontrib[t], u, max_used, order);
+            if (utnear) flags[t] |= FL_UT_NEAR;
         }
         free(cs);
     }
@@ -864,6 +874,178 @@ void or_floor(int nv, const double *cams, int n, const double *means, double *rh
         rho2[i] = isinf(best) ? 0.0 : best;
     }
     free(cs);
+}
+
+/* ------------------------------------------------------------------ unscented-transform binning
+ *
+ * The alternative binning backbone.  The paper plugs its response into two
+ * backbones (Sec. 3): 3DGEER and 3DGUT, and 3DGUT bounds each Gaussian on the
+ * image with an unscented transform (UT) of its 3D distribution through the
+ * camera model instead of a Jacobian.  The response (Eq. 9) is unchanged; only
+ * the set of (Gaussian, tile) pairs that is evaluated changes.  Definition
+ * (the scaled UT of Julier and Uhlmann with alpha = 1, beta = 2, kappa = 0 in
+ * n = 3 dimensions, so lambda = 0):
+ *   sigma points  X_0 = mu, X_{+-i} = mu +- sqrt(3) s_eff,i R_i  (i = 1..3),
+ *                 R_i the i-th principal axis, s_eff,i the floored scale (Eq. 10)
+ *   weights       mean w_0 = 0, w_{+-i} = 1/6; covariance w_0 = 2, w_{+-i} = 1/6
+ *   image         y_j = Pi(X_j) (the camera's own model), ybar = sum_j w_j y_j,
+ *                 Sigma_2 = sum_j w^c_j (y_j - ybar)(y_j - ybar)^T + I/12
+ *                 (1/12 px^2: the moment-matched variance of the half-pixel
+ *                 parallelogram of Eq. 8, seen on the image)
+ *   extent        k^2 = 2 ln(255 sigma_eff): alpha >= 1/255 needs a Mahalanobis
+ *                 distance^2 of at most k^2
+ *   tile test     keep tile (tx, ty) iff the minimum over its pixel-centre
+ *                 rectangle [8 tx + 1/2, min(8 tx + 15/2, W - 1/2)] x (same in y)
+ *                 of (y - ybar)^T Sigma_2^-1 (y - ybar) is at most k^2
+ *   fallback      the Gaussian keeps the conservative angular-tile rule when
+ *                 the rule's flag is not 1 (culled or pass-all), or when a
+ *                 sigma point leaves the camera's domain: pinhole p_z < 0.1 |p|
+ *                 (camera frame), fisheye polar angle > theta_lim.
+ * FP64 decisions within a relative eps of a threshold are reported as
+ * ambiguous (gate value 2): an FP32 implementation may take them either way. */
+
+#define UT_COSMIN 0.1
+#define UT_VLP (1.0 / 12.0)
+
+/* Minimum over [x0,x1] x [y0,y1] of Q(y) = (y - c)^T [[A,B],[B,C]] (y - c)
+ * (A, C > 0, AC > B^2).  Q is convex, so when c lies outside the rectangle the
+ * minimum is on its boundary; on an edge x = X it is at y = c_y - B (X - c_x) / C
+ * clamped to the edge (and symmetrically on y = Y). */
+double or_ut_rect_min(double cx, double cy, double A, double B, double C, double x0, double x1, double y0,
+                      double y1) {
+    const double dx0 = x0 - cx, dx1 = x1 - cx, dy0 = y0 - cy, dy1 = y1 - cy;
+    if (dx0 <= 0 && dx1 >= 0 && dy0 <= 0 && dy1 >= 0) return 0.0;
+    const double ex[2] = {dx0, dx1}, ey[2] = {dy0, dy1};
+    double best = INFINITY;
+    for (int e = 0; e < 2; ++e) {
+        double x = ex[e], y = -B * x / C;
+        y = y < dy0 ? dy0 : (y > dy1 ? dy1 : y);
+        double q = A * x * x + 2.0 * B * x * y + C * y * y;
+        if (q < best) best = q;
+        y = ey[e];
+        x = -B * y / A;
+        x = x < dx0 ? dx0 : (x > dx1 ? dx1 : x);
+        q = A * x * x + 2.0 * B * x * y + C * y * y;
+        if (q < best) best = q;
+    }
+    return best;
+}
+
+/* UT image ellipse of one Gaussian: returns 1 with ybar[2], conic[3] =
+ * Sigma_2^-1 (A, B, C) and k^2; 0 when a sigma point is outside the camera's
+ * domain.  *amb = 1 when that domain decision lies within eps of its limit. */
+static int ut_project(const ocam *c, const ogauss *g, double eps, double ybar[2], double conic[3], double *k2,
+                      int *amb) {
+    double X[7][3], y[7][2];
+    const double r3 = sqrt(3.0);
+    for (int k = 0; k < 3; ++k) X[0][k] = g->mu[k];
+    for (int i = 0; i < 3; ++i)
+        for (int k = 0; k < 3; ++k) {
+            /* column i of W^-1 = R S_eff is s_eff,i R_i */
+            X[1 + 2 * i][k] = g->mu[k] + r3 * g->Winv[3 * k + i];
+            X[2 + 2 * i][k] = g->mu[k] - r3 * g->Winv[3 * k + i];
+        }
+    int ok = 1;
+    *amb = 0;
+    for (int j = 0; j < 7; ++j) {
+        double w[3], p[3];
+        for (int k = 0; k < 3; ++k) w[k] = X[j][k] - c->o[k];
+        mv3(c->Rinv, w, p);
+        if (c->model == 0) {
+            const double nrm = sqrt(dot3(p, p));
+            const double cs = nrm > 0 ? p[2] / nrm : -1.0;
+            if (fabs(cs - UT_COSMIN) <= eps * UT_COSMIN) *amb = 1;
+            if (!(cs >= UT_COSMIN)) ok = 0;
+        } else {
+            const double th = atan2(sqrt(p[0] * p[0] + p[1] * p[1]), p[2]);
+            if (fabs(th - c->thlim) <= eps * c->thlim) *amb = 1;
+            if (!(th <= c->thlim)) ok = 0;
+        }
+    }
+    if (!ok) return 0;
+    for (int j = 0; j < 7; ++j)
+        if (!project(c, X[j], &y[j][0], &y[j][1])) return 0;
+    double wm[7], wc[7];
+    wm[0] = 0.0;
+    wc[0] = 2.0;
+    for (int j = 1; j < 7; ++j) wm[j] = wc[j] = 1.0 / 6.0;
+    ybar[0] = ybar[1] = 0.0;
+    for (int j = 0; j < 7; ++j) {
+        ybar[0] += wm[j] * y[j][0];
+        ybar[1] += wm[j] * y[j][1];
+    }
+    double Sxx = UT_VLP, Sxy = 0.0, Syy = UT_VLP;
+    for (int j = 0; j < 7; ++j) {
+        const double ax = y[j][0] - ybar[0], ay = y[j][1] - ybar[1];
+        Sxx += wc[j] * ax * ax;
+        Sxy += wc[j] * ax * ay;
+        Syy += wc[j] * ay * ay;
+    }
+    const double det = Sxx * Syy - Sxy * Sxy;
+    conic[0] = Syy / det;
+    conic[1] = -Sxy / det;
+    conic[2] = Sxx / det;
+    *k2 = 2.0 * log(255.0 * g->sig_eff);
+    return 1;
+}
+
+/* UT gate of every (Gaussian, tile), row-major tiles of 8 x 8 pixels:
+ *   gate[n * ntiles]: 0 drop, 1 keep, 2 ambiguous (within eps of k^2);
+ *   status[n]: 0 the angular-tile rule decides (flag != 1 or a sigma point
+ *     outside the domain; its row of gate is all 1: that rule is conservative),
+ *     1 UT, 2 the domain decision is ambiguous (row all 2);
+ *   geo[n * 6] (optional): ybar (2), conic A B C, k^2 of status-1 Gaussians.
+ * flags[n]: the angular-tile rule's per-Gaussian flag (0 culled, 1 normal, 2 pass-all). */
+void or_ut_gate(const double *campk, int n, const double *means, const double *log_scales, const double *quats,
+                const double *logits, const double *rho2, const int *flags, double eps, unsigned char *gate,
+                int *status, double *geo) {
+    ocam c;
+    unpack_cam(campk, &c);
+    const int ntx = (c.W + UT_TILE - 1) / UT_TILE, nty = (c.H + UT_TILE - 1) / UT_TILE, nt = ntx * nty;
+    double *sh0 = (double *)calloc((size_t)3 * (n > 0 ? n : 1), sizeof(double));
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int i = 0; i < n; ++i) {
+        unsigned char *row = gate + (size_t)i * nt;
+        double *gg = geo ? geo + 6 * (size_t)i : NULL;
+        if (gg)
+            for (int k = 0; k < 6; ++k) gg[k] = 0.0;
+        if (flags[i] != 1) {
+            status[i] = 0;
+            memset(row, 1, (size_t)nt);
+            continue;
+        }
+        ogauss g;
+        prep_gauss(c.o, means + 3 * (size_t)i, log_scales + 3 * (size_t)i, quats + 4 * (size_t)i, logits[i],
+                   sh0 + 3 * (size_t)i, 0, rho2 ? rho2[i] : 0.0, &g);
+        double yb[2], cn[3], k2;
+        int amb;
+        const int ok = ut_project(&c, &g, eps, yb, cn, &k2, &amb);
+        if (amb) {
+            status[i] = 2;
+            memset(row, 2, (size_t)nt);
+            continue;
+        }
+        if (!ok) {
+            status[i] = 0;
+            memset(row, 1, (size_t)nt);
+            continue;
+        }
+        status[i] = 1;
+        if (gg) {
+            gg[0] = yb[0]; gg[1] = yb[1]; gg[2] = cn[0]; gg[3] = cn[1]; gg[4] = cn[2]; gg[5] = k2;
+        }
+        const double tol = eps * (k2 > 1.0 ? k2 : 1.0);
+        for (int t = 0; t < nt; ++t) {
+            const int tx = t % ntx, ty = t / ntx;
+            const double x0 = UT_TILE * tx + 0.5, y0 = UT_TILE * ty + 0.5;
+            double x1 = UT_TILE * tx + UT_TILE - 0.5, y1 = UT_TILE * ty + UT_TILE - 0.5;
+            if (x1 > c.W - 0.5) x1 = c.W - 0.5;
+            if (y1 > c.H - 0.5) y1 = c.H - 0.5;
+            const double q = or_ut_rect_min(yb[0], yb[1], cn[0], cn[1], cn[2], x0, x1, y0, y1);
+            row[t] = fabs(q - k2) <= tol ? 2 : (q <= k2 ? 1 : 0);
+        }
+    }
+    free(sh0);
 }
 
 /* ======================================================================
