@@ -85,7 +85,16 @@ enum {
      * orthonormal basis across the pixel ray d, so the footprint is isotropic across
      * the ray with t^2 a^2 / 3 per axis (Eq. 8): */
     CONEGS_FILTER_ISO = 1u << 4, /* a^2 = (|dx_perp|^2 + |dy_perp|^2) / 2: half-trace of the true footprint */
-    CONEGS_FILTER_ZF = 1u << 5   /* a = |<d, z_cam>| / (2 f_x): paraxial z/f pixel size (VKRayGS-style sizing) */
+    CONEGS_FILTER_ZF = 1u << 5,  /* a = |<d, z_cam>| / (2 f_x): paraxial z/f pixel size (VKRayGS-style sizing) */
+    /* Unscented-transform binning (the 3DGUT-style backbone of Sec. 3) instead of the
+     * conservative angular-tile rule; the response is unchanged.  Each Gaussian's seven
+     * sigma points mu, mu +- sqrt(3) s_eff,i R_i go through the camera model (scaled UT,
+     * alpha 1, beta 2, kappa 0); a tile is kept when its pixel-centre rectangle meets
+     * the ellipse {y : (y - ybar)^T (Sigma_2 + I/12)^-1 (y - ybar) <= 2 ln(255 sigma_eff)}.
+     * Approximate: a pair the ellipse misses is not evaluated.  Gaussians with a sigma
+     * point outside the camera's domain (pinhole: p_z < 0.1 |p|; fisheye: beyond
+     * theta_lim) keep the angular-tile rule. */
+    CONEGS_BIN_UT = 1u << 6
 };
 
 typedef struct conegs_ctx conegs_ctx;

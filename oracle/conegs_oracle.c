@@ -901,11 +901,15 @@ void or_floor(int nv, const double *cams, int n, const double *means, double *rh
  *                 the rule's flag is not 1 (culled or pass-all), or when a
  *                 sigma point leaves the camera's domain: pinhole p_z < 0.1 |p|
  *                 (camera frame), fisheye polar angle > theta_lim.
- * FP64 decisions within a relative eps of a threshold are reported as
- * ambiguous (gate value 2): an FP32 implementation may take them either way. */
+ * FP64 decisions near a threshold are reported as ambiguous (gate value 2): an
+ * FP32 implementation may take them either way (the ellipse test within a
+ * relative eps of k^2, the domain test within a relative 1e-5 of its limit). */
 
 #define UT_COSMIN 0.1
 #define UT_VLP (1.0 / 12.0)
+/* relative band of the domain decision reported as ambiguous: far above the
+ * FP32 error of a camera-frame direction (~1e-7), far below the gate's eps */
+#define UT_EPS_DOMAIN 1e-5
 
 /* Minimum over [x0,x1] x [y0,y1] of Q(y) = (y - c)^T [[A,B],[B,C]] (y - c)
  * (A, C > 0, AC > B^2).  Q is convex, so when c lies outside the rectangle the
@@ -933,9 +937,8 @@ double or_ut_rect_min(double cx, double cy, double A, double B, double C, double
 
 /* UT image ellipse of one Gaussian: returns 1 with ybar[2], conic[3] =
  * Sigma_2^-1 (A, B, C) and k^2; 0 when a sigma point is outside the camera's
- * domain.  *amb = 1 when that domain decision lies within eps of its limit. */
-static int ut_project(const ocam *c, const ogauss *g, double eps, double ybar[2], double conic[3], double *k2,
-                      int *amb) {
+ * domain.  *amb = 1 when that domain decision lies within UT_EPS_DOMAIN of its limit. */
+static int ut_project(const ocam *c, const ogauss *g, double ybar[2], double conic[3], double *k2, int *amb) {
     double X[7][3], y[7][2];
     const double r3 = sqrt(3.0);
     for (int k = 0; k < 3; ++k) X[0][k] = g->mu[k];
@@ -954,11 +957,11 @@ static int ut_project(const ocam *c, const ogauss *g, double eps, double ybar[2]
         if (c->model == 0) {
             const double nrm = sqrt(dot3(p, p));
             const double cs = nrm > 0 ? p[2] / nrm : -1.0;
-            if (fabs(cs - UT_COSMIN) <= eps * UT_COSMIN) *amb = 1;
+            if (fabs(cs - UT_COSMIN) <= UT_EPS_DOMAIN * UT_COSMIN) *amb = 1;
             if (!(cs >= UT_COSMIN)) ok = 0;
         } else {
             const double th = atan2(sqrt(p[0] * p[0] + p[1] * p[1]), p[2]);
-            if (fabs(th - c->thlim) <= eps * c->thlim) *amb = 1;
+            if (fabs(th - c->thlim) <= UT_EPS_DOMAIN * c->thlim) *amb = 1;
             if (!(th <= c->thlim)) ok = 0;
         }
     }
@@ -1019,7 +1022,7 @@ void or_ut_gate(const double *campk, int n, const double *means, const double *l
                    sh0 + 3 * (size_t)i, 0, rho2 ? rho2[i] : 0.0, &g);
         double yb[2], cn[3], k2;
         int amb;
-        const int ok = ut_project(&c, &g, eps, yb, cn, &k2, &amb);
+        const int ok = ut_project(&c, &g, yb, cn, &k2, &amb);
         if (amb) {
             status[i] = 2;
             memset(row, 2, (size_t)nt);

@@ -26,12 +26,13 @@ cudaError_t launch_gauss_scene_rule(const SceneParams &sp, float *binrec, cudaSt
 cudaError_t launch_bin_count(const CamParams &c, const float *binrec, const float4 *gview, const float2 *gcone,
                              const uint8_t *gflag, const float *table, const float *super, const float *mcam,
                              float mzf, int64_t n, uint32_t *counts, uint4 *cache, uint32_t *blist,
-                             unsigned long long *bcursor, unsigned long long bcap, cudaStream_t s);
+                             unsigned long long *bcursor, unsigned long long bcap, const float *ut_means,
+                             const float *ut_W, const float *ut_sig_eff, cudaStream_t s);
 cudaError_t launch_bin_emit(const CamParams &c, const float *binrec, const float4 *gview, const float2 *gcone,
                             const uint8_t *gflag, const float *table, const float *super, const float *mcam,
                             float mzf, int64_t n_sorted, const uint32_t *order, const uint32_t *offsets,
                             const uint4 *cache, const uint32_t *blist, uint32_t *out_tile, uint32_t *out_gid,
-                            cudaStream_t s);
+                            bool ut, cudaStream_t s);
 cudaError_t launch_scene_cache(const SceneParams &sp, float *W, float *sig_eff, cudaStream_t s);
 cudaError_t launch_view_records(const CamParams &c, const SceneParams &sp, const float *mcam, float mzf,
                                 float4 *rec, float4 *gview, float2 *gcone, uint8_t *gflag, cudaStream_t s);
@@ -521,12 +522,13 @@ static conegs_status render_front(conegs_view *v, unsigned flags, cudaStream_t s
                                  v->gcone.as<float2>(), v->gflag.as<uint8_t>(), s));
     CUDA_TRY(cudaMemsetAsync(v->sums.as<unsigned long long>() + 2, 0, sizeof(unsigned long long), s));
     {
+        const bool ut = (flags & CONEGS_BIN_UT) != 0;
         const unsigned long long cap = std::min<unsigned long long>(v->binlist.bytes / sizeof(uint32_t), 0xffffffffull);
         CUDA_TRY(launch_bin_count(c, sp.binrec, v->gview.as<float4>(), v->gcone.as<float2>(), v->gflag.as<uint8_t>(),
                                   v->table.as<float>(), v->super.as<float>(), v->mcam.as<float>(),
                                   zf_bound(c, flags), n, v->counts.as<uint32_t>(), v->bincache.as<uint4>(),
-                                  v->binlist.as<uint32_t>(),
-                                  v->sums.as<unsigned long long>() + 2, cap, s));
+                                  v->binlist.as<uint32_t>(), v->sums.as<unsigned long long>() + 2, cap,
+                                  ut ? sp.means : nullptr, ut ? sp.W : nullptr, ut ? sp.sig_eff : nullptr, s));
     }
     CUDA_TRY(sum_counts(v->counts.as<uint32_t>(), n, v->sums.as<unsigned long long>(), s));
     CUDA_TRY(exclusive_scan(v->counts.as<uint32_t>(), v->vispos.as<uint32_t>(), n, v->scan_scr.as<uint32_t>(), 1, s));
@@ -575,7 +577,8 @@ static conegs_status render_back(conegs_view *v, float *out_rgb, float *out_T, u
     CUDA_TRY(launch_bin_emit(c, sp.binrec, v->gview.as<float4>(), v->gcone.as<float2>(), v->gflag.as<uint8_t>(),
                              v->table.as<float>(), v->super.as<float>(), v->mcam.as<float>(), zf_bound(c, flags), M,
                              v->dvals.as<uint32_t>(), v->offsets.as<uint32_t>(), v->bincache.as<uint4>(),
-                             v->binlist.as<uint32_t>(), v->pair_tile.as<uint32_t>(), v->pair_gid.as<uint32_t>(), s));
+                             v->binlist.as<uint32_t>(), v->pair_tile.as<uint32_t>(), v->pair_gid.as<uint32_t>(),
+                             (flags & CONEGS_BIN_UT) != 0, s));
     CUDA_TRY(radix_sort_pairs(v->pair_tile.as<uint32_t>(), v->pair_gid.as<uint32_t>(), v->pair_tile_alt.as<uint32_t>(),
                               v->pair_gid_alt.as<uint32_t>(), Pn, 0, bits_for(nt), v->rs_scr.as<uint32_t>(), s));
     CUDA_TRY(launch_ranges(v->pair_tile.as<uint32_t>(), Pn, v->ranges.as<uint2>(), nt, s));

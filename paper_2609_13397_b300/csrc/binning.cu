@@ -281,6 +281,181 @@ __device__ __forceinline__ bool kb_tile_box(const CamParams &c, const float4 gv,
     return true;
 }
 
+// ---------------------------------------------------------------- unscented-transform binning
+//
+// The alternative binning backbone of the 3DGUT family the paper renders with
+// (Sec. 3): each Gaussian is bounded on the image by an unscented transform of
+// its floored 3D distribution through the camera's own model, and a tile is
+// kept when its pixel-centre rectangle meets the ellipse of alpha >= 1/255.
+// The response (Eq. 9) is unchanged.  Definition (scaled UT with alpha = 1,
+// beta = 2, kappa = 0, n = 3): sigma points mu and mu +- sqrt(3) s_eff,i R_i,
+// mean weights 0 and 1/6, covariance weights 2 and 1/6; Sigma_2 gets I/12 px^2
+// (the half-pixel footprint of Eq. 8 on the image); k^2 = 2 ln(255 sigma_eff).
+// Gaussians with a sigma point outside the camera's domain (pinhole p_z <
+// 0.1 |p|, fisheye polar angle > theta_lim) keep the angular-tile rule.
+//
+// The ellipse is formed in the count pass only and kept in the bin cache when
+// the emit pass has to test tiles again, so both passes take every decision
+// from the same floats; the tile test is a fixed sequence of correctly rounded
+// operations, identical in both passes.
+struct UtArgs {
+    const float *means;     // [n][3]
+    const float *W;         // [n][9] W_eff = S_eff^-1 R^T
+    const float *sig_eff;   // [n]
+};
+
+constexpr float UT_COSMIN = 0.1f;
+constexpr float UT_VLP = 1.0f / 12.0f;
+constexpr uint32_t CACHE_UT = 2u;      // cache header .w: UT box and ellipse kept, tiles tested again
+
+// Image of a camera-frame point under the fisheye model relative to the
+// principal point (pixels); the caller has checked theta <= theta_lim.
+__device__ __forceinline__ float2 ut_kb_image(const CamParams &c, float px, float py, float pz) {
+    const float rho = sqrtf(px * px + py * py);
+    const float th = atan2f(rho, pz);
+    const float sc = rho > 0.0f ? kb_radius(c, th) / rho : 1.0f / pz;
+    return make_float2(c.fx * (sc * px), c.fy * (sc * py));
+}
+
+// The UT image ellipse of Gaussian gid: e = (ybar_x, ybar_y, A, B, C) with
+// [[A,B],[B,C]] = Sigma_2^-1, q = (k^2, -B/C, -B/A), and the candidate tile box.
+// Returns false when a sigma point leaves the camera's domain.
+__device__ bool ut_ellipse(const CamParams &c, const UtArgs &ua, uint32_t gid, float e[5], float4 &q, int &tx0,
+                           int &tx1, int &ty0, int &ty1) {
+    const float m0 = ua.means[3 * (size_t)gid] - c.o[0], m1 = ua.means[3 * (size_t)gid + 1] - c.o[1],
+                m2 = ua.means[3 * (size_t)gid + 2] - c.o[2];
+    // camera frame (R maps camera to world): p = R^T (mu - o)
+    const float p0x = c.R[0] * m0 + c.R[3] * m1 + c.R[6] * m2;
+    const float p0y = c.R[1] * m0 + c.R[4] * m1 + c.R[7] * m2;
+    const float p0z = c.R[2] * m0 + c.R[5] * m1 + c.R[8] * m2;
+    float D[3][3];   // camera-frame sigma offsets sqrt(3) s_i R_i = sqrt(3) row_i(W) / |row_i(W)|^2
+    const float *W = ua.W + 9 * (size_t)gid;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float w0 = W[3 * i], w1 = W[3 * i + 1], w2 = W[3 * i + 2];
+        const float f = 1.7320508f / (w0 * w0 + w1 * w1 + w2 * w2);
+        D[i][0] = f * (c.R[0] * w0 + c.R[3] * w1 + c.R[6] * w2);
+        D[i][1] = f * (c.R[1] * w0 + c.R[4] * w1 + c.R[7] * w2);
+        D[i][2] = f * (c.R[2] * w0 + c.R[5] * w1 + c.R[8] * w2);
+    }
+    // domain of all seven points
+    const float kb_c2 = cosf(c.thlim);
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < 7; ++j) {
+        const int i = (j - 1) >> 1;
+        const float sg = (j & 1) ? 1.0f : -1.0f;
+        const float px = j == 0 ? p0x : p0x + sg * D[i][0];
+        const float py = j == 0 ? p0y : p0y + sg * D[i][1];
+        const float pz = j == 0 ? p0z : p0z + sg * D[i][2];
+        const float n2 = px * px + py * py + pz * pz;
+        if (c.model == 0) {
+            ok = ok && pz > 0.0f && pz * pz >= UT_COSMIN * UT_COSMIN * n2;
+        } else {
+            // theta <= theta_lim  <=>  p_z >= cos(theta_lim) |p|  (theta_lim < pi)
+            const float nn = sqrtf(n2);
+            ok = ok && nn > 0.0f && pz >= kb_c2 * nn;
+        }
+    }
+    if (!ok) return false;
+    // image offsets of the six outer points from the centre's image
+    float dxs[6], dys[6], y0x, y0y;
+    if (c.model == 0) {
+        const float iz = 1.0f / p0z;
+        y0x = c.fx * (p0x * iz) + c.cx;
+        y0y = c.fy * (p0y * iz) + c.cy;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            // u(p0 +- D) - u(p0) = +- f_x (D_x p0z - p0x D_z) / ((p0z +- D_z) p0z): no cancellation
+            const float nx = D[i][0] * p0z - p0x * D[i][2], ny = D[i][1] * p0z - p0y * D[i][2];
+            const float ip = 1.0f / ((p0z + D[i][2]) * p0z), im = 1.0f / ((p0z - D[i][2]) * p0z);
+            dxs[2 * i] = c.fx * nx * ip;
+            dys[2 * i] = c.fy * ny * ip;
+            dxs[2 * i + 1] = -c.fx * nx * im;
+            dys[2 * i + 1] = -c.fy * ny * im;
+        }
+    } else {
+        const float2 y0 = ut_kb_image(c, p0x, p0y, p0z);
+        y0x = y0.x + c.cx;
+        y0y = y0.y + c.cy;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const float2 a = ut_kb_image(c, p0x + D[i][0], p0y + D[i][1], p0z + D[i][2]);
+            const float2 b = ut_kb_image(c, p0x - D[i][0], p0y - D[i][1], p0z - D[i][2]);
+            dxs[2 * i] = a.x - y0.x;
+            dys[2 * i] = a.y - y0.y;
+            dxs[2 * i + 1] = b.x - y0.x;
+            dys[2 * i + 1] = b.y - y0.y;
+        }
+    }
+    // mean (weights 1/6 on the outer points, 0 on the centre) and covariance
+    // 2 (0 - mbar)(0 - mbar)^T + sum_j (1/6)(d_j - mbar)(d_j - mbar)^T = (1/6) sum_j d_j d_j^T + mbar mbar^T
+    float mx = 0.f, my = 0.f, sxx = 0.f, sxy = 0.f, syy = 0.f;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        mx += dxs[j];
+        my += dys[j];
+        sxx += dxs[j] * dxs[j];
+        sxy += dxs[j] * dys[j];
+        syy += dys[j] * dys[j];
+    }
+    mx *= (1.0f / 6.0f);
+    my *= (1.0f / 6.0f);
+    sxx = sxx * (1.0f / 6.0f) + mx * mx + UT_VLP;
+    sxy = sxy * (1.0f / 6.0f) + mx * my;
+    syy = syy * (1.0f / 6.0f) + my * my + UT_VLP;
+    const float idet = 1.0f / (sxx * syy - sxy * sxy);
+    const float k2 = 2.0f * logf(255.0f * ua.sig_eff[gid]);
+    e[0] = y0x + mx;
+    e[1] = y0y + my;
+    e[2] = syy * idet;
+    e[3] = -sxy * idet;
+    e[4] = sxx * idet;
+    q = make_float4(k2, -e[3] / e[4], -e[3] / e[2], 0.0f);
+    if (!(k2 > 0.0f)) {
+        tx0 = ty0 = 0;
+        tx1 = ty1 = -1;
+        return true;
+    }
+    // tiles whose pixel-centre rectangle [8 t + 1/2, 8 t + 15/2] meets the ellipse's
+    // bounding box (widened by far more than its FP32 error; the test decides)
+    const float hx = sqrtf(k2 * sxx), hy = sqrtf(k2 * syy);
+    const float gx = 0.01f + 1e-3f * hx, gy = 0.01f + 1e-3f * hy;
+    const float lim = 1e8f;
+    tx0 = max((int)ceilf(fmaxf((e[0] - hx - gx - (TILE - 0.5f)) / TILE, -lim)), 0);
+    tx1 = min((int)floorf(fminf((e[0] + hx + gx - 0.5f) / TILE, lim)), c.tiles_x - 1);
+    ty0 = max((int)ceilf(fmaxf((e[1] - hy - gy - (TILE - 0.5f)) / TILE, -lim)), 0);
+    ty1 = min((int)floorf(fminf((e[1] + hy + gy - 0.5f) / TILE, lim)), c.tiles_y - 1);
+    return true;
+}
+
+// Tile (tx, ty) against a UT ellipse: min over the tile's pixel-centre rectangle
+// of Q(y) = (y - ybar)^T [[A,B],[B,C]] (y - ybar) <= k^2.  With ybar outside the
+// rectangle the minimum lies on an edge whose line separates ybar from it, at
+// the clamped stationary point of Q along that edge.
+__device__ __forceinline__ bool ut_tile_test(const CamParams &c, const float e[5], const float4 q, int tx,
+                                             int ty) {
+    const float x0 = (float)(TILE * tx) + 0.5f, y0 = (float)(TILE * ty) + 0.5f;
+    const float x1 = fminf(x0 + (float)(TILE - 1), (float)c.W - 0.5f);
+    const float y1 = fminf(y0 + (float)(TILE - 1), (float)c.H - 0.5f);
+    const float dx0 = r_sub(x0, e[0]), dx1 = r_sub(x1, e[0]), dy0 = r_sub(y0, e[1]), dy1 = r_sub(y1, e[1]);
+    const bool sx = dx0 > 0.0f || dx1 < 0.0f, sy = dy0 > 0.0f || dy1 < 0.0f;
+    if (!sx && !sy) return true;
+    float best = 3.0e38f;
+    if (sx) {
+        const float x = dx0 > 0.0f ? dx0 : dx1;
+        const float y = fminf(fmaxf(r_mul(q.y, x), dy0), dy1);
+        best = r_add(r_mul(x, r_add(r_mul(e[2], x), r_mul(2.0f, r_mul(e[3], y)))), r_mul(e[4], r_mul(y, y)));
+    }
+    if (sy) {
+        const float y = dy0 > 0.0f ? dy0 : dy1;
+        const float x = fminf(fmaxf(r_mul(q.z, y), dx0), dx1);
+        best = fminf(best, r_add(r_mul(x, r_add(r_mul(e[2], x), r_mul(2.0f, r_mul(e[3], y)))),
+                                 r_mul(e[4], r_mul(y, y))));
+    }
+    return best <= q.x;
+}
+
 // Count (MODE 0) and emit (MODE 1) of the (tile, Gaussian) pairs.
 //
 // Each lane prepares one Gaussian (slot): flag, rule record, direction, cone,
@@ -364,12 +539,14 @@ __device__ __forceinline__ uint32_t bin_walk_supers(const CamParams &c, const fl
 
 // Candidate box of one Gaussian walked by the whole warp; returns its pair count
 // and (boxes of at most MASK_MAX tiles) its pass mask in m (same on every lane).
-template <int MODE>
+// ut: the slot is a UT ellipse (g[0..4] = ybar, A, B, C; gv = k^2, -B/C, -B/A).
+template <int MODE, bool UT>
 __device__ __forceinline__ uint32_t bin_walk_box(const CamParams &c, const float *g, const float4 gv,
                                                  const float2 half, const float *__restrict__ table, float mzf,
                                                  int tx0, int ty0, int bw, uint32_t nb, uint32_t gid, uint32_t base,
                                                  uint32_t m[8], uint32_t *__restrict__ list,
-                                                 uint32_t *__restrict__ out_tile, uint32_t *__restrict__ out_gid) {
+                                                 uint32_t *__restrict__ out_tile, uint32_t *__restrict__ out_gid,
+                                                 bool ut) {
     const int lane = threadIdx.x & 31;
     uint32_t cnt = 0;
     int qy = 0, qx = lane;                     // candidate k0 + lane = qy * bw + qx
@@ -383,11 +560,15 @@ __device__ __forceinline__ uint32_t bin_walk_box(const CamParams &c, const float
         uint32_t tile = 0;
         if (k0 + (uint32_t)lane < nb) {
             tile = (uint32_t)((ty0 + qy) * c.tiles_x + tx0 + qx);
-            float tt[6];
-            tile_record(table, tile, mzf, tt);
-            if (cone_prefilter(gv, half, tt)) {
-                const int f = rule_test_fast(g, gv, tt);
-                tp = f == 2 ? rule_test(g, gv, tt) : f == 1;
+            if (UT && ut) {
+                tp = ut_tile_test(c, g, gv, tx0 + qx, ty0 + qy);
+            } else {
+                float tt[6];
+                tile_record(table, tile, mzf, tt);
+                if (cone_prefilter(gv, half, tt)) {
+                    const int f = rule_test_fast(g, gv, tt);
+                    tp = f == 2 ? rule_test(g, gv, tt) : f == 1;
+                }
             }
         }
         const uint32_t tb = __ballot_sync(0xffffffffu, tp);
@@ -413,8 +594,9 @@ __device__ __forceinline__ uint32_t bin_walk_box(const CamParams &c, const float
     return cnt;
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(32 * BIN_WARPS, 3) bin_kernel(CamParams c, const float *__restrict__ binrec,
+template <int MODE, bool UT>
+__global__ void __launch_bounds__(32 * BIN_WARPS, 3) bin_kernel(CamParams c, UtArgs ua,
+                                                                const float *__restrict__ binrec,
                                                                 const float4 *__restrict__ gview,
                                                                 const float2 *__restrict__ gcone,
                                                                 const uint8_t *__restrict__ gflag,
@@ -434,7 +616,7 @@ __global__ void __launch_bounds__(32 * BIN_WARPS, 3) bin_kernel(CamParams c, con
     __shared__ float s_g[BIN_WARPS][5][32];        // kap, ks, kr, r1sq, s2 (flag is 1 for boxed slots)
     __shared__ float4 s_gv[BIN_WARPS][32];
     __shared__ float2 s_half[BIN_WARPS][32];
-    __shared__ int4 s_box[BIN_WARPS][32];          // tx0, ty0, box width, cached (1) or not
+    __shared__ int4 s_box[BIN_WARPS][32];          // tx0, ty0, box width, bits: cached (1), UT ellipse (2)
     __shared__ float s_inv[BIN_WARPS][32];         // 1 / box width
     __shared__ uint4 s_mask[BIN_WARPS][2][32];     // MODE 1: cached pass mask (8 words)
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -444,7 +626,7 @@ __global__ void __launch_bounds__(32 * BIN_WARPS, 3) bin_kernel(CamParams c, con
     const uint32_t base = (MODE == 1 && have) ? offsets[pos] : 0u;
     // ---- slot set-up
     uint32_t nb = 0, fl = 0, npk = 0, lofs = 0, lcnt = 0;
-    bool walk = false, cached = false, big = false, listed = false;
+    bool walk = false, cached = false, big = false, listed = false, utslot = false;
     float g[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float4 gv = make_float4(0.f, 0.f, 0.f, 0.f);
     float2 half = make_float2(0.f, 1.f);
@@ -457,6 +639,21 @@ __global__ void __launch_bounds__(32 * BIN_WARPS, 3) bin_kernel(CamParams c, con
                 listed = true;
                 lofs = cc.x;
                 lcnt = cc.y;
+            } else if (UT && cc.w == CACHE_UT) {
+                // a UT slot whose tiles are tested again: box and ellipse from the count pass
+                utslot = true;
+                tx0 = (int)(cc.x & 0xffffu);
+                ty0 = (int)(cc.x >> 16);
+                tx1 = (int)(cc.y & 0xffffu);
+                ty1 = (int)(cc.y >> 16);
+                const uint4 e0 = cache[3 * (size_t)gid + 1], e1 = cache[3 * (size_t)gid + 2];
+                g[0] = __uint_as_float(e0.x); g[1] = __uint_as_float(e0.y); g[2] = __uint_as_float(e0.z);
+                g[3] = __uint_as_float(e0.w); g[4] = __uint_as_float(e1.x);
+                g[5] = 3.0f;
+                gv = make_float4(__uint_as_float(e1.y), __uint_as_float(e1.z), __uint_as_float(e1.w), 0.0f);
+                nb = (uint32_t)(tx1 - tx0 + 1) * (uint32_t)(ty1 - ty0 + 1);
+                big = nb > PACK_MAX;
+                npk = big ? 0u : nb;
             } else if (cc.w == CACHE_MASK) {
                 cached = true;
                 tx0 = (int)(cc.x & 0xffffu);
@@ -470,7 +667,19 @@ __global__ void __launch_bounds__(32 * BIN_WARPS, 3) bin_kernel(CamParams c, con
                                  __popc(m1.y) + __popc(m1.z) + __popc(m1.w));
             }
         }
-        if (fl != 0 && !cached && !listed) {
+        if (MODE == 0 && UT && fl == 1) {
+            float4 uq;
+            if (ut_ellipse(c, ua, gid, g, uq, tx0, tx1, ty0, ty1)) {
+                utslot = true;
+                g[5] = 3.0f;
+                gv = uq;
+                const int bw = tx1 - tx0 + 1, bh = ty1 - ty0 + 1;
+                nb = (bw > 0 && bh > 0) ? (uint32_t)(bw * bh) : 0u;
+                big = nb > PACK_MAX;
+                npk = big ? 0u : nb;
+            }
+        }
+        if (fl != 0 && !cached && !listed && !utslot) {
 #pragma unroll
             for (int k = 0; k < 5; ++k) g[k] = binrec[6 * (size_t)gid + k];
             g[5] = (float)fl;
@@ -494,7 +703,7 @@ __global__ void __launch_bounds__(32 * BIN_WARPS, 3) bin_kernel(CamParams c, con
     s_g[wid][3][lane] = g[3]; s_g[wid][4][lane] = g[4];
     s_gv[wid][lane] = gv;
     s_half[wid][lane] = half;
-    s_box[wid][lane] = make_int4(tx0, ty0, tx1 - tx0 + 1, cached ? 1 : 0);
+    s_box[wid][lane] = make_int4(tx0, ty0, tx1 - tx0 + 1, (cached ? 1 : 0) | (utslot ? 2 : 0));
     s_inv[wid][lane] = tx1 >= tx0 ? 1.0f / (float)(tx1 - tx0 + 1) : 0.0f;
     // exclusive prefix of the packed slots' candidate counts (a cached slot of the emit
     // pass contributes its passing candidates only; big boxes are walked below)
@@ -526,7 +735,7 @@ __global__ void __launch_bounds__(32 * BIN_WARPS, 3) bin_kernel(CamParams c, con
         if (p < total) {
             uint32_t k = p - sstart;
             const int4 bx = s_box[wid][sl];
-            if (MODE == 1 && bx.w) {
+            if (MODE == 1 && (bx.w & 1)) {
                 // the k-th passing candidate of a cached slot: the (k+1)-th set bit of its mask
                 const uint4 m0 = s_mask[wid][0][sl], m1 = s_mask[wid][1][sl];
                 const uint32_t mw[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
@@ -555,15 +764,19 @@ __global__ void __launch_bounds__(32 * BIN_WARPS, 3) bin_kernel(CamParams c, con
                 kx -= bx.z;
             }
             tile = (uint32_t)((bx.y + ky) * c.tiles_x + bx.x + kx);
-            if (!(MODE == 1 && bx.w)) {
+            if (!(MODE == 1 && (bx.w & 1))) {
                 const float gg[6] = {s_g[wid][0][sl], s_g[wid][1][sl], s_g[wid][2][sl], s_g[wid][3][sl],
                                      s_g[wid][4][sl], 1.0f};
                 const float4 sgv = s_gv[wid][sl];
-                float tt[6];
-                tile_record(table, tile, mzf, tt);
-                if (cone_prefilter(sgv, s_half[wid][sl], tt)) {
-                    const int f = rule_test_fast(gg, sgv, tt);
-                    tp = f == 2 ? rule_test(gg, sgv, tt) : f == 1;
+                if (UT && (bx.w & 2)) {
+                    tp = ut_tile_test(c, gg, sgv, bx.x + kx, bx.y + ky);
+                } else {
+                    float tt[6];
+                    tile_record(table, tile, mzf, tt);
+                    if (cone_prefilter(sgv, s_half[wid][sl], tt)) {
+                        const int f = rule_test_fast(gg, sgv, tt);
+                        tp = f == 2 ? rule_test(gg, sgv, tt) : f == 1;
+                    }
                 }
             }
         }
@@ -619,8 +832,8 @@ __global__ void __launch_bounds__(32 * BIN_WARPS, 3) bin_kernel(CamParams c, con
             lo = __shfl_sync(0xffffffffu, lo, 0);
             if (lo + bnb <= bcap) lst = blist + lo;
         }
-        const uint32_t wc = bin_walk_box<MODE>(c, gg, sgv, sh, table, mzf, btx0, bty0, bw, bnb, sgid, sbase, wm,
-                                               lst, out_tile, out_gid);
+        const uint32_t wc = bin_walk_box<MODE, UT>(c, gg, sgv, sh, table, mzf, btx0, bty0, bw, bnb, sgid, sbase,
+                                                   wm, lst, out_tile, out_gid, gg[5] == 3.0f);
         if (lane == sl) {
             cnt = wc;
 #pragma unroll
@@ -671,6 +884,13 @@ __global__ void __launch_bounds__(32 * BIN_WARPS, 3) bin_kernel(CamParams c, con
             cache[3 * (size_t)gid + 2] = make_uint4(pm[4], pm[5], pm[6], pm[7]);
         } else if (listed) {
             cache[3 * (size_t)gid] = make_uint4(lofs, cnt, 0u, CACHE_LIST);
+        } else if (UT && utslot) {
+            cache[3 * (size_t)gid] = make_uint4((uint32_t)tx0 | ((uint32_t)ty0 << 16),
+                                                (uint32_t)tx1 | ((uint32_t)ty1 << 16), 0u, CACHE_UT);
+            cache[3 * (size_t)gid + 1] = make_uint4(__float_as_uint(g[0]), __float_as_uint(g[1]),
+                                                    __float_as_uint(g[2]), __float_as_uint(g[3]));
+            cache[3 * (size_t)gid + 2] = make_uint4(__float_as_uint(g[4]), __float_as_uint(gv.x),
+                                                    __float_as_uint(gv.y), __float_as_uint(gv.z));
         } else {
             cache[3 * (size_t)gid] = make_uint4(0u, 0u, 0u, NO_CACHE);
         }
@@ -706,14 +926,23 @@ cudaError_t launch_gauss_view_rule(const CamParams &c, const SceneParams &sp, fl
     return cudaGetLastError();
 }
 
+// ut_means/ut_W/ut_sig_eff non-null: UT binning (the scene's means, W_eff and sigma_eff).
 cudaError_t launch_bin_count(const CamParams &c, const float *binrec, const float4 *gview, const float2 *gcone,
                              const uint8_t *gflag, const float *table, const float *super, const float *mcam,
                              float mzf, int64_t n, uint32_t *counts, uint4 *cache, uint32_t *blist,
-                             unsigned long long *bcursor, unsigned long long bcap, cudaStream_t s) {
+                             unsigned long long *bcursor, unsigned long long bcap, const float *ut_means,
+                             const float *ut_W, const float *ut_sig_eff, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    bin_kernel<0><<<(unsigned)div_up(n, 32 * BIN_WARPS), 32 * BIN_WARPS, 0, s>>>(
-        c, binrec, gview, gcone, gflag, table, super, mcam, mzf, n, nullptr, nullptr, counts, cache, blist, bcursor,
-        bcap, nullptr, nullptr);
+    const UtArgs ua{ut_means, ut_W, ut_sig_eff};
+    const unsigned grid = (unsigned)div_up(n, 32 * BIN_WARPS);
+    if (ut_means)
+        bin_kernel<0, true><<<grid, 32 * BIN_WARPS, 0, s>>>(c, ua, binrec, gview, gcone, gflag, table, super, mcam,
+                                                           mzf, n, nullptr, nullptr, counts, cache, blist, bcursor,
+                                                           bcap, nullptr, nullptr);
+    else
+        bin_kernel<0, false><<<grid, 32 * BIN_WARPS, 0, s>>>(c, ua, binrec, gview, gcone, gflag, table, super, mcam,
+                                                            mzf, n, nullptr, nullptr, counts, cache, blist, bcursor,
+                                                            bcap, nullptr, nullptr);
     note_launches(1);
     return cudaGetLastError();
 }
@@ -722,11 +951,21 @@ cudaError_t launch_bin_emit(const CamParams &c, const float *binrec, const float
                             const uint8_t *gflag, const float *table, const float *super, const float *mcam,
                             float mzf, int64_t n_sorted, const uint32_t *order, const uint32_t *offsets,
                             const uint4 *cache, const uint32_t *blist, uint32_t *out_tile, uint32_t *out_gid,
-                            cudaStream_t s) {
+                            bool ut, cudaStream_t s) {
     if (n_sorted == 0) return cudaSuccess;
-    bin_kernel<1><<<(unsigned)div_up(n_sorted, 32 * BIN_WARPS), 32 * BIN_WARPS, 0, s>>>(
-        c, binrec, gview, gcone, gflag, table, super, mcam, mzf, n_sorted, order, offsets, nullptr,
-        const_cast<uint4 *>(cache), const_cast<uint32_t *>(blist), nullptr, 0ull, out_tile, out_gid);
+    const UtArgs ua{nullptr, nullptr, nullptr};
+    const unsigned grid = (unsigned)div_up(n_sorted, 32 * BIN_WARPS);
+    if (ut)
+        bin_kernel<1, true><<<grid, 32 * BIN_WARPS, 0, s>>>(c, ua, binrec, gview, gcone, gflag, table, super, mcam,
+                                                           mzf, n_sorted, order, offsets, nullptr,
+                                                           const_cast<uint4 *>(cache), const_cast<uint32_t *>(blist),
+                                                           nullptr, 0ull, out_tile, out_gid);
+    else
+        bin_kernel<1, false><<<grid, 32 * BIN_WARPS, 0, s>>>(c, ua, binrec, gview, gcone, gflag, table, super, mcam,
+                                                            mzf, n_sorted, order, offsets, nullptr,
+                                                            const_cast<uint4 *>(cache),
+                                                            const_cast<uint32_t *>(blist), nullptr, 0ull, out_tile,
+                                                            out_gid);
     note_launches(1);
     return cudaGetLastError();
 }
