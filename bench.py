@@ -268,6 +268,32 @@ def run_ours(args, rank, world, local_rank):
     except cg.ConegsError as e:
         fwd_bwd = {"value": None, "unavailable": str(e)[:120]}
 
+    # the same forward step with unscented-transform binning (the 3DGUT-style backbone):
+    # fewer pairs, approximate (a pair its ellipse misses is not evaluated)
+    for _ in range(2):
+        step(flags=cg.BIN_UT)
+    torch.cuda.synchronize()
+    ev_ut = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev_ut[k][0].record(main)
+        step(flags=cg.BIN_UT)
+        ev_ut[k][1].record(main)
+    torch.cuda.synchronize()
+    ut_ms = reduce_step_time(sum(a.elapsed_time(b) for a, b in ev_ut) / args.steps, dev)
+    ut_pairs = [v.stats()["n_pairs"] for v in views]
+    # what the approximation loses: the UT images against the exact (angular-tile rule) ones
+    ut_imgs = [o[0].clone() for o in outs]
+    step()
+    torch.cuda.synchronize()
+    loss = []
+    for (o, _), u in zip(outs, ut_imgs):
+        d = (o - u).abs()
+        loss.append({"mean_abs_rgb": float(d.mean()), "frac_px_over_1_255": float((d.amax(0) > 1 / 255).float().mean())})
+    bin_ut = {"value": rays_per_step * world / (ut_ms * 1e-3) / 1e6, "unit": "Mrays/s", "ms_per_step": ut_ms,
+              "n_pairs": ut_pairs, "n_pairs_rule": [statistics.median(pv["n_pairs"]) for pv in per_view],
+              "vs_exact": loss}
+
     # end to end through the host-buffer entry point: camera in, image out every step
     host = [(torch.empty(3, c.height, c.width, pin_memory=True), torch.empty(c.height, c.width, pin_memory=True))
             for c in cams]
@@ -305,6 +331,7 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": WORKLOAD, "rays_per_step": rays_per_step, "gaussians": ctx.n,
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
         "fwd_bwd": fwd_bwd,
+        "bin_ut": bin_ut,
         "views": [{"camera": f"{c.width}x{c.height}", **{k: statistics.median(v) for k, v in pv.items()}}
                   for c, pv in zip(cams, per_view)],
         "roofline": {"bound": "alu", "kernel": "raster_seg_kernel<FILTER=1, FIRST=1> (1280x720 view)",
@@ -340,7 +367,7 @@ def run_probe(args):
     ctx.set_scene_from(sc, rho2=rho2)
     if args.probe == "raster-1/8":
         v.set_camera_from(cams[1])
-    flags = cg.KEEP_FOR_BACKWARD if args.probe == "backward" else 0
+    flags = {"backward": cg.KEEP_FOR_BACKWARD, "ut": cg.BIN_UT}.get(args.probe, 0)
     for _ in range(3):
         rgb, _ = v.render(flags=flags)
         if args.probe == "backward":
@@ -417,11 +444,20 @@ def run_config(args):
             fwd_bwd()
         ms_f = _timed(fwd, args.steps, main_s)
         ms_fb = _timed(fwd_bwd, args.steps, main_s)
+        v.render(out_rgb=out[0], out_T=out[1])
+        exact = out[0].clone()
+        v.render(flags=cg.BIN_UT, out_rgb=out[0], out_T=out[1])
+        dut = (out[0] - exact).abs()
+        ut_loss = {"mean_abs_rgb": float(dut.mean()), "frac_px_over_1_255": float((dut.amax(0) > 1 / 255).float().mean())}
+        ms_ut = _timed(lambda: v.render(flags=cg.BIN_UT, out_rgb=out[0], out_T=out[1]), args.steps, main_s)
+        ut_pairs = v.stats()["n_pairs"]
         v.render(flags=cg.PROFILE, out_rgb=out[0], out_T=out[1])
         st = v.stats()
         _line(nval / ms_f / 1e3, ms_f, args,
               "C3: KB fisheye 190 deg 1024x1024, k~U(-0.05,0.05), 1M Gaussians; L1 vs perturbed-scene render",
               {"fwd_bwd": {"value": nval / ms_fb / 1e3, "unit": "Mrays/s", "ms_per_step": ms_fb},
+               "bin_ut": {"value": nval / ms_ut / 1e3, "unit": "Mrays/s", "ms_per_step": ms_ut, "n_pairs": ut_pairs,
+                          "vs_exact": ut_loss},
                "rays_per_step": nval, "pairs": st["n_pairs"],
                "profile": {k: st[k] for k in ("n_visible", "n_walked", "n_evaluated", "ms_preprocess", "ms_sort",
                                               "ms_raster", "ms_total")}})
@@ -538,7 +574,7 @@ def main():
     ap.add_argument("--c5-slots", type=int, default=6)
     ap.add_argument("--c5-gaussians", type=int, default=5_000_000)
     ap.add_argument("--c5-sweep", default="50,100,125,150", help="request rates (Hz) of the C5 rate sweep")
-    ap.add_argument("--probe", choices=["raster", "raster-1/8", "backward"], default=None,
+    ap.add_argument("--probe", choices=["raster", "raster-1/8", "backward", "ut"], default=None,
                     help="set up C2 and render 3 times for a profiler capture (prints no JSON)")
     args = ap.parse_args()
     if args.probe:
