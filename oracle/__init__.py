@@ -268,11 +268,13 @@ def tile_table(cam) -> np.ndarray:
 
 
 def bin_gauss(cam, scene) -> np.ndarray:
+    """Per-Gaussian binning records [n,16]: u (3), L, kap, ks, kr, r1sq, s2, flag, Sigma_eff (6)."""
     n = scene.n
-    out = np.zeros((n, 10), np.float32)
+    out = np.zeros((n, 16), np.float32)
     lib().or_bin_gauss(_p(pack_camera(cam)), ctypes.c_int(n), _p(_f(scene.means), ctypes.c_float),
-                       _p(_f(scene.log_scales), ctypes.c_float), _p(_f(scene.opacity_logits), ctypes.c_float),
-                       _p(_f(scene.rho2), ctypes.c_float), _p(out, ctypes.c_float))
+                       _p(_f(scene.log_scales), ctypes.c_float), _p(_f(scene.quats), ctypes.c_float),
+                       _p(_f(scene.opacity_logits), ctypes.c_float), _p(_f(scene.rho2), ctypes.c_float),
+                       _p(out, ctypes.c_float))
     return out
 
 
@@ -296,9 +298,10 @@ def bin_counts(cam, scene, dense: bool = False, zf: bool = False):
     pg = np.zeros(n, np.int32)
     pt = np.zeros(nt, np.int32)
     pas = np.zeros((n, nt), np.uint8) if dense else None
+    means = _f(scene.means)
     total = lib().or_bin_counts(_p(pack_camera(cam)), _p(table, ctypes.c_float), ctypes.c_int(n),
-                                _p(recs, ctypes.c_float), _p(pg, ctypes.c_int), _p(pt, ctypes.c_int),
-                                _p(pas, ctypes.c_ubyte) if dense else None)
+                                _p(recs, ctypes.c_float), _p(means, ctypes.c_float), _p(pg, ctypes.c_int),
+                                _p(pt, ctypes.c_int), _p(pas, ctypes.c_ubyte) if dense else None)
     return int(total), pg, pt, pas
 
 

@@ -1216,9 +1216,13 @@ static float f_exp(float x) {
     return p * two.f;
 }
 
-/* Per-Gaussian binning record (10 floats): u0 u1 u2 L kap ks kr r1sq s2 flag
- * flag: 0 culled (can never reach alpha >= 1/255), 1 normal, 2 pass-all. */
-static void fgauss(const fcam *c, const float *mu, const float *ls, float logit, float rho2, float *rec) {
+/* Per-Gaussian binning record (16 floats): u0 u1 u2 L kap ks kr r1sq s2 flag
+ * Sigma_eff (xx xy xz yy yz zz); flag: 0 culled (can never reach alpha >=
+ * 1/255), 1 normal, 2 pass-all. */
+static void fsigma(const float *q, const float *ls, float rho2, float *S);
+
+static void fgauss(const fcam *c, const float *mu, const float *ls, const float *q, float logit, float rho2,
+                   float *rec) {
     const float K255 = 11.082528f; /* >= 2 ln 255 */
     const float LN2LO = 0.6931471f; /* <= ln 2 */
     float lmax = fmaxf(fmaxf(ls[0], ls[1]), ls[2]);
@@ -1230,6 +1234,7 @@ static void fgauss(const fcam *c, const float *mu, const float *ls, float logit,
     float L2 = (v0 * v0 + v1 * v1) + v2 * v2;
     float L = sqrtf(L2);
     for (int i = 0; i < 10; ++i) rec[i] = 0.0f;
+    fsigma(q, ls, rho2, rec + 10);
     rec[3] = L;
     if (!(kap2 > 0.0f)) { rec[9] = 0.0f; return; }
     if (!(L > 0.0f)) { rec[9] = 2.0f; return; }
@@ -1281,48 +1286,206 @@ static int ftest(const float *g, const float *t) {
     return ch2 <= lim * lim;
 }
 
-/* Per-Gaussian binning records [n*10] for one camera (FP32 inputs). */
-void or_bin_gauss(const double *campk, int n, const float *means, const float *log_scales, const float *logits,
-                  const float *rho2, float *recs) {
+/* Silhouette ellipse of the rule's bounding ellipsoid (pinhole cameras).
+ * A contributing pair's ray meets E = {x : (x - mu)^T C^-1 (x - mu) <= kap^2},
+ * C = Sigma_eff + t_b^2 m I; the lines through the camera centre that meet E
+ * trace an ellipse on the image plane.  Scene part: Sigma_eff (xx xy xz yy yz
+ * zz) from the FP32 quaternion and the rule's exp, s_eff^2 = exp(2 log s)
+ * 1.0001 + rho^2. */
+static void fsigma(const float *q, const float *ls, float rho2, float *S) {
+    float n2 = ((q[0] * q[0] + q[1] * q[1]) + q[2] * q[2]) + q[3] * q[3];
+    float inv = 1.0f / sqrtf(n2);
+    float w = q[0] * inv, x = q[1] * inv, y = q[2] * inv, z = q[3] * inv;
+    float R[9];
+    R[0] = 1.0f - 2.0f * (y * y + z * z);
+    R[1] = 2.0f * (x * y - w * z);
+    R[2] = 2.0f * (x * z + w * y);
+    R[3] = 2.0f * (x * y + w * z);
+    R[4] = 1.0f - 2.0f * (x * x + z * z);
+    R[5] = 2.0f * (y * z - w * x);
+    R[6] = 2.0f * (x * z - w * y);
+    R[7] = 2.0f * (y * z + w * x);
+    R[8] = 1.0f - 2.0f * (x * x + y * y);
+    float s2[3];
+    for (int a = 0; a < 3; ++a) s2[a] = f_exp(2.0f * ls[a]) * 1.0001f + rho2;
+    const int I[6] = {0, 0, 0, 1, 1, 2}, J[6] = {0, 1, 2, 1, 2, 2};
+    for (int k = 0; k < 6; ++k) {
+        int i = I[k], j = J[k];
+        S[k] = ((R[3 * i] * R[3 * j]) * s2[0] + (R[3 * i + 1] * R[3 * j + 1]) * s2[1]) +
+               (R[3 * i + 2] * R[3 * j + 2]) * s2[2];
+    }
+}
+
+/* View part: with v = (mu - o)/L in the camera frame, C normalised by its mean
+ * eigenvalue tau (+ 1e-4 I) and k^2 = kap^2 tau / L^2, a line of direction
+ * d = (x, y, 1) meets E iff delta = d - v/v_z satisfies
+ *   delta^T G delta - 2 h^T delta <= k0,  G = (a - k^2) Ci_xy - w_xy w_xy^T,
+ *   h = k^2 w_xy / v_z, k0 = k^2 a / v_z^2, w = Ci v, a = v^T w.
+ * Returns 1 with e = (centre x, centre y, A, B, C) in pixels and q =
+ * (1.01 * rhs, -B/C, -B/A); 0 when the test does not apply. */
+static int fellipse(const fcam *c, const float *g, const float *mu, float m, float *e, float *q) {
+    if (c->model != 0) return 0;
+    float L = g[3], kap = g[4], ks = g[5], kr = g[6], r1sq = g[7], s2 = g[8];
+    const float *S = g + 10;
+    float sm = sqrtf(m);
+    float cc = kr * sm;
+    float rfc = 255.0f * ks;
+    float tb, rf;
+    if (cc < 1.0f) {
+        float tbf = (L + ks) / (1.0f - cc);
+        float rff = kap * sqrtf(s2 + ((tbf * tbf) * r1sq) * m);
+        rf = fminf(rff, rfc);
+        tb = fminf(tbf, L + rf);
+    } else {
+        rf = rfc;
+        tb = L + rf;
+    }
+    if (!(L > rf)) return 0;
+    float w0 = mu[0] - c->o[0], w1 = mu[1] - c->o[1], w2 = mu[2] - c->o[2];
+    float iL = 1.0f / L;
+    float v[3];
+    for (int j = 0; j < 3; ++j) v[j] = ((c->R[j] * w0 + c->R[3 + j] * w1) + c->R[6 + j] * w2) * iL;
+    if (!(v[2] > 0.0f && v[2] * v[2] >= 0.05f)) return 0;
+    float Sf[9] = {S[0], S[1], S[2], S[1], S[3], S[4], S[2], S[4], S[5]};
+    float T[9];
+    for (int i = 0; i < 3; ++i)
+        for (int k = 0; k < 3; ++k)
+            T[3 * i + k] = (Sf[3 * i] * c->R[k] + Sf[3 * i + 1] * c->R[3 + k]) + Sf[3 * i + 2] * c->R[6 + k];
+    float Cc[6];
+    {
+        const int I[6] = {0, 0, 0, 1, 1, 2}, J[6] = {0, 1, 2, 1, 2, 2};
+        for (int k = 0; k < 6; ++k) {
+            int j = I[k], l = J[k];
+            Cc[k] = (c->R[j] * T[l] + c->R[3 + j] * T[3 + l]) + c->R[6 + j] * T[6 + l];
+        }
+    }
+    float iso = (tb * tb) * m + 1e-5f * s2;
+    Cc[0] = Cc[0] + iso;
+    Cc[3] = Cc[3] + iso;
+    Cc[5] = Cc[5] + iso;
+    float tau = ((Cc[0] + Cc[3]) + Cc[5]) / 3.0f;
+    float it = 1.0f / tau;
+    float cxx = Cc[0] * it + 1e-4f, cxy = Cc[1] * it, cxz = Cc[2] * it;
+    float cyy = Cc[3] * it + 1e-4f, cyz = Cc[4] * it, czz = Cc[5] * it + 1e-4f;
+    float k2 = ((kap * kap) * tau) / (L * L);
+    float a00 = cyy * czz - cyz * cyz;
+    float a01 = cxz * cyz - cxy * czz;
+    float a02 = cxy * cyz - cxz * cyy;
+    float a11 = cxx * czz - cxz * cxz;
+    float a12 = cxy * cxz - cxx * cyz;
+    float det = (cxx * a00 + cxy * a01) + cxz * a02;
+    if (!(det > 1e-12f)) return 0;
+    float id = 1.0f / det;
+    float i00 = a00 * id, i01 = a01 * id, i02 = a02 * id, i11 = a11 * id, i12 = a12 * id;
+    float i22 = (cxx * cyy - cxy * cxy) * id;
+    float wx = (i00 * v[0] + i01 * v[1]) + i02 * v[2];
+    float wy = (i01 * v[0] + i11 * v[1]) + i12 * v[2];
+    float wz = (i02 * v[0] + i12 * v[1]) + i22 * v[2];
+    float a = (v[0] * wx + v[1] * wy) + v[2] * wz;
+    float am = a - k2;
+    if (!(am > 0.01f * k2)) return 0;
+    float G00 = am * i00 - wx * wx;
+    float G01 = am * i01 - wx * wy;
+    float G11 = am * i11 - wy * wy;
+    float dG = G00 * G11 - G01 * G01;
+    float tG = G00 + G11;
+    if (!(G00 > 0.0f && dG > 1e-6f * (tG * tG))) return 0;
+    float ivz = 1.0f / v[2];
+    float hx = (k2 * wx) * ivz, hy = (k2 * wy) * ivz;
+    float k0 = (k2 * a) * (ivz * ivz);
+    float idG = 1.0f / dG;
+    float dcx = (G11 * hx - G01 * hy) * idG;
+    float dcy = (G00 * hy - G01 * hx) * idG;
+    float rhs = k0 + (hx * dcx + hy * dcy);
+    if (!(rhs > 0.0f && rhs < 1e30f)) return 0;
+    e[0] = c->fx * (v[0] * ivz + dcx) + c->cx;
+    e[1] = c->fy * (v[1] * ivz + dcy) + c->cy;
+    e[2] = G00 / (c->fx * c->fx);
+    e[3] = G01 / (c->fx * c->fy);
+    e[4] = G11 / (c->fy * c->fy);
+    q[0] = rhs * 1.01f;
+    q[1] = (-e[3]) / e[4];
+    q[2] = (-e[3]) / e[2];
+    return 1;
+}
+
+/* Tile (tx, ty) against the ellipse: the minimum over the tile's pixel-centre
+ * rectangle grown by `grow` pixels of (p - c)^T [[A,B],[B,C]] (p - c) is at most
+ * q[0] (edges that separate the centre from the rectangle, clamped stationary
+ * point along each). */
+static int fell_test(const fcam *c, const float *e, const float *q, int tx, int ty, float grow) {
+    float x0 = ((float)(TILE * tx) + 0.5f) - grow, y0 = ((float)(TILE * ty) + 0.5f) - grow;
+    float x1 = fminf(((float)(TILE * tx) + (float)TILE) - 0.5f, (float)c->W - 0.5f) + grow;
+    float y1 = fminf(((float)(TILE * ty) + (float)TILE) - 0.5f, (float)c->H - 0.5f) + grow;
+    float dx0 = x0 - e[0], dx1 = x1 - e[0], dy0 = y0 - e[1], dy1 = y1 - e[1];
+    int sx = dx0 > 0.0f || dx1 < 0.0f, sy = dy0 > 0.0f || dy1 < 0.0f;
+    if (!sx && !sy) return 1;
+    float best = 3.0e38f;
+    if (sx) {
+        float x = dx0 > 0.0f ? dx0 : dx1;
+        float y = fminf(fmaxf(q[1] * x, dy0), dy1);
+        best = x * (e[2] * x + 2.0f * (e[3] * y)) + e[4] * (y * y);
+    }
+    if (sy) {
+        float y = dy0 > 0.0f ? dy0 : dy1;
+        float x = fminf(fmaxf(q[2] * y, dx0), dx1);
+        float b2 = x * (e[2] * x + 2.0f * (e[3] * y)) + e[4] * (y * y);
+        best = fminf(best, b2);
+    }
+    return best <= q[0];
+}
+
+/* Per-Gaussian binning records [n*16] for one camera (FP32 inputs). */
+void or_bin_gauss(const double *campk, int n, const float *means, const float *log_scales, const float *quats,
+                  const float *logits, const float *rho2, float *recs) {
     fcam c;
     unpack_fcam(campk, &c);
 #pragma omp parallel for schedule(static)
     for (int i = 0; i < n; ++i)
-        fgauss(&c, means + 3 * (size_t)i, log_scales + 3 * (size_t)i, logits[i], rho2 ? rho2[i] : 0.0f,
-               recs + 10 * (size_t)i);
+        fgauss(&c, means + 3 * (size_t)i, log_scales + 3 * (size_t)i, quats + 4 * (size_t)i, logits[i],
+               rho2 ? rho2[i] : 0.0f, recs + 16 * (size_t)i);
 }
 
 /* Tile/Gaussian pair counts: per Gaussian (n) and per tile (ntiles); optional
- * dense pass matrix [n * ntiles] (bytes).  Returns the total pair count. */
-long or_bin_counts(const double *campk, const float *table, int n, const float *recs, int *per_gauss,
-                   int *per_tile, unsigned char *pass) {
+ * dense pass matrix [n * ntiles] (bytes).  Returns the total pair count.  A
+ * pair passes the cone test and, where it applies (pinhole cameras), the
+ * silhouette ellipse built with the largest tile footprint bound m. */
+long or_bin_counts(const double *campk, const float *table, int n, const float *recs, const float *means,
+                   int *per_gauss, int *per_tile, unsigned char *pass) {
     fcam c;
     unpack_fcam(campk, &c);
-    int nt = ((c.W + TILE - 1) / TILE) * ((c.H + TILE - 1) / TILE);
+    int ntx = (c.W + TILE - 1) / TILE;
+    int nt = ntx * ((c.H + TILE - 1) / TILE);
+    float mbar = 0.0f;
+    for (int t = 0; t < nt; ++t) mbar = fmaxf(mbar, table[6 * (size_t)t + 5]);
     long total = 0;
     for (int t = 0; t < nt; ++t) per_tile[t] = 0;
-#pragma omp parallel for schedule(dynamic, 64) reduction(+ : total)
-    for (int i = 0; i < n; ++i) {
-        int cnt = 0;
-        for (int t = 0; t < nt; ++t) {
-            int ok = ftest(recs + 10 * (size_t)i, table + 6 * (size_t)t);
-            if (pass) pass[(size_t)i * nt + t] = (unsigned char)ok;
-            cnt += ok;
-        }
-        per_gauss[i] = cnt;
-        total += cnt;
-    }
-    for (int i = 0; i < n; ++i)
-        for (int t = 0; t < nt; ++t)
-            if (pass ? pass[(size_t)i * nt + t] : 0) per_tile[t]++;
-    if (!pass) {
-        /* per-tile counts without the dense matrix */
-        for (int t = 0; t < nt; ++t) {
+    int *tcount = (int *)calloc((size_t)nt, sizeof(int));
+#pragma omp parallel
+    {
+        int *mine = (int *)calloc((size_t)nt, sizeof(int));
+#pragma omp for schedule(dynamic, 64) reduction(+ : total)
+        for (int i = 0; i < n; ++i) {
+            const float *g = recs + 16 * (size_t)i;
+            float e[5], q[3];
+            int ell = g[9] == 1.0f && fellipse(&c, g, means + 3 * (size_t)i, mbar, e, q);
             int cnt = 0;
-            for (int i = 0; i < n; ++i) cnt += ftest(recs + 10 * (size_t)i, table + 6 * (size_t)t);
-            per_tile[t] = cnt;
+            for (int t = 0; t < nt; ++t) {
+                int ok = ftest(g, table + 6 * (size_t)t);
+                if (ok && ell) ok = fell_test(&c, e, q, t % ntx, t / ntx, 0.05f);
+                if (pass) pass[(size_t)i * nt + t] = (unsigned char)ok;
+                mine[t] += ok;
+                cnt += ok;
+            }
+            per_gauss[i] = cnt;
+            total += cnt;
         }
+#pragma omp critical
+        for (int t = 0; t < nt; ++t) tcount[t] += mine[t];
+        free(mine);
     }
+    for (int t = 0; t < nt; ++t) per_tile[t] = tcount[t];
+    free(tcount);
     return total;
 }
 

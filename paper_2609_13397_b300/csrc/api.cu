@@ -26,16 +26,17 @@ cudaError_t launch_gauss_scene_rule(const SceneParams &sp, float *binrec, cudaSt
 cudaError_t launch_bin_count(const CamParams &c, const float *binrec, const float4 *gview, const float2 *gcone,
                              const uint8_t *gflag, const float *table, const float *super, const float *mcam,
                              float mzf, int64_t n, uint32_t *counts, uint4 *cache, uint32_t *blist,
-                             unsigned long long *bcursor, unsigned long long bcap, const float *ut_means,
-                             const float *ut_W, const float *ut_sig_eff, cudaStream_t s);
+                             unsigned long long *bcursor, unsigned long long bcap, const float4 *gell,
+                             const float *ut_means, const float *ut_W, const float *ut_sig_eff, cudaStream_t s);
 cudaError_t launch_bin_emit(const CamParams &c, const float *binrec, const float4 *gview, const float2 *gcone,
                             const uint8_t *gflag, const float *table, const float *super, const float *mcam,
                             float mzf, int64_t n_sorted, const uint32_t *order, const uint32_t *offsets,
                             const uint4 *cache, const uint32_t *blist, uint32_t *out_tile, uint32_t *out_gid,
-                            bool ut, cudaStream_t s);
+                            const float4 *gell, bool ut, cudaStream_t s);
 cudaError_t launch_scene_cache(const SceneParams &sp, float *W, float *sig_eff, cudaStream_t s);
 cudaError_t launch_view_records(const CamParams &c, const SceneParams &sp, const float *mcam, float mzf,
-                                float4 *rec, float4 *gview, float2 *gcone, uint8_t *gflag, cudaStream_t s);
+                                float4 *rec, float4 *gview, float2 *gcone, uint8_t *gflag, float4 *gell,
+                                cudaStream_t s);
 int64_t scan_scratch_words(int64_t n);
 cudaError_t exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *scratch, int pred,
                            cudaStream_t s);
@@ -145,7 +146,7 @@ struct conegs_view {
     uint64_t list_want = 0;   // tile ids the last count pass wanted to keep in binlist
     long long launches0 = 0;  // launch counter at the start of the current render
     // per-render scratch
-    DevBuf rec, gview, gcone, gflag, counts, vispos, scan_scr, dkeys, dvals, dkeys_alt, dvals_alt, sorted_counts, offsets;
+    DevBuf rec, gview, gcone, gflag, gell, counts, vispos, scan_scr, dkeys, dvals, dkeys_alt, dvals_alt, sorted_counts, offsets;
     DevBuf pair_tile, pair_gid, pair_tile_alt, pair_gid_alt, ranges, last, sums, rs_scr, tmp_rgb, tmp_T;
     DevBuf g_rec, keep_T, split;
     unsigned long long *h_sums = nullptr;   // pinned
@@ -320,7 +321,7 @@ conegs_status conegs_set_scene(conegs_ctx *ctx, int64_t n, const float *means, c
     std::lock_guard<std::mutex> lk(ctx->mu);
     TRY(ensure(ctx, ctx->W, sizeof(float) * 9 * (size_t)std::max<int64_t>(n, 1), s));
     TRY(ensure(ctx, ctx->sig_eff, sizeof(float) * (size_t)std::max<int64_t>(n, 1), s));
-    TRY(ensure(ctx, ctx->binrec, sizeof(float) * 6 * (size_t)std::max<int64_t>(n, 1), s));
+    TRY(ensure(ctx, ctx->binrec, sizeof(float) * BINREC * (size_t)std::max<int64_t>(n, 1), s));
     SceneParams sp{};
     sp.n = n;
     sp.sh_degree = sh_degree;
@@ -372,7 +373,7 @@ void conegs_view_destroy(conegs_view *v) {
         cudaEventSynchronize(v->done);
         cudaEventDestroy(v->done);
     }
-    DevBuf *bufs[] = {&v->d, &v->dx, &v->dy, &v->valid, &v->table, &v->super, &v->mcam, &v->rec, &v->gview, &v->gcone, &v->gflag, &v->bincache, &v->binlist,
+    DevBuf *bufs[] = {&v->d, &v->dx, &v->dy, &v->valid, &v->table, &v->super, &v->mcam, &v->rec, &v->gview, &v->gcone, &v->gflag, &v->gell, &v->bincache, &v->binlist,
                       &v->counts, &v->vispos, &v->scan_scr, &v->dkeys, &v->dvals, &v->dkeys_alt, &v->dvals_alt,
                       &v->sorted_counts, &v->offsets, &v->pair_tile, &v->pair_gid, &v->pair_tile_alt,
                       &v->pair_gid_alt, &v->ranges, &v->last, &v->sums, &v->rs_scr, &v->tmp_rgb, &v->tmp_T,
@@ -502,6 +503,7 @@ static conegs_status render_front(conegs_view *v, unsigned flags, cudaStream_t s
     TRY(ensure(ctx, v->rec, sizeof(float4) * REC_F4 * nn, s));
     TRY(ensure(ctx, v->gview, sizeof(float4) * nn, s));
     TRY(ensure(ctx, v->gcone, sizeof(float2) * nn, s));
+    TRY(ensure(ctx, v->gell, 2 * sizeof(float4) * nn, s));
     TRY(ensure(ctx, v->gflag, nn, s));
     TRY(ensure(ctx, v->bincache, 3 * sizeof(uint4) * nn, s));
     TRY(ensure(ctx, v->counts, sizeof(uint32_t) * nn, s));
@@ -519,7 +521,7 @@ static conegs_status render_front(conegs_view *v, unsigned flags, cudaStream_t s
         CUDA_TRY(cudaEventRecord(v->prof[0], s));
     }
     CUDA_TRY(launch_view_records(c, sp, v->mcam.as<float>(), zf_bound(c, flags), v->rec.as<float4>(), v->gview.as<float4>(),
-                                 v->gcone.as<float2>(), v->gflag.as<uint8_t>(), s));
+                                 v->gcone.as<float2>(), v->gflag.as<uint8_t>(), v->gell.as<float4>(), s));
     CUDA_TRY(cudaMemsetAsync(v->sums.as<unsigned long long>() + 2, 0, sizeof(unsigned long long), s));
     {
         const bool ut = (flags & CONEGS_BIN_UT) != 0;
@@ -528,7 +530,8 @@ static conegs_status render_front(conegs_view *v, unsigned flags, cudaStream_t s
                                   v->table.as<float>(), v->super.as<float>(), v->mcam.as<float>(),
                                   zf_bound(c, flags), n, v->counts.as<uint32_t>(), v->bincache.as<uint4>(),
                                   v->binlist.as<uint32_t>(), v->sums.as<unsigned long long>() + 2, cap,
-                                  ut ? sp.means : nullptr, ut ? sp.W : nullptr, ut ? sp.sig_eff : nullptr, s));
+                                  v->gell.as<float4>(), ut ? sp.means : nullptr, ut ? sp.W : nullptr,
+                                  ut ? sp.sig_eff : nullptr, s));
     }
     CUDA_TRY(sum_counts(v->counts.as<uint32_t>(), n, v->sums.as<unsigned long long>(), s));
     CUDA_TRY(exclusive_scan(v->counts.as<uint32_t>(), v->vispos.as<uint32_t>(), n, v->scan_scr.as<uint32_t>(), 1, s));
@@ -578,7 +581,7 @@ static conegs_status render_back(conegs_view *v, float *out_rgb, float *out_T, u
                              v->table.as<float>(), v->super.as<float>(), v->mcam.as<float>(), zf_bound(c, flags), M,
                              v->dvals.as<uint32_t>(), v->offsets.as<uint32_t>(), v->bincache.as<uint4>(),
                              v->binlist.as<uint32_t>(), v->pair_tile.as<uint32_t>(), v->pair_gid.as<uint32_t>(),
-                             (flags & CONEGS_BIN_UT) != 0, s));
+                             v->gell.as<float4>(), (flags & CONEGS_BIN_UT) != 0, s));
     CUDA_TRY(radix_sort_pairs(v->pair_tile.as<uint32_t>(), v->pair_gid.as<uint32_t>(), v->pair_tile_alt.as<uint32_t>(),
                               v->pair_gid_alt.as<uint32_t>(), Pn, 0, bits_for(nt), v->rs_scr.as<uint32_t>(), s));
     CUDA_TRY(launch_ranges(v->pair_tile.as<uint32_t>(), Pn, v->ranges.as<uint2>(), nt, s));
@@ -796,7 +799,7 @@ conegs_status conegs_get_stats(const conegs_view *v, conegs_stats *out) {
     out->tiles_y = v->cam.tiles_y;
     out->n_valid_pixels = v->n_valid;
     out->n_launches = v->n_launches;
-    const DevBuf *bufs[] = {&v->d, &v->dx, &v->dy, &v->valid, &v->table, &v->super, &v->mcam, &v->rec, &v->gview, &v->gcone, &v->gflag, &v->bincache, &v->binlist,
+    const DevBuf *bufs[] = {&v->d, &v->dx, &v->dy, &v->valid, &v->table, &v->super, &v->mcam, &v->rec, &v->gview, &v->gcone, &v->gflag, &v->gell, &v->bincache, &v->binlist,
                             &v->counts, &v->vispos, &v->scan_scr, &v->dkeys, &v->dvals, &v->dkeys_alt, &v->dvals_alt,
                             &v->sorted_counts, &v->offsets, &v->pair_tile, &v->pair_gid, &v->pair_tile_alt,
                             &v->pair_gid_alt, &v->ranges, &v->last, &v->sums, &v->rs_scr, &v->tmp_rgb, &v->tmp_T,

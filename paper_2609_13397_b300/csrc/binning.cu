@@ -161,7 +161,12 @@ __global__ void gauss_scene_rule_kernel(SceneParams sp, float *__restrict__ binr
     float rec[6];
     rule_gauss_scene(ls, logit, rho2, rec);
 #pragma unroll
-    for (int k = 0; k < 6; ++k) binrec[6 * i + k] = rec[k];
+    for (int k = 0; k < 6; ++k) binrec[BINREC * i + k] = rec[k];
+    const float q[4] = {sp.quats[4 * i], sp.quats[4 * i + 1], sp.quats[4 * i + 2], sp.quats[4 * i + 3]};
+    float S[6];
+    rule_gauss_sigma(q, ls, rho2, S);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) binrec[BINREC * i + 6 + k] = S[k];
 }
 
 // Per view: u, L (float4) and the view flag (0 culled, 1 normal, 2 pass-all).
@@ -170,7 +175,7 @@ __global__ void gauss_view_rule_kernel(CamParams c, SceneParams sp, float4 *__re
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= sp.n) return;
     float mu[3] = {sp.means[3 * i], sp.means[3 * i + 1], sp.means[3 * i + 2]};
-    float flag = sp.binrec[6 * i + 5], u[3], L;
+    float flag = sp.binrec[BINREC * i + 5], u[3], L;
     rule_gauss_view(c, mu, flag, u, L);
     gview[i] = make_float4(u[0], u[1], u[2], L);
     gflag[i] = (uint8_t)flag;
@@ -298,10 +303,11 @@ __device__ __forceinline__ bool kb_tile_box(const CamParams &c, const float4 gv,
 // the emit pass has to test tiles again, so both passes take every decision
 // from the same floats; the tile test is a fixed sequence of correctly rounded
 // operations, identical in both passes.
-struct UtArgs {
-    const float *means;     // [n][3]
-    const float *W;         // [n][9] W_eff = S_eff^-1 R^T
-    const float *sig_eff;   // [n]
+struct GaussArgs {
+    const float4 *ell;      // [n][2] the angular-tile rule's silhouette ellipse (view records)
+    const float *means;     // [n][3] (UT only)
+    const float *W;         // [n][9] W_eff = S_eff^-1 R^T (UT only)
+    const float *sig_eff;   // [n] (UT only)
 };
 
 constexpr float UT_COSMIN = 0.1f;
@@ -320,7 +326,7 @@ __device__ __forceinline__ float2 ut_kb_image(const CamParams &c, float px, floa
 // The UT image ellipse of Gaussian gid: e = (ybar_x, ybar_y, A, B, C) with
 // [[A,B],[B,C]] = Sigma_2^-1, q = (k^2, -B/C, -B/A), and the candidate tile box.
 // Returns false when a sigma point leaves the camera's domain.
-__device__ bool ut_ellipse(const CamParams &c, const UtArgs &ua, uint32_t gid, float e[5], float4 &q, int &tx0,
+__device__ bool ut_ellipse(const CamParams &c, const GaussArgs &ua, uint32_t gid, float e[5], float4 &q, int &tx0,
                            int &tx1, int &ty0, int &ty1) {
     const float m0 = ua.means[3 * (size_t)gid] - c.o[0], m1 = ua.means[3 * (size_t)gid + 1] - c.o[1],
                 m2 = ua.means[3 * (size_t)gid + 2] - c.o[2];
@@ -429,33 +435,6 @@ __device__ bool ut_ellipse(const CamParams &c, const UtArgs &ua, uint32_t gid, f
     return true;
 }
 
-// Tile (tx, ty) against a UT ellipse: min over the tile's pixel-centre rectangle
-// of Q(y) = (y - ybar)^T [[A,B],[B,C]] (y - ybar) <= k^2.  With ybar outside the
-// rectangle the minimum lies on an edge whose line separates ybar from it, at
-// the clamped stationary point of Q along that edge.
-__device__ __forceinline__ bool ut_tile_test(const CamParams &c, const float e[5], const float4 q, int tx,
-                                             int ty) {
-    const float x0 = (float)(TILE * tx) + 0.5f, y0 = (float)(TILE * ty) + 0.5f;
-    const float x1 = fminf(x0 + (float)(TILE - 1), (float)c.W - 0.5f);
-    const float y1 = fminf(y0 + (float)(TILE - 1), (float)c.H - 0.5f);
-    const float dx0 = r_sub(x0, e[0]), dx1 = r_sub(x1, e[0]), dy0 = r_sub(y0, e[1]), dy1 = r_sub(y1, e[1]);
-    const bool sx = dx0 > 0.0f || dx1 < 0.0f, sy = dy0 > 0.0f || dy1 < 0.0f;
-    if (!sx && !sy) return true;
-    float best = 3.0e38f;
-    if (sx) {
-        const float x = dx0 > 0.0f ? dx0 : dx1;
-        const float y = fminf(fmaxf(r_mul(q.y, x), dy0), dy1);
-        best = r_add(r_mul(x, r_add(r_mul(e[2], x), r_mul(2.0f, r_mul(e[3], y)))), r_mul(e[4], r_mul(y, y)));
-    }
-    if (sy) {
-        const float y = dy0 > 0.0f ? dy0 : dy1;
-        const float x = fminf(fmaxf(r_mul(q.z, y), dx0), dx1);
-        best = fminf(best, r_add(r_mul(x, r_add(r_mul(e[2], x), r_mul(2.0f, r_mul(e[3], y)))),
-                                 r_mul(e[4], r_mul(y, y))));
-    }
-    return best <= q.x;
-}
-
 // Count (MODE 0) and emit (MODE 1) of the (tile, Gaussian) pairs.
 //
 // Each lane prepares one Gaussian (slot): flag, rule record, direction, cone,
@@ -490,12 +469,13 @@ __device__ __forceinline__ void mask_or(uint32_t m[8], uint32_t bits, uint32_t a
 }
 
 // Super-tile walk for one Gaussian by the whole warp; returns its pair count.
+// ell: the slot's silhouette ellipse (e[5], threshold, -B/C, -B/A), or nullptr.
 template <int MODE>
 __device__ __forceinline__ uint32_t bin_walk_supers(const CamParams &c, const float *g, const float4 gv,
                                                     const float2 half, const float *__restrict__ table,
                                                     const float *__restrict__ super, float mzf, uint32_t gid,
                                                     uint32_t base, uint32_t *__restrict__ out_tile,
-                                                    uint32_t *__restrict__ out_gid) {
+                                                    uint32_t *__restrict__ out_gid, const float *ell) {
     const int lane = threadIdx.x & 31;
     const int nsup = c.supers_x * c.supers_y;
     uint32_t cnt = 0;
@@ -523,6 +503,8 @@ __device__ __forceinline__ uint32_t bin_walk_supers(const CamParams &c, const fl
                         const int f = rule_test_fast(g, gv, tt);
                         tp = f == 2 ? rule_test(g, gv, tt) : f == 1;
                     }
+                    if (tp && ell) tp = ellipse_rect_test(c, ell, make_float4(ell[5], ell[6], ell[7], 0.0f), tx, ty,
+                                                          ELL_GROW);
                 }
                 const uint32_t tb = __ballot_sync(0xffffffffu, tp);
                 if (MODE == 1 && tp) {
@@ -546,7 +528,7 @@ __device__ __forceinline__ uint32_t bin_walk_box(const CamParams &c, const float
                                                  int tx0, int ty0, int bw, uint32_t nb, uint32_t gid, uint32_t base,
                                                  uint32_t m[8], uint32_t *__restrict__ list,
                                                  uint32_t *__restrict__ out_tile, uint32_t *__restrict__ out_gid,
-                                                 bool ut) {
+                                                 bool ut, const float *ell) {
     const int lane = threadIdx.x & 31;
     uint32_t cnt = 0;
     int qy = 0, qx = lane;                     // candidate k0 + lane = qy * bw + qx
@@ -561,7 +543,7 @@ __device__ __forceinline__ uint32_t bin_walk_box(const CamParams &c, const float
         if (k0 + (uint32_t)lane < nb) {
             tile = (uint32_t)((ty0 + qy) * c.tiles_x + tx0 + qx);
             if (UT && ut) {
-                tp = ut_tile_test(c, g, gv, tx0 + qx, ty0 + qy);
+                tp = ellipse_rect_test(c, g, gv, tx0 + qx, ty0 + qy, 0.0f);
             } else {
                 float tt[6];
                 tile_record(table, tile, mzf, tt);
@@ -569,6 +551,9 @@ __device__ __forceinline__ uint32_t bin_walk_box(const CamParams &c, const float
                     const int f = rule_test_fast(g, gv, tt);
                     tp = f == 2 ? rule_test(g, gv, tt) : f == 1;
                 }
+                if (tp && ell)
+                    tp = ellipse_rect_test(c, ell, make_float4(ell[5], ell[6], ell[7], 0.0f), tx0 + qx, ty0 + qy,
+                                           ELL_GROW);
             }
         }
         const uint32_t tb = __ballot_sync(0xffffffffu, tp);
@@ -595,7 +580,7 @@ __device__ __forceinline__ uint32_t bin_walk_box(const CamParams &c, const float
 }
 
 template <int MODE, bool UT>
-__global__ void __launch_bounds__(32 * BIN_WARPS, 3) bin_kernel(CamParams c, UtArgs ua,
+__global__ void __launch_bounds__(32 * BIN_WARPS, 3) bin_kernel(CamParams c, GaussArgs ua,
                                                                 const float *__restrict__ binrec,
                                                                 const float4 *__restrict__ gview,
                                                                 const float2 *__restrict__ gcone,
@@ -616,9 +601,10 @@ __global__ void __launch_bounds__(32 * BIN_WARPS, 3) bin_kernel(CamParams c, UtA
     __shared__ float s_g[BIN_WARPS][5][32];        // kap, ks, kr, r1sq, s2 (flag is 1 for boxed slots)
     __shared__ float4 s_gv[BIN_WARPS][32];
     __shared__ float2 s_half[BIN_WARPS][32];
-    __shared__ int4 s_box[BIN_WARPS][32];          // tx0, ty0, box width, bits: cached (1), UT ellipse (2)
+    __shared__ int4 s_box[BIN_WARPS][32];          // tx0, ty0, box width, bits: cached (1), UT (2), silhouette (4)
     __shared__ float s_inv[BIN_WARPS][32];         // 1 / box width
     __shared__ uint4 s_mask[BIN_WARPS][2][32];     // MODE 1: cached pass mask (8 words)
+    __shared__ float s_ell[BIN_WARPS][8][32];      // silhouette ellipse (valid: s_box .w bit 4)
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t pos = ((int64_t)blockIdx.x * BIN_WARPS + wid) * 32 + lane;
     const bool have = pos < n;
@@ -626,7 +612,8 @@ __global__ void __launch_bounds__(32 * BIN_WARPS, 3) bin_kernel(CamParams c, UtA
     const uint32_t base = (MODE == 1 && have) ? offsets[pos] : 0u;
     // ---- slot set-up
     uint32_t nb = 0, fl = 0, npk = 0, lofs = 0, lcnt = 0;
-    bool walk = false, cached = false, big = false, listed = false, utslot = false;
+    bool walk = false, cached = false, big = false, listed = false, utslot = false, ellv = false;
+    float el[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float g[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float4 gv = make_float4(0.f, 0.f, 0.f, 0.f);
     float2 half = make_float2(0.f, 1.f);
@@ -681,10 +668,17 @@ __global__ void __launch_bounds__(32 * BIN_WARPS, 3) bin_kernel(CamParams c, UtA
         }
         if (fl != 0 && !cached && !listed && !utslot) {
 #pragma unroll
-            for (int k = 0; k < 5; ++k) g[k] = binrec[6 * (size_t)gid + k];
+            for (int k = 0; k < 5; ++k) g[k] = binrec[BINREC * (size_t)gid + k];
             g[5] = (float)fl;
             gv = gview[gid];
             half = gcone[gid];
+            if (fl == 1) {
+                // silhouette ellipse of the rule's bounding ellipsoid (view records; pinhole cameras)
+                const float4 e0 = ua.ell[2 * (size_t)gid], e1 = ua.ell[2 * (size_t)gid + 1];
+                el[0] = e0.x; el[1] = e0.y; el[2] = e0.z; el[3] = e0.w;
+                el[4] = e1.x; el[5] = e1.y; el[6] = e1.z; el[7] = e1.w;
+                ellv = el[5] > 0.0f;
+            }
             const bool boxed =
                 fl == 1 && half.y >= 1e-3f &&
                 (c.model == 0 ? pinhole_tile_box(c, gv, half, mcam[1], tx0, tx1, ty0, ty1)
@@ -703,7 +697,9 @@ __global__ void __launch_bounds__(32 * BIN_WARPS, 3) bin_kernel(CamParams c, UtA
     s_g[wid][3][lane] = g[3]; s_g[wid][4][lane] = g[4];
     s_gv[wid][lane] = gv;
     s_half[wid][lane] = half;
-    s_box[wid][lane] = make_int4(tx0, ty0, tx1 - tx0 + 1, (cached ? 1 : 0) | (utslot ? 2 : 0));
+    s_box[wid][lane] = make_int4(tx0, ty0, tx1 - tx0 + 1, (cached ? 1 : 0) | (utslot ? 2 : 0) | (ellv ? 4 : 0));
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s_ell[wid][k][lane] = el[k];
     s_inv[wid][lane] = tx1 >= tx0 ? 1.0f / (float)(tx1 - tx0 + 1) : 0.0f;
     // exclusive prefix of the packed slots' candidate counts (a cached slot of the emit
     // pass contributes its passing candidates only; big boxes are walked below)
@@ -769,13 +765,20 @@ __global__ void __launch_bounds__(32 * BIN_WARPS, 3) bin_kernel(CamParams c, UtA
                                      s_g[wid][4][sl], 1.0f};
                 const float4 sgv = s_gv[wid][sl];
                 if (UT && (bx.w & 2)) {
-                    tp = ut_tile_test(c, gg, sgv, bx.x + kx, bx.y + ky);
+                    tp = ellipse_rect_test(c, gg, sgv, bx.x + kx, bx.y + ky, 0.0f);
                 } else {
                     float tt[6];
                     tile_record(table, tile, mzf, tt);
                     if (cone_prefilter(sgv, s_half[wid][sl], tt)) {
                         const int f = rule_test_fast(gg, sgv, tt);
                         tp = f == 2 ? rule_test(gg, sgv, tt) : f == 1;
+                    }
+                    if (tp && (bx.w & 4)) {
+                        const float ee[5] = {s_ell[wid][0][sl], s_ell[wid][1][sl], s_ell[wid][2][sl],
+                                             s_ell[wid][3][sl], s_ell[wid][4][sl]};
+                        tp = ellipse_rect_test(c, ee,
+                                               make_float4(s_ell[wid][5][sl], s_ell[wid][6][sl], s_ell[wid][7][sl], 0.f),
+                                               bx.x + kx, bx.y + ky, ELL_GROW);
                     }
                 }
             }
@@ -832,8 +835,12 @@ __global__ void __launch_bounds__(32 * BIN_WARPS, 3) bin_kernel(CamParams c, UtA
             lo = __shfl_sync(0xffffffffu, lo, 0);
             if (lo + bnb <= bcap) lst = blist + lo;
         }
+        float sel[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) sel[k] = s_ell[wid][k][sl];
+        const bool sev = (s_box[wid][sl].w & 4) != 0;
         const uint32_t wc = bin_walk_box<MODE, UT>(c, gg, sgv, sh, table, mzf, btx0, bty0, bw, bnb, sgid, sbase,
-                                                   wm, lst, out_tile, out_gid, gg[5] == 3.0f);
+                                                   wm, lst, out_tile, out_gid, gg[5] == 3.0f, sev ? sel : nullptr);
         if (lane == sl) {
             cnt = wc;
 #pragma unroll
@@ -871,8 +878,12 @@ __global__ void __launch_bounds__(32 * BIN_WARPS, 3) bin_kernel(CamParams c, UtA
         sh.x = __shfl_sync(0xffffffffu, half.x, sl); sh.y = __shfl_sync(0xffffffffu, half.y, sl);
         const uint32_t sgid = __shfl_sync(0xffffffffu, gid, sl);
         const uint32_t sbase = __shfl_sync(0xffffffffu, base, sl);
-        const uint32_t wc =
-            bin_walk_supers<MODE>(c, gg, sgv, sh, table, super, mzf, sgid, sbase, out_tile, out_gid);
+        float sel[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) sel[k] = s_ell[wid][k][sl];
+        const bool sev = (s_box[wid][sl].w & 4) != 0;
+        const uint32_t wc = bin_walk_supers<MODE>(c, gg, sgv, sh, table, super, mzf, sgid, sbase, out_tile, out_gid,
+                                                  sev ? sel : nullptr);
         if (lane == sl) cnt = wc;
     }
     if (MODE == 0 && have) {
@@ -926,16 +937,16 @@ cudaError_t launch_gauss_view_rule(const CamParams &c, const SceneParams &sp, fl
     return cudaGetLastError();
 }
 
-// ut_means/ut_W/ut_sig_eff non-null: UT binning (the scene's means, W_eff and sigma_eff).
+// gell: silhouette ellipses from the view records; ut_means/ut_W/ut_sig_eff non-null: UT binning.
 cudaError_t launch_bin_count(const CamParams &c, const float *binrec, const float4 *gview, const float2 *gcone,
                              const uint8_t *gflag, const float *table, const float *super, const float *mcam,
                              float mzf, int64_t n, uint32_t *counts, uint4 *cache, uint32_t *blist,
-                             unsigned long long *bcursor, unsigned long long bcap, const float *ut_means,
-                             const float *ut_W, const float *ut_sig_eff, cudaStream_t s) {
+                             unsigned long long *bcursor, unsigned long long bcap, const float4 *gell,
+                             const float *ut_means, const float *ut_W, const float *ut_sig_eff, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    const UtArgs ua{ut_means, ut_W, ut_sig_eff};
+    const GaussArgs ua{gell, ut_means, ut_W, ut_sig_eff};
     const unsigned grid = (unsigned)div_up(n, 32 * BIN_WARPS);
-    if (ut_means)
+    if (ut_W)
         bin_kernel<0, true><<<grid, 32 * BIN_WARPS, 0, s>>>(c, ua, binrec, gview, gcone, gflag, table, super, mcam,
                                                            mzf, n, nullptr, nullptr, counts, cache, blist, bcursor,
                                                            bcap, nullptr, nullptr);
@@ -951,9 +962,9 @@ cudaError_t launch_bin_emit(const CamParams &c, const float *binrec, const float
                             const uint8_t *gflag, const float *table, const float *super, const float *mcam,
                             float mzf, int64_t n_sorted, const uint32_t *order, const uint32_t *offsets,
                             const uint4 *cache, const uint32_t *blist, uint32_t *out_tile, uint32_t *out_gid,
-                            bool ut, cudaStream_t s) {
+                            const float4 *gell, bool ut, cudaStream_t s) {
     if (n_sorted == 0) return cudaSuccess;
-    const UtArgs ua{nullptr, nullptr, nullptr};
+    const GaussArgs ua{gell, nullptr, nullptr, nullptr};
     const unsigned grid = (unsigned)div_up(n_sorted, 32 * BIN_WARPS);
     if (ut)
         bin_kernel<1, true><<<grid, 32 * BIN_WARPS, 0, s>>>(c, ua, binrec, gview, gcone, gflag, table, super, mcam,

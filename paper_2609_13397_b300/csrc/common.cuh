@@ -16,6 +16,7 @@ constexpr float ALPHA_MAX = 0.99f;
 constexpr float T_STOP = 1e-4f;
 constexpr float T_NEAR = 0.01f;
 constexpr int REC_F4 = 8;         // float4 words per per-view raster record
+constexpr int BINREC = 12;        // floats per Gaussian of the binning rule's scene record
 
 // Camera passed by value to kernels.
 struct CamParams {
@@ -40,7 +41,7 @@ struct SceneParams {
     // camera-independent cache
     const float *W;               // [n][9] W_eff = S_eff^-1 R^T
     const float *sig_eff;         // [n]
-    const float *binrec;          // [n][6] kap, ks, kr, r1sq, s2, flag
+    const float *binrec;          // [n][BINREC] kap, ks, kr, r1sq, s2, flag, Sigma_eff (xx xy xz yy yz zz)
 };
 
 __device__ __forceinline__ float load_scalar(const void *p, int64_t i, int storage) {

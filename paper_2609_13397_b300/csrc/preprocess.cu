@@ -149,11 +149,12 @@ __global__ void __launch_bounds__(256) view_records_kernel(CamParams c, ScenePar
                                                            float mzf,
                                                            float4 *__restrict__ rec, float4 *__restrict__ gview,
                                                            float2 *__restrict__ gcone,
-                                                           uint8_t *__restrict__ gflag) {
+                                                           uint8_t *__restrict__ gflag,
+                                                           float4 *__restrict__ gell) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= sp.n) return;
     const float mu[3] = {sp.means[3 * i], sp.means[3 * i + 1], sp.means[3 * i + 2]};
-    float flag = sp.binrec[6 * i + 5], u[3], L;
+    float flag = sp.binrec[BINREC * i + 5], u[3], L;
     rule_gauss_view(c, mu, flag, u, L);
     gview[i] = make_float4(u[0], u[1], u[2], L);
     gflag[i] = (uint8_t)flag;
@@ -176,8 +177,20 @@ __global__ void __launch_bounds__(256) view_records_kernel(CamParams c, ScenePar
     const float m = fmaxf(*mcam, mzf);   // footprint bound (raised for the z/f variant)
     // binning prefilter: the cone of the binning rule's own bound (its kappa and
     // scale bounds), camera-wide footprint, wide margin
-    const float *br = sp.binrec + 6 * i;
+    const float *br = sp.binrec + BINREC * i;
     gcone[i] = L > 0.0f ? cone_half_angle(br[0], br[4], sqrtf(br[3]), L, m, 1e-3f) : make_float2(1.0f, 0.0f);
+    // the binning rule's silhouette ellipse (pinhole; threshold -1 when it does not apply)
+    {
+        float4 e0 = make_float4(0.f, 0.f, 0.f, 0.f), e1 = make_float4(0.f, -1.f, 0.f, 0.f);
+        float e[5];
+        float4 q;
+        if (flag == 1.0f && rule_ellipse(c, br, L, mu, br + 6, m, e, q)) {
+            e0 = make_float4(e[0], e[1], e[2], e[3]);
+            e1 = make_float4(e[4], q.x, q.y, q.z);
+        }
+        gell[2 * i] = e0;
+        gell[2 * i + 1] = e1;
+    }
     // rasteriser pre-test, with the exact kappa^2 = 2 ln(255 sigma)
     float g[3] = {0.f, 0.f, 0.f}, C[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float pu[3] = {dx, dy, dz};
@@ -216,9 +229,11 @@ cudaError_t launch_scene_cache(const SceneParams &sp, float *W, float *sig_eff, 
 }
 
 cudaError_t launch_view_records(const CamParams &c, const SceneParams &sp, const float *mcam, float mzf,
-                                float4 *rec, float4 *gview, float2 *gcone, uint8_t *gflag, cudaStream_t s) {
+                                float4 *rec, float4 *gview, float2 *gcone, uint8_t *gflag, float4 *gell,
+                                cudaStream_t s) {
     if (sp.n == 0) return cudaSuccess;
-    view_records_kernel<<<(unsigned)div_up(sp.n, 256), 256, 0, s>>>(c, sp, mcam, mzf, rec, gview, gcone, gflag);
+    view_records_kernel<<<(unsigned)div_up(sp.n, 256), 256, 0, s>>>(c, sp, mcam, mzf, rec, gview, gcone, gflag,
+                                                                    gell);
     note_launches(1);
     return cudaGetLastError();
 }

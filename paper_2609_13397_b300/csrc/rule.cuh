@@ -241,4 +241,176 @@ __device__ __forceinline__ int rule_test_fast(const float *g, const float4 gv, c
     return 2;
 }
 
+// ---------------------------------------------------------------- silhouette ellipse (pinhole cameras)
+//
+// A contributing pair's ray passes through the ellipsoid
+//   E = {x : (x - mu)^T C^-1 (x - mu) <= kap^2},  C = Sigma_eff + t_b^2 m I
+// (Eq. 9 and 12: A >= I, the rendered footprint is at most t*^2 m I, t* <= t_b),
+// and the lines through the camera centre that meet E form an elliptic cone
+// whose trace on a pinhole's image plane is an ellipse.  With the scene
+// scaled by 1/L about the camera centre (v = (mu - o)/L, L = |mu - o|) and C
+// normalised by its mean eigenvalue tau, a line of direction d = (x, y, 1)
+// meets E iff, for delta = d - v/v_z,
+//   delta^T G delta - 2 h^T delta <= k0,  G = (a - k^2) Ci_xy - w_xy w_xy^T,
+//   h = k^2 w_xy / v_z,  k0 = k^2 a / v_z^2,  w = Ci v,  a = v^T w,  k^2 = kap^2 tau / L^2.
+// The rule keeps a tile only when this ellipse (rhs widened by 1%, the tile's
+// pixel-centre rectangle by 0.05 px, C by 1e-4 tau I) meets the rectangle.  It
+// applies when the camera lies outside E with margin, E is seen within ~77
+// degrees of the axis and the ellipse's aspect is below 1000; otherwise the
+// cone test alone decides.
+
+// Scene part: Sigma_eff = R diag(s_eff^2) R^T (xx xy xz yy yz zz),
+// s_eff^2 = exp(2 log s) * 1.0001 + rho^2.
+static __device__ void rule_gauss_sigma(const float q[4], const float ls[3], float rho2, float S[6]) {
+    const float n2 = r_add(r_add(r_add(r_mul(q[0], q[0]), r_mul(q[1], q[1])), r_mul(q[2], q[2])), r_mul(q[3], q[3]));
+    const float inv = r_div(1.0f, r_sqrt(n2));
+    const float w = r_mul(q[0], inv), x = r_mul(q[1], inv), y = r_mul(q[2], inv), z = r_mul(q[3], inv);
+    float R[9];
+    R[0] = r_sub(1.0f, r_mul(2.0f, r_add(r_mul(y, y), r_mul(z, z))));
+    R[1] = r_mul(2.0f, r_sub(r_mul(x, y), r_mul(w, z)));
+    R[2] = r_mul(2.0f, r_add(r_mul(x, z), r_mul(w, y)));
+    R[3] = r_mul(2.0f, r_add(r_mul(x, y), r_mul(w, z)));
+    R[4] = r_sub(1.0f, r_mul(2.0f, r_add(r_mul(x, x), r_mul(z, z))));
+    R[5] = r_mul(2.0f, r_sub(r_mul(y, z), r_mul(w, x)));
+    R[6] = r_mul(2.0f, r_sub(r_mul(x, z), r_mul(w, y)));
+    R[7] = r_mul(2.0f, r_add(r_mul(y, z), r_mul(w, x)));
+    R[8] = r_sub(1.0f, r_mul(2.0f, r_add(r_mul(x, x), r_mul(y, y))));
+    float s2[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) s2[a] = r_add(r_mul(rule_exp(r_mul(2.0f, ls[a])), 1.0001f), rho2);
+    const int I[6] = {0, 0, 0, 1, 1, 2}, J[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const int i = I[k], j = J[k];
+        S[k] = r_add(r_add(r_mul(r_mul(R[3 * i], R[3 * j]), s2[0]), r_mul(r_mul(R[3 * i + 1], R[3 * j + 1]), s2[1])),
+                     r_mul(r_mul(R[3 * i + 2], R[3 * j + 2]), s2[2]));
+    }
+}
+
+// View part: the silhouette ellipse in pixels, e = (centre x, centre y, A, B, C)
+// with Q(p) = (p - c)^T [[A,B],[B,C]] (p - c), q = (threshold, -B/C, -B/A).
+// g: scene record (kap ks kr r1sq s2); L: |mu - o|; m: the largest tile footprint bound.
+static __device__ bool rule_ellipse(const CamParams &c, const float *g, float L, const float mu[3], const float S[6],
+                                    float m, float e[5], float4 &q) {
+    if (c.model != 0) return false;
+    const float kap = g[0], ks = g[1], kr = g[2], r1sq = g[3], s2 = g[4];
+    const float sm = r_sqrt(m);
+    const float cc = r_mul(kr, sm);
+    const float rfc = r_mul(255.0f, ks);
+    float tb, rf;
+    if (cc < 1.0f) {
+        const float tbf = r_div(r_add(L, ks), r_sub(1.0f, cc));
+        const float rff = r_mul(kap, r_sqrt(r_add(s2, r_mul(r_mul(r_mul(tbf, tbf), r1sq), m))));
+        rf = fminf(rff, rfc);
+        tb = fminf(tbf, r_add(L, rf));
+    } else {
+        rf = rfc;
+        tb = r_add(L, rf);
+    }
+    if (!(L > rf)) return false;
+    const float w0 = r_sub(mu[0], c.o[0]), w1 = r_sub(mu[1], c.o[1]), w2 = r_sub(mu[2], c.o[2]);
+    const float iL = r_div(1.0f, L);
+    float v[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+        v[j] = r_mul(r_add(r_add(r_mul(c.R[j], w0), r_mul(c.R[3 + j], w1)), r_mul(c.R[6 + j], w2)), iL);
+    if (!(v[2] > 0.0f && r_mul(v[2], v[2]) >= 0.05f)) return false;
+    // covariance in the camera frame: Rc^T Sigma Rc
+    const float Sf[9] = {S[0], S[1], S[2], S[1], S[3], S[4], S[2], S[4], S[5]};
+    float T[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            T[3 * i + k] = r_add(r_add(r_mul(Sf[3 * i], c.R[k]), r_mul(Sf[3 * i + 1], c.R[3 + k])),
+                                 r_mul(Sf[3 * i + 2], c.R[6 + k]));
+    float Cc[6];
+    {
+        const int I[6] = {0, 0, 0, 1, 1, 2}, J[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const int j = I[k], l = J[k];
+            Cc[k] = r_add(r_add(r_mul(c.R[j], T[l]), r_mul(c.R[3 + j], T[3 + l])), r_mul(c.R[6 + j], T[6 + l]));
+        }
+    }
+    const float iso = r_add(r_mul(r_mul(tb, tb), m), r_mul(1e-5f, s2));
+    Cc[0] = r_add(Cc[0], iso);
+    Cc[3] = r_add(Cc[3], iso);
+    Cc[5] = r_add(Cc[5], iso);
+    const float tau = r_div(r_add(r_add(Cc[0], Cc[3]), Cc[5]), 3.0f);
+    const float it = r_div(1.0f, tau);
+    const float cxx = r_add(r_mul(Cc[0], it), 1e-4f), cxy = r_mul(Cc[1], it), cxz = r_mul(Cc[2], it);
+    const float cyy = r_add(r_mul(Cc[3], it), 1e-4f), cyz = r_mul(Cc[4], it), czz = r_add(r_mul(Cc[5], it), 1e-4f);
+    const float k2 = r_div(r_mul(r_mul(kap, kap), tau), r_mul(L, L));
+    // inverse by the adjugate
+    const float a00 = r_sub(r_mul(cyy, czz), r_mul(cyz, cyz));
+    const float a01 = r_sub(r_mul(cxz, cyz), r_mul(cxy, czz));
+    const float a02 = r_sub(r_mul(cxy, cyz), r_mul(cxz, cyy));
+    const float a11 = r_sub(r_mul(cxx, czz), r_mul(cxz, cxz));
+    const float a12 = r_sub(r_mul(cxy, cxz), r_mul(cxx, cyz));
+    const float det = r_add(r_add(r_mul(cxx, a00), r_mul(cxy, a01)), r_mul(cxz, a02));
+    if (!(det > 1e-12f)) return false;
+    const float id = r_div(1.0f, det);
+    const float i00 = r_mul(a00, id), i01 = r_mul(a01, id), i02 = r_mul(a02, id);
+    const float i11 = r_mul(a11, id), i12 = r_mul(a12, id);
+    const float i22 = r_mul(r_sub(r_mul(cxx, cyy), r_mul(cxy, cxy)), id);
+    const float wx = r_add(r_add(r_mul(i00, v[0]), r_mul(i01, v[1])), r_mul(i02, v[2]));
+    const float wy = r_add(r_add(r_mul(i01, v[0]), r_mul(i11, v[1])), r_mul(i12, v[2]));
+    const float wz = r_add(r_add(r_mul(i02, v[0]), r_mul(i12, v[1])), r_mul(i22, v[2]));
+    const float a = r_add(r_add(r_mul(v[0], wx), r_mul(v[1], wy)), r_mul(v[2], wz));
+    const float am = r_sub(a, k2);
+    if (!(am > r_mul(0.01f, k2))) return false;
+    const float G00 = r_sub(r_mul(am, i00), r_mul(wx, wx));
+    const float G01 = r_sub(r_mul(am, i01), r_mul(wx, wy));
+    const float G11 = r_sub(r_mul(am, i11), r_mul(wy, wy));
+    const float dG = r_sub(r_mul(G00, G11), r_mul(G01, G01));
+    const float tG = r_add(G00, G11);
+    if (!(G00 > 0.0f && dG > r_mul(1e-6f, r_mul(tG, tG)))) return false;
+    const float ivz = r_div(1.0f, v[2]);
+    const float hx = r_mul(r_mul(k2, wx), ivz), hy = r_mul(r_mul(k2, wy), ivz);
+    const float k0 = r_mul(r_mul(k2, a), r_mul(ivz, ivz));
+    const float idG = r_div(1.0f, dG);
+    const float dcx = r_mul(r_sub(r_mul(G11, hx), r_mul(G01, hy)), idG);
+    const float dcy = r_mul(r_sub(r_mul(G00, hy), r_mul(G01, hx)), idG);
+    const float rhs = r_add(k0, r_add(r_mul(hx, dcx), r_mul(hy, dcy)));
+    if (!(rhs > 0.0f && rhs < 1e30f)) return false;
+    e[0] = r_add(r_mul(c.fx, r_add(r_mul(v[0], ivz), dcx)), c.cx);
+    e[1] = r_add(r_mul(c.fy, r_add(r_mul(v[1], ivz), dcy)), c.cy);
+    e[2] = r_div(G00, r_mul(c.fx, c.fx));
+    e[3] = r_div(G01, r_mul(c.fx, c.fy));
+    e[4] = r_div(G11, r_mul(c.fy, c.fy));
+    q = make_float4(r_mul(rhs, 1.01f), r_div(-e[3], e[4]), r_div(-e[3], e[2]), 0.0f);
+    return true;
+}
+
+// Tile (tx, ty) against an ellipse: the minimum over the tile's pixel-centre
+// rectangle (grown by `grow` pixels) of Q(p) = (p - c)^T [[A,B],[B,C]] (p - c)
+// is at most q.x.  With c outside the rectangle the minimum lies on an edge
+// whose line separates c from it, at the clamped stationary point of Q along
+// that edge.
+__device__ __forceinline__ bool ellipse_rect_test(const CamParams &c, const float e[5], const float4 q, int tx,
+                                                  int ty, float grow) {
+    const float x0 = r_sub((float)(TILE * tx) + 0.5f, grow), y0 = r_sub((float)(TILE * ty) + 0.5f, grow);
+    const float x1 = r_add(fminf((float)(TILE * tx) + (float)TILE - 0.5f, (float)c.W - 0.5f), grow);
+    const float y1 = r_add(fminf((float)(TILE * ty) + (float)TILE - 0.5f, (float)c.H - 0.5f), grow);
+    const float dx0 = r_sub(x0, e[0]), dx1 = r_sub(x1, e[0]), dy0 = r_sub(y0, e[1]), dy1 = r_sub(y1, e[1]);
+    const bool sx = dx0 > 0.0f || dx1 < 0.0f, sy = dy0 > 0.0f || dy1 < 0.0f;
+    if (!sx && !sy) return true;
+    float best = 3.0e38f;
+    if (sx) {
+        const float x = dx0 > 0.0f ? dx0 : dx1;
+        const float y = fminf(fmaxf(r_mul(q.y, x), dy0), dy1);
+        best = r_add(r_mul(x, r_add(r_mul(e[2], x), r_mul(2.0f, r_mul(e[3], y)))), r_mul(e[4], r_mul(y, y)));
+    }
+    if (sy) {
+        const float y = dy0 > 0.0f ? dy0 : dy1;
+        const float x = fminf(fmaxf(r_mul(q.z, y), dx0), dx1);
+        best = fminf(best, r_add(r_mul(x, r_add(r_mul(e[2], x), r_mul(2.0f, r_mul(e[3], y)))),
+                                 r_mul(e[4], r_mul(y, y))));
+    }
+    return best <= q.x;
+}
+
+constexpr float ELL_GROW = 0.05f;   // pixel-centre rectangle growth of the silhouette test
+
 }  // namespace conegs

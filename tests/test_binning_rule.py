@@ -17,7 +17,15 @@ def _cases():
     blob_sc = S.blob_scene(3000, seed=1, cam=blob_cam)
     ragged = S.pinhole(70, 45, 40.0, 33.0, 21.0, cam_to_world=S.look_at((0.1, 0.0, -0.5), (0.2, 0.1, 4.0)))
     rag_sc = S.uniform_box_scene(500, seed=9, log_scale_mean=-2.5)
-    return {"c1": (c1cam, c1sc), "kb96": (kb, kb_sc), "blob160": (blob_cam, blob_sc), "ragged": (ragged, rag_sc)}
+    # strongly anisotropic Gaussians (log-scales N(-3, 1.5) per axis) around and in front of a
+    # wide, rotated pinhole with fx != fy: silhouette ellipses of every aspect, near the
+    # grazing limit, and cameras close to or inside the bound
+    wide = S.Camera(S.PINHOLE, 96, 64, 30.0, 36.0, 50.5, 30.25,
+                    cam_to_world=S.look_at((0.0, 0.1, 0.0), (1.0, 0.4, 2.0)))
+    an_sc = S.blob_scene(3000, seed=21, cam=wide, blob_frac=0.5, shell=(0.8, 4.0), log_scale_mean=-3.0,
+                         log_scale_std=1.5, sh_degree=0)
+    return {"c1": (c1cam, c1sc), "kb96": (kb, kb_sc), "blob160": (blob_cam, blob_sc), "ragged": (ragged, rag_sc),
+            "aniso_wide": (wide, an_sc)}
 
 
 CASES = _cases()
