@@ -435,6 +435,23 @@ __device__ bool ut_ellipse(const CamParams &c, const GaussArgs &ua, uint32_t gid
     return true;
 }
 
+// Candidate tiles of a silhouette ellipse e (centre, A, B, C, threshold): the
+// tiles whose pixel-centre rectangle meets the ellipse's bounding box, widened
+// by the test's rectangle growth and by 5% (det = AC - B^2 loses up to ~2.5% to
+// cancellation at the largest aspect the rule accepts, 1000).  The half-widths
+// of {Q <= t} are sqrt(t C / det) and sqrt(t A / det).
+__device__ __forceinline__ void ellipse_tile_box(const CamParams &c, const float *e, int &tx0, int &tx1, int &ty0,
+                                                 int &ty1) {
+    const float det = e[2] * e[4] - e[3] * e[3];
+    const float hx = sqrtf(fmaxf(e[5] * e[4] / det, 0.0f)) * 1.05f + ELL_GROW + 0.01f;
+    const float hy = sqrtf(fmaxf(e[5] * e[2] / det, 0.0f)) * 1.05f + ELL_GROW + 0.01f;
+    const float lim = 1e8f;
+    tx0 = max((int)ceilf(fmaxf((e[0] - hx - (TILE - 0.5f)) / TILE, -lim)), 0);
+    tx1 = min((int)floorf(fminf((e[0] + hx - 0.5f) / TILE, lim)), c.tiles_x - 1);
+    ty0 = max((int)ceilf(fmaxf((e[1] - hy - (TILE - 0.5f)) / TILE, -lim)), 0);
+    ty1 = min((int)floorf(fminf((e[1] + hy - 0.5f) / TILE, lim)), c.tiles_y - 1);
+}
+
 // Count (MODE 0) and emit (MODE 1) of the (tile, Gaussian) pairs.
 //
 // Each lane prepares one Gaussian (slot): flag, rule record, direction, cone,
@@ -679,10 +696,22 @@ __global__ void __launch_bounds__(32 * BIN_WARPS, 3) bin_kernel(CamParams c, Gau
                 el[4] = e1.x; el[5] = e1.y; el[6] = e1.z; el[7] = e1.w;
                 ellv = el[5] > 0.0f;
             }
-            const bool boxed =
+            bool boxed =
                 fl == 1 && half.y >= 1e-3f &&
                 (c.model == 0 ? pinhole_tile_box(c, gv, half, mcam[1], tx0, tx1, ty0, ty1)
                               : kb_tile_box(c, gv, half, mcam[1], tx0, tx1, ty0, ty1));
+            if (ellv) {
+                // every tile the silhouette test keeps lies in the ellipse's box
+                int ex0, ex1, ey0, ey1;
+                ellipse_tile_box(c, el, ex0, ex1, ey0, ey1);
+                if (boxed) {
+                    tx0 = max(tx0, ex0); tx1 = min(tx1, ex1);
+                    ty0 = max(ty0, ey0); ty1 = min(ty1, ey1);
+                } else {
+                    tx0 = ex0; tx1 = ex1; ty0 = ey0; ty1 = ey1;
+                    boxed = true;
+                }
+            }
             if (boxed) {
                 const int bw = tx1 - tx0 + 1, bh = ty1 - ty0 + 1;
                 nb = (bw > 0 && bh > 0) ? (uint32_t)(bw * bh) : 0u;
