@@ -1316,15 +1316,17 @@ static void fsigma(const float *q, const float *ls, float rho2, float *S) {
     }
 }
 
-/* View part: with v = (mu - o)/L in the camera frame, C normalised by its mean
+/* View part.  With v = (mu - o)/L in a frame F, C normalised by its mean
  * eigenvalue tau (+ 1e-4 I) and k^2 = kap^2 tau / L^2, a line of direction
- * d = (x, y, 1) meets E iff delta = d - v/v_z satisfies
+ * d = (x, y, 1) (in F) meets E iff delta = d - v/v_z satisfies
  *   delta^T G delta - 2 h^T delta <= k0,  G = (a - k^2) Ci_xy - w_xy w_xy^T,
  *   h = k^2 w_xy / v_z, k0 = k^2 a / v_z^2, w = Ci v, a = v^T w.
- * Returns 1 with e = (centre x, centre y, A, B, C) in pixels and q =
- * (1.01 * rhs, -B/C, -B/A); 0 when the test does not apply. */
-static int fellipse(const fcam *c, const float *g, const float *mu, float m, float *e, float *q) {
-    if (c->model != 0) return 0;
+ * Pinhole: F = the camera axes, the ellipse in pixels, el = (c_x, c_y, A, B, C,
+ * 1.01 rhs, -B/C, -B/A).  Fisheye: F = (e1, e2, u), u = (mu - o)/L, e1 from the
+ * world axis least aligned with u, so v = (0, 0, 1) and (x, y) are gnomonic
+ * coordinates around u; el = (c_x, c_y, G00, G01, G11, sqrt(1.01 rhs), sqrt(tr G), e1).
+ * Returns 0 when the test does not apply. */
+static int fellipse(const fcam *c, const float *g, const float *mu, float m, float *el) {
     float L = g[3], kap = g[4], ks = g[5], kr = g[6], r1sq = g[7], s2 = g[8];
     const float *S = g + 10;
     float sm = sqrtf(m);
@@ -1342,21 +1344,45 @@ static int fellipse(const fcam *c, const float *g, const float *mu, float m, flo
     }
     if (!(L > rf)) return 0;
     float w0 = mu[0] - c->o[0], w1 = mu[1] - c->o[1], w2 = mu[2] - c->o[2];
-    float iL = 1.0f / L;
-    float v[3];
-    for (int j = 0; j < 3; ++j) v[j] = ((c->R[j] * w0 + c->R[3 + j] * w1) + c->R[6 + j] * w2) * iL;
-    if (!(v[2] > 0.0f && v[2] * v[2] >= 0.05f)) return 0;
+    float F[9], v[3];
+    if (c->model == 0) {
+        for (int k = 0; k < 9; ++k) F[k] = c->R[k];
+        float iL = 1.0f / L;
+        for (int j = 0; j < 3; ++j) v[j] = ((c->R[j] * w0 + c->R[3 + j] * w1) + c->R[6 + j] * w2) * iL;
+        if (!(v[2] > 0.0f && v[2] * v[2] >= 0.05f)) return 0;
+    } else {
+        float u[3] = {w0 / L, w1 / L, w2 / L};
+        float au0 = fabsf(u[0]), au1 = fabsf(u[1]), au2 = fabsf(u[2]);
+        int k = (au0 <= au1 && au0 <= au2) ? 0 : (au1 <= au2 ? 1 : 2);
+        float b[3] = {0.0f, 0.0f, 0.0f};
+        b[k] = 1.0f;
+        float uk = u[k];
+        for (int j = 0; j < 3; ++j) b[j] = b[j] - uk * u[j];
+        float nb = sqrtf((b[0] * b[0] + b[1] * b[1]) + b[2] * b[2]);
+        float e1[3] = {b[0] / nb, b[1] / nb, b[2] / nb};
+        float e2[3] = {u[1] * e1[2] - u[2] * e1[1], u[2] * e1[0] - u[0] * e1[2], u[0] * e1[1] - u[1] * e1[0]};
+        for (int j = 0; j < 3; ++j) {
+            F[3 * j] = e1[j];
+            F[3 * j + 1] = e2[j];
+            F[3 * j + 2] = u[j];
+        }
+        v[0] = 0.0f;
+        v[1] = 0.0f;
+        v[2] = 1.0f;
+        el[7] = e1[0];
+        el[8] = e1[1];
+        el[9] = e1[2];
+    }
     float Sf[9] = {S[0], S[1], S[2], S[1], S[3], S[4], S[2], S[4], S[5]};
     float T[9];
     for (int i = 0; i < 3; ++i)
-        for (int k = 0; k < 3; ++k)
-            T[3 * i + k] = (Sf[3 * i] * c->R[k] + Sf[3 * i + 1] * c->R[3 + k]) + Sf[3 * i + 2] * c->R[6 + k];
+        for (int k = 0; k < 3; ++k) T[3 * i + k] = (Sf[3 * i] * F[k] + Sf[3 * i + 1] * F[3 + k]) + Sf[3 * i + 2] * F[6 + k];
     float Cc[6];
     {
         const int I[6] = {0, 0, 0, 1, 1, 2}, J[6] = {0, 1, 2, 1, 2, 2};
         for (int k = 0; k < 6; ++k) {
             int j = I[k], l = J[k];
-            Cc[k] = (c->R[j] * T[l] + c->R[3 + j] * T[3 + l]) + c->R[6 + j] * T[6 + l];
+            Cc[k] = (F[j] * T[l] + F[3 + j] * T[3 + l]) + F[6 + j] * T[6 + l];
         }
     }
     float iso = (tb * tb) * m + 1e-5f * s2;
@@ -1398,15 +1424,54 @@ static int fellipse(const fcam *c, const float *g, const float *mu, float m, flo
     float dcy = (G00 * hy - G01 * hx) * idG;
     float rhs = k0 + (hx * dcx + hy * dcy);
     if (!(rhs > 0.0f && rhs < 1e30f)) return 0;
-    e[0] = c->fx * (v[0] * ivz + dcx) + c->cx;
-    e[1] = c->fy * (v[1] * ivz + dcy) + c->cy;
-    e[2] = G00 / (c->fx * c->fx);
-    e[3] = G01 / (c->fx * c->fy);
-    e[4] = G11 / (c->fy * c->fy);
-    q[0] = rhs * 1.01f;
-    q[1] = (-e[3]) / e[4];
-    q[2] = (-e[3]) / e[2];
+    if (c->model == 0) {
+        el[0] = c->fx * (v[0] * ivz + dcx) + c->cx;
+        el[1] = c->fy * (v[1] * ivz + dcy) + c->cy;
+        el[2] = G00 / (c->fx * c->fx);
+        el[3] = G01 / (c->fx * c->fy);
+        el[4] = G11 / (c->fy * c->fy);
+        el[5] = rhs * 1.01f;
+        el[6] = (-el[3]) / el[4];
+        el[7] = (-el[3]) / el[2];
+    } else {
+        el[0] = dcx;
+        el[1] = dcy;
+        el[2] = G00;
+        el[3] = G01;
+        el[4] = G11;
+        el[5] = sqrtf(rhs * 1.01f);
+        el[6] = sqrtf(tG);
+    }
     return 1;
+}
+
+/* Fisheye tile test: the tile's rays lie within gamma of its axis a, so their
+ * gnomonic images lie within gamma / cos^2(phi + gamma) of a's (phi: the angle
+ * of a from u), and with |x|_G <= sqrt(tr G) |x| a tile that reaches the
+ * ellipse has |p_a - c|_G <= sqrt(threshold) + sqrt(tr G) gamma / cos^2(phi +
+ * gamma), gamma <= 2 sin(gamma/2) / cos(gamma/2).  Evaluated multiplied through
+ * by (a.u)^2, cos^4(phi + gamma) and cos^2(gamma/2), without division.  Tiles
+ * reaching beyond cos(phi + gamma) = 0.2 are kept.  u: the rule record's
+ * direction. */
+static int fkb_test(const float *el, const float *u, const float *t) {
+    float ca = (t[0] * u[0] + t[1] * u[1]) + t[2] * u[2];
+    float s = t[3], ch = t[4];
+    float sp = sqrtf(fmaxf(1.0f - ca * ca, 0.0f));
+    float cg = 1.0f - 2.0f * (s * s);
+    float sg = 2.0f * (s * ch);
+    float cpg = ca * cg - sp * sg;
+    if (!(cpg > 0.2f)) return 1;
+    float e1x = el[7], e1y = el[8], e1z = el[9];
+    float e2x = u[1] * e1z - u[2] * e1y;
+    float e2y = u[2] * e1x - u[0] * e1z;
+    float e2z = u[0] * e1y - u[1] * e1x;
+    float nx = ((t[0] * e1x + t[1] * e1y) + t[2] * e1z) - el[0] * ca;
+    float ny = ((t[0] * e2x + t[1] * e2y) + t[2] * e2z) - el[1] * ca;
+    float Qn = nx * (el[2] * nx + 2.0f * (el[3] * ny)) + el[4] * (ny * ny);
+    float c2 = cpg * cpg;
+    float lhs = (Qn * (c2 * c2)) * (ch * ch);
+    float r = (el[5] * c2) * ch + (2.0f * s) * el[6];
+    return lhs <= (r * r) * (ca * ca);
 }
 
 /* Tile (tx, ty) against the ellipse: the minimum over the tile's pixel-centre
@@ -1467,12 +1532,14 @@ long or_bin_counts(const double *campk, const float *table, int n, const float *
 #pragma omp for schedule(dynamic, 64) reduction(+ : total)
         for (int i = 0; i < n; ++i) {
             const float *g = recs + 16 * (size_t)i;
-            float e[5], q[3];
-            int ell = g[9] == 1.0f && fellipse(&c, g, means + 3 * (size_t)i, mbar, e, q);
+            float el[12];
+            int ell = g[9] == 1.0f && fellipse(&c, g, means + 3 * (size_t)i, mbar, el);
             int cnt = 0;
             for (int t = 0; t < nt; ++t) {
                 int ok = ftest(g, table + 6 * (size_t)t);
-                if (ok && ell) ok = fell_test(&c, e, q, t % ntx, t / ntx, 0.05f);
+                if (ok && ell)
+                    ok = c.model == 0 ? fell_test(&c, el, el + 5, t % ntx, t / ntx, 0.05f)
+                                      : fkb_test(el, g, table + 6 * (size_t)t);
                 if (pass) pass[(size_t)i * nt + t] = (unsigned char)ok;
                 mine[t] += ok;
                 cnt += ok;

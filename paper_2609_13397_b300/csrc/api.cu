@@ -503,7 +503,7 @@ static conegs_status render_front(conegs_view *v, unsigned flags, cudaStream_t s
     TRY(ensure(ctx, v->rec, sizeof(float4) * REC_F4 * nn, s));
     TRY(ensure(ctx, v->gview, sizeof(float4) * nn, s));
     TRY(ensure(ctx, v->gcone, sizeof(float2) * nn, s));
-    TRY(ensure(ctx, v->gell, 2 * sizeof(float4) * nn, s));
+    TRY(ensure(ctx, v->gell, 3 * sizeof(float4) * nn, s));
     TRY(ensure(ctx, v->gflag, nn, s));
     TRY(ensure(ctx, v->bincache, 3 * sizeof(uint4) * nn, s));
     TRY(ensure(ctx, v->counts, sizeof(uint32_t) * nn, s));

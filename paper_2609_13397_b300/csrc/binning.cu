@@ -304,7 +304,7 @@ __device__ __forceinline__ bool kb_tile_box(const CamParams &c, const float4 gv,
 // from the same floats; the tile test is a fixed sequence of correctly rounded
 // operations, identical in both passes.
 struct GaussArgs {
-    const float4 *ell;      // [n][2] the angular-tile rule's silhouette ellipse (view records)
+    const float4 *ell;      // [n][3] the angular-tile rule's silhouette ellipse (view records)
     const float *means;     // [n][3] (UT only)
     const float *W;         // [n][9] W_eff = S_eff^-1 R^T (UT only)
     const float *sig_eff;   // [n] (UT only)
@@ -486,7 +486,7 @@ __device__ __forceinline__ void mask_or(uint32_t m[8], uint32_t bits, uint32_t a
 }
 
 // Super-tile walk for one Gaussian by the whole warp; returns its pair count.
-// ell: the slot's silhouette ellipse (e[5], threshold, -B/C, -B/A), or nullptr.
+// ell: the slot's silhouette ellipse (ELL_F floats 32 apart, in shared memory), or nullptr.
 template <int MODE>
 __device__ __forceinline__ uint32_t bin_walk_supers(const CamParams &c, const float *g, const float4 gv,
                                                     const float2 half, const float *__restrict__ table,
@@ -520,8 +520,7 @@ __device__ __forceinline__ uint32_t bin_walk_supers(const CamParams &c, const fl
                         const int f = rule_test_fast(g, gv, tt);
                         tp = f == 2 ? rule_test(g, gv, tt) : f == 1;
                     }
-                    if (tp && ell) tp = ellipse_rect_test(c, ell, make_float4(ell[5], ell[6], ell[7], 0.0f), tx, ty,
-                                                          ELL_GROW);
+                    if (tp && ell) tp = ell_keep<32>(c, ell, gv, tt, tx, ty);
                 }
                 const uint32_t tb = __ballot_sync(0xffffffffu, tp);
                 if (MODE == 1 && tp) {
@@ -568,9 +567,7 @@ __device__ __forceinline__ uint32_t bin_walk_box(const CamParams &c, const float
                     const int f = rule_test_fast(g, gv, tt);
                     tp = f == 2 ? rule_test(g, gv, tt) : f == 1;
                 }
-                if (tp && ell)
-                    tp = ellipse_rect_test(c, ell, make_float4(ell[5], ell[6], ell[7], 0.0f), tx0 + qx, ty0 + qy,
-                                           ELL_GROW);
+                if (tp && ell) tp = ell_keep<32>(c, ell, gv, tt, tx0 + qx, ty0 + qy);
             }
         }
         const uint32_t tb = __ballot_sync(0xffffffffu, tp);
@@ -621,7 +618,7 @@ __global__ void __launch_bounds__(32 * BIN_WARPS, 3) bin_kernel(CamParams c, Gau
     __shared__ int4 s_box[BIN_WARPS][32];          // tx0, ty0, box width, bits: cached (1), UT (2), silhouette (4)
     __shared__ float s_inv[BIN_WARPS][32];         // 1 / box width
     __shared__ uint4 s_mask[BIN_WARPS][2][32];     // MODE 1: cached pass mask (8 words)
-    __shared__ float s_ell[BIN_WARPS][8][32];      // silhouette ellipse (valid: s_box .w bit 4)
+    __shared__ float s_ell[BIN_WARPS][ELL_F][32];  // silhouette ellipse (valid: s_box .w bit 4)
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t pos = ((int64_t)blockIdx.x * BIN_WARPS + wid) * 32 + lane;
     const bool have = pos < n;
@@ -630,7 +627,7 @@ __global__ void __launch_bounds__(32 * BIN_WARPS, 3) bin_kernel(CamParams c, Gau
     // ---- slot set-up
     uint32_t nb = 0, fl = 0, npk = 0, lofs = 0, lcnt = 0;
     bool walk = false, cached = false, big = false, listed = false, utslot = false, ellv = false;
-    float el[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float4 el0 = make_float4(0.f, 0.f, 0.f, 0.f), el1 = el0, el2 = el0;   // silhouette record
     float g[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float4 gv = make_float4(0.f, 0.f, 0.f, 0.f);
     float2 half = make_float2(0.f, 1.f);
@@ -691,19 +688,20 @@ __global__ void __launch_bounds__(32 * BIN_WARPS, 3) bin_kernel(CamParams c, Gau
             half = gcone[gid];
             if (fl == 1) {
                 // silhouette ellipse of the rule's bounding ellipsoid (view records; pinhole cameras)
-                const float4 e0 = ua.ell[2 * (size_t)gid], e1 = ua.ell[2 * (size_t)gid + 1];
-                el[0] = e0.x; el[1] = e0.y; el[2] = e0.z; el[3] = e0.w;
-                el[4] = e1.x; el[5] = e1.y; el[6] = e1.z; el[7] = e1.w;
-                ellv = el[5] > 0.0f;
+                el0 = ua.ell[3 * (size_t)gid];
+                el1 = ua.ell[3 * (size_t)gid + 1];
+                el2 = ua.ell[3 * (size_t)gid + 2];
+                ellv = el1.y > 0.0f;
             }
             bool boxed =
                 fl == 1 && half.y >= 1e-3f &&
                 (c.model == 0 ? pinhole_tile_box(c, gv, half, mcam[1], tx0, tx1, ty0, ty1)
                               : kb_tile_box(c, gv, half, mcam[1], tx0, tx1, ty0, ty1));
-            if (ellv) {
+            if (ellv && c.model == 0) {
                 // every tile the silhouette test keeps lies in the ellipse's box
                 int ex0, ex1, ey0, ey1;
-                ellipse_tile_box(c, el, ex0, ex1, ey0, ey1);
+                const float eb[6] = {el0.x, el0.y, el0.z, el0.w, el1.x, el1.y};
+                ellipse_tile_box(c, eb, ex0, ex1, ey0, ey1);
                 if (boxed) {
                     tx0 = max(tx0, ex0); tx1 = min(tx1, ex1);
                     ty0 = max(ty0, ey0); ty1 = min(ty1, ey1);
@@ -728,7 +726,11 @@ __global__ void __launch_bounds__(32 * BIN_WARPS, 3) bin_kernel(CamParams c, Gau
     s_half[wid][lane] = half;
     s_box[wid][lane] = make_int4(tx0, ty0, tx1 - tx0 + 1, (cached ? 1 : 0) | (utslot ? 2 : 0) | (ellv ? 4 : 0));
 #pragma unroll
-    for (int k = 0; k < 8; ++k) s_ell[wid][k][lane] = el[k];
+    for (int k = 0; k < 4; ++k) {
+        s_ell[wid][k][lane] = k == 0 ? el0.x : k == 1 ? el0.y : k == 2 ? el0.z : el0.w;
+        s_ell[wid][4 + k][lane] = k == 0 ? el1.x : k == 1 ? el1.y : k == 2 ? el1.z : el1.w;
+        s_ell[wid][8 + k][lane] = k == 0 ? el2.x : k == 1 ? el2.y : k == 2 ? el2.z : el2.w;
+    }
     s_inv[wid][lane] = tx1 >= tx0 ? 1.0f / (float)(tx1 - tx0 + 1) : 0.0f;
     // exclusive prefix of the packed slots' candidate counts (a cached slot of the emit
     // pass contributes its passing candidates only; big boxes are walked below)
@@ -802,13 +804,7 @@ __global__ void __launch_bounds__(32 * BIN_WARPS, 3) bin_kernel(CamParams c, Gau
                         const int f = rule_test_fast(gg, sgv, tt);
                         tp = f == 2 ? rule_test(gg, sgv, tt) : f == 1;
                     }
-                    if (tp && (bx.w & 4)) {
-                        const float ee[5] = {s_ell[wid][0][sl], s_ell[wid][1][sl], s_ell[wid][2][sl],
-                                             s_ell[wid][3][sl], s_ell[wid][4][sl]};
-                        tp = ellipse_rect_test(c, ee,
-                                               make_float4(s_ell[wid][5][sl], s_ell[wid][6][sl], s_ell[wid][7][sl], 0.f),
-                                               bx.x + kx, bx.y + ky, ELL_GROW);
-                    }
+                    if (tp && (bx.w & 4)) tp = ell_keep<32>(c, &s_ell[wid][0][sl], sgv, tt, bx.x + kx, bx.y + ky);
                 }
             }
         }
@@ -864,9 +860,7 @@ __global__ void __launch_bounds__(32 * BIN_WARPS, 3) bin_kernel(CamParams c, Gau
             lo = __shfl_sync(0xffffffffu, lo, 0);
             if (lo + bnb <= bcap) lst = blist + lo;
         }
-        float sel[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) sel[k] = s_ell[wid][k][sl];
+        const float *sel = &s_ell[wid][0][sl];
         const bool sev = (s_box[wid][sl].w & 4) != 0;
         const uint32_t wc = bin_walk_box<MODE, UT>(c, gg, sgv, sh, table, mzf, btx0, bty0, bw, bnb, sgid, sbase,
                                                    wm, lst, out_tile, out_gid, gg[5] == 3.0f, sev ? sel : nullptr);
@@ -907,9 +901,7 @@ __global__ void __launch_bounds__(32 * BIN_WARPS, 3) bin_kernel(CamParams c, Gau
         sh.x = __shfl_sync(0xffffffffu, half.x, sl); sh.y = __shfl_sync(0xffffffffu, half.y, sl);
         const uint32_t sgid = __shfl_sync(0xffffffffu, gid, sl);
         const uint32_t sbase = __shfl_sync(0xffffffffu, base, sl);
-        float sel[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) sel[k] = s_ell[wid][k][sl];
+        const float *sel = &s_ell[wid][0][sl];
         const bool sev = (s_box[wid][sl].w & 4) != 0;
         const uint32_t wc = bin_walk_supers<MODE>(c, gg, sgv, sh, table, super, mzf, sgid, sbase, out_tile, out_gid,
                                                   sev ? sel : nullptr);

@@ -179,17 +179,14 @@ __global__ void __launch_bounds__(256) view_records_kernel(CamParams c, ScenePar
     // scale bounds), camera-wide footprint, wide margin
     const float *br = sp.binrec + BINREC * i;
     gcone[i] = L > 0.0f ? cone_half_angle(br[0], br[4], sqrtf(br[3]), L, m, 1e-3f) : make_float2(1.0f, 0.0f);
-    // the binning rule's silhouette ellipse (pinhole; threshold -1 when it does not apply)
+    // the binning rule's silhouette ellipse (threshold -1 when it does not apply)
     {
-        float4 e0 = make_float4(0.f, 0.f, 0.f, 0.f), e1 = make_float4(0.f, -1.f, 0.f, 0.f);
-        float e[5];
-        float4 q;
-        if (flag == 1.0f && rule_ellipse(c, br, L, mu, br + 6, m, e, q)) {
-            e0 = make_float4(e[0], e[1], e[2], e[3]);
-            e1 = make_float4(e[4], q.x, q.y, q.z);
-        }
-        gell[2 * i] = e0;
-        gell[2 * i + 1] = e1;
+        float el[ELL_F] = {0.f, 0.f, 0.f, 0.f, 0.f, -1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (!(flag == 1.0f && rule_ellipse(c, br, L, mu, br + 6, m, el))) el[5] = -1.0f;
+        float4 *ge = gell + 3 * i;
+        ge[0] = make_float4(el[0], el[1], el[2], el[3]);
+        ge[1] = make_float4(el[4], el[5], el[6], el[7]);
+        ge[2] = make_float4(el[8], el[9], el[10], el[11]);
     }
     // rasteriser pre-test, with the exact kappa^2 = 2 ln(255 sigma)
     float g[3] = {0.f, 0.f, 0.f}, C[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};

@@ -259,6 +259,8 @@ __device__ __forceinline__ int rule_test_fast(const float *g, const float4 gv, c
 // degrees of the axis and the ellipse's aspect is below 1000; otherwise the
 // cone test alone decides.
 
+constexpr int ELL_F = 12;          // floats per Gaussian of the silhouette record
+
 // Scene part: Sigma_eff = R diag(s_eff^2) R^T (xx xy xz yy yz zz),
 // s_eff^2 = exp(2 log s) * 1.0001 + rho^2.
 static __device__ void rule_gauss_sigma(const float q[4], const float ls[3], float rho2, float S[6]) {
@@ -287,12 +289,15 @@ static __device__ void rule_gauss_sigma(const float q[4], const float ls[3], flo
     }
 }
 
-// View part: the silhouette ellipse in pixels, e = (centre x, centre y, A, B, C)
-// with Q(p) = (p - c)^T [[A,B],[B,C]] (p - c), q = (threshold, -B/C, -B/A).
+// View part.  el (ELL_F floats), written when the test applies (returns true):
+//   pinhole: the ellipse in pixels, Q(p) = (p - c)^T [[A,B],[B,C]] (p - c):
+//            c_x c_y A B C, threshold 1.01 rhs, -B/C, -B/A;
+//   fisheye: the ellipse in the plane tangent to the unit sphere at
+//            u = (mu - o)/L (gnomonic coordinates in the basis e1, e2 = u x e1):
+//            c_x c_y G00 G01 G11, sqrt(1.01 rhs), sqrt(tr G), e1 (3).
 // g: scene record (kap ks kr r1sq s2); L: |mu - o|; m: the largest tile footprint bound.
 static __device__ bool rule_ellipse(const CamParams &c, const float *g, float L, const float mu[3], const float S[6],
-                                    float m, float e[5], float4 &q) {
-    if (c.model != 0) return false;
+                                    float m, float el[ELL_F]) {
     const float kap = g[0], ks = g[1], kr = g[2], r1sq = g[3], s2 = g[4];
     const float sm = r_sqrt(m);
     const float cc = r_mul(kr, sm);
@@ -309,28 +314,60 @@ static __device__ bool rule_ellipse(const CamParams &c, const float *g, float L,
     }
     if (!(L > rf)) return false;
     const float w0 = r_sub(mu[0], c.o[0]), w1 = r_sub(mu[1], c.o[1]), w2 = r_sub(mu[2], c.o[2]);
-    const float iL = r_div(1.0f, L);
-    float v[3];
+    // frame F (columns, world): the camera axes (pinhole) or e1, e2, u (fisheye);
+    // v = (mu - o)/L in that frame
+    float F[9], v[3];
+    if (c.model == 0) {
 #pragma unroll
-    for (int j = 0; j < 3; ++j)
-        v[j] = r_mul(r_add(r_add(r_mul(c.R[j], w0), r_mul(c.R[3 + j], w1)), r_mul(c.R[6 + j], w2)), iL);
-    if (!(v[2] > 0.0f && r_mul(v[2], v[2]) >= 0.05f)) return false;
-    // covariance in the camera frame: Rc^T Sigma Rc
+        for (int k = 0; k < 9; ++k) F[k] = c.R[k];
+        const float iL = r_div(1.0f, L);
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            v[j] = r_mul(r_add(r_add(r_mul(c.R[j], w0), r_mul(c.R[3 + j], w1)), r_mul(c.R[6 + j], w2)), iL);
+        if (!(v[2] > 0.0f && r_mul(v[2], v[2]) >= 0.05f)) return false;
+    } else {
+        const float u[3] = {r_div(w0, L), r_div(w1, L), r_div(w2, L)};
+        const float au0 = fabsf(u[0]), au1 = fabsf(u[1]), au2 = fabsf(u[2]);
+        const int k = (au0 <= au1 && au0 <= au2) ? 0 : (au1 <= au2 ? 1 : 2);
+        float b[3] = {0.0f, 0.0f, 0.0f};
+        b[k] = 1.0f;
+        const float uk = u[k];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) b[j] = r_sub(b[j], r_mul(uk, u[j]));
+        const float nb = r_sqrt(r_add(r_add(r_mul(b[0], b[0]), r_mul(b[1], b[1])), r_mul(b[2], b[2])));
+        const float e1[3] = {r_div(b[0], nb), r_div(b[1], nb), r_div(b[2], nb)};
+        const float e2[3] = {r_sub(r_mul(u[1], e1[2]), r_mul(u[2], e1[1])),
+                             r_sub(r_mul(u[2], e1[0]), r_mul(u[0], e1[2])),
+                             r_sub(r_mul(u[0], e1[1]), r_mul(u[1], e1[0]))};
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            F[3 * j] = e1[j];
+            F[3 * j + 1] = e2[j];
+            F[3 * j + 2] = u[j];
+        }
+        v[0] = 0.0f;
+        v[1] = 0.0f;
+        v[2] = 1.0f;
+        el[7] = e1[0];
+        el[8] = e1[1];
+        el[9] = e1[2];
+    }
+    // covariance in the frame: F^T Sigma F
     const float Sf[9] = {S[0], S[1], S[2], S[1], S[3], S[4], S[2], S[4], S[5]};
     float T[9];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int k = 0; k < 3; ++k)
-            T[3 * i + k] = r_add(r_add(r_mul(Sf[3 * i], c.R[k]), r_mul(Sf[3 * i + 1], c.R[3 + k])),
-                                 r_mul(Sf[3 * i + 2], c.R[6 + k]));
+            T[3 * i + k] = r_add(r_add(r_mul(Sf[3 * i], F[k]), r_mul(Sf[3 * i + 1], F[3 + k])),
+                                 r_mul(Sf[3 * i + 2], F[6 + k]));
     float Cc[6];
     {
         const int I[6] = {0, 0, 0, 1, 1, 2}, J[6] = {0, 1, 2, 1, 2, 2};
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
             const int j = I[k], l = J[k];
-            Cc[k] = r_add(r_add(r_mul(c.R[j], T[l]), r_mul(c.R[3 + j], T[3 + l])), r_mul(c.R[6 + j], T[6 + l]));
+            Cc[k] = r_add(r_add(r_mul(F[j], T[l]), r_mul(F[3 + j], T[3 + l])), r_mul(F[6 + j], T[6 + l]));
         }
     }
     const float iso = r_add(r_mul(r_mul(tb, tb), m), r_mul(1e-5f, s2));
@@ -374,13 +411,56 @@ static __device__ bool rule_ellipse(const CamParams &c, const float *g, float L,
     const float dcy = r_mul(r_sub(r_mul(G00, hy), r_mul(G01, hx)), idG);
     const float rhs = r_add(k0, r_add(r_mul(hx, dcx), r_mul(hy, dcy)));
     if (!(rhs > 0.0f && rhs < 1e30f)) return false;
-    e[0] = r_add(r_mul(c.fx, r_add(r_mul(v[0], ivz), dcx)), c.cx);
-    e[1] = r_add(r_mul(c.fy, r_add(r_mul(v[1], ivz), dcy)), c.cy);
-    e[2] = r_div(G00, r_mul(c.fx, c.fx));
-    e[3] = r_div(G01, r_mul(c.fx, c.fy));
-    e[4] = r_div(G11, r_mul(c.fy, c.fy));
-    q = make_float4(r_mul(rhs, 1.01f), r_div(-e[3], e[4]), r_div(-e[3], e[2]), 0.0f);
+    if (c.model == 0) {
+        el[0] = r_add(r_mul(c.fx, r_add(r_mul(v[0], ivz), dcx)), c.cx);
+        el[1] = r_add(r_mul(c.fy, r_add(r_mul(v[1], ivz), dcy)), c.cy);
+        el[2] = r_div(G00, r_mul(c.fx, c.fx));
+        el[3] = r_div(G01, r_mul(c.fx, c.fy));
+        el[4] = r_div(G11, r_mul(c.fy, c.fy));
+        el[5] = r_mul(rhs, 1.01f);
+        el[6] = r_div(-el[3], el[4]);
+        el[7] = r_div(-el[3], el[2]);
+    } else {
+        el[0] = dcx;
+        el[1] = dcy;
+        el[2] = G00;
+        el[3] = G01;
+        el[4] = G11;
+        el[5] = r_sqrt(r_mul(rhs, 1.01f));
+        el[6] = r_sqrt(tG);
+    }
     return true;
+}
+
+// Fisheye tiles: the tile's rays lie within gamma of its axis a (sin(gamma/2) =
+// t[3]), so along the arc from a their gnomonic images move at most
+// gamma / cos^2(phi + gamma) (phi: the angle of a from u); with the G-norm
+// below sqrt(tr G) times the Euclidean one, a tile reaching the ellipse has
+// |p_a - c|_G <= sqrt(threshold) + sqrt(tr G) gamma / cos^2(phi + gamma), with
+// gamma <= 2 sin(gamma/2) / cos(gamma/2).  Multiplied through by cos^2(phi) =
+// (a.u)^2 (p_a = (a.e1, a.e2) / a.u), cos^4(phi + gamma) and cos^2(gamma/2), the
+// test needs no division.  Tiles reaching beyond cos(phi + gamma) = 0.2 are kept.
+template <int ST>
+__device__ __forceinline__ bool kb_ellipse_test(const float *el, const float4 gv, const float *t) {
+    const float ca = r_add(r_add(r_mul(t[0], gv.x), r_mul(t[1], gv.y)), r_mul(t[2], gv.z));
+    const float s = t[3], ch = t[4];
+    const float sp = r_sqrt(fmaxf(r_sub(1.0f, r_mul(ca, ca)), 0.0f));
+    const float cg = r_sub(1.0f, r_mul(2.0f, r_mul(s, s)));
+    const float sg = r_mul(2.0f, r_mul(s, ch));
+    const float cpg = r_sub(r_mul(ca, cg), r_mul(sp, sg));
+    if (!(cpg > 0.2f)) return true;
+    const float e1x = el[7 * ST], e1y = el[8 * ST], e1z = el[9 * ST];
+    const float e2x = r_sub(r_mul(gv.y, e1z), r_mul(gv.z, e1y));
+    const float e2y = r_sub(r_mul(gv.z, e1x), r_mul(gv.x, e1z));
+    const float e2z = r_sub(r_mul(gv.x, e1y), r_mul(gv.y, e1x));
+    const float nx = r_sub(r_add(r_add(r_mul(t[0], e1x), r_mul(t[1], e1y)), r_mul(t[2], e1z)), r_mul(el[0], ca));
+    const float ny = r_sub(r_add(r_add(r_mul(t[0], e2x), r_mul(t[1], e2y)), r_mul(t[2], e2z)), r_mul(el[ST], ca));
+    const float Qn = r_add(r_mul(nx, r_add(r_mul(el[2 * ST], nx), r_mul(2.0f, r_mul(el[3 * ST], ny)))),
+                           r_mul(el[4 * ST], r_mul(ny, ny)));
+    const float c2 = r_mul(cpg, cpg);
+    const float lhs = r_mul(r_mul(Qn, r_mul(c2, c2)), r_mul(ch, ch));
+    const float r = r_add(r_mul(r_mul(el[5 * ST], c2), ch), r_mul(r_mul(2.0f, s), el[6 * ST]));
+    return lhs <= r_mul(r_mul(r, r), r_mul(ca, ca));
 }
 
 // Tile (tx, ty) against an ellipse: the minimum over the tile's pixel-centre
@@ -388,7 +468,7 @@ static __device__ bool rule_ellipse(const CamParams &c, const float *g, float L,
 // is at most q.x.  With c outside the rectangle the minimum lies on an edge
 // whose line separates c from it, at the clamped stationary point of Q along
 // that edge.
-__device__ __forceinline__ bool ellipse_rect_test(const CamParams &c, const float e[5], const float4 q, int tx,
+__device__ __forceinline__ bool ellipse_rect_test(const CamParams &c, const float *e, const float4 q, int tx,
                                                   int ty, float grow) {
     const float x0 = r_sub((float)(TILE * tx) + 0.5f, grow), y0 = r_sub((float)(TILE * ty) + 0.5f, grow);
     const float x1 = r_add(fminf((float)(TILE * tx) + (float)TILE - 0.5f, (float)c.W - 0.5f), grow);
@@ -412,5 +492,17 @@ __device__ __forceinline__ bool ellipse_rect_test(const CamParams &c, const floa
 }
 
 constexpr float ELL_GROW = 0.05f;   // pixel-centre rectangle growth of the silhouette test
+
+// The silhouette test of tile (tx, ty) with record t (its cone) for a slot whose
+// ellipse applies; el[k * ST] is the record's k-th float, gv = (u, L) of the Gaussian.
+template <int ST>
+__device__ __forceinline__ bool ell_keep(const CamParams &c, const float *el, const float4 gv, const float *t, int tx,
+                                         int ty) {
+    if (c.model == 0) {
+        const float e[5] = {el[0], el[ST], el[2 * ST], el[3 * ST], el[4 * ST]};
+        return ellipse_rect_test(c, e, make_float4(el[5 * ST], el[6 * ST], el[7 * ST], 0.0f), tx, ty, ELL_GROW);
+    }
+    return kb_ellipse_test<ST>(el, gv, t);
+}
 
 }  // namespace conegs

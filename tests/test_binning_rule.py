@@ -24,8 +24,15 @@ def _cases():
                     cam_to_world=S.look_at((0.0, 0.1, 0.0), (1.0, 0.4, 2.0)))
     an_sc = S.blob_scene(3000, seed=21, cam=wide, blob_frac=0.5, shell=(0.8, 4.0), log_scale_mean=-3.0,
                          log_scale_std=1.5, sh_degree=0)
+    # the same kind of shell around a rotated fisheye with an off-centre principal point:
+    # Gaussians behind the camera, near the valid circle's rim and across the axis
+    fk = S.c3_camera(96, 80, seed=2)
+    fk = S.Camera(fk.model, fk.width, fk.height, fk.fx, fk.fy, 49.0, 38.5, k=fk.k,
+                  cam_to_world=S.look_at((0.1, 0.0, 0.1), (-1.0, 0.5, 2.0)), theta_lim=fk.theta_lim)
+    fk_sc = S.blob_scene(3000, seed=23, cam=S.pinhole(96, 80, 50.0), blob_frac=0.3, shell=(0.8, 4.0),
+                         log_scale_mean=-3.0, log_scale_std=1.2, sh_degree=0)
     return {"c1": (c1cam, c1sc), "kb96": (kb, kb_sc), "blob160": (blob_cam, blob_sc), "ragged": (ragged, rag_sc),
-            "aniso_wide": (wide, an_sc)}
+            "aniso_wide": (wide, an_sc), "kb_shell": (fk, fk_sc)}
 
 
 CASES = _cases()
