@@ -45,7 +45,7 @@ FLOPS_PER_PAIR_FLOOR = 212
 SMS, FP32_LANES = 148, 128
 # DRAM bytes (read + write) of one raster_seg_kernel<1, 1> launch on the 1280x720 view,
 # from the ncu capture summarised in profiles/raster_seg_c2_1280x720.md
-RASTER_MAIN_DRAM_BYTES = 92.99e6 + 9.10e6
+RASTER_MAIN_DRAM_BYTES = 76.45e6 + 7.52e6
 
 
 def _peaks():

@@ -31,7 +31,7 @@ from . import ConegsError, Context
 
 PER_PIXEL_BYTES = 37 + 16 + 16 + 8          # ray table + image + host staging + per-pixel state
 PER_TILE_BYTES = 24 + 8 + 8                 # tile cone, ranges, counters
-PER_GAUSSIAN_BYTES = 128 + 16 + 8 + 24 + 48  # view record, direction/depth, cone, counts/keys, binning cache
+PER_GAUSSIAN_BYTES = 128 + 16 + 8 + 24 + 48 + 48  # view record, direction/depth, cone, counts/keys, binning cache, silhouette
 PAIRS_PER_PIXEL = 12                        # pair-list allowance (8 B + 8 B sort scratch per pair)
 
 
