@@ -355,10 +355,20 @@ def run_ours(args, rank, world, local_rank):
 
 
 def run_probe(args):
-    """Small fixed workloads for ncu captures: set up C2 and render one view a few
-    times (no timing, no JSON)."""
+    """Small fixed workloads for ncu captures: set up C2 (or C3 for "c3") and render
+    one view a few times (no timing, no JSON)."""
     import torch
     import paper_2609_13397_b300 as cg
+    if args.probe == "c3":
+        ctx = cg.Context(0)
+        ctx.set_scene_from(S.c3_scene())
+        v = ctx.view()
+        v.set_camera_from(S.c3_camera())
+        for _ in range(3):
+            v.render()
+        torch.cuda.synchronize()
+        print("probe ok", args.probe, v.stats()["n_pairs"])
+        return
     cams, sc = build_workload()
     ctx = cg.Context(0)
     ctx.set_scene_from(sc)
@@ -575,7 +585,7 @@ def main():
     ap.add_argument("--c5-slots", type=int, default=6)
     ap.add_argument("--c5-gaussians", type=int, default=5_000_000)
     ap.add_argument("--c5-sweep", default="50,100,125,150", help="request rates (Hz) of the C5 rate sweep")
-    ap.add_argument("--probe", choices=["raster", "raster-1/8", "backward", "ut"], default=None,
+    ap.add_argument("--probe", choices=["raster", "raster-1/8", "backward", "ut", "c3"], default=None,
                     help="set up C2 and render 3 times for a profiler capture (prints no JSON)")
     args = ap.parse_args()
     if args.probe:
