@@ -101,3 +101,41 @@ def test_rule_culls_transparent_and_keeps_near(oracle_lib):
     assert recs[0, 9] == 0.0            # sigma < 1/255: can never contribute
     total, pg, pt, _ = oracle_lib.bin_counts(cam, sc)
     assert pg[0] == 0 and pg[2] == pt.size   # the near Gaussian covers every tile
+
+
+def _random_case(seed):
+    """A random small camera (pinhole or Kannala-Brandt, random pose, intrinsics and
+    distortion) inside a random mixture of clustered and surrounding Gaussians with
+    random size statistics."""
+    rng = np.random.default_rng(1000 + seed)
+    w, h = int(rng.integers(40, 90)), int(rng.integers(30, 70))
+    eye = rng.normal(0, 0.3, 3)
+    target = eye + rng.normal(0, 1, 3) + np.array([0.0, 0.0, 2.0])
+    pose = S.look_at(eye, target)
+    if seed % 2 == 0:
+        f = float(rng.uniform(0.4, 1.5) * w)
+        cam = S.Camera(S.PINHOLE, w, h, f, f * float(rng.uniform(0.8, 1.25)), w * float(rng.uniform(0.3, 0.7)),
+                       h * float(rng.uniform(0.3, 0.7)), cam_to_world=pose)
+    else:
+        base = S.c3_camera(w, w, seed=seed)
+        cam = S.Camera(base.model, w, h, base.fx, base.fy, w * float(rng.uniform(0.4, 0.6)),
+                       h * float(rng.uniform(0.4, 0.6)), k=base.k, cam_to_world=pose, theta_lim=base.theta_lim)
+    sc = S.blob_scene(700, seed=seed, cam=S.pinhole(w, h, 0.8 * w, cam_to_world=pose),
+                      blob_frac=float(rng.uniform(0.2, 0.8)), shell=(0.6, 5.0),
+                      log_scale_mean=float(rng.uniform(-4.0, -2.0)), log_scale_std=float(rng.uniform(0.3, 1.5)),
+                      sh_degree=0)
+    return cam, sc
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_binning_is_conservative_random(oracle_lib, seed):
+    """Random cameras and scenes: no pair that can reach alpha >= 1/255 falls in a
+    tile the rule (cone and silhouette tests) rejects."""
+    O = oracle_lib
+    cam, sc = _random_case(seed)
+    total, pg, pt, pas = O.bin_counts(cam, sc, dense=True)
+    pix, g = O.pairs_above(cam, sc, (1.0 / 255.0) * (1 - 1e-3))
+    tx, _ = O.tile_grid(cam)
+    tile = (pix // cam.width) // O.TILE * tx + (pix % cam.width) // O.TILE
+    missed = pas[g, tile] == 0
+    assert missed.sum() == 0, f"{missed.sum()} of {pix.size} contributing pairs not binned"

@@ -334,3 +334,18 @@ def test_render_host_batch_equals_device_render(cg):
     ctx.render_host_batch(views, host, streams=[torch.cuda.Stream() for _ in views])
     for (r, t), (hr, ht) in zip(dev, host):
         assert torch.equal(r.cpu(), hr) and torch.equal(t.cpu(), ht)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_pair_counts_bit_exact_random(cg, oracle_lib, seed):
+    """Random cameras (pinhole and Kannala-Brandt, random poses, intrinsics and
+    distortion) and scenes: per-Gaussian and per-tile counts bit-exact with the
+    oracle's FP32 emulation of the rule (cone and silhouette tests)."""
+    from test_binning_rule import _random_case
+    cam, sc = _random_case(seed)
+    ctx, v = _setup(cg, cam, sc)
+    v.render()
+    pg, pt = (t.cpu().numpy() for t in v.bin_counts())
+    total, opg, opt, _ = oracle_lib.bin_counts(cam, sc)
+    assert np.array_equal(pg, opg)
+    assert np.array_equal(pt, opt)
