@@ -123,12 +123,28 @@ __global__ void super_table_kernel(CamParams c, const float *__restrict__ table,
 
 // Camera-wide bounds over the tiles: out[0] = max m_t (footprint, for the
 // rasteriser's per-pixel pre-test), out[1] = max sin(gamma_t / 2) (tile cone
-// half-angle, for the binning candidate box).
-__global__ void max_m_kernel(const float *__restrict__ table, int nt, float *__restrict__ out) {
+// half-angle, for the binning candidate box).  Fisheye cameras also get
+// out[2 + j], j = 0..16: the largest sin(gamma_t / 2) over the tiles whose axis
+// lies within theta_lim j / 16 of the optical axis (a non-decreasing envelope;
+// tile cones grow toward a fisheye's rim).
+constexpr int GAMMA_BANDS = 16;
+
+__global__ void max_m_kernel(CamParams c, const float *__restrict__ table, int nt, float *__restrict__ out) {
+    __shared__ unsigned int s_band[GAMMA_BANDS + 1];
+    if (threadIdx.x <= GAMMA_BANDS) s_band[threadIdx.x] = 0u;
+    __syncthreads();
     float m = 0.0f, g = 0.0f;
     for (int t = threadIdx.x; t < nt; t += blockDim.x) {
-        m = fmaxf(m, table[6 * (size_t)t + 5]);
-        g = fmaxf(g, table[6 * (size_t)t + 3]);
+        const float *r = table + 6 * (size_t)t;
+        m = fmaxf(m, r[5]);
+        g = fmaxf(g, r[3]);
+        if (c.model != 0 && r[3] >= 0.0f) {
+            const float cz = r[0] * c.R[2] + r[1] * c.R[5] + r[2] * c.R[8];
+            const float th = acosf(fminf(fmaxf(cz, -1.0f), 1.0f));
+            // the band index rounds up (with margin), so band j covers every axis within its bound
+            const int j = min(GAMMA_BANDS, max(0, (int)ceilf(th / c.thlim * GAMMA_BANDS * 1.0001f + 1e-4f)));
+            atomicMax(&s_band[j], __float_as_uint(r[3]));    // non-negative floats order as their bits
+        }
     }
     for (int o = 16; o > 0; o >>= 1) {
         m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -145,8 +161,15 @@ __global__ void max_m_kernel(const float *__restrict__ table, int nt, float *__r
             m = fmaxf(m, sm[w]);
             g = fmaxf(g, sg[w]);
         }
-        out[0] = fmaxf(m, sm[0]);
-        out[1] = fmaxf(g, sg[0]);
+        m = fmaxf(m, sm[0]);
+        g = fmaxf(g, sg[0]);
+        out[0] = m;
+        out[1] = g;
+        float env = 0.0f;
+        for (int j = 0; j <= GAMMA_BANDS; ++j) {
+            env = c.model != 0 ? fmaxf(env, __uint_as_float(s_band[j])) : g;
+            out[2 + j] = env;
+        }
     }
 }
 
@@ -265,10 +288,20 @@ __device__ __forceinline__ float kb_radius(const CamParams &c, float th) {
 }
 
 __device__ __forceinline__ bool kb_tile_box(const CamParams &c, const float4 gv, const float2 half,
-                                            const float sg_max, int &tx0, int &tx1, int &ty0, int &ty1) {
+                                            const float *__restrict__ mcam, int &tx0, int &tx1, int &ty0,
+                                            int &ty1) {
     const float v0 = c.R[0] * gv.x + c.R[3] * gv.y + c.R[6] * gv.z;
     const float v1 = c.R[1] * gv.x + c.R[4] * gv.y + c.R[7] * gv.z;
     const float v2 = c.R[2] * gv.x + c.R[5] * gv.y + c.R[8] * gv.z;
+    // the largest tile cone among the tiles this Gaussian can reach: tile axes lie
+    // within phi + beta + gamma_max of the optical axis (gamma_max of the camera)
+    float sg_max = mcam[1];
+    {
+        const float sphi0 = sqrtf(v0 * v0 + v1 * v1);
+        const float reach = atan2f(sphi0, v2) + 2.0f * asinf(fminf(half.x, 1.0f)) + 2.0f * asinf(fminf(sg_max, 1.0f));
+        const int j = (int)ceilf(reach / c.thlim * GAMMA_BANDS * 1.0001f + 1e-4f);
+        if (j <= GAMMA_BANDS) sg_max = fminf(sg_max, mcam[2 + max(j, 0)]);
+    }
     const float cg = sqrtf(fmaxf(1.0f - sg_max * sg_max, 0.0f));
     const float sh = fminf((half.x * cg + half.y * sg_max) * 1.002f + 3e-5f, 1.0f);
     if (!(sh < 0.7f)) return false;
@@ -696,7 +729,7 @@ __global__ void __launch_bounds__(32 * BIN_WARPS, 3) bin_kernel(CamParams c, Gau
             bool boxed =
                 fl == 1 && half.y >= 1e-3f &&
                 (c.model == 0 ? pinhole_tile_box(c, gv, half, mcam[1], tx0, tx1, ty0, ty1)
-                              : kb_tile_box(c, gv, half, mcam[1], tx0, tx1, ty0, ty1));
+                              : kb_tile_box(c, gv, half, mcam, tx0, tx1, ty0, ty1));
             if (ellv && c.model == 0) {
                 // every tile the silhouette test keeps lies in the ellipse's box
                 int ex0, ex1, ey0, ey1;
@@ -938,7 +971,7 @@ cudaError_t launch_tile_tables(const CamParams &c, float *table, float *super, f
     note_launches(1);
     super_table_kernel<<<(unsigned)div_up(ns, 128), 128, 0, s>>>(c, table, super);
     note_launches(1);
-    max_m_kernel<<<1, 1024, 0, s>>>(table, nt, mcam);
+    max_m_kernel<<<1, 1024, 0, s>>>(c, table, nt, mcam);
     note_launches(1);
     return cudaGetLastError();
 }
