@@ -15,11 +15,17 @@
 //     Sigma_render <= Sigma_fp,eff, Eq. 9 and 12), with
 //     t* <= (L + kappa s_max) / (1 - kappa (1 + s_max/s_min) sqrt(m)) and
 //     |x* - mu| <= 255 kappa s_max (from det A <= (255 sigma)^2);
-//   * a (Gaussian, tile) pair is kept when the angle between mu - o and a_t
-//     is at most beta + gamma, sin(beta) = bound / L (chord form).
-// Two levels: super-tiles of 8x8 tiles and then tiles are pruned by a cheap
-// conservative cone test (fast math, wide margins); the exact per-tile rule
-// decides for the tiles that survive.
+//   * cone test: the angle between mu - o and a_t is at most beta + gamma,
+//     sin(beta) = bound / L (chord form);
+//   * silhouette test (rule.cuh): the Gaussian's bounding ellipsoid seen from
+//     the camera centre is an elliptic cone; its trace (an ellipse on a
+//     pinhole's image plane, or in the gnomonic plane around mu - o for a
+//     fisheye) must reach the tile's pixel-centre rectangle (pinhole) or the
+//     disc bounding the tile's rays (fisheye).
+// A pair is kept when both tests pass.  Candidates come from boxes (the
+// cone's image, cut to the ellipse's box on pinholes) or, without a box, from
+// super-tiles of 8x8 tiles pruned by a cheap conservative cone test (fast
+// math, wide margins); the exact tests decide for every candidate.
 #include "rule.cuh"
 
 namespace conegs {
@@ -488,10 +494,10 @@ __device__ __forceinline__ void ellipse_tile_box(const CamParams &c, const float
 // Count (MODE 0) and emit (MODE 1) of the (tile, Gaussian) pairs.
 //
 // Each lane prepares one Gaussian (slot): flag, rule record, direction, cone,
-// candidate box.  The warp then walks the concatenation of its 32 slots'
-// candidate tiles 32 at a time, each lane testing one (slot, tile) candidate
-// with the prefilter and the rule, so lanes stay busy whether a Gaussian
-// covers one tile or hundreds.  A slot's passes in an iteration are a
+// silhouette record, candidate box.  The warp then walks the concatenation of
+// its 32 slots' candidate tiles 32 at a time, each lane testing one (slot,
+// tile) candidate with the prefilter and the rule's two tests, so lanes stay
+// busy whether a Gaussian covers one tile or hundreds.  A slot's passes in an iteration are a
 // contiguous run of the ballot, which its owner lane folds into its count and,
 // for boxes of at most 256 tiles, into a 256-bit pass mask kept in the cache
 // (3 uint4 per Gaussian: box, mask) between the two passes.  MODE 1 (slots =
