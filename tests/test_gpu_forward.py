@@ -334,6 +334,11 @@ def test_render_host_batch_equals_device_render(cg):
     ctx.render_host_batch(views, host, streams=[torch.cuda.Stream() for _ in views])
     for (r, t), (hr, ht) in zip(dev, host):
         assert torch.equal(r.cpu(), hr) and torch.equal(t.cpu(), ht)
+    # pageable host memory: the copies complete before the call returns
+    plain = [(torch.empty(3, c.height, c.width), torch.empty(c.height, c.width)) for c in cams]
+    ctx.render_host_batch(views, plain, streams=[torch.cuda.Stream() for _ in views])
+    for (r, t), (hr, ht) in zip(dev, plain):
+        assert torch.equal(r.cpu(), hr) and torch.equal(t.cpu(), ht)
 
 
 @pytest.mark.parametrize("seed", range(8))
