@@ -80,6 +80,24 @@ __global__ void add_offsets_kernel(uint32_t *__restrict__ out, int64_t n, const 
     if (i < n) out[i] += offs[i / SCAN_TILE];
 }
 
+// One CTA per scan tile: adds the sum of the preceding tiles' totals (read
+// directly from block_sums, at most SCAN_TILE of them) to the tile's outputs,
+// so a scan of up to SCAN_TILE^2 items needs two launches.
+__global__ void __launch_bounds__(SCAN_THREADS) add_tile_prefix_kernel(uint32_t *__restrict__ out, int64_t n,
+                                                                       const uint32_t *__restrict__ block_sums) {
+    const int b = (int)blockIdx.x;
+    uint32_t v = 0u;
+    for (int j = threadIdx.x; j < b; j += SCAN_THREADS) v += block_sums[j];
+    uint32_t total;
+    block_exclusive_scan(v, total);
+    const int64_t base = (int64_t)b * SCAN_TILE;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        const int64_t i = base + (int64_t)k * SCAN_THREADS + threadIdx.x;
+        if (i < n) out[i] += total;
+    }
+}
+
 // Scratch words needed by exclusive_scan for n items.
 int64_t scan_scratch_words(int64_t n) {
     int64_t w = 0;
@@ -99,7 +117,10 @@ cudaError_t exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_
     uint32_t *bs = nb > 1 ? scratch : nullptr;
     scan_tiles_kernel<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, out, bs, pred);
     note_launches(1);
-    if (nb > 1) {
+    if (nb > 1 && nb <= SCAN_TILE) {
+        add_tile_prefix_kernel<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(out, n, bs);
+        note_launches(1);
+    } else if (nb > 1) {
         cudaError_t e = exclusive_scan(bs, bs, nb, scratch + nb, 0, s);
         if (e != cudaSuccess) return e;
         add_offsets_kernel<<<(unsigned)div_up(n, 256), 256, 0, s>>>(out, n, bs);
