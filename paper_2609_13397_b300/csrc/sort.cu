@@ -131,8 +131,9 @@ cudaError_t exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_
 
 // ---------------------------------------------------------------- reductions, compaction, gathers
 
-__global__ void sum_u64_kernel(const uint32_t *__restrict__ in, int64_t n, unsigned long long *__restrict__ total,
-                               unsigned long long *__restrict__ nonzero) {
+__global__ void __launch_bounds__(256) sum_u64_kernel(const uint32_t *__restrict__ in, int64_t n,
+                                                      unsigned long long *__restrict__ total,
+                                                      unsigned long long *__restrict__ nonzero) {
     unsigned long long s = 0, z = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t v = in[i];
@@ -143,7 +144,19 @@ __global__ void sum_u64_kernel(const uint32_t *__restrict__ in, int64_t n, unsig
         s += __shfl_xor_sync(0xffffffffu, s, o);
         z += __shfl_xor_sync(0xffffffffu, z, o);
     }
+    // one pair of atomics per block (per-warp atomics on two addresses serialise)
+    __shared__ unsigned long long ss[8], sz[8];
+    const int w = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0) {
+        ss[w] = s;
+        sz[w] = z;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+            s += ss[k];
+            z += sz[k];
+        }
         atomicAdd(total, s);
         atomicAdd(nonzero, z);
     }
