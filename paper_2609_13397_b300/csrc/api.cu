@@ -35,8 +35,8 @@ cudaError_t launch_bin_emit(const CamParams &c, const float *binrec, const float
                             const float4 *gell, bool ut, cudaStream_t s);
 cudaError_t launch_scene_cache(const SceneParams &sp, float *W, float *sig_eff, cudaStream_t s);
 cudaError_t launch_view_records(const CamParams &c, const SceneParams &sp, const float *mcam, float mzf,
-                                float4 *rec, float4 *gview, float2 *gcone, uint8_t *gflag, float4 *gell,
-                                cudaStream_t s);
+                                int fov_cull, float4 *rec, float4 *gview, float2 *gcone, uint8_t *gflag,
+                                float4 *gell, cudaStream_t s);
 int64_t scan_scratch_words(int64_t n);
 cudaError_t exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *scratch, int pred,
                            cudaStream_t s);
@@ -441,7 +441,7 @@ conegs_status conegs_set_camera(conegs_view *v, int model, int width, int height
     TRY(ensure(ctx, v->valid, P, s));
     TRY(ensure(ctx, v->table, sizeof(float) * 6 * nt, s));
     TRY(ensure(ctx, v->super, sizeof(float) * 6 * ns, s));
-    TRY(ensure(ctx, v->mcam, (2 + 17) * sizeof(float), s));
+    TRY(ensure(ctx, v->mcam, (3 + 17) * sizeof(float), s));
     TRY(ensure(ctx, v->ranges, sizeof(uint2) * nt, s));
     TRY(ensure(ctx, v->last, sizeof(uint32_t) * P, s));
     CUDA_TRY(launch_ray_table(c, v->d.as<float>(), v->dx.as<float>(), v->dy.as<float>(), v->valid.as<uint8_t>(), s));
@@ -520,7 +520,8 @@ static conegs_status render_front(conegs_view *v, unsigned flags, cudaStream_t s
         CUDA_TRY(cudaMemsetAsync(v->evaluated.p, 0, 2 * sizeof(unsigned long long), s));
         CUDA_TRY(cudaEventRecord(v->prof[0], s));
     }
-    CUDA_TRY(launch_view_records(c, sp, v->mcam.as<float>(), zf_bound(c, flags), v->rec.as<float4>(), v->gview.as<float4>(),
+    CUDA_TRY(launch_view_records(c, sp, v->mcam.as<float>(), zf_bound(c, flags), (flags & CONEGS_BIN_UT) ? 0 : 1,
+                                 v->rec.as<float4>(), v->gview.as<float4>(),
                                  v->gcone.as<float2>(), v->gflag.as<uint8_t>(), v->gell.as<float4>(), s));
     CUDA_TRY(cudaMemsetAsync(v->sums.as<unsigned long long>() + 2, 0, sizeof(unsigned long long), s));
     {

@@ -132,18 +132,26 @@ __global__ void super_table_kernel(CamParams c, const float *__restrict__ table,
 // half-angle, for the binning candidate box).  Fisheye cameras also get
 // out[2 + j], j = 0..16: the largest sin(gamma_t / 2) over the tiles whose axis
 // lies within theta_lim j / 16 of the optical axis (a non-decreasing envelope;
-// tile cones grow toward a fisheye's rim).
+// tile cones grow toward a fisheye's rim).  out[19]: the half-angle (rad,
+// widened) of a cone around the optical axis that contains every tile cone.
 constexpr int GAMMA_BANDS = 16;
 
 __global__ void max_m_kernel(CamParams c, const float *__restrict__ table, int nt, float *__restrict__ out) {
     __shared__ unsigned int s_band[GAMMA_BANDS + 1];
+    __shared__ unsigned int s_reach;
     if (threadIdx.x <= GAMMA_BANDS) s_band[threadIdx.x] = 0u;
+    if (threadIdx.x == 0) s_reach = 0u;
     __syncthreads();
-    float m = 0.0f, g = 0.0f;
+    float m = 0.0f, g = 0.0f, reach = 0.0f;
     for (int t = threadIdx.x; t < nt; t += blockDim.x) {
         const float *r = table + 6 * (size_t)t;
         m = fmaxf(m, r[5]);
         g = fmaxf(g, r[3]);
+        if (r[3] >= 0.0f) {
+            // the camera's cone: every tile cone lies within `reach` of the optical axis
+            const float cz = r[0] * c.R[2] + r[1] * c.R[5] + r[2] * c.R[8];
+            reach = fmaxf(reach, acosf(fminf(fmaxf(cz, -1.0f), 1.0f)) + 2.0f * asinf(fminf(r[3], 1.0f)));
+        }
         if (c.model != 0 && r[3] >= 0.0f) {
             const float cz = r[0] * c.R[2] + r[1] * c.R[5] + r[2] * c.R[8];
             const float th = acosf(fminf(fmaxf(cz, -1.0f), 1.0f));
@@ -155,7 +163,9 @@ __global__ void max_m_kernel(CamParams c, const float *__restrict__ table, int n
     for (int o = 16; o > 0; o >>= 1) {
         m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
         g = fmaxf(g, __shfl_xor_sync(0xffffffffu, g, o));
+        reach = fmaxf(reach, __shfl_xor_sync(0xffffffffu, reach, o));
     }
+    if ((threadIdx.x & 31) == 0) atomicMax(&s_reach, __float_as_uint(reach));   // non-negative: bit order
     __shared__ float sm[32], sg[32];
     if ((threadIdx.x & 31) == 0) {
         sm[threadIdx.x >> 5] = m;
@@ -176,6 +186,7 @@ __global__ void max_m_kernel(CamParams c, const float *__restrict__ table, int n
             env = c.model != 0 ? fmaxf(env, __uint_as_float(s_band[j])) : g;
             out[2 + j] = env;
         }
+        out[3 + GAMMA_BANDS] = __uint_as_float(s_reach) * 1.001f + 1e-4f;
     }
 }
 

@@ -146,7 +146,7 @@ __device__ bool tstar_bound(float kap, float s2, float r1, float L, float m, flo
 
 // Per view: binning direction/depth (the FP32 rule) and the raster record.
 __global__ void __launch_bounds__(256) view_records_kernel(CamParams c, SceneParams sp, const float *__restrict__ mcam,
-                                                           float mzf,
+                                                           float mzf, int fov_cull,
                                                            float4 *__restrict__ rec, float4 *__restrict__ gview,
                                                            float2 *__restrict__ gcone,
                                                            uint8_t *__restrict__ gflag,
@@ -157,6 +157,20 @@ __global__ void __launch_bounds__(256) view_records_kernel(CamParams c, ScenePar
     float flag = sp.binrec[BINREC * i + 5], u[3], L;
     rule_gauss_view(c, mu, flag, u, L);
     gview[i] = make_float4(u[0], u[1], u[2], L);
+    const float m = fmaxf(*mcam, mzf);   // footprint bound (raised for the z/f variant)
+    // binning prefilter: the cone of the binning rule's own bound (its kappa and
+    // scale bounds), camera-wide footprint, wide margin
+    const float *br = sp.binrec + BINREC * i;
+    const float2 gc = flag != 0.0f && L > 0.0f ? cone_half_angle(br[0], br[4], sqrtf(br[3]), L, m, 1e-3f)
+                                               : make_float2(1.0f, 0.0f);
+    gcone[i] = gc;
+    if (fov_cull && flag == 1.0f && gc.y > 1e-3f) {
+        // outside the camera's cone: every tile cone lies within mcam[19] of the
+        // optical axis, the Gaussian's within beta of u, so no tile can keep it
+        const float cz = u[0] * c.R[2] + u[1] * c.R[5] + u[2] * c.R[8];
+        const float ang = acosf(fminf(fmaxf(cz, -1.0f), 1.0f));
+        if (ang > 2.0f * asinf(fminf(gc.x, 1.0f)) + mcam[19] + 2e-3f) flag = 0.0f;
+    }
     gflag[i] = (uint8_t)flag;
     if (flag == 0.0f) return;
     float W[9];
@@ -174,11 +188,6 @@ __global__ void __launch_bounds__(256) view_records_kernel(CamParams c, ScenePar
     float col[3];
     sh_colour(sp.sh, i, sp.sh_degree, sp.storage, Y, col);
     const float rho2 = sp.rho2 ? sp.rho2[i] : 0.0f;
-    const float m = fmaxf(*mcam, mzf);   // footprint bound (raised for the z/f variant)
-    // binning prefilter: the cone of the binning rule's own bound (its kappa and
-    // scale bounds), camera-wide footprint, wide margin
-    const float *br = sp.binrec + BINREC * i;
-    gcone[i] = L > 0.0f ? cone_half_angle(br[0], br[4], sqrtf(br[3]), L, m, 1e-3f) : make_float2(1.0f, 0.0f);
     // the binning rule's silhouette ellipse (threshold -1 when it does not apply)
     {
         float el[ELL_F] = {0.f, 0.f, 0.f, 0.f, 0.f, -1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -226,11 +235,11 @@ cudaError_t launch_scene_cache(const SceneParams &sp, float *W, float *sig_eff, 
 }
 
 cudaError_t launch_view_records(const CamParams &c, const SceneParams &sp, const float *mcam, float mzf,
-                                float4 *rec, float4 *gview, float2 *gcone, uint8_t *gflag, float4 *gell,
-                                cudaStream_t s) {
+                                int fov_cull, float4 *rec, float4 *gview, float2 *gcone, uint8_t *gflag,
+                                float4 *gell, cudaStream_t s) {
     if (sp.n == 0) return cudaSuccess;
-    view_records_kernel<<<(unsigned)div_up(sp.n, 256), 256, 0, s>>>(c, sp, mcam, mzf, rec, gview, gcone, gflag,
-                                                                    gell);
+    view_records_kernel<<<(unsigned)div_up(sp.n, 256), 256, 0, s>>>(c, sp, mcam, mzf, fov_cull, rec, gview, gcone,
+                                                                    gflag, gell);
     note_launches(1);
     return cudaGetLastError();
 }
