@@ -737,7 +737,7 @@ __global__ void __launch_bounds__(32 * BIN_WARPS, 3) bin_kernel(CamParams c, Gau
             gv = gview[gid];
             half = gcone[gid];
             if (fl == 1) {
-                // silhouette ellipse of the rule's bounding ellipsoid (view records; pinhole cameras)
+                // silhouette record of the rule's bounding ellipsoid (from the view records)
                 el0 = ua.ell[3 * (size_t)gid];
                 el1 = ua.ell[3 * (size_t)gid + 1];
                 el2 = ua.ell[3 * (size_t)gid + 2];
