@@ -209,6 +209,27 @@ def test_empty_scene_and_invalid_pixels(cg):
     assert float(rgb[:, inv].abs().max()) == 0.0 and float(T[inv].min()) == 1.0
 
 
+@pytest.mark.parametrize("model", ["pinhole", "kb"])
+def test_every_gaussian_outside_the_view(cg, model):
+    """Gaussians all behind a pinhole (or beyond a fisheye's field of view):
+    background image and a zero adjoint.  Behind the pinhole they are culled
+    before binning (no pairs); a 64x64 fisheye's large footprint bound keeps a
+    few conservative pairs for the close, elongated ones, which contribute
+    nothing."""
+    sc = S.uniform_box_scene(300, seed=4)
+    sc.means[:, 2] = -sc.means[:, 2]                       # z in [-6, -2]: behind the camera
+    cam = S.pinhole(64, 48, 60.0) if model == "pinhole" else S.c3_camera(64, 64)
+    if model == "kb":
+        sc.means[:, :2] *= 0.05                            # straight behind: beyond the 95-degree half field
+    ctx, v = _setup(cg, cam, sc)
+    rgb, T = v.render(flags=cg.KEEP_FOR_BACKWARD)
+    assert float(rgb.abs().max()) == 0.0 and float(T.min()) == 1.0
+    if model == "pinhole":
+        assert v.stats()["n_pairs"] == 0 and v.stats()["n_visible"] == 0
+    g = v.render_backward(torch.ones_like(rgb))
+    assert all(float(t.abs().max()) == 0.0 for t in g.values())
+
+
 def test_floor_matches_oracle(cg, oracle_lib):
     sc = S.blob_scene(20000, seed=2, cam=S.pinhole(320, 180, 300.0))
     views = [S.pinhole(640, 360, 600.0), S.pinhole(320, 180, 300.0, cam_to_world=S.look_at((0.3, 0, 0), (0, 0, 6))),
