@@ -98,7 +98,10 @@ struct SegArgs {
 // Segment length L: with fewer non-empty tiles than two per resident CTA,
 // about two segments per resident CTA (at least 256 entries); otherwise 4x the
 // mean non-empty list (rounded up), so that only tail lists split.  Either way
-// the segment count stays below ntiles + max(2 CTA_SLOTS, ntiles / 4) + 1.
+// the segment count stays below ntiles + max(2 CTA_SLOTS, ntiles / 4) + 1, the
+// bound split_items_max sizes the split state with: a shorter L (more segments
+// per resident CTA) must raise that bound with it, or the passes write past
+// the state.
 static __device__ __forceinline__ uint32_t seg_length_dev(const unsigned long long *stat) {
     const unsigned long long ne = stat[0] > 0 ? stat[0] : 1, tot = stat[1];
     unsigned long long s;
