@@ -79,6 +79,14 @@ def num_threads() -> int:
     return int(lib().or_num_threads())
 
 
+def sh_basis(v) -> np.ndarray:
+    """The oracle's real SH basis (degrees 0-3, 16 values) of directions v [n,3]."""
+    v = _d(np.atleast_2d(v))
+    out = np.zeros((v.shape[0], 16))
+    lib().or_sh_basis(ctypes.c_int(v.shape[0]), _p(v), _p(out))
+    return out
+
+
 # ------------------------------------------------------------------ rays
 
 def rays(cam, xs=None, ys=None):

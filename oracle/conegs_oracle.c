@@ -287,6 +287,12 @@ static void prep_gauss(const double o[3], const double *mu, const double *ls, co
     }
 }
 
+/* The SH basis of n directions v[n*3] into Y[n*16] (exported so that the
+ * tests can pin it against its definition). */
+void or_sh_basis(int n, const double *v, double *Y) {
+    for (int i = 0; i < n; ++i) sh_basis(v + 3 * (size_t)i, Y + 16 * (size_t)i);
+}
+
 /* ------------------------------------------------------------------ 3x3 helpers */
 
 static void mv3(const double *M, const double *v, double *out) {
