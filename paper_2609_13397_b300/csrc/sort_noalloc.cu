@@ -22,6 +22,7 @@
 //     ordered by the caller (same stream, or events).  Nothing in the array
 //     needs to start at zero: each pass writes every counter and buffer
 //     entry it later reads.
+#include <cstdio>
 #include <mutex>
 
 #include "../../include/conegs.h"
@@ -87,6 +88,12 @@ extern "C" conegs_status conegs_radix_sort_pairs_noalloc(uint32_t *keys, uint32_
     }
     cudaError_t e = conegs::radix_sort_pairs(keys, values, base, base + NOALLOC_MAX_ITEMS, n, begin_bit, end_bit,
                                              base + 2 * NOALLOC_MAX_ITEMS, (cudaStream_t)stream);
-    if (e != cudaSuccess) return fail_msg(CONEGS_ERR_CUDA, "radix_sort_pairs_noalloc: kernel launch failed");
+    if (e != cudaSuccess) {
+        // the launch check can also surface an earlier, unrelated asynchronous fault: name the error
+        char msg[192];
+        snprintf(msg, sizeof msg, "radix_sort_pairs_noalloc: CUDA error after the sort launches: %s",
+                 cudaGetErrorString(e));
+        return fail_msg(CONEGS_ERR_CUDA, msg);
+    }
     return CONEGS_OK;
 }
