@@ -9,6 +9,11 @@ streams) into the C calls.
     view = ctx.view()
     view.set_camera(model, width, height, (fx, fy, cx, cy), k, cam_to_world, theta_lim)
     rgb, T = view.render()
+
+Differentiable form (the hand-written adjoint behind torch.autograd):
+
+    rgb, T = render_fn(view, means, log_scales, quats, opacity_logits, sh)
+    loss(rgb, T).backward()        # fills .grad of the five parameter tensors
 """
 from __future__ import annotations
 
@@ -27,7 +32,7 @@ FILTER_NONE, COMP_ADDITIVE, KEEP_FOR_BACKWARD, PROFILE, FILTER_ISO, FILTER_ZF, B
 _DTYPE_CODE = {torch.float32: F32, torch.bfloat16: BF16, torch.float16: F16}
 
 __all__ = ["Context", "View", "ConegsError", "PINHOLE", "KB_FISHEYE", "FILTER_NONE", "COMP_ADDITIVE",
-           "KEEP_FOR_BACKWARD", "PROFILE", "FILTER_ISO", "FILTER_ZF", "BIN_UT", "radix_sort_pairs"]
+           "KEEP_FOR_BACKWARD", "PROFILE", "FILTER_ISO", "FILTER_ZF", "BIN_UT", "radix_sort_pairs", "render_fn"]
 
 
 def _ptr(t: Optional[torch.Tensor]):
@@ -60,6 +65,9 @@ class Context:
         check(lib().conegs_create(ctypes.byref(h), device, mem_budget_bytes), "create")
         self._h = h
         self._scene_refs = None
+        self._scene_key = None      # (data_ptr, version) of the arrays the scene was set from
+        self._scene_gen = 0         # bumped by every set_scene
+        self._owned_copies = False  # the scene refs include copies this binding made
         self.n = 0
         self.sh_degree = 0
         self.storage = torch.float32
@@ -83,6 +91,8 @@ class Context:
         bf16/fp16 (``storage``); everything else is FP32."""
         dev = self.device
         storage = storage if storage is not None else torch.float32
+        given = dict(means=means, log_scales=log_scales, quats=quats, opacity_logits=opacity_logits, sh=sh,
+                     rho2=rho2)
         m = _dev(torch.as_tensor(means), dev)
         n = m.shape[0]
         refs = dict(
@@ -93,10 +103,19 @@ class Context:
             sh=_dev(torch.as_tensor(sh), dev, storage).reshape(n, (sh_degree + 1) ** 2, 3),
             rho2=None if rho2 is None else _dev(torch.as_tensor(rho2), dev).reshape(n),
         )
+        if self._owned_copies:
+            # the old scene arrays include copies made here: work queued on any stream
+            # may still read them, so let it finish before they can be freed
+            torch.cuda.synchronize(dev)
         check(lib().conegs_set_scene(self._h, n, _ptr(refs["means"]), _ptr(refs["log_scales"]), _ptr(refs["quats"]),
                                      _ptr(refs["opacity_logits"]), _ptr(refs["sh"]), sh_degree,
                                      _DTYPE_CODE[storage], _ptr(refs["rho2"]), _stream(stream)), "set_scene")
         self._scene_refs = refs
+        self._owned_copies = any(refs[k] is not None and not (isinstance(given[k], torch.Tensor) and
+                                                              refs[k].data_ptr() == given[k].data_ptr())
+                                 for k in refs)
+        self._scene_key = None
+        self._scene_gen += 1
         self.n, self.sh_degree, self.storage = n, sh_degree, storage
         return refs
 
@@ -125,6 +144,8 @@ class Context:
         rgb = (P * n)(*[_ptr(o[0]) for o in outs])
         Ts = (P * n)(*[_ptr(o[1]) for o in outs])
         st = (P * n)(*[_stream(None if streams is None else streams[i]) for i in range(n)])
+        for v in views:
+            v._bump()
         check(lib().conegs_render_batch(n, hv, rgb, Ts, flags, st), "render_batch")
         return list(outs)
 
@@ -137,6 +158,8 @@ class Context:
         rgb = (P * n)(*[_ptr(o[0]) for o in host_outs])
         Ts = (P * n)(*[_ptr(o[1]) for o in host_outs])
         st = (P * n)(*[_stream(None if streams is None else streams[i]) for i in range(n)])
+        for v in views:
+            v._bump()
         check(lib().conegs_render_host_batch(n, hv, rgb, Ts, flags, st), "render_host_batch")
         return list(host_outs)
 
@@ -157,6 +180,10 @@ class View:
         check(lib().conegs_view_create(ctx._h, ctypes.byref(h)), "view_create")
         self._h = h
         self.width = self.height = 0
+        self._token = 0       # bumped by every call that replaces the view's adjoint state
+
+    def _bump(self):
+        self._token += 1
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value and self.ctx._h is not None:
@@ -168,6 +195,7 @@ class View:
         check(lib().conegs_set_camera(self._h, int(model), int(width), int(height), _host_f32(intrinsics, 4),
                                       _host_f32(distortion, 4), _host_f32(cam_to_world, 12), float(theta_lim),
                                       _stream(stream)), "set_camera")
+        self._bump()
         self.width, self.height = int(width), int(height)
 
     def set_camera_from(self, cam, stream=None):
@@ -182,12 +210,14 @@ class View:
             out_rgb = torch.empty(3, self.height, self.width, device=dev, dtype=torch.float32)
         if out_T is None:
             out_T = torch.empty(self.height, self.width, device=dev, dtype=torch.float32)
+        self._bump()
         check(lib().conegs_render(self._h, _ptr(out_rgb), _ptr(out_T), flags, _stream(stream)), "render")
         return out_rgb, out_T
 
     def render_host(self, out_rgb_host: torch.Tensor, out_T_host: Optional[torch.Tensor] = None, flags: int = 0,
                     stream=None):
         """Render into (pinned) host tensors; returns after the copy completed."""
+        self._bump()
         check(lib().conegs_render_host(self._h, _ptr(out_rgb_host), _ptr(out_T_host), flags, _stream(stream)),
               "render_host")
         return out_rgb_host, out_T_host
@@ -200,11 +230,18 @@ class View:
         if grads is None:
             grads = {k: torch.zeros(refs[k].shape, device=dev, dtype=torch.float32)
                      for k in ("means", "log_scales", "quats", "opacity_logits", "sh")}
-        check(lib().conegs_render_backward(self._h, _ptr(dL_drgb.contiguous()),
-                                           _ptr(None if dL_dT is None else dL_dT.contiguous()),
+        g_rgb = _dev(dL_drgb, dev)
+        g_T = None if dL_dT is None else _dev(dL_dT, dev)
+        check(lib().conegs_render_backward(self._h, _ptr(g_rgb), _ptr(g_T),
                                            _ptr(grads.get("means")), _ptr(grads.get("log_scales")),
                                            _ptr(grads.get("quats")), _ptr(grads.get("opacity_logits")),
                                            _ptr(grads.get("sh")), _stream(stream)), "render_backward")
+        # copies made here are read asynchronously on `stream`: keep their memory from
+        # being handed out again before that work has run
+        s = stream if stream is not None else torch.cuda.current_stream(dev)
+        for mine, theirs in ((g_rgb, dL_drgb), (g_T, dL_dT)):
+            if mine is not None and mine is not theirs:
+                mine.record_stream(s)
         return grads
 
     def stats(self) -> dict:
@@ -241,6 +278,60 @@ class View:
         rng = torch.empty(st["tiles_x"] * st["tiles_y"], 2, device=self.ctx.device, dtype=torch.int32)
         check(lib().conegs_get_pairs(self._h, _ptr(gid), _ptr(rng), _stream(stream)), "get_pairs")
         return gid[: st["n_pairs"]], rng
+
+
+class _Render(torch.autograd.Function):
+    """Forward: conegs_render with KEEP_FOR_BACKWARD.  Backward: conegs_render_backward,
+    which recomputes the transmittance back to front (no per-pair state is stored)."""
+
+    @staticmethod
+    def forward(fctx, view, flags, means, log_scales, quats, opacity_logits, sh):
+        rgb, T = view.render(flags=flags | KEEP_FOR_BACKWARD)
+        fctx.view = view
+        fctx.token = (view._token, view.ctx._scene_gen)
+        fctx.dtypes = (means.dtype, log_scales.dtype, quats.dtype, opacity_logits.dtype, sh.dtype)
+        fctx.shapes = (means.shape, log_scales.shape, quats.shape, opacity_logits.shape, sh.shape)
+        return rgb, T
+
+    @staticmethod
+    @torch.autograd.function.once_differentiable
+    def backward(fctx, g_rgb, g_T):
+        view = fctx.view
+        if (view._token, view.ctx._scene_gen) != fctx.token:
+            raise RuntimeError("render_fn backward: the view was rendered again, or its camera or the scene "
+                               "was set, after this render; its adjoint state is gone (render each view once "
+                               "per backward, or use one view per render)")
+        if g_rgb is None:
+            g_rgb = torch.zeros(3, view.height, view.width, device=view.ctx.device)
+        grads = view.render_backward(g_rgb, g_T)
+        out = []
+        for k, dt, shp in zip(("means", "log_scales", "quats", "opacity_logits", "sh"), fctx.dtypes, fctx.shapes):
+            out.append(grads[k].reshape(shp).to(dt))
+        return (None, None, *out)
+
+
+def render_fn(view: View, means: torch.Tensor, log_scales: torch.Tensor, quats: torch.Tensor,
+              opacity_logits: torch.Tensor, sh: torch.Tensor, rho2: Optional[torch.Tensor] = None, flags: int = 0):
+    """Differentiable render of ``view`` (rgb [3,H,W], T [H,W]).
+
+    The five parameter tensors (device tensors: means, log_scales, quats FP32;
+    opacity_logits and sh FP32, BF16 or FP16 storage) become the context's
+    scene unless it was already set from exactly these tensors, unchanged since
+    (same storage and version).  ``loss.backward()`` then runs the library's
+    adjoint for this render and returns the gradients w.r.t. those tensors;
+    rho2 (the Eq. 10 floor) is not differentiated.  Each view keeps the state
+    of its last render only: render a view once per backward pass."""
+    ctx = view.ctx
+    key = tuple((t.data_ptr(), t._version) for t in (means, log_scales, quats, opacity_logits, sh)) + \
+        ((None,) if rho2 is None else ((rho2.data_ptr(), rho2._version),))
+    if ctx._scene_key != key:
+        k = sh.shape[1] if sh.dim() == 3 else sh.shape[-1] // 3
+        deg = int(round(k ** 0.5)) - 1
+        storage = sh.dtype if sh.dtype in (torch.bfloat16, torch.float16) else None
+        ctx.set_scene(means.detach(), log_scales.detach(), quats.detach(), opacity_logits.detach(), sh.detach(),
+                      deg, None if rho2 is None else rho2.detach(), storage=storage)
+        ctx._scene_key = key
+    return _Render.apply(view, int(flags), means, log_scales, quats, opacity_logits, sh)
 
 
 def radix_sort_pairs(ctx: Context, keys: torch.Tensor, values: torch.Tensor, begin_bit: int = 0, end_bit: int = 32,

@@ -351,7 +351,7 @@ conegs_status conegs_view_create(conegs_ctx *ctx, conegs_view **out) {
     v->ctx = ctx;
     cudaError_t e = cudaEventCreateWithFlags(&v->done, cudaEventDisableTiming);
     for (int k = 0; k < 6 && e == cudaSuccess; ++k) e = cudaEventCreate(&v->prof[k]);
-    if (e == cudaSuccess) e = cudaMallocHost(&v->h_sums, 4 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMallocHost(&v->h_sums, 5 * sizeof(unsigned long long));
     if (e != cudaSuccess) {
         if (v->done) cudaEventDestroy(v->done);
         delete v;
@@ -516,8 +516,8 @@ static conegs_status render_front(conegs_view *v, unsigned flags, cudaStream_t s
     SceneParams sp = ctx->sp;
     const bool prof = (flags & CONEGS_PROFILE) != 0;
     if (prof) {
-        TRY(ensure(ctx, v->evaluated, 2 * sizeof(unsigned long long), s));
-        CUDA_TRY(cudaMemsetAsync(v->evaluated.p, 0, 2 * sizeof(unsigned long long), s));
+        TRY(ensure(ctx, v->evaluated, 3 * sizeof(unsigned long long), s));
+        CUDA_TRY(cudaMemsetAsync(v->evaluated.p, 0, 3 * sizeof(unsigned long long), s));
         CUDA_TRY(cudaEventRecord(v->prof[0], s));
     }
     CUDA_TRY(launch_view_records(c, sp, v->mcam.as<float>(), zf_bound(c, flags), (flags & CONEGS_BIN_UT) ? 0 : 1,
@@ -615,7 +615,7 @@ static conegs_status render_back(conegs_view *v, float *out_rgb, float *out_T, u
                                  prof ? v->prof[4] : nullptr, prof ? v->prof[5] : nullptr));
     if (prof) {
         CUDA_TRY(cudaEventRecord(v->prof[3], s));
-        CUDA_TRY(cudaMemcpyAsync(v->h_sums + 2, v->evaluated.p, 2 * sizeof(unsigned long long),
+        CUDA_TRY(cudaMemcpyAsync(v->h_sums + 2, v->evaluated.p, 3 * sizeof(unsigned long long),
                                  cudaMemcpyDeviceToHost, s));
     }
     v->profiled = prof;
@@ -825,6 +825,7 @@ conegs_status conegs_get_stats(const conegs_view *v, conegs_stats *out) {
         out->ms_raster_main = t45;
         out->n_walked = (int64_t)v->h_sums[2];
         out->n_evaluated = (int64_t)v->h_sums[3];
+        out->n_evaluated_flat = (int64_t)v->h_sums[4];
     }
     return CONEGS_OK;
 }

@@ -25,22 +25,25 @@
 
 namespace conegs {
 
-// Reverse-mode of pair_response<FILTER> given dL/dT.  Accumulates dL/dW (9,
-// row-major), dL/do_u (3) and returns dL/dsigma_eff.
-template <bool FILTER>
-__device__ __forceinline__ float pair_adjoint(const PairFwd &f, const float4 r0, const float4 r1, const float4 r2,
-                                              const float sig, const float rho2, const PixelRays &px, float gT,
-                                              float gW[9], float gou[3]) {
-    const float T = f.T;
-    const float gsig = sig > 0.0f ? gT * T / sig : 0.0f;
-    const float gQ = -0.5f * T * gT;
-    float gqq = 0.0f, gdu[3] = {0.f, 0.f, 0.f}, gq[3] = {0.f, 0.f, 0.f}, gts = 0.0f, ginv_n = 0.0f;
-    float ggx[3] = {0.f, 0.f, 0.f}, ggy[3] = {0.f, 0.f, 0.f};
+// Reverse-mode of pair_response<FILTER, true, R> given dL/dT, in the same
+// arithmetic type R.  Accumulates dL/dW (9, row-major), dL/do_u (3) and
+// returns dL/dsigma_eff.
+template <bool FILTER, typename R>
+__device__ __forceinline__ float pair_adjoint(const PairFwdT<R> &f, const GaussRec<R> &gr, const PixelRays &px,
+                                              float gT_in, float gW[9], float gou[3]) {
+    const R third = R(1) / R(3);
+    const R gT = gT_in, sig = gr.sig, rho2 = gr.rho2;
+    const R T = f.T;
+    const R gsig = sig > R(0) ? gT * T / sig : R(0);
+    const R gQ = R(-0.5) * T * gT;
+    R gqq = R(0), gdu[3] = {R(0), R(0), R(0)}, gq[3] = {R(0), R(0), R(0)}, gts = R(0), ginv_n = R(0);
+    R ggx[3] = {R(0), R(0), R(0)}, ggy[3] = {R(0), R(0), R(0)};
+    R gou_r[3] = {R(0), R(0), R(0)};
     if (!FILTER) {
         gqq = gQ;
     } else {
-        float gdet = -0.5f * T * gT * f.inv_det;             // T ~ det^-1/2
-        float gbPb = 0.0f;
+        R gdet = -R(0.5) * T * gT * f.inv_det;             // T ~ det^-1/2
+        R gbPb = R(0);
         if (!f.clamped) {                                    // Q = qq - bPb/det
             gqq = gQ;
             gbPb = -gQ * f.inv_det;
@@ -50,87 +53,87 @@ __device__ __forceinline__ float pair_adjoint(const PairFwd &f, const float4 r0,
             gdet += -gQ * f.qq * f.inv_det * f.inv_det;
         }
         // bPb = b0^2 p00 + b0 b1 (p01 + p10) + b1^2 p11
-        const float b0 = f.b0, b1 = f.b1;
-        const float gb0 = gbPb * (2.0f * b0 * f.p00 + b1 * (f.p01 + f.p10));
-        const float gb1 = gbPb * (b0 * (f.p01 + f.p10) + 2.0f * b1 * f.p11);
-        const float gp00 = gbPb * b0 * b0, gp01 = gbPb * b0 * b1, gp10 = gp01, gp11 = gbPb * b1 * b1;
+        const R b0 = f.b0, b1 = f.b1;
+        const R gb0 = gbPb * (R(2) * b0 * f.p00 + b1 * (f.p01 + f.p10));
+        const R gb1 = gbPb * (b0 * (f.p01 + f.p10) + R(2) * b1 * f.p11);
+        const R gp00 = gbPb * b0 * b0, gp01 = gbPb * b0 * b1, gp10 = gp01, gp11 = gbPb * b1 * b1;
         // P = K adj(M)
-        const float k00 = f.k00, k01 = f.k01, k11 = f.k11;
-        const float m00 = f.m00, m01 = f.m01, m10 = f.m10, m11 = f.m11;
-        float gk00 = gp00 * m11 - gp01 * m01;
-        float gk01 = -gp00 * m10 + gp01 * m00 + gp10 * m11 - gp11 * m01;
-        float gk11 = -gp10 * m10 + gp11 * m00;
-        float gm00 = gp01 * k01 + gp11 * k11 + gdet * m11;
-        float gm11 = gp00 * k00 + gp10 * k01 + gdet * m00;
-        float gm01 = -gp01 * k00 - gp11 * k01 - gdet * m10;
-        float gm10 = -gp00 * k01 - gp10 * k11 - gdet * m01;
+        const R k00 = f.k00, k01 = f.k01, k11 = f.k11;
+        const R m00 = f.m00, m01 = f.m01, m10 = f.m10, m11 = f.m11;
+        R gk00 = gp00 * m11 - gp01 * m01;
+        R gk01 = -gp00 * m10 + gp01 * m00 + gp10 * m11 - gp11 * m01;
+        R gk11 = -gp10 * m10 + gp11 * m00;
+        R gm00 = gp01 * k01 + gp11 * k11 + gdet * m11;
+        R gm11 = gp00 * k00 + gp10 * k01 + gdet * m00;
+        R gm01 = -gp01 * k00 - gp11 * k01 - gdet * m10;
+        R gm10 = -gp00 * k01 - gp10 * k11 - gdet * m01;
         // M = I + G K
-        const float G00 = f.G00, G01 = f.G01, G11 = f.G11;
-        const float gG00 = gm00 * k00 + gm01 * k01;
-        const float gG01 = gm00 * k01 + gm01 * k11 + gm10 * k00 + gm11 * k01;
-        const float gG11 = gm10 * k01 + gm11 * k11;
+        const R G00 = f.G00, G01 = f.G01, G11 = f.G11;
+        const R gG00 = gm00 * k00 + gm01 * k01;
+        const R gG01 = gm00 * k01 + gm01 * k11 + gm10 * k00 + gm11 * k01;
+        const R gG11 = gm10 * k01 + gm11 * k11;
         gk00 += gm00 * G00 + gm10 * G01;
         gk01 += gm00 * G01 + gm01 * G00 + gm10 * G11 + gm11 * G01;
         gk11 += gm01 * G01 + gm11 * G11;
         // K = f(H') (Eq. 12); H' = t2 A, t2 = ts^2/3
-        float gcx = 0.0f, gcy = 0.0f;
+        R gcx = R(0), gcy = R(0);
         if (f.kcase == 1 || f.kcase == 2) {
-            const float h00 = f.h00, h01 = f.h01, h11 = f.h11;
-            float gh00 = 0.f, gh01 = 0.f, gh11 = 0.f;
-            const float dh = h00 * h11 - h01 * h01;
+            const R h00 = f.h00, h01 = f.h01, h11 = f.h11;
+            R gh00 = R(0), gh01 = R(0), gh11 = R(0);
+            const R dh = h00 * h11 - h01 * h01;
             if (f.kcase == 1) {                              // K = (I - rho2 H'^-1)/3
-                const float s = rho2 / dh;
-                const float gs = (-gk00 * h11 - gk11 * h00 + gk01 * h01) * (1.0f / 3.0f);
-                gh11 += -gk00 * s * (1.0f / 3.0f);
-                gh00 += -gk11 * s * (1.0f / 3.0f);
-                gh01 += gk01 * s * (1.0f / 3.0f);
-                const float gdh = -gs * s / dh;
+                const R s = rho2 / dh;
+                const R gs = (-gk00 * h11 - gk11 * h00 + gk01 * h01) * third;
+                gh11 += -gk00 * s * third;
+                gh00 += -gk11 * s * third;
+                gh01 += gk01 * s * third;
+                const R gdh = -gs * s / dh;
                 gh00 += gdh * h11;
                 gh11 += gdh * h00;
-                gh01 += -2.0f * gdh * h01;
+                gh01 += -R(2) * gdh * h01;
             } else {                                         // K = sc (H' - l2 I)
-                const float mean = 0.5f * (h00 + h11), half = 0.5f * (h00 - h11);
-                const float r2 = half * half + h01 * h01;
-                const float rad = r2 > 0.0f ? sqrtf(r2) : 0.0f;
-                const float l1 = mean + rad;
-                const float l2 = fmaxf(dh, 0.0f) / l1;
-                const float D = 3.0f * l1 * (l1 - l2);
-                const float sc = (l1 - rho2) / D;
-                const float gsc = gk00 * (h00 - l2) + gk11 * (h11 - l2) + gk01 * h01;
+                const R mean = R(0.5) * (h00 + h11), half = R(0.5) * (h00 - h11);
+                const R r2 = half * half + h01 * h01;
+                const R rad = r2 > R(0) ? Ar<R>::sqrt(r2) : R(0);
+                const R l1 = mean + rad;
+                const R l2 = Ar<R>::max(dh, R(0)) / l1;
+                const R D = R(3) * l1 * (l1 - l2);
+                const R sc = (l1 - rho2) / D;
+                const R gsc = gk00 * (h00 - l2) + gk11 * (h11 - l2) + gk01 * h01;
                 gh00 += gk00 * sc;
                 gh11 += gk11 * sc;
                 gh01 += gk01 * sc;
-                float gl2 = -(gk00 + gk11) * sc;
-                const float gN = gsc / D, gD = -gsc * sc / D;
-                float gl1 = gN + gD * 3.0f * (2.0f * l1 - l2);
-                gl2 += gD * (-3.0f * l1);
-                const float gdh2 = dh > 0.0f ? gl2 / l1 : 0.0f;
+                R gl2 = -(gk00 + gk11) * sc;
+                const R gN = gsc / D, gD = -gsc * sc / D;
+                R gl1 = gN + gD * R(3) * (R(2) * l1 - l2);
+                gl2 += gD * (-R(3) * l1);
+                const R gdh2 = dh > R(0) ? gl2 / l1 : R(0);
                 gl1 += -gl2 * l2 / l1;
                 gh00 += gdh2 * h11;
                 gh11 += gdh2 * h00;
-                gh01 += -2.0f * gdh2 * h01;
-                const float ghalf = rad > 0.0f ? gl1 * half / rad : 0.0f;
-                gh01 += rad > 0.0f ? gl1 * h01 / rad : 0.0f;
-                gh00 += 0.5f * gl1 + 0.5f * ghalf;
-                gh11 += 0.5f * gl1 - 0.5f * ghalf;
+                gh01 += -R(2) * gdh2 * h01;
+                const R ghalf = rad > R(0) ? gl1 * half / rad : R(0);
+                gh01 += rad > R(0) ? gl1 * h01 / rad : R(0);
+                gh00 += R(0.5) * gl1 + R(0.5) * ghalf;
+                gh11 += R(0.5) * gl1 - R(0.5) * ghalf;
             }
-            const float gt2 = gh00 * f.A00 + gh01 * f.A01 + gh11 * f.A11;
-            const float gA00 = gh00 * f.t2, gA01 = gh01 * f.t2, gA11 = gh11 * f.t2;
-            gts += gt2 * (2.0f / 3.0f) * f.ts;
-            gcx += gA00 * (2.0f * f.cx - 2.0f * px.d_dx) + gA01 * (f.cy - px.d_dy);
-            gcy += gA11 * (2.0f * f.cy - 2.0f * px.d_dy) + gA01 * (f.cx - px.d_dx);
+            const R gt2 = gh00 * f.A00 + gh01 * f.A01 + gh11 * f.A11;
+            const R gA00 = gh00 * f.t2, gA01 = gh01 * f.t2, gA11 = gh11 * f.t2;
+            gts += gt2 * (R(2) / R(3)) * f.ts;
+            gcx += gA00 * (R(2) * f.cx - R(2) * px.d_dx) + gA01 * (f.cy - px.d_dy);
+            gcy += gA11 * (R(2) * f.cy - R(2) * px.d_dy) + gA01 * (f.cx - px.d_dx);
         }
         // G, b from e_x, e_y, q
-        float gex[3], gey[3];
+        R gex[3], gey[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            gex[k] = 2.0f * gG00 * f.ex[k] + gG01 * f.ey[k] + gb0 * f.q[k];
-            gey[k] = 2.0f * gG11 * f.ey[k] + gG01 * f.ex[k] + gb1 * f.q[k];
+            gex[k] = R(2) * gG00 * f.ex[k] + gG01 * f.ey[k] + gb0 * f.q[k];
+            gey[k] = R(2) * gG11 * f.ey[k] + gG01 * f.ex[k] + gb1 * f.q[k];
             gq[k] += gb0 * f.ex[k] + gb1 * f.ey[k];
         }
         // e_i = ts (g_i - c_i du)
-        const float ts = f.ts;
-        float gxe = 0.f, gye = 0.f;
+        const R ts = f.ts;
+        R gxe = R(0), gye = R(0);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             gts += gex[k] * (f.gx[k] - f.cx * f.du[k]) + gey[k] * (f.gy[k] - f.cy * f.du[k]);
@@ -143,7 +146,7 @@ __device__ __forceinline__ float pair_adjoint(const PairFwd &f, const float4 r0,
         gcx += -ts * gxe;
         gcy += -ts * gye;
         // c_i = (du . g_i) inv_n
-        float dgx = 0.f, dgy = 0.f;
+        R dgx = R(0), dgy = R(0);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             gdu[k] += (gcx * f.gx[k] + gcy * f.gy[k]) * f.inv_n;
@@ -155,31 +158,52 @@ __device__ __forceinline__ float pair_adjoint(const PairFwd &f, const float4 r0,
         ginv_n += gcx * dgx + gcy * dgy;
     }
     // qq = q.q ; q = o_u + ts du
-    const float ou[3] = {r0.w, r1.w, r2.w};
+    const R *ou = gr.ou;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) gq[k] += 2.0f * gqq * f.q[k];
+    for (int k = 0; k < 3; ++k) gq[k] += R(2) * gqq * f.q[k];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        gou[k] += gq[k];
+        gou_r[k] += gq[k];
         gts += gq[k] * f.du[k];
         gdu[k] += f.ts * gq[k];
     }
     // ts = -p inv_n ; p = o_u . du ; inv_n = 1/n ; n = du . du
-    const float gp = -gts * f.inv_n;
+    const R gp = -gts * f.inv_n;
     ginv_n += -gts * f.p;
-    const float gn = -ginv_n * f.inv_n * f.inv_n;
+    const R gn = -ginv_n * f.inv_n * f.inv_n;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        gou[k] += gp * f.du[k];
-        gdu[k] += gp * ou[k] + 2.0f * gn * f.du[k];
+        gou_r[k] += gp * f.du[k];
+        gdu[k] += gp * ou[k] + R(2) * gn * f.du[k];
     }
     // du = W d, g_x = W dx, g_y = W dy
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
+    for (int a = 0; a < 3; ++a) {
+        gou[a] += (float)gou_r[a];
 #pragma unroll
         for (int b = 0; b < 3; ++b)
-            gW[3 * a + b] += gdu[a] * px.d[b] + (FILTER ? ggx[a] * px.dx[b] + ggy[a] * px.dy[b] : 0.0f);
-    return gsig;
+            gW[3 * a + b] += (float)(gdu[a] * R(px.d[b]) + (FILTER ? ggx[a] * R(px.dx[b]) + ggy[a] * R(px.dy[b]) : R(0)));
+    }
+    return (float)gsig;
+}
+
+// Adjoint of a flat Gaussian's pair, recomputed and differentiated in FP64
+// and added to its gradient record (out of line, like flat_response).
+// colw = (0, w dL/dC) carries the colour gradient w_k dL/dC of the pair.
+template <bool FILTER>
+__device__ __noinline__ void flat_pair_adjoint(const float4 r0, const float4 r1, const float4 r2, const float sig,
+                                               const float4 r7, const bool additive, const PixelRays px,
+                                               const float gT, const float4 colw, float4 *dst) {
+    const GaussRec<double> g64 = rec_f64(r0, r1, r2, sig, r7);
+    PairFwdT<double> f64;
+    float T64;
+    pair_response<FILTER, true, double>(g64, additive, px, T64, &f64);
+    float gW[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, gou[3] = {0.f, 0.f, 0.f};
+    const float gsig = pair_adjoint<FILTER, double>(f64, g64, px, gT, gW, gou);
+    atomicAdd(dst, make_float4(gW[0], gW[1], gW[2], gW[3]));
+    atomicAdd(dst + 1, make_float4(gW[4], gW[5], gW[6], gW[7]));
+    atomicAdd(dst + 2, make_float4(gW[8], gou[0], gou[1], gou[2]));
+    atomicAdd(dst + 3, make_float4(gsig, colw.y, colw.z, colw.w));
 }
 
 // One CTA per tile (FIRST: a tile's whole list, or the first segment of a split
@@ -278,11 +302,21 @@ __global__ void __launch_bounds__(TILE_PX, 12) raster_bwd_kernel(const RasterArg
             if (mask == 0ull) continue;
             const int b = 63 - __clzll((long long)mask);
             mask &= ~(1ull << b);
+            // the same response as the forward (FP64 for a flat Gaussian), so the
+            // same pairs pass the alpha and stop tests
+            const float4 r7 = s_rec[7][b];
+            const bool flat = rec_is_flat(r7);
             PairFwd f;
             float Tresp = 0.f;
-            if (!pair_response<FILTER, true>(s_rec[0][b], s_rec[1][b], s_rec[2][b], s_rec[3][b].w, s_rec[7][b].x,
-                                             a.additive != 0, px, Tresp, &f))
-                continue;
+            if (!flat) {
+                if (!pair_response<FILTER, true>(rec_f32(s_rec[0][b], s_rec[1][b], s_rec[2][b], s_rec[3][b].w, r7.x),
+                                                 a.additive != 0, px, Tresp, &f))
+                    continue;
+            } else {
+                Tresp = flat_response<FILTER>(s_rec[0][b], s_rec[1][b], s_rec[2][b], s_rec[3][b].w, r7,
+                                              a.additive != 0, px);
+                if (Tresp < 0.0f) continue;
+            }
             const float alpha = fminf(ALPHA_MAX, Tresp);
             if (alpha < ALPHA_MIN) continue;
             const float4 r3 = s_rec[3][b];
@@ -292,13 +326,18 @@ __global__ void __launch_bounds__(TILE_PX, 12) raster_bwd_kernel(const RasterArg
             const float SG = S[0] * GC[0] + S[1] * GC[1] + S[2] * GC[2];
             const float galpha = Tb * cG - (SG + GT * Tfin) / one_m;
             const float w = alpha * Tb;
-            float gW[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, gou[3] = {0.f, 0.f, 0.f};
             S[0] += r3.x * w; S[1] += r3.y * w; S[2] += r3.z * w;
             T = Tb;
             const float gT = Tresp < ALPHA_MAX ? galpha : 0.0f;
-            const float gsig = pair_adjoint<FILTER>(f, s_rec[0][b], s_rec[1][b], s_rec[2][b], r3.w, s_rec[7][b].x,
-                                                    px, gT, gW, gou);
             float4 *dst = reinterpret_cast<float4 *>(g_rec + 16 * (size_t)s_gid[b]);   // 64-byte aligned
+            if (flat) {
+                flat_pair_adjoint<FILTER>(s_rec[0][b], s_rec[1][b], s_rec[2][b], r3.w, r7, a.additive != 0, px, gT,
+                                          make_float4(0.f, w * GC[0], w * GC[1], w * GC[2]), dst);
+                continue;
+            }
+            float gW[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, gou[3] = {0.f, 0.f, 0.f};
+            const float gsig = pair_adjoint<FILTER>(f, rec_f32(s_rec[0][b], s_rec[1][b], s_rec[2][b], r3.w, r7.x), px,
+                                                    gT, gW, gou);
             atomicAdd(dst, make_float4(gW[0], gW[1], gW[2], gW[3]));
             atomicAdd(dst + 1, make_float4(gW[4], gW[5], gW[6], gW[7]));
             atomicAdd(dst + 2, make_float4(gW[8], gou[0], gou[1], gou[2]));

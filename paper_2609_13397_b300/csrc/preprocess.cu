@@ -9,8 +9,10 @@
 // The raster record is 8 float4 per Gaussian:
 //   [W row 0 | o_u.x] [W row 1 | o_u.y] [W row 2 | o_u.z] [rgb | sigma_eff]
 //   [u | g0] [g1, g2, C00, C11] [C22, 2 C01, 2 C02, 2 C12] [rho^2, 0, 0, 0]
+// (a flat Gaussian has [-rho^2, lo(o_u)] as its last word: see pair.cuh)
 // where (u, g, C) define the pixel pre-test: with e = d - u, a pixel ray d
 // with -1 + g.e + e^T C e > 0 cannot reach alpha >= 1/255 with this Gaussian.
+#include "pair.cuh"
 #include "rule.cuh"
 #include "sh.cuh"
 
@@ -216,6 +218,27 @@ __global__ void __launch_bounds__(256) view_records_kernel(CamParams c, ScenePar
             cone_quadric(W, ou, 1.01f * k2, tb * tb * m * 1.001f, L, g, C);
         }
     }
+    // flat Gaussian (s_eff,max / s_eff,min > FLAT_RATIO): the response is taken in
+    // FP64 from o_u = hi + lo, formed here in FP64 from the FP32 W, o and mu; the
+    // record marks it by the sign bit of its rho^2 word
+    float4 r7 = make_float4(rho2, 0.f, 0.f, 0.f);
+    {
+        const float lmax = fmaxf(fmaxf(sp.log_scales[3 * i], sp.log_scales[3 * i + 1]), sp.log_scales[3 * i + 2]);
+        const float lmin = fminf(fminf(sp.log_scales[3 * i], sp.log_scales[3 * i + 1]), sp.log_scales[3 * i + 2]);
+        const float s2max = expf(2.0f * lmax) + rho2, s2min = expf(2.0f * lmin) + rho2;
+        if (s2max > FLAT_RATIO * FLAT_RATIO * s2min) {
+            const double v0 = (double)c.o[0] - (double)mu[0], v1 = (double)c.o[1] - (double)mu[1],
+                         v2 = (double)c.o[2] - (double)mu[2];
+            float lo[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const double o64 = (double)W[3 * a] * v0 + (double)W[3 * a + 1] * v1 + (double)W[3 * a + 2] * v2;
+                ou[a] = (float)o64;
+                lo[a] = (float)(o64 - (double)ou[a]);
+            }
+            r7 = make_float4(-rho2, lo[0], lo[1], lo[2]);
+        }
+    }
     float4 *r = rec + (size_t)REC_F4 * i;
     r[0] = make_float4(W[0], W[1], W[2], ou[0]);
     r[1] = make_float4(W[3], W[4], W[5], ou[1]);
@@ -224,7 +247,7 @@ __global__ void __launch_bounds__(256) view_records_kernel(CamParams c, ScenePar
     r[4] = make_float4(pu[0], pu[1], pu[2], g[0]);
     r[5] = make_float4(g[1], g[2], C[0], C[1]);
     r[6] = make_float4(C[2], C[3], C[4], C[5]);
-    r[7] = make_float4(rho2, 0.f, 0.f, 0.f);
+    r[7] = r7;
 }
 
 cudaError_t launch_scene_cache(const SceneParams &sp, float *W, float *sig_eff, cudaStream_t s) {

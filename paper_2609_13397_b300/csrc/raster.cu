@@ -85,7 +85,7 @@ template <bool FILTER>
 __device__ __forceinline__ void walk_entries(const RasterArgs &a, float4 (*s_rec)[TILE_PX], uint32_t b0, uint32_t b1,
                                              uint32_t base, bool live, const PixelRays &px, float &C0, float &C1,
                                              float &C2, float &Tacc, uint32_t &last, bool &stopped,
-                                             uint32_t &walked, uint32_t &full) {
+                                             uint32_t &walked, uint32_t &full, uint32_t &nflat) {
     bool done = !live;
     for (uint32_t start = b0; start < b1; start += TILE_PX) {
         if (__syncthreads_count(done) == TILE_PX) break;
@@ -119,9 +119,10 @@ __device__ __forceinline__ void walk_entries(const RasterArgs &a, float4 (*s_rec
                 mask &= mask - 1ull;
                 ++full;
                 const float4 r3 = s_rec[3][b];
+                nflat += rec_is_flat(s_rec[7][b]) ? 1u : 0u;
                 float T;
-                if (pair_response<FILTER>(s_rec[0][b], s_rec[1][b], s_rec[2][b], r3.w, s_rec[7][b].x,
-                                          a.additive != 0, px, T)) {
+                if (record_response<FILTER>(s_rec[0][b], s_rec[1][b], s_rec[2][b], r3.w, s_rec[7][b],
+                                            a.additive != 0, px, T)) {
                     const float alpha = fminf(ALPHA_MAX, T);
                     if (!(alpha < ALPHA_MIN)) {
                         const float test = Tacc * (1.0f - alpha);
@@ -145,16 +146,18 @@ __device__ __forceinline__ void walk_entries(const RasterArgs &a, float4 (*s_rec
     }
 }
 
-__device__ __forceinline__ void count_walk(const RasterArgs &a, uint32_t walked, uint32_t full) {
+__device__ __forceinline__ void count_walk(const RasterArgs &a, uint32_t walked, uint32_t full, uint32_t nflat) {
     if (!a.evaluated) return;
-    unsigned long long wk = walked, f = full;
+    unsigned long long wk = walked, f = full, fl = nflat;
     for (int o = 16; o > 0; o >>= 1) {
         wk += __shfl_xor_sync(0xffffffffu, wk, o);
         f += __shfl_xor_sync(0xffffffffu, f, o);
+        fl += __shfl_xor_sync(0xffffffffu, fl, o);
     }
     if ((threadIdx.x & 31) == 0) {
         atomicAdd(a.evaluated, wk);
         atomicAdd(a.evaluated + 1, f);
+        if (fl) atomicAdd(a.evaluated + 2, fl);
     }
 }
 
@@ -170,7 +173,7 @@ __device__ __forceinline__ void write_pixel(const RasterArgs &a, int64_t pix, in
 
 // Pass A.  FIRST: one CTA per tile for its first segment; else one per later segment.
 template <bool FILTER, bool FIRST>
-__global__ void __launch_bounds__(TILE_PX) raster_seg_kernel(const RasterArgs a, const SegArgs g) {
+__global__ void __launch_bounds__(TILE_PX, 16) raster_seg_kernel(const RasterArgs a, const SegArgs g) {
     __shared__ float4 s_rec[REC_F4][TILE_PX];
     uint2 tw;
     if (FIRST) {
@@ -201,10 +204,10 @@ __global__ void __launch_bounds__(TILE_PX) raster_seg_kernel(const RasterArgs a,
     const uint32_t b0 = range.x + tw.y * seg;
     const uint32_t b1 = nseg == 1 ? range.y : min(range.y, b0 + seg);
     float C0 = 0.f, C1 = 0.f, C2 = 0.f, Tacc = 1.0f;
-    uint32_t last = 0, walked = 0, full = 0;
+    uint32_t last = 0, walked = 0, full = 0, nflat = 0;
     bool stopped = false;
-    walk_entries<FILTER>(a, s_rec, b0, b1, b0, live, px, C0, C1, C2, Tacc, last, stopped, walked, full);
-    count_walk(a, walked, full);
+    walk_entries<FILTER>(a, s_rec, b0, b1, b0, live, px, C0, C1, C2, Tacc, last, stopped, walked, full, nflat);
+    count_walk(a, walked, full, nflat);
     if (nseg == 1) {                       // the whole list: final result
         if (inside) write_pixel(a, pix, P, C0, C1, C2, Tacc, last);
         return;
@@ -276,7 +279,7 @@ __global__ void __launch_bounds__(TILE_PX) raster_merge_kernel(const RasterArgs 
 // whose walk stops in it, from their T_in, and writes their final result; the
 // segment's share of C and the final T replace its pass-A entry.
 template <bool FILTER>
-__global__ void __launch_bounds__(TILE_PX) raster_replay_kernel(const RasterArgs a, const SegArgs g, int ntiles) {
+__global__ void __launch_bounds__(TILE_PX, 16) raster_replay_kernel(const RasterArgs a, const SegArgs g, int ntiles) {
     __shared__ float4 s_rec[REC_F4][TILE_PX];
     uint2 tw;
     if ((int)blockIdx.x < ntiles) {
@@ -299,7 +302,7 @@ __global__ void __launch_bounds__(TILE_PX) raster_replay_kernel(const RasterArgs
     const bool mine = g.rp_need[q] == tw.y;
     float4 cin = make_float4(0.f, 0.f, 0.f, 1.0f);
     float C0 = 0.f, C1 = 0.f, C2 = 0.f, T = 1.0f;      // C: this segment's share
-    uint32_t last = 0, walked = 0, full = 0;
+    uint32_t last = 0, walked = 0, full = 0, nflat = 0;
     PixelRays px;
     if (mine) {
         cin = g.rp_c[q];
@@ -311,7 +314,7 @@ __global__ void __launch_bounds__(TILE_PX) raster_replay_kernel(const RasterArgs
     const uint32_t seg = seg_length_dev(g.stat);
     const uint32_t b0 = range.x + tw.y * seg, b1 = min(range.y, b0 + seg);
     bool stopped = false;
-    walk_entries<FILTER>(a, s_rec, b0, b1, range.x, mine, px, C0, C1, C2, T, last, stopped, walked, full);
+    walk_entries<FILTER>(a, s_rec, b0, b1, range.x, mine, px, C0, C1, C2, T, last, stopped, walked, full, nflat);
     if (mine) {
         g.seg_c[(size_t)w * TILE_PX + threadIdx.x] = make_float4(C0, C1, C2, T);
         if (inside) write_pixel(a, pix, P, cin.x + C0, cin.y + C1, cin.z + C2, T, last);

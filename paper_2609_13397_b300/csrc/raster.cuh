@@ -13,7 +13,8 @@ struct RasterArgs {
     const uint8_t *valid;
     float *out_rgb, *out_T, *keep_T;   // keep_T: copy of the final T kept for the adjoint (may be NULL)
     uint32_t *last;        // per pixel: list entries up to and including the last contributor
-    unsigned long long *evaluated;   // optional (profiling): [0] list entries walked, [1] full evaluations
+    unsigned long long *evaluated;   // optional (profiling): [0] list entries walked, [1] full evaluations,
+                                     // [2] of those, flat (FP64) evaluations
     int additive;
     int footprint;         // 0: the pixel's own differentials; 1: isotropic reduction; 2: z/f sizing
     float zax[3];          // z/f: optical axis (world); zf_scale = 1 / (2 f_x)

@@ -211,6 +211,66 @@ def blob_scene(n: int = 500_000, seed: int = 0, cam: Optional[Camera] = None, n_
                  logits.astype(np.float32), sh.astype(np.float32), sh_degree, np.zeros(n, np.float32))
 
 
+def _quat_from_matrix(R: np.ndarray) -> np.ndarray:
+    """(w, x, y, z) of rotation matrices R [n,3,3] (columns: the local axes in world)."""
+    n = R.shape[0]
+    q = np.zeros((n, 4))
+    tr = R[:, 0, 0] + R[:, 1, 1] + R[:, 2, 2]
+    for i in range(n):
+        m = R[i]
+        if tr[i] > 0:
+            s = 2.0 * math.sqrt(1.0 + tr[i])
+            q[i] = (0.25 * s, (m[2, 1] - m[1, 2]) / s, (m[0, 2] - m[2, 0]) / s, (m[1, 0] - m[0, 1]) / s)
+        else:
+            k = int(np.argmax([m[0, 0], m[1, 1], m[2, 2]]))
+            a, b = (k + 1) % 3, (k + 2) % 3
+            s = 2.0 * math.sqrt(1.0 + m[k, k] - m[a, a] - m[b, b])
+            v = np.zeros(3)
+            v[k] = 0.25 * s
+            v[a] = (m[a, k] + m[k, a]) / s
+            v[b] = (m[b, k] + m[k, b]) / s
+            q[i] = ((m[b, a] - m[a, b]) / s, *v)
+    return q
+
+
+def flat_scene(n: int, seed: int = 0, ratio: float = 1e3, tilt_deg=(0.0, 30.0), cam: Optional[Camera] = None,
+               fov_deg: float = 80.0, depth=(2.0, 6.0), log_scale_mean: float = -2.6, sh_degree: int = 1) -> Scene:
+    """Near-degenerate flat Gaussians (disks): two scales exp(N(log_scale_mean, 0.3)), the
+    third smaller than the larger of them by ``ratio`` x U(1.02, 1.3); the thin axis is
+    tilted by U(tilt_deg) from the direction of the optical centre (0: seen face-on;
+    near 90: edge-on, at a grazing angle).  Means: directions within ``fov_deg`` of the
+    camera's optical axis, distance U(depth).  Opacity logit N(1, 0.5)."""
+    rng = np.random.default_rng(seed)
+    cam = cam if cam is not None else pinhole(96, 72, 90.0)
+    Rc = cam.cam_to_world[:, :3].astype(np.float64)
+    o = cam.cam_to_world[:, 3].astype(np.float64)
+    ct = rng.uniform(math.cos(math.radians(fov_deg)), 1.0, n)
+    ph = rng.uniform(0.0, 2.0 * math.pi, n)
+    st = np.sqrt(1.0 - ct * ct)
+    dirs = np.stack([st * np.cos(ph), st * np.sin(ph), ct], 1) @ Rc.T
+    means = o + dirs * rng.uniform(depth[0], depth[1], n)[:, None]
+    tilt = np.radians(rng.uniform(tilt_deg[0], tilt_deg[1], n))
+    perp = np.cross(dirs, rng.standard_normal((n, 3)))
+    perp /= np.linalg.norm(perp, axis=1, keepdims=True)
+    thin = np.cos(tilt)[:, None] * dirs + np.sin(tilt)[:, None] * perp
+    e1 = np.cross(thin, rng.standard_normal((n, 3)))
+    e1 /= np.linalg.norm(e1, axis=1, keepdims=True)
+    e2 = np.cross(thin, e1)
+    R = np.stack([e1, e2, thin], 2)
+    big = rng.normal(log_scale_mean, 0.3, (n, 2))
+    small = big.max(1) - np.log(ratio * rng.uniform(1.02, 1.3, n))
+    log_scales = np.concatenate([big, small[:, None]], 1)
+    quats = _quat_from_matrix(R)
+    logits = rng.normal(1.0, 0.5, n)
+    k = (sh_degree + 1) ** 2
+    sh = np.zeros((n, k, 3))
+    sh[:, 0, :] = (rng.uniform(0, 1, (n, 3)) - 0.5) / SH_C0
+    if k > 1:
+        sh[:, 1:, :] = rng.normal(0, 0.3, (n, k - 1, 3))
+    return Scene(means.astype(np.float32), log_scales.astype(np.float32), quats.astype(np.float32),
+                 logits.astype(np.float32), sh.astype(np.float32), sh_degree, np.zeros(n, np.float32))
+
+
 def perturbed(scene: Scene, seed: int = 1) -> Scene:
     """The C3 target scene: mu + N(0,0.01), log s + N(0,0.05), DC + N(0,0.05), logit + N(0,0.1)."""
     rng = np.random.default_rng(seed)

@@ -1,7 +1,8 @@
 """GPU adjoint (conegs_render_backward) vs the FP64 gradient oracle (oracle/grad.py,
-itself pinned to finite differences of the C oracle).  Loss L = sum w_rgb . rgb +
-w_T . T with seeded weights; pixels the oracle flags as near a compositing
-threshold get zero weight (the render is not differentiable there)."""
+itself pinned to finite differences of the C oracle), entry by entry.  Loss
+L = sum w_rgb . rgb + w_T . T with seeded weights; pixels the oracle flags as
+near a compositing threshold get zero weight (the render is not
+differentiable there)."""
 import dataclasses
 
 import numpy as np
@@ -12,7 +13,23 @@ import synthetic as S
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-REL = 2e-3     # relative error of each gradient group (FP32 adjoint vs FP64 oracle)
+# element-wise bound of the FP32 adjoint against the FP64 gradient oracle:
+# |g - g_ref| <= ABS * max|g_ref| + REL * |g_ref| on every entry of every group
+REL = 2e-3
+ABS = 1e-5
+
+
+def assert_grads_close(got: dict, want: dict, names=(("means", "means"), ("log_scales", "log_scales"),
+                                                     ("quats", "quats"), ("opacity_logits", "logits"),
+                                                     ("sh", "sh")), rel=REL, abs_=ABS):
+    for gk, ok in names:
+        g = np.asarray(got[gk], np.float64).reshape(want[ok].shape)
+        w = want[ok]
+        bound = abs_ * np.abs(w).max() + rel * np.abs(w)
+        excess = np.abs(g - w) - bound
+        worst = int(np.argmax(excess))
+        assert excess.max() <= 0.0, (gk, worst, float(g.reshape(-1)[worst]), float(w.reshape(-1)[worst]),
+                                     float(np.abs(w).max()))
 
 
 @pytest.fixture(scope="module")
@@ -35,6 +52,9 @@ def _case(name):
         sc = S.uniform_box_scene(150, seed=6, log_scale_mean=-3.0, log_scale_std=0.6, sh_degree=3)
         import oracle
         sc = sc.with_rho2(oracle.floor_rho2([S.pinhole(80, 60, 72.0)], sc.means).astype(np.float32))
+    elif name == "flat":               # near-degenerate disks (s_max/s_min ~ 10^3), adjoint in FP64
+        cam = S.pinhole(40, 30, 36.0)
+        sc = S.flat_scene(150, seed=8, ratio=1e3, tilt_deg=(0.0, 89.0), cam=cam, fov_deg=25.0)
     else:                              # fisheye
         cam = S.c3_camera(48, 48)
         sc = S.uniform_box_scene(150, seed=5, log_scale_mean=-2.4, log_scale_std=0.4, sh_degree=1)
@@ -42,7 +62,7 @@ def _case(name):
 
 
 @pytest.mark.parametrize("name,mode", [("pinhole", "aniso"), ("floor", "aniso"), ("coarse_floor", "aniso"),
-                                       ("fisheye", "aniso"), ("pinhole", "filter_none"),
+                                       ("fisheye", "aniso"), ("flat", "aniso"), ("pinhole", "filter_none"),
                                        ("coarse_floor", "additive"), ("coarse_floor", "iso"), ("fisheye", "zf")])
 def test_backward_matches_gradient_oracle(cg, oracle_lib, name, mode):
     from oracle import grad as G
@@ -72,13 +92,7 @@ def test_backward_matches_gradient_oracle(cg, oracle_lib, name, mode):
     dL_dT = torch.from_numpy(w_T.reshape(cam.height, cam.width).astype(np.float32)).cuda()
     g = v.render_backward(dL_drgb, dL_dT)
     torch.cuda.synchronize()
-    pairs = [("means", "means"), ("log_scales", "log_scales"), ("quats", "quats"), ("opacity_logits", "logits"),
-             ("sh", "sh")]
-    for gk, ok in pairs:
-        got = g[gk].cpu().numpy().astype(np.float64).reshape(g_ref[ok].shape)
-        want = g_ref[ok]
-        err = np.linalg.norm(got - want) / max(np.linalg.norm(want), 1e-12)
-        assert err < REL, (gk, err)
+    assert_grads_close({k: t.cpu().numpy() for k, t in g.items()}, g_ref)
 
 
 def test_backward_requires_forward_state(cg):
@@ -146,8 +160,60 @@ def test_backward_split_lists_match_gradient_oracle(cg, oracle_lib):
     dL_dT = torch.from_numpy(w_T.reshape(cam.height, cam.width).astype(np.float32)).cuda()
     g = v.render_backward(dL_drgb, dL_dT)
     torch.cuda.synchronize()
-    for gk, ok_ in (("means", "means"), ("log_scales", "log_scales"), ("quats", "quats"),
-                    ("opacity_logits", "logits"), ("sh", "sh")):
-        got = g[gk].cpu().numpy().astype(np.float64).reshape(g_ref[ok_].shape)
-        err = np.linalg.norm(got - g_ref[ok_]) / max(np.linalg.norm(g_ref[ok_]), 1e-12)
-        assert err < REL, (gk, err)
+    assert_grads_close({k: t.cpu().numpy() for k, t in g.items()}, g_ref)
+
+
+def test_backward_full_size_c2_sampled(cg, oracle_lib):
+    """The adjoint on the benchmark workload: the 1280x720 view of the 500k-Gaussian
+    blob scene with SH degree 3 and the Eq. 11 floor, a loss on 300 sampled pixels.
+    The gradient oracle runs per pixel on the Gaussians that contribute there (the
+    others have no gradient through that pixel), and the sums are compared entry by
+    entry with the GPU adjoint, which walks the full tile lists."""
+    from oracle import grad as G
+    cam = S.c2_cameras()[0]
+    sc = S.c2_scene()
+    ctx = cg.Context(0)
+    ctx.set_scene_from(sc)
+    v = ctx.view()
+    v.set_camera_from(cam)
+    rho2 = ctx.compute_floor([v])
+    ctx.set_scene_from(sc, rho2=rho2)
+    sc = sc.with_rho2(rho2.cpu().numpy())
+    rng = np.random.default_rng(31)
+    pix = rng.choice(cam.n_pixels, size=300, replace=False).astype(np.int32)
+    MAXU = 512
+    ref = oracle_lib.render(cam, sc, pix=pix, eps=2e-4, max_used=MAXU)
+    keep = (ref.flags == 0) & (ref.ncontrib < MAXU) & (ref.ncontrib > 0)
+    assert keep.sum() > 200
+    w_rgb = rng.normal(size=(pix.size, 3)) * keep[:, None]
+    w_T = rng.normal(size=pix.size) * keep
+
+    dL_drgb = torch.zeros(3, cam.n_pixels, dtype=torch.float32)
+    dL_T = torch.zeros(cam.n_pixels, dtype=torch.float32)
+    dL_drgb[:, torch.from_numpy(pix).long()] = torch.from_numpy(w_rgb.T.astype(np.float32))
+    dL_T[torch.from_numpy(pix).long()] = torch.from_numpy(w_T.astype(np.float32))
+    rgb, T = v.render(flags=cg.KEEP_FOR_BACKWARD)
+    g = v.render_backward(dL_drgb.reshape(3, cam.height, cam.width).cuda(), dL_T.reshape(cam.height, cam.width).cuda())
+    torch.cuda.synchronize()
+    got = {k: t.cpu().numpy().astype(np.float64) for k, t in g.items()}
+
+    want = {"means": np.zeros((sc.n, 3)), "log_scales": np.zeros((sc.n, 3)), "quats": np.zeros((sc.n, 4)),
+            "logits": np.zeros(sc.n), "sh": np.zeros(sc.sh.shape)}
+    for t in np.nonzero(keep)[0]:
+        ids = np.sort(ref.used[t][ref.used[t] >= 0])
+        _, gp = G.loss_and_grad(cam, sc.subset(ids), pix[t:t + 1], w_rgb[t:t + 1], w_T[t:t + 1])
+        for k in want:
+            want[k][ids] += gp[k]
+    touched = np.zeros(sc.n, bool)
+    for t in np.nonzero(keep)[0]:
+        touched[ref.used[t][ref.used[t] >= 0]] = True
+    assert touched.sum() > 1000
+    sub = {k: a[touched] for k, a in want.items()}
+    assert_grads_close({"means": got["means"].reshape(-1, 3)[touched],
+                        "log_scales": got["log_scales"].reshape(-1, 3)[touched],
+                        "quats": got["quats"].reshape(-1, 4)[touched],
+                        "opacity_logits": got["opacity_logits"].reshape(-1)[touched],
+                        "sh": got["sh"].reshape(sc.sh.shape)[touched]}, sub)
+    # Gaussians that contribute to no kept pixel get no gradient
+    scale = max(np.abs(want["means"]).max(), 1e-12)
+    assert np.abs(got["means"].reshape(-1, 3)[~touched]).max() <= ABS * scale
