@@ -19,7 +19,8 @@
  *   marginal  Sigma_render = W [W^-1 Sigma_fp W^-T - rho^2 I]_+ W^T  (Eq. 12)
  *             (literal 3x3 form: Jacobi eigen-decomposition, clamp, re-whiten)
  *   response  T = sigma_eff det(A)^-1/2 exp(-q^T A^-1 q / 2),
- *             A = I + Sigma_render  (3x3 LU)                (Eq. 9)
+ *             A = I + Sigma_render, symmetric, A >= I: det A and
+ *             q^T A^-1 q from its eigen-decomposition      (Eq. 9)
  *   blend     c = sum_k c_k a_k prod_{j<k}(1-a_j), sorted by depth (Eq. 4)
  *   floor rho^2 = min_v tr(Sigma_fp^(v))/2 at the Gaussian-centre pixel (Eq. 11)
  *
@@ -352,38 +353,6 @@ static void jacobi3(const double *Ain, double lam[3], double V[9]) {
     lam[0] = A[0]; lam[1] = A[4]; lam[2] = A[8];
 }
 
-/* det(A) and x = A^-1 b via LU with partial pivoting. */
-static double lu_solve3(const double *Ain, const double *b, double *x) {
-    double A[9], r[3];
-    memcpy(A, Ain, sizeof(A));
-    memcpy(r, b, sizeof(r));
-    double det = 1.0;
-    for (int c = 0; c < 3; ++c) {
-        int piv = c;
-        for (int i = c + 1; i < 3; ++i)
-            if (fabs(A[3 * i + c]) > fabs(A[3 * piv + c])) piv = i;
-        if (piv != c) {
-            for (int j = 0; j < 3; ++j) {
-                double t = A[3 * c + j]; A[3 * c + j] = A[3 * piv + j]; A[3 * piv + j] = t;
-            }
-            double t = r[c]; r[c] = r[piv]; r[piv] = t;
-            det = -det;
-        }
-        det *= A[3 * c + c];
-        for (int i = c + 1; i < 3; ++i) {
-            double f = A[3 * i + c] / A[3 * c + c];
-            for (int j = c; j < 3; ++j) A[3 * i + j] -= f * A[3 * c + j];
-            r[i] -= f * r[c];
-        }
-    }
-    for (int i = 2; i >= 0; --i) {
-        double s = r[i];
-        for (int j = i + 1; j < 3; ++j) s -= A[3 * i + j] * x[j];
-        x[i] = s / A[3 * i + i];
-    }
-    return det;
-}
-
 /* ------------------------------------------------------------------ one pair */
 
 enum { FILTER_NONE = 0, FILTER_ANISO = 1, FILTER_ISO = 2, FILTER_ZF = 3 };
@@ -476,10 +445,24 @@ static int pair_response(const ogauss *g, const double o[3], const double d[3], 
         } else {
             memcpy(Sr, Sfp, sizeof(Sr));
         }
-        double A[9], xs[3];
-        for (int i = 0; i < 9; ++i) A[i] = Sr[i] + ((i % 4 == 0) ? 1.0 : 0.0);
-        detA = lu_solve3(A, q, xs);
-        Qf = dot3(q, xs);
+        /* Eq. 9: A = I + Sigma_render is symmetric with A >= I (Sigma_render is
+         * PSD by the clamp of Eq. 12), so det A and q^T A^-1 q are taken from its
+         * eigen-decomposition: det A = prod(1 + mu_i), q^T A^-1 q =
+         * sum (v_i . q)^2 / (1 + mu_i), mu_i >= 0 the eigenvalues of Sigma_render.
+         * (An LU of A loses its small pivots when Sigma_render is nearly rank one
+         * and huge, as for a flat Gaussian whose whitened footprint reaches 1e10.) */
+        double Ss[9], mu[3], V[9];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) Ss[3 * i + j] = 0.5 * (Sr[3 * i + j] + Sr[3 * j + i]);
+        jacobi3(Ss, mu, V);
+        detA = 1.0;
+        Qf = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            const double a = 1.0 + (mu[k] > 0 ? mu[k] : 0.0);
+            const double vq = V[k] * q[0] + V[3 + k] * q[1] + V[6 + k] * q[2];
+            detA *= a;
+            Qf += vq * vq / a;
+        }
     }
     *T = g->sig_eff / sqrt(detA) * exp(-0.5 * Qf);   /* Eq. 9 (C = 1) */
     if (detail) {
