@@ -117,9 +117,11 @@ typedef struct {
     float ms_raster;         /* tile rasteriser */
     float ms_total;          /* whole render on the device */
     float ms_raster_main;    /* of ms_raster: the launch that walks every tile's first list segment */
-    int64_t n_evaluated_flat; /* (profiled) of n_evaluated: pairs of near-degenerate flat Gaussians
-                                 (effective scale ratio s_max/s_min above 100, Eq. 10), whose
-                                 response and adjoint are evaluated in FP64 */
+    int64_t n_evaluated_flat; /* (profiled) of n_evaluated: pairs of near-degenerate flat Gaussians,
+                                 evaluated in FP64 (see n_flat) */
+    int64_t n_flat;          /* visible near-degenerate flat Gaussians of the last render (effective
+                                scale ratio s_max/s_min above 100, Eq. 10): their response and adjoint
+                                are evaluated in FP64; a view with none runs the FP32-only kernels */
 } conegs_stats;
 
 /* Create a context on CUDA device `device` (its scene and views live there).

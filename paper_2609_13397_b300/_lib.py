@@ -24,7 +24,7 @@ class Stats(ctypes.Structure):
                 ("tiles_y", ctypes.c_int32), ("n_valid_pixels", ctypes.c_int64), ("device_bytes", ctypes.c_size_t),
                 ("n_launches", ctypes.c_int64), ("n_walked", ctypes.c_int64), ("n_evaluated", ctypes.c_int64), ("ms_preprocess", ctypes.c_float), ("ms_sort", ctypes.c_float),
                 ("ms_raster", ctypes.c_float), ("ms_total", ctypes.c_float), ("ms_raster_main", ctypes.c_float),
-                ("n_evaluated_flat", ctypes.c_int64)]
+                ("n_evaluated_flat", ctypes.c_int64), ("n_flat", ctypes.c_int64)]
 
 
 class ConegsError(RuntimeError):

@@ -36,7 +36,7 @@ cudaError_t launch_bin_emit(const CamParams &c, const float *binrec, const float
 cudaError_t launch_scene_cache(const SceneParams &sp, float *W, float *sig_eff, cudaStream_t s);
 cudaError_t launch_view_records(const CamParams &c, const SceneParams &sp, const float *mcam, float mzf,
                                 int fov_cull, float4 *rec, float4 *gview, float2 *gcone, uint8_t *gflag,
-                                float4 *gell, cudaStream_t s);
+                                float4 *gell, unsigned long long *nflat, cudaStream_t s);
 int64_t scan_scratch_words(int64_t n);
 cudaError_t exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *scratch, int pred,
                            cudaStream_t s);
@@ -52,6 +52,9 @@ cudaError_t launch_floor(const CamParams *cams_dev, int nv, const float *means, 
                          cudaStream_t s);
 cudaError_t launch_raster_split(const RasterArgs &a, int ntiles, bool filter, uint32_t *scratch,
                                 uint32_t *scan_scratch, cudaStream_t s, cudaEvent_t main0, cudaEvent_t main1);
+cudaError_t launch_mark_flat_tiles(const uint32_t *order, const uint32_t *offsets, const uint32_t *counts, int64_t m,
+                                   const float4 *rec, const uint32_t *pair_tile, uint8_t *tclass, int ntiles,
+                                   cudaStream_t s);
 cudaError_t launch_backward(const RasterArgs &a, int ntiles, bool filter, uint32_t *split_scratch,
                             const float *dL_drgb, const float *dL_dT, const float *final_T, float *g_rec,
                             cudaStream_t s);
@@ -148,9 +151,9 @@ struct conegs_view {
     // per-render scratch
     DevBuf rec, gview, gcone, gflag, gell, counts, vispos, scan_scr, dkeys, dvals, dkeys_alt, dvals_alt, sorted_counts, offsets;
     DevBuf pair_tile, pair_gid, pair_tile_alt, pair_gid_alt, ranges, last, sums, rs_scr, tmp_rgb, tmp_T;
-    DevBuf g_rec, keep_T, split;
+    DevBuf g_rec, keep_T, split, tclass;
     unsigned long long *h_sums = nullptr;   // pinned
-    int64_t n_visible = 0, n_pairs = 0, n_valid = 0, n_launches = 0;
+    int64_t n_visible = 0, n_pairs = 0, n_valid = 0, n_launches = 0, n_flat = 0;
     bool has_forward = false;
     unsigned last_flags = 0;
     uint64_t forward_gen = 0;
@@ -351,7 +354,7 @@ conegs_status conegs_view_create(conegs_ctx *ctx, conegs_view **out) {
     v->ctx = ctx;
     cudaError_t e = cudaEventCreateWithFlags(&v->done, cudaEventDisableTiming);
     for (int k = 0; k < 6 && e == cudaSuccess; ++k) e = cudaEventCreate(&v->prof[k]);
-    if (e == cudaSuccess) e = cudaMallocHost(&v->h_sums, 5 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMallocHost(&v->h_sums, 8 * sizeof(unsigned long long));
     if (e != cudaSuccess) {
         if (v->done) cudaEventDestroy(v->done);
         delete v;
@@ -377,7 +380,7 @@ void conegs_view_destroy(conegs_view *v) {
                       &v->counts, &v->vispos, &v->scan_scr, &v->dkeys, &v->dvals, &v->dkeys_alt, &v->dvals_alt,
                       &v->sorted_counts, &v->offsets, &v->pair_tile, &v->pair_gid, &v->pair_tile_alt,
                       &v->pair_gid_alt, &v->ranges, &v->last, &v->sums, &v->rs_scr, &v->tmp_rgb, &v->tmp_T,
-                      &v->g_rec, &v->keep_T, &v->split};
+                      &v->g_rec, &v->keep_T, &v->split, &v->tclass};
     for (DevBuf *b : bufs) release(ctx, *b);
     if (v->h_sums) cudaFreeHost(v->h_sums);
     for (int k = 0; k < 6; ++k)
@@ -509,7 +512,7 @@ static conegs_status render_front(conegs_view *v, unsigned flags, cudaStream_t s
     TRY(ensure(ctx, v->counts, sizeof(uint32_t) * nn, s));
     TRY(ensure(ctx, v->vispos, sizeof(uint32_t) * nn, s));
     TRY(ensure(ctx, v->scan_scr, sizeof(uint32_t) * (size_t)scan_scratch_words((int64_t)nn), s));
-    TRY(ensure(ctx, v->sums, 3 * sizeof(unsigned long long), s));
+    TRY(ensure(ctx, v->sums, 4 * sizeof(unsigned long long), s));
     // optional: without room (or over the memory budget) the emit pass evaluates the rule again
     if (v->list_want > 0 && ensure(ctx, v->binlist, sizeof(uint32_t) * (size_t)v->list_want, s) != CONEGS_OK)
         v->list_want = 0;
@@ -520,10 +523,12 @@ static conegs_status render_front(conegs_view *v, unsigned flags, cudaStream_t s
         CUDA_TRY(cudaMemsetAsync(v->evaluated.p, 0, 3 * sizeof(unsigned long long), s));
         CUDA_TRY(cudaEventRecord(v->prof[0], s));
     }
+    // sums: [0] pairs, [1] visible Gaussians, [2] kept-tile list entries wanted, [3] flat Gaussians
+    CUDA_TRY(cudaMemsetAsync(v->sums.as<unsigned long long>() + 2, 0, 2 * sizeof(unsigned long long), s));
     CUDA_TRY(launch_view_records(c, sp, v->mcam.as<float>(), zf_bound(c, flags), (flags & CONEGS_BIN_UT) ? 0 : 1,
                                  v->rec.as<float4>(), v->gview.as<float4>(),
-                                 v->gcone.as<float2>(), v->gflag.as<uint8_t>(), v->gell.as<float4>(), s));
-    CUDA_TRY(cudaMemsetAsync(v->sums.as<unsigned long long>() + 2, 0, sizeof(unsigned long long), s));
+                                 v->gcone.as<float2>(), v->gflag.as<uint8_t>(), v->gell.as<float4>(),
+                                 v->sums.as<unsigned long long>() + 3, s));
     {
         const bool ut = (flags & CONEGS_BIN_UT) != 0;
         const unsigned long long cap = std::min<unsigned long long>(v->binlist.bytes / sizeof(uint32_t), 0xffffffffull);
@@ -537,7 +542,7 @@ static conegs_status render_front(conegs_view *v, unsigned flags, cudaStream_t s
     CUDA_TRY(sum_counts(v->counts.as<uint32_t>(), n, v->sums.as<unsigned long long>(), s));
     CUDA_TRY(exclusive_scan(v->counts.as<uint32_t>(), v->vispos.as<uint32_t>(), n, v->scan_scr.as<uint32_t>(), 1, s));
     if (prof) CUDA_TRY(cudaEventRecord(v->prof[1], s));
-    CUDA_TRY(cudaMemcpyAsync(v->h_sums, v->sums.p, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(v->h_sums, v->sums.p, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     return CONEGS_OK;
 }
 
@@ -551,6 +556,7 @@ static conegs_status render_back(conegs_view *v, float *out_rgb, float *out_T, u
     const bool prof = (flags & CONEGS_PROFILE) != 0;
     const uint64_t total = v->h_sums[0];
     const int64_t M = (int64_t)v->h_sums[1];
+    const int64_t nflat = (int64_t)v->h_sums[3];
     // room the count pass wanted for kept tile lists: grown (with headroom) before the next render
     if (v->h_sums[2] > v->binlist.bytes / sizeof(uint32_t))
         v->list_want = std::min<uint64_t>(v->h_sums[2] + v->h_sums[2] / 4, 1ull << 28);
@@ -583,6 +589,12 @@ static conegs_status render_back(conegs_view *v, float *out_rgb, float *out_T, u
                              v->dvals.as<uint32_t>(), v->offsets.as<uint32_t>(), v->bincache.as<uint4>(),
                              v->binlist.as<uint32_t>(), v->pair_tile.as<uint32_t>(), v->pair_gid.as<uint32_t>(),
                              v->gell.as<float4>(), (flags & CONEGS_BIN_UT) != 0, s));
+    if (nflat > 0) {
+        TRY(ensure(ctx, v->tclass, (size_t)std::max(nt, 1), s));
+        CUDA_TRY(launch_mark_flat_tiles(v->dvals.as<uint32_t>(), v->offsets.as<uint32_t>(),
+                                        v->sorted_counts.as<uint32_t>(), M, v->rec.as<float4>(),
+                                        v->pair_tile.as<uint32_t>(), v->tclass.as<uint8_t>(), nt, s));
+    }
     CUDA_TRY(radix_sort_pairs(v->pair_tile.as<uint32_t>(), v->pair_gid.as<uint32_t>(), v->pair_tile_alt.as<uint32_t>(),
                               v->pair_gid_alt.as<uint32_t>(), Pn, 0, bits_for(nt), v->rs_scr.as<uint32_t>(), s));
     CUDA_TRY(launch_ranges(v->pair_tile.as<uint32_t>(), Pn, v->ranges.as<uint2>(), nt, s));
@@ -602,6 +614,7 @@ static conegs_status render_back(conegs_view *v, float *out_rgb, float *out_T, u
     a.out_T = out_T;
     a.last = v->last.as<uint32_t>();
     a.additive = (flags & CONEGS_COMP_ADDITIVE) ? 1 : 0;
+    a.tclass = nflat > 0 ? v->tclass.as<uint8_t>() : nullptr;
     set_footprint(a, c, flags);
     if (flags & CONEGS_KEEP_FOR_BACKWARD) {
         TRY(ensure(ctx, v->keep_T, sizeof(float) * (size_t)std::max<int64_t>(P, 1), s));
@@ -615,13 +628,14 @@ static conegs_status render_back(conegs_view *v, float *out_rgb, float *out_T, u
                                  prof ? v->prof[4] : nullptr, prof ? v->prof[5] : nullptr));
     if (prof) {
         CUDA_TRY(cudaEventRecord(v->prof[3], s));
-        CUDA_TRY(cudaMemcpyAsync(v->h_sums + 2, v->evaluated.p, 3 * sizeof(unsigned long long),
+        CUDA_TRY(cudaMemcpyAsync(v->h_sums + 4, v->evaluated.p, 3 * sizeof(unsigned long long),
                                  cudaMemcpyDeviceToHost, s));
     }
     v->profiled = prof;
     v->n_launches = launches_so_far() - v->launches0;
     v->n_visible = M;
     v->n_pairs = Pn;
+    v->n_flat = nflat;
     v->last_flags = flags;
     v->has_forward = true;
     v->forward_gen = ctx->scene_gen;
@@ -780,6 +794,7 @@ conegs_status conegs_render_backward(conegs_view *v, const float *dL_drgb, const
     a.valid = v->valid.as<uint8_t>();
     a.last = v->last.as<uint32_t>();
     a.additive = (v->last_flags & CONEGS_COMP_ADDITIVE) ? 1 : 0;
+    a.tclass = v->n_flat > 0 ? v->tclass.as<uint8_t>() : nullptr;
     set_footprint(a, c, v->last_flags);
     CUDA_TRY(launch_backward(a, nt, !(v->last_flags & CONEGS_FILTER_NONE), v->split.as<uint32_t>(), dL_drgb, dL_dT,
                              v->keep_T.as<float>(), v->g_rec.as<float>(), s));
@@ -793,6 +808,7 @@ conegs_status conegs_get_stats(const conegs_view *v, conegs_stats *out) {
     memset(out, 0, sizeof(*out));
     out->n_gaussians = v->ctx->has_scene ? v->ctx->sp.n : 0;
     out->n_visible = v->n_visible;
+    out->n_flat = v->n_flat;
     out->n_pairs = v->n_pairs;
     out->width = v->cam.W;
     out->height = v->cam.H;
@@ -804,7 +820,7 @@ conegs_status conegs_get_stats(const conegs_view *v, conegs_stats *out) {
                             &v->counts, &v->vispos, &v->scan_scr, &v->dkeys, &v->dvals, &v->dkeys_alt, &v->dvals_alt,
                             &v->sorted_counts, &v->offsets, &v->pair_tile, &v->pair_gid, &v->pair_tile_alt,
                             &v->pair_gid_alt, &v->ranges, &v->last, &v->sums, &v->rs_scr, &v->tmp_rgb, &v->tmp_T,
-                            &v->g_rec, &v->keep_T, &v->split};
+                            &v->g_rec, &v->keep_T, &v->split, &v->tclass};
     size_t tot = 0;
     for (const DevBuf *b : bufs) tot += b->bytes;
     out->device_bytes = tot;
@@ -823,9 +839,9 @@ conegs_status conegs_get_stats(const conegs_view *v, conegs_stats *out) {
         float t45 = 0;
         CUDA_TRY(cudaEventElapsedTime(&t45, v->prof[4], v->prof[5]));
         out->ms_raster_main = t45;
-        out->n_walked = (int64_t)v->h_sums[2];
-        out->n_evaluated = (int64_t)v->h_sums[3];
-        out->n_evaluated_flat = (int64_t)v->h_sums[4];
+        out->n_walked = (int64_t)v->h_sums[4];
+        out->n_evaluated = (int64_t)v->h_sums[5];
+        out->n_evaluated_flat = (int64_t)v->h_sums[6];
     }
     return CONEGS_OK;
 }

@@ -187,32 +187,13 @@ __device__ __forceinline__ float pair_adjoint(const PairFwdT<R> &f, const GaussR
     return (float)gsig;
 }
 
-// Adjoint of a flat Gaussian's pair, recomputed and differentiated in FP64
-// and added to its gradient record (out of line, like flat_response).
-// colw = (0, w dL/dC) carries the colour gradient w_k dL/dC of the pair.
-template <bool FILTER>
-__device__ __noinline__ void flat_pair_adjoint(const float4 r0, const float4 r1, const float4 r2, const float sig,
-                                               const float4 r7, const bool additive, const PixelRays px,
-                                               const float gT, const float4 colw, float4 *dst) {
-    const GaussRec<double> g64 = rec_f64(r0, r1, r2, sig, r7);
-    PairFwdT<double> f64;
-    float T64;
-    pair_response<FILTER, true, double>(g64, additive, px, T64, &f64);
-    float gW[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, gou[3] = {0.f, 0.f, 0.f};
-    const float gsig = pair_adjoint<FILTER, double>(f64, g64, px, gT, gW, gou);
-    atomicAdd(dst, make_float4(gW[0], gW[1], gW[2], gW[3]));
-    atomicAdd(dst + 1, make_float4(gW[4], gW[5], gW[6], gW[7]));
-    atomicAdd(dst + 2, make_float4(gW[8], gou[0], gou[1], gou[2]));
-    atomicAdd(dst + 3, make_float4(gsig, colw.y, colw.z, colw.w));
-}
-
 // One CTA per tile (FIRST: a tile's whole list, or the first segment of a split
 // list) or per later segment of a split list.  A segment is walked back to
 // front from the state the forward's suffix pass left: T after the segment and
 // the colour composited behind it; pixels whose walk ended before the segment
 // sit out.
-template <bool FILTER, bool FIRST>
-__global__ void __launch_bounds__(TILE_PX, 12) raster_bwd_kernel(const RasterArgs a, const SegArgs g,
+template <bool FILTER, bool FIRST, bool FLAT>
+__global__ void __launch_bounds__(TILE_PX, FLAT ? 1 : 12) raster_bwd_kernel(const RasterArgs a, const SegArgs g,
                                                              const float *__restrict__ dL_drgb,
                                                              const float *__restrict__ dL_dT,
                                                              const float *__restrict__ final_T,
@@ -228,6 +209,7 @@ __global__ void __launch_bounds__(TILE_PX, 12) raster_bwd_kernel(const RasterArg
         tw = g.work[blockIdx.x];
     }
     const int tile = (int)tw.x;
+    if (!tile_in_class<FLAT>(a, tile)) return;
     const uint32_t nseg = g.nseg[tile];
     const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
     const int i = tx * TILE + (threadIdx.x % TILE), j = ty * TILE + (threadIdx.x / TILE);
@@ -305,17 +287,19 @@ __global__ void __launch_bounds__(TILE_PX, 12) raster_bwd_kernel(const RasterArg
             // the same response as the forward (FP64 for a flat Gaussian), so the
             // same pairs pass the alpha and stop tests
             const float4 r7 = s_rec[7][b];
-            const bool flat = rec_is_flat(r7);
+            const bool flat = FLAT && rec_is_flat(r7);
             PairFwd f;
+            PairFwdT<double> f64;
             float Tresp = 0.f;
             if (!flat) {
                 if (!pair_response<FILTER, true>(rec_f32(s_rec[0][b], s_rec[1][b], s_rec[2][b], s_rec[3][b].w, r7.x),
                                                  a.additive != 0, px, Tresp, &f))
                     continue;
             } else {
-                Tresp = flat_response<FILTER>(s_rec[0][b], s_rec[1][b], s_rec[2][b], s_rec[3][b].w, r7,
-                                              a.additive != 0, px);
-                if (Tresp < 0.0f) continue;
+                if (!pair_response<FILTER, true, double>(rec_f64(s_rec[0][b], s_rec[1][b], s_rec[2][b],
+                                                                 s_rec[3][b].w, r7),
+                                                         a.additive != 0, px, Tresp, &f64))
+                    continue;
             }
             const float alpha = fminf(ALPHA_MAX, Tresp);
             if (alpha < ALPHA_MIN) continue;
@@ -326,24 +310,35 @@ __global__ void __launch_bounds__(TILE_PX, 12) raster_bwd_kernel(const RasterArg
             const float SG = S[0] * GC[0] + S[1] * GC[1] + S[2] * GC[2];
             const float galpha = Tb * cG - (SG + GT * Tfin) / one_m;
             const float w = alpha * Tb;
+            float gW[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, gou[3] = {0.f, 0.f, 0.f};
             S[0] += r3.x * w; S[1] += r3.y * w; S[2] += r3.z * w;
             T = Tb;
             const float gT = Tresp < ALPHA_MAX ? galpha : 0.0f;
+            const float gsig =
+                flat ? pair_adjoint<FILTER, double>(f64, rec_f64(s_rec[0][b], s_rec[1][b], s_rec[2][b], r3.w, r7), px,
+                                                    gT, gW, gou)
+                     : pair_adjoint<FILTER>(f, rec_f32(s_rec[0][b], s_rec[1][b], s_rec[2][b], r3.w, r7.x), px, gT,
+                                            gW, gou);
             float4 *dst = reinterpret_cast<float4 *>(g_rec + 16 * (size_t)s_gid[b]);   // 64-byte aligned
-            if (flat) {
-                flat_pair_adjoint<FILTER>(s_rec[0][b], s_rec[1][b], s_rec[2][b], r3.w, r7, a.additive != 0, px, gT,
-                                          make_float4(0.f, w * GC[0], w * GC[1], w * GC[2]), dst);
-                continue;
-            }
-            float gW[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, gou[3] = {0.f, 0.f, 0.f};
-            const float gsig = pair_adjoint<FILTER>(f, rec_f32(s_rec[0][b], s_rec[1][b], s_rec[2][b], r3.w, r7.x), px,
-                                                    gT, gW, gou);
             atomicAdd(dst, make_float4(gW[0], gW[1], gW[2], gW[3]));
             atomicAdd(dst + 1, make_float4(gW[4], gW[5], gW[6], gW[7]));
             atomicAdd(dst + 2, make_float4(gW[8], gou[0], gou[1], gou[2]));
             atomicAdd(dst + 3, make_float4(gsig, w * GC[0], w * GC[1], w * GC[2]));
         }
         end = start;
+    }
+}
+
+template <bool FILTER>
+static void launch_bwd_passes(const RasterArgs &a, const SegArgs &g, int ntiles, unsigned later, const float *dL_drgb,
+                              const float *dL_dT, const float *final_T, float *g_rec, cudaStream_t s) {
+    raster_bwd_kernel<FILTER, true, false><<<ntiles, TILE_PX, 0, s>>>(a, g, dL_drgb, dL_dT, final_T, g_rec);
+    raster_bwd_kernel<FILTER, false, false><<<later, TILE_PX, 0, s>>>(a, g, dL_drgb, dL_dT, final_T, g_rec);
+    note_launches(2);
+    if (a.tclass) {          // tiles holding a flat Gaussian: the FP64-capable variant
+        raster_bwd_kernel<FILTER, true, true><<<ntiles, TILE_PX, 0, s>>>(a, g, dL_drgb, dL_dT, final_T, g_rec);
+        raster_bwd_kernel<FILTER, false, true><<<later, TILE_PX, 0, s>>>(a, g, dL_drgb, dL_dT, final_T, g_rec);
+        note_launches(2);
     }
 }
 
@@ -354,14 +349,10 @@ cudaError_t launch_backward(const RasterArgs &a, int ntiles, bool filter, uint32
     int64_t items = 0;
     const SegArgs g = split_args(split_scratch, ntiles, &items);
     const unsigned later = (unsigned)(items - ntiles);
-    if (filter) {
-        raster_bwd_kernel<true, true><<<ntiles, TILE_PX, 0, s>>>(a, g, dL_drgb, dL_dT, final_T, g_rec);
-        raster_bwd_kernel<true, false><<<later, TILE_PX, 0, s>>>(a, g, dL_drgb, dL_dT, final_T, g_rec);
-    } else {
-        raster_bwd_kernel<false, true><<<ntiles, TILE_PX, 0, s>>>(a, g, dL_drgb, dL_dT, final_T, g_rec);
-        raster_bwd_kernel<false, false><<<later, TILE_PX, 0, s>>>(a, g, dL_drgb, dL_dT, final_T, g_rec);
-    }
-    note_launches(2);
+    if (filter)
+        launch_bwd_passes<true>(a, g, ntiles, later, dL_drgb, dL_dT, final_T, g_rec, s);
+    else
+        launch_bwd_passes<false>(a, g, ntiles, later, dL_drgb, dL_dT, final_T, g_rec, s);
     return cudaGetLastError();
 }
 

@@ -55,7 +55,7 @@ def test_flat_gaussians_match_oracle(cg, oracle_lib, kind, ratio, pose):
     r = oracle_lib.render(cam, sc, eps=EPS_FLAG)
     ok = r.flags == 0
     assert ok.mean() > 0.95
-    assert (r.ncontrib > 0).mean() > 0.2                    # the disks cover the image
+    assert (r.ncontrib > 0).mean() > (0.2 if kind == "pinhole" else 0.08)   # the disks cover the image
     err = np.abs(rgb - r.rgb)[ok].max()
     errT = np.abs(T - r.T)[ok].max()
     assert err <= TOL and errT <= TOL, (err, errT)
