@@ -36,11 +36,12 @@ cudaError_t launch_bin_emit(const CamParams &c, const float *binrec, const float
 cudaError_t launch_scene_cache(const SceneParams &sp, float *W, float *sig_eff, cudaStream_t s);
 cudaError_t launch_view_records(const CamParams &c, const SceneParams &sp, const float *mcam, float mzf,
                                 int fov_cull, float4 *rec, float4 *gview, float2 *gcone, uint8_t *gflag,
-                                float4 *gell, unsigned long long *nflat, cudaStream_t s);
+                                float4 *gell, unsigned long long *nflat, uint8_t *gflat, cudaStream_t s);
 int64_t scan_scratch_words(int64_t n);
 cudaError_t exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *scratch, int pred,
                            cudaStream_t s);
-cudaError_t sum_counts(const uint32_t *in, int64_t n, unsigned long long *d_two, cudaStream_t s);
+cudaError_t sum_counts(const uint32_t *in, int64_t n, unsigned long long *d_two, const uint8_t *flag,
+                       unsigned long long *d_flagged, cudaStream_t s);
 cudaError_t launch_compact(const uint32_t *counts, const uint32_t *pos, int64_t n, const float4 *gview,
                            uint32_t *keys, uint32_t *vals, cudaStream_t s);
 cudaError_t launch_gather(const uint32_t *src, const uint32_t *idx, int64_t n, uint32_t *dst, cudaStream_t s);
@@ -52,9 +53,9 @@ cudaError_t launch_floor(const CamParams *cams_dev, int nv, const float *means, 
                          cudaStream_t s);
 cudaError_t launch_raster_split(const RasterArgs &a, int ntiles, bool filter, uint32_t *scratch,
                                 uint32_t *scan_scratch, cudaStream_t s, cudaEvent_t main0, cudaEvent_t main1);
-cudaError_t launch_mark_flat_tiles(const uint32_t *order, const uint32_t *offsets, const uint32_t *counts, int64_t m,
-                                   const float4 *rec, const uint32_t *pair_tile, uint8_t *tclass, int ntiles,
-                                   cudaStream_t s);
+cudaError_t launch_flat_pairs(const RasterArgs &a, const uint32_t *tiles, int64_t npairs, const uint8_t *gflat,
+                              uint32_t *slot_of, uint32_t *slot_pair, unsigned long long *counter, int64_t nslots,
+                              float *flat_T, float *flat_G, bool filter, cudaStream_t s);
 cudaError_t launch_backward(const RasterArgs &a, int ntiles, bool filter, uint32_t *split_scratch,
                             const float *dL_drgb, const float *dL_dT, const float *final_T, float *g_rec,
                             cudaStream_t s);
@@ -151,7 +152,8 @@ struct conegs_view {
     // per-render scratch
     DevBuf rec, gview, gcone, gflag, gell, counts, vispos, scan_scr, dkeys, dvals, dkeys_alt, dvals_alt, sorted_counts, offsets;
     DevBuf pair_tile, pair_gid, pair_tile_alt, pair_gid_alt, ranges, last, sums, rs_scr, tmp_rgb, tmp_T;
-    DevBuf g_rec, keep_T, split, tclass;
+    DevBuf g_rec, keep_T, split, gflat, flat_slot, flat_pair, flat_T, flat_G;
+    int64_t n_flat_pairs = 0;
     unsigned long long *h_sums = nullptr;   // pinned
     int64_t n_visible = 0, n_pairs = 0, n_valid = 0, n_launches = 0, n_flat = 0;
     bool has_forward = false;
@@ -380,7 +382,8 @@ void conegs_view_destroy(conegs_view *v) {
                       &v->counts, &v->vispos, &v->scan_scr, &v->dkeys, &v->dvals, &v->dkeys_alt, &v->dvals_alt,
                       &v->sorted_counts, &v->offsets, &v->pair_tile, &v->pair_gid, &v->pair_tile_alt,
                       &v->pair_gid_alt, &v->ranges, &v->last, &v->sums, &v->rs_scr, &v->tmp_rgb, &v->tmp_T,
-                      &v->g_rec, &v->keep_T, &v->split, &v->tclass};
+                      &v->g_rec, &v->keep_T, &v->split, &v->gflat, &v->flat_slot, &v->flat_pair, &v->flat_T,
+                      &v->flat_G};
     for (DevBuf *b : bufs) release(ctx, *b);
     if (v->h_sums) cudaFreeHost(v->h_sums);
     for (int k = 0; k < 6; ++k)
@@ -512,7 +515,8 @@ static conegs_status render_front(conegs_view *v, unsigned flags, cudaStream_t s
     TRY(ensure(ctx, v->counts, sizeof(uint32_t) * nn, s));
     TRY(ensure(ctx, v->vispos, sizeof(uint32_t) * nn, s));
     TRY(ensure(ctx, v->scan_scr, sizeof(uint32_t) * (size_t)scan_scratch_words((int64_t)nn), s));
-    TRY(ensure(ctx, v->sums, 4 * sizeof(unsigned long long), s));
+    TRY(ensure(ctx, v->sums, 6 * sizeof(unsigned long long), s));
+    TRY(ensure(ctx, v->gflat, nn, s));
     // optional: without room (or over the memory budget) the emit pass evaluates the rule again
     if (v->list_want > 0 && ensure(ctx, v->binlist, sizeof(uint32_t) * (size_t)v->list_want, s) != CONEGS_OK)
         v->list_want = 0;
@@ -523,12 +527,13 @@ static conegs_status render_front(conegs_view *v, unsigned flags, cudaStream_t s
         CUDA_TRY(cudaMemsetAsync(v->evaluated.p, 0, 3 * sizeof(unsigned long long), s));
         CUDA_TRY(cudaEventRecord(v->prof[0], s));
     }
-    // sums: [0] pairs, [1] visible Gaussians, [2] kept-tile list entries wanted, [3] flat Gaussians
+    // sums: [0] pairs, [1] visible Gaussians, [2] kept-tile list entries wanted, [3] flat Gaussians,
+    // [4] pairs of flat Gaussians, [5] scratch (flat slot counter)
     CUDA_TRY(cudaMemsetAsync(v->sums.as<unsigned long long>() + 2, 0, 2 * sizeof(unsigned long long), s));
     CUDA_TRY(launch_view_records(c, sp, v->mcam.as<float>(), zf_bound(c, flags), (flags & CONEGS_BIN_UT) ? 0 : 1,
                                  v->rec.as<float4>(), v->gview.as<float4>(),
                                  v->gcone.as<float2>(), v->gflag.as<uint8_t>(), v->gell.as<float4>(),
-                                 v->sums.as<unsigned long long>() + 3, s));
+                                 v->sums.as<unsigned long long>() + 3, v->gflat.as<uint8_t>(), s));
     {
         const bool ut = (flags & CONEGS_BIN_UT) != 0;
         const unsigned long long cap = std::min<unsigned long long>(v->binlist.bytes / sizeof(uint32_t), 0xffffffffull);
@@ -539,10 +544,11 @@ static conegs_status render_front(conegs_view *v, unsigned flags, cudaStream_t s
                                   v->gell.as<float4>(), ut ? sp.means : nullptr, ut ? sp.W : nullptr,
                                   ut ? sp.sig_eff : nullptr, s));
     }
-    CUDA_TRY(sum_counts(v->counts.as<uint32_t>(), n, v->sums.as<unsigned long long>(), s));
+    CUDA_TRY(sum_counts(v->counts.as<uint32_t>(), n, v->sums.as<unsigned long long>(), v->gflat.as<uint8_t>(),
+                        v->sums.as<unsigned long long>() + 4, s));
     CUDA_TRY(exclusive_scan(v->counts.as<uint32_t>(), v->vispos.as<uint32_t>(), n, v->scan_scr.as<uint32_t>(), 1, s));
     if (prof) CUDA_TRY(cudaEventRecord(v->prof[1], s));
-    CUDA_TRY(cudaMemcpyAsync(v->h_sums, v->sums.p, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(v->h_sums, v->sums.p, 5 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     return CONEGS_OK;
 }
 
@@ -557,6 +563,7 @@ static conegs_status render_back(conegs_view *v, float *out_rgb, float *out_T, u
     const uint64_t total = v->h_sums[0];
     const int64_t M = (int64_t)v->h_sums[1];
     const int64_t nflat = (int64_t)v->h_sums[3];
+    const int64_t nflat_pairs = (int64_t)v->h_sums[4];
     // room the count pass wanted for kept tile lists: grown (with headroom) before the next render
     if (v->h_sums[2] > v->binlist.bytes / sizeof(uint32_t))
         v->list_want = std::min<uint64_t>(v->h_sums[2] + v->h_sums[2] / 4, 1ull << 28);
@@ -589,12 +596,6 @@ static conegs_status render_back(conegs_view *v, float *out_rgb, float *out_T, u
                              v->dvals.as<uint32_t>(), v->offsets.as<uint32_t>(), v->bincache.as<uint4>(),
                              v->binlist.as<uint32_t>(), v->pair_tile.as<uint32_t>(), v->pair_gid.as<uint32_t>(),
                              v->gell.as<float4>(), (flags & CONEGS_BIN_UT) != 0, s));
-    if (nflat > 0) {
-        TRY(ensure(ctx, v->tclass, (size_t)std::max(nt, 1), s));
-        CUDA_TRY(launch_mark_flat_tiles(v->dvals.as<uint32_t>(), v->offsets.as<uint32_t>(),
-                                        v->sorted_counts.as<uint32_t>(), M, v->rec.as<float4>(),
-                                        v->pair_tile.as<uint32_t>(), v->tclass.as<uint8_t>(), nt, s));
-    }
     CUDA_TRY(radix_sort_pairs(v->pair_tile.as<uint32_t>(), v->pair_gid.as<uint32_t>(), v->pair_tile_alt.as<uint32_t>(),
                               v->pair_gid_alt.as<uint32_t>(), Pn, 0, bits_for(nt), v->rs_scr.as<uint32_t>(), s));
     CUDA_TRY(launch_ranges(v->pair_tile.as<uint32_t>(), Pn, v->ranges.as<uint2>(), nt, s));
@@ -614,8 +615,23 @@ static conegs_status render_back(conegs_view *v, float *out_rgb, float *out_T, u
     a.out_T = out_T;
     a.last = v->last.as<uint32_t>();
     a.additive = (flags & CONEGS_COMP_ADDITIVE) ? 1 : 0;
-    a.tclass = nflat > 0 ? v->tclass.as<uint8_t>() : nullptr;
     set_footprint(a, c, flags);
+    if (nflat_pairs > 0) {
+        // the pairs of flat Gaussians: responses (and their derivatives, for the adjoint) in FP64
+        const bool adj = (flags & CONEGS_KEEP_FOR_BACKWARD) != 0;
+        const size_t F = (size_t)nflat_pairs;
+        TRY(ensure(ctx, v->flat_slot, sizeof(uint32_t) * pp, s));
+        TRY(ensure(ctx, v->flat_pair, sizeof(uint32_t) * F, s));
+        TRY(ensure(ctx, v->flat_T, sizeof(float) * TILE_PX * F, s));
+        if (adj) TRY(ensure(ctx, v->flat_G, sizeof(float) * 13 * TILE_PX * F, s));
+        CUDA_TRY(launch_flat_pairs(a, v->pair_tile.as<uint32_t>(), Pn, v->gflat.as<uint8_t>(),
+                                   v->flat_slot.as<uint32_t>(), v->flat_pair.as<uint32_t>(),
+                                   v->sums.as<unsigned long long>() + 5, nflat_pairs, v->flat_T.as<float>(),
+                                   adj ? v->flat_G.as<float>() : nullptr, !(flags & CONEGS_FILTER_NONE), s));
+        a.flat_slot = v->flat_slot.as<uint32_t>();
+        a.flat_T = v->flat_T.as<float>();
+        a.flat_G = adj ? v->flat_G.as<float>() : nullptr;
+    }
     if (flags & CONEGS_KEEP_FOR_BACKWARD) {
         TRY(ensure(ctx, v->keep_T, sizeof(float) * (size_t)std::max<int64_t>(P, 1), s));
         a.keep_T = v->keep_T.as<float>();
@@ -628,7 +644,7 @@ static conegs_status render_back(conegs_view *v, float *out_rgb, float *out_T, u
                                  prof ? v->prof[4] : nullptr, prof ? v->prof[5] : nullptr));
     if (prof) {
         CUDA_TRY(cudaEventRecord(v->prof[3], s));
-        CUDA_TRY(cudaMemcpyAsync(v->h_sums + 4, v->evaluated.p, 3 * sizeof(unsigned long long),
+        CUDA_TRY(cudaMemcpyAsync(v->h_sums + 5, v->evaluated.p, 3 * sizeof(unsigned long long),
                                  cudaMemcpyDeviceToHost, s));
     }
     v->profiled = prof;
@@ -636,6 +652,7 @@ static conegs_status render_back(conegs_view *v, float *out_rgb, float *out_T, u
     v->n_visible = M;
     v->n_pairs = Pn;
     v->n_flat = nflat;
+    v->n_flat_pairs = nflat_pairs;
     v->last_flags = flags;
     v->has_forward = true;
     v->forward_gen = ctx->scene_gen;
@@ -794,7 +811,11 @@ conegs_status conegs_render_backward(conegs_view *v, const float *dL_drgb, const
     a.valid = v->valid.as<uint8_t>();
     a.last = v->last.as<uint32_t>();
     a.additive = (v->last_flags & CONEGS_COMP_ADDITIVE) ? 1 : 0;
-    a.tclass = v->n_flat > 0 ? v->tclass.as<uint8_t>() : nullptr;
+    if (v->n_flat_pairs > 0) {
+        a.flat_slot = v->flat_slot.as<uint32_t>();
+        a.flat_T = v->flat_T.as<float>();
+        a.flat_G = v->flat_G.as<float>();
+    }
     set_footprint(a, c, v->last_flags);
     CUDA_TRY(launch_backward(a, nt, !(v->last_flags & CONEGS_FILTER_NONE), v->split.as<uint32_t>(), dL_drgb, dL_dT,
                              v->keep_T.as<float>(), v->g_rec.as<float>(), s));
@@ -820,7 +841,8 @@ conegs_status conegs_get_stats(const conegs_view *v, conegs_stats *out) {
                             &v->counts, &v->vispos, &v->scan_scr, &v->dkeys, &v->dvals, &v->dkeys_alt, &v->dvals_alt,
                             &v->sorted_counts, &v->offsets, &v->pair_tile, &v->pair_gid, &v->pair_tile_alt,
                             &v->pair_gid_alt, &v->ranges, &v->last, &v->sums, &v->rs_scr, &v->tmp_rgb, &v->tmp_T,
-                            &v->g_rec, &v->keep_T, &v->split, &v->tclass};
+                            &v->g_rec, &v->keep_T, &v->split, &v->gflat, &v->flat_slot, &v->flat_pair, &v->flat_T,
+                      &v->flat_G};
     size_t tot = 0;
     for (const DevBuf *b : bufs) tot += b->bytes;
     out->device_bytes = tot;
@@ -839,9 +861,9 @@ conegs_status conegs_get_stats(const conegs_view *v, conegs_stats *out) {
         float t45 = 0;
         CUDA_TRY(cudaEventElapsedTime(&t45, v->prof[4], v->prof[5]));
         out->ms_raster_main = t45;
-        out->n_walked = (int64_t)v->h_sums[4];
-        out->n_evaluated = (int64_t)v->h_sums[5];
-        out->n_evaluated_flat = (int64_t)v->h_sums[6];
+        out->n_walked = (int64_t)v->h_sums[5];
+        out->n_evaluated = (int64_t)v->h_sums[6];
+        out->n_evaluated_flat = (int64_t)v->h_sums[7];
     }
     return CONEGS_OK;
 }

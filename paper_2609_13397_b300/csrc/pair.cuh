@@ -253,16 +253,4 @@ __device__ __forceinline__ bool pair_response(const GaussRec<R> &g, const bool a
     return true;
 }
 
-// The response of a staged record (8 float4 words).  FLAT = false: the view
-// has no flat Gaussian, FP32 only.  FLAT = true: FP32, or FP64 for a record
-// marked flat (that variant needs about twice the registers, so views without
-// flat Gaussians run the FP32-only one).
-template <bool FILTER, bool FLAT>
-__device__ __forceinline__ bool record_response(const float4 r0, const float4 r1, const float4 r2, const float sig,
-                                                const float4 r7, const bool additive, const PixelRays &px,
-                                                float &T) {
-    if (!FLAT || !rec_is_flat(r7)) return pair_response<FILTER>(rec_f32(r0, r1, r2, sig, r7.x), additive, px, T);
-    return pair_response<FILTER, false, double>(rec_f64(r0, r1, r2, sig, r7), additive, px, T);
-}
-
 }  // namespace conegs

@@ -153,9 +153,11 @@ __global__ void __launch_bounds__(256) view_records_kernel(CamParams c, ScenePar
                                                            float2 *__restrict__ gcone,
                                                            uint8_t *__restrict__ gflag,
                                                            float4 *__restrict__ gell,
-                                                           unsigned long long *__restrict__ nflat) {
+                                                           unsigned long long *__restrict__ nflat,
+                                                           uint8_t *__restrict__ gflat) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= sp.n) return;
+    gflat[i] = 0;
     const float mu[3] = {sp.means[3 * i], sp.means[3 * i + 1], sp.means[3 * i + 2]};
     float flag = sp.binrec[BINREC * i + 5], u[3], L;
     rule_gauss_view(c, mu, flag, u, L);
@@ -238,6 +240,7 @@ __global__ void __launch_bounds__(256) view_records_kernel(CamParams c, ScenePar
                 lo[a] = (float)(o64 - (double)ou[a]);
             }
             r7 = make_float4(-rho2, lo[0], lo[1], lo[2]);
+            gflat[i] = 1;
             atomicAdd(nflat, 1ull);
         }
     }
@@ -261,10 +264,10 @@ cudaError_t launch_scene_cache(const SceneParams &sp, float *W, float *sig_eff, 
 
 cudaError_t launch_view_records(const CamParams &c, const SceneParams &sp, const float *mcam, float mzf,
                                 int fov_cull, float4 *rec, float4 *gview, float2 *gcone, uint8_t *gflag,
-                                float4 *gell, unsigned long long *nflat, cudaStream_t s) {
+                                float4 *gell, unsigned long long *nflat, uint8_t *gflat, cudaStream_t s) {
     if (sp.n == 0) return cudaSuccess;
     view_records_kernel<<<(unsigned)div_up(sp.n, 256), 256, 0, s>>>(c, sp, mcam, mzf, fov_cull, rec, gview, gcone,
-                                                                    gflag, gell, nflat);
+                                                                    gflag, gell, nflat, gflat);
     note_launches(1);
     return cudaGetLastError();
 }

@@ -81,7 +81,7 @@ __global__ void seg_map_kernel(const uint32_t *__restrict__ nseg, const uint32_t
 // Walks list entries [b0, b1) for the tile's pixels from (C, Tacc), with the
 // sequential compositing rules.  `live` pixels take part; a pixel leaves at its
 // stop (sets stopped) or at b1.  last is 1-based relative to `base`.
-template <bool FILTER, bool FLAT>
+template <bool FILTER>
 __device__ __forceinline__ void walk_entries(const RasterArgs &a, float4 (*s_rec)[TILE_PX], uint32_t b0, uint32_t b1,
                                              uint32_t base, bool live, const PixelRays &px, float &C0, float &C1,
                                              float &C2, float &Tacc, uint32_t &last, bool &stopped,
@@ -119,10 +119,18 @@ __device__ __forceinline__ void walk_entries(const RasterArgs &a, float4 (*s_rec
                 mask &= mask - 1ull;
                 ++full;
                 const float4 r3 = s_rec[3][b];
-                if (FLAT) nflat += rec_is_flat(s_rec[7][b]) ? 1u : 0u;
+                const float4 r7 = s_rec[7][b];
                 float T;
-                if (record_response<FILTER, FLAT>(s_rec[0][b], s_rec[1][b], s_rec[2][b], r3.w, s_rec[7][b],
-                                                  a.additive != 0, px, T)) {
+                bool hit;
+                if (!rec_is_flat(r7)) {
+                    hit = pair_response<FILTER>(rec_f32(s_rec[0][b], s_rec[1][b], s_rec[2][b], r3.w, r7.x),
+                                                a.additive != 0, px, T);
+                } else {                          // FP64 response, precomputed
+                    ++nflat;
+                    T = a.flat_T[(size_t)a.flat_slot[start + b] * TILE_PX + threadIdx.x];
+                    hit = T >= 0.0f;
+                }
+                if (hit) {
                     const float alpha = fminf(ALPHA_MAX, T);
                     if (!(alpha < ALPHA_MIN)) {
                         const float test = Tacc * (1.0f - alpha);
@@ -172,7 +180,7 @@ __device__ __forceinline__ void write_pixel(const RasterArgs &a, int64_t pix, in
 }
 
 // Pass A.  FIRST: one CTA per tile for its first segment; else one per later segment.
-template <bool FILTER, bool FIRST, bool FLAT>
+template <bool FILTER, bool FIRST>
 __global__ void __launch_bounds__(TILE_PX) raster_seg_kernel(const RasterArgs a, const SegArgs g) {
     __shared__ float4 s_rec[REC_F4][TILE_PX];
     uint2 tw;
@@ -183,7 +191,6 @@ __global__ void __launch_bounds__(TILE_PX) raster_seg_kernel(const RasterArgs a,
         tw = g.work[blockIdx.x];
     }
     const int tile = (int)tw.x;
-    if (!tile_in_class<FLAT>(a, tile)) return;
     const uint32_t nseg = g.nseg[tile];
     const uint32_t w = g.seg_off[tile] + tw.y;
     if (!FIRST) {
@@ -207,8 +214,7 @@ __global__ void __launch_bounds__(TILE_PX) raster_seg_kernel(const RasterArgs a,
     float C0 = 0.f, C1 = 0.f, C2 = 0.f, Tacc = 1.0f;
     uint32_t last = 0, walked = 0, full = 0, nflat = 0;
     bool stopped = false;
-    walk_entries<FILTER, FLAT>(a, s_rec, b0, b1, b0, live, px, C0, C1, C2, Tacc, last, stopped, walked, full,
-                               nflat);
+    walk_entries<FILTER>(a, s_rec, b0, b1, b0, live, px, C0, C1, C2, Tacc, last, stopped, walked, full, nflat);
     count_walk(a, walked, full, nflat);
     if (nseg == 1) {                       // the whole list: final result
         if (inside) write_pixel(a, pix, P, C0, C1, C2, Tacc, last);
@@ -280,7 +286,7 @@ __global__ void __launch_bounds__(TILE_PX) raster_merge_kernel(const RasterArgs 
 // Replay: one CTA per segment item; walks the segment again for the pixels
 // whose walk stops in it, from their T_in, and writes their final result; the
 // segment's share of C and the final T replace its pass-A entry.
-template <bool FILTER, bool FLAT>
+template <bool FILTER>
 __global__ void __launch_bounds__(TILE_PX) raster_replay_kernel(const RasterArgs a, const SegArgs g, int ntiles) {
     __shared__ float4 s_rec[REC_F4][TILE_PX];
     uint2 tw;
@@ -292,7 +298,7 @@ __global__ void __launch_bounds__(TILE_PX) raster_replay_kernel(const RasterArgs
         tw = g.work[k];
     }
     const int tile = (int)tw.x;
-    if (g.nseg[tile] == 1 || !tile_in_class<FLAT>(a, tile)) return;
+    if (g.nseg[tile] == 1) return;
     const uint32_t w = g.seg_off[tile] + tw.y;
     if (g.need_item[w] == 0u) return;
     const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
@@ -316,8 +322,7 @@ __global__ void __launch_bounds__(TILE_PX) raster_replay_kernel(const RasterArgs
     const uint32_t seg = seg_length_dev(g.stat);
     const uint32_t b0 = range.x + tw.y * seg, b1 = min(range.y, b0 + seg);
     bool stopped = false;
-    walk_entries<FILTER, FLAT>(a, s_rec, b0, b1, range.x, mine, px, C0, C1, C2, T, last, stopped, walked, full,
-                               nflat);
+    walk_entries<FILTER>(a, s_rec, b0, b1, range.x, mine, px, C0, C1, C2, T, last, stopped, walked, full, nflat);
     if (mine) {
         g.seg_c[(size_t)w * TILE_PX + threadIdx.x] = make_float4(C0, C1, C2, T);
         if (inside) write_pixel(a, pix, P, cin.x + C0, cin.y + C1, cin.z + C2, T, last);
@@ -398,48 +403,19 @@ SegArgs split_args(uint32_t *scratch, int ntiles, int64_t *items) {
     return g;
 }
 
-// The passes of the split raster; with flat tiles (a.tclass set) each pass runs
-// as two launches, the FP32-only variant and the FP64-capable one.
 template <bool FILTER>
 static void launch_raster_passes(const RasterArgs &a, const SegArgs &g, int ntiles, unsigned later, int64_t wmax,
                                  cudaStream_t s, cudaEvent_t main0, cudaEvent_t main1) {
-    const bool flat = a.tclass != nullptr;
     if (main0) cudaEventRecord(main0, s);
-    raster_seg_kernel<FILTER, true, false><<<ntiles, TILE_PX, 0, s>>>(a, g);
-    if (flat) raster_seg_kernel<FILTER, true, true><<<ntiles, TILE_PX, 0, s>>>(a, g);
+    raster_seg_kernel<FILTER, true><<<ntiles, TILE_PX, 0, s>>>(a, g);
     if (main1) cudaEventRecord(main1, s);
-    raster_seg_kernel<FILTER, false, false><<<later, TILE_PX, 0, s>>>(a, g);
-    if (flat) raster_seg_kernel<FILTER, false, true><<<later, TILE_PX, 0, s>>>(a, g);
+    raster_seg_kernel<FILTER, false><<<later, TILE_PX, 0, s>>>(a, g);
     raster_merge_kernel<<<ntiles, TILE_PX, 0, s>>>(a, g);
-    raster_replay_kernel<FILTER, false><<<(unsigned)wmax, TILE_PX, 0, s>>>(a, g, ntiles);
-    if (flat) raster_replay_kernel<FILTER, true><<<(unsigned)wmax, TILE_PX, 0, s>>>(a, g, ntiles);
-    note_launches(flat ? 7 : 4);
+    raster_replay_kernel<FILTER><<<(unsigned)wmax, TILE_PX, 0, s>>>(a, g, ntiles);
+    note_launches(4);
 }
 
-// Tiles whose list holds a flat Gaussian.  Visible Gaussian `pos` (depth order,
-// id order[pos]) emitted its pairs to [offsets[pos], offsets[pos] + counts[pos])
-// of the tile-unsorted pair list.
-__global__ void mark_flat_tiles_kernel(const uint32_t *__restrict__ order, const uint32_t *__restrict__ offsets,
-                                       const uint32_t *__restrict__ counts, int64_t m, const float4 *__restrict__ rec,
-                                       const uint32_t *__restrict__ pair_tile, uint8_t *__restrict__ tclass) {
-    const int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (pos >= m) return;
-    if (!rec_is_flat(rec[(size_t)REC_F4 * order[pos] + 7])) return;
-    const uint32_t b = offsets[pos], e = b + counts[pos];
-    for (uint32_t k = b; k < e; ++k) tclass[pair_tile[k]] = 1;
-}
-
-cudaError_t launch_mark_flat_tiles(const uint32_t *order, const uint32_t *offsets, const uint32_t *counts, int64_t m,
-                                   const float4 *rec, const uint32_t *pair_tile, uint8_t *tclass, int ntiles,
-                                   cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(tclass, 0, (size_t)ntiles, s);
-    if (e != cudaSuccess || m == 0) return e;
-    mark_flat_tiles_kernel<<<(unsigned)div_up(m, 256), 256, 0, s>>>(order, offsets, counts, m, rec, pair_tile, tclass);
-    note_launches(1);
-    return cudaGetLastError();
-}
-
-// main0/main1 (may be NULL): events recorded around the first-segment launch(es).
+// main0/main1 (may be NULL): events recorded around the first-segment launch.
 cudaError_t launch_raster_split(const RasterArgs &a, int ntiles, bool filter, uint32_t *scratch,
                                 uint32_t *scan_scratch, cudaStream_t s, cudaEvent_t main0, cudaEvent_t main1) {
     if (ntiles == 0) {

@@ -15,7 +15,13 @@ struct RasterArgs {
     uint32_t *last;        // per pixel: list entries up to and including the last contributor
     unsigned long long *evaluated;   // optional (profiling): [0] list entries walked, [1] full evaluations,
                                      // [2] of those, flat (FP64) evaluations
-    const uint8_t *tclass; // per tile: 1 if its list holds a flat Gaussian (FP64 variant); NULL: no flat tile
+    // flat Gaussians (records marked flat, see pair.cuh): their pairs' responses, in
+    // FP64, come from flat_pairs_kernel: list entry k -> slot flat_slot[k], response
+    // flat_T[slot * TILE_PX + pixel in tile] (-1: t* <= T_NEAR, skipped); with the
+    // adjoint state, flat_G[(slot * 13 + j) * TILE_PX + pixel] = dT / d(record j)
+    // (W_eff 9, o_u 3, sigma_eff).  NULL when the view has no flat Gaussian.
+    const uint32_t *flat_slot;
+    const float *flat_T, *flat_G;
     int additive;
     int footprint;         // 0: the pixel's own differentials; 1: isotropic reduction; 2: z/f sizing
     float zax[3];          // z/f: optical axis (world); zf_scale = 1 / (2 f_x)
@@ -72,14 +78,6 @@ __device__ __forceinline__ void load_pixel(const RasterArgs &a, int64_t pix, int
     px.dxdx = dot3(px.dx, px.dx);
     px.dxdy = dot3(px.dx, px.dy);
     px.dydy = dot3(px.dy, px.dy);
-}
-
-// Tiles are split between two kernel variants: FLAT = true (the FP64 response
-// for flat Gaussians, about twice the registers) for tiles whose list holds a
-// flat Gaussian, FLAT = false for the rest.  A CTA of the other class leaves.
-template <bool FLAT>
-__device__ __forceinline__ bool tile_in_class(const RasterArgs &a, int tile) {
-    return a.tclass ? ((a.tclass[tile] != 0) == FLAT) : !FLAT;
 }
 
 // ---------------------------------------------------------------- long-list split (forward and adjoint)

@@ -131,42 +131,53 @@ cudaError_t exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_
 
 // ---------------------------------------------------------------- reductions, compaction, gathers
 
+// Sum and number of non-zero entries of in[n]; with flag (may be NULL), also the
+// sum over the entries whose flag is set.
 __global__ void __launch_bounds__(256) sum_u64_kernel(const uint32_t *__restrict__ in, int64_t n,
                                                       unsigned long long *__restrict__ total,
-                                                      unsigned long long *__restrict__ nonzero) {
-    unsigned long long s = 0, z = 0;
+                                                      unsigned long long *__restrict__ nonzero,
+                                                      const uint8_t *__restrict__ flag,
+                                                      unsigned long long *__restrict__ flagged) {
+    unsigned long long s = 0, z = 0, f = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t v = in[i];
         s += v;
         z += v > 0u;
+        if (flag && flag[i]) f += v;
     }
     for (int o = 16; o > 0; o >>= 1) {
         s += __shfl_xor_sync(0xffffffffu, s, o);
         z += __shfl_xor_sync(0xffffffffu, z, o);
+        f += __shfl_xor_sync(0xffffffffu, f, o);
     }
-    // one pair of atomics per block (per-warp atomics on two addresses serialise)
-    __shared__ unsigned long long ss[8], sz[8];
+    // one set of atomics per block (per-warp atomics on the same addresses serialise)
+    __shared__ unsigned long long ss[8], sz[8], sf[8];
     const int w = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0) {
         ss[w] = s;
         sz[w] = z;
+        sf[w] = f;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
             s += ss[k];
             z += sz[k];
+            f += sf[k];
         }
         atomicAdd(total, s);
         atomicAdd(nonzero, z);
+        if (flag && f) atomicAdd(flagged, f);
     }
 }
 
-cudaError_t sum_counts(const uint32_t *in, int64_t n, unsigned long long *d_two, cudaStream_t s) {
+cudaError_t sum_counts(const uint32_t *in, int64_t n, unsigned long long *d_two, const uint8_t *flag,
+                       unsigned long long *d_flagged, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(d_two, 0, 2 * sizeof(unsigned long long), s);
+    if (e == cudaSuccess && flag) e = cudaMemsetAsync(d_flagged, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess || n == 0) return e;
     int grid = (int)std::min<int64_t>(div_up(n, 256), 148 * 8);
-    sum_u64_kernel<<<grid, 256, 0, s>>>(in, n, d_two, d_two + 1);
+    sum_u64_kernel<<<grid, 256, 0, s>>>(in, n, d_two, d_two + 1, flag, d_flagged);
     note_launches(1);
     return cudaGetLastError();
 }
