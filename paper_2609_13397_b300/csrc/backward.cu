@@ -122,10 +122,10 @@ __global__ void __launch_bounds__(TILE_PX, 12) raster_bwd_kernel(const RasterArg
             if (mask == 0ull) continue;
             const int b = 63 - __clzll((long long)mask);
             mask &= ~(1ull << b);
-            const float4 r7 = s_rec[7][b];
+            const float r7x = s_rec[7][b].x;              // rho^2 (sign bit: flat)
             const float4 r3 = s_rec[3][b];
             float4 *dst = reinterpret_cast<float4 *>(g_rec + 16 * (size_t)s_gid[b]);   // 64-byte aligned
-            if (rec_is_flat(r7)) {
+            if (rec_is_flat(r7x)) {
                 // flat Gaussian: the forward's FP64 response and its derivatives
                 // dT/d(record), precomputed; dL/d(record) = dL/dT dT/d(record)
                 const size_t fs = a.flat_slot[start + b];
@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(TILE_PX, 12) raster_bwd_kernel(const RasterArg
             }
             PairFwd f;
             float Tresp = 0.f;
-            if (!pair_response<FILTER, true>(rec_f32(s_rec[0][b], s_rec[1][b], s_rec[2][b], r3.w, r7.x),
+            if (!pair_response<FILTER, true>(rec_f32(s_rec[0][b], s_rec[1][b], s_rec[2][b], r3.w, r7x),
                                              a.additive != 0, px, Tresp, &f))
                 continue;
             const float alpha = fminf(ALPHA_MAX, Tresp);
@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(TILE_PX, 12) raster_bwd_kernel(const RasterArg
             S[0] += r3.x * w; S[1] += r3.y * w; S[2] += r3.z * w;
             T = Tb;
             const float gT = Tresp < ALPHA_MAX ? galpha : 0.0f;
-            const float gsig = pair_adjoint<FILTER>(f, rec_f32(s_rec[0][b], s_rec[1][b], s_rec[2][b], r3.w, r7.x), px,
+            const float gsig = pair_adjoint<FILTER>(f, rec_f32(s_rec[0][b], s_rec[1][b], s_rec[2][b], r3.w, r7x), px,
                                                     gT, gW, gou);
             atomicAdd(dst, make_float4(gW[0], gW[1], gW[2], gW[3]));
             atomicAdd(dst + 1, make_float4(gW[4], gW[5], gW[6], gW[7]));

@@ -86,7 +86,8 @@ struct GaussRec {
 
 // The flat flag is the sign bit of the record's rho^2 word; a flat record keeps
 // the low-order parts of o_u (o_u = hi + lo in FP64) in the three words after it.
-__device__ __forceinline__ bool rec_is_flat(const float4 r7) { return signbit(r7.x); }
+__device__ __forceinline__ bool rec_is_flat(const float rho2_word) { return signbit(rho2_word); }
+__device__ __forceinline__ bool rec_is_flat(const float4 r7) { return rec_is_flat(r7.x); }
 
 __device__ __forceinline__ GaussRec<float> rec_f32(const float4 r0, const float4 r1, const float4 r2, float sig,
                                                    float rho2) {

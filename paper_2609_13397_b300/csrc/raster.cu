@@ -119,11 +119,11 @@ __device__ __forceinline__ void walk_entries(const RasterArgs &a, float4 (*s_rec
                 mask &= mask - 1ull;
                 ++full;
                 const float4 r3 = s_rec[3][b];
-                const float4 r7 = s_rec[7][b];
+                const float r7x = s_rec[7][b].x;          // rho^2 (sign bit: flat)
                 float T;
                 bool hit;
-                if (!rec_is_flat(r7)) {
-                    hit = pair_response<FILTER>(rec_f32(s_rec[0][b], s_rec[1][b], s_rec[2][b], r3.w, r7.x),
+                if (!rec_is_flat(r7x)) {
+                    hit = pair_response<FILTER>(rec_f32(s_rec[0][b], s_rec[1][b], s_rec[2][b], r3.w, r7x),
                                                 a.additive != 0, px, T);
                 } else {                          // FP64 response, precomputed
                     ++nflat;
