@@ -8,7 +8,7 @@ namespace conegs {
 // arithmetic type R.  Accumulates dL/dW (9, row-major), dL/do_u (3) and
 // returns dL/dsigma_eff.
 template <bool FILTER, typename R>
-__device__ __forceinline__ float pair_adjoint(const PairFwdT<R> &f, const GaussRec<R> &gr, const PixelRays &px,
+__device__ __forceinline__ float pair_adjoint(const PairFwdT<R> &f, const GaussRec<R> &gr, const PixelRaysT<R> &px,
                                               float gT_in, float gW[9], float gou[3]) {
     const R third = R(1) / R(3);
     const R gT = gT_in, sig = gr.sig, rho2 = gr.rho2;
@@ -73,9 +73,9 @@ __device__ __forceinline__ float pair_adjoint(const PairFwdT<R> &f, const GaussR
             } else {                                         // K = sc (H' - l2 I)
                 const R mean = R(0.5) * (h00 + h11), half = R(0.5) * (h00 - h11);
                 const R r2 = half * half + h01 * h01;
-                const R rad = r2 > R(0) ? Ar<R>::sqrt(r2) : R(0);
+                const R rad = r2 > R(0) ? Ops<R>::sqrt(r2) : R(0);
                 const R l1 = mean + rad;
-                const R l2 = Ar<R>::max(dh, R(0)) / l1;
+                const R l2 = Ops<R>::max(dh, R(0)) / l1;
                 const R D = R(3) * l1 * (l1 - l2);
                 const R sc = (l1 - rho2) / D;
                 const R gsc = gk00 * (h00 - l2) + gk11 * (h11 - l2) + gk01 * h01;

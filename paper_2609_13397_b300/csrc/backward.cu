@@ -110,11 +110,8 @@ __global__ void __launch_bounds__(TILE_PX, 12) raster_bwd_kernel(const RasterArg
                 const uint32_t walk = start + b - range.x + 1;     // 1-based walk index of this entry
                 if (walk > last) break;
                 const float4 r4 = s_rec[4][b], r5 = s_rec[5][b], r6 = s_rec[6][b];
-                const float e0 = px.d[0] - r4.x, e1 = px.d[1] - r4.y, e2 = px.d[2] - r4.z;
-                const float qa = r5.z * e0 + r6.y * e1 + r6.z * e2;
-                const float qb = r5.w * e1 + r6.w * e2;
-                const float cone = -1.0f + r4.w * e0 + r5.x * e1 + r5.y * e2 + qa * e0 + qb * e1 + r6.x * e2 * e2;
-                if (!(cone > 1e-3f)) mask |= 1ull << b;
+                if (pretest<float>(r4.x, r4.y, r4.z, r4.w, r5.x, r5.y, r5.z, r5.w, r6.x, r6.y, r6.z, r6.w, px.d))
+                    mask |= 1ull << b;
             }
         }
         // phase 2: lanes walk their own passing entries back to front in lockstep

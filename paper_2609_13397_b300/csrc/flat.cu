@@ -44,8 +44,9 @@ __global__ void __launch_bounds__(TILE_PX) flat_pairs_kernel(const RasterArgs a,
     float T = -1.0f;
     float gW[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, gou[3] = {0.f, 0.f, 0.f}, gsig = 0.f;
     if (i < a.W && j < a.H && a.valid[pix]) {
-        PixelRays px;
-        load_pixel(a, pix, P, px);
+        PixelRays px32;
+        load_pixel(a, pix, P, px32);
+        const PixelRaysT<double> px = widen(px32);
         const GaussRec<double> g = rec_f64(r[0], r[1], r[2], r[3].w, r[7]);
         if (ADJ) {
             PairFwdT<double> f;

@@ -1,15 +1,23 @@
 // Per pixel-Gaussian pair response (Sec. 4.1-4.2) in registers.
 //
-// The arithmetic type R is float for every Gaussian but the near-degenerate
-// flat ones (effective scale ratio above FLAT_RATIO), which take R = double:
-// their whitening W has a row of length 1/s_min, so the whitened camera
-// centre o_u and ray d_u are large, t* and q = o_u + t* d_u cancel, and the
-// final |q|^2 - b^T K (I + GK)^-1 b cancels again.  In FP32 the response of
-// such a disk seen at a grazing angle is off by ~3e-4 at s_max/s_min = 300
-// and by ~2e-3 at 10^4 (face-on); up to 100 it stays within ~5e-5, hence the
-// threshold.  FP32 uses the SFU
-// approximations of reciprocal, square root and exp (about 1-2 ulp), far
-// inside the 1e-4 output tolerance; FP64 uses the correctly rounded ones.
+// One implementation, generic over the arithmetic type V:
+//   float   one pair (the adjoint recomputes the forward's pairs with it);
+//   float2  two pixels against the same Gaussian in packed FP32: every add,
+//           multiply and fused multiply-add issues as one f32x2 instruction of
+//           the Blackwell FMA pipe; reciprocal, square root and exp stay per
+//           element on the SFU.  Element k of every result is bit for bit the
+//           float evaluation of pixel k: the same correctly rounded operations
+//           in the same order, so the forward (packed) and the adjoint (scalar)
+//           take the same compositing decisions;
+//   double  near-degenerate flat Gaussians (effective scale ratio above
+//           FLAT_RATIO): their whitening W has a row of length 1/s_min, so the
+//           whitened camera centre o_u and ray d_u are large, t* and
+//           q = o_u + t* d_u cancel, and the final |q|^2 - b^T K (I + GK)^-1 b
+//           cancels again.  In FP32 the response of such a disk seen at a
+//           grazing angle is off by ~3e-4 at s_max/s_min = 300 and by ~2e-3 at
+//           10^4 (face-on); up to 100 it stays within ~5e-5, hence the threshold.
+// FP32 uses the SFU approximations of reciprocal, square root and exp (about
+// 1-2 ulp), far inside the 1e-4 output tolerance; FP64 the correctly rounded ones.
 //
 // With d_u = W d, g_i = W delta_i (W = W_eff), n = |d_u|^2:
 //   t* = -<o_u, d_u>/n,  q = o_u + t* d_u                          (Eq. 2)
@@ -34,54 +42,150 @@ namespace conegs {
 // (the effective scales of Eq. 10, after the floor).
 constexpr float FLAT_RATIO = 100.0f;
 
-struct PixelRays {
-    float d[3], dx[3], dy[3];
-    float d_dx, d_dy, dxdx, dxdy, dydy;   // for the marginal rule (Eq. 12)
+// ---------------------------------------------------------------- arithmetic per type
+
+struct Bool2 {
+    bool x, y;
 };
 
-// Intermediates of one pair evaluation, kept for the adjoint.
-template <typename R>
-struct PairFwdT {
-    R du[3], gx[3], gy[3], inv_n, p, ts, q[3], qq, cx, cy, ex[3], ey[3];
-    R G00, G01, G11, b0, b1;
-    int kcase;                 // 0: K = I/3; 1: K = (I - rho2 H'^-1)/3; 2: rank-1 K; 3: K = 0
-    R k00, k01, k11;
-    R t2, A00, A01, A11, h00, h01, h11;
-    R m00, m01, m10, m11, det, p00, p01, p10, p11, bPb, inv_det;
-    bool clamped;              // Q = |q|^2/det (lower bound) was active
-    R T;
-};
-using PairFwd = PairFwdT<float>;
+template <typename V>
+struct Ops;
 
-// Elementary operations per arithmetic type.
-template <typename R>
-struct Ar;
 template <>
-struct Ar<float> {
-    static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
-    static __device__ __forceinline__ float rsqrt(float x) { return rsqrtf(x); }
-    static __device__ __forceinline__ float sqrt(float x) { return sqrtf(x); }
-    static __device__ __forceinline__ float exp(float x) { return __expf(x); }
+struct Ops<float> {
+    using B = bool;
+    static __device__ __forceinline__ float S(float a) { return a; }
+    static __device__ __forceinline__ B SB(bool a) { return a; }
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+    static __device__ __forceinline__ float neg(float a) { return -a; }
+    static __device__ __forceinline__ float rcp(float a) { return __fdividef(1.0f, a); }
+    static __device__ __forceinline__ float rsqrt(float a) { return rsqrtf(a); }
+    static __device__ __forceinline__ float sqrt(float a) { return sqrtf(a); }
+    static __device__ __forceinline__ float exp(float a) { return __expf(a); }
     static __device__ __forceinline__ float max(float a, float b) { return fmaxf(a, b); }
-};
-template <>
-struct Ar<double> {
-    static __device__ __forceinline__ double div(double a, double b) { return a / b; }
-    static __device__ __forceinline__ double rsqrt(double x) { return ::rsqrt(x); }
-    static __device__ __forceinline__ double sqrt(double x) { return ::sqrt(x); }
-    static __device__ __forceinline__ double exp(double x) { return ::exp(x); }
-    static __device__ __forceinline__ double max(double a, double b) { return fmax(a, b); }
+    static __device__ __forceinline__ B gt(float a, float b) { return a > b; }
+    static __device__ __forceinline__ B eq(float a, float b) { return a == b; }
+    static __device__ __forceinline__ B bor(B a, B b) { return a || b; }
+    static __device__ __forceinline__ B bnot(B a) { return !a; }
+    static __device__ __forceinline__ float sel(B c, float a, float b) { return c ? a : b; }
+    // sqrt(r2) as r2 * rsqrt(r2) (0 at 0)
+    static __device__ __forceinline__ float root(float r2) { return r2 > 0.0f ? r2 * rsqrtf(r2) : 0.0f; }
 };
 
-__device__ __forceinline__ float dot3(const float a[3], const float b[3]) {
-    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+template <>
+struct Ops<float2> {
+    using B = Bool2;
+    using F = Ops<float>;
+    static __device__ __forceinline__ float2 S(float a) { return make_float2(a, a); }
+    static __device__ __forceinline__ B SB(bool a) { return B{a, a}; }
+    static __device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+    static __device__ __forceinline__ float2 sub(float2 a, float2 b) {
+        return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);   // a - b, one rounding
+    }
+    static __device__ __forceinline__ float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+    static __device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+    static __device__ __forceinline__ float2 neg(float2 a) { return make_float2(-a.x, -a.y); }
+    static __device__ __forceinline__ float2 rcp(float2 a) { return make_float2(F::rcp(a.x), F::rcp(a.y)); }
+    static __device__ __forceinline__ float2 rsqrt(float2 a) { return make_float2(rsqrtf(a.x), rsqrtf(a.y)); }
+    static __device__ __forceinline__ float2 exp(float2 a) { return make_float2(__expf(a.x), __expf(a.y)); }
+    static __device__ __forceinline__ float2 max(float2 a, float2 b) {
+        return make_float2(fmaxf(a.x, b.x), fmaxf(a.y, b.y));
+    }
+    static __device__ __forceinline__ B gt(float2 a, float2 b) { return B{a.x > b.x, a.y > b.y}; }
+    static __device__ __forceinline__ B eq(float2 a, float2 b) { return B{a.x == b.x, a.y == b.y}; }
+    static __device__ __forceinline__ B bor(B a, B b) { return B{a.x || b.x, a.y || b.y}; }
+    static __device__ __forceinline__ B bnot(B a) { return B{!a.x, !a.y}; }
+    static __device__ __forceinline__ float2 sel(B c, float2 a, float2 b) {
+        return make_float2(c.x ? a.x : b.x, c.y ? a.y : b.y);
+    }
+    static __device__ __forceinline__ float2 root(float2 r2) { return make_float2(F::root(r2.x), F::root(r2.y)); }
+};
+
+template <>
+struct Ops<double> {
+    using B = bool;
+    static __device__ __forceinline__ double S(double a) { return a; }
+    static __device__ __forceinline__ B SB(bool a) { return a; }
+    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+    static __device__ __forceinline__ double neg(double a) { return -a; }
+    static __device__ __forceinline__ double rcp(double a) { return 1.0 / a; }
+    static __device__ __forceinline__ double rsqrt(double a) { return ::rsqrt(a); }
+    static __device__ __forceinline__ double sqrt(double a) { return ::sqrt(a); }
+    static __device__ __forceinline__ double exp(double a) { return ::exp(a); }
+    static __device__ __forceinline__ double max(double a, double b) { return fmax(a, b); }
+    static __device__ __forceinline__ B gt(double a, double b) { return a > b; }
+    static __device__ __forceinline__ B eq(double a, double b) { return a == b; }
+    static __device__ __forceinline__ B bor(B a, B b) { return a || b; }
+    static __device__ __forceinline__ B bnot(B a) { return !a; }
+    static __device__ __forceinline__ double sel(B c, double a, double b) { return c ? a : b; }
+    static __device__ __forceinline__ double root(double r2) { return r2 > 0.0 ? ::sqrt(r2) : 0.0; }
+};
+
+// a . b of 3-vectors, in a fixed order of correctly rounded operations
+template <typename V>
+__device__ __forceinline__ V dot3v(V a0, V a1, V a2, V b0, V b1, V b2) {
+    using O = Ops<V>;
+    return O::fma(a2, b2, O::fma(a1, b1, O::mul(a0, b0)));
 }
 
-// Everything of a Gaussian's view record the response needs, in type R:
-// W_eff rows, o_u, sigma_eff, rho^2.
-template <typename R>
+__device__ __forceinline__ float dot3(const float a[3], const float b[3]) {
+    return dot3v(a[0], a[1], a[2], b[0], b[1], b[2]);
+}
+
+// ---------------------------------------------------------------- inputs
+
+// The pixel's centre ray d and half-edge differentials, with the Gram terms of Eq. 12.
+template <typename V>
+struct PixelRaysT {
+    V d[3], dx[3], dy[3];
+    V d_dx, d_dy, dxdx, dxdy, dydy;
+};
+using PixelRays = PixelRaysT<float>;
+
+__device__ __forceinline__ PixelRaysT<float2> pack_pixels(const PixelRays &a, const PixelRays &b) {
+    PixelRaysT<float2> p;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        p.d[k] = make_float2(a.d[k], b.d[k]);
+        p.dx[k] = make_float2(a.dx[k], b.dx[k]);
+        p.dy[k] = make_float2(a.dy[k], b.dy[k]);
+    }
+    p.d_dx = make_float2(a.d_dx, b.d_dx);
+    p.d_dy = make_float2(a.d_dy, b.d_dy);
+    p.dxdx = make_float2(a.dxdx, b.dxdx);
+    p.dxdy = make_float2(a.dxdy, b.dxdy);
+    p.dydy = make_float2(a.dydy, b.dydy);
+    return p;
+}
+
+__device__ __forceinline__ PixelRaysT<double> widen(const PixelRays &a) {
+    PixelRaysT<double> p;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        p.d[k] = a.d[k];
+        p.dx[k] = a.dx[k];
+        p.dy[k] = a.dy[k];
+    }
+    // the Gram terms again in FP64
+    p.d_dx = dot3v(p.d[0], p.d[1], p.d[2], p.dx[0], p.dx[1], p.dx[2]);
+    p.d_dy = dot3v(p.d[0], p.d[1], p.d[2], p.dy[0], p.dy[1], p.dy[2]);
+    p.dxdx = dot3v(p.dx[0], p.dx[1], p.dx[2], p.dx[0], p.dx[1], p.dx[2]);
+    p.dxdy = dot3v(p.dx[0], p.dx[1], p.dx[2], p.dy[0], p.dy[1], p.dy[2]);
+    p.dydy = dot3v(p.dy[0], p.dy[1], p.dy[2], p.dy[0], p.dy[1], p.dy[2]);
+    return p;
+}
+
+// Everything of a Gaussian's view record the response needs: W_eff rows, o_u,
+// sigma_eff, rho^2.
+template <typename V>
 struct GaussRec {
-    R W[9], ou[3], sig, rho2;
+    V W[9], ou[3], sig, rho2;
 };
 
 // The flat flag is the sign bit of the record's rho^2 word; a flat record keeps
@@ -101,157 +205,203 @@ __device__ __forceinline__ GaussRec<double> rec_f64(const float4 r0, const float
                             sig, (double)fabsf(r7.x)};
 }
 
-// 2x2 matrix function K = f(H') of Eq. 12 (H' symmetric PSD), f(l) = max(l - rho2, 0) / (3 l).
-// Returns the case (1: both eigenvalues above rho2, 2: only the larger, 3: neither).
+// ---------------------------------------------------------------- Eq. 12: K = f(H')
+
+// Intermediates of one pair evaluation, kept for the adjoint.
 template <typename R>
-__device__ __forceinline__ int marginal_K(R h00, R h01, R h11, R rho2, R &k00, R &k01, R &k11) {
-    using A = Ar<R>;
-    const R third = R(1) / R(3);
-    const R mean = R(0.5) * (h00 + h11);
-    const R half = R(0.5) * (h00 - h11);
-    const R r2 = half * half + h01 * h01;
-    const R rad = r2 > R(0) ? r2 * A::rsqrt(r2) : R(0);
-    const R l1 = mean + rad;
-    if (!(l1 > rho2)) {
-        k00 = k01 = k11 = R(0);
-        return 3;
-    }
-    const R det = h00 * h11 - h01 * h01;
-    const R l2 = A::div(A::max(det, R(0)), l1);   // smaller eigenvalue without cancellation
-    if (l2 > rho2) {
-        // both directions exceed the floor: K = (I - rho2 H'^-1)/3
-        const R s = A::div(rho2, det);
-        k00 = (R(1) - s * h11) * third;
-        k11 = (R(1) - s * h00) * third;
-        k01 = (s * h01) * third;
-        return 1;
-    } else {
-        // only the major direction exceeds: K = f(l1) (H' - l2 I)/(l1 - l2)
-        const R sc = A::div(l1 - rho2, R(3) * l1 * (l1 - l2));
-        k00 = sc * (h00 - l2);
-        k11 = sc * (h11 - l2);
-        k01 = sc * h01;
-        return 2;
-    }
+struct PairFwdT {
+    R du[3], gx[3], gy[3], inv_n, p, ts, q[3], qq, cx, cy, ex[3], ey[3];
+    R G00, G01, G11, b0, b1;
+    int kcase;                 // 0: K = I/3; 1: K = (I - rho2 H'^-1)/3; 2: rank-1 K; 3: K = 0
+    R k00, k01, k11;
+    R t2, A00, A01, A11, h00, h01, h11;
+    R m00, m01, m10, m11, det, p00, p01, p10, p11, bPb, inv_det;
+    bool clamped;              // Q = |q|^2/det (lower bound) was active
+    R T;
+};
+using PairFwd = PairFwdT<float>;
+
+// Both eigenvalues of H' above rho^2: K = (I - rho^2 H'^-1)/3.
+template <typename V>
+__device__ __forceinline__ void K_both(V h00, V h01, V h11, V dh, V rho2, V &k00, V &k01, V &k11) {
+    using O = Ops<V>;
+    const V third = O::S(1.0f / 3.0f);
+    const V s = O::mul(rho2, O::rcp(dh));
+    k00 = O::mul(O::fma(O::neg(s), h11, O::S(1.0f)), third);
+    k11 = O::mul(O::fma(O::neg(s), h00, O::S(1.0f)), third);
+    k01 = O::mul(O::mul(s, h01), third);
 }
 
-// Response of one pair in arithmetic type R (the pixel's rays are FP32 and
-// are widened for R = double).  Returns false when t* <= T_NEAR (pair
-// skipped).  With STORE the intermediates are copied to *st (the arithmetic
-// is the same either way).
-template <bool FILTER, bool STORE = false, typename R = float>
-__device__ __forceinline__ bool pair_response(const GaussRec<R> &g, const bool additive, const PixelRays &px,
-                                              float &Tout, PairFwdT<R> *st = nullptr) {
-    using A = Ar<R>;
-    const R third = R(1) / R(3);
-    const R *W = g.W;
-    const R d0 = px.d[0], d1 = px.d[1], d2 = px.d[2];
-    const R du0 = W[0] * d0 + W[1] * d1 + W[2] * d2;
-    const R du1 = W[3] * d0 + W[4] * d1 + W[5] * d2;
-    const R du2 = W[6] * d0 + W[7] * d1 + W[8] * d2;
-    const R n = du0 * du0 + du1 * du1 + du2 * du2;
-    const R inv_n = A::div(R(1), n);
-    const R p = g.ou[0] * du0 + g.ou[1] * du1 + g.ou[2] * du2;
-    const R ts = -p * inv_n;
-    if (!(ts > R(T_NEAR))) return false;
-    const R q0 = g.ou[0] + ts * du0, q1 = g.ou[1] + ts * du1, q2 = g.ou[2] + ts * du2;
-    const R qq = q0 * q0 + q1 * q1 + q2 * q2;
-    if (STORE) {
+// Only the larger above rho^2: K = f(l1) (H' - l2 I)/(l1 - l2), f(l) = (l - rho^2)/(3 l).
+template <typename V>
+__device__ __forceinline__ void K_major(V h00, V h01, V h11, V l1, V l2, V rho2, V &k00, V &k01, V &k11) {
+    using O = Ops<V>;
+    const V sc = O::mul(O::sub(l1, rho2), O::rcp(O::mul(O::mul(O::S(3.0f), l1), O::sub(l1, l2))));
+    k00 = O::mul(sc, O::sub(h00, l2));
+    k11 = O::mul(sc, O::sub(h11, l2));
+    k01 = O::mul(sc, h01);
+}
+
+// ---------------------------------------------------------------- the response
+
+// Response of the pair(s) in type V.  hit: false where t* <= T_NEAR (the pair is
+// skipped).  With STORE (scalar types) the intermediates are copied to *st; the
+// arithmetic is the same either way.  A scalar call returns early when t* fails.
+template <bool FILTER, bool STORE = false, typename V = float>
+__device__ __forceinline__ void pair_eval(const GaussRec<V> &g, const bool additive, const PixelRaysT<V> &px, V &T,
+                                          typename Ops<V>::B &hit, PairFwdT<V> *st = nullptr) {
+    using O = Ops<V>;
+    using B = typename O::B;
+    constexpr bool SCALAR = sizeof(V) != sizeof(float2);
+    const V *W = g.W;
+    const V du0 = dot3v(W[0], W[1], W[2], px.d[0], px.d[1], px.d[2]);
+    const V du1 = dot3v(W[3], W[4], W[5], px.d[0], px.d[1], px.d[2]);
+    const V du2 = dot3v(W[6], W[7], W[8], px.d[0], px.d[1], px.d[2]);
+    const V n = dot3v(du0, du1, du2, du0, du1, du2);
+    const V inv_n = O::rcp(n);
+    const V p = dot3v(g.ou[0], g.ou[1], g.ou[2], du0, du1, du2);
+    const V ts = O::neg(O::mul(p, inv_n));
+    hit = O::gt(ts, O::S(T_NEAR));
+    if constexpr (SCALAR) {
+        if (!hit) return;
+    }
+    const V q0 = O::fma(ts, du0, g.ou[0]), q1 = O::fma(ts, du1, g.ou[1]), q2 = O::fma(ts, du2, g.ou[2]);
+    const V qq = dot3v(q0, q1, q2, q0, q1, q2);
+    if constexpr (STORE) {
         st->du[0] = du0; st->du[1] = du1; st->du[2] = du2;
         st->inv_n = inv_n; st->p = p; st->ts = ts;
         st->q[0] = q0; st->q[1] = q1; st->q[2] = q2; st->qq = qq;
     }
-    if (!FILTER) {
-        const R T = g.sig * A::exp(R(-0.5) * qq);
-        Tout = (float)T;
-        if (STORE) st->T = T;
-        return true;
-    }
-    const R x0 = px.dx[0], x1 = px.dx[1], x2 = px.dx[2];
-    const R y0 = px.dy[0], y1 = px.dy[1], y2 = px.dy[2];
-    const R gx0 = W[0] * x0 + W[1] * x1 + W[2] * x2;
-    const R gx1 = W[3] * x0 + W[4] * x1 + W[5] * x2;
-    const R gx2 = W[6] * x0 + W[7] * x1 + W[8] * x2;
-    const R gy0 = W[0] * y0 + W[1] * y1 + W[2] * y2;
-    const R gy1 = W[3] * y0 + W[4] * y1 + W[5] * y2;
-    const R gy2 = W[6] * y0 + W[7] * y1 + W[8] * y2;
-    const R cx = (du0 * gx0 + du1 * gx1 + du2 * gx2) * inv_n;
-    const R cy = (du0 * gy0 + du1 * gy1 + du2 * gy2) * inv_n;
-    const R ex0 = ts * (gx0 - cx * du0), ex1 = ts * (gx1 - cx * du1), ex2 = ts * (gx2 - cx * du2);
-    const R ey0 = ts * (gy0 - cy * du0), ey1 = ts * (gy1 - cy * du1), ey2 = ts * (gy2 - cy * du2);
-    const R G00 = ex0 * ex0 + ex1 * ex1 + ex2 * ex2;
-    const R G01 = ex0 * ey0 + ex1 * ey1 + ex2 * ey2;
-    const R G11 = ey0 * ey0 + ey1 * ey1 + ey2 * ey2;
-    const R b0 = ex0 * q0 + ex1 * q1 + ex2 * q2;
-    const R b1 = ey0 * q0 + ey1 * q1 + ey2 * q2;
-    R det, bPb;
-    if (g.rho2 == R(0) || additive) {
-        // K = I/3
-        const R m00 = R(1) + G00 * third, m11 = R(1) + G11 * third, m01 = G01 * third;
-        det = m00 * m11 - m01 * m01;
-        bPb = (b0 * b0 * m11 - R(2) * b0 * b1 * m01 + b1 * b1 * m00) * third;
-        if (STORE) {
-            st->kcase = 0;
-            st->k00 = st->k11 = third; st->k01 = R(0);
-            st->m00 = m00; st->m01 = m01; st->m10 = m01; st->m11 = m11;
-            st->p00 = m11 * third; st->p01 = -m01 * third;
-            st->p10 = -m01 * third; st->p11 = m00 * third;
-        }
+    if constexpr (!FILTER) {
+        T = O::mul(g.sig, O::exp(O::mul(O::S(-0.5f), qq)));
+        if constexpr (STORE) st->T = T;
+        return;
     } else {
-        // the pixel's ray Gram terms: precomputed in FP32, recomputed for FP64
-        R d_dx, d_dy, dxdx, dxdy, dydy;
-        if (sizeof(R) == sizeof(float)) {
-            d_dx = px.d_dx; d_dy = px.d_dy; dxdx = px.dxdx; dxdy = px.dxdy; dydy = px.dydy;
+        const V gx0 = dot3v(W[0], W[1], W[2], px.dx[0], px.dx[1], px.dx[2]);
+        const V gx1 = dot3v(W[3], W[4], W[5], px.dx[0], px.dx[1], px.dx[2]);
+        const V gx2 = dot3v(W[6], W[7], W[8], px.dx[0], px.dx[1], px.dx[2]);
+        const V gy0 = dot3v(W[0], W[1], W[2], px.dy[0], px.dy[1], px.dy[2]);
+        const V gy1 = dot3v(W[3], W[4], W[5], px.dy[0], px.dy[1], px.dy[2]);
+        const V gy2 = dot3v(W[6], W[7], W[8], px.dy[0], px.dy[1], px.dy[2]);
+        const V cx = O::mul(dot3v(du0, du1, du2, gx0, gx1, gx2), inv_n);
+        const V cy = O::mul(dot3v(du0, du1, du2, gy0, gy1, gy2), inv_n);
+        const V ncx = O::neg(cx), ncy = O::neg(cy);
+        const V ex0 = O::mul(ts, O::fma(ncx, du0, gx0)), ex1 = O::mul(ts, O::fma(ncx, du1, gx1)),
+                ex2 = O::mul(ts, O::fma(ncx, du2, gx2));
+        const V ey0 = O::mul(ts, O::fma(ncy, du0, gy0)), ey1 = O::mul(ts, O::fma(ncy, du1, gy1)),
+                ey2 = O::mul(ts, O::fma(ncy, du2, gy2));
+        const V G00 = dot3v(ex0, ex1, ex2, ex0, ex1, ex2);
+        const V G01 = dot3v(ex0, ex1, ex2, ey0, ey1, ey2);
+        const V G11 = dot3v(ey0, ey1, ey2, ey0, ey1, ey2);
+        const V b0 = dot3v(ex0, ex1, ex2, q0, q1, q2);
+        const V b1 = dot3v(ey0, ey1, ey2, q0, q1, q2);
+        // Eq. 12: H' = t*^2/3 [f_i . f_j], f_i = delta_i - c_i d, and the case of K
+        const V third = O::S(1.0f / 3.0f);
+        const V t2 = O::mul(O::mul(ts, ts), third);
+        const V A00 = O::fma(cx, O::sub(cx, O::mul(O::S(2.0f), px.d_dx)), px.dxdx);
+        const V A01 = O::sub(O::fma(cx, O::sub(cy, px.d_dy), px.dxdy), O::mul(cy, px.d_dx));
+        const V A11 = O::fma(cy, O::sub(cy, O::mul(O::S(2.0f), px.d_dy)), px.dydy);
+        const V h00 = O::mul(t2, A00), h01 = O::mul(t2, A01), h11 = O::mul(t2, A11);
+        const V mean = O::mul(O::S(0.5f), O::add(h00, h11));
+        const V half = O::mul(O::S(0.5f), O::sub(h00, h11));
+        const V l1 = O::add(mean, O::root(O::fma(half, half, O::mul(h01, h01))));
+        const V dh = O::fma(h00, h11, O::neg(O::mul(h01, h01)));
+        const V l2 = O::mul(O::max(dh, O::S(0.0f)), O::rcp(l1));   // smaller eigenvalue without cancellation
+        const B id = O::bor(O::eq(g.rho2, O::S(0.0f)), O::SB(additive));
+        const B none = O::bnot(O::gt(l1, g.rho2));
+        const B both = O::gt(l2, g.rho2);
+        V k00, k01, k11;
+        int kc = 0;
+        if constexpr (SCALAR) {
+            // the case taken, with exactly the operations the packed form selects from
+            kc = id ? 0 : none ? 3 : both ? 1 : 2;
+            if (kc == 0) {
+                k00 = k11 = third;
+                k01 = O::S(0.0f);
+            } else if (kc == 3) {
+                k00 = k01 = k11 = O::S(0.0f);
+            } else if (kc == 1) {
+                K_both(h00, h01, h11, dh, g.rho2, k00, k01, k11);
+            } else {
+                K_major(h00, h01, h11, l1, l2, g.rho2, k00, k01, k11);
+            }
         } else {
-            d_dx = d0 * x0 + d1 * x1 + d2 * x2;
-            d_dy = d0 * y0 + d1 * y1 + d2 * y2;
-            dxdx = x0 * x0 + x1 * x1 + x2 * x2;
-            dxdy = x0 * y0 + x1 * y1 + x2 * y2;
-            dydy = y0 * y0 + y1 * y1 + y2 * y2;
+            V a00, a01, a11, c00, c01, c11;
+            K_both(h00, h01, h11, dh, g.rho2, a00, a01, a11);
+            K_major(h00, h01, h11, l1, l2, g.rho2, c00, c01, c11);
+            k00 = O::sel(both, a00, c00);
+            k01 = O::sel(both, a01, c01);
+            k11 = O::sel(both, a11, c11);
+            k00 = O::sel(none, O::S(0.0f), k00);
+            k01 = O::sel(none, O::S(0.0f), k01);
+            k11 = O::sel(none, O::S(0.0f), k11);
+            k00 = O::sel(id, third, k00);
+            k01 = O::sel(id, O::S(0.0f), k01);
+            k11 = O::sel(id, third, k11);
         }
-        const R t2 = ts * ts * third;
-        const R A00 = dxdx - R(2) * cx * d_dx + cx * cx;
-        const R A01 = dxdy - cx * d_dy - cy * d_dx + cx * cy;
-        const R A11 = dydy - R(2) * cy * d_dy + cy * cy;
-        const R h00 = t2 * A00, h01 = t2 * A01, h11 = t2 * A11;
-        R k00, k01, k11;
-        const int kc = marginal_K<R>(h00, h01, h11, g.rho2, k00, k01, k11);
-        const R m00 = R(1) + G00 * k00 + G01 * k01, m01 = G00 * k01 + G01 * k11;
-        const R m10 = G01 * k00 + G11 * k01, m11 = R(1) + G01 * k01 + G11 * k11;
-        det = m00 * m11 - m01 * m10;
-        const R p00 = k00 * m11 - k01 * m10, p01 = k01 * m00 - k00 * m01;
-        const R p10 = k01 * m11 - k11 * m10, p11 = k11 * m00 - k01 * m01;
-        bPb = b0 * b0 * p00 + b0 * b1 * (p01 + p10) + b1 * b1 * p11;
-        if (STORE) {
+        // M = I + G K, det A = det M, P = K adj(M), b^T P b
+        const V m00 = O::fma(G00, k00, O::fma(G01, k01, O::S(1.0f))), m01 = O::fma(G00, k01, O::mul(G01, k11));
+        const V m10 = O::fma(G01, k00, O::mul(G11, k01)), m11 = O::fma(G01, k01, O::fma(G11, k11, O::S(1.0f)));
+        const V det = O::fma(m00, m11, O::neg(O::mul(m01, m10)));
+        const V p00 = O::fma(k00, m11, O::neg(O::mul(k01, m10))), p01 = O::fma(k01, m00, O::neg(O::mul(k00, m01)));
+        const V p10 = O::fma(k01, m11, O::neg(O::mul(k11, m10))), p11 = O::fma(k11, m00, O::neg(O::mul(k01, m01)));
+        const V bPb =
+            O::fma(O::mul(b0, b0), p00, O::fma(O::mul(b0, b1), O::add(p01, p10), O::mul(O::mul(b1, b1), p11)));
+        // q^T A^-1 q >= |q|^2 / lambda_max(A) >= |q|^2 / det A (A = I + a PSD rank-2
+        // matrix), a bound that also guards the difference against cancellation for
+        // far Gaussians seen at grazing angles.
+        const V rdet = O::rsqrt(det);
+        const V inv_det = O::mul(rdet, rdet);
+        const V Qa = O::fma(O::neg(bPb), inv_det, qq), Qb = O::mul(qq, inv_det);
+        const V Q = O::max(Qa, Qb);
+        T = O::mul(O::mul(g.sig, rdet), O::exp(O::mul(O::S(-0.5f), Q)));
+        if constexpr (STORE) {
+            st->gx[0] = gx0; st->gx[1] = gx1; st->gx[2] = gx2;
+            st->gy[0] = gy0; st->gy[1] = gy1; st->gy[2] = gy2;
+            st->cx = cx; st->cy = cy;
+            st->ex[0] = ex0; st->ex[1] = ex1; st->ex[2] = ex2;
+            st->ey[0] = ey0; st->ey[1] = ey1; st->ey[2] = ey2;
+            st->G00 = G00; st->G01 = G01; st->G11 = G11; st->b0 = b0; st->b1 = b1;
             st->kcase = kc;
             st->k00 = k00; st->k01 = k01; st->k11 = k11;
             st->t2 = t2; st->A00 = A00; st->A01 = A01; st->A11 = A11;
             st->h00 = h00; st->h01 = h01; st->h11 = h11;
             st->m00 = m00; st->m01 = m01; st->m10 = m10; st->m11 = m11;
             st->p00 = p00; st->p01 = p01; st->p10 = p10; st->p11 = p11;
+            st->det = det; st->bPb = bPb; st->inv_det = inv_det;
+            st->clamped = !(Qa >= Qb);
+            st->T = T;
         }
     }
-    // q^T A^-1 q >= |q|^2 / lambda_max(A) >= |q|^2 / det A (A = I + a PSD rank-2
-    // matrix), a bound that also guards the FP32 difference against cancellation
-    // for far Gaussians seen at grazing angles.
-    const R rdet = A::rsqrt(det);
-    const R inv_det = rdet * rdet;
-    const R Qa = qq - bPb * inv_det, Qb = qq * inv_det;
-    const R Q = A::max(Qa, Qb);
-    const R T = g.sig * rdet * A::exp(R(-0.5) * Q);
+}
+
+// Scalar convenience form: true when the pair is evaluated (t* > T_NEAR), T the response.
+template <bool FILTER, bool STORE = false, typename R = float>
+__device__ __forceinline__ bool pair_response(const GaussRec<R> &g, const bool additive, const PixelRaysT<R> &px,
+                                              float &Tout, PairFwdT<R> *st = nullptr) {
+    R T = R(0);
+    bool hit;
+    pair_eval<FILTER, STORE, R>(g, additive, px, T, hit, st);
     Tout = (float)T;
-    if (STORE) {
-        st->gx[0] = gx0; st->gx[1] = gx1; st->gx[2] = gx2;
-        st->gy[0] = gy0; st->gy[1] = gy1; st->gy[2] = gy2;
-        st->cx = cx; st->cy = cy;
-        st->ex[0] = ex0; st->ex[1] = ex1; st->ex[2] = ex2;
-        st->ey[0] = ey0; st->ey[1] = ey1; st->ey[2] = ey2;
-        st->G00 = G00; st->G01 = G01; st->G11 = G11; st->b0 = b0; st->b1 = b1;
-        st->det = det; st->bPb = bPb; st->inv_det = inv_det;
-        st->clamped = !(Qa >= Qb);
-        st->T = T;
-    }
-    return true;
+    return hit;
+}
+
+// ---------------------------------------------------------------- the rasteriser's pre-test
+
+// Visual-cone pre-test (view record words u, g, C; see preprocess.cu): a pixel
+// ray d with -1 + g.e + e^T C e > 1e-3, e = d - u, cannot reach alpha >= 1/255
+// with the Gaussian.  Returns true when the pair must be evaluated.  The same
+// operations in the forward (packed) and the adjoint (scalar).
+template <typename V>
+__device__ __forceinline__ typename Ops<V>::B pretest(V u0, V u1, V u2, V g0, V g1, V g2, V C00, V C11, V C22, V C01,
+                                                      V C02, V C12, const V d[3]) {
+    using O = Ops<V>;
+    const V e0 = O::sub(d[0], u0), e1 = O::sub(d[1], u1), e2 = O::sub(d[2], u2);
+    const V qa = O::fma(C02, e2, O::fma(C01, e1, O::mul(C00, e0)));
+    const V qb = O::fma(C12, e2, O::mul(C11, e1));
+    const V quad = O::fma(O::mul(C22, e2), e2, O::fma(qb, e1, O::mul(qa, e0)));
+    const V lin = O::fma(g2, e2, O::fma(g1, e1, O::fma(g0, e0, O::S(-1.0f))));
+    return O::bnot(O::gt(O::add(lin, quad), O::S(1e-3f)));
 }
 
 }  // namespace conegs
