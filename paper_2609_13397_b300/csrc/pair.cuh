@@ -11,11 +11,11 @@
 //           take the same compositing decisions;
 //   double  near-degenerate flat Gaussians (effective scale ratio above
 //           FLAT_RATIO): their whitening W has a row of length 1/s_min, so the
-//           whitened camera centre o_u and ray d_u are large, t* and
-//           q = o_u + t* d_u cancel, and the final |q|^2 - b^T K (I + GK)^-1 b
-//           cancels again.  In FP32 the response of such a disk seen at a
-//           grazing angle is off by ~3e-4 at s_max/s_min = 300 and by ~2e-3 at
-//           10^4 (face-on); up to 100 it stays within ~5e-5, hence the threshold.
+//           whitened camera centre o_u is large and t* and q = o_u + t* d_u
+//           cancel.  Measured against the FP64 oracle, the FP32 form below
+//           stays within ~2e-5 up to s_max/s_min = 250 at any viewing angle and
+//           size, reaches ~9e-5 at 400 and ~3e-4 at 600 (small disks seen
+//           face-on), hence the threshold of 200.
 // FP32 uses the SFU approximations of reciprocal, square root and exp (about
 // 1-2 ulp), far inside the 1e-4 output tolerance; FP64 the correctly rounded ones.
 //
@@ -28,11 +28,11 @@
 // H' = [f_i . f_j]/3 (eigenpairs lambda_j, v_j) the clamped, re-whitened
 // footprint is E K E^T with K = sum_j max(lambda_j - rho^2, 0)/(3 lambda_j)
 // v_j v_j^T, a 2x2 matrix function of H' (rho = 0 gives K = I/3).
-// A = I + E K E^T, so with G = E^T E and b = E^T q (Sylvester / Woodbury):
-//   det A = det(I + G K),  q^T A^-1 q = |q|^2 - b^T K (I + G K)^-1 b
+// A = I + E K E^T; with an orthonormal basis [e1 e2] of span(E), E = [e1 e2] R:
+//   det A = det(I + N),  q^T A^-1 q = |q_perp|^2 + q_E^T (I + N)^-1 q_E,
+//   N = R K R^T, q_E = [e1 e2]^T q, q_perp = q - [e1 e2] q_E,
 //   T = sigma_eff det(A)^-1/2 exp(-q^T A^-1 q / 2)                   (Eq. 9)
-// with q^T A^-1 q clamped below by |q|^2 / det A (exact bound, see below).
-// No 3x3 matrix and no plane basis is formed.
+// No 3x3 matrix is formed.
 #pragma once
 #include "common.cuh"
 
@@ -40,7 +40,7 @@ namespace conegs {
 
 // A Gaussian is "flat" (evaluated in FP64) when s_eff,max / s_eff,min > FLAT_RATIO
 // (the effective scales of Eq. 10, after the floor).
-constexpr float FLAT_RATIO = 100.0f;
+constexpr float FLAT_RATIO = 200.0f;
 
 // ---------------------------------------------------------------- arithmetic per type
 
@@ -63,6 +63,7 @@ struct Ops<float> {
     static __device__ __forceinline__ float neg(float a) { return -a; }
     static __device__ __forceinline__ float rcp(float a) { return __fdividef(1.0f, a); }
     static __device__ __forceinline__ float rsqrt(float a) { return rsqrtf(a); }
+    static __device__ __forceinline__ float rsqrt0(float a) { return a > 0.0f ? rsqrtf(a) : 0.0f; }
     static __device__ __forceinline__ float sqrt(float a) { return sqrtf(a); }
     static __device__ __forceinline__ float exp(float a) { return __expf(a); }
     static __device__ __forceinline__ float max(float a, float b) { return fmaxf(a, b); }
@@ -90,6 +91,7 @@ struct Ops<float2> {
     static __device__ __forceinline__ float2 neg(float2 a) { return make_float2(-a.x, -a.y); }
     static __device__ __forceinline__ float2 rcp(float2 a) { return make_float2(F::rcp(a.x), F::rcp(a.y)); }
     static __device__ __forceinline__ float2 rsqrt(float2 a) { return make_float2(rsqrtf(a.x), rsqrtf(a.y)); }
+    static __device__ __forceinline__ float2 rsqrt0(float2 a) { return make_float2(F::rsqrt0(a.x), F::rsqrt0(a.y)); }
     static __device__ __forceinline__ float2 exp(float2 a) { return make_float2(__expf(a.x), __expf(a.y)); }
     static __device__ __forceinline__ float2 max(float2 a, float2 b) {
         return make_float2(fmaxf(a.x, b.x), fmaxf(a.y, b.y));
@@ -116,6 +118,7 @@ struct Ops<double> {
     static __device__ __forceinline__ double neg(double a) { return -a; }
     static __device__ __forceinline__ double rcp(double a) { return 1.0 / a; }
     static __device__ __forceinline__ double rsqrt(double a) { return ::rsqrt(a); }
+    static __device__ __forceinline__ double rsqrt0(double a) { return a > 0.0 ? ::rsqrt(a) : 0.0; }
     static __device__ __forceinline__ double sqrt(double a) { return ::sqrt(a); }
     static __device__ __forceinline__ double exp(double a) { return ::exp(a); }
     static __device__ __forceinline__ double max(double a, double b) { return fmax(a, b); }
@@ -290,11 +293,6 @@ __device__ __forceinline__ void pair_eval(const GaussRec<V> &g, const bool addit
                 ex2 = O::mul(ts, O::fma(ncx, du2, gx2));
         const V ey0 = O::mul(ts, O::fma(ncy, du0, gy0)), ey1 = O::mul(ts, O::fma(ncy, du1, gy1)),
                 ey2 = O::mul(ts, O::fma(ncy, du2, gy2));
-        const V G00 = dot3v(ex0, ex1, ex2, ex0, ex1, ex2);
-        const V G01 = dot3v(ex0, ex1, ex2, ey0, ey1, ey2);
-        const V G11 = dot3v(ey0, ey1, ey2, ey0, ey1, ey2);
-        const V b0 = dot3v(ex0, ex1, ex2, q0, q1, q2);
-        const V b1 = dot3v(ey0, ey1, ey2, q0, q1, q2);
         // Eq. 12: H' = t*^2/3 [f_i . f_j], f_i = delta_i - c_i d, and the case of K
         const V third = O::S(1.0f / 3.0f);
         const V t2 = O::mul(O::mul(ts, ts), third);
@@ -339,23 +337,61 @@ __device__ __forceinline__ void pair_eval(const GaussRec<V> &g, const bool addit
             k01 = O::sel(id, O::S(0.0f), k01);
             k11 = O::sel(id, third, k11);
         }
-        // M = I + G K, det A = det M, P = K adj(M), b^T P b
-        const V m00 = O::fma(G00, k00, O::fma(G01, k01, O::S(1.0f))), m01 = O::fma(G00, k01, O::mul(G01, k11));
-        const V m10 = O::fma(G01, k00, O::mul(G11, k01)), m11 = O::fma(G01, k01, O::fma(G11, k11, O::S(1.0f)));
-        const V det = O::fma(m00, m11, O::neg(O::mul(m01, m10)));
-        const V p00 = O::fma(k00, m11, O::neg(O::mul(k01, m10))), p01 = O::fma(k01, m00, O::neg(O::mul(k00, m01)));
-        const V p10 = O::fma(k01, m11, O::neg(O::mul(k11, m10))), p11 = O::fma(k11, m00, O::neg(O::mul(k01, m01)));
-        const V bPb =
-            O::fma(O::mul(b0, b0), p00, O::fma(O::mul(b0, b1), O::add(p01, p10), O::mul(O::mul(b1, b1), p11)));
-        // q^T A^-1 q >= |q|^2 / lambda_max(A) >= |q|^2 / det A (A = I + a PSD rank-2
-        // matrix), a bound that also guards the difference against cancellation for
-        // far Gaussians seen at grazing angles.
-        const V rdet = O::rsqrt(det);
-        const V inv_det = O::mul(rdet, rdet);
-        const V Qa = O::fma(O::neg(bPb), inv_det, qq), Qb = O::mul(qq, inv_det);
-        const V Q = O::max(Qa, Qb);
+        // Eq. 9 in an orthonormal basis (e1, e2) of span(E): E = [e1 e2] R with
+        // R = [[r00, r01], [0, r11]] (Gram-Schmidt), N = R K R^T, so that
+        //   det A = det(I + N),  q^T A^-1 q = |q_perp|^2 + q_E^T (I + N)^-1 q_E,
+        // q_E = (e1.q, e2.q), q_perp = q - e1 (e1.q) - e2 (e2.q).  No difference of
+        // two large quadratic forms is taken: q_perp is formed as a vector, so its
+        // rounding stays at the size of q's components, which keeps FP32 accurate
+        // for strongly anisotropic Gaussians at grazing angles.
+        const V r00s = dot3v(ex0, ex1, ex2, ex0, ex1, ex2);
+        const V i0 = O::rsqrt0(r00s);
+        const V e10 = O::mul(ex0, i0), e11 = O::mul(ex1, i0), e12 = O::mul(ex2, i0);
+        const V r00 = O::mul(r00s, i0);
+        const V r01 = dot3v(ey0, ey1, ey2, e10, e11, e12);
+        const V nr01 = O::neg(r01);
+        const V w0 = O::fma(nr01, e10, ey0), w1 = O::fma(nr01, e11, ey1), w2 = O::fma(nr01, e12, ey2);
+        const V r11s = dot3v(w0, w1, w2, w0, w1, w2);
+        const V i1 = O::rsqrt0(r11s);
+        const V e20 = O::mul(w0, i1), e21 = O::mul(w1, i1), e22 = O::mul(w2, i1);
+        const V r11 = O::mul(r11s, i1);
+        const V qe1 = dot3v(q0, q1, q2, e10, e11, e12), qe2 = dot3v(q0, q1, q2, e20, e21, e22);
+        const V nq1 = O::neg(qe1), nq2 = O::neg(qe2);
+        const V qp0 = O::fma(nq2, e20, O::fma(nq1, e10, q0)), qp1 = O::fma(nq2, e21, O::fma(nq1, e11, q1)),
+                qp2 = O::fma(nq2, e22, O::fma(nq1, e12, q2));
+        const V qperp = dot3v(qp0, qp1, qp2, qp0, qp1, qp2);
+        const V RK00 = O::fma(r00, k00, O::mul(r01, k01)), RK01 = O::fma(r00, k01, O::mul(r01, k11));
+        const V N11 = O::fma(RK00, r00, O::mul(RK01, r01));
+        const V N12 = O::mul(RK01, r11);
+        const V N22 = O::mul(O::mul(r11, k11), r11);
+        const V a1 = O::add(O::S(1.0f), N11), a2 = O::add(O::S(1.0f), N22);
+        const V detA = O::fma(a1, a2, O::neg(O::mul(N12, N12)));
+        const V num = O::fma(O::mul(qe1, qe1), a2,
+                             O::fma(O::mul(qe2, qe2), a1, O::mul(O::mul(O::S(-2.0f), O::mul(qe1, qe2)), N12)));
+        const V rdet = O::rsqrt(detA);
+        const V Q = O::max(O::fma(num, O::mul(rdet, rdet), qperp), O::S(0.0f));
         T = O::mul(O::mul(g.sig, rdet), O::exp(O::mul(O::S(-0.5f), Q)));
         if constexpr (STORE) {
+            // what the adjoint differentiates: the same T through G = E^T E, b = E^T q,
+            // M = I + G K, P = K adj(M): q^T A^-1 q = max(|q|^2 - b^T P b / det M, |q|^2 / det M)
+            const V G00 = dot3v(ex0, ex1, ex2, ex0, ex1, ex2);
+            const V G01 = dot3v(ex0, ex1, ex2, ey0, ey1, ey2);
+            const V G11 = dot3v(ey0, ey1, ey2, ey0, ey1, ey2);
+            const V b0 = dot3v(ex0, ex1, ex2, q0, q1, q2);
+            const V b1 = dot3v(ey0, ey1, ey2, q0, q1, q2);
+            const V m00 = O::fma(G00, k00, O::fma(G01, k01, O::S(1.0f))), m01 = O::fma(G00, k01, O::mul(G01, k11));
+            const V m10 = O::fma(G01, k00, O::mul(G11, k01)), m11 = O::fma(G01, k01, O::fma(G11, k11, O::S(1.0f)));
+            const V det = O::fma(m00, m11, O::neg(O::mul(m01, m10)));
+            const V p00 = O::fma(k00, m11, O::neg(O::mul(k01, m10))), p01 = O::fma(k01, m00, O::neg(O::mul(k00, m01)));
+            const V p10 = O::fma(k01, m11, O::neg(O::mul(k11, m10))), p11 = O::fma(k11, m00, O::neg(O::mul(k01, m01)));
+            const V bPb =
+                O::fma(O::mul(b0, b0), p00, O::fma(O::mul(b0, b1), O::add(p01, p10), O::mul(O::mul(b1, b1), p11)));
+            const V inv_det = O::rcp(det);
+            const V Qa = O::fma(O::neg(bPb), inv_det, qq), Qb = O::mul(qq, inv_det);
+            st->m00 = m00; st->m01 = m01; st->m10 = m10; st->m11 = m11;
+            st->p00 = p00; st->p01 = p01; st->p10 = p10; st->p11 = p11;
+            st->det = det; st->bPb = bPb; st->inv_det = inv_det;
+            st->clamped = !(Qa >= Qb);
             st->gx[0] = gx0; st->gx[1] = gx1; st->gx[2] = gx2;
             st->gy[0] = gy0; st->gy[1] = gy1; st->gy[2] = gy2;
             st->cx = cx; st->cy = cy;
@@ -366,10 +402,6 @@ __device__ __forceinline__ void pair_eval(const GaussRec<V> &g, const bool addit
             st->k00 = k00; st->k01 = k01; st->k11 = k11;
             st->t2 = t2; st->A00 = A00; st->A01 = A01; st->A11 = A11;
             st->h00 = h00; st->h01 = h01; st->h11 = h11;
-            st->m00 = m00; st->m01 = m01; st->m10 = m10; st->m11 = m11;
-            st->p00 = p00; st->p01 = p01; st->p10 = p10; st->p11 = p11;
-            st->det = det; st->bPb = bPb; st->inv_det = inv_det;
-            st->clamped = !(Qa >= Qb);
             st->T = T;
         }
     }

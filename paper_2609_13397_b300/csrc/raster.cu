@@ -1,19 +1,18 @@
 // K5: tile rasteriser, forward (Sec. 3 Eq. 4 compositing over Eq. 9 responses).
 //
-// One warp per 8x8 tile (per list segment, for long lists), each lane two
-// horizontally adjacent pixels whose responses it evaluates together in
-// packed FP32 (f32x2 instructions, pair_eval<float2>).  The tile's
-// depth-sorted Gaussian list is walked in batches of 32: each lane stages one
-// Gaussian's view record into shared memory, every value the packed
-// evaluation reads stored twice; every lane then pre-tests the batch against
-// its two pixels' rays (broadcast reads) and walks the entries either pixel
-// passed in depth order, the warp's lanes on different entries in lockstep.
-// Compositing follows the 3DGS conventions: a = min(0.99, T); pairs with
-// a < 1/255 are skipped; a pixel stops before the pair that would take its
-// transmittance below 1e-4; the warp leaves the list as soon as all 64 pixels
-// have stopped.  Per pixel the kernels write rgb, the final transmittance and
-// the number of list entries walked up to the last contributing pair (for the
-// adjoint, which recomputes the same responses bit for bit in scalar form).
+// One CTA of 64 threads per 8x8 tile (per list segment, for long lists), one
+// thread per pixel.  The tile's depth-sorted Gaussian list is walked in
+// batches of 64: each thread loads one Gaussian's 128-byte view record (8 x
+// float4, coalesced gather) into shared memory; every thread then pre-tests
+// the batch against its pixel's ray (a broadcast read per entry) and
+// evaluates its passing entries in depth order, the warp's lanes on different
+// entries in lockstep.  Compositing follows the 3DGS conventions: a =
+// min(0.99, T); pairs with a < 1/255 are skipped; a pixel stops before the
+// pair that would take its transmittance below 1e-4; the CTA leaves the list
+// as soon as all its pixels have stopped (__syncthreads_count).  Per pixel the
+// kernels write rgb, the final transmittance and the number of list entries
+// walked up to the last contributing pair (for the adjoint, which recomputes
+// the same pre-test and responses bit for bit).
 #include <algorithm>
 
 #include "raster.cuh"
@@ -80,131 +79,76 @@ __global__ void seg_map_kernel(const uint32_t *__restrict__ nseg, const uint32_t
     if (t == nt - 1) *total = off[t] + nseg[t] - (uint32_t)nt;
 }
 
-// ---------------------------------------------------------------- the walk
-//
-// One warp per tile (or list segment): lane l owns the horizontally adjacent
-// pixels (2 (l mod 4), l / 4) and (2 (l mod 4) + 1, l / 4) of the 8x8 tile,
-// and evaluates both against each Gaussian in packed FP32 (pair_eval<float2>).
-// The list is staged BATCH entries at a time in shared memory, every value the
-// packed evaluation reads stored twice (a float2 per scalar), so that it loads
-// ready for the f32x2 instructions.  Phase 1 pre-tests every staged entry
-// against both pixels (broadcast reads); phase 2 walks, in depth order, the
-// entries either pixel passed, each lane on its own entries, and composites
-// each pixel with the entries it passed itself.
-
-constexpr int RASTER_THREADS = 32;
-constexpr int BATCH = 32;
-
-struct StagedBatch {
-    float2 w[14][BATCH];   // W_eff rows (9), o_u (3), sigma_eff, rho^2 (sign bit: flat)
-    float2 t[12][BATCH];   // pre-test: u (3), g (3), C00, C11, C22, 2 C01, 2 C02, 2 C12
-    float4 c[BATCH];       // rgb
-};
-
-struct PixState {
-    float C0, C1, C2, T;
-    uint32_t last;         // list entries up to and including the last contributor (1-based)
-    bool stopped;
-};
-
-__device__ __forceinline__ void stage_entry(StagedBatch &sb, int k, const float4 *r) {
-    const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3], r4 = r[4], r5 = r[5], r6 = r[6];
-    const float r7x = r[7].x;
-    const float w[14] = {r0.x, r0.y, r0.z, r1.x, r1.y, r1.z, r2.x, r2.y, r2.z, r0.w, r1.w, r2.w, r3.w, r7x};
-    const float t[12] = {r4.x, r4.y, r4.z, r4.w, r5.x, r5.y, r5.z, r5.w, r6.x, r6.y, r6.z, r6.w};
-#pragma unroll
-    for (int j = 0; j < 14; ++j) sb.w[j][k] = make_float2(w[j], w[j]);
-#pragma unroll
-    for (int j = 0; j < 12; ++j) sb.t[j][k] = make_float2(t[j], t[j]);
-    sb.c[k] = r3;
-}
-
-// One compositing step (Eq. 4 with the 3DGS conventions): a = min(0.99, T);
-// a < 1/255 is skipped; the pixel stops before the pair that would take its
-// transmittance below 1e-4 (returns true); else the pair's colour is added.
-__device__ __forceinline__ bool composite_step(PixState &s, float T, const float4 rgb, uint32_t walk1) {
-    const float alpha = fminf(ALPHA_MAX, T);
-    if (alpha < ALPHA_MIN) return false;
-    const float test = s.T * (1.0f - alpha);
-    if (test < T_STOP) return true;
-    const float wgt = alpha * s.T;
-    s.C0 += rgb.x * wgt;
-    s.C1 += rgb.y * wgt;
-    s.C2 += rgb.z * wgt;
-    s.T = test;
-    s.last = walk1;
-    return false;
-}
-
-// Walks list entries [b0, b1) for the lane's two pixels (tile pixel indices qa,
-// qa + 1) from their states, with the sequential compositing rules.  Live
-// pixels take part; a pixel leaves at its stop (sets stopped) or at b1.  last is
-// 1-based relative to `base`.  Counters: list entries walked and evaluations
-// past the pre-test, per pixel; of those, FP64 (flat) ones.
+// Walks list entries [b0, b1) for the tile's pixels from (C, Tacc), with the
+// sequential compositing rules.  `live` pixels take part; a pixel leaves at its
+// stop (sets stopped) or at b1.  last is 1-based relative to `base`.
 template <bool FILTER>
-__device__ __forceinline__ void walk2(const RasterArgs &a, StagedBatch &sb, uint32_t b0, uint32_t b1, uint32_t base,
-                                      bool liveA, bool liveB, const PixelRaysT<float2> &px, int qa, PixState &A,
-                                      PixState &B, uint32_t &walked, uint32_t &full, uint32_t &nflat) {
-    using O = Ops<float2>;
-    bool doneA = !liveA, doneB = !liveB;
-    for (uint32_t start = b0; start < b1; start += BATCH) {
-        if (__all_sync(0xffffffffu, doneA && doneB)) break;
+__device__ __forceinline__ void walk_entries(const RasterArgs &a, float4 (*s_rec)[TILE_PX], uint32_t b0, uint32_t b1,
+                                             uint32_t base, bool live, const PixelRays &px, float &C0, float &C1,
+                                             float &C2, float &Tacc, uint32_t &last, bool &stopped,
+                                             uint32_t &walked, uint32_t &full, uint32_t &nflat) {
+    bool done = !live;
+    for (uint32_t start = b0; start < b1; start += TILE_PX) {
+        if (__syncthreads_count(done) == TILE_PX) break;
         const uint32_t idx = start + threadIdx.x;
-        __syncwarp();
-        if (idx < b1) stage_entry(sb, threadIdx.x, a.rec + (size_t)REC_F4 * a.gids[idx]);
-        __syncwarp();
-        const int nb = (int)min((uint32_t)BATCH, b1 - start);
-        // phase 1: pre-test of every staged entry against both pixels
-        uint32_t mA = 0u, mB = 0u;
-        if (!(doneA && doneB)) {
-            walked += (uint32_t)nb * ((doneA ? 0u : 1u) + (doneB ? 0u : 1u));
+        if (idx < b1) {
+            const float4 *r = a.rec + (size_t)REC_F4 * a.gids[idx];
+#pragma unroll
+            for (int k = 0; k < REC_F4; ++k) s_rec[k][threadIdx.x] = r[k];
+        }
+        __syncthreads();
+        const int nb = (int)min((uint32_t)TILE_PX, b1 - start);
+        // phase 1: cone pre-test of every staged entry against this pixel (the
+        // shared-memory reads are broadcasts: all lanes read the same entry)
+        unsigned long long mask = 0ull;
+        if (!done) {
+            walked += (uint32_t)nb;
             for (int b = 0; b < nb; ++b) {
-                const Bool2 pass = pretest<float2>(sb.t[0][b], sb.t[1][b], sb.t[2][b], sb.t[3][b], sb.t[4][b],
-                                                   sb.t[5][b], sb.t[6][b], sb.t[7][b], sb.t[8][b], sb.t[9][b],
-                                                   sb.t[10][b], sb.t[11][b], px.d);
-                mA |= (pass.x ? 1u : 0u) << b;
-                mB |= (pass.y ? 1u : 0u) << b;
-            }
-            if (doneA) mA = 0u;
-            if (doneB) mB = 0u;
-        }
-        // phase 2: the entries either pixel passed, in depth order
-        uint32_t m = mA | mB;
-        while (__any_sync(0xffffffffu, m != 0u)) {
-            if (m == 0u) continue;
-            const int b = __ffs(m) - 1;
-            m &= m - 1u;
-            const bool inA = (mA >> b) & 1u, inB = (mB >> b) & 1u;
-            full += (inA ? 1u : 0u) + (inB ? 1u : 0u);
-            const float2 r7 = sb.w[13][b];
-            float2 T;
-            Bool2 hit;
-            if (!rec_is_flat(r7.x)) {
-                const GaussRec<float2> g{{sb.w[0][b], sb.w[1][b], sb.w[2][b], sb.w[3][b], sb.w[4][b], sb.w[5][b],
-                                          sb.w[6][b], sb.w[7][b], sb.w[8][b]},
-                                         {sb.w[9][b], sb.w[10][b], sb.w[11][b]},
-                                         sb.w[12][b],
-                                         r7};
-                pair_eval<FILTER, false, float2>(g, a.additive != 0, px, T, hit);
-            } else {                                  // FP64 responses, precomputed
-                const float *ft = a.flat_T + (size_t)a.flat_slot[start + b] * TILE_PX + qa;
-                T = make_float2(ft[0], ft[1]);
-                hit = Bool2{T.x >= 0.0f, T.y >= 0.0f};
-                nflat += (inA ? 1u : 0u) + (inB ? 1u : 0u);
-            }
-            const float4 rgb = sb.c[b];
-            const uint32_t walk1 = start - base + (uint32_t)b + 1u;
-            if (inA && hit.x && composite_step(A, T.x, rgb, walk1)) {
-                A.stopped = doneA = true;
-                mA = 0u;
-                m &= mB;
-            }
-            if (inB && hit.y && composite_step(B, T.y, rgb, walk1)) {
-                B.stopped = doneB = true;
-                mB = 0u;
-                m &= mA;
+                const float4 r4 = s_rec[4][b], r5 = s_rec[5][b], r6 = s_rec[6][b];
+                if (pretest<float>(r4.x, r4.y, r4.z, r4.w, r5.x, r5.y, r5.z, r5.w, r6.x, r6.y, r6.z, r6.w, px.d))
+                    mask |= 1ull << b;
             }
         }
+        // phase 2: each lane walks its own passing entries in depth order, so
+        // the warp's lanes evaluate different entries in lockstep
+        while (__any_sync(0xffffffffu, mask != 0ull)) {
+            if (mask != 0ull) {
+                const int b = __ffsll((long long)mask) - 1;
+                mask &= mask - 1ull;
+                ++full;
+                const float4 r3 = s_rec[3][b];
+                const float r7x = s_rec[7][b].x;          // rho^2 (sign bit: flat)
+                float T;
+                bool hit;
+                if (!rec_is_flat(r7x)) {
+                    hit = pair_response<FILTER>(rec_f32(s_rec[0][b], s_rec[1][b], s_rec[2][b], r3.w, r7x),
+                                                a.additive != 0, px, T);
+                } else {                          // FP64 response, precomputed
+                    ++nflat;
+                    T = a.flat_T[(size_t)a.flat_slot[start + b] * TILE_PX + threadIdx.x];
+                    hit = T >= 0.0f;
+                }
+                if (hit) {
+                    const float alpha = fminf(ALPHA_MAX, T);
+                    if (!(alpha < ALPHA_MIN)) {
+                        const float test = Tacc * (1.0f - alpha);
+                        if (test < T_STOP) {
+                            done = true;
+                            stopped = true;
+                            mask = 0ull;
+                        } else {
+                            const float wgt = alpha * Tacc;
+                            C0 += r3.x * wgt;
+                            C1 += r3.y * wgt;
+                            C2 += r3.z * wgt;
+                            Tacc = test;
+                            last = start - base + (uint32_t)b + 1u;
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -233,40 +177,10 @@ __device__ __forceinline__ void write_pixel(const RasterArgs &a, int64_t pix, in
     if (a.last) a.last[pix] = last;
 }
 
-// The lane's two pixels: tile pixel indices q, q + 1; image coordinates; rays.
-struct LanePixels {
-    int q;
-    int64_t pixA, pixB;
-    bool insideA, insideB, liveA, liveB;
-};
-
-__device__ __forceinline__ LanePixels lane_pixels(const RasterArgs &a, int tile) {
-    LanePixels L;
-    const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
-    const int row = threadIdx.x >> 2, col = (threadIdx.x & 3) * 2;
-    L.q = row * TILE + col;
-    const int i = tx * TILE + col, j = ty * TILE + row;
-    L.pixA = (int64_t)j * a.W + i;
-    L.pixB = L.pixA + 1;
-    L.insideA = i < a.W && j < a.H;
-    L.insideB = i + 1 < a.W && j < a.H;
-    L.liveA = L.insideA && a.valid[L.pixA];
-    L.liveB = L.insideB && a.valid[L.pixB];
-    return L;
-}
-
-__device__ __forceinline__ PixelRaysT<float2> lane_rays(const RasterArgs &a, const LanePixels &L, int64_t P,
-                                                        bool useA, bool useB) {
-    PixelRays ra{}, rb{};
-    if (useA) load_pixel(a, L.pixA, P, ra);
-    if (useB) load_pixel(a, L.pixB, P, rb);
-    return pack_pixels(ra, rb);
-}
-
-// Pass A.  FIRST: one warp per tile for its first segment; else one per later segment.
+// Pass A.  FIRST: one CTA per tile for its first segment; else one per later segment.
 template <bool FILTER, bool FIRST>
-__global__ void __launch_bounds__(RASTER_THREADS) raster_seg_kernel(const RasterArgs a, const SegArgs g) {
-    __shared__ StagedBatch sb;
+__global__ void __launch_bounds__(TILE_PX) raster_seg_kernel(const RasterArgs a, const SegArgs g) {
+    __shared__ float4 s_rec[REC_F4][TILE_PX];
     uint2 tw;
     if (FIRST) {
         tw = make_uint2(blockIdx.x, 0u);
@@ -283,28 +197,30 @@ __global__ void __launch_bounds__(RASTER_THREADS) raster_seg_kernel(const Raster
         for (uint32_t k = g.seg_off[tile]; k < w && !skip; ++k) skip = ((volatile uint32_t *)g.seg_all)[k] != 0u;
         if (skip) return;
     }
-    const LanePixels L = lane_pixels(a, tile);
+    const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+    const int i = tx * TILE + (threadIdx.x % TILE), j = ty * TILE + (threadIdx.x / TILE);
     const int64_t P = (int64_t)a.W * a.H;
-    const PixelRaysT<float2> px = lane_rays(a, L, P, L.liveA, L.liveB);
+    const bool inside = i < a.W && j < a.H;
+    const int64_t pix = (int64_t)j * a.W + i;
+    const bool live = inside && a.valid[pix];
+    PixelRays px;
+    if (live) load_pixel(a, pix, P, px);
     const uint2 range = a.ranges[tile];
     const uint32_t seg = seg_length_dev(g.stat);
     const uint32_t b0 = range.x + tw.y * seg;
     const uint32_t b1 = nseg == 1 ? range.y : min(range.y, b0 + seg);
-    PixState A{0.f, 0.f, 0.f, 1.0f, 0u, false}, B{0.f, 0.f, 0.f, 1.0f, 0u, false};
-    uint32_t walked = 0, full = 0, nflat = 0;
-    walk2<FILTER>(a, sb, b0, b1, b0, L.liveA, L.liveB, px, L.q, A, B, walked, full, nflat);
+    float C0 = 0.f, C1 = 0.f, C2 = 0.f, Tacc = 1.0f;
+    uint32_t last = 0, walked = 0, full = 0, nflat = 0;
+    bool stopped = false;
+    walk_entries<FILTER>(a, s_rec, b0, b1, b0, live, px, C0, C1, C2, Tacc, last, stopped, walked, full, nflat);
     count_walk(a, walked, full, nflat);
     if (nseg == 1) {                       // the whole list: final result
-        if (L.insideA) write_pixel(a, L.pixA, P, A.C0, A.C1, A.C2, A.T, A.last);
-        if (L.insideB) write_pixel(a, L.pixB, P, B.C0, B.C1, B.C2, B.T, B.last);
+        if (inside) write_pixel(a, pix, P, C0, C1, C2, Tacc, last);
         return;
     }
-    const size_t o = (size_t)w * TILE_PX + L.q;
-    g.seg_c[o] = make_float4(A.C0, A.C1, A.C2, A.T);
-    g.seg_c[o + 1] = make_float4(B.C0, B.C1, B.C2, B.T);
-    g.seg_l[o] = A.last | (A.stopped ? 0x80000000u : 0u);
-    g.seg_l[o + 1] = B.last | (B.stopped ? 0x80000000u : 0u);
-    const bool all = __all_sync(0xffffffffu, (A.stopped || !L.liveA) && (B.stopped || !L.liveB));
+    g.seg_c[(size_t)w * TILE_PX + threadIdx.x] = make_float4(C0, C1, C2, Tacc);
+    g.seg_l[(size_t)w * TILE_PX + threadIdx.x] = last | (stopped ? 0x80000000u : 0u);
+    const int all = __syncthreads_and(stopped || !live);
     if (threadIdx.x == 0) g.seg_all[w] = all ? 1u : 0u;
 }
 
@@ -365,13 +281,12 @@ __global__ void __launch_bounds__(TILE_PX) raster_merge_kernel(const RasterArgs 
     }
 }
 
-// Replay: one warp per segment item; walks the segment again for the pixels
+// Replay: one CTA per segment item; walks the segment again for the pixels
 // whose walk stops in it, from their T_in, and writes their final result; the
 // segment's share of C and the final T replace its pass-A entry.
 template <bool FILTER>
-__global__ void __launch_bounds__(RASTER_THREADS) raster_replay_kernel(const RasterArgs a, const SegArgs g,
-                                                                       int ntiles) {
-    __shared__ StagedBatch sb;
+__global__ void __launch_bounds__(TILE_PX) raster_replay_kernel(const RasterArgs a, const SegArgs g, int ntiles) {
+    __shared__ float4 s_rec[REC_F4][TILE_PX];
     uint2 tw;
     if ((int)blockIdx.x < ntiles) {
         tw = make_uint2(blockIdx.x, 0u);
@@ -384,35 +299,31 @@ __global__ void __launch_bounds__(RASTER_THREADS) raster_replay_kernel(const Ras
     if (g.nseg[tile] == 1) return;
     const uint32_t w = g.seg_off[tile] + tw.y;
     if (g.need_item[w] == 0u) return;
-    const LanePixels L = lane_pixels(a, tile);
+    const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+    const int i = tx * TILE + (threadIdx.x % TILE), j = ty * TILE + (threadIdx.x / TILE);
     const int64_t P = (int64_t)a.W * a.H;
-    const size_t q = (size_t)tile * TILE_PX + L.q;
-    const bool mineA = g.rp_need[q] == tw.y, mineB = g.rp_need[q + 1] == tw.y;
-    float4 cinA = make_float4(0.f, 0.f, 0.f, 1.0f), cinB = cinA;
-    PixState A{0.f, 0.f, 0.f, 1.0f, 0u, false}, B{0.f, 0.f, 0.f, 1.0f, 0u, false};   // C: this segment's share
-    if (mineA) {
-        cinA = g.rp_c[q];
-        A.T = cinA.w;
-        A.last = g.rp_last[q];
+    const bool inside = i < a.W && j < a.H;
+    const int64_t pix = (int64_t)j * a.W + i;
+    const size_t q = (size_t)tile * TILE_PX + threadIdx.x;
+    const bool mine = g.rp_need[q] == tw.y;
+    float4 cin = make_float4(0.f, 0.f, 0.f, 1.0f);
+    float C0 = 0.f, C1 = 0.f, C2 = 0.f, T = 1.0f;      // C: this segment's share
+    uint32_t last = 0, walked = 0, full = 0, nflat = 0;
+    PixelRays px;
+    if (mine) {
+        cin = g.rp_c[q];
+        T = cin.w;
+        last = g.rp_last[q];
+        load_pixel(a, pix, P, px);
     }
-    if (mineB) {
-        cinB = g.rp_c[q + 1];
-        B.T = cinB.w;
-        B.last = g.rp_last[q + 1];
-    }
-    const PixelRaysT<float2> px = lane_rays(a, L, P, mineA, mineB);
     const uint2 range = a.ranges[tile];
     const uint32_t seg = seg_length_dev(g.stat);
     const uint32_t b0 = range.x + tw.y * seg, b1 = min(range.y, b0 + seg);
-    uint32_t walked = 0, full = 0, nflat = 0;
-    walk2<FILTER>(a, sb, b0, b1, range.x, mineA, mineB, px, L.q, A, B, walked, full, nflat);
-    if (mineA) {
-        g.seg_c[(size_t)w * TILE_PX + L.q] = make_float4(A.C0, A.C1, A.C2, A.T);
-        if (L.insideA) write_pixel(a, L.pixA, P, cinA.x + A.C0, cinA.y + A.C1, cinA.z + A.C2, A.T, A.last);
-    }
-    if (mineB) {
-        g.seg_c[(size_t)w * TILE_PX + L.q + 1] = make_float4(B.C0, B.C1, B.C2, B.T);
-        if (L.insideB) write_pixel(a, L.pixB, P, cinB.x + B.C0, cinB.y + B.C1, cinB.z + B.C2, B.T, B.last);
+    bool stopped = false;
+    walk_entries<FILTER>(a, s_rec, b0, b1, range.x, mine, px, C0, C1, C2, T, last, stopped, walked, full, nflat);
+    if (mine) {
+        g.seg_c[(size_t)w * TILE_PX + threadIdx.x] = make_float4(C0, C1, C2, T);
+        if (inside) write_pixel(a, pix, P, cin.x + C0, cin.y + C1, cin.z + C2, T, last);
     }
 }
 
@@ -494,11 +405,11 @@ template <bool FILTER>
 static void launch_raster_passes(const RasterArgs &a, const SegArgs &g, int ntiles, unsigned later, int64_t wmax,
                                  cudaStream_t s, cudaEvent_t main0, cudaEvent_t main1) {
     if (main0) cudaEventRecord(main0, s);
-    raster_seg_kernel<FILTER, true><<<ntiles, RASTER_THREADS, 0, s>>>(a, g);
+    raster_seg_kernel<FILTER, true><<<ntiles, TILE_PX, 0, s>>>(a, g);
     if (main1) cudaEventRecord(main1, s);
-    raster_seg_kernel<FILTER, false><<<later, RASTER_THREADS, 0, s>>>(a, g);
+    raster_seg_kernel<FILTER, false><<<later, TILE_PX, 0, s>>>(a, g);
     raster_merge_kernel<<<ntiles, TILE_PX, 0, s>>>(a, g);
-    raster_replay_kernel<FILTER><<<(unsigned)wmax, RASTER_THREADS, 0, s>>>(a, g, ntiles);
+    raster_replay_kernel<FILTER><<<(unsigned)wmax, TILE_PX, 0, s>>>(a, g, ntiles);
     note_launches(4);
 }
 

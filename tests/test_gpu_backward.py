@@ -55,6 +55,10 @@ def _case(name):
     elif name == "flat":               # near-degenerate disks (s_max/s_min ~ 10^3), adjoint in FP64
         cam = S.pinhole(40, 30, 36.0)
         sc = S.flat_scene(150, seed=8, ratio=1e3, tilt_deg=(0.0, 89.0), cam=cam, fov_deg=25.0)
+    elif name == "anisotropic":        # s_max/s_min ~ 100 at all angles: FP32, through the orthonormal basis
+        cam = S.pinhole(40, 30, 36.0)
+        sc = S.flat_scene(150, seed=9, ratio=100.0, tilt_deg=(0.0, 89.5), cam=cam, fov_deg=25.0,
+                          log_scale_mean=-3.5)
     else:                              # fisheye
         cam = S.c3_camera(48, 48)
         sc = S.uniform_box_scene(150, seed=5, log_scale_mean=-2.4, log_scale_std=0.4, sh_degree=1)
@@ -62,7 +66,8 @@ def _case(name):
 
 
 @pytest.mark.parametrize("name,mode", [("pinhole", "aniso"), ("floor", "aniso"), ("coarse_floor", "aniso"),
-                                       ("fisheye", "aniso"), ("flat", "aniso"), ("pinhole", "filter_none"),
+                                       ("fisheye", "aniso"), ("flat", "aniso"), ("anisotropic", "aniso"),
+                                       ("pinhole", "filter_none"),
                                        ("coarse_floor", "additive"), ("coarse_floor", "iso"), ("fisheye", "zf")])
 def test_backward_matches_gradient_oracle(cg, oracle_lib, name, mode):
     from oracle import grad as G

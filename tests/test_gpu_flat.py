@@ -2,10 +2,11 @@
 face-on and at grazing angles) through a pinhole and a Kannala-Brandt fisheye.
 
 Their whitening W_eff has a row of length 1/s_min (Sec. 3), so the closed-form
-response of Eq. 9 cancels badly in FP32: the library evaluates Gaussians with an
-effective scale ratio above 100 in FP64 (the footprint-convolved covariance's
-inverse and determinant, with t*, q and e_i feeding them).  The image must match
-the FP64 oracle within 1e-4, the pair counts bit for bit, and the profiled
+response of Eq. 9 cancels in FP32: the library evaluates Gaussians with an
+effective scale ratio above 200 in FP64 (the footprint-convolved covariance's
+inverse and determinant, with t*, q and e_i feeding them) and the rest in FP32
+through an orthonormal basis of the footprint.  The image must match the FP64
+oracle within 1e-4 either way, the pair counts bit for bit, and the profiled
 counters must show which path ran."""
 import numpy as np
 import pytest
@@ -18,6 +19,7 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-4
 EPS_FLAG = 2e-4
 POSES = {"face_on": (0.0, 30.0), "grazing": (80.0, 89.5)}
+FLAT_RATIO = 200.0   # the library's FP64 threshold on s_eff,max / s_eff,min
 
 
 @pytest.fixture(scope="module")
@@ -40,7 +42,7 @@ def _scene(kind, ratio, pose, floor=False, seed=1):
 
 
 @pytest.mark.parametrize("kind", ["pinhole", "kb"])
-@pytest.mark.parametrize("ratio", [60.0, 150.0, 1e3, 1e4])
+@pytest.mark.parametrize("ratio", [60.0, 150.0, 400.0, 1e3, 1e4])
 @pytest.mark.parametrize("pose", list(POSES))
 def test_flat_gaussians_match_oracle(cg, oracle_lib, kind, ratio, pose):
     cam, sc = _scene(kind, ratio, pose)
@@ -59,9 +61,9 @@ def test_flat_gaussians_match_oracle(cg, oracle_lib, kind, ratio, pose):
     err = np.abs(rgb - r.rgb)[ok].max()
     errT = np.abs(T - r.T)[ok].max()
     assert err <= TOL and errT <= TOL, (err, errT)
-    if ratio > 100.0:
+    if ratio * 1.02 > FLAT_RATIO:       # flat_scene draws the ratio as ratio x U(1.02, 1.3)
         assert st["n_evaluated_flat"] > 0 and st["n_evaluated_flat"] == st["n_evaluated"]
-    else:
+    elif ratio * 1.3 < FLAT_RATIO:
         assert st["n_evaluated_flat"] == 0
     pg, pt = (t.cpu().numpy() for t in v.bin_counts())
     total, opg, opt, _ = oracle_lib.bin_counts(cam, sc)
