@@ -258,6 +258,16 @@ conegs_status conegs_get_pairs(const conegs_view *view, int32_t *gaussian_ids, i
 conegs_status conegs_radix_sort_pairs(conegs_ctx *ctx, uint32_t *keys, uint32_t *values, int64_t n, int begin_bit,
                                       int end_bit, void *stream);
 
+/* Measured FP32 fused multiply-add throughput of device `device` (TFLOP/s, an
+ * FMA counted as 2 flops): the denominator of the rasteriser's roofline, whose
+ * pair response (Eq. 2-12) runs on the FP32 FMA pipe.  Runs independent FMA
+ * chains (scalar and packed f32x2) on every SM for a few milliseconds and
+ * reports the larger rate in *tflops_host and that launch's time in *ms_host
+ * (may be NULL).  Allocates a small device buffer; synchronises the device's
+ * legacy default stream.  The paper has no counterpart; this is a measurement
+ * utility. */
+conegs_status conegs_measure_fp32_peak(int device, double *tflops_host, double *ms_host);
+
 /* The same stable radix sort, for callers that cannot allocate device memory
  * while they sort: their device memory may be fully reserved by another
  * allocator (a framework's caching allocator), or they run in a

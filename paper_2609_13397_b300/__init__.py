@@ -32,7 +32,8 @@ FILTER_NONE, COMP_ADDITIVE, KEEP_FOR_BACKWARD, PROFILE, FILTER_ISO, FILTER_ZF, B
 _DTYPE_CODE = {torch.float32: F32, torch.bfloat16: BF16, torch.float16: F16}
 
 __all__ = ["Context", "View", "ConegsError", "PINHOLE", "KB_FISHEYE", "FILTER_NONE", "COMP_ADDITIVE",
-           "KEEP_FOR_BACKWARD", "PROFILE", "FILTER_ISO", "FILTER_ZF", "BIN_UT", "radix_sort_pairs", "render_fn"]
+           "KEEP_FOR_BACKWARD", "PROFILE", "FILTER_ISO", "FILTER_ZF", "BIN_UT", "radix_sort_pairs", "render_fn",
+           "measure_fp32_peak"]
 
 
 def _ptr(t: Optional[torch.Tensor]):
@@ -341,3 +342,11 @@ def radix_sort_pairs(ctx: Context, keys: torch.Tensor, values: torch.Tensor, beg
     check(lib().conegs_radix_sort_pairs(ctx._h, _ptr(keys), _ptr(values), keys.numel(), begin_bit, end_bit,
                                         _stream(stream)), "radix_sort_pairs")
     return keys, values
+
+
+def measure_fp32_peak(device: int = 0):
+    """Measured FP32 FMA throughput of the device: (TFLOP/s, ms of the timed launch)."""
+    t = ctypes.c_double()
+    m = ctypes.c_double()
+    check(lib().conegs_measure_fp32_peak(int(device), ctypes.byref(t), ctypes.byref(m)), "measure_fp32_peak")
+    return t.value, m.value

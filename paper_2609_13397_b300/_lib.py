@@ -67,6 +67,8 @@ def lib():
         "conegs_get_pairs": ([P, P, P, P], c_int),
         "conegs_radix_sort_pairs": ([P, P, P, c_int64, c_int, c_int, P], c_int),
         "conegs_radix_sort_pairs_noalloc": ([P, P, c_int64, c_int, c_int, P], c_int),
+        "conegs_measure_fp32_peak": ([c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
+                                     c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -83,7 +85,7 @@ def exported_symbols():
             "conegs_render_host_batch", "conegs_render_host",
             "conegs_render_backward", "conegs_get_stats", "conegs_compute_floor", "conegs_get_rays",
             "conegs_get_tile_table", "conegs_get_bin_counts", "conegs_get_pairs", "conegs_radix_sort_pairs",
-            "conegs_radix_sort_pairs_noalloc"]
+            "conegs_radix_sort_pairs_noalloc", "conegs_measure_fp32_peak"]
 
 
 def check(status: int, what: str = ""):

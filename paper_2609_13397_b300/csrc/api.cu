@@ -81,6 +81,28 @@ long long launches_so_far() { return g_launches.load(); }
 
 namespace {
 
+}  // namespace
+
+namespace conegs {
+int num_sms() {
+    static int sms[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!sms[dev]) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) {
+            cudaGetLastError();
+            v = 1;
+        }
+        sms[dev] = v;
+    }
+    return sms[dev];
+}
+}  // namespace conegs
+
+namespace {
+
 conegs_status fail(conegs_status st, const char *fmt, ...) {
     char buf[512];
     va_list ap;

@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(TILE_PX, 12) raster_bwd_kernel(const RasterArg
     const uint2 range = a.ranges[tile];
     uint32_t b0 = range.x, b1 = range.y;
     if (nseg > 1) {
-        const uint32_t seg = seg_length_dev(g.stat);
+        const uint32_t seg = seg_length_dev(g);
         b0 = range.x + tw.y * seg;
         b1 = min(range.y, b0 + seg);
     }

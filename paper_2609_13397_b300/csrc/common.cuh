@@ -52,6 +52,9 @@ __device__ __forceinline__ float load_scalar(const void *p, int64_t i, int stora
 
 __host__ __device__ __forceinline__ int64_t div_up(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// Streaming multiprocessors of the current device (queried once per device).
+int num_sms();
+
 // Host-side count of kernel launches issued by the library (reported by
 // conegs_get_stats for the last render).
 void note_launches(int k);

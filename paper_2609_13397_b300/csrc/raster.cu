@@ -39,7 +39,7 @@ namespace conegs {
 // from which the adjoint walks each segment back to front on its own.
 
 int64_t split_items_max(int ntiles) {
-    return (int64_t)ntiles + std::max<int64_t>(2 * (int64_t)CTA_SLOTS, ntiles / 4 + 1) + 1;
+    return (int64_t)ntiles + std::max<int64_t>(2 * (int64_t)raster_slots(), ntiles / 4 + 1) + 1;
 }
 
 // Non-empty tile count and total list length (stat[0], stat[1]).
@@ -61,10 +61,10 @@ __global__ void seg_stat_kernel(const uint2 *__restrict__ ranges, int nt, unsign
 }
 
 __global__ void seg_count_kernel(const uint2 *__restrict__ ranges, int nt, const unsigned long long *__restrict__ stat,
-                                 uint32_t *__restrict__ nseg) {
+                                 uint32_t slots, uint32_t *__restrict__ nseg) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nt) return;
-    const uint32_t seg = seg_length_dev(stat);
+    const uint32_t seg = seg_length_dev(stat, slots);
     const uint32_t len = ranges[t].y - ranges[t].x;
     nseg[t] = len > seg ? (len + seg - 1) / seg : 1u;
 }
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(TILE_PX) raster_seg_kernel(const RasterArgs a,
     PixelRays px;
     if (live) load_pixel(a, pix, P, px);
     const uint2 range = a.ranges[tile];
-    const uint32_t seg = seg_length_dev(g.stat);
+    const uint32_t seg = seg_length_dev(g);
     const uint32_t b0 = range.x + tw.y * seg;
     const uint32_t b1 = nseg == 1 ? range.y : min(range.y, b0 + seg);
     float C0 = 0.f, C1 = 0.f, C2 = 0.f, Tacc = 1.0f;
@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(TILE_PX) raster_merge_kernel(const RasterArgs 
     const int64_t P = (int64_t)a.W * a.H;
     const bool inside = i < a.W && j < a.H;
     const int64_t pix = (int64_t)j * a.W + i;
-    const uint32_t seg = seg_length_dev(g.stat);
+    const uint32_t seg = seg_length_dev(g);
     float C0 = 0.f, C1 = 0.f, C2 = 0.f, Tin = 1.0f;
     uint32_t last = 0, need = NO_STOP, reach = NO_STOP;
     const uint32_t w0 = g.seg_off[tile];
@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(TILE_PX) raster_replay_kernel(const RasterArgs
         load_pixel(a, pix, P, px);
     }
     const uint2 range = a.ranges[tile];
-    const uint32_t seg = seg_length_dev(g.stat);
+    const uint32_t seg = seg_length_dev(g);
     const uint32_t b0 = range.x + tw.y * seg, b1 = min(range.y, b0 + seg);
     bool stopped = false;
     walk_entries<FILTER>(a, s_rec, b0, b1, range.x, mine, px, C0, C1, C2, T, last, stopped, walked, full, nflat);
@@ -345,6 +345,23 @@ __global__ void __launch_bounds__(TILE_PX) raster_suffix_kernel(const SegArgs g)
         S1 += c.y;
         S2 += c.z;
     }
+}
+
+uint32_t raster_slots() {
+    static uint32_t slots[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!slots[dev]) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, raster_seg_kernel<true, true>, TILE_PX, 0) !=
+                cudaSuccess || per_sm < 1) {
+            cudaGetLastError();
+            per_sm = 16;
+        }
+        slots[dev] = (uint32_t)(per_sm * num_sms());
+    }
+    return slots[dev];
 }
 
 cudaError_t exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *scratch, int pred,
@@ -384,6 +401,7 @@ int64_t split_scratch_words(int ntiles) { return split_layout(ntiles).words; }
 SegArgs split_args(uint32_t *scratch, int ntiles, int64_t *items) {
     const SplitLayout L = split_layout(ntiles);
     SegArgs g;
+    g.slots = raster_slots();
     g.nseg = scratch + L.o_nseg;
     g.seg_off = scratch + L.o_off;
     g.total = scratch + L.o_total;
@@ -428,8 +446,9 @@ cudaError_t launch_raster_split(const RasterArgs &a, int ntiles, bool filter, ui
     unsigned long long *stat = const_cast<unsigned long long *>(g.stat);
     cudaError_t e0 = cudaMemsetAsync(stat, 0, 2 * sizeof(unsigned long long), s);
     if (e0 != cudaSuccess) return e0;
-    seg_stat_kernel<<<(unsigned)std::min<int64_t>(div_up(ntiles, 256), 148), 256, 0, s>>>(a.ranges, ntiles, stat);
-    seg_count_kernel<<<(unsigned)div_up(ntiles, 256), 256, 0, s>>>(a.ranges, ntiles, stat, nseg);
+    seg_stat_kernel<<<(unsigned)std::min<int64_t>(div_up(ntiles, 256), num_sms()), 256, 0, s>>>(a.ranges, ntiles,
+                                                                                              stat);
+    seg_count_kernel<<<(unsigned)div_up(ntiles, 256), 256, 0, s>>>(a.ranges, ntiles, stat, g.slots, nseg);
     note_launches(2);
     cudaError_t e = exclusive_scan(nseg, off, ntiles, scan_scratch, 0, s);
     if (e != cudaSuccess) return e;

@@ -83,10 +83,14 @@ __device__ __forceinline__ void load_pixel(const RasterArgs &a, int64_t pix, int
 // ---------------------------------------------------------------- long-list split (forward and adjoint)
 
 constexpr uint32_t SEG_MIN = 256;
-constexpr uint32_t CTA_SLOTS = 148 * 16;   // resident 64-thread raster CTAs on a B300
 constexpr uint32_t NO_STOP = 0xffffffffu;
 
+// Resident raster CTAs on the device (SMs x CTAs per SM of the forward raster
+// kernel), the unit of the long-list split; queried once per device.
+uint32_t raster_slots();
+
 struct SegArgs {
+    uint32_t slots;                   // raster_slots() of the device
     const unsigned long long *stat;   // [0] non-empty tiles, [1] total list length -> segment length
     const uint32_t *nseg, *seg_off;   // per tile: segment count, first item
     const uint2 *work;      // (tile, segment >= 1)
@@ -106,15 +110,15 @@ struct SegArgs {
 // Segment length L: with fewer non-empty tiles than two per resident CTA,
 // about two segments per resident CTA (at least 256 entries); otherwise 4x the
 // mean non-empty list (rounded up), so that only tail lists split.  Either way
-// the segment count stays below ntiles + max(2 CTA_SLOTS, ntiles / 4) + 1, the
+// the segment count stays below ntiles + max(2 slots, ntiles / 4) + 1, the
 // bound split_items_max sizes the split state with: a shorter L (more segments
 // per resident CTA) must raise that bound with it, or the passes write past
 // the state.
-static __device__ __forceinline__ uint32_t seg_length_dev(const unsigned long long *stat) {
+static __device__ __forceinline__ uint32_t seg_length_dev(const unsigned long long *stat, uint32_t slots) {
     const unsigned long long ne = stat[0] > 0 ? stat[0] : 1, tot = stat[1];
     unsigned long long s;
-    if (ne < 2ull * CTA_SLOTS) {
-        s = (tot + 2ull * CTA_SLOTS - 1) / (2ull * CTA_SLOTS);
+    if (ne < 2ull * slots) {
+        s = (tot + 2ull * slots - 1) / (2ull * slots);
         s = (s + TILE_PX - 1) / TILE_PX * TILE_PX;
     } else {
         s = (4ull * tot + ne - 1) / ne;
@@ -122,6 +126,7 @@ static __device__ __forceinline__ uint32_t seg_length_dev(const unsigned long lo
     if (s < SEG_MIN) s = SEG_MIN;
     return (uint32_t)(s < 0x7fffffffull ? s : 0x7fffffffull);
 }
+static __device__ __forceinline__ uint32_t seg_length_dev(const SegArgs &g) { return seg_length_dev(g.stat, g.slots); }
 
 // The split state of a view with ntiles tiles inside its scratch buffer
 // (split_scratch_words(ntiles) words); *items: the item bound (grid size).

@@ -176,7 +176,7 @@ cudaError_t sum_counts(const uint32_t *in, int64_t n, unsigned long long *d_two,
     cudaError_t e = cudaMemsetAsync(d_two, 0, 2 * sizeof(unsigned long long), s);
     if (e == cudaSuccess && flag) e = cudaMemsetAsync(d_flagged, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess || n == 0) return e;
-    int grid = (int)std::min<int64_t>(div_up(n, 256), 148 * 8);
+    int grid = (int)std::min<int64_t>(div_up(n, 256), 8 * (int64_t)num_sms());
     sum_u64_kernel<<<grid, 256, 0, s>>>(in, n, d_two, d_two + 1, flag, d_flagged);
     note_launches(1);
     return cudaGetLastError();
@@ -237,8 +237,8 @@ constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
 constexpr int RS_ROUNDS_LARGE = 16;                 // 32-item rounds per warp per tile: 4096-item tiles
 constexpr int RS_ROUNDS_SMALL = 4;                  // 1024-item tiles for sorts of up to RS_SMALL_N items
-constexpr int64_t RS_SMALL_N = 1 << 20;             // (their 4096-item tiles would not fill 148 SMs)
-constexpr int RS_MAX_BLOCKS = 148 * 4;
+constexpr int64_t RS_SMALL_N = 1 << 20;             // (their 4096-item tiles would not fill the SMs)
+constexpr int RS_BLOCKS_PER_SM = 4;
 
 struct RsPlan {
     int64_t n;
@@ -253,7 +253,7 @@ RsPlan rs_plan(int64_t n) {
     p.rounds = n <= RS_SMALL_N ? RS_ROUNDS_SMALL : RS_ROUNDS_LARGE;
     const int64_t tile = (int64_t)RS_THREADS * p.rounds;
     int64_t tiles = div_up(n, tile);
-    int64_t blocks = std::min<int64_t>(tiles, RS_MAX_BLOCKS);
+    int64_t blocks = std::min<int64_t>(tiles, (int64_t)RS_BLOCKS_PER_SM * num_sms());
     if (blocks < 1) blocks = 1;
     int64_t tiles_per = div_up(tiles, blocks);
     p.chunk = tiles_per * tile;
