@@ -69,10 +69,12 @@ def estimate_bytes(cam, n_gaussians: int) -> int:
 
 
 class Server:
-    def __init__(self, ctx: Context, slots: int = 4, mem_budget_bytes: int = 32 << 30, keep_images: bool = False):
+    def __init__(self, ctx: Context, slots: int = 4, mem_budget_bytes: int = 32 << 30, keep_images: int = 0):
+        """keep_images: how many results keep a copy of their image (True: all)."""
         self.ctx = ctx
         self.budget = int(mem_budget_bytes)
-        self.keep_images = keep_images
+        self.keep_images = (1 << 62) if keep_images is True else int(keep_images)
+        self._kept = 0
         self._slots = [(ctx.view(), torch.cuda.Stream(device=ctx.device)) for _ in range(slots)]
         self._queue: collections.deque = collections.deque()
         self._cv = threading.Condition()
@@ -133,7 +135,10 @@ class Server:
                     view.set_camera_from(cam, stream=stream)
                     view.render_host(h_rgb, h_T, flags=req.flags, stream=stream)
                 res.rays = int(view.stats()["n_valid_pixels"])
-                if self.keep_images:
+                with self._cv:
+                    keep = self._kept < self.keep_images
+                    self._kept += 1 if keep else 0
+                if keep:
                     res.rgb, res.T = h_rgb.clone(), h_T.clone()
             except ConegsError as e:
                 if e.status == 7:                       # library budget: retry when memory frees up

@@ -271,6 +271,25 @@ def flat_scene(n: int, seed: int = 0, ratio: float = 1e3, tilt_deg=(0.0, 30.0), 
                  logits.astype(np.float32), sh.astype(np.float32), sh_degree, np.zeros(n, np.float32))
 
 
+def _round_bf16(a: np.ndarray) -> np.ndarray:
+    """FP32 values rounded to the nearest BF16 value (ties to even), as FP32."""
+    u = np.ascontiguousarray(a, np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32)
+
+
+def quantized(scene: Scene, kind: str) -> Scene:
+    """The scene with SH coefficients and opacity logits rounded to the half
+    precision they are stored in ("bf16" or "f16"), kept as FP32 values."""
+    if kind == "bf16":
+        q = _round_bf16
+    elif kind == "f16":
+        q = lambda a: np.asarray(a, np.float32).astype(np.float16).astype(np.float32)
+    else:
+        raise ValueError(kind)
+    return dataclasses.replace(scene, sh=q(scene.sh), opacity_logits=q(scene.opacity_logits))
+
+
 def perturbed(scene: Scene, seed: int = 1) -> Scene:
     """The C3 target scene: mu + N(0,0.01), log s + N(0,0.05), DC + N(0,0.05), logit + N(0,0.1)."""
     rng = np.random.default_rng(seed)

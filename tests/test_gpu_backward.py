@@ -222,3 +222,36 @@ def test_backward_full_size_c2_sampled(cg, oracle_lib):
     # Gaussians that contribute to no kept pixel get no gradient
     scale = max(np.abs(want["means"]).max(), 1e-12)
     assert np.abs(got["means"].reshape(-1, 3)[~touched]).max() <= ABS * scale
+
+
+def test_backward_accumulates_views_like_the_oracle(cg, oracle_lib):
+    """Gradients of a loss over several views (a pinhole and a fisheye of one scene)
+    accumulated into one buffer, as a training step over a camera batch does, against
+    the sum of the gradient oracle's per-view gradients."""
+    from oracle import grad as G
+    sc = S.uniform_box_scene(150, seed=31, log_scale_mean=-2.6, log_scale_std=0.4, sh_degree=1)
+    cams = [S.pinhole(40, 30, 36.0, cam_to_world=S.look_at((0.05, 0.0, 0.0), (0.1, 0.05, 4.0))),
+            S.c3_camera(48, 48)]
+    sc = sc.with_rho2(oracle_lib.floor_rho2([c.scaled(2.0) for c in cams], sc.means).astype(np.float32))
+    ctx = cg.Context(0)
+    ctx.set_scene_from(sc)
+    grads = None
+    total = None
+    rng = np.random.default_rng(32)
+    for cam in cams:
+        P = cam.n_pixels
+        w_rgb = rng.normal(size=(P, 3))
+        w_T = rng.normal(size=P)
+        ref = oracle_lib.render(cam, sc, eps=2e-4)
+        w_rgb[ref.flags != 0] = 0.0
+        w_T[ref.flags != 0] = 0.0
+        _, g_ref = G.loss_and_grad(cam, sc, np.arange(P), w_rgb, w_T)
+        total = g_ref if total is None else {k: total[k] + g_ref[k] for k in total}
+        v = ctx.view()
+        v.set_camera_from(cam)
+        v.render(flags=cg.KEEP_FOR_BACKWARD)
+        dL_drgb = torch.from_numpy(w_rgb.T.reshape(3, cam.height, cam.width).astype(np.float32)).cuda()
+        dL_dT = torch.from_numpy(w_T.reshape(cam.height, cam.width).astype(np.float32)).cuda()
+        grads = v.render_backward(dL_drgb, dL_dT, grads=grads)
+    torch.cuda.synchronize()
+    assert_grads_close({k: t.cpu().numpy() for k, t in grads.items()}, total)

@@ -375,3 +375,82 @@ def test_pair_counts_bit_exact_random(cg, oracle_lib, seed):
     total, opg, opt, _ = oracle_lib.bin_counts(cam, sc)
     assert np.array_equal(pg, opg)
     assert np.array_equal(pt, opt)
+
+
+def _sampled_parity(oracle_lib, cam, sc, rgb, T, npx, seed, tol=TOL, eps=EPS_FLAG, min_ok=0.9):
+    valid = oracle_lib.rays(cam)[3]
+    cand = np.nonzero(valid)[0]
+    rng = np.random.default_rng(seed)
+    pix = rng.choice(cand, size=min(npx, cand.size), replace=False).astype(np.int32)
+    r = oracle_lib.render(cam, sc, pix=pix, eps=eps)
+    ok = r.flags == 0
+    assert ok.mean() > min_ok, ok.mean()
+    err = np.abs(rgb.reshape(3, -1).T[pix] - r.rgb)[ok].max(initial=0.0)
+    errT = np.abs(T.reshape(-1)[pix] - r.T)[ok].max(initial=0.0)
+    assert err <= tol and errT <= tol, (err, errT)
+    return r
+
+
+def test_full_size_c3_fisheye_sampled(cg, oracle_lib):
+    """The differentiation workload's camera and scene at full size: a 190-degree
+    Kannala-Brandt fisheye at 1024x1024 and 1M Gaussians; sampled pixels against
+    the oracle, the pair counts of sampled Gaussians bit-exact."""
+    cam, sc = S.c3_camera(), S.c3_scene()
+    ctx, v = _setup(cg, cam, sc)
+    rgb, T = v.render()
+    r = _sampled_parity(oracle_lib, cam, sc, rgb.cpu().numpy(), T.cpu().numpy(), 400, seed=3)
+    assert (r.ncontrib > 0).mean() > 0.2
+    pg, _ = v.bin_counts()
+    sub = np.random.default_rng(4).choice(sc.n, size=3000, replace=False)
+    _, opg, _, _ = oracle_lib.bin_counts(cam, sc.subset(sub))
+    assert np.array_equal(pg.cpu().numpy()[sub], opg)
+
+
+def test_full_size_c4_rig_bf16_sampled(cg, oracle_lib):
+    """The eight-camera rig (4 pinhole, 4 fisheye at 1, 1/2, 1/4, 1/8 of 1080p), 3M
+    Gaussians with the Eq. 11 floor over the rig, SH and opacity stored in BF16: every
+    view on sampled pixels against the oracle on the quantised values (FP32 arithmetic:
+    1e-4) and on the FP32 values (the storage's budget: 2e-3, away from thresholds)."""
+    rig = S.c4_rig()
+    sc = S.blob_scene(3_000_000, seed=0, cam=rig[0])
+    ctx = cg.Context(0)
+    ctx.set_scene_from(sc, storage=torch.bfloat16)
+    views = []
+    for c in rig:
+        v = ctx.view()
+        v.set_camera_from(c)
+        views.append(v)
+    rho2 = ctx.compute_floor(views)
+    ctx.set_scene_from(sc, storage=torch.bfloat16, rho2=rho2)
+    sc = sc.with_rho2(rho2.cpu().numpy())
+    q = S.quantized(sc, "bf16")
+    outs = ctx.render_batch(views, streams=[torch.cuda.Stream() for _ in views])
+    torch.cuda.synchronize()
+    for k, (cam, (rgb, T)) in enumerate(zip(rig, outs)):
+        rgb, T = rgb.cpu().numpy(), T.cpu().numpy()
+        _sampled_parity(oracle_lib, cam, q, rgb, T, 80, seed=10 + k)
+        _sampled_parity(oracle_lib, cam, sc, rgb, T, 80, seed=10 + k, tol=2e-3, eps=5e-3, min_ok=0.8)
+
+
+def test_full_size_c5_request_4k_fp16_sampled(cg, oracle_lib):
+    """The largest serving request: 3840x2160 of the 5M-Gaussian scene with SH degree 3
+    stored in FP16 (floor from the rig), through a fisheye and a pinhole."""
+    rig = S.c4_rig()
+    sc = S.blob_scene(5_000_000, seed=0, cam=rig[0])
+    ctx = cg.Context(0)
+    ctx.set_scene_from(sc, storage=torch.float16)
+    vs = []
+    for c in rig:
+        v = ctx.view()
+        v.set_camera_from(c)
+        vs.append(v)
+    rho2 = ctx.compute_floor(vs)
+    ctx.set_scene_from(sc, storage=torch.float16, rho2=rho2)
+    sc = S.quantized(sc.with_rho2(rho2.cpu().numpy()), "f16")
+    pose = rig[2].cam_to_world
+    for k, cam in enumerate([S.pinhole(3840, 2160, 3840 * 60.0 / 64.0, cam_to_world=pose),
+                             S.kb_fisheye(3840, 2160, rig[4].k, cam_to_world=pose)]):
+        v = ctx.view()
+        v.set_camera_from(cam)
+        rgb, T = v.render()
+        _sampled_parity(oracle_lib, cam, sc, rgb.cpu().numpy(), T.cpu().numpy(), 150, seed=20 + k)
