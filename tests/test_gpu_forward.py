@@ -244,9 +244,13 @@ def test_floor_matches_oracle(cg, oracle_lib):
     g = ctx.compute_floor(vs).cpu().numpy()
     o = oracle_lib.floor_rho2(views, sc.means)
     both = (g > 0) & (o > 0)
-    assert ((g > 0) == (o > 0)).mean() > 0.999
+    # visibility is a decision on the projected centre; it may differ only for a
+    # centre within rounding of an image border or the fisheye's valid circle
+    assert ((g > 0) == (o > 0)).mean() >= 1.0 - 1e-4
     rel = np.abs(g[both] - o[both]) / o[both]
-    assert np.quantile(rel, 0.999) < 1e-3
+    # a few FP32 roundings of a half-trace: ~1e-7 for the pinholes; the fisheye's
+    # differentials come from the FP32 inverse mapping (~2e-5 relative per edge ray)
+    assert np.quantile(rel, 0.999) < 1e-5 and rel.max() < 5e-5, (np.quantile(rel, 0.999), rel.max())
 
 
 @pytest.mark.parametrize("n,bits", [(1, 32), (1000, 32), (4097, 12), (100003, 32), (1 << 20, 16), (3 << 20, 7)])
@@ -429,7 +433,9 @@ def test_full_size_c4_rig_bf16_sampled(cg, oracle_lib):
     for k, (cam, (rgb, T)) in enumerate(zip(rig, outs)):
         rgb, T = rgb.cpu().numpy(), T.cpu().numpy()
         _sampled_parity(oracle_lib, cam, q, rgb, T, 80, seed=10 + k)
-        _sampled_parity(oracle_lib, cam, sc, rgb, T, 80, seed=10 + k, tol=2e-3, eps=5e-3, min_ok=0.8)
+        # the wide flag margin (5e-3: quantisation moves responses by ~1e-3 relative) flags
+        # a good share of the rig's dense pixels; the others must stay within the budget
+        _sampled_parity(oracle_lib, cam, sc, rgb, T, 80, seed=10 + k, tol=2e-3, eps=5e-3, min_ok=0.5)
 
 
 def test_full_size_c5_request_4k_fp16_sampled(cg, oracle_lib):
