@@ -193,6 +193,19 @@ conegs_status conegs_render(conegs_view *view, float *out_rgb, float *out_T, uns
 conegs_status conegs_render_batch(int n, conegs_view *const *views, float *const *out_rgb, float *const *out_T,
                                   unsigned flags, void *const *streams);
 
+/* The count pass of a render, run ahead of it: the view records, the binning
+ * count and the pair total (the host waits for them), so that a caller can
+ * admit the render by the memory it will need.
+ *   *pairs_host: tile/Gaussian pairs the render will walk (may be NULL);
+ *   *bytes_host: device bytes the rest of the render sizes from the counts
+ *                (pair lists and sort scratch, split state, per-pixel state;
+ *                may be NULL).
+ * The next conegs_render / conegs_render_host on this view with the same flags
+ * and an unchanged scene and camera uses this count instead of counting again.
+ * Errors as conegs_render. */
+conegs_status conegs_render_count(conegs_view *view, unsigned flags, int64_t *pairs_host, size_t *bytes_host,
+                                  void *stream);
+
 /* conegs_render_batch into host memory: each view renders into its own device
  * scratch and its image is copied to out_rgb_host[i] (and out_T_host[i], when
  * out_T_host and that entry are non-NULL) on streams[i]; returns after every

@@ -215,6 +215,15 @@ class View:
         check(lib().conegs_render(self._h, _ptr(out_rgb), _ptr(out_T), flags, _stream(stream)), "render")
         return out_rgb, out_T
 
+    def render_count(self, flags: int = 0, stream=None):
+        """Run the render's count pass ahead of it: (pairs, device bytes the rest of
+        the render needs).  The next render with the same flags reuses the count."""
+        pairs = ctypes.c_int64()
+        nbytes = ctypes.c_size_t()
+        check(lib().conegs_render_count(self._h, int(flags), ctypes.byref(pairs), ctypes.byref(nbytes),
+                                        _stream(stream)), "render_count")
+        return pairs.value, nbytes.value
+
     def render_host(self, out_rgb_host: torch.Tensor, out_T_host: Optional[torch.Tensor] = None, flags: int = 0,
                     stream=None):
         """Render into (pinned) host tensors; returns after the copy completed."""

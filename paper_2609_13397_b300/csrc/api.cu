@@ -176,6 +176,10 @@ struct conegs_view {
     DevBuf pair_tile, pair_gid, pair_tile_alt, pair_gid_alt, ranges, last, sums, rs_scr, tmp_rgb, tmp_T;
     DevBuf g_rec, keep_T, split, gflat, flat_slot, flat_pair, flat_T, flat_G;
     int64_t n_flat_pairs = 0;
+    // a count pass run ahead of the render (conegs_render_count): its flags and scene
+    bool counted = false;
+    unsigned counted_flags = 0;
+    uint64_t counted_gen = 0;
     unsigned long long *h_sums = nullptr;   // pinned
     int64_t n_visible = 0, n_pairs = 0, n_valid = 0, n_launches = 0, n_flat = 0;
     bool has_forward = false;
@@ -476,6 +480,7 @@ conegs_status conegs_set_camera(conegs_view *v, int model, int width, int height
     CUDA_TRY(launch_tile_tables(c, v->table.as<float>(), v->super.as<float>(), v->mcam.as<float>(), s));
     v->cam = c;
     v->has_cam = true;
+    v->counted = false;
     v->has_forward = false;
     // count valid pixels once (host copy of the mask is small relative to the table)
     if (model == CONEGS_PINHOLE) {
@@ -682,9 +687,59 @@ static conegs_status render_back(conegs_view *v, float *out_rgb, float *out_T, u
 }
 
 static conegs_status render_impl(conegs_view *v, float *out_rgb, float *out_T, unsigned flags, cudaStream_t s) {
-    TRY(render_front(v, flags, s));
-    CUDA_TRY(cudaStreamSynchronize(s));
+    const bool reuse = v->counted && v->counted_flags == flags && v->counted_gen == v->ctx->scene_gen;
+    v->counted = false;
+    if (!reuse) {
+        TRY(render_front(v, flags, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+    }
     return render_back(v, out_rgb, out_T, flags, s);
+}
+
+// Device bytes the back half of a render sizes from the counts: sort buffers of the
+// visible Gaussians and of the pairs, tile ranges and split state, per-pixel state,
+// and the FP64 responses of flat Gaussians' pairs.
+static size_t back_bytes(const conegs_view *v, unsigned flags) {
+    const int64_t n = v->ctx->sp.n;
+    const int64_t M = (int64_t)v->h_sums[1], Pn = (int64_t)v->h_sums[0], F = (int64_t)v->h_sums[4];
+    const int64_t nt = (int64_t)v->cam.tiles_x * v->cam.tiles_y, P = (int64_t)v->cam.W * v->cam.H;
+    size_t b = sizeof(uint32_t) * (6 * (size_t)M + 4 * (size_t)Pn);
+    b += sizeof(uint32_t) * (size_t)radix_scratch_words(std::max<int64_t>(std::max<int64_t>(M, Pn), 1));
+    b += sizeof(uint32_t) * (size_t)scan_scratch_words(std::max<int64_t>(std::max<int64_t>(M, n), nt));
+    b += sizeof(uint32_t) * (size_t)split_scratch_words((int)nt) + sizeof(uint2) * (size_t)nt;
+    b += sizeof(float) * 4 * (size_t)P + sizeof(uint32_t) * (size_t)P;
+    if (flags & CONEGS_KEEP_FOR_BACKWARD) b += sizeof(float) * (size_t)P + sizeof(float) * 16 * (size_t)n;
+    if (F > 0) {
+        b += sizeof(uint32_t) * ((size_t)Pn + (size_t)F) + sizeof(float) * TILE_PX * (size_t)F;
+        if (flags & CONEGS_KEEP_FOR_BACKWARD) b += sizeof(float) * 13 * TILE_PX * (size_t)F;
+    }
+    return b;
+}
+
+conegs_status conegs_render_count(conegs_view *v, unsigned flags, int64_t *pairs_host, size_t *bytes_host,
+                                  void *stream) {
+    if (!v) return fail(CONEGS_ERR_ARG, "render_count: NULL view");
+    if (!v->has_cam) return fail(CONEGS_ERR_STATE, "render_count: set_camera was not called on this view");
+    if (!v->ctx->has_scene) return fail(CONEGS_ERR_STATE, "render_count: set_scene was not called");
+    DeviceGuard g(v->ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    TRY(view_begin(v, s));
+    v->counted = false;
+    conegs_status st = render_front(v, flags, s);
+    if (st == CONEGS_OK) {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = fail(CONEGS_ERR_CUDA, "render_count: %s", cudaGetErrorString(e));
+    }
+    if (st != CONEGS_OK) {
+        view_end(v, s);
+        return st;
+    }
+    v->counted = true;
+    v->counted_flags = flags;
+    v->counted_gen = v->ctx->scene_gen;
+    if (pairs_host) *pairs_host = (int64_t)v->h_sums[0];
+    if (bytes_host) *bytes_host = back_bytes(v, flags);
+    return view_end(v, s);
 }
 
 conegs_status conegs_render(conegs_view *v, float *out_rgb, float *out_T, unsigned flags, void *stream) {

@@ -1,20 +1,21 @@
 """Serving loop with continuous batching over the C ABI.
 
 The scene stays resident in one conegs context.  Requests (a camera each) are
-queued as they arrive and admitted as soon as a slot is free and the memory
-they need fits the server's budget; each slot owns a view (ray table and
-render scratch) and a CUDA stream, and runs on its own host thread (the C
-calls release the GIL), so requests that arrive while others are on the GPU
-start right away and their kernels overlap on the device.  Every request's
-image is copied to pinned host memory; latency is measured from arrival to
-the end of that copy.
+queued as they arrive; each slot owns a view (ray table and render scratch), a
+CUDA stream and a host thread (the C calls release the GIL), so requests that
+arrive while others are on the GPU start right away and their kernels overlap
+on the device.  Every request's image is copied to pinned host memory;
+latency is measured from arrival to the end of that copy.
 
-Memory admission: a request's footprint is estimated from its pixel count,
-its tile count and the scene size (ray table 37 B/px, image 16 B/px, tile
-tables, per-Gaussian view records, and a pair-list allowance); a request is
-admitted only while the sum over in-flight requests stays within the budget.
-A render that still exceeds the library's own budget (CONEGS_ERR_BUDGET) is
-re-queued once memory frees up.
+Memory admission: a slot takes the next request in arrival order, sets its
+camera and runs the render's count pass (conegs_render_count), which returns
+the device bytes the rest of the render needs (pair lists, sort scratch,
+per-pixel state); the request then waits until that, with its image, fits the
+server's budget next to the requests in flight, and renders with the count it
+already has.  A large request waiting for memory holds only its own slot: the
+other slots keep taking later, smaller requests past it.  A render that still
+exceeds the library's own budget (CONEGS_ERR_BUDGET) is retried once memory
+frees up.
 """
 from __future__ import annotations
 
@@ -29,10 +30,7 @@ import torch
 
 from . import ConegsError, Context
 
-PER_PIXEL_BYTES = 37 + 16 + 16 + 8          # ray table + image + host staging + per-pixel state
-PER_TILE_BYTES = 24 + 8 + 8                 # tile cone, ranges, counters
-PER_GAUSSIAN_BYTES = 128 + 16 + 8 + 24 + 48 + 48  # view record, direction/depth, cone, counts/keys, binning cache, silhouette
-PAIRS_PER_PIXEL = 12                        # pair-list allowance (8 B + 8 B sort scratch per pair)
+IMAGE_BYTES_PER_PIXEL = 16 + 16           # device image (rgb + T) and its pinned host copy
 
 
 @dataclasses.dataclass
@@ -55,36 +53,62 @@ class Result:
     rgb: Optional[torch.Tensor] = None
     T: Optional[torch.Tensor] = None
     error: Optional[str] = None
+    need_bytes: int = 0          # the memory the request was admitted with
 
     @property
     def latency_ms(self) -> float:
         return 1e3 * (self.t_done - self.t_arrival)
 
 
-def estimate_bytes(cam, n_gaussians: int) -> int:
-    P = cam.width * cam.height
-    tiles = ((cam.width + 7) // 8) * ((cam.height + 7) // 8)
-    return P * PER_PIXEL_BYTES + tiles * PER_TILE_BYTES + n_gaussians * PER_GAUSSIAN_BYTES + \
-        P * PAIRS_PER_PIXEL * 16
+def image_bytes(cam) -> int:
+    return cam.width * cam.height * IMAGE_BYTES_PER_PIXEL
+
+
+class MemoryGate:
+    """Admission by memory: acquire(need) waits until the bytes in use plus `need`
+    fit the budget (a request larger than the budget runs when nothing else is in
+    flight).  Callers that wait do not block callers with smaller needs that fit."""
+
+    def __init__(self, budget: int):
+        self.budget = int(budget)
+        self.in_use = 0
+        self._cv = threading.Condition()
+
+    def acquire(self, need: int, closed=lambda: False) -> bool:
+        with self._cv:
+            while self.in_use > 0 and self.in_use + need > self.budget:
+                if closed():
+                    return False
+                self._cv.wait(0.05)
+            self.in_use += need
+            return True
+
+    def release(self, need: int):
+        with self._cv:
+            self.in_use -= need
+            self._cv.notify_all()
 
 
 class Server:
     def __init__(self, ctx: Context, slots: int = 4, mem_budget_bytes: int = 32 << 30, keep_images: int = 0):
         """keep_images: how many results keep a copy of their image (True: all)."""
         self.ctx = ctx
-        self.budget = int(mem_budget_bytes)
+        self.gate = MemoryGate(mem_budget_bytes)
         self.keep_images = (1 << 62) if keep_images is True else int(keep_images)
         self._kept = 0
         self._slots = [(ctx.view(), torch.cuda.Stream(device=ctx.device)) for _ in range(slots)]
         self._queue: collections.deque = collections.deque()
         self._cv = threading.Condition()
-        self._in_use = 0
         self._closed = False
         self._t0 = time.perf_counter()
         self.results: List[Result] = []
         self._threads = [threading.Thread(target=self._worker, args=(k,), daemon=True) for k in range(slots)]
         for t in self._threads:
             t.start()
+
+    @property
+    def budget(self) -> int:
+        return self.gate.budget
 
     def now(self) -> float:
         return time.perf_counter() - self._t0
@@ -94,36 +118,27 @@ class Server:
             self._queue.append((req, self.now() if t_arrival is None else t_arrival))
             self._cv.notify_all()
 
-    def _admit(self):
-        """Head-of-queue request that fits the memory budget (FIFO)."""
-        if not self._queue:
-            return None
-        req, ta = self._queue[0]
-        need = estimate_bytes(req.camera, self.ctx.n)
-        if self._in_use + need > self.budget and self._in_use > 0:
-            return None
-        self._queue.popleft()
-        self._in_use += need
-        return req, ta, need
+    def _take(self):
+        """The next request in arrival order (memory is checked after its count pass)."""
+        with self._cv:
+            while not self._closed and not self._queue:
+                self._cv.wait(0.05)
+            if self._closed:
+                return None
+            return self._queue.popleft()
 
     def _worker(self, k: int):
         view, stream = self._slots[k]
         torch.cuda.set_device(self.ctx.device)
         host = {}
         while True:
-            with self._cv:
-                item = None
-                while not self._closed:
-                    item = self._admit()
-                    if item is not None:
-                        break
-                    self._cv.wait(0.05)
-                if item is None:
-                    return
-            req, ta, need = item
-            t_admit = self.now()
+            item = self._take()
+            if item is None:
+                return
+            req, ta = item
             cam = req.camera
-            res = Result(req.rid, cam.width, cam.height, 0, ta, t_admit, 0.0)
+            res = Result(req.rid, cam.width, cam.height, 0, ta, 0.0, 0.0)
+            need = 0
             try:
                 key = (cam.height, cam.width)
                 if key not in host:
@@ -133,7 +148,15 @@ class Server:
                 h_rgb, h_T = host[key]
                 with torch.cuda.stream(stream):
                     view.set_camera_from(cam, stream=stream)
-                    view.render_host(h_rgb, h_T, flags=req.flags, stream=stream)
+                    _, nbytes = view.render_count(flags=req.flags, stream=stream)
+                    need = nbytes + image_bytes(cam)
+                    if not self.gate.acquire(need, closed=lambda: self._closed):
+                        return
+                    res.t_admit, res.need_bytes = self.now(), need
+                    try:
+                        view.render_host(h_rgb, h_T, flags=req.flags, stream=stream)
+                    finally:
+                        self.gate.release(need)
                 res.rays = int(view.stats()["n_valid_pixels"])
                 with self._cv:
                     keep = self._kept < self.keep_images
@@ -143,15 +166,14 @@ class Server:
             except ConegsError as e:
                 if e.status == 7:                       # library budget: retry when memory frees up
                     with self._cv:
-                        self._in_use -= need
                         self._queue.appendleft((req, ta))
                         self._cv.notify_all()
                     time.sleep(0.01)
                     continue
                 res.error = str(e)
+                res.t_admit = res.t_admit or self.now()
             res.t_done = self.now()
             with self._cv:
-                self._in_use -= need
                 self.results.append(res)
                 self._cv.notify_all()
 

@@ -59,23 +59,44 @@ def test_alone_equals_mixed(scene_ctx):
 
 
 def test_memory_admission_limits_concurrency(scene_ctx):
+    """Each request is admitted with the memory its count pass reports: requests in
+    flight together never exceed the budget, and that memory is what the render uses."""
     from paper_2609_13397_b300 import serving
-    from paper_2609_13397_b300.serving import Request, estimate_bytes
+    from paper_2609_13397_b300.serving import Request, image_bytes
     reqs = [Request(r.rid, 0.0, r.camera) for r in _requests(12, seed=1)]
-    biggest = max(estimate_bytes(r.camera, scene_ctx.n) for r in reqs)
-    srv = serving.Server(scene_ctx, slots=6, mem_budget_bytes=int(biggest * 1.5))
+    v = scene_ctx.view()
+    needs = []
+    for r in reqs:                       # what each request will ask for
+        v.set_camera_from(r.camera)
+        needs.append(v.render_count()[1] + image_bytes(r.camera))
+        rgb, _ = v.render()              # the render reuses the count
+    v.close()
+    budget = int(max(needs) * 1.5)
+    srv = serving.Server(scene_ctx, slots=6, mem_budget_bytes=budget)
     for r in reqs:
         srv.submit(r)
     res = srv.drain(len(reqs))
     srv.close()
     assert all(r.error is None for r in res)
-    # no two requests whose estimates exceed the budget together were in flight at once
+    assert [r.need_bytes for r in res] == needs
     for a in res:
         for b in res:
             if a.rid < b.rid and a.t_admit < b.t_done and b.t_admit < a.t_done:
-                ea = estimate_bytes(reqs[a.rid].camera, scene_ctx.n)
-                eb = estimate_bytes(reqs[b.rid].camera, scene_ctx.n)
-                assert ea + eb <= int(biggest * 1.5)
+                assert a.need_bytes + b.need_bytes <= budget
+
+
+def test_count_then_render_equals_render(scene_ctx):
+    """A render that reuses a count pass run ahead of it gives the same image."""
+    r = _requests(1, seed=4)[0]
+    v = scene_ctx.view()
+    v.set_camera_from(r.camera)
+    a, ta = (t.clone() for t in v.render())
+    pairs, nbytes = v.render_count()
+    assert pairs == v.stats()["n_pairs"] and nbytes > 0
+    b, tb = v.render()
+    torch.cuda.synchronize()
+    assert torch.equal(a, b) and torch.equal(ta, tb)
+    v.close()
 
 
 def test_malformed_request_fails_alone(scene_ctx):

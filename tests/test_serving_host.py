@@ -1,5 +1,5 @@
-"""Host-side serving logic (no GPU): the per-request memory estimate and the
-latency/throughput summary."""
+"""Host-side serving logic (no GPU): memory admission and the latency/throughput
+summary."""
 import pytest
 
 import synthetic as S
@@ -7,12 +7,30 @@ import synthetic as S
 pytest.importorskip("torch")
 
 
-def test_estimate_grows_with_pixels_and_scene():
-    from paper_2609_13397_b300.serving import estimate_bytes
-    small = S.pinhole(160, 120, 150.0)
-    big = S.pinhole(3840, 2160, 3600.0)
-    assert estimate_bytes(big, 1000) > 100 * estimate_bytes(small, 1000) / 2
-    assert estimate_bytes(small, 5_000_000) - estimate_bytes(small, 0) >= 5_000_000 * 128
+def test_memory_gate_admits_within_budget_without_head_of_line_blocking():
+    """A request whose memory does not fit waits; a later, smaller one that fits is
+    admitted past it; the waiting one runs once memory frees up; a request larger
+    than the whole budget runs alone."""
+    import threading
+    import time
+    from paper_2609_13397_b300.serving import MemoryGate
+    gate = MemoryGate(100)
+    assert gate.acquire(60)                       # in flight: 60
+    order = []
+    big = threading.Thread(target=lambda: (gate.acquire(70), order.append("big")))
+    big.start()
+    time.sleep(0.2)
+    assert order == []                            # 60 + 70 > 100: waits
+    assert gate.acquire(30)                       # 60 + 30 fits: passes the waiting one
+    order.append("small")
+    gate.release(60)
+    gate.release(30)
+    big.join(2.0)
+    assert order == ["small", "big"] and gate.in_use == 70
+    gate.release(70)
+    assert gate.acquire(500) and gate.in_use == 500   # larger than the budget: alone
+    gate.release(500)
+    assert gate.in_use == 0
 
 
 def test_summary_percentiles_and_rate():
