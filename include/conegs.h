@@ -94,7 +94,16 @@ enum {
      * Approximate: a pair the ellipse misses is not evaluated.  Gaussians with a sigma
      * point outside the camera's domain (pinhole: p_z < 0.1 |p|; fisheye: beyond
      * theta_lim) keep the angular-tile rule. */
-    CONEGS_BIN_UT = 1u << 6
+    CONEGS_BIN_UT = 1u << 6,
+    /* Per-ray compositing order (Sec. 3: pairs composited by their max-response depth
+     * t*_k): each pixel re-orders the pairs of its tile list by its own t* through a
+     * k-buffer of 32 pairs (per pixel), instead of the tile list's per-Gaussian key
+     * |mu - o|.  Exactly the per-pixel t* order (ties: key, then index) whenever a
+     * pixel has at most 32 pairs with alpha >= 1/255 before it stops, and whenever no
+     * contributing pair is displaced by 32 or more contributing pairs between the two
+     * orders; otherwise an approximation of it.  Forward only: with
+     * CONEGS_KEEP_FOR_BACKWARD the render fails with CONEGS_ERR_ARG. */
+    CONEGS_ORDER_TSTAR = 1u << 7
 };
 
 typedef struct conegs_ctx conegs_ctx;

@@ -189,9 +189,11 @@ def render(cam, scene, pix: Optional[Sequence[int]] = None, filter: int = FILTER
            comp: int = COMP_MARGINAL, cull: bool = True, eps: float = 1e-5, eps_key: float = 0.0,
            max_used: int = 0, order: int = 0, gate: Optional[np.ndarray] = None) -> Render:
     """Render pixels (indices into the row-major W x H grid; None = all).  order: 0
-    the canonical per-Gaussian key |mu - o|, 1 the exact per-ray t* order.  gate: a
-    [n, ntiles] UT gate (``ut_gate``): only kept tiles are evaluated; pixels where an
-    ambiguous entry contributes get FL_UT_NEAR."""
+    the canonical per-Gaussian key |mu - o|, 1 the exact per-ray t* order (with
+    eps_key > 0, near ties in t* between pairs that may contribute set FL_KEY_TIE).
+    gate: a [n, ntiles] UT gate (``ut_gate``): only kept tiles are evaluated; pixels
+    where an ambiguous entry contributes get FL_UT_NEAR.  The result's ``nalpha``:
+    per pixel, the pairs with T >= 1/255 (reached before the stop or not)."""
     if gate is not None:
         gate = np.ascontiguousarray(gate, np.uint8)
         tx, ty = tile_grid(cam)
@@ -207,14 +209,17 @@ def render(cam, scene, pix: Optional[Sequence[int]] = None, filter: int = FILTER
     flags = np.zeros(npix, np.int32)
     ncon = np.zeros(npix, np.int32)
     used = np.full((npix, max(max_used, 1)), -1, np.int32)
+    nalpha = np.zeros(npix, np.int32)
     lib().or_render(_p(pack_camera(cam)), ctypes.c_int(n), _p(_d(scene.means)), _p(_d(scene.log_scales)),
                     _p(_d(scene.quats)), _p(_d(scene.opacity_logits)), _p(_d(scene.sh)),
                     ctypes.c_int(scene.sh_degree), _p(_d(scene.rho2)), ctypes.c_int(filter), ctypes.c_int(comp),
                     ctypes.c_int(npix), pptr, ctypes.c_int(int(cull)), ctypes.c_double(eps),
                     ctypes.c_double(eps_key), _p(rgb), _p(T), _p(flags, ctypes.c_int), _p(ncon, ctypes.c_int),
                     _p(used, ctypes.c_int) if max_used > 0 else None, ctypes.c_int(max_used), ctypes.c_int(order),
-                    _p(gate, ctypes.c_ubyte) if gate is not None else None)
-    return Render(rgb, T, flags, ncon, pix_arr, used if max_used > 0 else None)
+                    _p(gate, ctypes.c_ubyte) if gate is not None else None, _p(nalpha, ctypes.c_int))
+    r = Render(rgb, T, flags, ncon, pix_arr, used if max_used > 0 else None)
+    r.nalpha = nalpha
+    return r
 
 
 def render_subrays(cam, scene, pix: Optional[Sequence[int]] = None, nsub: int = 8, order: int = 0):

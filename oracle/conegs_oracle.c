@@ -496,7 +496,12 @@ static void prep_all(const ocam *c, const oscene *s, ogauss *g) {
  * T >= 1/255 has q^T A^-1 q <= kappa^2 = 2 ln(255 sigma), so the
  * perpendicular distance from mu to the ray is at most
  * kappa sqrt(s_max^2 + t*^2 m), m = (|dx|^2+|dy|^2)/3, and
- * t* <= (L + kappa s_max) / (1 - kappa (1 + s_max/s_min) sqrt(m)). */
+ * t* <= (L + kappa s_max) / (1 - kappa r1 sqrt(m)), r1 = (r + 1/r)/2 with
+ * r = s_max/s_min: the world half-edges f_i = delta_i - c_i d (Eq. 6 mapped
+ * back to world space) keep delta_i's part across d, and their part along d
+ * is at most beta |delta_i|, beta = max_d |P_perp Sigma^-1 d| / d^T Sigma^-1 d
+ * = (r - 1/r)/2 (the two extreme eigenvalues of Sigma^-1), so
+ * |f_i| <= sqrt(1 + beta^2) |delta_i| = r1 |delta_i|. */
 static int oracle_keep(const ogauss *g, const double o[3], const double d[3], double m) {
     double k2 = 2.0 * log(255.0 * g->sig);
     if (!(k2 > 0)) return 0;
@@ -506,7 +511,7 @@ static int oracle_keep(const ogauss *g, const double o[3], const double d[3], do
         smax = g->seff[i] > smax ? g->seff[i] : smax;
         smin = g->seff[i] < smin ? g->seff[i] : smin;
     }
-    double r1 = 1.0 + smax / smin, sm = sqrt(m), c = kap * r1 * sm, tb, rf;
+    double r = smax / smin, r1 = 0.5 * (r + 1.0 / r), sm = sqrt(m), c = kap * r1 * sm, tb, rf;
     if (c < 0.5) {
         tb = (g->L + kap * smax) / (1.0 - c);
         rf = kap * sqrt(smax * smax + tb * tb * r1 * r1 * m);
@@ -553,15 +558,32 @@ enum { ORDER_KEY = 0, ORDER_TSTAR = 1 };
 enum { FL_ALPHA_MIN = 1, FL_ALPHA_MAX = 2, FL_STOP = 4, FL_KEY_TIE = 8, FL_TNEAR = 16, FL_UT_NEAR = 32 };
 
 /* Composite one pixel's candidates (Eq. 4 with the 3DGS conventions). */
+/* *nalpha (optional): the number of candidates with T >= 1/255, whether or not
+ * the pixel reached them before its stop. */
 static void composite(cand *cs, int nc, const ogauss *g, double eps, double eps_key, double rgb[3],
-                      double *Tout, int *flags, int *ncontrib, int *used_idx, int max_used, int order) {
+                      double *Tout, int *flags, int *ncontrib, int *used_idx, int max_used, int order,
+                      int *nalpha) {
     qsort(cs, nc, sizeof(cand), order == ORDER_TSTAR ? cand_cmp_ts : cand_cmp);
+    if (nalpha) {
+        int na = 0;
+        for (int k = 0; k < nc; ++k) na += cs[k].T >= ALPHA_MIN;
+        *nalpha = na;
+    }
     double Tacc = 1.0, C[3] = {0, 0, 0};
-    int fl = 0, nu = 0;
+    int fl = 0, nu = 0, prev = -1;
     for (int k = 0; k < nc; ++k) {
         double T = cs[k].T;
         if (fabs(cs[k].ts - T_NEAR) <= eps * T_NEAR) fl |= FL_TNEAR;
-        if (eps_key > 0 && k > 0 && fabs(cs[k].L - cs[k - 1].L) <= eps_key * cs[k].L) fl |= FL_KEY_TIE;
+        if (order == ORDER_TSTAR) {
+            /* a near tie in t* between two pairs that may contribute: the order may
+             * go either way in another precision */
+            if (eps_key > 0 && T >= ALPHA_MIN * (1.0 - eps)) {
+                if (prev >= 0 && fabs(cs[k].ts - cs[prev].ts) <= eps_key * fabs(cs[k].ts)) fl |= FL_KEY_TIE;
+                prev = k;
+            }
+        } else if (eps_key > 0 && k > 0 && fabs(cs[k].L - cs[k - 1].L) <= eps_key * cs[k].L) {
+            fl |= FL_KEY_TIE;
+        }
         if (fabs(T - ALPHA_MIN) <= eps * ALPHA_MIN) fl |= FL_ALPHA_MIN;
         if (fabs(T - ALPHA_MAX) <= eps * ALPHA_MAX) fl |= FL_ALPHA_MAX;
         if (T < ALPHA_MIN) continue;
@@ -672,11 +694,13 @@ double or_bundle(const double *campk, double x, double y, const double *mu, cons
  * Outputs rgb[npix*3], T[npix], flags[npix], ncontrib[npix]; optionally the
  * ids of the contributing Gaussians (used[npix*max_used]).  gate (optional,
  * from or_ut_gate): the pixel's tile must be kept for a Gaussian to be
- * evaluated; a contributing pair whose gate entry is ambiguous sets FL_UT_NEAR. */
+ * evaluated; a contributing pair whose gate entry is ambiguous sets FL_UT_NEAR.
+ * nalpha (optional, [npix]): per pixel, the pairs with T >= 1/255. */
 void or_render(const double *campk, int n, const double *means, const double *log_scales, const double *quats,
                const double *logits, const double *sh, int deg, const double *rho2, int filter, int comp,
                int npix, const int *pix, int cull, double eps, double eps_key, double *rgb, double *Tout,
-               int *flags, int *ncontrib, int *used, int max_used, int order, const unsigned char *gate) {
+               int *flags, int *ncontrib, int *used, int max_used, int order, const unsigned char *gate,
+               int *nalpha) {
     ocam c;
     unpack_cam(campk, &c);
     oscene s = {n, deg, means, log_scales, quats, logits, sh, rho2};
@@ -698,6 +722,7 @@ void or_render(const double *campk, int n, const double *means, const double *lo
                 Tout[t] = 1.0;
                 flags[t] = 0;
                 ncontrib[t] = 0;
+                if (nalpha) nalpha[t] = 0;
                 continue;
             }
             footprint_variant(&c, filter, d, dx, dy);
@@ -721,7 +746,8 @@ void or_render(const double *campk, int n, const double *means, const double *lo
                 cs[nc].L = g[k].key; cs[nc].T = T; cs[nc].ts = ts; cs[nc].idx = k;
                 ++nc;
             }
-            composite(cs, nc, g, eps, eps_key, o_rgb, &Tout[t], &flags[t], &ncontrib[t], u, max_used, order);
+            composite(cs, nc, g, eps, eps_key, o_rgb, &Tout[t], &flags[t], &ncontrib[t], u, max_used, order,
+                      nalpha ? &nalpha[t] : NULL);
             if (utnear) flags[t] |= FL_UT_NEAR;
         }
         free(cs);
@@ -767,7 +793,7 @@ void or_render_subrays(const double *campk, int n, const double *means, const do
                     }
                     double sub_rgb[3], sub_T;
                     int fl, nu;
-                    composite(cs, nc, g, 0.0, 0.0, sub_rgb, &sub_T, &fl, &nu, NULL, 0, order);
+                    composite(cs, nc, g, 0.0, 0.0, sub_rgb, &sub_T, &fl, &nu, NULL, 0, order, NULL);
                     for (int q = 0; q < 3; ++q) acc[q] += sub_rgb[q];
                     accT += sub_T;
                     ++cnt;
@@ -1230,7 +1256,8 @@ static void fgauss(const fcam *c, const float *mu, const float *ls, const float 
     rec[0] = v0 / L; rec[1] = v1 / L; rec[2] = v2 / L;
     float kap = sqrtf(kap2);
     float s = sqrtf(s2);
-    float r1 = 1.0f + s / sqrtf(s2mn);
+    float rr = s / sqrtf(s2mn);
+    float r1 = fmaxf(((rr + 1.0f / rr) * 0.5f) * 1.00001f, 1.0f);
     rec[4] = kap;
     rec[5] = kap * s;
     rec[6] = kap * r1;

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(os.path.dirname(HERE), "_build")
 LIB = os.path.join(HERE, "libconegs.so")
 SOURCES = ["api.cu", "camera.cu", "binning.cu", "preprocess.cu", "sort.cu", "raster.cu", "backward.cu",
-           "floor.cu", "sort_noalloc.cu", "flat.cu", "peak.cu"]
+           "floor.cu", "sort_noalloc.cu", "flat.cu", "peak.cu", "tstar.cu"]
 HEADERS = ["common.cuh", "rule.cuh", "camera.cuh", "pair.cuh", "raster.cuh", "sh.cuh", "adjoint.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")

@@ -53,6 +53,7 @@ cudaError_t launch_floor(const CamParams *cams_dev, int nv, const float *means, 
                          cudaStream_t s);
 cudaError_t launch_raster_split(const RasterArgs &a, int ntiles, bool filter, uint32_t *scratch,
                                 uint32_t *scan_scratch, cudaStream_t s, cudaEvent_t main0, cudaEvent_t main1);
+cudaError_t launch_raster_tstar(const RasterArgs &a, int ntiles, bool filter, cudaStream_t s);
 cudaError_t launch_flat_pairs(const RasterArgs &a, const uint32_t *tiles, int64_t npairs, const uint8_t *gflat,
                               uint32_t *slot_of, uint32_t *slot_pair, unsigned long long *counter, int64_t nslots,
                               float *flat_T, float *flat_G, bool filter, cudaStream_t s);
@@ -526,6 +527,8 @@ static conegs_status render_front(conegs_view *v, unsigned flags, cudaStream_t s
     {
         const unsigned fp = flags & (CONEGS_FILTER_NONE | CONEGS_FILTER_ISO | CONEGS_FILTER_ZF);
         if (fp & (fp - 1u)) return fail(CONEGS_ERR_ARG, "render: FILTER_NONE, FILTER_ISO and FILTER_ZF exclude each other");
+        if ((flags & CONEGS_ORDER_TSTAR) && (flags & CONEGS_KEEP_FOR_BACKWARD))
+            return fail(CONEGS_ERR_ARG, "render: ORDER_TSTAR is forward only (no KEEP_FOR_BACKWARD)");
     }
     conegs_ctx *ctx = v->ctx;
     const CamParams &c = v->cam;
@@ -666,9 +669,15 @@ static conegs_status render_back(conegs_view *v, float *out_rgb, float *out_T, u
     a.evaluated = prof ? v->evaluated.as<unsigned long long>() : nullptr;
     TRY(ensure(ctx, v->split, sizeof(uint32_t) * (size_t)split_scratch_words(nt), s));
     TRY(ensure(ctx, v->scan_scr, sizeof(uint32_t) * (size_t)scan_scratch_words(std::max<int64_t>(std::max<int64_t>(M, n), nt)), s));
-    CUDA_TRY(launch_raster_split(a, nt, !(flags & CONEGS_FILTER_NONE), v->split.as<uint32_t>(),
-                                 v->scan_scr.as<uint32_t>(), s,
-                                 prof ? v->prof[4] : nullptr, prof ? v->prof[5] : nullptr));
+    if (flags & CONEGS_ORDER_TSTAR) {
+        if (prof) CUDA_TRY(cudaEventRecord(v->prof[4], s));
+        CUDA_TRY(launch_raster_tstar(a, nt, !(flags & CONEGS_FILTER_NONE), s));
+        if (prof) CUDA_TRY(cudaEventRecord(v->prof[5], s));
+    } else {
+        CUDA_TRY(launch_raster_split(a, nt, !(flags & CONEGS_FILTER_NONE), v->split.as<uint32_t>(),
+                                     v->scan_scr.as<uint32_t>(), s,
+                                     prof ? v->prof[4] : nullptr, prof ? v->prof[5] : nullptr));
+    }
     if (prof) {
         CUDA_TRY(cudaEventRecord(v->prof[3], s));
         CUDA_TRY(cudaMemcpyAsync(v->h_sums + 5, v->evaluated.p, 3 * sizeof(unsigned long long),

@@ -217,7 +217,8 @@ __global__ void __launch_bounds__(256) view_records_kernel(CamParams c, ScenePar
             C[0] = C[1] = C[2] = 100.0f;
         } else if (L > 0.0f) {
             float tb;
-            tstar_bound(sqrtf(k2), s2, 1.0f + sqrtf(s2 / s2mn), L, m, tb);
+            const float rr = sqrtf(s2 / s2mn);    // s_max / s_min; |f_i| <= (r + 1/r)/2 |delta_i|
+            tstar_bound(sqrtf(k2), s2, fmaxf(0.5f * (rr + 1.0f / rr) * 1.00001f, 1.0f), L, m, tb);
             cone_quadric(W, ou, 1.01f * k2, tb * tb * m * 1.001f, L, g, C);
         }
     }

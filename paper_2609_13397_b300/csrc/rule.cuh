@@ -129,7 +129,13 @@ static __device__ void rule_gauss_scene(const float ls[3], float logit, float rh
     }
     float kap = r_sqrt(kap2);
     float s = r_sqrt(s2);
-    float r1 = r_add(1.0f, r_div(s, r_sqrt(s2mn)));
+    // r1 bounds |f_i| / |delta_i| for the world half-edges f_i = delta_i - c_i d of
+    // Eq. 6 mapped back by W^-1: their part across d is delta_i's own, their part
+    // along d at most beta |delta_i| with beta = max |P_perp S^-1 d| / (d^T S^-1 d)
+    // = (r - 1/r) / 2, r = s_max / s_min (S = Sigma_eff), so r1 = sqrt(1 + beta^2)
+    // = (r + 1/r) / 2 (with a relative margin for the rounding)
+    float rr = r_div(s, r_sqrt(s2mn));
+    float r1 = fmaxf(r_mul(r_mul(r_add(rr, r_div(1.0f, rr)), 0.5f), 1.00001f), 1.0f);
     rec[0] = kap;
     rec[1] = r_mul(kap, s);
     rec[2] = r_mul(kap, r1);

@@ -139,3 +139,46 @@ def test_binning_is_conservative_random(oracle_lib, seed):
     tile = (pix // cam.width) // O.TILE * tx + (pix % cam.width) // O.TILE
     missed = pas[g, tile] == 0
     assert missed.sum() == 0, f"{missed.sum()} of {pix.size} contributing pairs not binned"
+
+
+def _lowres_case(seed):
+    """A very low-resolution camera (12-40 px wide: large footprints, so the t* bound
+    and its anisotropy factor decide most tiles) inside close, strongly anisotropic
+    Gaussians (log-scale std 1.5, shell from 0.3), some with the Eq. 11 floor."""
+    rng = np.random.default_rng(5000 + seed)
+    w = int(rng.integers(12, 40))
+    h = int(w * rng.uniform(0.56, 1.0))
+    eye = rng.normal(0, 0.3, 3)
+    pose = S.look_at(eye, eye + rng.normal(0, 1, 3) + np.array([0.0, 0.0, 2.0]))
+    if seed % 2 == 0:
+        f = float(rng.uniform(0.4, 1.2) * w)
+        cam = S.Camera(S.PINHOLE, w, h, f, f, w / 2, h / 2, cam_to_world=pose)
+    else:
+        base = S.c3_camera(w, w, seed=seed)
+        cam = S.Camera(base.model, w, h, base.fx, base.fy, w / 2, h / 2, k=base.k, cam_to_world=pose,
+                       theta_lim=base.theta_lim)
+    sc = S.blob_scene(1500, seed=seed, cam=S.pinhole(w, h, 0.8 * w, cam_to_world=pose), blob_frac=0.3,
+                      shell=(0.3, 3.0), log_scale_mean=float(rng.uniform(-3.0, -1.5)), log_scale_std=1.5,
+                      sh_degree=0)
+    return cam, sc
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_binning_is_conservative_lowres(oracle_lib, seed):
+    """Where the anisotropy factor of the t* bound, r1 = (r + 1/r)/2, decides:
+    no pair that can reach alpha >= 1/255 is lost."""
+    O = oracle_lib
+    cam, sc = _lowres_case(seed)
+    if seed % 3 == 0:
+        fcam = S.Camera(S.PINHOLE, 4 * cam.width, 4 * cam.height, 3.2 * cam.width, 3.2 * cam.width,
+                        2.0 * cam.width, 2.0 * cam.height, cam_to_world=cam.cam_to_world)
+        sc = sc.with_rho2(O.floor_rho2([fcam], sc.means).astype(np.float32))
+    total, pg, pt, pas = O.bin_counts(cam, sc, dense=True)
+    pix, g = O.pairs_above(cam, sc, (1.0 / 255.0) * (1 - 1e-3))
+    assert pix.size > 1000
+    tx, _ = O.tile_grid(cam)
+    tile = (pix // cam.width) // O.TILE * tx + (pix % cam.width) // O.TILE
+    missed = pas[g, tile] == 0
+    assert missed.sum() == 0, f"{missed.sum()} of {pix.size} contributing pairs not binned"
+    # not every Gaussian may pass every tile (the bound must decide somewhere)
+    assert total < (pg > 0).sum() * pt.size

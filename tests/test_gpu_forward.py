@@ -51,6 +51,13 @@ def _cases():
                     cam_to_world=S.look_at((0.1, 0.0, 0.1), (-1.0, 0.5, 2.0)), theta_lim=fcam.theta_lim)
     out["kb_surround"] = (fcam, S.blob_scene(3000, seed=17, cam=S.pinhole(112, 96, 60.0), blob_frac=0.3,
                                              shell=(1.5, 4.0), log_scale_mean=-2.5, sh_degree=1))
+    # very low resolution fisheye among close, strongly anisotropic Gaussians: the
+    # t* bound's anisotropy factor decides most tiles
+    lcam = S.c3_camera(24, 20, seed=1)
+    lcam = S.Camera(lcam.model, 24, 20, lcam.fx, lcam.fy, 12.0, 10.0, k=lcam.k,
+                    cam_to_world=S.look_at((0.1, -0.2, 0.0), (0.4, 0.3, 2.0)), theta_lim=lcam.theta_lim)
+    out["lowres_kb"] = (lcam, S.blob_scene(1500, seed=31, cam=S.pinhole(24, 20, 19.0), blob_frac=0.3,
+                                           shell=(0.3, 3.0), log_scale_mean=-2.2, log_scale_std=1.5, sh_degree=1))
     return out
 
 

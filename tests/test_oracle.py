@@ -663,3 +663,30 @@ def test_flat_gaussians_world_space_form(oracle_lib, kind, pose):
             assert abs(r["T"] - want) <= 2e-6 + 1e-9 * want, (k, p, r["T"], want)
             checked += 1
     assert checked > 250
+
+
+def test_render_nalpha_and_tstar_tie_flag(oracle_lib):
+    """nalpha counts every pair with T >= 1/255: where no pixel stops (C1 scene, T
+    stays above 1e-4), that is exactly the pairs composited, in either order.  In
+    the per-ray order, stacked Gaussians (identical t*) raise the tie flag; well
+    separated ones do not."""
+    O = oracle_lib
+    cam, sc = S.c1()
+    for order in (0, 1):
+        r = O.render(cam, sc, order=order, eps=0.0)
+        assert (r.T > 1e-3).all()
+        assert np.array_equal(r.nalpha, r.ncontrib)
+    cam = S.pinhole(16, 16, 20.0)
+
+    def stack(z):
+        n = len(z)
+        return S.Scene(means=np.array([[0.0, 0.0, zz] for zz in z], np.float32),
+                       log_scales=np.full((n, 3), np.log(0.3), np.float32),
+                       quats=np.tile(np.array([1, 0, 0, 0], np.float32), (n, 1)),
+                       opacity_logits=np.zeros(n, np.float32), sh=np.zeros((n, 1, 3), np.float32), sh_degree=0,
+                       rho2=np.zeros(n, np.float32))
+    c = 8 * 16 + 8
+    tie = O.render(cam, stack([3.0, 3.0]), pix=[c], order=1, eps=0.0, eps_key=1e-6)
+    sep = O.render(cam, stack([3.0, 3.5]), pix=[c], order=1, eps=0.0, eps_key=1e-6)
+    assert tie.flags[0] & O.FL_KEY_TIE and not sep.flags[0] & O.FL_KEY_TIE
+    assert tie.nalpha[0] == 2 and sep.nalpha[0] == 2
