@@ -513,8 +513,10 @@ def run_ours(args, rank, world, local_rank):
     with ClockSampler(local_rank) as clk:
         c2 = bench_c2(args, world, local_rank, peak)
         if world == 1 and not args.headline_only:
+            extra = [w.strip() for w in args.extra.split(",") if w.strip()]
             for name, fn in (("c3", bench_c3), ("c4", bench_c4), ("c5", bench_c5), ("c1", bench_c1)):
-                others[name] = fn(args)
+                if name in extra:
+                    others[name] = fn(args)
     line = {
         "metric": METRIC, "value": c2["value"], "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": c2["ms"], "higher_is_better": True, "scaling": "weak",
@@ -550,6 +552,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--headline-only", action="store_true", help="time the headline workload only")
+    ap.add_argument("--extra", default="c3,c4,c5,c1", help="the other workloads timed after the headline one")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--c5-requests", type=int, default=300)
     ap.add_argument("--c5-rate", type=float, default=200.0)

@@ -5,15 +5,17 @@
 namespace conegs {
 
 // Reverse-mode of pair_response<FILTER, true, R> given dL/dT, in the same
-// arithmetic type R.  Accumulates dL/dW (9, row-major), dL/do_u (3) and
-// returns dL/dsigma_eff.
+// arithmetic type R (divisions as products with Ops<R>::rcp: the SFU
+// reciprocal in FP32, the correctly rounded one in FP64).  Accumulates dL/dW
+// (9, row-major), dL/do_u (3) and returns dL/dsigma_eff.
 template <bool FILTER, typename R>
 __device__ __forceinline__ float pair_adjoint(const PairFwdT<R> &f, const GaussRec<R> &gr, const PixelRaysT<R> &px,
                                               float gT_in, float gW[9], float gou[3]) {
+    using O = Ops<R>;
     const R third = R(1) / R(3);
     const R gT = gT_in, sig = gr.sig, rho2 = gr.rho2;
     const R T = f.T;
-    const R gsig = sig > R(0) ? gT * T / sig : R(0);
+    const R gsig = sig > R(0) ? gT * T * O::rcp(sig) : R(0);
     const R gQ = R(-0.5) * T * gT;
     R gqq = R(0), gdu[3] = {R(0), R(0), R(0)}, gq[3] = {R(0), R(0), R(0)}, gts = R(0), ginv_n = R(0);
     R ggx[3] = {R(0), R(0), R(0)}, ggy[3] = {R(0), R(0), R(0)};
@@ -61,38 +63,42 @@ __device__ __forceinline__ float pair_adjoint(const PairFwdT<R> &f, const GaussR
             R gh00 = R(0), gh01 = R(0), gh11 = R(0);
             const R dh = h00 * h11 - h01 * h01;
             if (f.kcase == 1) {                              // K = (I - rho2 H'^-1)/3
-                const R s = rho2 / dh;
+                const R inv_dh = O::rcp(dh);
+                const R s = rho2 * inv_dh;
                 const R gs = (-gk00 * h11 - gk11 * h00 + gk01 * h01) * third;
                 gh11 += -gk00 * s * third;
                 gh00 += -gk11 * s * third;
                 gh01 += gk01 * s * third;
-                const R gdh = -gs * s / dh;
+                const R gdh = -gs * s * inv_dh;
                 gh00 += gdh * h11;
                 gh11 += gdh * h00;
                 gh01 += -R(2) * gdh * h01;
             } else {                                         // K = sc (H' - l2 I)
                 const R mean = R(0.5) * (h00 + h11), half = R(0.5) * (h00 - h11);
                 const R r2 = half * half + h01 * h01;
-                const R rad = r2 > R(0) ? Ops<R>::sqrt(r2) : R(0);
+                const R rad = O::root(r2);
                 const R l1 = mean + rad;
-                const R l2 = Ops<R>::max(dh, R(0)) / l1;
+                const R inv_l1 = O::rcp(l1);
+                const R l2 = O::max(dh, R(0)) * inv_l1;
                 const R D = R(3) * l1 * (l1 - l2);
-                const R sc = (l1 - rho2) / D;
+                const R inv_D = O::rcp(D);
+                const R sc = (l1 - rho2) * inv_D;
                 const R gsc = gk00 * (h00 - l2) + gk11 * (h11 - l2) + gk01 * h01;
                 gh00 += gk00 * sc;
                 gh11 += gk11 * sc;
                 gh01 += gk01 * sc;
                 R gl2 = -(gk00 + gk11) * sc;
-                const R gN = gsc / D, gD = -gsc * sc / D;
+                const R gN = gsc * inv_D, gD = -gsc * sc * inv_D;
                 R gl1 = gN + gD * R(3) * (R(2) * l1 - l2);
                 gl2 += gD * (-R(3) * l1);
-                const R gdh2 = dh > R(0) ? gl2 / l1 : R(0);
-                gl1 += -gl2 * l2 / l1;
+                const R gdh2 = dh > R(0) ? gl2 * inv_l1 : R(0);
+                gl1 += -gl2 * l2 * inv_l1;
                 gh00 += gdh2 * h11;
                 gh11 += gdh2 * h00;
                 gh01 += -R(2) * gdh2 * h01;
-                const R ghalf = rad > R(0) ? gl1 * half / rad : R(0);
-                gh01 += rad > R(0) ? gl1 * h01 / rad : R(0);
+                const R inv_rad = rad > R(0) ? O::rcp(rad) : R(0);
+                const R ghalf = gl1 * half * inv_rad;
+                gh01 += gl1 * h01 * inv_rad;
                 gh00 += R(0.5) * gl1 + R(0.5) * ghalf;
                 gh11 += R(0.5) * gl1 - R(0.5) * ghalf;
             }

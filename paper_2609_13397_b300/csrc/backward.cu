@@ -130,11 +130,11 @@ __global__ void __launch_bounds__(TILE_PX, 12) raster_bwd_kernel(const RasterArg
                 if (Tf < 0.0f) continue;
                 const float alpha = fminf(ALPHA_MAX, Tf);
                 if (alpha < ALPHA_MIN) continue;
-                const float one_m = 1.0f - alpha;
-                const float Tb = T / one_m;
+                const float inv_m = sfu_rcp(1.0f - alpha);
+                const float Tb = T * inv_m;
                 const float cG = r3.x * GC[0] + r3.y * GC[1] + r3.z * GC[2];
                 const float SG = S[0] * GC[0] + S[1] * GC[1] + S[2] * GC[2];
-                const float galpha = Tb * cG - (SG + GT * Tfin) / one_m;
+                const float galpha = Tb * cG - (SG + GT * Tfin) * inv_m;
                 const float w = alpha * Tb;
                 S[0] += r3.x * w; S[1] += r3.y * w; S[2] += r3.z * w;
                 T = Tb;
@@ -155,11 +155,11 @@ __global__ void __launch_bounds__(TILE_PX, 12) raster_bwd_kernel(const RasterArg
                 continue;
             const float alpha = fminf(ALPHA_MAX, Tresp);
             if (alpha < ALPHA_MIN) continue;
-            const float one_m = 1.0f - alpha;
-            const float Tb = T / one_m;                     // transmittance before this pair
+            const float inv_m = sfu_rcp(1.0f - alpha);
+            const float Tb = T * inv_m;                     // transmittance before this pair
             const float cG = r3.x * GC[0] + r3.y * GC[1] + r3.z * GC[2];
             const float SG = S[0] * GC[0] + S[1] * GC[1] + S[2] * GC[2];
-            const float galpha = Tb * cG - (SG + GT * Tfin) / one_m;
+            const float galpha = Tb * cG - (SG + GT * Tfin) * inv_m;
             const float w = alpha * Tb;
             float gW[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, gou[3] = {0.f, 0.f, 0.f};
             S[0] += r3.x * w; S[1] += r3.y * w; S[2] += r3.z * w;

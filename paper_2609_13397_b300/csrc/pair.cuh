@@ -1,14 +1,9 @@
 // Per pixel-Gaussian pair response (Sec. 4.1-4.2) in registers.
 //
-// One implementation, generic over the arithmetic type V:
-//   float   one pair (the adjoint recomputes the forward's pairs with it);
-//   float2  two pixels against the same Gaussian in packed FP32: every add,
-//           multiply and fused multiply-add issues as one f32x2 instruction of
-//           the Blackwell FMA pipe; reciprocal, square root and exp stay per
-//           element on the SFU.  Element k of every result is bit for bit the
-//           float evaluation of pixel k: the same correctly rounded operations
-//           in the same order, so the forward (packed) and the adjoint (scalar)
-//           take the same compositing decisions;
+// One implementation, generic over the arithmetic type V, with a fixed
+// sequence of correctly rounded operations (so the forward and the adjoint,
+// which recomputes the forward's pairs, take the same compositing decisions):
+//   float   every pair of an ordinary Gaussian;
 //   double  near-degenerate flat Gaussians (effective scale ratio above
 //           FLAT_RATIO): their whitening W has a row of length 1/s_min, so the
 //           whitened camera centre o_u is large and t* and q = o_u + t* d_u
@@ -16,8 +11,9 @@
 //           stays within ~2e-5 up to s_max/s_min = 250 at any viewing angle and
 //           size, reaches ~9e-5 at 400 and ~3e-4 at 600 (small disks seen
 //           face-on), hence the threshold of 200.
-// FP32 uses the SFU approximations of reciprocal, square root and exp (about
-// 1-2 ulp), far inside the 1e-4 output tolerance; FP64 the correctly rounded ones.
+// FP32 uses the SFU approximations of reciprocal, reciprocal square root and
+// 2^x (about 1-2 ulp, subnormals flushed), far inside the 1e-4 output tolerance;
+// FP64 the correctly rounded operations.
 //
 // With d_u = W d, g_i = W delta_i (W = W_eff), n = |d_u|^2:
 //   t* = -<o_u, d_u>/n,  q = o_u + t* d_u                          (Eq. 2)
@@ -44,9 +40,32 @@ constexpr float FLAT_RATIO = 200.0f;
 
 // ---------------------------------------------------------------- arithmetic per type
 
-struct Bool2 {
-    bool x, y;
-};
+// The special-function unit's approximations (reciprocal, reciprocal square
+// root, 2^x) with subnormal inputs and results flushed to zero: one SFU
+// instruction each, where the non-flushing forms add range scaling around it.
+// Nothing the pair response decides rests on values that small: a response
+// below 2^-126 lies far under the 1/255 opacity threshold, and the ray
+// quantities that are inverted are bounded away from zero.
+__device__ __forceinline__ float sfu_rcp(float a) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
+__device__ __forceinline__ float sfu_rsqrt(float a) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
+__device__ __forceinline__ float sfu_exp2(float a) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
+// e^a = 2^(a log2 e)
+__device__ __forceinline__ float sfu_exp(float a) { return sfu_exp2(__fmul_rn(a, 1.4426950408889634f)); }
+// Smallest argument the guarded forms pass to the SFU: a zero argument gives
+// a zero result (r2 * rsqrt(max(r2, tiny)) = 0) without a compare and select.
+constexpr float SFU_TINY = 1e-36f;
 
 template <typename V>
 struct Ops;
@@ -61,11 +80,13 @@ struct Ops<float> {
     static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
     static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
     static __device__ __forceinline__ float neg(float a) { return -a; }
-    static __device__ __forceinline__ float rcp(float a) { return __fdividef(1.0f, a); }
-    static __device__ __forceinline__ float rsqrt(float a) { return rsqrtf(a); }
-    static __device__ __forceinline__ float rsqrt0(float a) { return a > 0.0f ? rsqrtf(a) : 0.0f; }
+    static __device__ __forceinline__ float rcp(float a) { return sfu_rcp(a); }
+    static __device__ __forceinline__ float rsqrt(float a) { return sfu_rsqrt(a); }
+    // 1/sqrt(a) for a > 0; a = 0 (a zero vector's squared length) gives a finite
+    // factor that keeps the vector's zero components zero
+    static __device__ __forceinline__ float rsqrt0(float a) { return sfu_rsqrt(fmaxf(a, SFU_TINY)); }
     static __device__ __forceinline__ float sqrt(float a) { return sqrtf(a); }
-    static __device__ __forceinline__ float exp(float a) { return __expf(a); }
+    static __device__ __forceinline__ float exp(float a) { return sfu_exp(a); }
     static __device__ __forceinline__ float max(float a, float b) { return fmaxf(a, b); }
     static __device__ __forceinline__ B gt(float a, float b) { return a > b; }
     static __device__ __forceinline__ B eq(float a, float b) { return a == b; }
@@ -73,37 +94,7 @@ struct Ops<float> {
     static __device__ __forceinline__ B bnot(B a) { return !a; }
     static __device__ __forceinline__ float sel(B c, float a, float b) { return c ? a : b; }
     // sqrt(r2) as r2 * rsqrt(r2) (0 at 0)
-    static __device__ __forceinline__ float root(float r2) { return r2 > 0.0f ? r2 * rsqrtf(r2) : 0.0f; }
-};
-
-template <>
-struct Ops<float2> {
-    using B = Bool2;
-    using F = Ops<float>;
-    static __device__ __forceinline__ float2 S(float a) { return make_float2(a, a); }
-    static __device__ __forceinline__ B SB(bool a) { return B{a, a}; }
-    static __device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
-    static __device__ __forceinline__ float2 sub(float2 a, float2 b) {
-        return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);   // a - b, one rounding
-    }
-    static __device__ __forceinline__ float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
-    static __device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-    static __device__ __forceinline__ float2 neg(float2 a) { return make_float2(-a.x, -a.y); }
-    static __device__ __forceinline__ float2 rcp(float2 a) { return make_float2(F::rcp(a.x), F::rcp(a.y)); }
-    static __device__ __forceinline__ float2 rsqrt(float2 a) { return make_float2(rsqrtf(a.x), rsqrtf(a.y)); }
-    static __device__ __forceinline__ float2 rsqrt0(float2 a) { return make_float2(F::rsqrt0(a.x), F::rsqrt0(a.y)); }
-    static __device__ __forceinline__ float2 exp(float2 a) { return make_float2(__expf(a.x), __expf(a.y)); }
-    static __device__ __forceinline__ float2 max(float2 a, float2 b) {
-        return make_float2(fmaxf(a.x, b.x), fmaxf(a.y, b.y));
-    }
-    static __device__ __forceinline__ B gt(float2 a, float2 b) { return B{a.x > b.x, a.y > b.y}; }
-    static __device__ __forceinline__ B eq(float2 a, float2 b) { return B{a.x == b.x, a.y == b.y}; }
-    static __device__ __forceinline__ B bor(B a, B b) { return B{a.x || b.x, a.y || b.y}; }
-    static __device__ __forceinline__ B bnot(B a) { return B{!a.x, !a.y}; }
-    static __device__ __forceinline__ float2 sel(B c, float2 a, float2 b) {
-        return make_float2(c.x ? a.x : b.x, c.y ? a.y : b.y);
-    }
-    static __device__ __forceinline__ float2 root(float2 r2) { return make_float2(F::root(r2.x), F::root(r2.y)); }
+    static __device__ __forceinline__ float root(float r2) { return __fmul_rn(r2, sfu_rsqrt(fmaxf(r2, SFU_TINY))); }
 };
 
 template <>
@@ -150,22 +141,6 @@ struct PixelRaysT {
     V d_dx, d_dy, dxdx, dxdy, dydy;
 };
 using PixelRays = PixelRaysT<float>;
-
-__device__ __forceinline__ PixelRaysT<float2> pack_pixels(const PixelRays &a, const PixelRays &b) {
-    PixelRaysT<float2> p;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        p.d[k] = make_float2(a.d[k], b.d[k]);
-        p.dx[k] = make_float2(a.dx[k], b.dx[k]);
-        p.dy[k] = make_float2(a.dy[k], b.dy[k]);
-    }
-    p.d_dx = make_float2(a.d_dx, b.d_dx);
-    p.d_dy = make_float2(a.d_dy, b.d_dy);
-    p.dxdx = make_float2(a.dxdx, b.dxdx);
-    p.dxdy = make_float2(a.dxdy, b.dxdy);
-    p.dydy = make_float2(a.dydy, b.dydy);
-    return p;
-}
 
 __device__ __forceinline__ PixelRaysT<double> widen(const PixelRays &a) {
     PixelRaysT<double> p;
@@ -247,15 +222,14 @@ __device__ __forceinline__ void K_major(V h00, V h01, V h11, V l1, V l2, V rho2,
 
 // ---------------------------------------------------------------- the response
 
-// Response of the pair(s) in type V.  hit: false where t* <= T_NEAR (the pair is
-// skipped).  With STORE (scalar types) the intermediates are copied to *st; the
-// arithmetic is the same either way.  A scalar call returns early when t* fails.
+// Response of the pair in type V.  hit: false where t* <= T_NEAR (the pair is
+// skipped; the call returns early).  With STORE the intermediates are copied to
+// *st; the arithmetic is the same either way.
 template <bool FILTER, bool STORE = false, typename V = float>
 __device__ __forceinline__ void pair_eval(const GaussRec<V> &g, const bool additive, const PixelRaysT<V> &px, V &T,
                                           typename Ops<V>::B &hit, PairFwdT<V> *st = nullptr) {
     using O = Ops<V>;
     using B = typename O::B;
-    constexpr bool SCALAR = sizeof(V) != sizeof(float2);
     const V *W = g.W;
     const V du0 = dot3v(W[0], W[1], W[2], px.d[0], px.d[1], px.d[2]);
     const V du1 = dot3v(W[3], W[4], W[5], px.d[0], px.d[1], px.d[2]);
@@ -265,9 +239,7 @@ __device__ __forceinline__ void pair_eval(const GaussRec<V> &g, const bool addit
     const V p = dot3v(g.ou[0], g.ou[1], g.ou[2], du0, du1, du2);
     const V ts = O::neg(O::mul(p, inv_n));
     hit = O::gt(ts, O::S(T_NEAR));
-    if constexpr (SCALAR) {
-        if (!hit) return;
-    }
+    if (!hit) return;
     const V q0 = O::fma(ts, du0, g.ou[0]), q1 = O::fma(ts, du1, g.ou[1]), q2 = O::fma(ts, du2, g.ou[2]);
     const V qq = dot3v(q0, q1, q2, q0, q1, q2);
     if constexpr (STORE) {
@@ -308,35 +280,19 @@ __device__ __forceinline__ void pair_eval(const GaussRec<V> &g, const bool addit
         const B id = O::bor(O::eq(g.rho2, O::S(0.0f)), O::SB(additive));
         const B none = O::bnot(O::gt(l1, g.rho2));
         const B both = O::gt(l2, g.rho2);
-        V k00, k01, k11;
-        int kc = 0;
-        if constexpr (SCALAR) {
-            // the case taken, with exactly the operations the packed form selects from
-            kc = id ? 0 : none ? 3 : both ? 1 : 2;
-            if (kc == 0) {
-                k00 = k11 = third;
-                k01 = O::S(0.0f);
-            } else if (kc == 3) {
-                k00 = k01 = k11 = O::S(0.0f);
-            } else if (kc == 1) {
-                K_both(h00, h01, h11, dh, g.rho2, k00, k01, k11);
-            } else {
-                K_major(h00, h01, h11, l1, l2, g.rho2, k00, k01, k11);
-            }
-        } else {
-            V a00, a01, a11, c00, c01, c11;
-            K_both(h00, h01, h11, dh, g.rho2, a00, a01, a11);
-            K_major(h00, h01, h11, l1, l2, g.rho2, c00, c01, c11);
-            k00 = O::sel(both, a00, c00);
-            k01 = O::sel(both, a01, c01);
-            k11 = O::sel(both, a11, c11);
-            k00 = O::sel(none, O::S(0.0f), k00);
-            k01 = O::sel(none, O::S(0.0f), k01);
-            k11 = O::sel(none, O::S(0.0f), k11);
-            k00 = O::sel(id, third, k00);
-            k01 = O::sel(id, O::S(0.0f), k01);
-            k11 = O::sel(id, third, k11);
-        }
+        // K for every case, chosen without a branch (the warp's lanes evaluate
+        // different pairs, whose cases differ)
+        V a00, a01, a11, c00, c01, c11;
+        K_both(h00, h01, h11, dh, g.rho2, a00, a01, a11);
+        K_major(h00, h01, h11, l1, l2, g.rho2, c00, c01, c11);
+        V k00 = O::sel(both, a00, c00), k01 = O::sel(both, a01, c01), k11 = O::sel(both, a11, c11);
+        k00 = O::sel(none, O::S(0.0f), k00);
+        k01 = O::sel(none, O::S(0.0f), k01);
+        k11 = O::sel(none, O::S(0.0f), k11);
+        k00 = O::sel(id, third, k00);
+        k01 = O::sel(id, O::S(0.0f), k01);
+        k11 = O::sel(id, third, k11);
+        const int kc = id ? 0 : none ? 3 : both ? 1 : 2;
         // Eq. 9 in an orthonormal basis (e1, e2) of span(E): E = [e1 e2] R with
         // R = [[r00, r01], [0, r11]] (Gram-Schmidt), N = R K R^T, so that
         //   det A = det(I + N),  q^T A^-1 q = |q_perp|^2 + q_E^T (I + N)^-1 q_E,
@@ -423,7 +379,7 @@ __device__ __forceinline__ bool pair_response(const GaussRec<R> &g, const bool a
 // Visual-cone pre-test (view record words u, g, C; see preprocess.cu): a pixel
 // ray d with -1 + g.e + e^T C e > 1e-3, e = d - u, cannot reach alpha >= 1/255
 // with the Gaussian.  Returns true when the pair must be evaluated.  The same
-// operations in the forward (packed) and the adjoint (scalar).
+// operations in the forward and the adjoint.
 template <typename V>
 __device__ __forceinline__ typename Ops<V>::B pretest(V u0, V u1, V u2, V g0, V g1, V g2, V C00, V C11, V C22, V C01,
                                                       V C02, V C12, const V d[3]) {

@@ -54,6 +54,7 @@ class Result:
     T: Optional[torch.Tensor] = None
     error: Optional[str] = None
     need_bytes: int = 0          # the memory the request was admitted with
+    t_release: float = 0.0       # when that memory went back to the gate
 
     @property
     def latency_ms(self) -> float:
@@ -156,6 +157,7 @@ class Server:
                     try:
                         view.render_host(h_rgb, h_T, flags=req.flags, stream=stream)
                     finally:
+                        res.t_release = self.now()
                         self.gate.release(need)
                 res.rays = int(view.stats()["n_valid_pixels"])
                 with self._cv:

@@ -79,9 +79,10 @@ def test_memory_admission_limits_concurrency(scene_ctx):
     srv.close()
     assert all(r.error is None for r in res)
     assert [r.need_bytes for r in res] == needs
+    # memory is held from admission to release (the end of the copy, before t_done)
     for a in res:
         for b in res:
-            if a.rid < b.rid and a.t_admit < b.t_done and b.t_admit < a.t_done:
+            if a.rid < b.rid and a.t_admit < b.t_release and b.t_admit < a.t_release:
                 assert a.need_bytes + b.need_bytes <= budget
 
 
