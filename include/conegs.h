@@ -103,7 +103,14 @@ enum {
      * contributing pair is displaced by 32 or more contributing pairs between the two
      * orders; otherwise an approximation of it.  Forward only: with
      * CONEGS_KEEP_FOR_BACKWARD the render fails with CONEGS_ERR_ARG. */
-    CONEGS_ORDER_TSTAR = 1u << 7
+    CONEGS_ORDER_TSTAR = 1u << 7,
+    /* The rasteriser's pre-test (which skips pairs that cannot reach alpha >= 1/255;
+     * it changes no result) in its ray-direction form on pinhole views as well.  By
+     * default a pinhole view tests each pixel centre against the ellipse that the
+     * same visual cone cuts from the image plane, a cheaper test; fisheye views
+     * always use the ray-direction form.  Both forms are conservative, so images are
+     * the same either way; the flag exists to check exactly that. */
+    CONEGS_PRETEST_RAY = 1u << 8
 };
 
 typedef struct conegs_ctx conegs_ctx;

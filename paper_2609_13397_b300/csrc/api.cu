@@ -35,7 +35,7 @@ cudaError_t launch_bin_emit(const CamParams &c, const float *binrec, const float
                             const float4 *gell, bool ut, cudaStream_t s);
 cudaError_t launch_scene_cache(const SceneParams &sp, float *W, float *sig_eff, cudaStream_t s);
 cudaError_t launch_view_records(const CamParams &c, const SceneParams &sp, const float *mcam, float mzf,
-                                int fov_cull, float4 *rec, float4 *gview, float2 *gcone, uint8_t *gflag,
+                                int fov_cull, int pixtest, float4 *rec, float4 *gview, float2 *gcone, uint8_t *gflag,
                                 float4 *gell, unsigned long long *nflat, uint8_t *gflat, cudaStream_t s);
 int64_t scan_scratch_words(int64_t n);
 cudaError_t exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *scratch, int pred,
@@ -510,6 +510,12 @@ static float zf_bound(const CamParams &c, unsigned flags) {
     return 1.0f / d6;
 }
 
+// The records of a pinhole view hold the pixel-space form of the pre-test unless
+// the render asks for the ray-direction form.
+static int pixel_pretest(const CamParams &c, unsigned flags) {
+    return c.model == 0 && !(flags & CONEGS_PRETEST_RAY) ? 1 : 0;
+}
+
 static void set_footprint(RasterArgs &a, const CamParams &c, unsigned flags) {
     a.footprint = footprint_mode(flags);
     a.zax[0] = c.R[2];
@@ -561,7 +567,7 @@ static conegs_status render_front(conegs_view *v, unsigned flags, cudaStream_t s
     // [4] pairs of flat Gaussians, [5] scratch (flat slot counter)
     CUDA_TRY(cudaMemsetAsync(v->sums.as<unsigned long long>() + 2, 0, 2 * sizeof(unsigned long long), s));
     CUDA_TRY(launch_view_records(c, sp, v->mcam.as<float>(), zf_bound(c, flags), (flags & CONEGS_BIN_UT) ? 0 : 1,
-                                 v->rec.as<float4>(), v->gview.as<float4>(),
+                                 pixel_pretest(c, flags), v->rec.as<float4>(), v->gview.as<float4>(),
                                  v->gcone.as<float2>(), v->gflag.as<uint8_t>(), v->gell.as<float4>(),
                                  v->sums.as<unsigned long long>() + 3, v->gflat.as<uint8_t>(), s));
     {
@@ -645,6 +651,7 @@ static conegs_status render_back(conegs_view *v, float *out_rgb, float *out_T, u
     a.out_T = out_T;
     a.last = v->last.as<uint32_t>();
     a.additive = (flags & CONEGS_COMP_ADDITIVE) ? 1 : 0;
+    a.pixtest = pixel_pretest(c, flags);
     set_footprint(a, c, flags);
     if (nflat_pairs > 0) {
         // the pairs of flat Gaussians: responses (and their derivatives, for the adjoint) in FP64
@@ -897,6 +904,7 @@ conegs_status conegs_render_backward(conegs_view *v, const float *dL_drgb, const
     a.valid = v->valid.as<uint8_t>();
     a.last = v->last.as<uint32_t>();
     a.additive = (v->last_flags & CONEGS_COMP_ADDITIVE) ? 1 : 0;
+    a.pixtest = pixel_pretest(c, v->last_flags);
     if (v->n_flat_pairs > 0) {
         a.flat_slot = v->flat_slot.as<uint32_t>();
         a.flat_T = v->flat_T.as<float>();

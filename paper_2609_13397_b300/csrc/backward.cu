@@ -31,7 +31,7 @@ namespace conegs {
 // front from the state the forward's suffix pass left: T after the segment and
 // the colour composited behind it; pixels whose walk ended before the segment
 // sit out.
-template <bool FILTER, bool FIRST>
+template <bool FILTER, bool FIRST, bool PIX>
 __global__ void __launch_bounds__(TILE_PX, 12) raster_bwd_kernel(const RasterArgs a, const SegArgs g,
                                                              const float *__restrict__ dL_drgb,
                                                              const float *__restrict__ dL_dT,
@@ -109,9 +109,7 @@ __global__ void __launch_bounds__(TILE_PX, 12) raster_bwd_kernel(const RasterArg
             for (int b = 0; b < (int)nb; ++b) {
                 const uint32_t walk = start + b - range.x + 1;     // 1-based walk index of this entry
                 if (walk > last) break;
-                const float4 r4 = s_rec[4][b], r5 = s_rec[5][b], r6 = s_rec[6][b];
-                if (pretest<float>(r4.x, r4.y, r4.z, r4.w, r5.x, r5.y, r5.z, r5.w, r6.x, r6.y, r6.z, r6.w, px.d))
-                    mask |= 1ull << b;
+                if (staged_pretest<PIX>(s_rec, b, px)) mask |= 1ull << b;
             }
         }
         // phase 2: lanes walk their own passing entries back to front in lockstep
@@ -183,12 +181,18 @@ cudaError_t launch_backward(const RasterArgs &a, int ntiles, bool filter, uint32
     int64_t items = 0;
     const SegArgs g = split_args(split_scratch, ntiles, &items);
     const unsigned later = (unsigned)(items - ntiles);
-    if (filter) {
-        raster_bwd_kernel<true, true><<<ntiles, TILE_PX, 0, s>>>(a, g, dL_drgb, dL_dT, final_T, g_rec);
-        raster_bwd_kernel<true, false><<<later, TILE_PX, 0, s>>>(a, g, dL_drgb, dL_dT, final_T, g_rec);
+    if (filter && a.pixtest) {
+        raster_bwd_kernel<true, true, true><<<ntiles, TILE_PX, 0, s>>>(a, g, dL_drgb, dL_dT, final_T, g_rec);
+        raster_bwd_kernel<true, false, true><<<later, TILE_PX, 0, s>>>(a, g, dL_drgb, dL_dT, final_T, g_rec);
+    } else if (filter) {
+        raster_bwd_kernel<true, true, false><<<ntiles, TILE_PX, 0, s>>>(a, g, dL_drgb, dL_dT, final_T, g_rec);
+        raster_bwd_kernel<true, false, false><<<later, TILE_PX, 0, s>>>(a, g, dL_drgb, dL_dT, final_T, g_rec);
+    } else if (a.pixtest) {
+        raster_bwd_kernel<false, true, true><<<ntiles, TILE_PX, 0, s>>>(a, g, dL_drgb, dL_dT, final_T, g_rec);
+        raster_bwd_kernel<false, false, true><<<later, TILE_PX, 0, s>>>(a, g, dL_drgb, dL_dT, final_T, g_rec);
     } else {
-        raster_bwd_kernel<false, true><<<ntiles, TILE_PX, 0, s>>>(a, g, dL_drgb, dL_dT, final_T, g_rec);
-        raster_bwd_kernel<false, false><<<later, TILE_PX, 0, s>>>(a, g, dL_drgb, dL_dT, final_T, g_rec);
+        raster_bwd_kernel<false, true, false><<<ntiles, TILE_PX, 0, s>>>(a, g, dL_drgb, dL_dT, final_T, g_rec);
+        raster_bwd_kernel<false, false, false><<<later, TILE_PX, 0, s>>>(a, g, dL_drgb, dL_dT, final_T, g_rec);
     }
     note_launches(2);
     return cudaGetLastError();

@@ -139,6 +139,7 @@ template <typename V>
 struct PixelRaysT {
     V d[3], dx[3], dy[3];
     V d_dx, d_dy, dxdx, dxdy, dydy;
+    float pc[2];          // pixel centre (i + 1/2, j + 1/2), for the pinhole pre-test
 };
 using PixelRays = PixelRaysT<float>;
 
@@ -156,6 +157,8 @@ __device__ __forceinline__ PixelRaysT<double> widen(const PixelRays &a) {
     p.dxdx = dot3v(p.dx[0], p.dx[1], p.dx[2], p.dx[0], p.dx[1], p.dx[2]);
     p.dxdy = dot3v(p.dx[0], p.dx[1], p.dx[2], p.dy[0], p.dy[1], p.dy[2]);
     p.dydy = dot3v(p.dy[0], p.dy[1], p.dy[2], p.dy[0], p.dy[1], p.dy[2]);
+    p.pc[0] = a.pc[0];
+    p.pc[1] = a.pc[1];
     return p;
 }
 
@@ -390,6 +393,32 @@ __device__ __forceinline__ typename Ops<V>::B pretest(V u0, V u1, V u2, V g0, V 
     const V quad = O::fma(O::mul(C22, e2), e2, O::fma(qb, e1, O::mul(qa, e0)));
     const V lin = O::fma(g2, e2, O::fma(g1, e1, O::fma(g0, e0, O::S(-1.0f))));
     return O::bnot(O::gt(O::add(lin, quad), O::S(1e-3f)));
+}
+
+// Pinhole form of the same pre-test (view record words r4 = (c_x, c_y, G00, 2 G01),
+// r5.xy = (G11, t); see preprocess.cu): the pixel centre p must satisfy
+// (p - c)^T G (p - c) <= t, the ellipse the visual cone cuts from the image
+// plane, in pixels.  Fixed, correctly rounded operations (the forward and the
+// adjoint take the same decision).
+__device__ __forceinline__ bool pretest_pix(const float4 r4, const float2 r5, const float pc[2]) {
+    const float ex = __fsub_rn(pc[0], r4.x), ey = __fsub_rn(pc[1], r4.y);
+    const float t = __fmaf_rn(r4.w, ey, __fmul_rn(r4.z, ex));            // G00 ex + 2 G01 ey
+    const float q = __fmaf_rn(t, ex, __fmul_rn(__fmul_rn(r5.x, ey), ey));
+    return q <= r5.y;
+}
+
+// The pre-test of staged record b (records staged as s[word][entry]) against a
+// pixel: PIX selects the pinhole form.
+template <bool PIX, int N>
+__device__ __forceinline__ bool staged_pretest(const float4 (*s)[N], int b, const PixelRays &px) {
+    if constexpr (PIX) {
+        const float4 r4 = s[4][b];
+        const float2 r5 = *reinterpret_cast<const float2 *>(&s[5][b]);
+        return pretest_pix(r4, r5, px.pc);
+    } else {
+        const float4 r4 = s[4][b], r5 = s[5][b], r6 = s[6][b];
+        return pretest<float>(r4.x, r4.y, r4.z, r4.w, r5.x, r5.y, r5.z, r5.w, r6.x, r6.y, r6.z, r6.w, px.d);
+    }
 }
 
 }  // namespace conegs

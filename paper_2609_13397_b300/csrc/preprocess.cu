@@ -12,6 +12,8 @@
 // (a flat Gaussian has [-rho^2, lo(o_u)] as its last word: see pair.cuh)
 // where (u, g, C) define the pixel pre-test: with e = d - u, a pixel ray d
 // with -1 + g.e + e^T C e > 0 cannot reach alpha >= 1/255 with this Gaussian.
+// On pinhole views the words [4] and [5] hold that test's pixel-space ellipse
+// instead, [c_x, c_y, G00, 2 G01] [G11, t, 0, 0] (pixel_cone_ellipse).
 #include "pair.cuh"
 #include "rule.cuh"
 #include "sh.cuh"
@@ -128,6 +130,67 @@ __device__ void cone_quadric(const float W[9], const float ou[3], float kap2, fl
     for (int k = 0; k < 3; ++k) g[k] = 2.0f * L * b * Mv[k];
 }
 
+// Pinhole form of the same pre-test: the pixel centres whose rays meet the
+// ellipsoid E = mu + {x : x^T M x <= 1} of cone_quadric (same M).  In the camera
+// frame (m = R^T (mu - o), P = R^T M R, a = m^T P m, z = P m) the ray of direction
+// d = m / m_z + delta, delta = (delta_x, delta_y, 0) on the plane z = 1, meets E iff
+// (a - 1) d^T P d <= (d^T P m)^2, i.e.
+//   delta^T G delta - 2 h^T delta <= k0,  G = (a - 1) P_xy - z_xy z_xy^T,
+//   h = z_xy / m_z,  k0 = a / m_z^2
+// (the constant and linear terms in delta cancel in closed form, so narrow cones
+// of far, small Gaussians keep their digits); all three are scaled by 1/a here.
+// With G positive definite this is the ellipse (delta - delta0)^T G (delta -
+// delta0) <= k0 + h^T delta0, delta0 = G^-1 h; in pixels (delta = D (p - p_m),
+// D = diag(1/f_x, 1/f_y), p_m the projection of mu) its centre is p_m + D^-1
+// delta0 and its matrix D G D.  FP32 margins: the threshold x 1.01 (relative
+// errors of the axes), then the ellipse grown by 0.02 px (rounding of the centre).
+// Where the test does not apply (the camera within E, E reaching the camera
+// plane, m_z <= 0) the record passes every pixel.  Output: r4 = (c_x, c_y, G00,
+// 2 G01), r5 = (G11, t, 0, 0), the words pretest_pix reads.
+__device__ void pixel_cone_ellipse(const CamParams &c, const float W[9], const float ou[3], float kap2, float tau,
+                                   const float mu[3], float4 &r4, float4 &r5) {
+    r4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    r5 = make_float4(0.f, 1.0f, 0.f, 0.f);            // pass every pixel
+    const float v0 = mu[0] - c.o[0], v1 = mu[1] - c.o[1], v2 = mu[2] - c.o[2];
+    const float mx = c.R[0] * v0 + c.R[3] * v1 + c.R[6] * v2;
+    const float my = c.R[1] * v0 + c.R[4] * v1 + c.R[7] * v2;
+    const float mz = c.R[2] * v0 + c.R[5] * v1 + c.R[8] * v2;
+    if (!(mz > 0.0f)) return;
+    float a = 0.f, P00 = 0.f, P01 = 0.f, P11 = 0.f, z0 = 0.f, z1 = 0.f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float *w = W + 3 * i;
+        const float w2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+        const float ci = 1.0f / (kap2 * (1.0f + tau * w2));
+        const float wc0 = c.R[0] * w[0] + c.R[3] * w[1] + c.R[6] * w[2];   // R^T w_i, camera x and y
+        const float wc1 = c.R[1] * w[0] + c.R[4] * w[1] + c.R[7] * w[2];
+        a += ci * ou[i] * ou[i];                       // w_i . (mu - o) = -ou_i
+        P00 += ci * wc0 * wc0;
+        P01 += ci * wc0 * wc1;
+        P11 += ci * wc1 * wc1;
+        z0 -= ci * ou[i] * wc0;
+        z1 -= ci * ou[i] * wc1;
+    }
+    if (!(a > 1.0f)) return;
+    const float ia = 1.0f / a, b = 1.0f - ia;
+    const float G00 = b * P00 - z0 * z0 * ia, G01 = b * P01 - z0 * z1 * ia, G11 = b * P11 - z1 * z1 * ia;
+    const float det = G00 * G11 - G01 * G01;
+    if (!(G00 > 0.0f && G11 > 0.0f && det > 0.0f)) return;
+    const float imz = 1.0f / mz;
+    const float h0 = z0 * ia * imz, h1 = z1 * ia * imz;
+    const float idet = 1.0f / det;
+    const float d0 = (G11 * h0 - G01 * h1) * idet, d1 = (G00 * h1 - G01 * h0) * idet;
+    const float thr = imz * imz + h0 * d0 + h1 * d1;
+    const float cxp = c.cx + c.fx * (mx * imz + d0), cyp = c.cy + c.fy * (my * imz + d1);
+    const float ifx = 1.0f / c.fx, ify = 1.0f / c.fy;
+    const float g00 = G00 * ifx * ifx, g01 = G01 * ifx * ify, g11 = G11 * ify * ify;
+    const float grown = sqrtf(1.01f * fmaxf(thr, 0.0f)) + 0.02f * sqrtf(g00 + g11);
+    const float t = grown * grown;
+    if (!(isfinite(t) && isfinite(cxp) && isfinite(cyp) && isfinite(g00) && isfinite(g01) && isfinite(g11))) return;
+    r4 = make_float4(cxp, cyp, g00, 2.0f * g01);
+    r5 = make_float4(g11, t, 0.f, 0.f);
+}
+
 // t* bound of the binning rule (see cone_half_angle); false = no useful bound.
 __device__ bool tstar_bound(float kap, float s2, float r1, float L, float m, float &tb) {
     const float s = sqrtf(s2);
@@ -148,7 +211,7 @@ __device__ bool tstar_bound(float kap, float s2, float r1, float L, float m, flo
 
 // Per view: binning direction/depth (the FP32 rule) and the raster record.
 __global__ void __launch_bounds__(256) view_records_kernel(CamParams c, SceneParams sp, const float *__restrict__ mcam,
-                                                           float mzf, int fov_cull,
+                                                           float mzf, int fov_cull, int pixtest,
                                                            float4 *__restrict__ rec, float4 *__restrict__ gview,
                                                            float2 *__restrict__ gcone,
                                                            uint8_t *__restrict__ gflag,
@@ -202,9 +265,11 @@ __global__ void __launch_bounds__(256) view_records_kernel(CamParams c, ScenePar
         ge[1] = make_float4(el[4], el[5], el[6], el[7]);
         ge[2] = make_float4(el[8], el[9], el[10], el[11]);
     }
-    // rasteriser pre-test, with the exact kappa^2 = 2 ln(255 sigma)
+    // rasteriser pre-test, with the exact kappa^2 = 2 ln(255 sigma): its ray-direction
+    // form (u, g, C), or on pinhole views (pixtest) the pixel-space ellipse
     float g[3] = {0.f, 0.f, 0.f}, C[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float pu[3] = {dx, dy, dz};
+    float4 pix4 = make_float4(0.f, 0.f, 0.f, 0.f), pix5 = make_float4(0.f, -1.0f, 0.f, 0.f);   // rejects every pixel
     {
         const float sig = 1.0f / (1.0f + expf(-load_scalar(sp.logits, i, sp.storage)));
         const float k2 = 2.0f * logf(255.0f * sig);
@@ -219,7 +284,12 @@ __global__ void __launch_bounds__(256) view_records_kernel(CamParams c, ScenePar
             float tb;
             const float rr = sqrtf(s2 / s2mn);    // s_max / s_min; |f_i| <= (r + 1/r)/2 |delta_i|
             tstar_bound(sqrtf(k2), s2, fmaxf(0.5f * (rr + 1.0f / rr) * 1.00001f, 1.0f), L, m, tb);
-            cone_quadric(W, ou, 1.01f * k2, tb * tb * m * 1.001f, L, g, C);
+            if (pixtest)
+                pixel_cone_ellipse(c, W, ou, 1.01f * k2, tb * tb * m * 1.001f, mu, pix4, pix5);
+            else
+                cone_quadric(W, ou, 1.01f * k2, tb * tb * m * 1.001f, L, g, C);
+        } else {
+            pix5 = make_float4(0.f, 1.0f, 0.f, 0.f);     // mu at the optical centre: every pixel
         }
     }
     // flat Gaussian (s_eff,max / s_eff,min > FLAT_RATIO): the response is taken in
@@ -250,9 +320,15 @@ __global__ void __launch_bounds__(256) view_records_kernel(CamParams c, ScenePar
     r[1] = make_float4(W[3], W[4], W[5], ou[1]);
     r[2] = make_float4(W[6], W[7], W[8], ou[2]);
     r[3] = make_float4(col[0], col[1], col[2], sp.sig_eff[i]);
-    r[4] = make_float4(pu[0], pu[1], pu[2], g[0]);
-    r[5] = make_float4(g[1], g[2], C[0], C[1]);
-    r[6] = make_float4(C[2], C[3], C[4], C[5]);
+    if (pixtest) {
+        r[4] = pix4;
+        r[5] = pix5;
+        r[6] = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+        r[4] = make_float4(pu[0], pu[1], pu[2], g[0]);
+        r[5] = make_float4(g[1], g[2], C[0], C[1]);
+        r[6] = make_float4(C[2], C[3], C[4], C[5]);
+    }
     r[7] = r7;
 }
 
@@ -264,11 +340,11 @@ cudaError_t launch_scene_cache(const SceneParams &sp, float *W, float *sig_eff, 
 }
 
 cudaError_t launch_view_records(const CamParams &c, const SceneParams &sp, const float *mcam, float mzf,
-                                int fov_cull, float4 *rec, float4 *gview, float2 *gcone, uint8_t *gflag,
+                                int fov_cull, int pixtest, float4 *rec, float4 *gview, float2 *gcone, uint8_t *gflag,
                                 float4 *gell, unsigned long long *nflat, uint8_t *gflat, cudaStream_t s) {
     if (sp.n == 0) return cudaSuccess;
-    view_records_kernel<<<(unsigned)div_up(sp.n, 256), 256, 0, s>>>(c, sp, mcam, mzf, fov_cull, rec, gview, gcone,
-                                                                    gflag, gell, nflat, gflat);
+    view_records_kernel<<<(unsigned)div_up(sp.n, 256), 256, 0, s>>>(c, sp, mcam, mzf, fov_cull, pixtest, rec, gview,
+                                                                    gcone, gflag, gell, nflat, gflat);
     note_launches(1);
     return cudaGetLastError();
 }

@@ -81,8 +81,9 @@ __global__ void seg_map_kernel(const uint32_t *__restrict__ nseg, const uint32_t
 
 // Walks list entries [b0, b1) for the tile's pixels from (C, Tacc), with the
 // sequential compositing rules.  `live` pixels take part; a pixel leaves at its
-// stop (sets stopped) or at b1.  last is 1-based relative to `base`.
-template <bool FILTER>
+// stop (sets stopped) or at b1.  last is 1-based relative to `base`.  PIX: the
+// records hold the pinhole (pixel-space) form of the pre-test.
+template <bool FILTER, bool PIX>
 __device__ __forceinline__ void walk_entries(const RasterArgs &a, float4 (*s_rec)[TILE_PX], uint32_t b0, uint32_t b1,
                                              uint32_t base, bool live, const PixelRays &px, float &C0, float &C1,
                                              float &C2, float &Tacc, uint32_t &last, bool &stopped,
@@ -103,11 +104,8 @@ __device__ __forceinline__ void walk_entries(const RasterArgs &a, float4 (*s_rec
         unsigned long long mask = 0ull;
         if (!done) {
             walked += (uint32_t)nb;
-            for (int b = 0; b < nb; ++b) {
-                const float4 r4 = s_rec[4][b], r5 = s_rec[5][b], r6 = s_rec[6][b];
-                if (pretest<float>(r4.x, r4.y, r4.z, r4.w, r5.x, r5.y, r5.z, r5.w, r6.x, r6.y, r6.z, r6.w, px.d))
-                    mask |= 1ull << b;
-            }
+            for (int b = 0; b < nb; ++b)
+                if (staged_pretest<PIX>(s_rec, b, px)) mask |= 1ull << b;
         }
         // phase 2: each lane walks its own passing entries in depth order, so
         // the warp's lanes evaluate different entries in lockstep
@@ -178,7 +176,7 @@ __device__ __forceinline__ void write_pixel(const RasterArgs &a, int64_t pix, in
 }
 
 // Pass A.  FIRST: one CTA per tile for its first segment; else one per later segment.
-template <bool FILTER, bool FIRST>
+template <bool FILTER, bool FIRST, bool PIX>
 __global__ void __launch_bounds__(TILE_PX) raster_seg_kernel(const RasterArgs a, const SegArgs g) {
     __shared__ float4 s_rec[REC_F4][TILE_PX];
     uint2 tw;
@@ -212,7 +210,7 @@ __global__ void __launch_bounds__(TILE_PX) raster_seg_kernel(const RasterArgs a,
     float C0 = 0.f, C1 = 0.f, C2 = 0.f, Tacc = 1.0f;
     uint32_t last = 0, walked = 0, full = 0, nflat = 0;
     bool stopped = false;
-    walk_entries<FILTER>(a, s_rec, b0, b1, b0, live, px, C0, C1, C2, Tacc, last, stopped, walked, full, nflat);
+    walk_entries<FILTER, PIX>(a, s_rec, b0, b1, b0, live, px, C0, C1, C2, Tacc, last, stopped, walked, full, nflat);
     count_walk(a, walked, full, nflat);
     if (nseg == 1) {                       // the whole list: final result
         if (inside) write_pixel(a, pix, P, C0, C1, C2, Tacc, last);
@@ -284,7 +282,7 @@ __global__ void __launch_bounds__(TILE_PX) raster_merge_kernel(const RasterArgs 
 // Replay: one CTA per segment item; walks the segment again for the pixels
 // whose walk stops in it, from their T_in, and writes their final result; the
 // segment's share of C and the final T replace its pass-A entry.
-template <bool FILTER>
+template <bool FILTER, bool PIX>
 __global__ void __launch_bounds__(TILE_PX) raster_replay_kernel(const RasterArgs a, const SegArgs g, int ntiles) {
     __shared__ float4 s_rec[REC_F4][TILE_PX];
     uint2 tw;
@@ -320,7 +318,8 @@ __global__ void __launch_bounds__(TILE_PX) raster_replay_kernel(const RasterArgs
     const uint32_t seg = seg_length_dev(g);
     const uint32_t b0 = range.x + tw.y * seg, b1 = min(range.y, b0 + seg);
     bool stopped = false;
-    walk_entries<FILTER>(a, s_rec, b0, b1, range.x, mine, px, C0, C1, C2, T, last, stopped, walked, full, nflat);
+    walk_entries<FILTER, PIX>(a, s_rec, b0, b1, range.x, mine, px, C0, C1, C2, T, last, stopped, walked, full,
+                              nflat);
     if (mine) {
         g.seg_c[(size_t)w * TILE_PX + threadIdx.x] = make_float4(C0, C1, C2, T);
         if (inside) write_pixel(a, pix, P, cin.x + C0, cin.y + C1, cin.z + C2, T, last);
@@ -354,7 +353,7 @@ uint32_t raster_slots() {
     if (dev < 0 || dev >= 64) dev = 0;
     if (!slots[dev]) {
         int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, raster_seg_kernel<true, true>, TILE_PX, 0) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, raster_seg_kernel<true, true, false>, TILE_PX, 0) !=
                 cudaSuccess || per_sm < 1) {
             cudaGetLastError();
             per_sm = 16;
@@ -419,15 +418,15 @@ SegArgs split_args(uint32_t *scratch, int ntiles, int64_t *items) {
     return g;
 }
 
-template <bool FILTER>
+template <bool FILTER, bool PIX>
 static void launch_raster_passes(const RasterArgs &a, const SegArgs &g, int ntiles, unsigned later, int64_t wmax,
                                  cudaStream_t s, cudaEvent_t main0, cudaEvent_t main1) {
     if (main0) cudaEventRecord(main0, s);
-    raster_seg_kernel<FILTER, true><<<ntiles, TILE_PX, 0, s>>>(a, g);
+    raster_seg_kernel<FILTER, true, PIX><<<ntiles, TILE_PX, 0, s>>>(a, g);
     if (main1) cudaEventRecord(main1, s);
-    raster_seg_kernel<FILTER, false><<<later, TILE_PX, 0, s>>>(a, g);
+    raster_seg_kernel<FILTER, false, PIX><<<later, TILE_PX, 0, s>>>(a, g);
     raster_merge_kernel<<<ntiles, TILE_PX, 0, s>>>(a, g);
-    raster_replay_kernel<FILTER><<<(unsigned)wmax, TILE_PX, 0, s>>>(a, g, ntiles);
+    raster_replay_kernel<FILTER, PIX><<<(unsigned)wmax, TILE_PX, 0, s>>>(a, g, ntiles);
     note_launches(4);
 }
 
@@ -461,10 +460,14 @@ cudaError_t launch_raster_split(const RasterArgs &a, int ntiles, bool filter, ui
     ez = cudaMemsetAsync(g.need_item, 0, sizeof(uint32_t) * (size_t)wmax, s);
     if (ez != cudaSuccess) return ez;
     const unsigned later = (unsigned)(wmax - ntiles);
-    if (filter)
-        launch_raster_passes<true>(a, g, ntiles, later, wmax, s, main0, main1);
+    if (filter && a.pixtest)
+        launch_raster_passes<true, true>(a, g, ntiles, later, wmax, s, main0, main1);
+    else if (filter)
+        launch_raster_passes<true, false>(a, g, ntiles, later, wmax, s, main0, main1);
+    else if (a.pixtest)
+        launch_raster_passes<false, true>(a, g, ntiles, later, wmax, s, main0, main1);
     else
-        launch_raster_passes<false>(a, g, ntiles, later, wmax, s, main0, main1);
+        launch_raster_passes<false, false>(a, g, ntiles, later, wmax, s, main0, main1);
     if (a.keep_T) {
         raster_suffix_kernel<<<ntiles, TILE_PX, 0, s>>>(g);
         note_launches(1);

@@ -23,6 +23,7 @@ struct RasterArgs {
     const uint32_t *flat_slot;
     const float *flat_T, *flat_G;
     int additive;
+    int pixtest;           // 1: the records hold the pinhole (pixel-space) pre-test
     int footprint;         // 0: the pixel's own differentials; 1: isotropic reduction; 2: z/f sizing
     float zax[3];          // z/f: optical axis (world); zf_scale = 1 / (2 f_x)
     float zf_scale;
@@ -78,6 +79,9 @@ __device__ __forceinline__ void load_pixel(const RasterArgs &a, int64_t pix, int
     px.dxdx = dot3(px.dx, px.dx);
     px.dxdy = dot3(px.dx, px.dy);
     px.dydy = dot3(px.dy, px.dy);
+    const uint32_t p32 = (uint32_t)pix, w32 = (uint32_t)a.W;
+    px.pc[0] = (float)(p32 % w32) + 0.5f;
+    px.pc[1] = (float)(p32 / w32) + 0.5f;
 }
 
 // ---------------------------------------------------------------- long-list split (forward and adjoint)

@@ -46,7 +46,7 @@ __device__ __forceinline__ bool ts_emit(const RasterArgs &a, float alpha, uint32
 
 }  // namespace
 
-template <bool FILTER>
+template <bool FILTER, bool PIX>
 __global__ void __launch_bounds__(TILE_PX) raster_tstar_kernel(const RasterArgs a) {
     __shared__ float4 s_rec[REC_F4][TILE_PX];
     __shared__ uint32_t s_gid[TILE_PX];
@@ -82,9 +82,7 @@ __global__ void __launch_bounds__(TILE_PX) raster_tstar_kernel(const RasterArgs 
         const int nb = (int)min((uint32_t)TILE_PX, range.y - start);
         if (!done) walked += (uint32_t)nb;
         for (int b = 0; b < nb && !done; ++b) {
-            const float4 r4 = s_rec[4][b], r5 = s_rec[5][b], r6 = s_rec[6][b];
-            if (!pretest<float>(r4.x, r4.y, r4.z, r4.w, r5.x, r5.y, r5.z, r5.w, r6.x, r6.y, r6.z, r6.w, px.d))
-                continue;
+            if (!staged_pretest<PIX>(s_rec, b, px)) continue;
             ++full;
             const float r7x = s_rec[7][b].x;
             const GaussRec<float> g = rec_f32(s_rec[0][b], s_rec[1][b], s_rec[2][b], s_rec[3][b].w, r7x);
@@ -159,10 +157,14 @@ __global__ void __launch_bounds__(TILE_PX) raster_tstar_kernel(const RasterArgs 
 
 cudaError_t launch_raster_tstar(const RasterArgs &a, int ntiles, bool filter, cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;
-    if (filter)
-        raster_tstar_kernel<true><<<ntiles, TILE_PX, 0, s>>>(a);
+    if (filter && a.pixtest)
+        raster_tstar_kernel<true, true><<<ntiles, TILE_PX, 0, s>>>(a);
+    else if (filter)
+        raster_tstar_kernel<true, false><<<ntiles, TILE_PX, 0, s>>>(a);
+    else if (a.pixtest)
+        raster_tstar_kernel<false, true><<<ntiles, TILE_PX, 0, s>>>(a);
     else
-        raster_tstar_kernel<false><<<ntiles, TILE_PX, 0, s>>>(a);
+        raster_tstar_kernel<false, false><<<ntiles, TILE_PX, 0, s>>>(a);
     note_launches(1);
     return cudaGetLastError();
 }
