@@ -429,21 +429,40 @@ def bench_c1(args):
 
 # ---------------------------------------------------------------- the oracle on the host (CPU leg)
 
-def cpu_baseline(sc, cam, budget_s=10.0):
-    """The FP64 oracle as it stands, on the host cores, on a bounded pixel sample."""
+def _oracle_rate(sc, cam, budget_s, seed):
+    """Pixels per second of the oracle on random pixels of cam, the sample grown until
+    one call takes about budget_s / 4."""
     import oracle
-    rng = np.random.default_rng(1)
-    npx = 16
+    rng = np.random.default_rng(seed)
+    cap = min(65536, cam.n_pixels)
+    npx = min(16, cap)
     while True:
         pix = rng.choice(cam.n_pixels, size=npx, replace=False).astype(np.int32)
         t0 = time.perf_counter()
         oracle.render(cam, sc, pix=pix)
         t = time.perf_counter() - t0
-        if t > budget_s / 4 or npx >= 65536:
+        if t > budget_s / 4 or npx >= cap:
             break
-        npx = int(min(65536, npx * max(2.0, min(8.0, budget_s / 4 / max(t, 1e-3)))))
-    return {"value": npx / t / 1e6, "unit": "Mrays/s", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"{npx} random pixels of the 1280x720 view (same 500k-Gaussian scene, culled FP64 oracle)"}
+        npx = int(min(cap, npx * max(2.0, min(8.0, budget_s / 4 / max(t, 1e-3)))))
+    return npx / t, npx
+
+
+def cpu_baseline(sc, cam, budget_s=10.0, single_thread=True):
+    """The FP64 oracle as it stands, on the host cores, on a bounded pixel sample; and
+    (single_thread) the same on one core."""
+    import oracle
+    cores = oracle.num_threads()
+    rate, npx = _oracle_rate(sc, cam, budget_s, seed=1)
+    out = {"value": rate / 1e6, "unit": "Mrays/s", "cores": cores, "kind": "oracle",
+           "sample": f"{npx} random pixels of the 1280x720 view (same 500k-Gaussian scene, culled FP64 oracle)"}
+    if single_thread:
+        oracle.set_threads(1)
+        try:
+            rate1, npx1 = _oracle_rate(sc, cam, budget_s / 2, seed=3)
+        finally:
+            oracle.set_threads(cores)
+        out["single_thread"] = {"value": rate1 / 1e6, "unit": "Mrays/s", "cores": 1, "sample": f"{npx1} pixels"}
+    return out
 
 
 def oracle_error(work, px_per_view, seed=5):
@@ -481,7 +500,7 @@ def run_reference(args, rank, world):
     cams, sc = S.c2_cameras(), S.c2_scene()
     rho2 = oracle.floor_rho2([cams[0]], sc.means).astype(np.float32)
     scr = sc.with_rho2(rho2)
-    cal = cpu_baseline(scr, cams[0], budget_s=4.0)
+    cal = cpu_baseline(scr, cams[0], budget_s=4.0, single_thread=False)
     per_step_px = max(64, int(cal["value"] * 1e6 * 3.0))   # about 3 s of CPU work per step
     rng = np.random.default_rng(2)
     times = []

@@ -79,6 +79,11 @@ def num_threads() -> int:
     return int(lib().or_num_threads())
 
 
+def set_threads(n: int) -> None:
+    """Host threads of the oracle's parallel loops from now on (timing only)."""
+    lib().or_set_threads(int(n))
+
+
 def sh_basis(v) -> np.ndarray:
     """The oracle's real SH basis (degrees 0-3, 16 values) of directions v [n,3]."""
     v = _d(np.atleast_2d(v))

@@ -1589,3 +1589,12 @@ int or_num_threads(void) {
     return 1;
 #endif
 }
+
+/* Threads of the following parallel loops (timing only: no result depends on it). */
+void or_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
