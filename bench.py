@@ -53,6 +53,10 @@ WORKLOAD = "pinhole 1280x720 + 160x90 (1/8), 500k Gaussians (64 blobs + shell), 
 # of H' and K (Eq. 12) 22; the orthonormal basis of the footprint and q's parts 58;
 # N, det A, the quadratic form, T (Eq. 9) 37; compositing (Eq. 4) 9.
 FLOPS_PER_EVAL = 237
+# DRAM bytes (read + write) of one 1280x720 first-segment raster launch of this
+# workload, from ncu (dram__bytes_read.sum + dram__bytes_write.sum: 76.42 + 7.51 MB)
+# on this kernel's current code; to be taken again whenever the kernel changes.
+RASTER_MAIN_TRAFFIC_BYTES = 83.93e6
 
 
 class ClockSampler:
@@ -264,8 +268,9 @@ def bench_c2(args, world, local_rank, peak_tflops):
     v0 = views[0]
     achieved = FLOPS_PER_EVAL * v0["n_evaluated"] / (v0["ms_raster_main"] * 1e-3) / 1e12
     out["roofline"] = {
-        "bound": "alu", "kernel": "raster_seg_kernel<FILTER=1, FIRST=1> (1280x720 view)", "achieved": achieved,
-        "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
+        "bound": "alu", "kernel": "raster_seg_kernel<FILTER=1, FIRST=1, PIX=1> (1280x720 view)", "achieved": achieved,
+        "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+        "traffic": RASTER_MAIN_TRAFFIC_BYTES, "traffic_unit": "bytes per launch (ncu)",
         "peak_basis": "measured FP32 FMA throughput of this device (conegs_measure_fp32_peak; FMA = 2 flops)",
         "flops_per_eval": FLOPS_PER_EVAL, "evals_per_launch": v0["n_evaluated"],
         "entries_walked_per_launch": v0["n_walked"], "ms_per_launch": v0["ms_raster_main"],
