@@ -47,6 +47,10 @@ cudaError_t launch_compact(const uint32_t *counts, const uint32_t *pos, int64_t 
 cudaError_t launch_gather(const uint32_t *src, const uint32_t *idx, int64_t n, uint32_t *dst, cudaStream_t s);
 cudaError_t launch_ranges(const uint32_t *keys, int64_t n, uint2 *ranges, int ntiles, cudaStream_t s);
 int64_t radix_scratch_words(int64_t n);
+// Scratch words of a render's two radix sorts (M depth keys, Pn tile ids).
+static int64_t sort_scratch_words(int64_t M, int64_t Pn) {
+    return std::max(radix_scratch_words(std::max<int64_t>(M, 1)), radix_scratch_words(std::max<int64_t>(Pn, 1)));
+}
 cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *alt_keys, uint32_t *alt_vals, int64_t n,
                              int begin_bit, int end_bit, uint32_t *scratch, cudaStream_t s);
 cudaError_t launch_floor(const CamParams *cams_dev, int nv, const float *means, int64_t n, float *rho2,
@@ -617,8 +621,9 @@ static conegs_status render_back(conegs_view *v, float *out_rgb, float *out_T, u
     TRY(ensure(ctx, v->pair_gid, sizeof(uint32_t) * pp, s));
     TRY(ensure(ctx, v->pair_tile_alt, sizeof(uint32_t) * pp, s));
     TRY(ensure(ctx, v->pair_gid_alt, sizeof(uint32_t) * pp, s));
-    const int64_t sortmax = std::max<int64_t>(std::max<int64_t>(M, Pn), 1);
-    TRY(ensure(ctx, v->rs_scr, sizeof(uint32_t) * (size_t)radix_scratch_words(sortmax), s));
+    // the two sorts (depth keys of M items, tile ids of Pn) plan their grids apart, and a
+    // small sort may use more CTAs than a larger one: room for whichever needs more
+    TRY(ensure(ctx, v->rs_scr, sizeof(uint32_t) * (size_t)sort_scratch_words(M, Pn), s));
     TRY(ensure(ctx, v->scan_scr, sizeof(uint32_t) * (size_t)scan_scratch_words(std::max<int64_t>(M, n)), s));
     CUDA_TRY(launch_compact(v->counts.as<uint32_t>(), v->vispos.as<uint32_t>(), n, v->gview.as<float4>(),
                             v->dkeys.as<uint32_t>(), v->dvals.as<uint32_t>(), s));
@@ -720,7 +725,7 @@ static size_t back_bytes(const conegs_view *v, unsigned flags) {
     const int64_t M = (int64_t)v->h_sums[1], Pn = (int64_t)v->h_sums[0], F = (int64_t)v->h_sums[4];
     const int64_t nt = (int64_t)v->cam.tiles_x * v->cam.tiles_y, P = (int64_t)v->cam.W * v->cam.H;
     size_t b = sizeof(uint32_t) * (6 * (size_t)M + 4 * (size_t)Pn);
-    b += sizeof(uint32_t) * (size_t)radix_scratch_words(std::max<int64_t>(std::max<int64_t>(M, Pn), 1));
+    b += sizeof(uint32_t) * (size_t)sort_scratch_words(M, Pn);
     b += sizeof(uint32_t) * (size_t)scan_scratch_words(std::max<int64_t>(std::max<int64_t>(M, n), nt));
     b += sizeof(uint32_t) * (size_t)split_scratch_words((int)nt) + sizeof(uint2) * (size_t)nt;
     b += sizeof(float) * 4 * (size_t)P + sizeof(uint32_t) * (size_t)P;

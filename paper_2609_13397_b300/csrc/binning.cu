@@ -644,7 +644,7 @@ __device__ __forceinline__ uint32_t bin_walk_box(const CamParams &c, const float
 }
 
 template <int MODE, bool UT>
-__global__ void __launch_bounds__(32 * BIN_WARPS, 3) bin_kernel(CamParams c, GaussArgs ua,
+__global__ void __launch_bounds__(32 * BIN_WARPS, 4) bin_kernel(CamParams c, GaussArgs ua,
                                                                 const float *__restrict__ binrec,
                                                                 const float4 *__restrict__ gview,
                                                                 const float2 *__restrict__ gcone,

@@ -238,7 +238,10 @@ constexpr int RS_WARPS = RS_THREADS / 32;
 constexpr int RS_ROUNDS_LARGE = 16;                 // 32-item rounds per warp per tile: 4096-item tiles
 constexpr int RS_ROUNDS_SMALL = 4;                  // 1024-item tiles for sorts of up to RS_SMALL_N items
 constexpr int64_t RS_SMALL_N = 1 << 20;             // (their 4096-item tiles would not fill the SMs)
-constexpr int RS_BLOCKS_PER_SM = 4;
+
+// Resident scatter CTAs per SM of the tile size (queried once per device): the
+// grid is one wave of them, each CTA walking its own contiguous chunk.
+int rs_blocks_per_sm(bool small);
 
 struct RsPlan {
     int64_t n;
@@ -253,7 +256,7 @@ RsPlan rs_plan(int64_t n) {
     p.rounds = n <= RS_SMALL_N ? RS_ROUNDS_SMALL : RS_ROUNDS_LARGE;
     const int64_t tile = (int64_t)RS_THREADS * p.rounds;
     int64_t tiles = div_up(n, tile);
-    int64_t blocks = std::min<int64_t>(tiles, (int64_t)RS_BLOCKS_PER_SM * num_sms());
+    int64_t blocks = std::min<int64_t>(tiles, (int64_t)rs_blocks_per_sm(p.rounds == RS_ROUNDS_SMALL) * num_sms());
     if (blocks < 1) blocks = 1;
     int64_t tiles_per = div_up(tiles, blocks);
     p.chunk = tiles_per * tile;
@@ -302,13 +305,19 @@ __global__ void __launch_bounds__(RS_THREADS) rs_downsweep(const uint32_t *__res
     for (int64_t t0 = beg; t0 < end; t0 += RS_TILE) {
         const int tn = (int)std::min<int64_t>(RS_TILE, end - t0);
         uint32_t k[RS_ROUNDS], v[RS_ROUNDS], rank[RS_ROUNDS];
-        // 1. stable rank of each item among the earlier items of its warp with the same digit
+        // 0. every load of the tile issued before any is used (all in flight at once)
 #pragma unroll
         for (int r = 0; r < RS_ROUNDS; ++r) {
             const int li = wid * (RS_ROUNDS * 32) + r * 32 + lane;
             const bool ok = li < tn;
             k[r] = ok ? kin[t0 + li] : 0u;
             v[r] = ok ? vin[t0 + li] : 0u;
+        }
+        // 1. stable rank of each item among the earlier items of its warp with the same digit
+#pragma unroll
+        for (int r = 0; r < RS_ROUNDS; ++r) {
+            const int li = wid * (RS_ROUNDS * 32) + r * 32 + lane;
+            const bool ok = li < tn;
             const uint32_t dig = ok ? ((k[r] >> shift) & mask) : (256u + (uint32_t)lane);
             const uint32_t peers = __match_any_sync(0xffffffffu, dig);
             const int leader = __ffs(peers) - 1;
@@ -372,6 +381,27 @@ __global__ void __launch_bounds__(RS_THREADS) rs_downsweep(const uint32_t *__res
         }
         __syncthreads();
     }
+}
+
+int rs_blocks_per_sm(bool small) {
+    static int cached[64][2] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    int &c = cached[dev][small ? 1 : 0];
+    if (!c) {
+        int per_sm = 0;
+        const cudaError_t e = small ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                          &per_sm, rs_downsweep<RS_ROUNDS_SMALL>, RS_THREADS, 0)
+                                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                          &per_sm, rs_downsweep<RS_ROUNDS_LARGE>, RS_THREADS, 0);
+        if (e != cudaSuccess || per_sm < 1) {
+            cudaGetLastError();
+            per_sm = 2;
+        }
+        c = std::min(per_sm, 8);
+    }
+    return c;
 }
 
 // Stable sort of (keys, vals) on bits [begin_bit, end_bit); result ends in

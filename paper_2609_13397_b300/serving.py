@@ -131,7 +131,9 @@ class Server:
     def _worker(self, k: int):
         view, stream = self._slots[k]
         torch.cuda.set_device(self.ctx.device)
-        host = {}
+        # the slot's pinned host buffer for images (rgb and T), grown to the largest
+        # request seen and reused: allocating pinned memory per request size stalls
+        host = None
         while True:
             item = self._take()
             if item is None:
@@ -141,12 +143,11 @@ class Server:
             res = Result(req.rid, cam.width, cam.height, 0, ta, 0.0, 0.0)
             need = 0
             try:
-                key = (cam.height, cam.width)
-                if key not in host:
-                    host.clear()
-                    host[key] = (torch.empty(3, cam.height, cam.width, pin_memory=True),
-                                 torch.empty(cam.height, cam.width, pin_memory=True))
-                h_rgb, h_T = host[key]
+                P = cam.height * cam.width
+                if host is None or host.numel() < 4 * P:
+                    host = torch.empty(max(4 * P, 0 if host is None else host.numel() * 3 // 2), pin_memory=True)
+                h_rgb = host[:3 * P].view(3, cam.height, cam.width)
+                h_T = host[3 * P:4 * P].view(cam.height, cam.width)
                 with torch.cuda.stream(stream):
                     view.set_camera_from(cam, stream=stream)
                     _, nbytes = view.render_count(flags=req.flags, stream=stream)
