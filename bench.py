@@ -382,6 +382,10 @@ def bench_c5(args):
     reqs = [serving.Request(r.rid, r.arrival_s, r.camera)
             for r in S.c5_requests(args.c5_requests, rate_hz=args.c5_rate, seed=0)]
     srv = serving.Server(ctx, slots=args.c5_slots, mem_budget_bytes=64 << 30)
+    # the server's start-up: every slot renders the stream's largest pinhole and fisheye
+    # request once (its buffers grow now), then a few requests of the stream
+    srv.warm([max((r.camera for r in reqs if r.camera.model == m), key=lambda c: c.width * c.height)
+              for m in (S.PINHOLE, S.KB_FISHEYE) if any(r.camera.model == m for r in reqs)])
     warm = [serving.Request(10_000 + r.rid, 0.0, r.camera) for r in reqs[:2 * args.c5_slots]]
     for r in warm:
         srv.submit(r)

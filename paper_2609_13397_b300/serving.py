@@ -98,6 +98,7 @@ class Server:
         self.keep_images = (1 << 62) if keep_images is True else int(keep_images)
         self._kept = 0
         self._slots = [(ctx.view(), torch.cuda.Stream(device=ctx.device)) for _ in range(slots)]
+        self._host = [None] * slots     # per slot: pinned host buffer for images (rgb and T)
         self._queue: collections.deque = collections.deque()
         self._cv = threading.Condition()
         self._closed = False
@@ -128,12 +129,32 @@ class Server:
                 return None
             return self._queue.popleft()
 
+    def _host_images(self, k: int, cam):
+        """Views (rgb, T) into slot k's pinned host buffer, grown to the largest request
+        seen and reused: allocating pinned memory per request stalls every slot."""
+        P = cam.height * cam.width
+        host = self._host[k]
+        if host is None or host.numel() < 4 * P:
+            host = torch.empty(max(4 * P, 0 if host is None else host.numel() * 3 // 2), pin_memory=True)
+            self._host[k] = host
+        return host[:3 * P].view(3, cam.height, cam.width), host[3 * P:4 * P].view(cam.height, cam.width)
+
+    def warm(self, cameras, flags: int = 0):
+        """Render each camera once on every slot, before requests arrive: the slots' device
+        buffers and pinned host buffers grow to those sizes now, not while serving."""
+        with self._cv:
+            if self._queue:
+                raise RuntimeError("warm() runs before requests are submitted")
+        for k, (view, stream) in enumerate(self._slots):
+            for cam in cameras:
+                h_rgb, h_T = self._host_images(k, cam)
+                with torch.cuda.stream(stream):
+                    view.set_camera_from(cam, stream=stream)
+                    view.render_host(h_rgb, h_T, flags=flags, stream=stream)
+
     def _worker(self, k: int):
         view, stream = self._slots[k]
         torch.cuda.set_device(self.ctx.device)
-        # the slot's pinned host buffer for images (rgb and T), grown to the largest
-        # request seen and reused: allocating pinned memory per request size stalls
-        host = None
         while True:
             item = self._take()
             if item is None:
@@ -143,11 +164,7 @@ class Server:
             res = Result(req.rid, cam.width, cam.height, 0, ta, 0.0, 0.0)
             need = 0
             try:
-                P = cam.height * cam.width
-                if host is None or host.numel() < 4 * P:
-                    host = torch.empty(max(4 * P, 0 if host is None else host.numel() * 3 // 2), pin_memory=True)
-                h_rgb = host[:3 * P].view(3, cam.height, cam.width)
-                h_T = host[3 * P:4 * P].view(cam.height, cam.width)
+                h_rgb, h_T = self._host_images(k, cam)
                 with torch.cuda.stream(stream):
                     view.set_camera_from(cam, stream=stream)
                     _, nbytes = view.render_count(flags=req.flags, stream=stream)

@@ -113,3 +113,25 @@ def test_malformed_request_fails_alone(scene_ctx):
     srv.close()
     assert res[2].error is not None and "ERR_ARG" in res[2].error
     assert all(r.error is None for k, r in enumerate(res) if k != 2)
+
+
+def test_warm_slots_then_serve(scene_ctx):
+    """Warming every slot with the largest cameras first changes no result: the
+    requests served after it are bitwise those of a server that was not warmed."""
+    from paper_2609_13397_b300 import serving
+    from paper_2609_13397_b300.serving import Request
+    reqs = [Request(r.rid, 0.0, r.camera) for r in _requests(10, seed=7)]
+    big = [max((r.camera for r in reqs if r.camera.model == m), key=lambda c: c.width * c.height)
+           for m in (S.PINHOLE, S.KB_FISHEYE) if any(r.camera.model == m for r in reqs)]
+    out = []
+    for warm in (False, True):
+        srv = serving.Server(scene_ctx, slots=3, keep_images=True)
+        if warm:
+            srv.warm(big)
+        for r in reqs:
+            srv.submit(r)
+        out.append(srv.drain(len(reqs)))
+        srv.close()
+    for a, b in zip(*out):
+        assert a.error is None and b.error is None
+        assert torch.equal(a.rgb, b.rgb) and torch.equal(a.T, b.T)
