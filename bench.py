@@ -243,25 +243,41 @@ def bench_c2(args, world, local_rank, peak_tflops):
         loss.append({"mean_abs_rgb": float(d.mean()), "frac_px_over_1_255": float((d.amax(0) > 1 / 255).float().mean())})
     out["bin_ut"] = {"value": rays * world / (ut_ms * 1e-3) / 1e6, "unit": "Mrays/s", "ms_per_step": ut_ms,
                      "n_pairs": ut_pairs, "n_pairs_rule": [v["n_pairs"] for v in views], "vs_exact": loss}
-    # end to end through the host-buffer entry point: camera in, image out every step
-    host = [(torch.empty(3, c.height, c.width, pin_memory=True), torch.empty(c.height, c.width, pin_memory=True))
-            for c in cams]
+    # end to end through the host-buffer entry points: every step sets both cameras from
+    # host parameters and reads both images (rgb and T) back into pinned host memory.
+    # Pipelined (render_host_batch_async): a step's copies overlap the next step's
+    # render; every copy has landed when the clock stops.  Blocking (render_host_batch):
+    # each step waits for its own copies.
+    host = [[(torch.empty(3, c.height, c.width, pin_memory=True), torch.empty(c.height, c.width, pin_memory=True))
+             for c in cams] for _ in range(2)]
 
-    def e2e_step():
+    def set_cams():
         for v, c, st in zip(b.views, cams, b.streams):
             v.set_camera_from(c, stream=st)
-        ctx.render_host_batch(b.views, host, streams=b.streams)
-    for _ in range(2):
-        e2e_step()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        e2e_step()
-    torch.cuda.synchronize()
-    e2e_ms = reduce_step_time((time.perf_counter() - t0) * 1e3 / args.steps, dev)
-    out["e2e"] = {"value": rays * world / (e2e_ms * 1e-3) / 1e6, "unit": "Mrays/s",
+
+    def e2e_run(steps, pipelined):
+        for k in range(steps):
+            set_cams()
+            if pipelined:
+                ctx.render_host_batch_async(b.views, host[k % 2], streams=b.streams)
+            else:
+                ctx.render_host_batch(b.views, host[k % 2], streams=b.streams)
+        for v in b.views:
+            v.host_wait()
+    e2e = {}
+    for pipelined in (True, False):
+        e2e_run(2, pipelined)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_run(args.steps, pipelined)
+        torch.cuda.synchronize()
+        e2e[pipelined] = reduce_step_time((time.perf_counter() - t0) * 1e3 / args.steps, dev)
+    out["e2e"] = {"value": rays * world / (e2e[True] * 1e-3) / 1e6, "unit": "Mrays/s", "ms_per_step": e2e[True],
                   "h2d_bytes_per_step": len(cams) * (4 + 4 + 12) * 4,
-                  "d2h_bytes_per_step": sum(4 * 4 * c.width * c.height for c in cams)}
+                  "d2h_bytes_per_step": sum(4 * 4 * c.width * c.height for c in cams),
+                  "api": "render_host_batch_async (copies overlap the next step's render)",
+                  "blocking": {"value": rays * world / (e2e[False] * 1e-3) / 1e6, "unit": "Mrays/s",
+                               "ms_per_step": e2e[False], "api": "render_host_batch"}}
     # roofline of the dominant kernel: the 1280x720 view's first-segment raster launch
     # (its tile lists are all shorter than the segment length, so the launch does the
     # view's whole raster work), timed by CUDA events on its stream inside the step

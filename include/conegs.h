@@ -230,6 +230,23 @@ conegs_status conegs_render_count(conegs_view *view, unsigned flags, int64_t *pa
 conegs_status conegs_render_host_batch(int n, conegs_view *const *views, float *const *out_rgb_host,
                                        float *const *out_T_host, unsigned flags, void *const *streams);
 
+/* Pipelined form of conegs_render_host_batch: renders the views and ENQUEUES
+ * the copies of their images (rgb, and T where out_T_host and its entry are
+ * non-NULL) to the host buffers, then returns without waiting for them.  Each
+ * view renders into one of two view-owned device staging images in turn and
+ * copies it back on a copy stream of its own, so the copy of one call overlaps
+ * the next call's render of the same view (that render waits only for the copy
+ * of two calls back, which used the same staging image).
+ * Ownership: the host buffers must be pinned (the copies are asynchronous) and
+ * stay valid, unread and unwritten until conegs_view_host_wait(view) returns.
+ * Errors as conegs_render_batch; after an error no copy of that call is pending. */
+conegs_status conegs_render_host_batch_async(int n, conegs_view *const *views, float *const *out_rgb_host,
+                                             float *const *out_T_host, unsigned flags, void *const *streams);
+
+/* Blocks until every image copy that conegs_render_host_batch_async enqueued for
+ * this view has reached host memory.  CONEGS_ERR_CUDA if a copy failed. */
+conegs_status conegs_view_host_wait(conegs_view *view);
+
 /* Same as conegs_render, with HOST output buffers (pinned memory recommended):
  * renders into view-owned device memory and copies the result back on
  * `stream`; returns after the copy has completed. */

@@ -165,6 +165,25 @@ class Context:
         check(lib().conegs_render_host_batch(n, hv, rgb, Ts, flags, st), "render_host_batch")
         return list(host_outs)
 
+    def render_host_batch_async(self, views: Sequence["View"], host_outs, flags: int = 0, streams=None):
+        """render_host_batch without the wait: the image copies into the (pinned) host
+        tensors [(rgb, T or None)] are enqueued on each view's copy stream; read them
+        only after ``view.host_wait()``.  The copy of one call overlaps the next call's
+        render of the same view."""
+        n = len(views)
+        P = ctypes.c_void_p
+        hv = (P * n)(*[v._h for v in views])
+        rgb = (P * n)(*[_ptr(o[0]) for o in host_outs])
+        Ts = (P * n)(*[_ptr(o[1]) for o in host_outs])
+        st = (P * n)(*[_stream(None if streams is None else streams[i]) for i in range(n)])
+        for v in views:
+            v._bump()
+            # keeps the host tensors alive while their copies may be in flight (at most
+            # the last two calls' per view: a render waits for the copy of two calls back)
+            v._pending = v._pending[-1:] + [host_outs]
+        check(lib().conegs_render_host_batch_async(n, hv, rgb, Ts, flags, st), "render_host_batch_async")
+        return list(host_outs)
+
     def compute_floor(self, views: Sequence["View"], stream=None) -> torch.Tensor:
         """Eq. 11 training-frequency floor of the current scene's Gaussians over ``views``."""
         out = torch.empty(self.n, device=self.device, dtype=torch.float32)
@@ -183,6 +202,7 @@ class View:
         self._h = h
         self.width = self.height = 0
         self._token = 0       # bumped by every call that replaces the view's adjoint state
+        self._pending = []    # host tensors of copies in flight (render_host_batch_async)
 
     def _bump(self):
         self._token += 1
@@ -232,6 +252,12 @@ class View:
         check(lib().conegs_render_host(self._h, _ptr(out_rgb_host), _ptr(out_T_host), flags, _stream(stream)),
               "render_host")
         return out_rgb_host, out_T_host
+
+    def host_wait(self):
+        """Wait until every image copy that render_host_batch_async enqueued for this view
+        has reached host memory."""
+        check(lib().conegs_view_host_wait(self._h), "view_host_wait")
+        self._pending.clear()
 
     def render_backward(self, dL_drgb: torch.Tensor, dL_dT: Optional[torch.Tensor] = None, grads=None,
                         stream=None):

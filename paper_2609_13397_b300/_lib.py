@@ -57,6 +57,8 @@ def lib():
         "conegs_render": ([P, P, P, c_uint, P], c_int),
         "conegs_render_batch": ([c_int, P, P, P, c_uint, P], c_int),
         "conegs_render_host_batch": ([c_int, P, P, P, c_uint, P], c_int),
+        "conegs_render_host_batch_async": ([c_int, P, P, P, c_uint, P], c_int),
+        "conegs_view_host_wait": ([P], c_int),
         "conegs_render_host": ([P, P, P, c_uint, P], c_int),
         "conegs_render_count": ([P, c_uint, ctypes.POINTER(c_int64), ctypes.POINTER(c_size_t), P], c_int),
         "conegs_render_backward": ([P, P, P, P, P, P, P, P, P], c_int),
@@ -83,7 +85,8 @@ def exported_symbols():
     """Names declared in include/conegs.h (for the ABI completeness test)."""
     return ["conegs_create", "conegs_destroy", "conegs_last_error", "conegs_version", "conegs_set_scene",
             "conegs_view_create", "conegs_view_destroy", "conegs_set_camera", "conegs_render", "conegs_render_batch",
-            "conegs_render_host_batch", "conegs_render_host", "conegs_render_count",
+            "conegs_render_host_batch", "conegs_render_host_batch_async", "conegs_view_host_wait",
+            "conegs_render_host", "conegs_render_count",
             "conegs_render_backward", "conegs_get_stats", "conegs_compute_floor", "conegs_get_rays",
             "conegs_get_tile_table", "conegs_get_bin_counts", "conegs_get_pairs", "conegs_radix_sort_pairs",
             "conegs_radix_sort_pairs_noalloc", "conegs_measure_fp32_peak"]

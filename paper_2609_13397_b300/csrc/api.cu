@@ -196,6 +196,14 @@ struct conegs_view {
     DevBuf evaluated;
     cudaStream_t last_stream = nullptr;
     bool has_stream = false;
+    // pipelined host renders: two device staging images used in turn, their copies
+    // to the host on a stream of the view's own, each marked done by copied[k]
+    DevBuf stage_rgb[2], stage_T[2];
+    int stage = 0;
+    bool stage_pending[2] = {false, false};
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t copied[2] = {nullptr, nullptr};
+    cudaEvent_t rendered = nullptr;
 };
 
 namespace {
@@ -408,6 +416,16 @@ void conegs_view_destroy(conegs_view *v) {
     if (v->done) {
         cudaEventSynchronize(v->done);
         cudaEventDestroy(v->done);
+    }
+    if (v->copy_stream) {
+        cudaStreamSynchronize(v->copy_stream);
+        cudaStreamDestroy(v->copy_stream);
+    }
+    for (cudaEvent_t e : {v->copied[0], v->copied[1], v->rendered})
+        if (e) cudaEventDestroy(e);
+    for (int k = 0; k < 2; ++k) {
+        release(ctx, v->stage_rgb[k]);
+        release(ctx, v->stage_T[k]);
     }
     DevBuf *bufs[] = {&v->d, &v->dx, &v->dy, &v->valid, &v->table, &v->super, &v->mcam, &v->rec, &v->gview, &v->gcone, &v->gflag, &v->gell, &v->bincache, &v->binlist,
                       &v->counts, &v->vispos, &v->scan_scr, &v->dkeys, &v->dvals, &v->dkeys_alt, &v->dvals_alt,
@@ -854,6 +872,68 @@ conegs_status conegs_render_host_batch(int n, conegs_view *const *views, float *
         TRY(view_end(v, s));
     }
     for (int i = 0; i < n; ++i) CUDA_TRY(cudaStreamSynchronize(streams ? (cudaStream_t)streams[i] : (cudaStream_t)0));
+    return CONEGS_OK;
+}
+
+conegs_status conegs_render_host_batch_async(int n, conegs_view *const *views, float *const *out_rgb_host,
+                                             float *const *out_T_host, unsigned flags, void *const *streams) {
+    if (n < 0 || (n > 0 && (!views || !out_rgb_host)))
+        return fail(CONEGS_ERR_ARG, "render_host_batch_async: bad argument");
+    if (n == 0) return CONEGS_OK;
+    std::vector<float *> drgb((size_t)n), dT((size_t)n);
+    auto stream_of = [&](int i) { return streams ? (cudaStream_t)streams[i] : (cudaStream_t)0; };
+    for (int i = 0; i < n; ++i) {
+        if (!views[i] || !out_rgb_host[i])
+            return fail(CONEGS_ERR_ARG, "render_host_batch_async: NULL view or output %d", i);
+        if (!views[i]->has_cam) return fail(CONEGS_ERR_STATE, "render_host_batch_async: view %d has no camera", i);
+        conegs_view *v = views[i];
+        DeviceGuard g(v->ctx->device);
+        if (!v->copy_stream) {
+            cudaError_t e = cudaStreamCreateWithFlags(&v->copy_stream, cudaStreamNonBlocking);
+            for (int k = 0; k < 2 && e == cudaSuccess; ++k)
+                e = cudaEventCreateWithFlags(&v->copied[k], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&v->rendered, cudaEventDisableTiming);
+            if (e != cudaSuccess) return fail(CONEGS_ERR_CUDA, "render_host_batch_async: %s", cudaGetErrorString(e));
+        }
+        const cudaStream_t s = stream_of(i);
+        const int k = v->stage;
+        const size_t P = (size_t)v->cam.W * v->cam.H;
+        TRY(view_begin(v, s));
+        // the staging image's previous copy (two calls back) must be done before it is
+        // written again, or freed and grown
+        if (v->stage_pending[k]) CUDA_TRY(cudaStreamWaitEvent(s, v->copied[k], 0));
+        TRY(ensure(v->ctx, v->stage_rgb[k], sizeof(float) * 3 * P, s));
+        TRY(ensure(v->ctx, v->stage_T[k], sizeof(float) * P, s));
+        TRY(view_end(v, s));
+        drgb[(size_t)i] = v->stage_rgb[k].as<float>();
+        dT[(size_t)i] = v->stage_T[k].as<float>();
+    }
+    TRY(conegs_render_batch(n, views, drgb.data(), dT.data(), flags, streams));
+    DeviceGuard g(views[0]->ctx->device);
+    for (int i = 0; i < n; ++i) {
+        conegs_view *v = views[i];
+        const cudaStream_t s = stream_of(i);
+        const int k = v->stage;
+        const size_t P = (size_t)v->cam.W * v->cam.H;
+        CUDA_TRY(cudaEventRecord(v->rendered, s));
+        CUDA_TRY(cudaStreamWaitEvent(v->copy_stream, v->rendered, 0));
+        CUDA_TRY(cudaMemcpyAsync(out_rgb_host[i], v->stage_rgb[k].p, sizeof(float) * 3 * P, cudaMemcpyDeviceToHost,
+                                 v->copy_stream));
+        if (out_T_host && out_T_host[i])
+            CUDA_TRY(cudaMemcpyAsync(out_T_host[i], v->stage_T[k].p, sizeof(float) * P, cudaMemcpyDeviceToHost,
+                                     v->copy_stream));
+        CUDA_TRY(cudaEventRecord(v->copied[k], v->copy_stream));
+        v->stage_pending[k] = true;
+        v->stage ^= 1;
+    }
+    return CONEGS_OK;
+}
+
+conegs_status conegs_view_host_wait(conegs_view *v) {
+    if (!v) return fail(CONEGS_ERR_ARG, "view_host_wait: NULL view");
+    if (!v->copy_stream) return CONEGS_OK;
+    DeviceGuard g(v->ctx->device);
+    CUDA_TRY(cudaStreamSynchronize(v->copy_stream));
     return CONEGS_OK;
 }
 

@@ -373,6 +373,39 @@ def test_render_host_batch_equals_device_render(cg):
         assert torch.equal(r.cpu(), hr) and torch.equal(t.cpu(), ht)
 
 
+def test_pipelined_host_renders_equal_device_renders(cg):
+    """render_host_batch_async: six calls in a row, the cameras changing every call,
+    each into its own pinned host buffers and read only after host_wait; every image
+    equals the device render of its camera (the staging images alternate, so a
+    render never overwrites an image whose copy is still in flight)."""
+    cams = [S.pinhole(160, 96, 150.0), S.c3_camera(128, 112)]
+    sc = S.blob_scene(8000, seed=5, cam=cams[0])
+    ctx = cg.Context(0)
+    ctx.set_scene_from(sc)
+    views = [ctx.view() for _ in cams]
+    streams = [torch.cuda.Stream() for _ in views]
+    poses = [S.look_at((0.05 * k, 0.0, 0.0), (0.1 * k, 0.05, 4.0)) for k in range(6)]
+    outs = []
+    for k, pose in enumerate(poses):
+        for v, c in zip(views, cams):
+            c2 = S.Camera(c.model, c.width, c.height, c.fx, c.fy, c.cx, c.cy, k=c.k, cam_to_world=pose,
+                          theta_lim=c.theta_lim)
+            v.set_camera_from(c2)
+        host = [(torch.empty(3, c.height, c.width, pin_memory=True), torch.empty(c.height, c.width, pin_memory=True))
+                for c in cams]
+        ctx.render_host_batch_async(views, host, streams=streams)
+        outs.append(host)
+    for v in views:
+        v.host_wait()
+    ref_view = ctx.view()
+    for pose, host in zip(poses, outs):
+        for c, (h_rgb, h_T) in zip(cams, host):
+            ref_view.set_camera_from(S.Camera(c.model, c.width, c.height, c.fx, c.fy, c.cx, c.cy, k=c.k,
+                                              cam_to_world=pose, theta_lim=c.theta_lim))
+            rgb, T = ref_view.render()
+            assert torch.equal(rgb.cpu(), h_rgb) and torch.equal(T.cpu(), h_T)
+
+
 @pytest.mark.parametrize("seed", range(8))
 def test_pair_counts_bit_exact_random(cg, oracle_lib, seed):
     """Random cameras (pinhole and Kannala-Brandt, random poses, intrinsics and
