@@ -16,6 +16,10 @@ already has.  A large request waiting for memory holds only its own slot: the
 other slots keep taking later, smaller requests past it.  A render that still
 exceeds the library's own budget (CONEGS_ERR_BUDGET) is retried once memory
 frees up.
+
+Start-up: Server.warm(cameras) renders the given cameras (say the largest a
+stream will see) once on every slot, so that the slots' device and pinned host
+buffers grow before requests arrive instead of stalling the first ones.
 """
 from __future__ import annotations
 
