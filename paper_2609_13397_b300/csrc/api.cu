@@ -22,6 +22,8 @@ namespace conegs {
 // launchers defined in the other translation units
 cudaError_t launch_ray_table(const CamParams &c, float *d, float *dx, float *dy, uint8_t *valid, cudaStream_t s);
 cudaError_t launch_tile_tables(const CamParams &c, float *table, float *super, float *mcam, cudaStream_t s);
+cudaError_t launch_footprint_min(const float *d, const float *dx, const float *dy, const uint8_t *valid, int64_t P,
+                                 float *out, cudaStream_t s);
 cudaError_t launch_gauss_scene_rule(const SceneParams &sp, float *binrec, cudaStream_t s);
 cudaError_t launch_bin_count(const CamParams &c, const float *binrec, const float4 *gview, const float2 *gcone,
                              const uint8_t *gflag, const float *table, const float *super, const float *mcam,
@@ -35,7 +37,7 @@ cudaError_t launch_bin_emit(const CamParams &c, const float *binrec, const float
                             const float4 *gell, bool ut, cudaStream_t s);
 cudaError_t launch_scene_cache(const SceneParams &sp, float *W, float *sig_eff, cudaStream_t s);
 cudaError_t launch_view_records(const CamParams &c, const SceneParams &sp, const float *mcam, float mzf,
-                                int fov_cull, int pixtest, float4 *rec, float4 *gview, float2 *gcone, uint8_t *gflag,
+                                int fov_cull, int pixtest, int dilute, float4 *rec, float4 *gview, float2 *gcone, uint8_t *gflag,
                                 float4 *gell, unsigned long long *nflat, uint8_t *gflat, cudaStream_t s);
 int64_t scan_scratch_words(int64_t n);
 cudaError_t exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *scratch, int pred,
@@ -496,11 +498,13 @@ conegs_status conegs_set_camera(conegs_view *v, int model, int width, int height
     TRY(ensure(ctx, v->valid, P, s));
     TRY(ensure(ctx, v->table, sizeof(float) * 6 * nt, s));
     TRY(ensure(ctx, v->super, sizeof(float) * 6 * ns, s));
-    TRY(ensure(ctx, v->mcam, (3 + 17) * sizeof(float), s));
+    TRY(ensure(ctx, v->mcam, (3 + 17 + 1) * sizeof(float), s));
     TRY(ensure(ctx, v->ranges, sizeof(uint2) * nt, s));
     TRY(ensure(ctx, v->last, sizeof(uint32_t) * P, s));
     CUDA_TRY(launch_ray_table(c, v->d.as<float>(), v->dx.as<float>(), v->dy.as<float>(), v->valid.as<uint8_t>(), s));
     CUDA_TRY(launch_tile_tables(c, v->table.as<float>(), v->super.as<float>(), v->mcam.as<float>(), s));
+    CUDA_TRY(launch_footprint_min(v->d.as<float>(), v->dx.as<float>(), v->dy.as<float>(), v->valid.as<uint8_t>(),
+                                  (int64_t)c.W * c.H, v->mcam.as<float>() + 20, s));
     v->cam = c;
     v->has_cam = true;
     v->counted = false;
@@ -589,7 +593,8 @@ static conegs_status render_front(conegs_view *v, unsigned flags, cudaStream_t s
     // [4] pairs of flat Gaussians, [5] scratch (flat slot counter)
     CUDA_TRY(cudaMemsetAsync(v->sums.as<unsigned long long>() + 2, 0, 2 * sizeof(unsigned long long), s));
     CUDA_TRY(launch_view_records(c, sp, v->mcam.as<float>(), zf_bound(c, flags), (flags & CONEGS_BIN_UT) ? 0 : 1,
-                                 pixel_pretest(c, flags), v->rec.as<float4>(), v->gview.as<float4>(),
+                                 pixel_pretest(c, flags), (flags & (CONEGS_FILTER_NONE | CONEGS_FILTER_ZF)) ? 0 : 1,
+                                 v->rec.as<float4>(), v->gview.as<float4>(),
                                  v->gcone.as<float2>(), v->gflag.as<uint8_t>(), v->gell.as<float4>(),
                                  v->sums.as<unsigned long long>() + 3, v->gflat.as<uint8_t>(), s));
     {

@@ -13,6 +13,8 @@
 //            half-angle products.  Newton on theta runs in FP32 and is
 //            polished in FP64 only near the edge of the field of view.
 // Layout: SoA float d[3][P], dx[3][P], dy[3][P], uint8 valid[P] (P = W*H).
+#include <algorithm>
+
 #include "camera.cuh"
 
 namespace conegs {
@@ -34,6 +36,46 @@ __global__ void __launch_bounds__(256) ray_table_kernel(CamParams c, float *__re
     rotate(c, vy, w);
     dy[p] = ok ? w[0] : 0.0f; dy[P + p] = ok ? w[1] : 0.0f; dy[2 * P + p] = ok ? w[2] : 0.0f;
     valid[p] = ok ? 1 : 0;
+}
+
+// Smallest footprint of the view: min over valid pixels of the smaller eigenvalue
+// of [dp_i . dp_j] / 3, dp_i = delta_i - (delta_i . d) d the half-edge
+// differentials across the centre ray (per unit depth).  At depth t a pixel's
+// world footprint of Eq. 8 (its half-edges f_i = t (delta_i - c_i d)) has both
+// eigenvalues at least t^2 times this.  The result (float bits, non-negative)
+// goes to *out, which must hold 0xffffffff before the launch.
+__global__ void __launch_bounds__(256) footprint_min_kernel(const float *__restrict__ d, const float *__restrict__ dx,
+                                                            const float *__restrict__ dy,
+                                                            const uint8_t *__restrict__ valid, int64_t P,
+                                                            unsigned int *__restrict__ out) {
+    float best = 3.0e38f;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
+        if (!valid[p]) continue;
+        const float d0 = d[p], d1 = d[P + p], d2 = d[2 * P + p];
+        const float x0 = dx[p], x1 = dx[P + p], x2 = dx[2 * P + p];
+        const float y0 = dy[p], y1 = dy[P + p], y2 = dy[2 * P + p];
+        const float sx = x0 * d0 + x1 * d1 + x2 * d2, sy = y0 * d0 + y1 * d1 + y2 * d2;
+        const float u0 = x0 - sx * d0, u1 = x1 - sx * d1, u2 = x2 - sx * d2;
+        const float v0 = y0 - sy * d0, v1 = y1 - sy * d1, v2 = y2 - sy * d2;
+        const float a = (u0 * u0 + u1 * u1 + u2 * u2) / 3.0f, b = (u0 * v0 + u1 * v1 + u2 * v2) / 3.0f,
+                    c = (v0 * v0 + v1 * v1 + v2 * v2) / 3.0f;
+        const float h = 0.5f * (a - c);
+        const float lmax = 0.5f * (a + c) + sqrtf(h * h + b * b);
+        const float lmin = lmax > 0.0f ? fmaxf(a * c - b * b, 0.0f) / lmax : 0.0f;   // det / lmax: no cancellation
+        best = fminf(best, lmin);
+    }
+    for (int o = 16; o > 0; o >>= 1) best = fminf(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if ((threadIdx.x & 31) == 0 && best < 3.0e38f) atomicMin(out, __float_as_uint(best));
+}
+
+cudaError_t launch_footprint_min(const float *d, const float *dx, const float *dy, const uint8_t *valid, int64_t P,
+                                 float *out, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(out, 0xff, sizeof(float), s);
+    if (e != cudaSuccess || P == 0) return e;
+    const unsigned grid = (unsigned)std::min<int64_t>(div_up(P, 256), 4 * (int64_t)num_sms());
+    footprint_min_kernel<<<grid, 256, 0, s>>>(d, dx, dy, valid, P, reinterpret_cast<unsigned int *>(out));
+    note_launches(1);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_ray_table(const CamParams &c, float *d, float *dx, float *dy, uint8_t *valid, cudaStream_t s) {

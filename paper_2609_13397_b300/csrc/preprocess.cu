@@ -192,11 +192,11 @@ __device__ void pixel_cone_ellipse(const CamParams &c, const float W[9], const f
 }
 
 // t* bound of the binning rule (see cone_half_angle); false = no useful bound.
-__device__ bool tstar_bound(float kap, float s2, float r1, float L, float m, float &tb) {
+// rf: the bound on |x* - mu| (x* the ray's closest-response point) it came with.
+__device__ bool tstar_bound(float kap, float s2, float r1, float L, float m, float &tb, float &rf) {
     const float s = sqrtf(s2);
     const float c = kap * r1 * sqrtf(m);
     const float rfc = 255.0f * kap * s;
-    float rf;
     if (c < 1.0f) {
         const float tbf = (L + kap * s) / (1.0f - c);
         rf = fminf(kap * sqrtf(s2 + tbf * tbf * r1 * r1 * m), rfc);
@@ -211,7 +211,7 @@ __device__ bool tstar_bound(float kap, float s2, float r1, float L, float m, flo
 
 // Per view: binning direction/depth (the FP32 rule) and the raster record.
 __global__ void __launch_bounds__(256) view_records_kernel(CamParams c, SceneParams sp, const float *__restrict__ mcam,
-                                                           float mzf, int fov_cull, int pixtest,
+                                                           float mzf, int fov_cull, int pixtest, int dilute,
                                                            float4 *__restrict__ rec, float4 *__restrict__ gview,
                                                            float2 *__restrict__ gcone,
                                                            uint8_t *__restrict__ gflag,
@@ -266,7 +266,14 @@ __global__ void __launch_bounds__(256) view_records_kernel(CamParams c, ScenePar
         ge[2] = make_float4(el[8], el[9], el[10], el[11]);
     }
     // rasteriser pre-test, with the exact kappa^2 = 2 ln(255 sigma): its ray-direction
-    // form (u, g, C), or on pinhole views (pixtest) the pixel-space ellipse
+    // form (u, g, C), or on pinhole views (pixtest) the pixel-space ellipse.
+    // With `dilute`, the footprint's dilution of the peak narrows it: det A >= 1 +
+    // tr(W Sigma_render W^T) >= 1 + tr(Sigma_render) / s_eff,max^2, and both
+    // eigenvalues of the world footprint at depth t* are at least t*^2 mu_min (the
+    // view's smallest per-unit-depth footprint) so that, clamped by the floor
+    // (Eq. 12), tr(Sigma_render) >= 2 (t*^2 mu_min - rho^2)_+; with t* >= L - r_f
+    // (r_f bounding |x* - mu|), a pair reaching alpha >= 1/255 has
+    // q^T A^-1 q <= 2 ln(255 sigma_eff) - ln(1 + x), x = 2 ((L - r_f)^2 mu_min - rho^2)_+ / s_eff,max^2.
     float g[3] = {0.f, 0.f, 0.f}, C[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float pu[3] = {dx, dy, dz};
     float4 pix4 = make_float4(0.f, 0.f, 0.f, 0.f), pix5 = make_float4(0.f, -1.0f, 0.f, 0.f);   // rejects every pixel
@@ -281,13 +288,26 @@ __global__ void __launch_bounds__(256) view_records_kernel(CamParams c, ScenePar
             pu[0] = pu[1] = pu[2] = 0.0f;
             C[0] = C[1] = C[2] = 100.0f;
         } else if (L > 0.0f) {
-            float tb;
+            float tb, rf;
             const float rr = sqrtf(s2 / s2mn);    // s_max / s_min; |f_i| <= (r + 1/r)/2 |delta_i|
-            tstar_bound(sqrtf(k2), s2, fmaxf(0.5f * (rr + 1.0f / rr) * 1.00001f, 1.0f), L, m, tb);
-            if (pixtest)
-                pixel_cone_ellipse(c, W, ou, 1.01f * k2, tb * tb * m * 1.001f, mu, pix4, pix5);
-            else
-                cone_quadric(W, ou, 1.01f * k2, tb * tb * m * 1.001f, L, g, C);
+            tstar_bound(sqrtf(k2), s2, fmaxf(0.5f * (rr + 1.0f / rr) * 1.00001f, 1.0f), L, m, tb, rf);
+            float kq2 = k2;
+            if (dilute) {
+                const float mumin = fmaxf(__uint_as_float(__float_as_uint(mcam[20]) == 0xffffffffu ? 0u
+                                                          : __float_as_uint(mcam[20])), 0.0f) * 0.99f;
+                const float tlo = fmaxf(L - rf * 1.001f, 0.0f);
+                const float x = 2.0f * fmaxf(tlo * tlo * mumin - rho2 * 1.001f, 0.0f) / s2;
+                kq2 = 2.0f * logf(255.0f * sp.sig_eff[i] * 1.0001f) - log1pf(x * 0.999f);
+            }
+            if (!(kq2 > 0.0f)) {
+                // the footprint dilutes this Gaussian below the alpha cut in this view
+                pu[0] = pu[1] = pu[2] = 0.0f;
+                C[0] = C[1] = C[2] = 100.0f;
+            } else if (pixtest) {
+                pixel_cone_ellipse(c, W, ou, 1.01f * kq2, tb * tb * m * 1.001f, mu, pix4, pix5);
+            } else {
+                cone_quadric(W, ou, 1.01f * kq2, tb * tb * m * 1.001f, L, g, C);
+            }
         } else {
             pix5 = make_float4(0.f, 1.0f, 0.f, 0.f);     // mu at the optical centre: every pixel
         }
@@ -340,11 +360,12 @@ cudaError_t launch_scene_cache(const SceneParams &sp, float *W, float *sig_eff, 
 }
 
 cudaError_t launch_view_records(const CamParams &c, const SceneParams &sp, const float *mcam, float mzf,
-                                int fov_cull, int pixtest, float4 *rec, float4 *gview, float2 *gcone, uint8_t *gflag,
+                                int fov_cull, int pixtest, int dilute, float4 *rec, float4 *gview, float2 *gcone,
+                                uint8_t *gflag,
                                 float4 *gell, unsigned long long *nflat, uint8_t *gflat, cudaStream_t s) {
     if (sp.n == 0) return cudaSuccess;
-    view_records_kernel<<<(unsigned)div_up(sp.n, 256), 256, 0, s>>>(c, sp, mcam, mzf, fov_cull, pixtest, rec, gview,
-                                                                    gcone, gflag, gell, nflat, gflat);
+    view_records_kernel<<<(unsigned)div_up(sp.n, 256), 256, 0, s>>>(c, sp, mcam, mzf, fov_cull, pixtest, dilute, rec,
+                                                                    gview, gcone, gflag, gell, nflat, gflat);
     note_launches(1);
     return cudaGetLastError();
 }
