@@ -383,6 +383,94 @@ __global__ void __launch_bounds__(RS_THREADS) rs_downsweep(const uint32_t *__res
     }
 }
 
+// Sorts of at most RS_ONE_MAX items: one CTA does every pass in shared memory
+// (one launch instead of an upsweep, a scan and a scatter per pass), with the
+// same stable ranking as rs_downsweep: each warp ranks its items in lane order
+// (match_any), the warps in order, the digits by an exclusive scan.
+constexpr int RS_ONE_THREADS = 256;
+constexpr int RS_ONE_WARPS = RS_ONE_THREADS / 32;
+constexpr int RS_ONE_ROUNDS = 8;
+constexpr int RS_ONE_MAX = RS_ONE_THREADS * RS_ONE_ROUNDS;   // 2048 items
+
+__global__ void __launch_bounds__(RS_ONE_THREADS) rs_one_cta_kernel(uint32_t *__restrict__ keys,
+                                                                    uint32_t *__restrict__ vals, int n, int begin_bit,
+                                                                    int end_bit) {
+    __shared__ uint32_t sk[2][RS_ONE_MAX], sv[2][RS_ONE_MAX];
+    __shared__ uint32_t wcount[RS_ONE_WARPS][256];
+    __shared__ uint32_t wsum[RS_ONE_WARPS];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    for (int i = threadIdx.x; i < n; i += RS_ONE_THREADS) {
+        sk[0][i] = keys[i];
+        sv[0][i] = vals[i];
+    }
+    int cur = 0;
+    for (int shift = begin_bit; shift < end_bit; shift += 8) {
+        const uint32_t mask = (1u << min(8, end_bit - shift)) - 1u;
+#pragma unroll
+        for (int w = 0; w < RS_ONE_WARPS; ++w) wcount[w][threadIdx.x] = 0u;
+        __syncthreads();
+        uint32_t k[RS_ONE_ROUNDS], v[RS_ONE_ROUNDS], rank[RS_ONE_ROUNDS];
+#pragma unroll
+        for (int r = 0; r < RS_ONE_ROUNDS; ++r) {
+            const int li = wid * (RS_ONE_ROUNDS * 32) + r * 32 + lane;
+            const bool ok = li < n;
+            k[r] = ok ? sk[cur][li] : 0u;
+            v[r] = ok ? sv[cur][li] : 0u;
+            const uint32_t dig = ok ? ((k[r] >> shift) & mask) : (256u + (uint32_t)lane);
+            const uint32_t peers = __match_any_sync(0xffffffffu, dig);
+            const int leader = __ffs(peers) - 1;
+            uint32_t old = 0u;
+            if (ok && lane == leader) {
+                old = wcount[wid][dig];
+                wcount[wid][dig] = old + (uint32_t)__popc(peers);
+            }
+            old = __shfl_sync(0xffffffffu, old, leader);
+            rank[r] = ok ? old + (uint32_t)__popc(peers & lt) : 0xffffffffu;
+            __syncwarp();
+        }
+        __syncthreads();
+        // digit d (thread d): total, exclusive scan over digits, per-warp bases
+        const int d = threadIdx.x;
+        uint32_t tot = 0;
+#pragma unroll
+        for (int w = 0; w < RS_ONE_WARPS; ++w) tot += wcount[w][d];
+        uint32_t x = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[wid] = x;
+        __syncthreads();
+        uint32_t before = 0;
+#pragma unroll
+        for (int w = 0; w < RS_ONE_WARPS; ++w) before += w < wid ? wsum[w] : 0u;
+        uint32_t b = before + x - tot;
+#pragma unroll
+        for (int w = 0; w < RS_ONE_WARPS; ++w) {
+            const uint32_t c = wcount[w][d];
+            wcount[w][d] = b;
+            b += c;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < RS_ONE_ROUNDS; ++r) {
+            if (rank[r] != 0xffffffffu) {
+                const uint32_t slot = wcount[wid][(k[r] >> shift) & mask] + rank[r];
+                sk[cur ^ 1][slot] = k[r];
+                sv[cur ^ 1][slot] = v[r];
+            }
+        }
+        __syncthreads();
+        cur ^= 1;
+    }
+    for (int i = threadIdx.x; i < n; i += RS_ONE_THREADS) {
+        keys[i] = sk[cur][i];
+        vals[i] = sv[cur][i];
+    }
+}
+
 int rs_blocks_per_sm(bool small) {
     static int cached[64][2] = {};
     int dev = 0;
@@ -409,6 +497,11 @@ int rs_blocks_per_sm(bool small) {
 cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *alt_keys, uint32_t *alt_vals, int64_t n,
                              int begin_bit, int end_bit, uint32_t *scratch, cudaStream_t s) {
     if (n <= 1 || end_bit <= begin_bit) return cudaSuccess;
+    if (n <= RS_ONE_MAX) {
+        rs_one_cta_kernel<<<1, RS_ONE_THREADS, 0, s>>>(keys, vals, (int)n, begin_bit, end_bit);
+        note_launches(1);
+        return cudaGetLastError();
+    }
     const RsPlan p = rs_plan(n);
     const int64_t cnt = 256LL * p.blocks;
     uint32_t *counts = scratch, *offs = scratch + cnt, *scan_scr = scratch + 2 * cnt;
