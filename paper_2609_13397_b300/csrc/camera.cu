@@ -38,17 +38,20 @@ __global__ void __launch_bounds__(256) ray_table_kernel(CamParams c, float *__re
     valid[p] = ok ? 1 : 0;
 }
 
-// Smallest footprint of the view: min over valid pixels of the smaller eigenvalue
-// of [dp_i . dp_j] / 3, dp_i = delta_i - (delta_i . d) d the half-edge
-// differentials across the centre ray (per unit depth).  At depth t a pixel's
-// world footprint of Eq. 8 (its half-edges f_i = t (delta_i - c_i d)) has both
-// eigenvalues at least t^2 times this.  The result (float bits, non-negative)
-// goes to *out, which must hold 0xffffffff before the launch.
+// Footprint extremes of the view, per unit depth, over its valid pixels:
+//   out[0]: the smallest eigenvalue of [dp_i . dp_j] / 3, dp_i = delta_i -
+//           (delta_i . d) d the half-edge differentials across the centre ray.
+//           At depth t a pixel's world footprint of Eq. 8 (its half-edges
+//           f_i = t (delta_i - c_i d)) has both eigenvalues at least t^2 times this.
+//   out[1]: the largest eigenvalue of [delta_i . delta_j] / 3 (the differentials
+//           themselves), so that t^2 sum_i delta_i delta_i^T / 3 <= t^2 out[1] I.
+// Float bits of non-negative values: *out must hold 0xffffffff and out[1] zero
+// before the launch (unsigned min and max order them as the floats).
 __global__ void __launch_bounds__(256) footprint_min_kernel(const float *__restrict__ d, const float *__restrict__ dx,
                                                             const float *__restrict__ dy,
                                                             const uint8_t *__restrict__ valid, int64_t P,
                                                             unsigned int *__restrict__ out) {
-    float best = 3.0e38f;
+    float best = 3.0e38f, top = 0.0f;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
         if (!valid[p]) continue;
         const float d0 = d[p], d1 = d[P + p], d2 = d[2 * P + p];
@@ -63,14 +66,25 @@ __global__ void __launch_bounds__(256) footprint_min_kernel(const float *__restr
         const float lmax = 0.5f * (a + c) + sqrtf(h * h + b * b);
         const float lmin = lmax > 0.0f ? fmaxf(a * c - b * b, 0.0f) / lmax : 0.0f;   // det / lmax: no cancellation
         best = fminf(best, lmin);
+        const float A = (x0 * x0 + x1 * x1 + x2 * x2) / 3.0f, B = (x0 * y0 + x1 * y1 + x2 * y2) / 3.0f,
+                    C = (y0 * y0 + y1 * y1 + y2 * y2) / 3.0f;
+        const float H = 0.5f * (A - C);
+        top = fmaxf(top, 0.5f * (A + C) + sqrtf(H * H + B * B));
     }
-    for (int o = 16; o > 0; o >>= 1) best = fminf(best, __shfl_xor_sync(0xffffffffu, best, o));
-    if ((threadIdx.x & 31) == 0 && best < 3.0e38f) atomicMin(out, __float_as_uint(best));
+    for (int o = 16; o > 0; o >>= 1) {
+        best = fminf(best, __shfl_xor_sync(0xffffffffu, best, o));
+        top = fmaxf(top, __shfl_xor_sync(0xffffffffu, top, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (best < 3.0e38f) atomicMin(out, __float_as_uint(best));
+        atomicMax(out + 1, __float_as_uint(top));
+    }
 }
 
 cudaError_t launch_footprint_min(const float *d, const float *dx, const float *dy, const uint8_t *valid, int64_t P,
                                  float *out, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(out, 0xff, sizeof(float), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(out + 1, 0, sizeof(float), s);
     if (e != cudaSuccess || P == 0) return e;
     const unsigned grid = (unsigned)std::min<int64_t>(div_up(P, 256), 4 * (int64_t)num_sms());
     footprint_min_kernel<<<grid, 256, 0, s>>>(d, dx, dy, valid, P, reinterpret_cast<unsigned int *>(out));

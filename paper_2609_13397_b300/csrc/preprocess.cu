@@ -84,7 +84,8 @@ __device__ float2 cone_half_angle(float kap, float s2, float r1, float L, float 
 // world terms x = mu - x* (x* the closest-response point on the ray) lies in
 // {x : x^T (Sigma_eff + F)^-1 x <= kappa^2} with F the world footprint
 // (Eq. 12: Sigma_render <= Sigma_fp,eff), whose part across the ray is at most
-// t*^2 m (m >= (|dx|^2 + |dy|^2)/3).  So the centre ray must meet the
+// t*^2 m I (m at least the largest eigenvalue of [delta_i . delta_j]/3 over the
+// view's pixels).  So the centre ray must meet the
 // ellipsoid mu + {x : x^T M x <= 1}, M = (kappa'^2 (Sigma_eff + tau I))^-1,
 // tau = t_b^2 m, kappa'^2 = 1.01 kappa^2 (margin for FP32 rounding).  The line
 // o + t d meets it iff d^T C d <= 0, C = (1 - 1/v^T M v) M - (M v)(M v)^T / v^T M v,
@@ -210,7 +211,10 @@ __device__ bool tstar_bound(float kap, float s2, float r1, float L, float m, flo
 }
 
 // Per view: binning direction/depth (the FP32 rule) and the raster record.
-__global__ void __launch_bounds__(256) view_records_kernel(CamParams c, SceneParams sp, const float *__restrict__ mcam,
+// Latency-bound (one Gaussian per thread, dependent loads and transcendental
+// chains): four CTAs per SM (64 registers, a few bytes of spill) run it faster
+// than three at the 79 registers it would otherwise take.
+__global__ void __launch_bounds__(256, 4) view_records_kernel(CamParams c, SceneParams sp, const float *__restrict__ mcam,
                                                            float mzf, int fov_cull, int pixtest, int dilute,
                                                            float4 *__restrict__ rec, float4 *__restrict__ gview,
                                                            float2 *__restrict__ gcone,
@@ -267,22 +271,34 @@ __global__ void __launch_bounds__(256) view_records_kernel(CamParams c, ScenePar
     }
     // rasteriser pre-test, with the exact kappa^2 = 2 ln(255 sigma): its ray-direction
     // form (u, g, C), or on pinhole views (pixtest) the pixel-space ellipse.
-    // With `dilute`, the footprint's dilution of the peak narrows it: det A >= 1 +
-    // tr(W Sigma_render W^T) >= 1 + tr(Sigma_render) / s_eff,max^2, and both
-    // eigenvalues of the world footprint at depth t* are at least t*^2 mu_min (the
-    // view's smallest per-unit-depth footprint) so that, clamped by the floor
-    // (Eq. 12), tr(Sigma_render) >= 2 (t*^2 mu_min - rho^2)_+; with t* >= L - r_f
-    // (r_f bounding |x* - mu|), a pair reaching alpha >= 1/255 has
-    // q^T A^-1 q <= 2 ln(255 sigma_eff) - ln(1 + x), x = 2 ((L - r_f)^2 mu_min - rho^2)_+ / s_eff,max^2.
+    // The ellipsoid is that of Sigma_eff + tau I, tau = t_b^2 mu_max (mu_max: the
+    // view's largest per-unit-depth footprint eigenvalue, t_b >= t*): the
+    // whitened footprint M_perp W (t*^2 sum_i delta_i delta_i^T / 3) W^T M_perp is
+    // at most tau M_perp W W^T M_perp, so q^T A^-1 q is at least the ray's
+    // distance in the metric of I + tau W W^T.
+    // With `dilute`, the footprint's dilution of the peak narrows it.  Clamped by
+    // the floor (Eq. 12), the world footprint Sigma_render has eigenvalues
+    // (lambda_j - rho^2)_+, with both lambda_j >= t*^2 mu_min (the view's smallest
+    // per-unit-depth footprint); the two non-zero eigenvalues nu_k of W
+    // Sigma_render W^T then have nu_1 + nu_2 >= c (1/s_max^2 + 1/s_mid^2) and
+    // nu_1 nu_2 >= c^2 / (s_max^2 s_mid^2) (interlacing of the compression of W^T W,
+    // whose eigenvalues are 1/s_eff,a^2), c = (t*^2 mu_min - rho^2)_+, so that
+    // det A >= (1 + c/s_max^2)(1 + c/s_mid^2).  With t* >= L - r_f (r_f bounding
+    // |x* - mu|), a pair reaching alpha >= 1/255 has
+    // q^T A^-1 q <= 2 ln(255 sigma_eff) - ln(1 + c/s_max^2) - ln(1 + c/s_mid^2).
     float g[3] = {0.f, 0.f, 0.f}, C[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float pu[3] = {dx, dy, dz};
     float4 pix4 = make_float4(0.f, 0.f, 0.f, 0.f), pix5 = make_float4(0.f, -1.0f, 0.f, 0.f);   // rejects every pixel
     {
         const float sig = 1.0f / (1.0f + expf(-load_scalar(sp.logits, i, sp.storage)));
         const float k2 = 2.0f * logf(255.0f * sig);
-        const float lmax = fmaxf(fmaxf(sp.log_scales[3 * i], sp.log_scales[3 * i + 1]), sp.log_scales[3 * i + 2]);
-        const float lmin = fminf(fminf(sp.log_scales[3 * i], sp.log_scales[3 * i + 1]), sp.log_scales[3 * i + 2]);
+        const float l0 = sp.log_scales[3 * i], l1 = sp.log_scales[3 * i + 1], l2 = sp.log_scales[3 * i + 2];
+        const float lmax = fmaxf(fmaxf(l0, l1), l2), lmin = fminf(fminf(l0, l1), l2);
+        const float lmid = fmaxf(fminf(l0, l1), fminf(fmaxf(l0, l1), l2));
         const float s2 = expf(2.0f * lmax) * 1.00001f + rho2, s2mn = expf(2.0f * lmin) * 0.99999f + rho2;
+        // footprint bound of the ellipsoid: largest eigenvalue per unit depth, or
+        // the z/f variant's own bound
+        const float mlam = fmaxf(mcam[21] * 1.01f, mzf);
         if (!(k2 > 0.0f)) {
             // sigma < 1/255: never reaches the alpha cut (value 99 for every unit d)
             pu[0] = pu[1] = pu[2] = 0.0f;
@@ -296,17 +312,19 @@ __global__ void __launch_bounds__(256) view_records_kernel(CamParams c, ScenePar
                 const float mumin = fmaxf(__uint_as_float(__float_as_uint(mcam[20]) == 0xffffffffu ? 0u
                                                           : __float_as_uint(mcam[20])), 0.0f) * 0.99f;
                 const float tlo = fmaxf(L - rf * 1.001f, 0.0f);
-                const float x = 2.0f * fmaxf(tlo * tlo * mumin - rho2 * 1.001f, 0.0f) / s2;
-                kq2 = 2.0f * logf(255.0f * sp.sig_eff[i] * 1.0001f) - log1pf(x * 0.999f);
+                const float cf = fmaxf(tlo * tlo * mumin - rho2 * 1.001f, 0.0f);
+                const float s2md = expf(2.0f * lmid) * 1.00001f + rho2;
+                kq2 = 2.0f * logf(255.0f * sp.sig_eff[i] * 1.0001f) -
+                      0.999f * (log1pf(cf / s2) + log1pf(cf / s2md));
             }
             if (!(kq2 > 0.0f)) {
                 // the footprint dilutes this Gaussian below the alpha cut in this view
                 pu[0] = pu[1] = pu[2] = 0.0f;
                 C[0] = C[1] = C[2] = 100.0f;
             } else if (pixtest) {
-                pixel_cone_ellipse(c, W, ou, 1.01f * kq2, tb * tb * m * 1.001f, mu, pix4, pix5);
+                pixel_cone_ellipse(c, W, ou, 1.01f * kq2, tb * tb * mlam * 1.001f, mu, pix4, pix5);
             } else {
-                cone_quadric(W, ou, 1.01f * kq2, tb * tb * m * 1.001f, L, g, C);
+                cone_quadric(W, ou, 1.01f * kq2, tb * tb * mlam * 1.001f, L, g, C);
             }
         } else {
             pix5 = make_float4(0.f, 1.0f, 0.f, 0.f);     // mu at the optical centre: every pixel
