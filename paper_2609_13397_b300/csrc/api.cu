@@ -22,8 +22,8 @@ namespace conegs {
 // launchers defined in the other translation units
 cudaError_t launch_ray_table(const CamParams &c, float *d, float *dx, float *dy, uint8_t *valid, cudaStream_t s);
 cudaError_t launch_tile_tables(const CamParams &c, float *table, float *super, float *mcam, cudaStream_t s);
-cudaError_t launch_footprint_min(const float *d, const float *dx, const float *dy, const uint8_t *valid, int64_t P,
-                                 float *out, cudaStream_t s);
+cudaError_t launch_footprint_min(const CamParams &c, const float *d, const float *dx, const float *dy,
+                                 const uint8_t *valid, float *out, cudaStream_t s);
 cudaError_t launch_gauss_scene_rule(const SceneParams &sp, float *binrec, cudaStream_t s);
 cudaError_t launch_bin_count(const CamParams &c, const float *binrec, const float4 *gview, const float2 *gcone,
                              const uint8_t *gflag, const float *table, const float *super, const float *mcam,
@@ -498,13 +498,13 @@ conegs_status conegs_set_camera(conegs_view *v, int model, int width, int height
     TRY(ensure(ctx, v->valid, P, s));
     TRY(ensure(ctx, v->table, sizeof(float) * 6 * nt, s));
     TRY(ensure(ctx, v->super, sizeof(float) * 6 * ns, s));
-    TRY(ensure(ctx, v->mcam, (3 + 17 + 2) * sizeof(float), s));
+    TRY(ensure(ctx, v->mcam, MCAM_FLOATS * sizeof(float), s));
     TRY(ensure(ctx, v->ranges, sizeof(uint2) * nt, s));
     TRY(ensure(ctx, v->last, sizeof(uint32_t) * P, s));
     CUDA_TRY(launch_ray_table(c, v->d.as<float>(), v->dx.as<float>(), v->dy.as<float>(), v->valid.as<uint8_t>(), s));
     CUDA_TRY(launch_tile_tables(c, v->table.as<float>(), v->super.as<float>(), v->mcam.as<float>(), s));
-    CUDA_TRY(launch_footprint_min(v->d.as<float>(), v->dx.as<float>(), v->dy.as<float>(), v->valid.as<uint8_t>(),
-                                  (int64_t)c.W * c.H, v->mcam.as<float>() + 20, s));
+    CUDA_TRY(launch_footprint_min(c, v->d.as<float>(), v->dx.as<float>(), v->dy.as<float>(), v->valid.as<uint8_t>(),
+                                  v->mcam.as<float>() + FP_MIN, s));
     v->cam = c;
     v->has_cam = true;
     v->counted = false;

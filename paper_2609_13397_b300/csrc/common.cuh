@@ -17,6 +17,15 @@ constexpr float T_STOP = 1e-4f;
 constexpr float T_NEAR = 0.01f;
 constexpr int REC_F4 = 8;         // float4 words per per-view raster record
 constexpr int BINREC = 12;        // floats per Gaussian of the binning rule's scene record
+// Per-view footprint extremes (per unit depth) for the rasteriser's pre-test,
+// in the view's camera-bound block after the binning rule's words: the view-wide
+// smallest eigenvalue, then FP_BANDS polar-angle bands of it (band j: the pixel
+// rays at angle [j, j+1) pi / FP_BANDS from the optical axis), the view-wide
+// largest eigenvalue, then its bands.
+constexpr int FP_BANDS = 64;
+constexpr int FP_MIN = 20;                        // offset of the smallest eigenvalue block
+constexpr int FP_MAX = FP_MIN + 1 + FP_BANDS;     // offset of the largest eigenvalue block
+constexpr int MCAM_FLOATS = FP_MAX + 1 + FP_BANDS;
 
 // Camera passed by value to kernels.
 struct CamParams {

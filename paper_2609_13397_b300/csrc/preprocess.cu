@@ -210,6 +210,35 @@ __device__ bool tstar_bound(float kap, float s2, float r1, float L, float m, flo
     return true;
 }
 
+// The footprint extremes (per unit depth) over the pixels a Gaussian can reach:
+// the polar-angle bands of the view (see footprint_min_kernel) within beta of
+// the angle of its direction u from the optical axis (beta: the half-angle of
+// its binning cone, which holds every pixel ray it can reach alpha >= 1/255
+// with), widened by 2e-3 rad for the rounding of both angles.  Empty bands
+// are skipped; with none left, the view-wide values.
+__device__ void footprint_range(const CamParams &c, const float *__restrict__ mcam, const float u[3], float2 gc,
+                                float &mu_min, float &mu_max) {
+    const float *bmin = mcam + FP_MIN + 1, *bmax = mcam + FP_MAX + 1;
+    int j0 = 0, j1 = FP_BANDS - 1;
+    if (gc.x < 1.0f) {
+        const float cz = u[0] * c.R[2] + u[1] * c.R[5] + u[2] * c.R[8];
+        const float th = acosf(fminf(fmaxf(cz, -1.0f), 1.0f));
+        const float beta = 2.0f * asinf(gc.x) + 2e-3f;
+        const float band_scale = (float)FP_BANDS / 3.14159265f;
+        j0 = max(0, (int)floorf((th - beta) * band_scale));
+        j1 = min(FP_BANDS - 1, (int)floorf((th + beta) * band_scale));
+    }
+    unsigned int lo = 0xffffffffu, hi = 0u;
+    for (int j = j0; j <= j1; ++j) {
+        const unsigned int a = __float_as_uint(bmin[j]), b = __float_as_uint(bmax[j]);
+        lo = min(lo, a);        // non-negative floats order as their bits; empty: 0xffffffff
+        hi = max(hi, b);        // empty: 0
+    }
+    const unsigned int glo = __float_as_uint(mcam[FP_MIN]);
+    mu_min = __uint_as_float(lo != 0xffffffffu ? lo : (glo != 0xffffffffu ? glo : 0u));
+    mu_max = hi != 0u ? __uint_as_float(hi) : mcam[FP_MAX];
+}
+
 // Per view: binning direction/depth (the FP32 rule) and the raster record.
 // Latency-bound (one Gaussian per thread, dependent loads and transcendental
 // chains): four CTAs per SM (64 registers, a few bytes of spill) run it faster
@@ -272,14 +301,15 @@ __global__ void __launch_bounds__(256, 4) view_records_kernel(CamParams c, Scene
     // rasteriser pre-test, with the exact kappa^2 = 2 ln(255 sigma): its ray-direction
     // form (u, g, C), or on pinhole views (pixtest) the pixel-space ellipse.
     // The ellipsoid is that of Sigma_eff + tau I, tau = t_b^2 mu_max (mu_max: the
-    // view's largest per-unit-depth footprint eigenvalue, t_b >= t*): the
+    // largest per-unit-depth footprint eigenvalue over the pixels the Gaussian
+    // can reach, footprint_range; t_b >= t*): the
     // whitened footprint M_perp W (t*^2 sum_i delta_i delta_i^T / 3) W^T M_perp is
     // at most tau M_perp W W^T M_perp, so q^T A^-1 q is at least the ray's
     // distance in the metric of I + tau W W^T.
     // With `dilute`, the footprint's dilution of the peak narrows it.  Clamped by
     // the floor (Eq. 12), the world footprint Sigma_render has eigenvalues
-    // (lambda_j - rho^2)_+, with both lambda_j >= t*^2 mu_min (the view's smallest
-    // per-unit-depth footprint); the two non-zero eigenvalues nu_k of W
+    // (lambda_j - rho^2)_+, with both lambda_j >= t*^2 mu_min (the smallest
+    // per-unit-depth footprint over the same pixels); the two non-zero eigenvalues nu_k of W
     // Sigma_render W^T then have nu_1 + nu_2 >= c (1/s_max^2 + 1/s_mid^2) and
     // nu_1 nu_2 >= c^2 / (s_max^2 s_mid^2) (interlacing of the compression of W^T W,
     // whose eigenvalues are 1/s_eff,a^2), c = (t*^2 mu_min - rho^2)_+, so that
@@ -296,9 +326,11 @@ __global__ void __launch_bounds__(256, 4) view_records_kernel(CamParams c, Scene
         const float lmax = fmaxf(fmaxf(l0, l1), l2), lmin = fminf(fminf(l0, l1), l2);
         const float lmid = fmaxf(fminf(l0, l1), fminf(fmaxf(l0, l1), l2));
         const float s2 = expf(2.0f * lmax) * 1.00001f + rho2, s2mn = expf(2.0f * lmin) * 0.99999f + rho2;
-        // footprint bound of the ellipsoid: largest eigenvalue per unit depth, or
-        // the z/f variant's own bound
-        const float mlam = fmaxf(mcam[21] * 1.01f, mzf);
+        // footprint extremes per unit depth over the pixels the Gaussian can reach;
+        // the ellipsoid's bound is the largest eigenvalue, or the z/f variant's own
+        float mu_lo, mu_hi;
+        footprint_range(c, mcam, u, gc, mu_lo, mu_hi);
+        const float mlam = fmaxf(mu_hi * 1.01f, mzf);
         if (!(k2 > 0.0f)) {
             // sigma < 1/255: never reaches the alpha cut (value 99 for every unit d)
             pu[0] = pu[1] = pu[2] = 0.0f;
@@ -309,8 +341,7 @@ __global__ void __launch_bounds__(256, 4) view_records_kernel(CamParams c, Scene
             tstar_bound(sqrtf(k2), s2, fmaxf(0.5f * (rr + 1.0f / rr) * 1.00001f, 1.0f), L, m, tb, rf);
             float kq2 = k2;
             if (dilute) {
-                const float mumin = fmaxf(__uint_as_float(__float_as_uint(mcam[20]) == 0xffffffffu ? 0u
-                                                          : __float_as_uint(mcam[20])), 0.0f) * 0.99f;
+                const float mumin = fmaxf(mu_lo, 0.0f) * 0.99f;
                 const float tlo = fmaxf(L - rf * 1.001f, 0.0f);
                 const float cf = fmaxf(tlo * tlo * mumin - rho2 * 1.001f, 0.0f);
                 const float s2md = expf(2.0f * lmid) * 1.00001f + rho2;
