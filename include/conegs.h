@@ -110,7 +110,12 @@ enum {
      * same visual cone cuts from the image plane, a cheaper test; fisheye views
      * always use the ray-direction form.  Both forms are conservative, so images are
      * the same either way; the flag exists to check exactly that. */
-    CONEGS_PRETEST_RAY = 1u << 8
+    CONEGS_PRETEST_RAY = 1u << 8,
+    /* No pre-test: the rasteriser and its adjoint fully evaluate every pair of the
+     * tile lists.  Slower, and bitwise the same images, transmittance and adjoint
+     * state as with the pre-test (which only skips pairs that cannot reach
+     * alpha >= 1/255); the flag exists to check that. */
+    CONEGS_PRETEST_OFF = 1u << 9
 };
 
 typedef struct conegs_ctx conegs_ctx;

@@ -27,13 +27,14 @@ from ._lib import ConegsError, check, lib
 
 PINHOLE, KB_FISHEYE = 0, 1
 F32, BF16, F16 = 0, 1, 2
-FILTER_NONE, COMP_ADDITIVE, KEEP_FOR_BACKWARD, PROFILE, FILTER_ISO, FILTER_ZF, BIN_UT, ORDER_TSTAR, PRETEST_RAY = (
-    1, 2, 4, 8, 16, 32, 64, 128, 256)
+(FILTER_NONE, COMP_ADDITIVE, KEEP_FOR_BACKWARD, PROFILE, FILTER_ISO, FILTER_ZF, BIN_UT, ORDER_TSTAR, PRETEST_RAY,
+ PRETEST_OFF) = (1, 2, 4, 8, 16, 32, 64, 128, 256, 512)
 
 _DTYPE_CODE = {torch.float32: F32, torch.bfloat16: BF16, torch.float16: F16}
 
 __all__ = ["Context", "View", "ConegsError", "PINHOLE", "KB_FISHEYE", "FILTER_NONE", "COMP_ADDITIVE",
            "KEEP_FOR_BACKWARD", "PROFILE", "FILTER_ISO", "FILTER_ZF", "BIN_UT", "ORDER_TSTAR", "PRETEST_RAY",
+           "PRETEST_OFF",
            "radix_sort_pairs", "render_fn", "measure_fp32_peak"]
 
 

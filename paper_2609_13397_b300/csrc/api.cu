@@ -37,8 +37,9 @@ cudaError_t launch_bin_emit(const CamParams &c, const float *binrec, const float
                             const float4 *gell, bool ut, cudaStream_t s);
 cudaError_t launch_scene_cache(const SceneParams &sp, float *W, float *sig_eff, cudaStream_t s);
 cudaError_t launch_view_records(const CamParams &c, const SceneParams &sp, const float *mcam, float mzf,
-                                int fov_cull, int pixtest, int dilute, float4 *rec, float4 *gview, float2 *gcone, uint8_t *gflag,
-                                float4 *gell, unsigned long long *nflat, uint8_t *gflat, cudaStream_t s);
+                                int fov_cull, int pretest, int pixtest, int dilute, float4 *rec, float4 *gview,
+                                float2 *gcone, uint8_t *gflag, float4 *gell, unsigned long long *nflat,
+                                uint8_t *gflat, cudaStream_t s);
 int64_t scan_scratch_words(int64_t n);
 cudaError_t exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *scratch, int pred,
                            cudaStream_t s);
@@ -593,7 +594,8 @@ static conegs_status render_front(conegs_view *v, unsigned flags, cudaStream_t s
     // [4] pairs of flat Gaussians, [5] scratch (flat slot counter)
     CUDA_TRY(cudaMemsetAsync(v->sums.as<unsigned long long>() + 2, 0, 2 * sizeof(unsigned long long), s));
     CUDA_TRY(launch_view_records(c, sp, v->mcam.as<float>(), zf_bound(c, flags), (flags & CONEGS_BIN_UT) ? 0 : 1,
-                                 pixel_pretest(c, flags), (flags & (CONEGS_FILTER_NONE | CONEGS_FILTER_ZF)) ? 0 : 1,
+                                 (flags & CONEGS_PRETEST_OFF) ? 0 : 1, pixel_pretest(c, flags),
+                                 (flags & (CONEGS_FILTER_NONE | CONEGS_FILTER_ZF)) ? 0 : 1,
                                  v->rec.as<float4>(), v->gview.as<float4>(),
                                  v->gcone.as<float2>(), v->gflag.as<uint8_t>(), v->gell.as<float4>(),
                                  v->sums.as<unsigned long long>() + 3, v->gflat.as<uint8_t>(), s));

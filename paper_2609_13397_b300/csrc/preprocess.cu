@@ -244,7 +244,8 @@ __device__ void footprint_range(const CamParams &c, const float *__restrict__ mc
 // chains): four CTAs per SM (64 registers, a few bytes of spill) run it faster
 // than three at the 79 registers it would otherwise take.
 __global__ void __launch_bounds__(256, 4) view_records_kernel(CamParams c, SceneParams sp, const float *__restrict__ mcam,
-                                                           float mzf, int fov_cull, int pixtest, int dilute,
+                                                           float mzf, int fov_cull, int pretest, int pixtest,
+                                                           int dilute,
                                                            float4 *__restrict__ rec, float4 *__restrict__ gview,
                                                            float2 *__restrict__ gcone,
                                                            uint8_t *__restrict__ gflag,
@@ -319,7 +320,9 @@ __global__ void __launch_bounds__(256, 4) view_records_kernel(CamParams c, Scene
     float g[3] = {0.f, 0.f, 0.f}, C[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float pu[3] = {dx, dy, dz};
     float4 pix4 = make_float4(0.f, 0.f, 0.f, 0.f), pix5 = make_float4(0.f, -1.0f, 0.f, 0.f);   // rejects every pixel
-    {
+    if (!pretest) {
+        pix5 = make_float4(0.f, 1.0f, 0.f, 0.f);        // every pixel (g = C = 0: every ray)
+    } else {
         const float sig = 1.0f / (1.0f + expf(-load_scalar(sp.logits, i, sp.storage)));
         const float k2 = 2.0f * logf(255.0f * sig);
         const float l0 = sp.log_scales[3 * i], l1 = sp.log_scales[3 * i + 1], l2 = sp.log_scales[3 * i + 2];
@@ -337,8 +340,12 @@ __global__ void __launch_bounds__(256, 4) view_records_kernel(CamParams c, Scene
             C[0] = C[1] = C[2] = 100.0f;
         } else if (L > 0.0f) {
             float tb, rf;
-            const float rr = sqrtf(s2 / s2mn);    // s_max / s_min; |f_i| <= (r + 1/r)/2 |delta_i|
-            tstar_bound(sqrtf(k2), s2, fmaxf(0.5f * (rr + 1.0f / rr) * 1.00001f, 1.0f), L, m, tb, rf);
+            // s_max / s_min: the world half-edges are f = (I - d w^T) delta with
+            // |I - d w^T| <= (r + 1/r)/2 (Kantorovich), so the world footprint's
+            // largest eigenvalue is at most ((r + 1/r)/2)^2 t*^2 mlam: the t* bound
+            // holds with mlam in place of the rule's trace bound m
+            const float rr = sqrtf(s2 / s2mn);
+            tstar_bound(sqrtf(k2), s2, fmaxf(0.5f * (rr + 1.0f / rr) * 1.00001f, 1.0f), L, mlam, tb, rf);
             float kq2 = k2;
             if (dilute) {
                 const float mumin = fmaxf(mu_lo, 0.0f) * 0.99f;
@@ -409,11 +416,13 @@ cudaError_t launch_scene_cache(const SceneParams &sp, float *W, float *sig_eff, 
 }
 
 cudaError_t launch_view_records(const CamParams &c, const SceneParams &sp, const float *mcam, float mzf,
-                                int fov_cull, int pixtest, int dilute, float4 *rec, float4 *gview, float2 *gcone,
+                                int fov_cull, int pretest, int pixtest, int dilute, float4 *rec, float4 *gview,
+                                float2 *gcone,
                                 uint8_t *gflag,
                                 float4 *gell, unsigned long long *nflat, uint8_t *gflat, cudaStream_t s) {
     if (sp.n == 0) return cudaSuccess;
-    view_records_kernel<<<(unsigned)div_up(sp.n, 256), 256, 0, s>>>(c, sp, mcam, mzf, fov_cull, pixtest, dilute, rec,
+    view_records_kernel<<<(unsigned)div_up(sp.n, 256), 256, 0, s>>>(c, sp, mcam, mzf, fov_cull, pretest, pixtest,
+                                                                    dilute, rec,
                                                                     gview, gcone, gflag, gell, nflat, gflat);
     note_launches(1);
     return cudaGetLastError();

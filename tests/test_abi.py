@@ -45,3 +45,14 @@ def test_arguments_rejected_before_any_device_work():
     assert L.conegs_render(None, None, None, 0, None) == 1
     assert b"NULL" in L.conegs_last_error()
     assert L.conegs_set_scene(None, 0, None, None, None, None, None, 0, 0, None, None) == 1
+
+
+def test_binding_flags_match_the_header():
+    """Every render flag of the header's enum has the same value in the binding."""
+    import paper_2609_13397_b300 as cg
+    src = open(os.path.join(ROOT, "include", "conegs.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    flags = re.findall(r"\bCONEGS_([A-Z_]+)\s*=\s*1u\s*<<\s*(\d+)", src)
+    assert len(flags) >= 10
+    for name, shift in flags:
+        assert getattr(cg, name) == 1 << int(shift), name
