@@ -175,7 +175,9 @@ def test_pretest_drops_no_contributing_pair(cg, name):
     # (walked counts whole staged batches, so a pixel that stops mid-batch has
     # walked a few entries more)
     assert st_a["n_evaluated"] <= st_b["n_evaluated"] <= st_b["n_walked"]
-    for k in g_a:                                   # equal up to the order of the atomic sums
+    # the same per-pair contributions, summed by atomics in a run-dependent order:
+    # FP32 rounding of long sums with cancellation, at the scale of the largest entry
+    for k in g_a:
         a, b = g_a[k], g_b[k]
-        bound = 1e-5 * float(b.abs().max()) + 1e-4 * b.abs()
+        bound = 1e-4 * float(b.abs().max()) + 1e-4 * b.abs()
         assert bool(((a - b).abs() <= bound).all()), (k, float((a - b).abs().max()))
