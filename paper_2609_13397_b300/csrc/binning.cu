@@ -132,7 +132,8 @@ __global__ void super_table_kernel(CamParams c, const float *__restrict__ table,
 // half-angle, for the binning candidate box).  Fisheye cameras also get
 // out[2 + j], j = 0..16: the largest sin(gamma_t / 2) over the tiles whose axis
 // lies within theta_lim j / 16 of the optical axis (a non-decreasing envelope;
-// tile cones grow toward a fisheye's rim).  out[19]: the half-angle (rad,
+// tile cones grow toward a fisheye's rim).  out[MCAM_MMIN]: the smallest m over
+// the valid tiles (3e38 without one).  out[19]: the half-angle (rad,
 // widened) of a cone around the optical axis that contains every tile cone.
 constexpr int GAMMA_BANDS = 16;
 
@@ -142,12 +143,13 @@ __global__ void max_m_kernel(CamParams c, const float *__restrict__ table, int n
     if (threadIdx.x <= GAMMA_BANDS) s_band[threadIdx.x] = 0u;
     if (threadIdx.x == 0) s_reach = 0u;
     __syncthreads();
-    float m = 0.0f, g = 0.0f, reach = 0.0f;
+    float m = 0.0f, g = 0.0f, reach = 0.0f, mlo = 3.0e38f;
     for (int t = threadIdx.x; t < nt; t += blockDim.x) {
         const float *r = table + 6 * (size_t)t;
         m = fmaxf(m, r[5]);
         g = fmaxf(g, r[3]);
         if (r[3] >= 0.0f) {
+            mlo = fminf(mlo, r[5]);
             // the camera's cone: every tile cone lies within `reach` of the optical axis
             const float cz = r[0] * c.R[2] + r[1] * c.R[5] + r[2] * c.R[8];
             reach = fmaxf(reach, acosf(fminf(fmaxf(cz, -1.0f), 1.0f)) + 2.0f * asinf(fminf(r[3], 1.0f)));
@@ -164,23 +166,28 @@ __global__ void max_m_kernel(CamParams c, const float *__restrict__ table, int n
         m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
         g = fmaxf(g, __shfl_xor_sync(0xffffffffu, g, o));
         reach = fmaxf(reach, __shfl_xor_sync(0xffffffffu, reach, o));
+        mlo = fminf(mlo, __shfl_xor_sync(0xffffffffu, mlo, o));
     }
     if ((threadIdx.x & 31) == 0) atomicMax(&s_reach, __float_as_uint(reach));   // non-negative: bit order
-    __shared__ float sm[32], sg[32];
+    __shared__ float sm[32], sg[32], slo[32];
     if ((threadIdx.x & 31) == 0) {
         sm[threadIdx.x >> 5] = m;
         sg[threadIdx.x >> 5] = g;
+        slo[threadIdx.x >> 5] = mlo;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
             m = fmaxf(m, sm[w]);
             g = fmaxf(g, sg[w]);
+            mlo = fminf(mlo, slo[w]);
         }
         m = fmaxf(m, sm[0]);
         g = fmaxf(g, sg[0]);
+        mlo = fminf(mlo, slo[0]);
         out[0] = m;
         out[1] = g;
+        out[MCAM_MMIN] = mlo;     // 3e38 without a valid tile
         float env = 0.0f;
         for (int j = 0; j <= GAMMA_BANDS; ++j) {
             env = c.model != 0 ? fmaxf(env, __uint_as_float(s_band[j])) : g;
@@ -542,7 +549,8 @@ __device__ __forceinline__ uint32_t bin_walk_supers(const CamParams &c, const fl
                                                     const float2 half, const float *__restrict__ table,
                                                     const float *__restrict__ super, float mzf, uint32_t gid,
                                                     uint32_t base, uint32_t *__restrict__ out_tile,
-                                                    uint32_t *__restrict__ out_gid, const float *ell) {
+                                                    uint32_t *__restrict__ out_gid, const float *ell,
+                                                    const float2 lo) {
     const int lane = threadIdx.x & 31;
     const int nsup = c.supers_x * c.supers_y;
     uint32_t cnt = 0;
@@ -567,7 +575,7 @@ __device__ __forceinline__ uint32_t bin_walk_supers(const CamParams &c, const fl
                     float tt[6];
                     tile_record(table, tile, mzf, tt);
                     if (cone_prefilter(gv, half, tt)) {
-                        const int f = rule_test_fast(g, gv, tt);
+                        const int f = rule_pass_lo(lo.x, lo.y, gv, tt) ? 1 : rule_test_fast(g, gv, tt);
                         tp = f == 2 ? rule_test(g, gv, tt) : f == 1;
                     }
                     if (tp && ell) tp = ell_keep<32>(c, ell, gv, tt, tx, ty);
@@ -594,7 +602,7 @@ __device__ __forceinline__ uint32_t bin_walk_box(const CamParams &c, const float
                                                  int tx0, int ty0, int bw, uint32_t nb, uint32_t gid, uint32_t base,
                                                  uint32_t m[8], uint32_t *__restrict__ list,
                                                  uint32_t *__restrict__ out_tile, uint32_t *__restrict__ out_gid,
-                                                 bool ut, const float *ell) {
+                                                 bool ut, const float *ell, const float2 lo) {
     const int lane = threadIdx.x & 31;
     uint32_t cnt = 0;
     int qy = 0, qx = lane;                     // candidate k0 + lane = qy * bw + qx
@@ -614,7 +622,7 @@ __device__ __forceinline__ uint32_t bin_walk_box(const CamParams &c, const float
                 float tt[6];
                 tile_record(table, tile, mzf, tt);
                 if (cone_prefilter(gv, half, tt)) {
-                    const int f = rule_test_fast(g, gv, tt);
+                    const int f = rule_pass_lo(lo.x, lo.y, gv, tt) ? 1 : rule_test_fast(g, gv, tt);
                     tp = f == 2 ? rule_test(g, gv, tt) : f == 1;
                 }
                 if (tp && ell) tp = ell_keep<32>(c, ell, gv, tt, tx0 + qx, ty0 + qy);
@@ -665,6 +673,7 @@ __global__ void __launch_bounds__(32 * BIN_WARPS, 4) bin_kernel(CamParams c, Gau
     __shared__ float s_g[BIN_WARPS][5][32];        // kap, ks, kr, r1sq, s2 (flag is 1 for boxed slots)
     __shared__ float4 s_gv[BIN_WARPS][32];
     __shared__ float2 s_half[BIN_WARPS][32];
+    __shared__ float2 s_lo[BIN_WARPS][32];         // rule_pass_lo's cone at the view's smallest m
     __shared__ int4 s_box[BIN_WARPS][32];          // tx0, ty0, box width, bits: cached (1), UT (2), silhouette (4)
     __shared__ float s_inv[BIN_WARPS][32];         // 1 / box width
     __shared__ uint4 s_mask[BIN_WARPS][2][32];     // MODE 1: cached pass mask (8 words)
@@ -681,6 +690,7 @@ __global__ void __launch_bounds__(32 * BIN_WARPS, 4) bin_kernel(CamParams c, Gau
     float g[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float4 gv = make_float4(0.f, 0.f, 0.f, 0.f);
     float2 half = make_float2(0.f, 1.f);
+    float2 lo2 = make_float2(RULE_NONE, 0.f);
     int tx0 = 0, tx1 = -1, ty0 = 0, ty1 = -1;
     if (have) {
         fl = gflag[gid];
@@ -736,6 +746,7 @@ __global__ void __launch_bounds__(32 * BIN_WARPS, 4) bin_kernel(CamParams c, Gau
             g[5] = (float)fl;
             gv = gview[gid];
             half = gcone[gid];
+            lo2 = rule_lo(g, gv.w, fmaxf(mcam[MCAM_MMIN], mzf));
             if (fl == 1) {
                 // silhouette record of the rule's bounding ellipsoid (from the view records)
                 el0 = ua.ell[3 * (size_t)gid];
@@ -774,6 +785,7 @@ __global__ void __launch_bounds__(32 * BIN_WARPS, 4) bin_kernel(CamParams c, Gau
     s_g[wid][3][lane] = g[3]; s_g[wid][4][lane] = g[4];
     s_gv[wid][lane] = gv;
     s_half[wid][lane] = half;
+    s_lo[wid][lane] = lo2;
     s_box[wid][lane] = make_int4(tx0, ty0, tx1 - tx0 + 1, (cached ? 1 : 0) | (utslot ? 2 : 0) | (ellv ? 4 : 0));
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -851,7 +863,8 @@ __global__ void __launch_bounds__(32 * BIN_WARPS, 4) bin_kernel(CamParams c, Gau
                     float tt[6];
                     tile_record(table, tile, mzf, tt);
                     if (cone_prefilter(sgv, s_half[wid][sl], tt)) {
-                        const int f = rule_test_fast(gg, sgv, tt);
+                        const float2 lo = s_lo[wid][sl];
+                        const int f = rule_pass_lo(lo.x, lo.y, sgv, tt) ? 1 : rule_test_fast(gg, sgv, tt);
                         tp = f == 2 ? rule_test(gg, sgv, tt) : f == 1;
                     }
                     if (tp && (bx.w & 4)) tp = ell_keep<32>(c, &s_ell[wid][0][sl], sgv, tt, bx.x + kx, bx.y + ky);
@@ -913,7 +926,8 @@ __global__ void __launch_bounds__(32 * BIN_WARPS, 4) bin_kernel(CamParams c, Gau
         const float *sel = &s_ell[wid][0][sl];
         const bool sev = (s_box[wid][sl].w & 4) != 0;
         const uint32_t wc = bin_walk_box<MODE, UT>(c, gg, sgv, sh, table, mzf, btx0, bty0, bw, bnb, sgid, sbase,
-                                                   wm, lst, out_tile, out_gid, gg[5] == 3.0f, sev ? sel : nullptr);
+                                                   wm, lst, out_tile, out_gid, gg[5] == 3.0f, sev ? sel : nullptr,
+                                                   s_lo[wid][sl]);
         if (lane == sl) {
             cnt = wc;
 #pragma unroll
@@ -954,7 +968,7 @@ __global__ void __launch_bounds__(32 * BIN_WARPS, 4) bin_kernel(CamParams c, Gau
         const float *sel = &s_ell[wid][0][sl];
         const bool sev = (s_box[wid][sl].w & 4) != 0;
         const uint32_t wc = bin_walk_supers<MODE>(c, gg, sgv, sh, table, super, mzf, sgid, sbase, out_tile, out_gid,
-                                                  sev ? sel : nullptr);
+                                                  sev ? sel : nullptr, s_lo[wid][sl]);
         if (lane == sl) cnt = wc;
     }
     if (MODE == 0 && have) {

@@ -25,7 +25,8 @@ constexpr int BINREC = 12;        // floats per Gaussian of the binning rule's s
 constexpr int FP_BANDS = 64;
 constexpr int FP_MIN = 20;                        // offset of the smallest eigenvalue block
 constexpr int FP_MAX = FP_MIN + 1 + FP_BANDS;     // offset of the largest eigenvalue block
-constexpr int MCAM_FLOATS = FP_MAX + 1 + FP_BANDS;
+constexpr int MCAM_MMIN = FP_MAX + 1 + FP_BANDS;   // the smallest footprint bound m over the valid tiles
+constexpr int MCAM_FLOATS = MCAM_MMIN + 1;
 
 // Camera passed by value to kernels.
 struct CamParams {

@@ -159,13 +159,11 @@ __device__ __forceinline__ void rule_gauss_view(const CamParams &c, const float 
     u[0] = r_div(v0, L); u[1] = r_div(v1, L); u[2] = r_div(v2, L);
 }
 
-// The per (Gaussian, tile) test.  g: scene rec (kap ks kr r1sq s2 flag); gv: u0 u1 u2 L.
-__device__ __forceinline__ bool rule_test(const float *g, const float4 gv, const float *t) {
-    if (t[3] < 0.0f) return false;
-    if (g[5] == 0.0f) return false;
-    if (g[5] == 2.0f) return true;
-    const float L = gv.w, kap = g[0], ks = g[1], kr = g[2], r1sq = g[3], s2 = g[4];
-    const float m = t[5];
+// The Gaussian's side of the rule at footprint bound m: sin and cos of half
+// the half-angle beta of its cone (sbh, cbh).  Returns true when every valid
+// tile passes at this m (L <= r_f or r_p >= L).  The rule is monotone in m.
+__device__ __forceinline__ bool rule_half(const float *g, const float L, const float m, float &sbh, float &cbh) {
+    const float kap = g[0], ks = g[1], kr = g[2], r1sq = g[3], s2 = g[4];
     float sm = r_sqrt(m);
     float cc = r_mul(kr, sm);
     // two valid bounds on |x* - mu| and t*, combined by min (monotone in m)
@@ -186,8 +184,18 @@ __device__ __forceinline__ bool rule_test(const float *g, const float4 gv, const
     float sb = r_div(rp, L);
     float cb = r_sqrt(r_sub(1.0f, r_mul(sb, sb)));
     float sh2 = r_div(r_mul(sb, sb), r_mul(2.0f, r_add(1.0f, cb)));
-    float sbh = r_sqrt(sh2);
-    float cbh = r_sqrt(r_sub(1.0f, sh2));
+    sbh = r_sqrt(sh2);
+    cbh = r_sqrt(r_sub(1.0f, sh2));
+    return false;
+}
+
+// The per (Gaussian, tile) test.  g: scene rec (kap ks kr r1sq s2 flag); gv: u0 u1 u2 L.
+__device__ __forceinline__ bool rule_test(const float *g, const float4 gv, const float *t) {
+    if (t[3] < 0.0f) return false;
+    if (g[5] == 0.0f) return false;
+    if (g[5] == 2.0f) return true;
+    float sbh, cbh;
+    if (rule_half(g, gv.w, t[5], sbh, cbh)) return true;
     float sphi = r_add(r_mul(sbh, t[4]), r_mul(cbh, t[3]));
     float e0 = r_sub(gv.x, t[0]), e1 = r_sub(gv.y, t[1]), e2 = r_sub(gv.z, t[2]);
     float ch2 = r_add(r_add(r_mul(e0, e0), r_mul(e1, e1)), r_mul(e2, e2));
@@ -245,6 +253,36 @@ __device__ __forceinline__ int rule_test_fast(const float *g, const float4 gv, c
     if (ch2 < l2 * (1.0f - 1e-4f) - 1e-12f) return 1;
     if (ch2 > l2 * (1.0f + 1e-4f) + 1e-12f) return 0;
     return 2;
+}
+
+// A tile the exact rule certainly keeps: its axis lies inside the Gaussian's
+// cone at a footprint bound m_lo no larger than the tile's own (sbh_lo, cbh_lo
+// from rule_half at m_lo; sbh_lo = RULE_ALL when every valid tile passes at
+// m_lo), with a relative margin of 1e-5.  The rule is monotone in m, and
+// sin((beta + gamma)/2) grows with beta while (beta + gamma)/2 stays below 90
+// degrees (beta <= 90, tile cones below 90 degrees here); the margin is far
+// above the rounding of this test and of the rule's chain (both
+// well-conditioned here: sphi is a sum of non-negative terms).
+// sbh_lo = RULE_NONE: no such bound (the test never decides).
+constexpr float RULE_ALL = 1e30f, RULE_NONE = -1.0f;
+__device__ __forceinline__ bool rule_pass_lo(const float sbh_lo, const float cbh_lo, const float4 gv, const float *t) {
+    if (t[3] < 0.0f || sbh_lo < 0.0f) return false;
+    if (sbh_lo == RULE_ALL) return true;
+    if (t[3] > 0.7f) return false;
+    const float e0 = gv.x - t[0], e1 = gv.y - t[1], e2 = gv.z - t[2];
+    const float ch2 = e0 * e0 + e1 * e1 + e2 * e2;
+    const float lim = (2.0f * 1.0001f) * (sbh_lo * t[4] + cbh_lo * t[3]) + 4e-6f;
+    return ch2 <= lim * lim * 0.99999f;
+}
+
+// (sbh_lo, cbh_lo) of rule_pass_lo for a Gaussian with scene record g (flag
+// g[5]) at the view's smallest footprint bound m_lo.
+__device__ __forceinline__ float2 rule_lo(const float *g, const float L, const float m_lo) {
+    if (g[5] == 2.0f) return make_float2(RULE_ALL, 0.0f);
+    if (g[5] != 1.0f || !(m_lo >= 0.0f && m_lo < 1e30f)) return make_float2(RULE_NONE, 0.0f);
+    float sbh, cbh;
+    if (rule_half(g, L, m_lo, sbh, cbh)) return make_float2(RULE_ALL, 0.0f);
+    return make_float2(sbh, cbh);
 }
 
 // ---------------------------------------------------------------- silhouette ellipse (pinhole cameras)

@@ -214,19 +214,39 @@ cudaError_t launch_gather(const uint32_t *src, const uint32_t *idx, int64_t n, u
     return cudaGetLastError();
 }
 
-// Per-tile [begin, end) ranges from the tile-sorted key array.
+// Per-tile [begin, end) ranges from the tile-sorted key array: a tile's range
+// starts where its key differs from the one before and ends where it differs
+// from the one after.  Each thread takes four consecutive keys with one 16-byte
+// load (keys 16-byte aligned) and reads the two neighbours once.
 __global__ void ranges_kernel(const uint32_t *__restrict__ keys, int64_t n, uint2 *__restrict__ ranges) {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    const uint32_t t = keys[p];
-    if (p == 0 || keys[p - 1] != t) ranges[t].x = (uint32_t)p;
-    if (p == n - 1 || keys[p + 1] != t) ranges[t].y = (uint32_t)(p + 1);
+    const int64_t p0 = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    if (p0 >= n) return;
+    uint32_t k[4];
+    if (p0 + 4 <= n) {
+        const uint4 v = *reinterpret_cast<const uint4 *>(keys + p0);
+        k[0] = v.x; k[1] = v.y; k[2] = v.z; k[3] = v.w;
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) k[j] = p0 + j < n ? keys[p0 + j] : 0u;
+    }
+    uint32_t prev = p0 > 0 ? keys[p0 - 1] : ~k[0];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int64_t p = p0 + j;
+        if (p >= n) break;
+        const uint32_t t = k[j];
+        const uint32_t next = p + 1 >= n ? ~t : (j < 3 ? k[j + 1] : keys[p + 1]);
+        if (prev != t) ranges[t].x = (uint32_t)p;
+        if (next != t) ranges[t].y = (uint32_t)(p + 1);
+        prev = t;
+    }
 }
 
 cudaError_t launch_ranges(const uint32_t *keys, int64_t n, uint2 *ranges, int ntiles, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)ntiles, s);
     if (e != cudaSuccess || n == 0) return e;
-    ranges_kernel<<<(unsigned)div_up(n, 256), 256, 0, s>>>(keys, n, ranges);
+    if (reinterpret_cast<uintptr_t>(keys) % 16 != 0) return cudaErrorMisalignedAddress;
+    ranges_kernel<<<(unsigned)div_up(div_up(n, 4), 256), 256, 0, s>>>(keys, n, ranges);
     note_launches(1);
     return cudaGetLastError();
 }
