@@ -6,7 +6,7 @@
 //   scan      exclusive scan of the 256*G counters (digit-major)
 //   downsweep per tile (4096 items; 1024 for sorts of up to 2^20 items, so that
 //             small sorts still spread over the SMs): each warp ranks its items in lane order
-//             with __match_any_sync (stable), warps are offset by a per-digit
+//             with bit-sliced ballots (stable), warps are offset by a per-digit
 //             scan across warps; the tile is rearranged in shared memory in
 //             digit order and written out so that runs of one digit land on
 //             consecutive addresses (coalesced stores).
@@ -253,6 +253,19 @@ cudaError_t launch_ranges(const uint32_t *keys, int64_t n, uint2 *ranges, int nt
 
 // ---------------------------------------------------------------- radix sort
 
+// Lanes of the warp holding the same digit as this lane (bit-sliced: one ballot
+// per digit bit); lanes without an item (ok false) match only themselves.
+__device__ __forceinline__ uint32_t digit_peers(uint32_t dig, int nbits, bool ok) {
+    const uint32_t okm = __ballot_sync(0xffffffffu, ok);
+    uint32_t peers = okm;
+    for (int b = 0; b < nbits; ++b) {
+        const bool on = (dig >> b) & 1u;
+        const uint32_t v = __ballot_sync(0xffffffffu, on);
+        peers &= on ? v : ~v;
+    }
+    return ok ? peers : (1u << (threadIdx.x & 31));
+}
+
 constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
 constexpr int RS_ROUNDS_LARGE = 16;                 // 32-item rounds per warp per tile: 4096-item tiles
@@ -339,7 +352,7 @@ __global__ void __launch_bounds__(RS_THREADS) rs_downsweep(const uint32_t *__res
             const int li = wid * (RS_ROUNDS * 32) + r * 32 + lane;
             const bool ok = li < tn;
             const uint32_t dig = ok ? ((k[r] >> shift) & mask) : (256u + (uint32_t)lane);
-            const uint32_t peers = __match_any_sync(0xffffffffu, dig);
+            const uint32_t peers = digit_peers(dig, __popc(mask), ok);
             const int leader = __ffs(peers) - 1;
             uint32_t old = 0u;
             if (ok && lane == leader) {
@@ -406,7 +419,7 @@ __global__ void __launch_bounds__(RS_THREADS) rs_downsweep(const uint32_t *__res
 // Sorts of at most RS_ONE_MAX items: one CTA does every pass in shared memory
 // (one launch instead of an upsweep, a scan and a scatter per pass), with the
 // same stable ranking as rs_downsweep: each warp ranks its items in lane order
-// (match_any), the warps in order, the digits by an exclusive scan.
+// (digit_peers), the warps in order, the digits by an exclusive scan.
 constexpr int RS_ONE_THREADS = 256;
 constexpr int RS_ONE_WARPS = RS_ONE_THREADS / 32;
 constexpr int RS_ONE_ROUNDS = 8;
@@ -438,7 +451,7 @@ __global__ void __launch_bounds__(RS_ONE_THREADS) rs_one_cta_kernel(uint32_t *__
             k[r] = ok ? sk[cur][li] : 0u;
             v[r] = ok ? sv[cur][li] : 0u;
             const uint32_t dig = ok ? ((k[r] >> shift) & mask) : (256u + (uint32_t)lane);
-            const uint32_t peers = __match_any_sync(0xffffffffu, dig);
+            const uint32_t peers = digit_peers(dig, __popc(mask), ok);
             const int leader = __ffs(peers) - 1;
             uint32_t old = 0u;
             if (ok && lane == leader) {
