@@ -30,9 +30,10 @@ namespace conegs {
 // list) or per later segment of a split list.  A segment is walked back to
 // front from the state the forward's suffix pass left: T after the segment and
 // the colour composited behind it; pixels whose walk ended before the segment
-// sit out.
+// sit out.  Ten CTAs per SM leave it 96 registers and no spills; at twelve (80
+// registers) the local-memory loads of the spilled pair state stalled the walk.
 template <bool FILTER, bool FIRST, bool PIX>
-__global__ void __launch_bounds__(TILE_PX, 12) raster_bwd_kernel(const RasterArgs a, const SegArgs g,
+__global__ void __launch_bounds__(TILE_PX, 10) raster_bwd_kernel(const RasterArgs a, const SegArgs g,
                                                              const float *__restrict__ dL_drgb,
                                                              const float *__restrict__ dL_dT,
                                                              const float *__restrict__ final_T,
