@@ -1,10 +1,10 @@
 // K4: device scan, compaction and stable LSD radix sort of (key, value) pairs.
 //
 // Radix sort: 8-bit digits, reduce-then-scan.  A fixed grid of G blocks
-// each owns one contiguous chunk (a multiple of 4096 items); per pass
+// each owns one contiguous chunk (a multiple of its tile size); per pass
 //   upsweep   per-block digit histogram             -> counts[digit][block]
 //   scan      exclusive scan of the 256*G counters (digit-major)
-//   downsweep per tile (4096 items; 1024 for sorts of up to 2^20 items, so that
+//   downsweep per tile (3072 items; 1024 for sorts of up to 2^20 items, so that
 //             small sorts still spread over the SMs): each warp ranks its items in lane order
 //             with bit-sliced ballots (stable), warps are offset by a per-digit
 //             scan across warps; the tile is rearranged in shared memory in
@@ -268,9 +268,9 @@ __device__ __forceinline__ uint32_t digit_peers(uint32_t dig, int nbits, bool ok
 
 constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
-constexpr int RS_ROUNDS_LARGE = 16;                 // 32-item rounds per warp per tile: 4096-item tiles
+constexpr int RS_ROUNDS_LARGE = 12;                 // 32-item rounds per warp per tile: 3072-item tiles
 constexpr int RS_ROUNDS_SMALL = 4;                  // 1024-item tiles for sorts of up to RS_SMALL_N items
-constexpr int64_t RS_SMALL_N = 1 << 20;             // (their 4096-item tiles would not fill the SMs)
+constexpr int64_t RS_SMALL_N = 1 << 20;             // (their 3072-item tiles would not fill the SMs)
 
 // Resident scatter CTAs per SM of the tile size (queried once per device): the
 // grid is one wave of them, each CTA walking its own contiguous chunk.
